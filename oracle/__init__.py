@@ -1,0 +1,235 @@
+"""FP64 CPU oracle of the START hot path (test infrastructure only).
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+import this package.  The product library never calls it and has no CPU
+fallback.  ``build()`` compiles ``start_oracle.c`` with gcc (OpenMP, no
+floating-point contraction) into ``oracle/_build/libstart_oracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "start_oracle.c"
+BUILD = HERE / "_build"
+LIB = BUILD / "libstart_oracle.so"
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle shared library (idempotent)."""
+    BUILD.mkdir(exist_ok=True)
+    if not force and LIB.exists() and LIB.stat().st_mtime >= SRC.stat().st_mtime:
+        return LIB
+    tmp = BUILD / f".libstart_oracle.{os.getpid()}.so"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", str(SRC), "-o", str(tmp), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class OrcParams(C.Structure):
+    _fields_ = [("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
+                ("alpha_A", C.c_double), ("alpha_B", C.c_double),
+                ("src_leaf", C.c_int), ("ptree_leaf", C.c_int),
+                ("diffuse", C.c_int), ("pad_", C.c_int)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(str(build()))
+        vp, lp, ip, dp, fp = C.c_void_p, C.c_long, C.c_int, C.c_double, C.c_float
+        P = C.POINTER
+        lib.orc_create.restype = vp
+        lib.orc_create.argtypes = [P(OrcParams)]
+        lib.orc_destroy.argtypes = [vp]
+        lib.orc_threads.restype = ip
+        lib.orc_build.restype = ip
+        lib.orc_build.argtypes = [vp, vp, vp, lp, vp, vp, lp, vp]
+        lib.orc_frame.argtypes = [vp, vp]
+        lib.orc_keys.argtypes = [vp, ip, vp]
+        lib.orc_perm.argtypes = [vp, ip, vp]
+        lib.orc_tree_size.restype = lp
+        lib.orc_tree_size.argtypes = [vp, ip]
+        lib.orc_tree_get.argtypes = [vp, ip] + [vp] * 9
+        lib.orc_nbr_total.restype = lp
+        lib.orc_nbr_total.argtypes = [vp]
+        lib.orc_nbr_get.argtypes = [vp, vp, vp]
+        lib.orc_set_emitters.argtypes = [vp, vp, vp]
+        lib.orc_emitter_L.restype = dp
+        lib.orc_emitter_L.argtypes = [vp, lp]
+        lib.orc_list.restype = lp
+        lib.orc_list.argtypes = [vp, ip, fp, lp, vp, lp]
+        lib.orc_march.restype = dp
+        lib.orc_march.argtypes = [vp, lp, vp, vp, vp, vp, lp, vp]
+        lib.orc_gamma.restype = ip
+        lib.orc_gamma.argtypes = [vp, vp, fp, vp, lp, vp, vp]
+        lib.orc_ionize.argtypes = [vp, vp, vp, vp, dp, lp, vp, vp]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def threads() -> int:
+    return int(_load().orc_threads())
+
+
+class Oracle:
+    """One oracle problem: particles, sources, trees and neighbour lists.
+
+    Arrays are float32 SoA (3, N) positions, float32 h, float64 luminosities
+    (photons/s) and float64 volumes (length unit^3).  Indices are input
+    (original) indices unless a name says "rank" (sorted Morton order).
+    """
+
+    def __init__(self, pos, h, src_pos, src_L, V=None, *, sigma_cm2, len_unit_cm,
+                 alpha_A, alpha_B, diffuse=False, src_leaf=1, ptree_leaf=8):
+        self.lib = _load()
+        self.params = OrcParams(sigma_cm2, len_unit_cm, alpha_A, alpha_B,
+                                int(src_leaf), int(ptree_leaf), int(bool(diffuse)), 0)
+        self.h_ = self.lib.orc_create(C.byref(self.params))
+        self.diffuse = bool(diffuse)
+        self.pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(3, -1)
+        self.h = np.ascontiguousarray(h, dtype=np.float32)
+        self.src_pos = np.ascontiguousarray(src_pos, dtype=np.float32).reshape(3, -1)
+        self.src_L = np.ascontiguousarray(src_L, dtype=np.float64)
+        self.V = None if V is None else np.ascontiguousarray(V, dtype=np.float64)
+        self.np_ = self.pos.shape[1]
+        self.ns = self.src_pos.shape[1]
+        rc = self.lib.orc_build(self.h_, _p(self.pos), _p(self.h), self.np_, _p(self.src_pos),
+                                _p(self.src_L), self.ns, _p(self.V))
+        if rc != 0:
+            raise ValueError(f"oracle build failed: {rc}")
+
+    @classmethod
+    def from_workload(cls, w, **over):
+        kw = dict(sigma_cm2=w.params["sigma_cm2"], len_unit_cm=w.params["len_unit_cm"],
+                  alpha_A=w.params["alpha_A"], alpha_B=w.params["alpha_B"],
+                  diffuse=w.diffuse, src_leaf=w.params.get("src_leaf", 1))
+        kw.update(over)
+        return cls(w.pos, w.h, w.src_pos, w.src_L, w.V, **kw)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h_", None):
+                self.lib.orc_destroy(self.h_)
+                self.h_ = None
+        except Exception:
+            pass
+
+    # --- structure ---------------------------------------------------
+    def frame(self):
+        out = np.zeros(4)
+        self.lib.orc_frame(self.h_, _p(out))
+        return out[:3].copy(), float(out[3])
+
+    def keys(self, which: int):
+        n = self.np_ if which == 0 else self.ns
+        out = np.zeros(n, dtype=np.uint64)
+        self.lib.orc_keys(self.h_, which, _p(out))
+        return out
+
+    def perm(self, which: int):
+        n = self.np_ if which == 0 else self.ns
+        out = np.zeros(n, dtype=np.int64)
+        self.lib.orc_perm(self.h_, which, _p(out))
+        return out
+
+    def tree(self, which: int) -> dict:
+        """which: 0 particle tree, 1 source tree, 2 emitter tree."""
+        n = int(self.lib.orc_tree_size(self.h_, which))
+        t = dict(level=np.zeros(n, np.int32), first=np.zeros(n, np.int64),
+                 count=np.zeros(n, np.int64), skip=np.zeros(n, np.int64),
+                 leaf=np.zeros(n, np.int32), cube=np.zeros((n, 4)), L=np.zeros(n),
+                 M=np.zeros((n, 3)), cen=np.zeros((n, 3), np.float32))
+        self.lib.orc_tree_get(self.h_, which, _p(t["level"]), _p(t["first"]), _p(t["count"]),
+                              _p(t["skip"]), _p(t["leaf"]), _p(t["cube"]), _p(t["L"]),
+                              _p(t["M"]), _p(t["cen"]))
+        return t
+
+    def neighbours(self):
+        tot = int(self.lib.orc_nbr_total(self.h_))
+        off = np.zeros(self.np_ + 1, np.int64)
+        idx = np.zeros(tot, np.int64)
+        self.lib.orc_nbr_get(self.h_, _p(off), _p(idx))
+        return off, idx
+
+    def set_emitters(self, y, n_H):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        n_H = np.ascontiguousarray(n_H, dtype=np.float32)
+        self.lib.orc_set_emitters(self.h_, _p(y), _p(n_H))
+
+    def emitter_L(self):
+        return np.array([self.lib.orc_emitter_L(self.h_, i) for i in range(self.np_)])
+
+    def list(self, theta: float, target: int, which: int = 1):
+        cap = 1 << 12
+        while True:
+            out = np.zeros(cap, np.int64)
+            n = int(self.lib.orc_list(self.h_, which, C.c_float(theta), int(target), _p(out), cap))
+            if n <= cap:
+                return out[:n].copy()
+            cap = n
+
+    def march(self, target: int, rs, nHI, with_chain: bool = False):
+        rs = np.ascontiguousarray(rs, dtype=np.float32)
+        nHI = np.ascontiguousarray(nHI, dtype=np.float32)
+        hops = C.c_long(0)
+        if with_chain:
+            cap = self.np_ + 2
+            chain = np.zeros(cap, np.int64)
+            clen = C.c_long(0)
+            tau = self.lib.orc_march(self.h_, int(target), _p(rs), _p(nHI), C.byref(hops),
+                                     _p(chain), cap, C.byref(clen))
+            return tau, hops.value, chain[:clen.value].copy()
+        tau = self.lib.orc_march(self.h_, int(target), _p(rs), _p(nHI), C.byref(hops),
+                                 None, 0, None)
+        return tau, hops.value
+
+    def gamma(self, nHI, theta: float, targets=None):
+        """Gamma in photons cm^-2 s^-1 at targets (input indices)."""
+        nHI = np.ascontiguousarray(nHI, dtype=np.float32)
+        if targets is None:
+            n = self.np_
+            tp = None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            n = len(targets)
+            tp = _p(targets)
+        out = np.zeros(n)
+        stats = np.zeros(2, np.int64)
+        self.lib.orc_gamma(self.h_, _p(nHI), C.c_float(theta), tp, n, _p(out), _p(stats))
+        self.last_stats = dict(rays=int(stats[0]), hops=int(stats[1]))
+        return out
+
+    def ionize(self, gamma, n_H, y0, dt):
+        gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+        n_H = np.ascontiguousarray(n_H, dtype=np.float32)
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        n = len(y0)
+        y1 = np.zeros(n)
+        nHI = np.zeros(n, np.float32)
+        self.lib.orc_ionize(self.h_, _p(gamma), _p(n_H), _p(y0), float(dt), n, _p(y1), _p(nHI))
+        return y1, nHI
+
+    def step(self, y, n_H, theta: float, dt: float):
+        """One operator-split step: Gamma from the step-start state, then the
+        implicit update.  Returns (gamma, y1)."""
+        nHI = (np.asarray(y, np.float64) * np.asarray(n_H, np.float32).astype(np.float64)).astype(np.float32)
+        if self.diffuse:
+            self.set_emitters(y, n_H)
+        g = self.gamma(nHI, theta)
+        y1, _ = self.ionize(g, n_H, y, dt)
+        return g, y1

@@ -1,0 +1,707 @@
+/*
+ * FP64 CPU oracle of the START radiative-transfer hot path
+ * (Hasegawa & Umemura 2010, "START: SPH with tree-based accelerated
+ * radiative transfer", Sections 2.2.1, 2.2.2, 4.1 and Appendix A).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously
+ * correct statement of what the GPU path computes.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg load it; the
+ * product library never links, calls or falls back to it.  It shares no
+ * code, header or constant with the CUDA sources.
+ *
+ * Everything is FP64 (inputs are the caller's float32 values promoted
+ * exactly), compiled with -ffp-contract=off so that no multiply-add is
+ * fused.  Particles are addressed by their input (original) index.
+ *
+ * Steps, each following the paper's description:
+ *   frame + Morton keys   cubic cells subdivided into 8 (Section 2.2.2)
+ *   octrees               split until a cell holds at most `leaf` members
+ *                         (one radiation source per cell, Section 2.2.2)
+ *   moments               L = sum L_j, r = sum L_j r_j / sum L_j (Section 2.2.2;
+ *                         the same form with N_rec for emitters, Eq. ssum)
+ *   neighbours            particles within 2h of the target (Section 2.2.1)
+ *   walk                  accept a cell when l/d <= theta_crit and its parent
+ *                         was not accepted (Eqs. con1, con2)
+ *   march                 tau_target = tau_up + d_tau, the upstream particle
+ *                         being the neighbour with the smallest angle to the
+ *                         ray (Eq. tau), d_tau = sigma dl (n_t + n_up)/2
+ *   Gamma                 sum L exp(-tau) / (4 pi r^2) (Eq. solution2 with
+ *                         geometric dilution, Eq. ksum / Appendix A)
+ *   ionisation            implicit (backward Euler) hydrogen update
+ *                         (Appendix A), with alpha_B on the spot or alpha_A
+ *                         plus the self term k_self (Eq. kself1) in the
+ *                         diffuse case (Section 4.1)
+ *
+ * Readings of points the paper leaves open (the same readings bind the GPU
+ * path):
+ *   - d in Eq. con1 is the Euclidean distance from the target to the cell
+ *     cube (zero inside); the test is l*l <= theta^2 * d*d.  The root is
+ *     tested by con1 alone.
+ *   - A leaf that is not accepted contributes its sources individually.
+ *   - The upstream particle of j for a source at r_s is the neighbour k of j
+ *     that is strictly closer to r_s than j and maximises
+ *     c_k = (r_s - r_j).(r_k - r_j) / |r_k - r_j| (smallest angle phi);
+ *     ties go to the smaller input index.  When no neighbour is closer the
+ *     chain ends with d_tau = sigma n_j |r_j - r_s|.
+ *   - dl = |r_j - r_s| - |r_up - r_s| (radial difference).
+ *   - n in d_tau is the neutral density n_HI.
+ *   - r in the dilution is floored at 1e-6 of the root cube's side.
+ *   - Single-member cells take the member's position as centroid; cells
+ *     with zero luminosity take their cube centre.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_LEVELS 21
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+    double sigma_cm2;    /* photoionisation cross-section, cm^2 */
+    double len_unit_cm;  /* length unit of positions, cm */
+    double alpha_A;      /* recombination to all levels, cm^3/s */
+    double alpha_B;      /* recombination to excited levels, cm^3/s */
+    int src_leaf;        /* max sources per source-tree leaf (paper: 1) */
+    int ptree_leaf;      /* max particles per particle-tree leaf */
+    int diffuse;         /* 1: every particle emits recombination photons */
+    int pad_;
+} orc_params;
+
+typedef struct {
+    long n, cap;
+    int *level, *leaf;
+    long *first, *count, *skip;
+    double *clo;   /* 3 per node: lower cube corner */
+    double *edge;  /* cube edge */
+    double *L;     /* summed luminosity (photons/s) */
+    double *M;     /* 3 per node: summed L*r */
+    float *cen;    /* 3 per node: luminosity centre rounded to float */
+} otree;
+
+typedef struct {
+    orc_params p;
+    long np, ns;
+    float *px, *py, *pz, *h;
+    float *sx, *sy, *sz;
+    double *sL, *V;
+    double lo[3], side;
+    uint64_t *pkey, *skey;       /* keys in input order */
+    long *pperm, *sperm;         /* sorted rank -> input index */
+    long *prank;                 /* input index -> sorted rank */
+    otree pt, st, et;
+    long *nb_off, *nb_idx;
+    double *eL;                  /* emitter luminosity per particle, photons/s */
+} orc;
+
+/* ------------------------------------------------------------------ */
+/* small helpers                                                       */
+
+static double d2_64(double ax, double ay, double az, double bx, double by, double bz)
+{
+    double dx = ax - bx, dy = ay - by, dz = az - bz;
+    return (dx * dx + dy * dy) + dz * dz;
+}
+
+static void *xmalloc(size_t n) { void *p = malloc(n ? n : 1); return p; }
+
+static void tree_free(otree *t)
+{
+    free(t->level); free(t->leaf); free(t->first); free(t->count); free(t->skip);
+    free(t->clo); free(t->edge); free(t->L); free(t->M); free(t->cen);
+    memset(t, 0, sizeof(*t));
+}
+
+static long tree_push(otree *t)
+{
+    if (t->n == t->cap) {
+        long c = t->cap ? 2 * t->cap : 64;
+        t->level = realloc(t->level, c * sizeof(int));
+        t->leaf = realloc(t->leaf, c * sizeof(int));
+        t->first = realloc(t->first, c * sizeof(long));
+        t->count = realloc(t->count, c * sizeof(long));
+        t->skip = realloc(t->skip, c * sizeof(long));
+        t->clo = realloc(t->clo, 3 * c * sizeof(double));
+        t->edge = realloc(t->edge, c * sizeof(double));
+        t->L = realloc(t->L, c * sizeof(double));
+        t->M = realloc(t->M, 3 * c * sizeof(double));
+        t->cen = realloc(t->cen, 3 * c * sizeof(float));
+        t->cap = c;
+    }
+    return t->n++;
+}
+
+/* ------------------------------------------------------------------ */
+/* frame and Morton keys: cubic cells, Section 2.2.2                    */
+
+/* Common root cube over particles and sources: lower corner = coordinate
+ * minima, side = largest extent (1 when every point coincides). */
+static void make_frame(orc *o)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (long i = 0; i < o->np; ++i) {
+        double v[3] = {o->px[i], o->py[i], o->pz[i]};
+        for (int a = 0; a < 3; ++a) { if (v[a] < lo[a]) lo[a] = v[a]; if (v[a] > hi[a]) hi[a] = v[a]; }
+    }
+    for (long i = 0; i < o->ns; ++i) {
+        double v[3] = {o->sx[i], o->sy[i], o->sz[i]};
+        for (int a = 0; a < 3; ++a) { if (v[a] < lo[a]) lo[a] = v[a]; if (v[a] > hi[a]) hi[a] = v[a]; }
+    }
+    double side = 0.0;
+    for (int a = 0; a < 3; ++a) { double e = hi[a] - lo[a]; if (e > side) side = e; }
+    if (!(side > 0.0)) side = 1.0;
+    for (int a = 0; a < 3; ++a) o->lo[a] = lo[a];
+    o->side = side;
+}
+
+/* 21 bits per axis: q = clamp(floor((x - lo) * 2^21 / side)); the key
+ * interleaves the bits from the top, x above y above z within each level. */
+static uint64_t morton_key(const orc *o, float x, float y, float z)
+{
+    double scale = 2097152.0 / o->side;
+    double v[3] = {x, y, z};
+    uint64_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        double t = floor((v[a] - o->lo[a]) * scale);
+        if (t < 0.0) t = 0.0;
+        if (t > 2097151.0) t = 2097151.0;
+        q[a] = (uint64_t)t;
+    }
+    uint64_t key = 0;
+    for (int b = ORC_LEVELS - 1; b >= 0; --b)
+        key = (key << 3) | (((q[0] >> b) & 1u) << 2) | (((q[1] >> b) & 1u) << 1) | ((q[2] >> b) & 1u);
+    return key;
+}
+
+static const uint64_t *g_sort_keys;
+static int cmp_key_index(const void *a, const void *b)
+{
+    long i = *(const long *)a, j = *(const long *)b;
+    uint64_t ki = g_sort_keys[i], kj = g_sort_keys[j];
+    if (ki < kj) return -1;
+    if (ki > kj) return 1;
+    return (i > j) - (i < j);
+}
+
+/* stable order by (key, input index) */
+static void sort_by_key(const uint64_t *key, long n, long *perm)
+{
+    for (long i = 0; i < n; ++i) perm[i] = i;
+    g_sort_keys = key;
+    qsort(perm, n, sizeof(long), cmp_key_index);
+}
+
+/* ------------------------------------------------------------------ */
+/* octree: a cell is split into its non-empty octants while it holds
+ * more than `leaf` members and is above the finest level.              */
+
+static int digit_at(uint64_t key, int level)   /* octant digit of level 1..21 */
+{
+    return (int)((key >> (3 * (ORC_LEVELS - level))) & 7u);
+}
+
+static long build_node(const orc *o, otree *t, const uint64_t *skeys, int level,
+                       long first, long count, long leaf)
+{
+    long id = tree_push(t);
+    t->level[id] = level;
+    t->first[id] = first;
+    t->count[id] = count;
+    /* cube of this cell from the key prefix of its first member */
+    uint64_t prefix = level ? (skeys[first] >> (3 * (ORC_LEVELS - level))) : 0;
+    uint64_t ix[3] = {0, 0, 0};
+    for (int m = 0; m < level; ++m) {
+        ix[0] |= ((prefix >> (3 * m + 2)) & 1u) << m;
+        ix[1] |= ((prefix >> (3 * m + 1)) & 1u) << m;
+        ix[2] |= ((prefix >> (3 * m)) & 1u) << m;
+    }
+    double l = ldexp(o->side, -level);
+    t->edge[id] = l;
+    for (int a = 0; a < 3; ++a) t->clo[3 * id + a] = o->lo[a] + (double)ix[a] * l;
+    int split = count > leaf && level < ORC_LEVELS;
+    t->leaf[id] = !split;
+    if (split) {
+        long i = first, end = first + count;
+        while (i < end) {
+            int d = digit_at(skeys[i], level + 1);
+            long j = i;
+            while (j < end && digit_at(skeys[j], level + 1) == d) ++j;
+            build_node(o, t, skeys, level + 1, i, j - i, leaf);
+            i = j;
+        }
+    }
+    t->skip[id] = t->n;
+    return id;
+}
+
+static void build_tree(const orc *o, otree *t, const uint64_t *skeys, long n, long leaf)
+{
+    tree_free(t);
+    if (n > 0) build_node(o, t, skeys, 0, 0, n, leaf);
+}
+
+/* Luminosity moments (Section 2.2.2 / Eq. ssum): a leaf sums its members in
+ * sorted order, an inner cell sums its children in octant order. */
+static void moments_node(otree *t, long n, const long *perm, const float *x, const float *y,
+                         const float *z, const double *L)
+{
+    double S = 0.0, Mx = 0.0, My = 0.0, Mz = 0.0;
+    if (t->leaf[n]) {
+        for (long r = t->first[n]; r < t->first[n] + t->count[n]; ++r) {
+            long j = perm[r];
+            S += L[j];
+            Mx += L[j] * (double)x[j];
+            My += L[j] * (double)y[j];
+            Mz += L[j] * (double)z[j];
+        }
+    } else {
+        for (long c = n + 1; c < t->skip[n]; c = t->skip[c]) {
+            moments_node(t, c, perm, x, y, z, L);
+            S += t->L[c];
+            Mx += t->M[3 * c];
+            My += t->M[3 * c + 1];
+            Mz += t->M[3 * c + 2];
+        }
+    }
+    t->L[n] = S;
+    t->M[3 * n] = Mx; t->M[3 * n + 1] = My; t->M[3 * n + 2] = Mz;
+    if (t->count[n] == 1) {
+        long j = perm[t->first[n]];
+        t->cen[3 * n] = x[j]; t->cen[3 * n + 1] = y[j]; t->cen[3 * n + 2] = z[j];
+    } else if (S > 0.0) {
+        t->cen[3 * n] = (float)(Mx / S);
+        t->cen[3 * n + 1] = (float)(My / S);
+        t->cen[3 * n + 2] = (float)(Mz / S);
+    } else {
+        for (int a = 0; a < 3; ++a)
+            t->cen[3 * n + a] = (float)(t->clo[3 * n + a] + 0.5 * t->edge[n]);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* neighbours: N(i) = { k != i : |r_k - r_i| < 2 h_i }, found through the
+ * particle octree (Section 2.2.2 reuses the gravity tree).              */
+
+typedef struct { long *v; long n, cap; } lvec;
+static void lvec_push(lvec *a, long x)
+{
+    if (a->n == a->cap) { a->cap = a->cap ? 2 * a->cap : 64; a->v = realloc(a->v, a->cap * sizeof(long)); }
+    a->v[a->n++] = x;
+}
+
+static double box_d2(const otree *t, long n, double px, double py, double pz)
+{
+    double l = t->edge[n];
+    double p[3] = {px, py, pz};
+    double d[3];
+    for (int a = 0; a < 3; ++a) {
+        double lo = t->clo[3 * n + a], hi = lo + l;
+        d[a] = 0.0;
+        if (p[a] < lo) d[a] = lo - p[a];
+        else if (p[a] > hi) d[a] = p[a] - hi;
+    }
+    return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+}
+
+static void nb_collect(const orc *o, long n, long i, lvec *out)
+{
+    const otree *t = &o->pt;
+    double px = o->px[i], py = o->py[i], pz = o->pz[i];
+    double two_h = 2.0 * (double)o->h[i];
+    double r2 = two_h * two_h;
+    /* cells are visited with a small slack: members can sit a rounding
+     * error outside their cube; the member test below is exact. */
+    double slack = 1e-9 * o->side;
+    double bd = sqrt(box_d2(t, n, px, py, pz));
+    if (bd > two_h + slack) return;
+    if (t->leaf[n]) {
+        for (long r = t->first[n]; r < t->first[n] + t->count[n]; ++r) {
+            long k = o->pperm[r];
+            if (k == i) continue;
+            if (d2_64(o->px[k], o->py[k], o->pz[k], px, py, pz) < r2) lvec_push(out, k);
+        }
+        return;
+    }
+    for (long c = n + 1; c < t->skip[n]; c = t->skip[c]) nb_collect(o, c, i, out);
+}
+
+static int cmp_long(const void *a, const void *b)
+{
+    long x = *(const long *)a, y = *(const long *)b;
+    return (x > y) - (x < y);
+}
+
+static void build_neighbours(orc *o)
+{
+    free(o->nb_off); free(o->nb_idx);
+    o->nb_off = xmalloc((o->np + 1) * sizeof(long));
+    lvec *rows = calloc(o->np ? o->np : 1, sizeof(lvec));
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long i = 0; i < o->np; ++i) {
+        if (o->pt.n) nb_collect(o, 0, i, &rows[i]);
+        qsort(rows[i].v, rows[i].n, sizeof(long), cmp_long);
+    }
+    long tot = 0;
+    for (long i = 0; i < o->np; ++i) { o->nb_off[i] = tot; tot += rows[i].n; }
+    o->nb_off[o->np] = tot;
+    o->nb_idx = xmalloc(tot * sizeof(long));
+    for (long i = 0; i < o->np; ++i) {
+        if (rows[i].n) memcpy(o->nb_idx + o->nb_off[i], rows[i].v, rows[i].n * sizeof(long));
+        free(rows[i].v);
+    }
+    free(rows);
+}
+
+/* ------------------------------------------------------------------ */
+/* walk: Eqs. con1 / con2                                               */
+
+static int accept_cell(const otree *t, long n, double px, double py, double pz, double th2)
+{
+    double l = t->edge[n];
+    return l * l <= th2 * box_d2(t, n, px, py, pz);
+}
+
+/* Entries: node id >= 0 for an accepted cell, -(1 + sorted rank) for an
+ * individual member of a leaf that was not accepted. */
+static void walk_node(const otree *t, long n, double px, double py, double pz, double th2,
+                      long self_rank, lvec *out)
+{
+    if (accept_cell(t, n, px, py, pz, th2)) { lvec_push(out, n); return; }
+    if (t->leaf[n]) {
+        for (long r = t->first[n]; r < t->first[n] + t->count[n]; ++r)
+            if (r != self_rank) lvec_push(out, -(1 + r));
+        return;
+    }
+    for (long c = n + 1; c < t->skip[n]; c = t->skip[c])
+        walk_node(t, c, px, py, pz, th2, self_rank, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* march: Eq. tau and the trapezoidal d_tau (Section 2.2.1)             */
+
+static double march(const orc *o, long i, const double rs[3], const float *nHI, long *hops,
+                    lvec *chain)
+{
+    double sig = o->p.sigma_cm2 * o->p.len_unit_cm;   /* per length unit per cm^-3 */
+    long j = i;
+    double tau = 0.0;
+    long nh = 0;
+    for (;;) {
+        double jx = o->px[j], jy = o->py[j], jz = o->pz[j];
+        double Dj = d2_64(jx, jy, jz, rs[0], rs[1], rs[2]);
+        double bx = rs[0] - jx, by = rs[1] - jy, bz = rs[2] - jz;
+        long best = -1;
+        double cbest = 0.0;
+        ++nh;
+        for (long e = o->nb_off[j]; e < o->nb_off[j + 1]; ++e) {
+            long k = o->nb_idx[e];
+            double kx = o->px[k], ky = o->py[k], kz = o->pz[k];
+            double Dk = d2_64(kx, ky, kz, rs[0], rs[1], rs[2]);
+            if (!(Dk < Dj)) continue;
+            double ax = kx - jx, ay = ky - jy, az = kz - jz;
+            double dot = (bx * ax + by * ay) + bz * az;
+            double c = dot / sqrt(d2_64(kx, ky, kz, jx, jy, jz));
+            if (best < 0 || c > cbest || (c == cbest && k < best)) { best = k; cbest = c; }
+        }
+        if (chain) lvec_push(chain, j);
+        if (best < 0) {
+            tau += sig * (double)nHI[j] * sqrt(Dj);
+            break;
+        }
+        double Db = d2_64(o->px[best], o->py[best], o->pz[best], rs[0], rs[1], rs[2]);
+        double dl = sqrt(Dj) - sqrt(Db);
+        tau += sig * 0.5 * ((double)nHI[j] + (double)nHI[best]) * dl;
+        j = best;
+        if (nh > o->np + 1) break;   /* cannot happen: distances strictly decrease */
+    }
+    if (hops) *hops += nh;
+    return tau;
+}
+
+/* ------------------------------------------------------------------ */
+/* public API                                                          */
+
+orc *orc_create(const orc_params *p)
+{
+    orc *o = calloc(1, sizeof(orc));
+    o->p = *p;
+    if (o->p.src_leaf < 1) o->p.src_leaf = 1;
+    if (o->p.ptree_leaf < 1) o->p.ptree_leaf = 8;
+    return o;
+}
+
+void orc_destroy(orc *o)
+{
+    if (!o) return;
+    free(o->px); free(o->py); free(o->pz); free(o->h);
+    free(o->sx); free(o->sy); free(o->sz); free(o->sL); free(o->V);
+    free(o->pkey); free(o->skey); free(o->pperm); free(o->sperm); free(o->prank);
+    tree_free(&o->pt); tree_free(&o->st); tree_free(&o->et);
+    free(o->nb_off); free(o->nb_idx); free(o->eL);
+    free(o);
+}
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* pos/src_pos are SoA (3 x n) float32, h float32, src_L photons/s, V in
+ * length-unit^3 (may be NULL when not diffuse). */
+int orc_build(orc *o, const float *pos, const float *h, long np, const float *spos,
+              const double *sL, long ns, const double *V)
+{
+    if (np < 0 || ns < 0) return -1;
+    o->np = np; o->ns = ns;
+    size_t fp = (np ? np : 1) * sizeof(float), fs = (ns ? ns : 1) * sizeof(float);
+    o->px = realloc(o->px, fp); o->py = realloc(o->py, fp); o->pz = realloc(o->pz, fp);
+    o->h = realloc(o->h, fp);
+    o->sx = realloc(o->sx, fs); o->sy = realloc(o->sy, fs); o->sz = realloc(o->sz, fs);
+    o->sL = realloc(o->sL, (ns ? ns : 1) * sizeof(double));
+    o->V = realloc(o->V, (np ? np : 1) * sizeof(double));
+    memcpy(o->px, pos, np * sizeof(float));
+    memcpy(o->py, pos + np, np * sizeof(float));
+    memcpy(o->pz, pos + 2 * np, np * sizeof(float));
+    memcpy(o->h, h, np * sizeof(float));
+    memcpy(o->sx, spos, ns * sizeof(float));
+    memcpy(o->sy, spos + ns, ns * sizeof(float));
+    memcpy(o->sz, spos + 2 * ns, ns * sizeof(float));
+    memcpy(o->sL, sL, ns * sizeof(double));
+    for (long i = 0; i < np; ++i) o->V[i] = V ? V[i] : 0.0;
+
+    make_frame(o);
+    o->pkey = realloc(o->pkey, (np ? np : 1) * sizeof(uint64_t));
+    o->skey = realloc(o->skey, (ns ? ns : 1) * sizeof(uint64_t));
+    for (long i = 0; i < np; ++i) o->pkey[i] = morton_key(o, o->px[i], o->py[i], o->pz[i]);
+    for (long i = 0; i < ns; ++i) o->skey[i] = morton_key(o, o->sx[i], o->sy[i], o->sz[i]);
+    o->pperm = realloc(o->pperm, (np ? np : 1) * sizeof(long));
+    o->sperm = realloc(o->sperm, (ns ? ns : 1) * sizeof(long));
+    o->prank = realloc(o->prank, (np ? np : 1) * sizeof(long));
+    sort_by_key(o->pkey, np, o->pperm);
+    sort_by_key(o->skey, ns, o->sperm);
+    for (long r = 0; r < np; ++r) o->prank[o->pperm[r]] = r;
+
+    uint64_t *pks = xmalloc((np ? np : 1) * sizeof(uint64_t));
+    uint64_t *sks = xmalloc((ns ? ns : 1) * sizeof(uint64_t));
+    for (long r = 0; r < np; ++r) pks[r] = o->pkey[o->pperm[r]];
+    for (long r = 0; r < ns; ++r) sks[r] = o->skey[o->sperm[r]];
+    build_tree(o, &o->pt, pks, np, o->p.ptree_leaf);
+    build_tree(o, &o->st, sks, ns, o->p.src_leaf);
+    if (o->p.diffuse) build_tree(o, &o->et, pks, np, o->p.src_leaf);
+    else tree_free(&o->et);
+    free(pks); free(sks);
+    if (o->st.n) moments_node(&o->st, 0, o->sperm, o->sx, o->sy, o->sz, o->sL);
+    build_neighbours(o);
+    free(o->eL);
+    o->eL = calloc(np ? np : 1, sizeof(double));
+    if (o->et.n) moments_node(&o->et, 0, o->pperm, o->px, o->py, o->pz, o->eL);
+    return 0;
+}
+
+void orc_frame(const orc *o, double out[4])
+{
+    out[0] = o->lo[0]; out[1] = o->lo[1]; out[2] = o->lo[2]; out[3] = o->side;
+}
+
+/* which: 0 particles, 1 sources */
+void orc_keys(const orc *o, int which, uint64_t *out)
+{
+    if (which == 0) memcpy(out, o->pkey, o->np * sizeof(uint64_t));
+    else memcpy(out, o->skey, o->ns * sizeof(uint64_t));
+}
+
+void orc_perm(const orc *o, int which, long *out)
+{
+    if (which == 0) memcpy(out, o->pperm, o->np * sizeof(long));
+    else memcpy(out, o->sperm, o->ns * sizeof(long));
+}
+
+static const otree *pick_tree(const orc *o, int which)
+{
+    return which == 0 ? &o->pt : which == 1 ? &o->st : &o->et;
+}
+
+/* which: 0 particle tree, 1 source tree, 2 emitter tree */
+long orc_tree_size(const orc *o, int which) { return pick_tree(o, which)->n; }
+
+void orc_tree_get(const orc *o, int which, int *level, long *first, long *count, long *skip,
+                  int *leaf, double *cube4, double *L, double *M3, float *cen3)
+{
+    const otree *t = pick_tree(o, which);
+    for (long n = 0; n < t->n; ++n) {
+        if (level) level[n] = t->level[n];
+        if (first) first[n] = t->first[n];
+        if (count) count[n] = t->count[n];
+        if (skip) skip[n] = t->skip[n];
+        if (leaf) leaf[n] = t->leaf[n];
+        if (cube4) {
+            cube4[4 * n] = t->clo[3 * n]; cube4[4 * n + 1] = t->clo[3 * n + 1];
+            cube4[4 * n + 2] = t->clo[3 * n + 2]; cube4[4 * n + 3] = t->edge[n];
+        }
+        if (L) L[n] = t->L[n];
+        if (M3) { M3[3 * n] = t->M[3 * n]; M3[3 * n + 1] = t->M[3 * n + 1]; M3[3 * n + 2] = t->M[3 * n + 2]; }
+        if (cen3) { cen3[3 * n] = t->cen[3 * n]; cen3[3 * n + 1] = t->cen[3 * n + 1]; cen3[3 * n + 2] = t->cen[3 * n + 2]; }
+    }
+}
+
+long orc_nbr_total(const orc *o) { return o->np ? o->nb_off[o->np] : 0; }
+
+void orc_nbr_get(const orc *o, long *off, long *idx)
+{
+    memcpy(off, o->nb_off, (o->np + 1) * sizeof(long));
+    memcpy(idx, o->nb_idx, orc_nbr_total(o) * sizeof(long));
+}
+
+/* Recombination emitters (Section 4.1): N_rec,j = alpha_1 n_e n_p V_j with
+ * n_e = n_p = x n_H (hydrogen only), alpha_1 = alpha_A - alpha_B; then the
+ * emitter tree's moments.  y is the neutral fraction in input order. */
+void orc_set_emitters(orc *o, const double *y, const float *nH)
+{
+    double a1 = o->p.alpha_A - o->p.alpha_B;
+    double lu3 = o->p.len_unit_cm * o->p.len_unit_cm * o->p.len_unit_cm;
+    for (long i = 0; i < o->np; ++i) {
+        double ne = (1.0 - y[i]) * (double)nH[i];
+        o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);
+    }
+    if (o->et.n) moments_node(&o->et, 0, o->pperm, o->px, o->py, o->pz, o->eL);
+}
+
+double orc_emitter_L(const orc *o, long i) { return o->eL[i]; }
+
+/* Interaction list of one target (input index) on tree `which` (1 sources,
+ * 2 emitters).  Returns the number of entries; writes at most cap. */
+long orc_list(const orc *o, int which, float theta, long target, long *out, long cap)
+{
+    const otree *t = pick_tree(o, which);
+    lvec v = {0};
+    double th = theta;
+    if (t->n) walk_node(t, 0, o->px[target], o->py[target], o->pz[target], th * th,
+                        which == 2 ? o->prank[target] : -1, &v);
+    long n = v.n;
+    for (long e = 0; e < n && e < cap; ++e) out[e] = v.v[e];
+    free(v.v);
+    return n;
+}
+
+/* Optical depth from a source at rs to particle `target`; the visited chain
+ * (input indices, target first) goes to chain_out when given. */
+double orc_march(const orc *o, long target, const float rs32[3], const float *nHI, long *hops,
+                 long *chain_out, long cap, long *chain_len)
+{
+    double rs[3] = {rs32[0], rs32[1], rs32[2]};
+    lvec ch = {0};
+    long nh = 0;
+    double tau = march(o, target, rs, nHI, &nh, chain_out ? &ch : NULL);
+    if (hops) *hops = nh;
+    if (chain_out) {
+        for (long e = 0; e < ch.n && e < cap; ++e) chain_out[e] = ch.v[e];
+        if (chain_len) *chain_len = ch.n;
+    }
+    free(ch.v);
+    return tau;
+}
+
+/* Gamma of one target from one tree: sum over its list in walk order. */
+static double gamma_tree(const orc *o, int which, long i, double th, const float *nHI,
+                         long long *rays, long long *hops)
+{
+    const otree *t = pick_tree(o, which);
+    if (!t->n) return 0.0;
+    lvec v = {0};
+    walk_node(t, 0, o->px[i], o->py[i], o->pz[i], th * th, which == 2 ? o->prank[i] : -1, &v);
+    double lu = o->p.len_unit_cm;
+    double rfloor = 1e-6 * o->side;
+    double g = 0.0;
+    for (long e = 0; e < v.n; ++e) {
+        double rs[3], L;
+        long ent = v.v[e];
+        if (ent >= 0) {
+            rs[0] = t->cen[3 * ent]; rs[1] = t->cen[3 * ent + 1]; rs[2] = t->cen[3 * ent + 2];
+            L = t->L[ent];
+        } else {
+            long r = -ent - 1;
+            if (which == 1) {
+                long j = o->sperm[r];
+                rs[0] = o->sx[j]; rs[1] = o->sy[j]; rs[2] = o->sz[j];
+                L = o->sL[j];
+            } else {
+                long j = o->pperm[r];
+                rs[0] = o->px[j]; rs[1] = o->py[j]; rs[2] = o->pz[j];
+                L = o->eL[j];
+            }
+        }
+        long nh = 0;
+        double tau = march(o, i, rs, nHI, &nh, NULL);
+        double r2 = d2_64(o->px[i], o->py[i], o->pz[i], rs[0], rs[1], rs[2]);
+        if (r2 < rfloor * rfloor) r2 = rfloor * rfloor;
+        g += L * exp(-tau) / (4.0 * ORC_PI * r2 * lu * lu);
+        *rays += 1;
+        *hops += nh;
+    }
+    free(v.v);
+    return g;
+}
+
+/* Photoionisation rate Gamma (photons cm^-2 s^-1) at the given targets
+ * (input indices; NULL = all particles in order).  nHI is in input order.
+ * In the diffuse case the emitter tree (after orc_set_emitters) adds the
+ * recombination photons of every other particle.  stats = {rays, hops}. */
+int orc_gamma(const orc *o, const float *nHI, float theta, const long *targets, long nt,
+              double *gamma_out, long long *stats)
+{
+    long n = targets ? nt : o->np;
+    long long rays = 0, hops = 0;
+    double th = theta;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : rays, hops)
+    for (long t = 0; t < n; ++t) {
+        long i = targets ? targets[t] : t;
+        long long r = 0, hcount = 0;
+        double g = gamma_tree(o, 1, i, th, nHI, &r, &hcount);
+        if (o->p.diffuse) g += gamma_tree(o, 2, i, th, nHI, &r, &hcount);
+        gamma_out[t] = g;
+        rays += r;
+        hops += hcount;
+    }
+    if (stats) { stats[0] = rays; stats[1] = hops; }
+    return 0;
+}
+
+/* Implicit hydrogen update over dt (Appendix A), hydrogen only, isothermal:
+ * dy/dt = -k y + alpha n_H (1 - y)^2 for the neutral fraction y, solved by
+ * one backward-Euler step.  k = sigma Gamma, plus in the diffuse case the
+ * self term of Eq. kself1 per neutral atom, alpha_1 x^2 n_H^2 sigma R phi
+ * (tau_s) with R = (3V/4pi)^(1/3), tau_s = sigma n_HI R and
+ * phi(t) = (1 - e^-t)/t, taken from the step-start state.  Writes y1 and
+ * the float32 neutral density y1 n_H. */
+void orc_ionize(const orc *o, const double *gamma, const float *nH, const double *y0, double dt,
+                long n, double *y1, float *nHI_out)
+{
+    double alpha = o->p.diffuse ? o->p.alpha_A : o->p.alpha_B;
+    double a1 = o->p.alpha_A - o->p.alpha_B;
+    double sig = o->p.sigma_cm2;
+    for (long i = 0; i < n; ++i) {
+        double nh = nH[i];
+        double k = sig * gamma[i];
+        if (o->p.diffuse) {
+            double x0 = 1.0 - y0[i];
+            double R = cbrt(3.0 * o->V[i] / (4.0 * ORC_PI)) * o->p.len_unit_cm;
+            double ts = sig * (y0[i] * nh) * R;
+            double phi = ts > 0.0 ? -expm1(-ts) / ts : 1.0;
+            k += a1 * x0 * x0 * nh * nh * sig * R * phi;
+        }
+        /* y1 - y0 = dt (-k y1 + alpha n_H (1 - y1)^2): A y1^2 - b y1 + c = 0 */
+        double A = alpha * nh * dt, K = k * dt;
+        double b = 2.0 * A + K + 1.0, c = A + y0[i];
+        double disc = (K + 1.0) * (K + 1.0) + 4.0 * A * (K + 1.0 - y0[i]);
+        double y = 2.0 * c / (b + sqrt(disc));
+        y1[i] = y;
+        if (nHI_out) nHI_out[i] = (float)(y * nh);
+    }
+}
