@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of the START hot path on one GB300 (or N replicas under torchrun).
+
+A step is one pass of the whole path over the multiple-source workload
+(64^3 = 262144 particles on a jittered lattice, 1024 sources with
+log-normal luminosity, uniform n_H = 1e-3 in a 6.6 kpc box): frame, Morton
+keys, sorts, source and particle octrees, moments, neighbour lists, walk,
+ray march, Gamma and the implicit 1 Myr ionisation update, coupled from step
+to step.  The metric is rays per second (a ray is one (target, virtual
+source) pair whose optical depth is evaluated); theta_crit = 0.5 is the
+headline and 1.0 is reported beside it.
+
+Prints one JSON line.  --impl reference times the FP64 oracle on the host
+cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES_PER_HOP = 516     # 32 u32 neighbour indices + 32 float3 positions + 1 float n_HI
+ALGO_BYTES_PER_RAY = 16      # virtual source record
+ALGO_BYTES_PER_TARGET = 8    # Gamma out, target record
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--theta2", type=float, default=1.0)
+    ap.add_argument("--march-group", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-targets", type=int, default=192)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_1005_5312_gb300", "csrc", d["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d if d.get("source_sha") == h else None
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, w):
+    import numpy as np
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    oracle.build()
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
+    nHI = w.n_HI()
+    rng = np.random.default_rng(7)
+    per_step = max(8, args.cpu_targets // 4)
+    times, rays = [], []
+    for s in range(args.warmup + args.steps):
+        idx = rng.choice(w.n_p, per_step, replace=False)
+        t0 = time.perf_counter()
+        orc.gamma(nHI, args.theta, targets=idx)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            rays.append(orc.last_stats["rays"])
+    v = sum(rays) / sum(times)
+    cores = oracle.threads()
+    return {"impl": "reference", "metric": f"RT rays/s at theta_crit={args.theta}",
+            "value": v, "unit": "rays/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "theta": args.theta,
+                       "sample": f"{per_step} random targets per step"},
+            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random targets of {w.n_p} per step"},
+            "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, w):
+    import numpy as np
+    import torch
+    import paper_1005_5312_gb300 as S
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    S.build()
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    pos, h, spos, sL = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L)
+    nH, y0 = T(w.n_H), T(w.y0)
+    y = y0.clone()
+    g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(theta):
+        ctx.build_trees(pos, h, spos, sL)
+        ctx.set_state(nH, y)
+        ctx.rt_solve(theta, gamma_out=g)
+        ctx.ionize(w.dt_s, y_out=y)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(theta, steps, warmup):
+        y.copy_(y0)
+        for _ in range(warmup):
+            step(theta)
+        torch.cuda.synchronize(dev)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        march_ms, rays, hops, fbs = [], [], [], []
+        l0 = ctx.stats()["launches"]
+        barrier()
+        t_wall = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()                      # evict L2 between timed steps
+            ev0[k].record(stream)
+            step(theta)
+            ev1[k].record(stream)
+            tm = ctx.timings()
+            st = ctx.stats()
+            march_ms.append(tm["march"])
+            rays.append(st["rays"])
+            hops.append(st["hops"])
+            fbs.append(st["march_fallbacks"])
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+        launches = ctx.stats()["launches"] - l0
+        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        return dict(step_ms=step_ms, march_ms=march_ms, rays=rays, hops=hops, fbs=fbs,
+                    launches=launches, wall=t_wall)
+
+    with ClockSampler(local) as clk:
+        r1 = timed(args.theta, args.steps, args.warmup)
+    r2 = timed(args.theta2, max(2, args.steps // 2), 1)
+
+    tot_ms = sum(r1["step_ms"])
+    rays = sum(r1["rays"])
+    if ws > 1:
+        import torch.distributed as dist
+        gathered = [None] * ws
+        dist.all_gather_object(gathered, (tot_ms, rays))
+        tot_ms = max(x[0] for x in gathered)
+        rays = sum(x[1] for x in gathered)
+    value = rays / (tot_ms * 1e-3)
+
+    # roofline of the march kernel (the dominant launch)
+    peak, peak_kind = measured_peaks()
+    mk = [(m, r, hp) for m, r, hp in zip(r1["march_ms"], r1["rays"], r1["hops"]) if m > 0]
+    algo = [ALGO_BYTES_PER_HOP * hp + ALGO_BYTES_PER_RAY * r + ALGO_BYTES_PER_TARGET * w.n_p
+            for _, r, hp in mk]
+    avg_ms = sum(m for m, _, _ in mk) / len(mk)
+    achieved = (sum(algo) / len(algo)) / (avg_ms * 1e-3) / 1e9
+    tr = traffic_record("k_march")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "kernel": "k_march", "kernel_ms": avg_ms,
+            "algorithmic_bytes_per_launch": sum(algo) / len(algo)}
+
+    out = {"metric": f"RT rays/s at theta_crit={args.theta}", "value": value, "unit": "rays/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "theta": args.theta,
+                      "dt_s": w.dt_s, "march_group": args.march_group,
+                      "l2": "512 MB buffer written between timed steps",
+                      "step": "build_trees + set_state + rt_solve + ionize, coupled"},
+           "rays_per_step": rays / args.steps / ws,
+           "hops_per_ray": sum(r1["hops"]) / max(1, sum(r1["rays"])),
+           "march_fallbacks_per_step": sum(r1["fbs"]) / args.steps,
+           "gpu_launches": r1["launches"],
+           "roofline": roof, "clocks": clk.summary()}
+    t2 = sum(r2["step_ms"])
+    out[f"theta_{args.theta2}"] = {"value": sum(r2["rays"]) / (t2 * 1e-3), "unit": "rays/s",
+                                   "ms_per_step": t2 / len(r2["step_ms"]),
+                                   "rays_per_step": sum(r2["rays"]) / len(r2["rays"]),
+                                   "march_ms": sum(r2["march_ms"]) / len(r2["march_ms"])}
+    phases = ctx.timings()
+    out["phase_ms_last_step"] = phases
+
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers: H2D copies of the
+        # step's inputs and D2H of Gamma and y inside the timed region
+        hpos, hh, hsp, hsL = w.pos, w.h, w.src_pos, w.src_L
+        hnH = w.n_H
+        hy = w.y0.copy()
+        hg = np.zeros(w.n_p, np.float32)
+        ctx_h = S.Context(march_group=args.march_group)
+
+        def hstep():
+            ctx_h.build_trees(hpos, hh, hsp, hsL)
+            ctx_h.set_state(hnH, hy)
+            ctx_h.rt_solve(args.theta, gamma_out=hg)
+            ctx_h.ionize(w.dt_s, y_out=hy)
+
+        for _ in range(args.warmup):
+            hstep()
+        hy[:] = w.y0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e_rays = 0
+        for _ in range(args.steps):
+            hstep()
+            e_rays += ctx_h.stats()["rays"]
+        te = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            gathered = [None] * ws
+            dist.all_gather_object(gathered, (te, e_rays))
+            te = max(x[0] for x in gathered)
+            e_rays = sum(x[1] for x in gathered)
+        h2d = hpos.nbytes + hh.nbytes + hsp.nbytes + hsL.nbytes + hnH.nbytes + hy.nbytes
+        d2h = hg.nbytes + hy.nbytes
+        out["e2e"] = {"value": e_rays / te, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * te / args.steps}
+        ctx_h.close()
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import numpy as np2
+        import oracle
+        oracle.build()
+        orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
+        idx = np2.random.default_rng(5).choice(w.n_p, args.cpu_targets, replace=False)
+        nHI = w.n_HI()
+        t0 = time.perf_counter()
+        orc.gamma(nHI, args.theta, targets=idx)
+        tc = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": orc.last_stats["rays"] / tc, "unit": "rays/s",
+                               "cores": oracle.threads(), "kind": "oracle",
+                               "sample": f"Gamma at {args.cpu_targets} random targets of {w.n_p}, "
+                                         f"theta={args.theta}, neutral start ({tc:.1f} s)"}
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def main():
+    args = parse()
+    from start_inputs import config2
+    w = config2()
+    res = run_reference(args, w) if args.impl == "reference" else run_gpu(args, w)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * start.h -- C ABI of the GB300 (sm_103a) implementation of the START
+ * radiative-transfer hot path (Hasegawa & Umemura 2010, "START: Smoothed
+ * particle hydrodynamics with tree-based accelerated radiative transfer").
+ *
+ * The hot path, per time step:
+ *   1. frame + Morton keys of particles and sources; stable sort      (Sec. 2.2.2)
+ *   2. source octree, one source per leaf by default                  (Sec. 2.2.2)
+ *   3. luminosity moments: L = sum L_j, r = sum L_j r_j / sum L_j      (Sec. 2.2.2)
+ *   4. particle octree and neighbour lists N(i) = {k : |r_k-r_i| < 2h_i}
+ *                                                                     (Sec. 2.2.1)
+ *   5. per target: walk the source tree, accepting a cell when
+ *      l/d <= theta_crit and its parent was not accepted              (Eqs. con1, con2)
+ *   6. per accepted cell / individual source: optical depth by upstream
+ *      ray marching, tau_t = tau_up + sigma dl (n_t + n_up)/2          (Eq. tau, Sec. 2.2.1)
+ *   7. Gamma_i = sum L e^-tau / (4 pi r^2)                             (Eq. solution2, ksum)
+ *   8. implicit hydrogen ionisation update                             (Appendix A)
+ *   9. diffuse mode: every particle also emits N_rec = alpha_1 n_e n_p V
+ *      and receives the self term k_self                               (Sec. 4.1, Eqs. ssum, kself1)
+ *
+ * Readings of points the paper leaves open (identical in the library and
+ * in its test oracle):
+ *   - d in con1 is the Euclidean distance from the target to the cell cube
+ *     (0 inside); the root is tested by con1 alone; a leaf that is not
+ *     accepted contributes its sources one by one.
+ *   - the upstream particle of j toward a source at r_s is the neighbour k
+ *     strictly closer to r_s maximising (r_s-r_j).(r_k-r_j)/|r_k-r_j|
+ *     (smallest angle), ties to the smaller input index; a chain with no
+ *     closer neighbour ends with sigma n_j |r_j - r_s|.
+ *   - dl = |r_j - r_s| - |r_up - r_s|; n is the neutral density n_HI.
+ *   - r in the dilution is floored at 1e-6 of the root cube side.
+ *   - hydrogen only, isothermal; alpha_B on the spot, alpha_A (and the
+ *     diffuse emitters) in diffuse mode; one backward-Euler step in the
+ *     neutral fraction y = 1 - x_HII per call.
+ *
+ * Conventions for every function below:
+ *   - Return value: START_OK (0) or a negative START_E* status; no
+ *     exception crosses the ABI.  start_last_error() describes the last
+ *     failure of a context.
+ *   - Pointers may address host or device memory (anything the CUDA
+ *     runtime can address under unified virtual addressing).  Inputs are
+ *     copied into library-owned device buffers; the caller keeps ownership
+ *     and may free or reuse them when the call returns.  Outputs in device
+ *     memory are written by stream-ordered kernels and are valid once the
+ *     context's stream is synchronised; outputs in host memory are valid
+ *     when the call returns (the call synchronises the stream).
+ *   - All work is issued on start_params.stream (NULL = legacy default
+ *     stream) of the current CUDA device at start_create.
+ *   - Positions are float32, structure-of-arrays (x[0..n), y[0..n),
+ *     z[0..n)) in units of len_unit_cm.  Luminosities are float64 photons
+ *     per second (they exceed float32's range).  Gamma is float32 photons
+ *     cm^-2 s^-1.  Neutral fractions y are float64.
+ *   - Particle arrays are in the caller's (input) order on both sides of
+ *     the ABI; the library works internally in Morton order.
+ */
+#ifndef START_H
+#define START_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define START_OK 0
+#define START_EINVAL (-1)     /* invalid argument: NaN/Inf, h <= 0, L < 0, theta < 0, ... */
+#define START_ENOMEM (-2)     /* device allocation failed */
+#define START_ENOTBUILT (-3)  /* start_build_trees / start_set_state not called yet */
+#define START_ECUDA (-4)      /* a CUDA runtime call failed */
+#define START_ETIMEOUT (-5)   /* a device wait exceeded spin_cap (reserved) */
+#define START_ECHAIN (-6)     /* a ray chain exceeded hop_cap */
+#define START_ERANGE (-7)     /* a size exceeds the library's limits (N >= 2^30) */
+
+#define START_DIFFUSE 1u      /* start_build_trees flag: particles also emit */
+
+#define START_MAX_N (1LL << 30)
+
+/* Run parameters.  start_default_params fills the values of the
+ * monochromatic 13.6 eV, T = 1e4 K problem with lengths in kpc. */
+typedef struct start_params {
+    int src_leaf;          /* max sources per source-tree leaf; 1 = the paper's
+                              "each cell contains only one radiation source" */
+    int ptree_leaf;        /* max particles per particle-tree leaf (neighbour
+                              search only; does not change any result) */
+    int march_group;       /* lanes cooperating on one ray: 8, 16 or 32
+                              (0 = default); does not change any result */
+    int timing;            /* 1: record CUDA events around each phase (see
+                              start_get_timings); 0: none */
+    double sigma_cm2;      /* HI photoionisation cross-section (6.3e-18) */
+    double len_unit_cm;    /* length unit of positions (kpc = 3.0857e21) */
+    double L_unit;         /* internal luminosity scale, photons/s (1e48) */
+    double alpha_A;        /* case-A recombination coefficient, cm^3/s */
+    double alpha_B;        /* case-B recombination coefficient, cm^3/s */
+    double tau_cut;        /* rays stop once tau exceeds this (default 110;
+                              e^-110 is below float32's smallest subnormal
+                              relative to any representable flux) */
+    long long hop_cap;     /* max upstream steps per ray (0 = N_p + 1) */
+    long long spin_cap;    /* max iterations of any device wait (reserved) */
+    void *stream;          /* cudaStream_t to issue work on (NULL = default) */
+} start_params;
+
+/* Counters of the last start_rt_solve. */
+typedef struct start_stats {
+    long long rays;             /* (target, virtual source) pairs evaluated */
+    long long hops;             /* neighbour-list evaluations over all rays */
+    long long march_fallbacks;  /* upstream choices decided in FP64 */
+    long long walk_fallbacks;   /* opening tests decided in FP64 */
+    long long nbr_fallbacks;    /* neighbour tests decided in FP64 (last build) */
+    long long nodes_src;        /* nodes of the source tree */
+    long long nodes_emit;       /* nodes of the emitter tree (diffuse) */
+    long long nodes_part;       /* nodes of the particle tree */
+    long long nbr_total;        /* neighbour-list entries */
+    long long max_hops;         /* longest chain of the last solve */
+    long long launches;         /* kernels launched by this context so far */
+} start_stats;
+
+/* Phases timed when start_params.timing = 1 (milliseconds of the last
+ * occurrence of each, from CUDA events on the context's stream). */
+#define START_PHASE_BUILD 0   /* start_build_trees */
+#define START_PHASE_WALK 1    /* interaction lists */
+#define START_PHASE_MARCH 2   /* ray march (the dominant kernel) */
+#define START_PHASE_GAMMA 3   /* Gamma reduction */
+#define START_PHASE_IONIZE 4  /* implicit update */
+#define START_PHASE_EMIT 5    /* diffuse emitters and their moments */
+#define START_NPHASES 6
+
+typedef struct start_ctx start_ctx;
+
+/* Fill *p with defaults.  Returns START_EINVAL if p is NULL. */
+int start_default_params(start_params *p);
+
+/* Create a context bound to the current CUDA device and p->stream.
+ * The library owns the context and every buffer in it. */
+int start_create(start_ctx **out, const start_params *p);
+
+/* Release the context and its device buffers (synchronises its stream). */
+int start_destroy(start_ctx *c);
+
+/* Steps 1-4 (and the emitter tree in diffuse mode): frame, keys, sorts,
+ * source tree + moments, particle tree, neighbour lists.
+ *   pos    [3 * n_p] float32 SoA particle positions
+ *   h      [n_p]     float32 smoothing lengths (> 0); neighbours are the
+ *                    particles within 2h
+ *   src_pos[3 * n_s] float32 SoA source positions
+ *   src_L  [n_s]     float64 ionising photons per second (>= 0)
+ *   V      [n_p]     float64 particle volumes in len_unit^3 (> 0); required
+ *                    with START_DIFFUSE, ignored (may be NULL) otherwise
+ *   flags  START_DIFFUSE or 0
+ * n_p = 0 or n_s = 0 is allowed.  Sizes >= START_MAX_N give START_ERANGE.
+ * Resets the chemistry state to y = 1, n_H = 0 (call start_set_state). */
+int start_build_trees(start_ctx *c, const float *pos, const float *h, long long n_p,
+                      const float *src_pos, const double *src_L, long long n_s,
+                      const double *V, unsigned flags);
+
+/* Resident chemistry state (input order): n_H [n_p] float32 cm^-3 (>= 0),
+ * y [n_p] float64 neutral fraction in [0, 1].  Sets n_HI = y n_H. */
+int start_set_state(start_ctx *c, const float *n_H, const double *y);
+
+/* Steps 5-7 at opening angle theta (>= 0): Gamma for every particle.
+ *   n_HI      [n_p] float32 neutral density (>= 0), or NULL to use the
+ *             resident n_HI = y n_H
+ *   gamma_out [n_p] float32 photons cm^-2 s^-1, input order; may be NULL
+ *             (Gamma is kept resident for start_ionize)
+ * In diffuse mode the emitters' luminosities come from the resident state
+ * (start_set_state / start_ionize) and the emitter tree adds their
+ * photons (self excluded). */
+int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_out);
+
+/* Step 8: advance the resident y by dt_s seconds with the resident Gamma
+ * of the last start_rt_solve (one backward-Euler step), update the
+ * resident n_HI, and copy y to y_out [n_p] (input order) when not NULL. */
+int start_ionize(start_ctx *c, double dt_s, double *y_out);
+
+/* Stateless form: build + set_state(n_H = n_HI, y = 1) + solve on a
+ * temporary context.  Equivalent to the calls above; p may be NULL. */
+int start_rt_solve_oneshot(const start_params *p, const float *pos, const float *h,
+                           long long n_p, const float *n_HI, const float *src_pos,
+                           const double *src_L, long long n_s, float theta,
+                           float *gamma_out);
+
+/* ---- introspection (tests, metrics); all outputs may be host memory ---- */
+
+/* Frame: out[0..2] lower corner, out[3] side of the root cube. */
+int start_get_frame(start_ctx *c, double out[4]);
+
+/* which = 0 particles, 1 sources.  perm[rank] = input index (sorted order);
+ * keys[i] = 63-bit Morton key of input i. */
+int start_get_perm(start_ctx *c, int which, unsigned *perm);
+int start_get_keys(start_ctx *c, int which, unsigned long long *keys);
+
+/* which = 0 particle tree, 1 source tree, 2 emitter tree.  Nodes are in
+ * depth-first pre-order with children in octant order; first/count index
+ * the sorted members; skip = index after the node's subtree; cube4 =
+ * (lower corner x, y, z, edge) in float64; L = summed luminosity (float64,
+ * photons/s); cen3 = luminosity centre in float32.  Any output may be
+ * NULL.  start_tree_size returns the node count (or a negative status). */
+long long start_tree_size(start_ctx *c, int which);
+int start_get_tree(start_ctx *c, int which, int *level, unsigned *first, unsigned *count,
+                   unsigned *skip, int *leaf, double *cube4, double *L, float *cen3);
+
+/* Neighbour lists in input order: off [n_p + 1], idx [start_nbr_total]
+ * (input indices, any order within a row). */
+long long start_nbr_total(start_ctx *c);
+int start_get_neighbors(start_ctx *c, unsigned long long *off, unsigned *idx);
+
+/* Interaction lists at theta, rows in input order of the targets:
+ * off [n_p + 1]; entries [off[n_p]] may be NULL to query the size.  An
+ * entry is the source-tree node id (accepted cell), or
+ * START_ENTRY_SOURCE | sorted source rank (member of a leaf that was not
+ * accepted); START_ENTRY_EMITTER marks entries of the emitter tree.
+ * Entries of one target are in walk order (point sources first). */
+#define START_ENTRY_SOURCE 0x80000000u
+#define START_ENTRY_EMITTER 0x40000000u
+int start_get_lists(start_ctx *c, float theta, unsigned long long *off, unsigned *entries);
+
+/* Per-particle float32 luminosity of the emitters (input order), photons/s
+ * divided by L_unit, as used by the last diffuse solve. */
+int start_get_emitter_L(start_ctx *c, float *out);
+
+int start_get_stats(start_ctx *c, start_stats *out);
+
+/* ms[k] = duration of the last phase k (START_PHASE_*), or -1 if it was not
+ * recorded; n entries are written (n <= START_NPHASES).  Synchronises. */
+int start_get_timings(start_ctx *c, double *ms, int n);
+
+/* Message of the last failure on c (never NULL). */
+const char *start_last_error(const start_ctx *c);
+
+/* Name of a status code. */
+const char *start_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* START_H */

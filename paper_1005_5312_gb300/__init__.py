@@ -1,0 +1,263 @@
+"""GB300 (sm_103a) implementation of the START radiative-transfer hot path.
+
+Thin Python binding of the C ABI in ``include/start.h``: argument
+marshalling only.  Every step of the path (frame, keys, sorts, octrees,
+moments, neighbour lists, walk, ray march, Gamma, ionisation) runs in the
+CUDA kernels of ``csrc/``, compiled into ``_build/libstart.so``.  There is no
+CPU fallback: if the library is missing, importing the binding raises.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; the library
+accepts host or device pointers and copies inputs into its own buffers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build_lib import LIB_PATH, build  # noqa: F401
+
+START_OK = 0
+START_EINVAL = -1
+START_ENOMEM = -2
+START_ENOTBUILT = -3
+START_ECUDA = -4
+START_ETIMEOUT = -5
+START_ECHAIN = -6
+START_ERANGE = -7
+START_DIFFUSE = 1
+START_ENTRY_SOURCE = 0x80000000
+START_ENTRY_EMITTER = 0x40000000
+
+
+class StartParams(C.Structure):
+    _fields_ = [("src_leaf", C.c_int), ("ptree_leaf", C.c_int), ("march_group", C.c_int),
+                ("timing", C.c_int), ("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
+                ("L_unit", C.c_double), ("alpha_A", C.c_double), ("alpha_B", C.c_double),
+                ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("spin_cap", C.c_longlong),
+                ("stream", C.c_void_p)]
+
+
+class StartStats(C.Structure):
+    _fields_ = [(n, C.c_longlong) for n in (
+        "rays", "hops", "march_fallbacks", "walk_fallbacks", "nbr_fallbacks", "nodes_src",
+        "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches")]
+
+
+class StartError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libstart.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, ll, i, f, d = C.c_void_p, C.c_longlong, C.c_int, C.c_float, C.c_double
+        P = C.POINTER
+        sig = {
+            "start_default_params": (i, [P(StartParams)]),
+            "start_create": (i, [P(vp), P(StartParams)]),
+            "start_destroy": (i, [vp]),
+            "start_build_trees": (i, [vp, vp, vp, ll, vp, vp, ll, vp, C.c_uint]),
+            "start_set_state": (i, [vp, vp, vp]),
+            "start_rt_solve": (i, [vp, vp, f, vp]),
+            "start_ionize": (i, [vp, d, vp]),
+            "start_rt_solve_oneshot": (i, [P(StartParams), vp, vp, ll, vp, vp, vp, ll, f, vp]),
+            "start_get_frame": (i, [vp, vp]),
+            "start_get_perm": (i, [vp, i, vp]),
+            "start_get_keys": (i, [vp, i, vp]),
+            "start_tree_size": (ll, [vp, i]),
+            "start_get_tree": (i, [vp, i] + [vp] * 8),
+            "start_nbr_total": (ll, [vp]),
+            "start_get_neighbors": (i, [vp, vp, vp]),
+            "start_get_lists": (i, [vp, f, vp, vp]),
+            "start_get_emitter_L": (i, [vp, vp]),
+            "start_get_stats": (i, [vp, P(StartStats)]),
+            "start_get_timings": (i, [vp, P(d), i]),
+            "start_last_error": (C.c_char_p, [vp]),
+            "start_status_string": (C.c_char_p, [i]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check(ctx, rc):
+    if rc != START_OK:
+        L = lib()
+        msg = L.start_last_error(ctx).decode() if ctx else ""
+        raise StartError(rc, f"{L.start_status_string(rc).decode()}: {msg}")
+    return rc
+
+
+def default_params(**over) -> StartParams:
+    p = StartParams()
+    lib().start_default_params(C.byref(p))
+    for k, v in over.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(v.cuda_stream)
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------- C-ABI names
+def start_create(params: StartParams | None = None):
+    h = C.c_void_p()
+    _check(None, lib().start_create(C.byref(h), C.byref(params) if params is not None else None))
+    return h
+
+
+def start_destroy(ctx):
+    return lib().start_destroy(ctx)
+
+
+def start_build_trees(ctx, pos, h, n_p, src_pos, src_L, n_s, V=None, flags=0):
+    return _check(ctx, lib().start_build_trees(ctx, _ptr(pos), _ptr(h), int(n_p), _ptr(src_pos),
+                                               _ptr(src_L), int(n_s), _ptr(V), int(flags)))
+
+
+def start_set_state(ctx, n_H, y):
+    return _check(ctx, lib().start_set_state(ctx, _ptr(n_H), _ptr(y)))
+
+
+def start_rt_solve(ctx, n_HI, theta, gamma_out):
+    return _check(ctx, lib().start_rt_solve(ctx, _ptr(n_HI), float(theta), _ptr(gamma_out)))
+
+
+def start_ionize(ctx, dt, y_out=None):
+    return _check(ctx, lib().start_ionize(ctx, float(dt), _ptr(y_out)))
+
+
+def start_rt_solve_oneshot(pos, h, n_p, n_HI, src_pos, src_L, n_s, theta, gamma_out,
+                           params: StartParams | None = None):
+    return _check(None, lib().start_rt_solve_oneshot(
+        C.byref(params) if params is not None else None, _ptr(pos), _ptr(h), int(n_p),
+        _ptr(n_HI), _ptr(src_pos), _ptr(src_L), int(n_s), float(theta), _ptr(gamma_out)))
+
+
+# ---------------------------------------------------------------- convenience
+class Context:
+    """One resident problem: trees, neighbour lists and chemistry state."""
+
+    def __init__(self, **params):
+        self.params = default_params(**params)
+        self.h = start_create(self.params)
+        self.n_p = 0
+        self.n_s = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            start_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_trees(self, pos, h, src_pos, src_L, V=None, diffuse=False):
+        self.n_p = int(h.shape[0])
+        self.n_s = int(src_L.shape[0])
+        start_build_trees(self.h, pos, h, self.n_p, src_pos, src_L, self.n_s, V,
+                          START_DIFFUSE if diffuse else 0)
+
+    def set_state(self, n_H, y):
+        start_set_state(self.h, n_H, y)
+
+    def rt_solve(self, theta, n_HI=None, gamma_out=None):
+        start_rt_solve(self.h, n_HI, theta, gamma_out)
+        return gamma_out
+
+    def ionize(self, dt, y_out=None):
+        start_ionize(self.h, dt, y_out)
+        return y_out
+
+    # introspection (numpy on the host)
+    def frame(self):
+        out = np.zeros(4)
+        _check(self.h, lib().start_get_frame(self.h, out.ctypes.data))
+        return out[:3].copy(), float(out[3])
+
+    def perm(self, which):
+        n = self.n_p if which == 0 else self.n_s
+        out = np.zeros(max(n, 1), np.uint32)
+        _check(self.h, lib().start_get_perm(self.h, which, out.ctypes.data))
+        return out[:n]
+
+    def keys(self, which):
+        n = self.n_p if which == 0 else self.n_s
+        out = np.zeros(max(n, 1), np.uint64)
+        _check(self.h, lib().start_get_keys(self.h, which, out.ctypes.data))
+        return out[:n]
+
+    def tree(self, which):
+        n = int(lib().start_tree_size(self.h, which))
+        if n < 0:
+            _check(self.h, n)
+        m = max(n, 1)
+        t = dict(level=np.zeros(m, np.int32), first=np.zeros(m, np.uint32),
+                 count=np.zeros(m, np.uint32), skip=np.zeros(m, np.uint32),
+                 leaf=np.zeros(m, np.int32), cube=np.zeros((m, 4)), L=np.zeros(m),
+                 cen=np.zeros((m, 3), np.float32))
+        _check(self.h, lib().start_get_tree(self.h, which, *(t[k].ctypes.data for k in (
+            "level", "first", "count", "skip", "leaf", "cube", "L", "cen"))))
+        return {k: v[:n] for k, v in t.items()}
+
+    def neighbors(self):
+        tot = int(lib().start_nbr_total(self.h))
+        off = np.zeros(self.n_p + 1, np.uint64)
+        idx = np.zeros(max(tot, 1), np.uint32)
+        _check(self.h, lib().start_get_neighbors(self.h, off.ctypes.data, idx.ctypes.data))
+        return off, idx[:tot]
+
+    def lists(self, theta):
+        off = np.zeros(self.n_p + 1, np.uint64)
+        _check(self.h, lib().start_get_lists(self.h, float(theta), off.ctypes.data, None))
+        ent = np.zeros(max(int(off[-1]), 1), np.uint32)
+        _check(self.h, lib().start_get_lists(self.h, float(theta), off.ctypes.data, ent.ctypes.data))
+        return off, ent[:int(off[-1])]
+
+    def emitter_L(self):
+        out = np.zeros(max(self.n_p, 1), np.float32)
+        _check(self.h, lib().start_get_emitter_L(self.h, out.ctypes.data))
+        return out[:self.n_p]
+
+    def timings(self) -> dict:
+        """Milliseconds of the last build / walk / march / gamma / ionize /
+        emitter phase (needs timing=1)."""
+        ms = (C.c_double * 6)()
+        _check(self.h, lib().start_get_timings(self.h, ms, 6))
+        return dict(zip(("build", "walk", "march", "gamma", "ionize", "emit"), list(ms)))
+
+    def stats(self) -> dict:
+        s = StartStats()
+        _check(self.h, lib().start_get_stats(self.h, C.byref(s)))
+        return {n: getattr(s, n) for n, _ in StartStats._fields_}

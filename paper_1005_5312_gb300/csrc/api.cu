@@ -1,0 +1,745 @@
+// C ABI of the START library (declared in include/start.h): context
+// lifetime, input staging (host or device pointers), validation, the
+// build / state / solve / ionise sequence and test introspection.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace st {
+
+int finish_gamma(start_ctx *c, float *gout_dev);
+int run_walk(start_ctx *c, float theta);
+
+// ---------------------------------------------------------------- buffers and errors
+int ensure(DBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (bytes <= b.cap) return START_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = bytes + bytes / 8 + 256;
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return START_ENOMEM;
+    }
+    b.cap = want;
+    return START_OK;
+}
+
+int ensure_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s)
+{
+    if (bytes <= b.cap) return START_OK;
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return START_ENOMEM;
+    }
+    if (b.p && used) cudaMemcpyAsync(q, b.p, std::min(used, b.cap), cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    if (b.p) cudaFree(b.p);
+    b.p = q;
+    b.cap = bytes;
+    return START_OK;
+}
+
+void release(DBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+void phase_mark(start_ctx *c, int phase, bool end)
+{
+    if (!c->p.timing) return;
+    if (!c->ev_init) {
+        for (int k = 0; k < 2 * START_NPHASES; ++k) cudaEventCreate(&c->ev[k]);
+        c->ev_init = true;
+    }
+    cudaEventRecord(c->ev[2 * phase + (end ? 1 : 0)], c->stream);
+    if (end) c->ev_rec[phase] = true;
+}
+
+int set_err(start_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_check(start_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return START_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return set_err(c, START_ECUDA, m);
+}
+
+static bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copies n bytes of a caller pointer (host or device) into b.
+static int stage_in(start_ctx *c, DBuf &b, const void *src, size_t n)
+{
+    ST_TRY(ensure(b, n));
+    if (n) ST_CUDA(c, cudaMemcpyAsync(b.p, src, n, cudaMemcpyDefault, c->stream));
+    return START_OK;
+}
+
+// Copies n bytes of device data to a caller pointer (host or device);
+// synchronises when the destination is host memory.
+static int copy_out(start_ctx *c, void *dst, const void *src, size_t n)
+{
+    if (!n || !dst) return START_OK;
+    ST_CUDA(c, cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, c->stream));
+    if (!is_device_ptr(dst)) ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    return START_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------- small kernels
+__global__ void k_check_pos_h(const float *h, long long n, unsigned long long *bad)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(isfinite(h[i]) && h[i] > 0.f)) atomicAdd(bad, 1ull);
+}
+__global__ void k_check_nonneg_f(const float *v, long long n, unsigned long long *bad)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(isfinite(v[i]) && v[i] >= 0.f)) atomicAdd(bad, 1ull);
+}
+__global__ void k_check_nonneg_d(const double *v, long long n, unsigned long long *bad, int strict)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(isfinite(v[i]) && (strict ? v[i] > 0.0 : v[i] >= 0.0))) atomicAdd(bad, 1ull);
+}
+__global__ void k_check_unit_d(const double *v, long long n, unsigned long long *bad)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(v[i] >= 0.0 && v[i] <= 1.0)) atomicAdd(bad, 1ull);
+}
+
+__global__ void k_invert(const u32 *perm, long long n, u32 *inv)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) inv[perm[r]] = (u32)r;
+}
+
+// Morton-ordered particle records from the staged SoA inputs.
+__global__ void k_gather_particles(const float *pos, const float *h, const double *V,
+                                   const u32 *perm, long long n, float4 *pq, float *ph,
+                                   double *Vm, float *nH, double *y, float *gam)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    u32 i = perm[r];
+    pq[r] = make_float4(pos[i], pos[n + i], pos[2 * n + i], 0.f);
+    ph[r] = h[i];
+    if (V) Vm[r] = V[i];
+    else Vm[r] = 0.0;
+    nH[r] = 0.f;
+    y[r] = 1.0;
+    gam[r] = 0.f;
+}
+
+__global__ void k_gather_sources(const float *pos, const double *L, const u32 *perm, long long n,
+                                 double L_unit, float4 *sq, double *sL)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    u32 i = perm[r];
+    double Lj = L[i];
+    sq[r] = make_float4(pos[i], pos[n + i], pos[2 * n + i],
+                        __double2float_rn(__ddiv_rn(Lj, L_unit)));
+    sL[r] = Lj;
+}
+
+__global__ void k_set_state(const float *nH_in, const double *y_in, const u32 *inv, long long n,
+                            float *nH, double *y, float4 *pq)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u32 r = inv[i];
+    double yy = y_in ? y_in[i] : 1.0;
+    float nh = nH_in[i];
+    nH[r] = nh;
+    y[r] = yy;
+    pq[r].w = __double2float_rn(yy * (double)nh);
+}
+
+__global__ void k_set_nHI(const float *nHI, const u32 *inv, long long n, float4 *pq)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pq[inv[i]].w = nHI[i];
+}
+
+template <class T>
+__global__ void k_to_input_order(const T *m, const u32 *perm, long long n, T *out)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) out[perm[r]] = m[r];
+}
+
+static unsigned long long read_counter(start_ctx *c, int slot)
+{
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, c->counters.as<unsigned long long>() + slot, sizeof(v),
+                    cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return v;
+}
+
+static int check_bad(start_ctx *c, const char *what)
+{
+    unsigned long long bad = read_counter(c, C_BAD_INPUT);
+    ST_CUDA(c, cudaGetLastError());
+    if (bad) {
+        ST_CUDA(c, cudaMemsetAsync(c->counters.as<unsigned long long>() + C_BAD_INPUT, 0,
+                                   sizeof(unsigned long long), c->stream));
+        return set_err(c, START_EINVAL, std::string("invalid values in ") + what);
+    }
+    return START_OK;
+}
+
+// Reorders Morton-row CSR (u32 or u64 offsets) into input order on the host.
+template <class O>
+static void csr_to_input(long long n, const std::vector<O> &moff, const std::vector<u32> &mval,
+                         const std::vector<u32> &porig, bool map_vals, std::vector<u64> &off,
+                         std::vector<u32> &val)
+{
+    std::vector<u64> cnt(n + 1, 0);
+    for (long long r = 0; r < n; ++r) cnt[porig[r]] = (u64)(moff[r + 1] - moff[r]);
+    off.assign(n + 1, 0);
+    for (long long i = 0; i < n; ++i) off[i + 1] = off[i] + cnt[i];
+    val.resize(off[n]);
+    for (long long r = 0; r < n; ++r) {
+        u64 w = off[porig[r]];
+        for (O e = moff[r]; e < moff[r + 1]; ++e) val[w++] = map_vals ? porig[mval[e]] : mval[e];
+    }
+}
+
+static void release_all(start_ctx *c)
+{
+    DBuf *all[] = {&c->pq, &c->ph, &c->porig, &c->pinv, &c->pkey, &c->nH, &c->y, &c->V,
+                   &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
+                   &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,
+                   &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
+                   &c->scan_tmp, &c->stage, &c->flags, &c->counters};
+    for (DBuf *b : all) release(*b);
+    tree_release(c->pt);
+    tree_release(c->stree);
+    tree_release(c->et);
+    if (c->ev_init)
+        for (int k = 0; k < 2 * START_NPHASES; ++k) cudaEventDestroy(c->ev[k]);
+    c->ev_init = false;
+}
+
+}  // namespace st
+
+using namespace st;
+
+// ---------------------------------------------------------------- staging buffers
+namespace {
+struct Staged {
+    DBuf pos, h, spos, L, V;
+    ~Staged()
+    {
+        release(pos);
+        release(h);
+        release(spos);
+        release(L);
+        release(V);
+    }
+};
+}  // namespace
+
+extern "C" {
+
+int start_default_params(start_params *p)
+{
+    if (!p) return START_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->src_leaf = 1;
+    p->ptree_leaf = 16;
+    p->march_group = 8;
+    p->sigma_cm2 = 6.3e-18;
+    p->len_unit_cm = 3.0857e21;
+    p->L_unit = 1e48;
+    p->alpha_A = 4.18e-13;
+    p->alpha_B = 2.59e-13;
+    p->tau_cut = 110.0;
+    p->hop_cap = 0;
+    p->spin_cap = 1 << 24;
+    p->stream = nullptr;
+    return START_OK;
+}
+
+int start_create(start_ctx **out, const start_params *p)
+{
+    if (!out) return START_EINVAL;
+    *out = nullptr;
+    start_params d;
+    start_default_params(&d);
+    if (p) d = *p;
+    if (d.src_leaf < 1 || d.ptree_leaf < 1 || !(d.sigma_cm2 > 0) || !(d.len_unit_cm > 0) ||
+        !(d.L_unit > 0) || !(d.alpha_A >= 0) || !(d.alpha_B >= 0) || !(d.tau_cut > 0))
+        return START_EINVAL;
+    if (d.march_group != 0 && d.march_group != 8 && d.march_group != 16 && d.march_group != 32)
+        return START_EINVAL;
+    if (d.march_group == 0) d.march_group = 8;
+    start_ctx *c = new (std::nothrow) start_ctx();
+    if (!c) return START_ENOMEM;
+    c->p = d;
+    c->stream = (cudaStream_t)d.stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return START_ECUDA;
+    }
+    if (ensure(c->counters, C_COUNT * sizeof(unsigned long long)) ||
+        cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), c->stream) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        release_all(c);
+        delete c;
+        return START_ENOMEM;
+    }
+    *out = c;
+    return START_OK;
+}
+
+int start_destroy(start_ctx *c)
+{
+    if (!c) return START_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_all(c);
+    delete c;
+    return START_OK;
+}
+
+int start_build_trees(start_ctx *c, const float *pos, const float *h, long long n_p,
+                      const float *src_pos, const double *src_L, long long n_s, const double *V,
+                      unsigned flags)
+{
+    if (!c) return START_EINVAL;
+    DeviceGuard g(c->device);
+    c->built = c->has_state = c->solved = false;
+    if (n_p < 0 || n_s < 0) return set_err(c, START_EINVAL, "negative size");
+    if (n_p >= START_MAX_N || n_s >= START_MAX_N)
+        return set_err(c, START_ERANGE, "n_p and n_s must be below 2^30");
+    if ((n_p && (!pos || !h)) || (n_s && (!src_pos || !src_L)))
+        return set_err(c, START_EINVAL, "NULL input array");
+    bool diffuse = (flags & START_DIFFUSE) != 0;
+    if (diffuse && n_p && !V) return set_err(c, START_EINVAL, "diffuse mode needs V");
+    c->np = n_p;
+    c->ns = n_s;
+    c->diffuse = diffuse;
+    cudaStream_t s = c->stream;
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    ST_CUDA(c, cudaMemsetAsync(ctr, 0, C_COUNT * sizeof(unsigned long long), s));
+
+    phase_mark(c, START_PHASE_BUILD, false);
+    Staged in;
+    ST_TRY(stage_in(c, in.pos, pos, 3 * n_p * sizeof(float)));
+    ST_TRY(stage_in(c, in.h, h, n_p * sizeof(float)));
+    ST_TRY(stage_in(c, in.spos, src_pos, 3 * n_s * sizeof(float)));
+    ST_TRY(stage_in(c, in.L, src_L, n_s * sizeof(double)));
+    if (diffuse) ST_TRY(stage_in(c, in.V, V, n_p * sizeof(double)));
+    if (n_p) { k_check_pos_h<<<grid_for(n_p, 256), 256, 0, s>>>(in.h.as<float>(), n_p, ctr + C_BAD_INPUT); ++c->launches; }
+    if (n_s) { k_check_nonneg_d<<<grid_for(n_s, 256), 256, 0, s>>>(in.L.as<double>(), n_s, ctr + C_BAD_INPUT, 0); ++c->launches; }
+    if (diffuse && n_p)
+        k_check_nonneg_d<<<grid_for(n_p, 256), 256, 0, s>>>(in.V.as<double>(), n_p, ctr + C_BAD_INPUT, 1); ++c->launches;
+    ST_TRY(check_bad(c, "h, src_L or V"));
+    if (n_p + n_s == 0) {
+        c->pt.n = c->stree.n = c->et.n = 0;
+        c->nb_total = 0;
+        c->built = true;
+        return START_OK;
+    }
+    ST_TRY(compute_frame(c, in.pos.as<float>(), n_p, in.spos.as<float>(), n_s, &c->fr));
+
+    // particles: keys, stable sort, Morton-ordered records
+    size_t P = (size_t)(n_p ? n_p : 1), S = (size_t)(n_s ? n_s : 1);
+    if (ensure(c->pkey, P * 8) || ensure(c->tk[1], P * 8) || ensure(c->porig, P * 4) ||
+        ensure(c->pinv, P * 4) || ensure(c->pq, P * 16) || ensure(c->ph, P * 4) ||
+        ensure(c->nH, P * 4) || ensure(c->y, P * 8) || ensure(c->V, P * 8) ||
+        ensure(c->gam, P * 4) || ensure(c->eL, P * 8) || ensure(c->eLs, P * 4) ||
+        ensure(c->skey, S * 8) || ensure(c->tv[1], S * 8) || ensure(c->sorig, S * 4) ||
+        ensure(c->sq, S * 16) || ensure(c->sL, S * 8))
+        return set_err(c, START_ENOMEM, "out of device memory (inputs)");
+    u64 *pks = c->tk[1].as<u64>();
+    if (n_p) {
+        ST_TRY(morton_keys(c, in.pos.as<float>(), n_p, c->fr, pks, c->porig.as<u32>()));
+        ST_CUDA(c, cudaMemcpyAsync(c->pkey.p, pks, n_p * 8, cudaMemcpyDeviceToDevice, s));
+        ST_TRY(radix_sort_pairs(c, pks, c->porig.as<u32>(), n_p));
+        k_invert<<<grid_for(n_p, 256), 256, 0, s>>>(c->porig.as<u32>(), n_p, c->pinv.as<u32>()); ++c->launches;
+        k_gather_particles<<<grid_for(n_p, 256), 256, 0, s>>>(
+            in.pos.as<float>(), in.h.as<float>(), diffuse ? in.V.as<double>() : nullptr,
+            c->porig.as<u32>(), n_p, c->pq.as<float4>(), c->ph.as<float>(), c->V.as<double>(),
+            c->nH.as<float>(), c->y.as<double>(), c->gam.as<float>()); ++c->launches;
+        ST_CUDA(c, cudaMemsetAsync(c->eL.p, 0, n_p * 8, s));
+        ST_CUDA(c, cudaMemsetAsync(c->eLs.p, 0, n_p * 4, s));
+        ST_CUDA(c, cudaGetLastError());
+    }
+    u64 *sks = c->tv[1].as<u64>();
+    if (n_s) {
+        ST_TRY(morton_keys(c, in.spos.as<float>(), n_s, c->fr, sks, c->sorig.as<u32>()));
+        ST_CUDA(c, cudaMemcpyAsync(c->skey.p, sks, n_s * 8, cudaMemcpyDeviceToDevice, s));
+        ST_TRY(radix_sort_pairs(c, sks, c->sorig.as<u32>(), n_s));
+        k_gather_sources<<<grid_for(n_s, 256), 256, 0, s>>>(in.spos.as<float>(), in.L.as<double>(),
+                                                            c->sorig.as<u32>(), n_s, c->p.L_unit,
+                                                            c->sq.as<float4>(), c->sL.as<double>()); ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+    }
+    ST_TRY(build_octree(c, c->pt, pks, n_p, c->p.ptree_leaf, c->fr));
+    ST_TRY(build_octree(c, c->stree, sks, n_s, c->p.src_leaf, c->fr));
+    ST_TRY(tree_moments(c, c->stree, c->sq.as<float4>(), c->sL.as<double>(), c->p.L_unit));
+    if (diffuse) ST_TRY(build_octree(c, c->et, pks, n_p, c->p.src_leaf, c->fr));
+    else c->et.n = 0;
+    ST_TRY(build_neighbours(c));
+    phase_mark(c, START_PHASE_BUILD, true);
+    ST_CUDA(c, cudaStreamSynchronize(s));
+    ST_CUDA(c, cudaGetLastError());
+    if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency (neighbour lists)");
+    c->built = true;
+    return START_OK;
+}
+
+int start_set_state(start_ctx *c, const float *n_H, const double *y)
+{
+    if (!c) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c->device);
+    long long n = c->np;
+    if (n && !n_H) return set_err(c, START_EINVAL, "NULL n_H");
+    if (n == 0) {
+        c->has_state = true;
+        return START_OK;
+    }
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    Staged in;
+    ST_TRY(stage_in(c, in.h, n_H, n * sizeof(float)));
+    if (y) ST_TRY(stage_in(c, in.V, y, n * sizeof(double)));
+    k_check_nonneg_f<<<grid_for(n, 256), 256, 0, c->stream>>>(in.h.as<float>(), n, ctr + C_BAD_INPUT); ++c->launches;
+    if (y) { k_check_unit_d<<<grid_for(n, 256), 256, 0, c->stream>>>(in.V.as<double>(), n, ctr + C_BAD_INPUT); ++c->launches; }
+    ST_TRY(check_bad(c, "n_H or y"));
+    k_set_state<<<grid_for(n, 256), 256, 0, c->stream>>>(in.h.as<float>(), y ? in.V.as<double>() : nullptr,
+                                                        c->pinv.as<u32>(), n, c->nH.as<float>(),
+                                                        c->y.as<double>(), c->pq.as<float4>()); ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->has_state = true;
+    return START_OK;
+}
+
+int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_out)
+{
+    if (!c) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    if (!(theta >= 0.f) || !isfinite(theta)) return set_err(c, START_EINVAL, "theta must be >= 0");
+    DeviceGuard g(c->device);
+    long long n = c->np;
+    if (n_HI && n) {
+        Staged in;
+        unsigned long long *ctr = c->counters.as<unsigned long long>();
+        ST_TRY(stage_in(c, in.h, n_HI, n * sizeof(float)));
+        k_check_nonneg_f<<<grid_for(n, 256), 256, 0, c->stream>>>(in.h.as<float>(), n, ctr + C_BAD_INPUT); ++c->launches;
+        ST_TRY(check_bad(c, "n_HI"));
+        k_set_nHI<<<grid_for(n, 256), 256, 0, c->stream>>>(in.h.as<float>(), c->pinv.as<u32>(), n,
+                                                          c->pq.as<float4>()); ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+    } else if (!n_HI && c->diffuse && !c->has_state && n) {
+        return set_err(c, START_ENOTBUILT, "diffuse mode needs start_set_state");
+    }
+    ST_TRY(run_solve(c, theta, false));
+    bool dev_out = gamma_out && is_device_ptr(gamma_out);
+    if (gamma_out && !dev_out) ST_TRY(ensure(c->stage, (n ? n : 1) * sizeof(float)));
+    ST_TRY(finish_gamma(c, dev_out ? gamma_out : (gamma_out ? c->stage.as<float>() : nullptr)));
+    if (gamma_out && !dev_out) ST_TRY(copy_out(c, gamma_out, c->stage.p, n * sizeof(float)));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency (interaction lists)");
+    if (read_counter(c, C_CHAIN_OVF)) return set_err(c, START_ECHAIN, "a ray exceeded hop_cap");
+    c->solved = true;
+    return START_OK;
+}
+
+int start_ionize(start_ctx *c, double dt_s, double *y_out)
+{
+    if (!c) return START_EINVAL;
+    if (!c->built || !c->solved) return set_err(c, START_ENOTBUILT, "start_rt_solve first");
+    if (!(dt_s >= 0.0) || !isfinite(dt_s)) return set_err(c, START_EINVAL, "dt must be >= 0");
+    DeviceGuard g(c->device);
+    ST_TRY(run_ionize(c, dt_s));
+    if (y_out && c->np) {
+        bool dev = is_device_ptr(y_out);
+        double *dst = y_out;
+        if (!dev) {
+            ST_TRY(ensure(c->stage, c->np * sizeof(double)));
+            dst = c->stage.as<double>();
+        }
+        k_to_input_order<double><<<grid_for(c->np, 256), 256, 0, c->stream>>>(
+            c->y.as<double>(), c->porig.as<u32>(), c->np, dst); ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+        if (!dev) ST_TRY(copy_out(c, y_out, dst, c->np * sizeof(double)));
+    }
+    return START_OK;
+}
+
+int start_rt_solve_oneshot(const start_params *p, const float *pos, const float *h, long long n_p,
+                           const float *n_HI, const float *src_pos, const double *src_L,
+                           long long n_s, float theta, float *gamma_out)
+{
+    start_ctx *c = nullptr;
+    int rc = start_create(&c, p);
+    if (rc) return rc;
+    rc = start_build_trees(c, pos, h, n_p, src_pos, src_L, n_s, nullptr, 0);
+    if (!rc && n_p) rc = n_HI ? START_OK : START_EINVAL;
+    if (!rc) rc = start_rt_solve(c, n_HI, theta, gamma_out);
+    if (!rc) cudaStreamSynchronize(c->stream);
+    start_destroy(c);
+    return rc;
+}
+
+int start_get_frame(start_ctx *c, double out[4])
+{
+    if (!c || !out) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    for (int a = 0; a < 3; ++a) out[a] = c->fr.lo[a];
+    out[3] = c->fr.side;
+    return START_OK;
+}
+
+int start_get_perm(start_ctx *c, int which, unsigned *perm)
+{
+    if (!c || !perm || (which != 0 && which != 1)) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c->device);
+    long long n = which ? c->ns : c->np;
+    return copy_out(c, perm, which ? c->sorig.p : c->porig.p, n * sizeof(u32));
+}
+
+int start_get_keys(start_ctx *c, int which, unsigned long long *keys)
+{
+    if (!c || !keys || (which != 0 && which != 1)) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c->device);
+    long long n = which ? c->ns : c->np;
+    return copy_out(c, keys, which ? c->skey.p : c->pkey.p, n * sizeof(u64));
+}
+
+static Tree *pick_tree(start_ctx *c, int which)
+{
+    return which == 0 ? &c->pt : which == 1 ? &c->stree : which == 2 ? &c->et : nullptr;
+}
+
+long long start_tree_size(start_ctx *c, int which)
+{
+    if (!c || !pick_tree(c, which)) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    return pick_tree(c, which)->n;
+}
+
+int start_get_tree(start_ctx *c, int which, int *level, unsigned *first, unsigned *count,
+                   unsigned *skip, int *leaf, double *cube4, double *L, float *cen3)
+{
+    Tree *t = c ? pick_tree(c, which) : nullptr;
+    if (!t) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c->device);
+    long long n = t->n;
+    if (n == 0) return START_OK;
+    if (which == 2 && c->diffuse && c->has_state) ST_TRY(refresh_emitters(c));
+    std::vector<uint4> meta(n);
+    ST_CUDA(c, cudaMemcpyAsync(meta.data(), t->meta.p, n * sizeof(uint4), cudaMemcpyDeviceToHost,
+                               c->stream));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<unsigned> a(n), b(n), d(n);
+    std::vector<int> lf(n);
+    for (long long i = 0; i < n; ++i) {
+        d[i] = meta[i].x;
+        a[i] = meta[i].y;
+        b[i] = meta[i].z;
+        lf[i] = (int)meta[i].w;
+    }
+    ST_TRY(copy_out(c, level, t->level.p, n * sizeof(int)));
+    if (first) ST_CUDA(c, cudaMemcpy(first, a.data(), n * 4, cudaMemcpyDefault));
+    if (count) ST_CUDA(c, cudaMemcpy(count, b.data(), n * 4, cudaMemcpyDefault));
+    if (skip) ST_CUDA(c, cudaMemcpy(skip, d.data(), n * 4, cudaMemcpyDefault));
+    if (leaf) ST_CUDA(c, cudaMemcpy(leaf, lf.data(), n * 4, cudaMemcpyDefault));
+    ST_TRY(copy_out(c, cube4, t->cube.p, n * 4 * sizeof(double)));
+    bool has_mom = which != 0 && t->L.p && t->vsrc.p;
+    if (L) {
+        if (has_mom) ST_TRY(copy_out(c, L, t->L.p, n * sizeof(double)));
+        else ST_CUDA(c, cudaMemset(L, 0, n * sizeof(double)));
+    }
+    if (cen3) {
+        std::vector<float4> v(n);
+        if (has_mom) {
+            ST_CUDA(c, cudaMemcpyAsync(v.data(), t->vsrc.p, n * sizeof(float4),
+                                       cudaMemcpyDeviceToHost, c->stream));
+            ST_CUDA(c, cudaStreamSynchronize(c->stream));
+        } else {
+            memset(v.data(), 0, n * sizeof(float4));
+        }
+        std::vector<float> cc(3 * n);
+        for (long long i = 0; i < n; ++i) {
+            cc[3 * i] = v[i].x;
+            cc[3 * i + 1] = v[i].y;
+            cc[3 * i + 2] = v[i].z;
+        }
+        ST_CUDA(c, cudaMemcpy(cen3, cc.data(), 3 * n * sizeof(float), cudaMemcpyDefault));
+    }
+    return START_OK;
+}
+
+long long start_nbr_total(start_ctx *c)
+{
+    if (!c) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    return c->nb_total;
+}
+
+int start_get_neighbors(start_ctx *c, unsigned long long *off, unsigned *idx)
+{
+    if (!c || !off) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c->device);
+    long long n = c->np;
+    std::vector<u32> moff(n + 1), mval(c->nb_total), porig(n);
+    ST_CUDA(c, cudaMemcpy(moff.data(), c->nb_off.p, (n + 1) * 4, cudaMemcpyDeviceToHost));
+    if (c->nb_total) ST_CUDA(c, cudaMemcpy(mval.data(), c->nb_idx.p, c->nb_total * 4, cudaMemcpyDeviceToHost));
+    if (n) ST_CUDA(c, cudaMemcpy(porig.data(), c->porig.p, n * 4, cudaMemcpyDeviceToHost));
+    std::vector<u64> o;
+    std::vector<u32> v;
+    csr_to_input<u32>(n, moff, mval, porig, true, o, v);
+    ST_CUDA(c, cudaMemcpy(off, o.data(), (n + 1) * 8, cudaMemcpyDefault));
+    if (idx && !v.empty()) ST_CUDA(c, cudaMemcpy(idx, v.data(), v.size() * 4, cudaMemcpyDefault));
+    return START_OK;
+}
+
+int start_get_lists(start_ctx *c, float theta, unsigned long long *off, unsigned *entries)
+{
+    if (!c || !off) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    if (!(theta >= 0.f) || !isfinite(theta)) return set_err(c, START_EINVAL, "theta must be >= 0");
+    DeviceGuard g(c->device);
+    long long n = c->np;
+    if (c->diffuse && c->has_state) ST_TRY(refresh_emitters(c));
+    ST_TRY(run_walk(c, theta));
+    std::vector<u64> moff(n + 1);
+    std::vector<u32> mval(c->npairs), porig(n);
+    ST_CUDA(c, cudaMemcpy(moff.data(), c->loff.p, (n + 1) * 8, cudaMemcpyDeviceToHost));
+    if (c->npairs) ST_CUDA(c, cudaMemcpy(mval.data(), c->pent.p, c->npairs * 4, cudaMemcpyDeviceToHost));
+    if (n) ST_CUDA(c, cudaMemcpy(porig.data(), c->porig.p, n * 4, cudaMemcpyDeviceToHost));
+    std::vector<u64> o;
+    std::vector<u32> v;
+    csr_to_input<u64>(n, moff, mval, porig, false, o, v);
+    ST_CUDA(c, cudaMemcpy(off, o.data(), (n + 1) * 8, cudaMemcpyDefault));
+    if (entries && !v.empty()) ST_CUDA(c, cudaMemcpy(entries, v.data(), v.size() * 4, cudaMemcpyDefault));
+    return START_OK;
+}
+
+int start_get_emitter_L(start_ctx *c, float *out)
+{
+    if (!c || !out) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c->device);
+    if (c->np == 0) return START_OK;
+    if (c->diffuse && c->has_state) ST_TRY(refresh_emitters(c));
+    ST_TRY(ensure(c->stage, c->np * sizeof(float)));
+    k_to_input_order<float><<<grid_for(c->np, 256), 256, 0, c->stream>>>(
+        c->eLs.as<float>(), c->porig.as<u32>(), c->np, c->stage.as<float>()); ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    return copy_out(c, out, c->stage.p, c->np * sizeof(float));
+}
+
+int start_get_stats(start_ctx *c, start_stats *out)
+{
+    if (!c || !out) return START_EINVAL;
+    DeviceGuard g(c->device);
+    unsigned long long v[C_COUNT];
+    ST_CUDA(c, cudaMemcpyAsync(v, c->counters.p, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    memset(out, 0, sizeof(*out));
+    out->rays = (long long)v[C_RAYS];
+    out->hops = (long long)v[C_HOPS];
+    out->march_fallbacks = (long long)v[C_MARCH_FB];
+    out->walk_fallbacks = (long long)v[C_WALK_FB];
+    out->nbr_fallbacks = (long long)v[C_NBR_FB];
+    out->max_hops = (long long)v[C_MAX_HOPS];
+    out->nodes_src = c->stree.n;
+    out->nodes_emit = c->et.n;
+    out->nodes_part = c->pt.n;
+    out->nbr_total = c->nb_total;
+    out->launches = (long long)c->launches;
+    return START_OK;
+}
+
+int start_get_timings(start_ctx *c, double *ms, int n)
+{
+    if (!c || !ms || n < 0 || n > START_NPHASES) return START_EINVAL;
+    DeviceGuard g(c->device);
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < n; ++k) {
+        ms[k] = -1.0;
+        if (c->ev_init && c->ev_rec[k]) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, c->ev[2 * k], c->ev[2 * k + 1]) == cudaSuccess) ms[k] = t;
+            else cudaGetLastError();
+        }
+    }
+    return START_OK;
+}
+
+const char *start_last_error(const start_ctx *c)
+{
+    if (!c) return "NULL context";
+    return c->err.c_str();
+}
+
+const char *start_status_string(int s)
+{
+    switch (s) {
+    case START_OK: return "START_OK";
+    case START_EINVAL: return "START_EINVAL";
+    case START_ENOMEM: return "START_ENOMEM";
+    case START_ENOTBUILT: return "START_ENOTBUILT";
+    case START_ECUDA: return "START_ECUDA";
+    case START_ETIMEOUT: return "START_ETIMEOUT";
+    case START_ECHAIN: return "START_ECHAIN";
+    case START_ERANGE: return "START_ERANGE";
+    default: return "START_E?";
+    }
+}
+
+}  // extern "C"

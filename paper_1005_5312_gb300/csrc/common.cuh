@@ -1,0 +1,251 @@
+// Internal declarations of the START GB300 library: the context, device
+// buffers, launch wrappers shared between translation units, and the
+// device-side geometric predicates.
+//
+// Every discrete decision of the method (Morton cell, octree split, the
+// opening test of Eqs. con1/con2, the neighbour test, the upstream choice of
+// Eq. tau) is evaluated first in FP32 with a certified error bound and,
+// when the FP32 margin is inside that bound, again in FP64 with a fixed
+// operation order and no fused multiply-add (the __d*_rn intrinsics are
+// never contracted).  The FP64 expressions are the definitions stated in
+// start.h, so every decision is the one the FP64 definition takes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "start.h"
+
+namespace st {
+
+typedef uint32_t u32;
+typedef uint64_t u64;
+
+constexpr int kLevels = 21;                 // Morton bits per axis
+constexpr u32 kEntrySrc = START_ENTRY_SOURCE;
+constexpr u32 kEntryEmit = START_ENTRY_EMITTER;
+constexpr u32 kEntryIdMask = 0x3fffffffu;
+constexpr float kU32 = 5.9604645e-8f;       // unit roundoff of float32, 2^-24
+
+// ---------------------------------------------------------------- buffers
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Grow-only device buffer; returns a START_* status.
+int ensure(DBuf &b, size_t bytes);
+void release(DBuf &b);
+
+// ---------------------------------------------------------------- trees
+// Octree in depth-first pre-order (children in octant order).
+struct Tree {
+    long long n = 0;           // nodes
+    int depth = 0;             // deepest level present
+    DBuf box;                  // float4: cube lower corner (rounded to float), edge
+    DBuf meta;                 // uint4: skip, first, count, leaf
+    DBuf cube;                 // double4-like: lower corner x,y,z, edge (exact frame values)
+    DBuf level;                // int
+    DBuf vsrc;                 // float4: luminosity centre, L / L_unit
+    DBuf L;                    // double summed luminosity (photons/s)
+    DBuf M;                    // double[3] summed L * r
+    // breadth-first bookkeeping used by the bottom-up moments
+    std::vector<long long> lvl_off;   // BFS index of the first node of each level
+    DBuf bfs2dfs;              // u32
+    DBuf bfs_first, bfs_count; // u32
+    DBuf bfs_cb, bfs_nc;       // u32 first child (BFS index), child count
+};
+
+struct Frame {
+    double lo[3];
+    double side;
+    double scale;              // 2^21 / side
+    float cmag;                // bound on |coordinate| of any point or cube corner
+};
+
+}  // namespace st
+
+struct start_ctx {
+    start_params p;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    bool built = false, has_state = false, solved = false, diffuse = false;
+    long long np = 0, ns = 0;
+    st::Frame fr;
+
+    // particles, Morton order
+    st::DBuf pq;      // float4 x, y, z, n_HI
+    st::DBuf ph;      // float h
+    st::DBuf porig;   // u32 sorted rank -> input index
+    st::DBuf pinv;    // u32 input index -> sorted rank
+    st::DBuf pkey;    // u64 Morton key, input order
+    st::DBuf nH;      // float n_H
+    st::DBuf y;       // double neutral fraction
+    st::DBuf V;       // double volume (len_unit^3)
+    st::DBuf gam;     // float Gamma (cgs)
+    st::DBuf eL;      // double emitter luminosity, photons/s
+    st::DBuf eLs;     // float emitter luminosity / L_unit
+
+    // sources, sorted order
+    st::DBuf sq;      // float4 x, y, z, L / L_unit
+    st::DBuf sorig;   // u32 sorted rank -> input index
+    st::DBuf skey;    // u64 Morton key, input order
+    st::DBuf sL;      // double L, sorted order
+
+    st::Tree pt, stree, et;
+
+    st::DBuf nb_off;  // u32 [np + 1]
+    st::DBuf nb_idx;  // u32 Morton indices
+    long long nb_total = 0;
+
+    // solve workspace
+    st::DBuf lcount;  // u32 per target
+    st::DBuf loff;    // u64 [np + 1]
+    st::DBuf pent;    // u32 entry per pair
+    st::DBuf ptgt;    // u32 target per pair
+    st::DBuf pcon;    // float contribution per pair
+    long long npairs = 0;
+
+    // generic scratch
+    st::DBuf tk[2], tv[2], hist, scan_tmp, stage, flags;
+    st::DBuf counters; // u64[16]
+
+    start_stats stats{};
+    unsigned long long launches = 0;        // kernels launched by this context
+    cudaEvent_t ev[2 * START_NPHASES] = {};  // phase begin/end events (timing = 1)
+    bool ev_init = false;
+    bool ev_rec[START_NPHASES] = {};
+};
+
+namespace st {
+
+// counters[] slots
+enum Counter {
+    C_RAYS = 0, C_HOPS, C_MARCH_FB, C_WALK_FB, C_NBR_FB, C_MAX_HOPS, C_BAD_INPUT, C_CHAIN_OVF,
+    C_INTERNAL,   // count/fill disagreement or an out-of-range index (never expected)
+    C_COUNT = 16
+};
+
+// ---------------------------------------------------------------- error helpers
+int set_err(start_ctx *c, int code, const std::string &msg);
+int cuda_check(start_ctx *c, cudaError_t e, const char *what);
+#define ST_CUDA(c, expr)                                              \
+    do {                                                              \
+        cudaError_t e_ = (expr);                                      \
+        if (e_ != cudaSuccess) return ::st::cuda_check((c), e_, #expr); \
+    } while (0)
+#define ST_TRY(expr)                  \
+    do {                              \
+        int r_ = (expr);              \
+        if (r_ != START_OK) return r_; \
+    } while (0)
+
+inline unsigned grid_for(long long n, int threads, long long cap = 1 << 30)
+{
+    long long g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// Records the begin (end = false) or end event of a phase when timing is on.
+void phase_mark(start_ctx *c, int phase, bool end);
+
+// ---------------------------------------------------------------- launch wrappers
+// scan_sort.cu
+int exclusive_scan_u32(start_ctx *c, const u32 *in, u32 *out, long long n, u32 *total_dev);
+int exclusive_scan_u32_to_u64(start_ctx *c, const u32 *in, u64 *out, long long n);
+int radix_sort_pairs(start_ctx *c, u64 *keys, u32 *vals, long long n);
+int compute_frame(start_ctx *c, const float *ppos, long long np, const float *spos, long long ns,
+                  Frame *fr);
+int morton_keys(start_ctx *c, const float *pos_soa, long long n, const Frame &fr, u64 *keys,
+                u32 *idx);
+
+// tree.cu
+int build_octree(start_ctx *c, Tree &t, const u64 *sorted_keys, long long n, int leaf,
+                 const Frame &fr);
+int tree_moments(start_ctx *c, Tree &t, const float4 *mem_pos, const double *mem_L,
+                 double L_unit);
+void tree_release(Tree &t);
+
+// neighbors.cu
+int build_neighbours(start_ctx *c);
+
+// solve.cu
+int run_solve(start_ctx *c, float theta, bool keep_lists);
+int run_ionize(start_ctx *c, double dt);
+int refresh_emitters(start_ctx *c);
+
+// ---------------------------------------------------------------- device helpers
+// FP64 squared distance with the operation order of the definition:
+// ((ax-bx)^2 + (ay-by)^2) + (az-bz)^2, never contracted.
+__device__ __forceinline__ double d2_64(double ax, double ay, double az, double bx, double by,
+                                        double bz)
+{
+    double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by), dz = __dsub_rn(az, bz);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Squared distance from p to the cube [lo, lo + l]^3, FP64, the definition's
+// order: per axis lo - p below, p - hi above, 0 inside; then summed.
+__device__ __forceinline__ double box_d2_64(const double *lo, double l, double px, double py,
+                                            double pz)
+{
+    double p[3] = {px, py, pz};
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double lw = lo[a], hi = __dadd_rn(lo[a], l);
+        d[a] = 0.0;
+        if (p[a] < lw) d[a] = __dsub_rn(lw, p[a]);
+        else if (p[a] > hi) d[a] = __dsub_rn(p[a], hi);
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+// Opening test of Eq. con1 in FP64: l^2 <= theta^2 d^2.
+__device__ __forceinline__ bool accept_64(const double *cube4, double th2, float px, float py,
+                                          float pz)
+{
+    double l = cube4[3];
+    double d2 = box_d2_64(cube4, l, (double)px, (double)py, (double)pz);
+    return __dmul_rn(l, l) <= __dmul_rn(th2, d2);
+}
+
+// Opening test with the FP32 filter.  box = (lo.x, lo.y, lo.z, l) rounded to
+// float; cmag bounds every |coordinate|.  Returns 1 accept, 0 reject,
+// -1 undecided (the caller evaluates accept_64).
+__device__ __forceinline__ int accept_32(float4 box, float th2, float px, float py, float pz,
+                                         float cmag)
+{
+    // every operation explicitly rounded: the count and fill passes of the
+    // walk must take bit-identical decisions
+    float l = box.w;
+    float hx = __fadd_rn(box.x, l), hy = __fadd_rn(box.y, l), hz = __fadd_rn(box.z, l);
+    float dx = px < box.x ? __fsub_rn(box.x, px) : (px > hx ? __fsub_rn(px, hx) : 0.f);
+    float dy = py < box.y ? __fsub_rn(box.y, py) : (py > hy ? __fsub_rn(py, hy) : 0.f);
+    float dz = pz < box.z ? __fsub_rn(box.z, pz) : (pz > hz ? __fsub_rn(pz, hz) : 0.f);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    float l2 = __fmul_rn(l, l);
+    float t = __fmul_rn(th2, d2);
+    float m = __fsub_rn(t, l2);
+    // error bound: coordinates of the cube and of its far side carry up to
+    // 3u*cmag each; every rounded operation adds u of its result.
+    float d = __fsqrt_rn(d2);
+    float e = __fmul_rn(kU32, __fadd_rn(__fmul_rn(3.f, cmag), d));
+    float b1 = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(3.4641f, d), e), __fmul_rn(__fmul_rn(3.f, e), e)),
+                         __fmul_rn(__fmul_rn(5.1f, kU32), d2));
+    float bound = __fadd_rn(__fadd_rn(__fmul_rn(th2, b1), __fmul_rn(__fmul_rn(3.1f, kU32), l2)),
+                            __fmul_rn(__fmul_rn(2.1f, kU32), t));
+    bound = __fadd_rn(__fmul_rn(2.f, bound), 1e-30f);
+    if (m > bound) return 1;
+    if (m < -bound) return 0;
+    return -1;
+}
+
+}  // namespace st

@@ -1,0 +1,530 @@
+// The radiative-transfer solve: source-tree walk (Eqs. con1, con2), upstream
+// ray march (Eq. tau with the trapezoidal d_tau of Section 2.2.1), Gamma
+// accumulation (Eq. solution2 with geometric dilution, summed as in Eq.
+// ksum), the implicit hydrogen update (Appendix A) and the diffuse emitters
+// of Section 4.1 (N_rec = alpha_1 n_e n_p V, self term of Eq. kself1).
+//
+// Layout: particles in Morton order as float4 (x, y, z, n_HI), so one
+// 16-byte load per neighbour brings both the position used by the upstream
+// test and the density used by d_tau.  Neighbour lists are CSR of Morton
+// indices.  The walk writes one (entry, target) pair per ray; the march
+// evaluates every pair with G cooperating lanes (one neighbour slot per lane
+// per step), and a per-target pass sums the contributions in list order.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace st {
+
+constexpr u32 kNone = 0xffffffffu;
+
+// ---------------------------------------------------------------- walk
+struct TreeView {
+    const float4 *box;
+    const uint4 *meta;
+    const double *cube;
+    u32 n;
+};
+
+template <bool FILL>
+__device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2f, double th2d,
+                                          float cmag, u32 self, u32 tag, u32 i, u32 &c, u64 &w,
+                                          u64 wend, u32 *ent, u32 *tgt, unsigned &fb)
+{
+    u32 n = 0;
+    while (n < t.n) {
+        float4 b = t.box[n];
+        uint4 mt = t.meta[n];
+        int a = accept_32(b, th2f, p.x, p.y, p.z, cmag);
+        if (a < 0) {
+            a = accept_64(t.cube + 4 * (size_t)n, th2d, p.x, p.y, p.z) ? 1 : 0;
+            ++fb;
+        }
+        if (a) {
+            if (FILL) {
+                if (w < wend) { ent[w] = n | tag; tgt[w] = i; }   // never past this row
+                ++w;
+            } else {
+                ++c;
+            }
+            n = mt.x;
+        } else if (mt.w) {
+            for (u32 r = mt.y; r < mt.y + mt.z; ++r) {
+                if (r == self) continue;
+                if (FILL) {
+                    if (w < wend) { ent[w] = kEntrySrc | tag | r; tgt[w] = i; }
+                    ++w;
+                } else {
+                    ++c;
+                }
+            }
+            n = mt.x;
+        } else {
+            n = n + 1;
+        }
+    }
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long np, TreeView st_,
+                                              TreeView et_, float th2f, double th2d, float cmag,
+                                              u32 *cnt, const u64 *off, u32 *ent, u32 *tgt,
+                                              unsigned long long *fb_total)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned fb = 0;
+    if (i < np) {
+        float4 p = pq[i];
+        u32 c = 0;
+        u64 w = FILL ? off[i] : 0ull;
+        const u64 wend = FILL ? off[i + 1] : 0ull;
+        walk_tree<FILL>(st_, p, th2f, th2d, cmag, kNone, 0u, (u32)i, c, w, wend, ent, tgt, fb);
+        walk_tree<FILL>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, (u32)i, c, w, wend, ent, tgt,
+                        fb);
+        if (!FILL) cnt[i] = c;
+        else if (w != wend) atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
+    }
+    if (!FILL) {
+        for (int o = 16; o; o >>= 1) fb += __shfl_xor_sync(0xffffffffu, fb, o);
+        if ((threadIdx.x & 31) == 0 && fb) atomicAdd(fb_total, (unsigned long long)fb);
+    }
+}
+
+// ---------------------------------------------------------------- march
+struct MarchArgs {
+    const u32 *pent, *ptgt;
+    long long npairs;
+    u32 np, n_svs, n_ssrc, n_evs;   // bounds of every index the march dereferences
+    const float4 *pq;
+    const u32 *nb_off, *nb_idx, *porig;
+    const float4 *svsrc;   // source-tree virtual sources (centre, L / L_unit)
+    const float4 *ssrc;    // individual sources (position, L / L_unit), sorted
+    const float4 *evsrc;   // emitter-tree virtual sources
+    const float *eLs;      // individual emitters' L / L_unit, Morton order
+    float sig;             // sigma * len_unit (per length unit per cm^-3)
+    float rfloor2;         // squared dilution floor
+    float tau_cut;
+    long long hop_cap;
+    float *pcon;           // per-pair contribution L e^-tau / (4 pi r^2), scaled units
+    unsigned long long *counters;
+};
+
+// Position and L / L_unit of a pair's source; an out-of-range entry (never
+// expected) yields a dark source and raises the internal-error counter.
+__device__ __forceinline__ float4 pair_source(const MarchArgs &a, u32 e)
+{
+    u32 id = e & kEntryIdMask;
+    bool src = (e & kEntrySrc) != 0;
+    u32 lim = (e & kEntryEmit) ? (src ? a.np : a.n_evs) : (src ? a.n_ssrc : a.n_svs);
+    if (id >= lim) {
+        atomicAdd(&a.counters[C_INTERNAL], 1ull);
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (!(e & kEntryEmit)) return src ? a.ssrc[id] : a.svsrc[id];
+    if (src) {
+        float4 q = a.pq[id];
+        return make_float4(q.x, q.y, q.z, a.eLs[id]);
+    }
+    return a.evsrc[id];
+}
+
+__device__ __forceinline__ u32 pair_target(const MarchArgs &a, long long p)
+{
+    u32 t = a.ptgt[p];
+    if (t >= a.np) {
+        atomicAdd(&a.counters[C_INTERNAL], 1ull);
+        return 0u;
+    }
+    return t;
+}
+
+// FP64 upstream choice with the definition's operation order; the group's
+// lanes share the neighbour slots and reduce with (c desc, input index asc).
+template <int G>
+__device__ u32 upstream_64(const MarchArgs &a, float4 pj, float4 src, u32 s0, u32 s1, int gl,
+                           unsigned gmask)
+{
+    double jx = pj.x, jy = pj.y, jz = pj.z, sx = src.x, sy = src.y, sz = src.z;
+    double Dj = d2_64(jx, jy, jz, sx, sy, sz);
+    double bx = __dsub_rn(sx, jx), by = __dsub_rn(sy, jy), bz = __dsub_rn(sz, jz);
+    double bc = 0.0;
+    u32 bo = kNone, bk = kNone;
+    for (u32 s = s0 + gl; s < s1; s += G) {
+        u32 k = a.nb_idx[s];
+        if (k >= a.np) continue;
+        float4 pk = a.pq[k];
+        double kx = pk.x, ky = pk.y, kz = pk.z;
+        double Dk = d2_64(kx, ky, kz, sx, sy, sz);
+        if (!(Dk < Dj)) continue;
+        double ax = __dsub_rn(kx, jx), ay = __dsub_rn(ky, jy), az = __dsub_rn(kz, jz);
+        double dot = __dadd_rn(__dadd_rn(__dmul_rn(bx, ax), __dmul_rn(by, ay)), __dmul_rn(bz, az));
+        double cval = __ddiv_rn(dot, __dsqrt_rn(d2_64(kx, ky, kz, jx, jy, jz)));
+        u32 o = a.porig[k];
+        if (bk == kNone || cval > bc || (cval == bc && o < bo)) {
+            bk = k;
+            bc = cval;
+            bo = o;
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off; off >>= 1) {
+        double oc = __shfl_xor_sync(gmask, bc, off, G);
+        u32 oo = __shfl_xor_sync(gmask, bo, off, G);
+        u32 ok = __shfl_xor_sync(gmask, bk, off, G);
+        bool take = ok != kNone && (bk == kNone || oc > bc || (oc == bc && oo < bo));
+        if (take) {
+            bc = oc;
+            bo = oo;
+            bk = ok;
+        }
+    }
+    return bk;
+}
+
+// One ray per group of G lanes; groups refill independently so that the
+// warp stays converged on the hop body.
+template <int G>
+__global__ void __launch_bounds__(256) k_march(MarchArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const int gbase = lane - gl;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const long long ngroups = ((long long)gridDim.x * blockDim.x) / G;
+    const float two_eps = 32.f * kU32;
+    const float eps_q = 16.f * kU32;
+
+    unsigned long long rays = 0, hops = 0, fbs = 0, ovf = 0;
+    u32 maxh = 0;
+
+    long long pidx = gid;
+    bool have = pidx < a.npairs;
+    float4 src = make_float4(0.f, 0.f, 0.f, 0.f), pt = src;
+    u32 j = 0, nh = 0;
+    float tau = 0.f, comp = 0.f;
+    if (have) {
+        src = pair_source(a, a.pent[pidx]);
+        j = pair_target(a, pidx);
+        pt = a.pq[j];
+    }
+    while (__any_sync(0xffffffffu, have)) {
+        if (have) {
+            float4 pj = a.pq[j];
+            float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
+            float bn = sqrtf(bx * bx + by * by + bz * bz);
+            u32 s0 = a.nb_off[j], s1 = a.nb_off[j + 1];
+            float bc = -1.f, sc = -1.f;
+            u32 bk = kNone;
+            bool unsure = false;
+#pragma unroll 4
+            for (u32 s = s0 + gl; s < s1; s += G) {
+                u32 k = a.nb_idx[s];
+                if (k >= a.np) continue;   // cannot happen: lists hold particle indices
+                float4 pk = a.pq[k];
+                float ax = pk.x - pj.x, ay = pk.y - pj.y, az = pk.z - pj.z;
+                float dot = bx * ax + by * ay + bz * az;
+                float a2 = ax * ax + ay * ay + az * az;
+                float an = sqrtf(a2);
+                float q = 2.f * dot - a2;
+                float eq = eps_q * (2.f * an * bn + a2) + 1e-37f;
+                if (q > eq) {
+                    float cv = __fdiv_rn(dot, an);
+                    if (cv > bc) {
+                        sc = bc;
+                        bc = cv;
+                        bk = k;
+                    } else if (cv > sc) {
+                        sc = cv;
+                    }
+                } else if (q >= -eq) {
+                    unsure = true;
+                }
+            }
+            float mc = bc;
+            u32 mk = bk;
+#pragma unroll
+            for (int o = G / 2; o; o >>= 1) {
+                float oc = __shfl_xor_sync(gmask, mc, o, G);
+                u32 ok = __shfl_xor_sync(gmask, mk, o, G);
+                if (oc > mc || (oc == mc && ok < mk)) {
+                    mc = oc;
+                    mk = ok;
+                }
+            }
+            // every certified candidate has c > 0; -1 marks "none"
+            float lim = mc - two_eps * bn;
+            bool amb = unsure || (bk != mk && bc > 0.f && bc > lim) || (sc > 0.f && sc > lim);
+            if (__any_sync(gmask, amb)) {
+                mk = upstream_64<G>(a, pj, src, s0, s1, gl, gmask);
+                ++fbs;
+            }
+            ++nh;
+            bool done = false;
+            float dt;
+            if (mk == kNone) {
+                dt = a.sig * pj.w * bn;
+                done = true;
+            } else {
+                float4 pu = a.pq[mk];
+                float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
+                float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
+                float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+                float dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
+                dt = a.sig * 0.5f * (pj.w + pu.w) * dl;
+                j = mk;
+            }
+            float yk = dt - comp;
+            float tk = tau + yk;
+            comp = (tk - tau) - yk;
+            tau = tk;
+            if (tau > a.tau_cut) done = true;
+            if (!done && (long long)nh > a.hop_cap) {
+                done = true;
+                if (gl == 0) ++ovf;
+            }
+            if (done) {
+                if (gl == 0) {
+                    float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
+                    float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.rfloor2);
+                    a.pcon[pidx] = src.w * expf(-tau) / (12.566370614359172f * r2);
+                    ++rays;
+                    hops += nh;
+                    maxh = max(maxh, nh);
+                }
+                pidx += ngroups;
+                have = pidx < a.npairs;
+                if (have) {
+                    src = pair_source(a, a.pent[pidx]);
+                    j = pair_target(a, pidx);
+                    pt = a.pq[j];
+                    tau = 0.f;
+                    comp = 0.f;
+                    nh = 0;
+                }
+            }
+        }
+    }
+    if (gl != 0) fbs = 0;  // every lane of a group counted the same fallbacks
+    for (int o = 16; o; o >>= 1) {
+        rays += __shfl_xor_sync(0xffffffffu, rays, o);
+        hops += __shfl_xor_sync(0xffffffffu, hops, o);
+        fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
+        ovf += __shfl_xor_sync(0xffffffffu, ovf, o);
+        maxh = max(maxh, __shfl_xor_sync(0xffffffffu, maxh, o));
+    }
+    if (lane == 0) {
+        if (rays) atomicAdd(&a.counters[C_RAYS], rays);
+        if (hops) atomicAdd(&a.counters[C_HOPS], hops);
+        if (fbs) atomicAdd(&a.counters[C_MARCH_FB], fbs);
+        if (ovf) atomicAdd(&a.counters[C_CHAIN_OVF], ovf);
+        if (maxh) atomicMax(&a.counters[C_MAX_HOPS], (unsigned long long)maxh);
+    }
+}
+
+// ---------------------------------------------------------------- Gamma
+// Per target: compensated sum of its contributions in list order, converted
+// to photons cm^-2 s^-1.
+__global__ void k_gamma(const float *pcon, const u64 *off, long long np, float conv,
+                        const u32 *porig, float *gam, float *gout)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    float s = 0.f, cmp = 0.f;
+    for (u64 e = off[i]; e < off[i + 1]; ++e) {
+        float yk = pcon[e] - cmp;
+        float tk = s + yk;
+        cmp = (tk - s) - yk;
+        s = tk;
+    }
+    float g = s * conv;
+    gam[i] = g;
+    if (gout) gout[porig[i]] = g;
+}
+
+// ---------------------------------------------------------------- emitters
+// N_rec = alpha_1 (x n_H)^2 V (Section 4.1), same operation order as the
+// definition: ((alpha_1 n_e) n_e) (V len^3).
+__global__ void k_emitters(const double *y, const float *nH, const double *V, long long np,
+                           double a1, double lu3, double L_unit, double *eL, float *eLs)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    double ne = __dmul_rn(__dsub_rn(1.0, y[i]), (double)nH[i]);
+    double L = __dmul_rn(__dmul_rn(__dmul_rn(a1, ne), ne), __dmul_rn(V[i], lu3));
+    eL[i] = L;
+    eLs[i] = __double2float_rn(__ddiv_rn(L, L_unit));
+}
+
+int refresh_emitters(start_ctx *c)
+{
+    if (!c->diffuse || c->np == 0) return START_OK;
+    double lu = c->p.len_unit_cm;
+    double lu3 = (lu * lu) * lu;
+    double a1 = c->p.alpha_A - c->p.alpha_B;
+    phase_mark(c, START_PHASE_EMIT, false);
+    k_emitters<<<grid_for(c->np, 256), 256, 0, c->stream>>>(
+        c->y.as<double>(), c->nH.as<float>(), c->V.as<double>(), c->np, a1, lu3, c->p.L_unit,
+        c->eL.as<double>(), c->eLs.as<float>()); ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    ST_TRY(tree_moments(c, c->et, c->pq.as<float4>(), c->eL.as<double>(), c->p.L_unit));
+    phase_mark(c, START_PHASE_EMIT, true);
+    return START_OK;
+}
+
+// ---------------------------------------------------------------- solve
+template <int G>
+static void launch_march(const MarchArgs &a, cudaStream_t s, int nsm)
+{
+    long long groups_needed = a.npairs;
+    long long threads = groups_needed * G;
+    long long blocks = (threads + 255) / 256;
+    long long cap = (long long)nsm * 8;   // 8 resident blocks of 256 threads per SM
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_march<G><<<(unsigned)blocks, 256, 0, s>>>(a);
+}
+
+// Interaction lists of every target: count, scan, fill.
+int run_walk(start_ctx *c, float theta)
+{
+    long long np = c->np;
+    cudaStream_t s = c->stream;
+    c->npairs = 0;
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    if (np == 0) return START_OK;
+    phase_mark(c, START_PHASE_WALK, false);
+    TreeView sv{c->stree.box.as<float4>(), c->stree.meta.as<uint4>(), c->stree.cube.as<double>(),
+                (u32)c->stree.n};
+    TreeView ev{c->et.box.as<float4>(), c->et.meta.as<uint4>(), c->et.cube.as<double>(),
+                (u32)(c->diffuse ? c->et.n : 0)};
+    float th2f = theta * theta;
+    double th2d = (double)theta * (double)theta;
+    ST_TRY(ensure(c->lcount, np * sizeof(u32)));
+    ST_TRY(ensure(c->loff, (np + 1) * sizeof(u64)));
+    k_walk<false><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), np, sv, ev, th2f, th2d,
+                                                    c->fr.cmag, c->lcount.as<u32>(), nullptr,
+                                                    nullptr, nullptr, ctr + C_WALK_FB); ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    ST_TRY(exclusive_scan_u32_to_u64(c, c->lcount.as<u32>(), c->loff.as<u64>(), np));
+    unsigned long long total = 0;
+    ST_CUDA(c, cudaMemcpyAsync(&total, c->loff.as<u64>() + np, sizeof(total),
+                               cudaMemcpyDeviceToHost, s));
+    ST_CUDA(c, cudaStreamSynchronize(s));
+    c->npairs = (long long)total;
+    size_t np2 = total ? total : 1;
+    if (ensure(c->pent, np2 * sizeof(u32)) || ensure(c->ptgt, np2 * sizeof(u32)) ||
+        ensure(c->pcon, np2 * sizeof(float)))
+        return set_err(c, START_ENOMEM, "out of device memory (interaction lists)");
+    k_walk<true><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), np, sv, ev, th2f, th2d,
+                                                   c->fr.cmag, nullptr, c->loff.as<u64>(),
+                                                   c->pent.as<u32>(), c->ptgt.as<u32>(), ctr + C_INTERNAL); ++c->launches;
+    phase_mark(c, START_PHASE_WALK, true);
+    return cuda_check(c, cudaGetLastError(), "k_walk");
+}
+
+int run_solve(start_ctx *c, float theta, bool /*keep_lists*/)
+{
+    long long np = c->np;
+    cudaStream_t s = c->stream;
+    c->npairs = 0;
+    ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    if (np == 0) return START_OK;
+    if (c->diffuse) ST_TRY(refresh_emitters(c));
+    ST_TRY(run_walk(c, theta));
+
+    MarchArgs a;
+    a.pent = c->pent.as<u32>();
+    a.ptgt = c->ptgt.as<u32>();
+    a.npairs = c->npairs;
+    a.np = (u32)np;
+    a.n_svs = (u32)c->stree.n;
+    a.n_ssrc = (u32)c->ns;
+    a.n_evs = (u32)(c->diffuse ? c->et.n : 0);
+    a.pq = c->pq.as<float4>();
+    a.nb_off = c->nb_off.as<u32>();
+    a.nb_idx = c->nb_idx.as<u32>();
+    a.porig = c->porig.as<u32>();
+    a.svsrc = c->stree.vsrc.as<float4>();
+    a.ssrc = c->sq.as<float4>();
+    a.evsrc = c->et.vsrc.as<float4>();
+    a.eLs = c->eLs.as<float>();
+    a.sig = (float)(c->p.sigma_cm2 * c->p.len_unit_cm);
+    double rf = 1e-6 * c->fr.side;
+    a.rfloor2 = (float)(rf * rf);
+    a.tau_cut = (float)c->p.tau_cut;
+    a.hop_cap = c->p.hop_cap > 0 ? c->p.hop_cap : np + 1;
+    a.pcon = c->pcon.as<float>();
+    a.counters = ctr;
+    if (c->npairs > 0) {
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+        if (nsm <= 0) nsm = 1;
+        phase_mark(c, START_PHASE_MARCH, false);
+        switch (c->p.march_group) {
+        case 32: launch_march<32>(a, s, nsm); break;
+        case 16: launch_march<16>(a, s, nsm); break;
+        default: launch_march<8>(a, s, nsm); break;
+        }
+        ++c->launches;
+        phase_mark(c, START_PHASE_MARCH, true);
+        ST_CUDA(c, cudaGetLastError());
+    }
+    return START_OK;
+}
+
+// Writes Gamma (Morton, resident) and optionally the input-order copy.
+int finish_gamma(start_ctx *c, float *gout_dev)
+{
+    if (c->np == 0) return START_OK;
+    float conv = (float)(c->p.L_unit / (c->p.len_unit_cm * c->p.len_unit_cm));
+    phase_mark(c, START_PHASE_GAMMA, false);
+    k_gamma<<<grid_for(c->np, 256), 256, 0, c->stream>>>(c->pcon.as<float>(), c->loff.as<u64>(),
+                                                          c->np, conv, c->porig.as<u32>(),
+                                                          c->gam.as<float>(), gout_dev);
+    return cuda_check(c, cudaGetLastError(), "k_gamma");
+}
+
+// ---------------------------------------------------------------- ionise
+// One backward-Euler step of dy/dt = -k y + alpha n_H (1 - y)^2 in the
+// neutral fraction y (hydrogen only, n_e = x n_H), solved with the
+// cancellation-free root 2c / (b + sqrt((K+1)^2 + 4A(K+1-y0))).
+__global__ void k_ionize(double *y, float4 *pq, const float *gam, const float *nH, const double *V,
+                         long long np, double dt, double sigma, double alpha, double a1,
+                         double len_cm, int diffuse)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    double y0 = y[i];
+    double nh = (double)nH[i];
+    double k = sigma * (double)gam[i];
+    if (diffuse) {
+        double x0 = 1.0 - y0;
+        double R = cbrt(3.0 * V[i] / (4.0 * 3.14159265358979323846)) * len_cm;
+        double ts = sigma * (y0 * nh) * R;
+        double phi = ts > 0.0 ? -expm1(-ts) / ts : 1.0;
+        k += a1 * x0 * x0 * nh * nh * sigma * R * phi;
+    }
+    double A = alpha * nh * dt, K = k * dt;
+    double b = 2.0 * A + K + 1.0, cc = A + y0;
+    double disc = (K + 1.0) * (K + 1.0) + 4.0 * A * (K + 1.0 - y0);
+    double y1 = 2.0 * cc / (b + sqrt(disc));
+    y[i] = y1;
+    pq[i].w = __double2float_rn(y1 * nh);
+}
+
+int run_ionize(start_ctx *c, double dt)
+{
+    if (c->np == 0) return START_OK;
+    double alpha = c->diffuse ? c->p.alpha_A : c->p.alpha_B;
+    phase_mark(c, START_PHASE_IONIZE, false);
+    k_ionize<<<grid_for(c->np, 256), 256, 0, c->stream>>>(
+        c->y.as<double>(), c->pq.as<float4>(), c->gam.as<float>(), c->nH.as<float>(),
+        c->V.as<double>(), c->np, dt, c->p.sigma_cm2, alpha, c->p.alpha_A - c->p.alpha_B,
+        c->p.len_unit_cm, c->diffuse ? 1 : 0); ++c->launches;
+    phase_mark(c, START_PHASE_IONIZE, true);
+    return cuda_check(c, cudaGetLastError(), "k_ionize");
+}
+
+}  // namespace st

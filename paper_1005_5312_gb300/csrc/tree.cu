@@ -1,0 +1,318 @@
+// Octree over Morton-sorted members (Section 2.2.2: cubic cells divided into
+// 8 subcells until a cell holds at most `leaf` members, one radiation source
+// per cell for the source tree) and its luminosity moments (L = sum L_j,
+// r = sum L_j r_j / sum L_j; the same form with N_rec for emitters, Eq. ssum).
+//
+// Construction is level-synchronous: the children of every split cell of a
+// level are found by binary search of the octant digit in the sorted keys
+// (one thread per cell), compacted by a scan, and appended as the next
+// level.  Subtree sizes (bottom-up) then give every node its depth-first
+// pre-order index and skip pointer, which is the layout the stackless walks
+// read.
+#include "common.cuh"
+
+namespace st {
+
+int ensure_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s);
+
+__device__ __forceinline__ int digit_at(u64 key, int level)
+{
+    return (int)((key >> (3 * (kLevels - level))) & 7u);
+}
+
+// first index in [lo, hi) whose digit at `level` is >= d (digits ascend)
+__device__ __forceinline__ u32 lower_digit(const u64 *keys, u32 lo, u32 hi, int level, int d)
+{
+    while (lo < hi) {
+        u32 mid = lo + ((hi - lo) >> 1);
+        if (digit_at(keys[mid], level) < d) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_count_children(const u64 *keys, const u32 *first, const u32 *count, long long m,
+                                 int level, int leaf, u32 *nc)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    u32 f = first[b], n = count[b];
+    if (!(n > (u32)leaf && level < kLevels)) { nc[b] = 0; return; }
+    u32 e = f + n, cnt = 0, prev = f;
+    for (int d = 1; d <= 8; ++d) {
+        u32 bd = d < 8 ? lower_digit(keys, prev, e, level + 1, d) : e;
+        cnt += bd > prev;
+        prev = bd;
+    }
+    nc[b] = cnt;
+}
+
+__global__ void k_emit_children(const u64 *keys, u32 *first, u32 *count, long long off_cur,
+                                long long m, int level, const u32 *nc, const u32 *cpos,
+                                long long off_next, u32 *cb)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    long long gb = off_cur + b;
+    u32 k = nc[b];
+    cb[gb] = (u32)(off_next + cpos[b]);
+    if (!k) return;
+    u32 f = first[gb], e = f + count[gb];
+    long long pos = off_next + cpos[b];
+    u32 prev = f;
+    for (int d = 1; d <= 8; ++d) {
+        u32 bd = d < 8 ? lower_digit(keys, prev, e, level + 1, d) : e;
+        if (bd > prev) {
+            first[pos] = prev;
+            count[pos] = bd - prev;
+            ++pos;
+        }
+        prev = bd;
+    }
+}
+
+__global__ void k_subtree_size(const u32 *cb, const u32 *nc, long long off, long long m, u32 *size)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    long long gb = off + b;
+    u32 s = 1, k = nc[gb], c0 = cb[gb];
+    for (u32 c = 0; c < k; ++c) s += size[c0 + c];
+    size[gb] = s;
+}
+
+__global__ void k_dfs_pos(const u32 *cb, const u32 *nc, const u32 *size, long long off, long long m,
+                          u32 *dfs)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    long long gb = off + b;
+    u32 k = nc[gb], c0 = cb[gb];
+    u32 p = dfs[gb] + 1;
+    for (u32 c = 0; c < k; ++c) {
+        dfs[c0 + c] = p;
+        p += size[c0 + c];
+    }
+}
+
+__device__ __forceinline__ u32 compact3(u64 v)
+{
+    v &= 0x1249249249249249ull;
+    v = (v | (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v | (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v | (v >> 16)) & 0x1f00000000ffffull;
+    v = (v | (v >> 32)) & 0x1fffffull;
+    return (u32)v;
+}
+
+// Writes the depth-first arrays of one level's nodes.
+__global__ void k_finalize(const u64 *keys, const u32 *first, const u32 *count, const u32 *nc,
+                           const u32 *dfs, const u32 *size, long long off, long long m, int level,
+                           double lox, double loy, double loz, double side, float4 *box,
+                           uint4 *meta, double *cube, int *lev)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    long long gb = off + b;
+    u32 i = dfs[gb];
+    u32 f = first[gb];
+    u64 prefix = level ? (keys[f] >> (3 * (kLevels - level))) : 0ull;
+    u32 ix = compact3(prefix >> 2), iy = compact3(prefix >> 1), iz = compact3(prefix);
+    double l = ldexp(side, -level);
+    double cx = __dadd_rn(lox, __dmul_rn((double)ix, l));
+    double cy = __dadd_rn(loy, __dmul_rn((double)iy, l));
+    double cz = __dadd_rn(loz, __dmul_rn((double)iz, l));
+    cube[4 * (size_t)i + 0] = cx;
+    cube[4 * (size_t)i + 1] = cy;
+    cube[4 * (size_t)i + 2] = cz;
+    cube[4 * (size_t)i + 3] = l;
+    box[i] = make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz),
+                         __double2float_rn(l));
+    meta[i] = make_uint4(i + size[gb], f, count[gb], nc[gb] == 0 ? 1u : 0u);
+    lev[i] = level;
+}
+
+__global__ void k_bfs2dfs(const u32 *dfs, long long n, u32 *out)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) out[b] = dfs[b];
+}
+
+int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, const Frame &fr)
+{
+    t.n = 0;
+    t.depth = 0;
+    t.lvl_off.clear();
+    if (n <= 0) return START_OK;
+    cudaStream_t s = c->stream;
+    size_t cap = (size_t)(2 * n + 64);
+    ST_TRY(ensure(t.bfs_first, cap * sizeof(u32)));
+    ST_TRY(ensure(t.bfs_count, cap * sizeof(u32)));
+    ST_TRY(ensure(t.bfs_cb, cap * sizeof(u32)));
+    ST_TRY(ensure(t.bfs_nc, cap * sizeof(u32)));
+    u32 root[2] = {0u, (u32)n};
+    ST_CUDA(c, cudaMemcpyAsync(t.bfs_first.p, &root[0], sizeof(u32), cudaMemcpyHostToDevice, s));
+    ST_CUDA(c, cudaMemcpyAsync(t.bfs_count.p, &root[1], sizeof(u32), cudaMemcpyHostToDevice, s));
+    ST_TRY(ensure(c->flags, 64));
+    u32 *total_dev = c->flags.as<u32>() + 8;
+    long long off = 0, m = 1;
+    int level = 0;
+    DBuf cpos;
+    for (;;) {
+        t.lvl_off.push_back(off);
+        // children counts of this level
+        size_t used = (size_t)(off + m);
+        if (cap < used) return set_err(c, START_ECUDA, "octree bookkeeping overflow");
+        k_count_children<<<grid_for(m, 256), 256, 0, s>>>(keys, t.bfs_first.as<u32>() + off,
+                                                           t.bfs_count.as<u32>() + off, m, level,
+                                                           leaf, t.bfs_nc.as<u32>() + off); ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+        int rc = ensure(cpos, (size_t)m * sizeof(u32));
+        if (rc) return set_err(c, rc, "out of device memory (octree)");
+        ST_TRY(exclusive_scan_u32(c, t.bfs_nc.as<u32>() + off, cpos.as<u32>(), m, total_dev));
+        u32 mnext = 0;
+        ST_CUDA(c, cudaMemcpyAsync(&mnext, total_dev, sizeof(u32), cudaMemcpyDeviceToHost, s));
+        ST_CUDA(c, cudaStreamSynchronize(s));
+        long long off_next = off + m;
+        size_t need = (size_t)(off_next + mnext);
+        if (need > cap) {
+            size_t nc = need + need / 2 + 64;
+            ST_TRY(ensure_keep(t.bfs_first, nc * sizeof(u32), used * sizeof(u32), s));
+            ST_TRY(ensure_keep(t.bfs_count, nc * sizeof(u32), used * sizeof(u32), s));
+            ST_TRY(ensure_keep(t.bfs_cb, nc * sizeof(u32), used * sizeof(u32), s));
+            ST_TRY(ensure_keep(t.bfs_nc, nc * sizeof(u32), used * sizeof(u32), s));
+            cap = nc;
+        }
+        k_emit_children<<<grid_for(m, 256), 256, 0, s>>>(keys, t.bfs_first.as<u32>(),
+                                                          t.bfs_count.as<u32>(), off, m, level,
+                                                          t.bfs_nc.as<u32>() + off, cpos.as<u32>(),
+                                                          off_next, t.bfs_cb.as<u32>()); ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+        if (mnext == 0) break;
+        off = off_next;
+        m = mnext;
+        ++level;
+    }
+    release(cpos);
+    long long total = off + m;
+    t.n = total;
+    t.depth = level;
+    t.lvl_off.push_back(total);
+    // subtree sizes bottom-up, pre-order positions top-down
+    DBuf size, dfs;
+    if (ensure(size, total * sizeof(u32)) || ensure(dfs, total * sizeof(u32)))
+        return set_err(c, START_ENOMEM, "out of device memory (octree)");
+    for (int l = t.depth; l >= 0; --l) {
+        long long o = t.lvl_off[l], mm = t.lvl_off[l + 1] - o;
+        k_subtree_size<<<grid_for(mm, 256), 256, 0, s>>>(t.bfs_cb.as<u32>(), t.bfs_nc.as<u32>(), o,
+                                                          mm, size.as<u32>()); ++c->launches;
+    }
+    ST_CUDA(c, cudaMemsetAsync(dfs.p, 0, sizeof(u32), s));
+    for (int l = 0; l <= t.depth; ++l) {
+        long long o = t.lvl_off[l], mm = t.lvl_off[l + 1] - o;
+        k_dfs_pos<<<grid_for(mm, 256), 256, 0, s>>>(t.bfs_cb.as<u32>(), t.bfs_nc.as<u32>(),
+                                                     size.as<u32>(), o, mm, dfs.as<u32>()); ++c->launches;
+    }
+    ST_CUDA(c, cudaGetLastError());
+    if (ensure(t.box, total * sizeof(float4)) || ensure(t.meta, total * sizeof(uint4)) ||
+        ensure(t.cube, total * 4 * sizeof(double)) || ensure(t.level, total * sizeof(int)) ||
+        ensure(t.bfs2dfs, total * sizeof(u32)))
+        return set_err(c, START_ENOMEM, "out of device memory (octree)");
+    for (int l = 0; l <= t.depth; ++l) {
+        long long o = t.lvl_off[l], mm = t.lvl_off[l + 1] - o;
+        k_finalize<<<grid_for(mm, 256), 256, 0, s>>>(
+            keys, t.bfs_first.as<u32>(), t.bfs_count.as<u32>(), t.bfs_nc.as<u32>(), dfs.as<u32>(),
+            size.as<u32>(), o, mm, l, fr.lo[0], fr.lo[1], fr.lo[2], fr.side, t.box.as<float4>(),
+            t.meta.as<uint4>(), t.cube.as<double>(), t.level.as<int>()); ++c->launches;
+    }
+    k_bfs2dfs<<<grid_for(total, 256), 256, 0, s>>>(dfs.as<u32>(), total, t.bfs2dfs.as<u32>()); ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    ST_CUDA(c, cudaStreamSynchronize(s));
+    release(size);
+    release(dfs);
+    return START_OK;
+}
+
+// ---------------------------------------------------------------- moments
+// One level, deepest first.  A leaf sums its members in sorted order; an
+// inner cell sums its children in octant order (FP64, never contracted).
+__global__ void k_moments_level(const u32 *first, const u32 *count, const u32 *cb, const u32 *nc,
+                                const u32 *b2d, long long off, long long m,
+                                const float4 *mem_pos, const double *mem_L, const double *cube,
+                                double L_unit, double *L, double *M, float4 *vsrc)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    long long gb = off + b;
+    u32 i = b2d[gb];
+    double S = 0.0, Mx = 0.0, My = 0.0, Mz = 0.0;
+    u32 k = nc[gb];
+    u32 f = first[gb], n = count[gb];
+    if (k == 0) {
+        for (u32 r = f; r < f + n; ++r) {
+            double Lj = mem_L[r];
+            float4 p = mem_pos[r];
+            S = __dadd_rn(S, Lj);
+            Mx = __dadd_rn(Mx, __dmul_rn(Lj, (double)p.x));
+            My = __dadd_rn(My, __dmul_rn(Lj, (double)p.y));
+            Mz = __dadd_rn(Mz, __dmul_rn(Lj, (double)p.z));
+        }
+    } else {
+        u32 c0 = cb[gb];
+        for (u32 cc = 0; cc < k; ++cc) {
+            u32 j = b2d[c0 + cc];
+            S = __dadd_rn(S, L[j]);
+            Mx = __dadd_rn(Mx, M[3 * (size_t)j + 0]);
+            My = __dadd_rn(My, M[3 * (size_t)j + 1]);
+            Mz = __dadd_rn(Mz, M[3 * (size_t)j + 2]);
+        }
+    }
+    L[i] = S;
+    M[3 * (size_t)i + 0] = Mx;
+    M[3 * (size_t)i + 1] = My;
+    M[3 * (size_t)i + 2] = Mz;
+    float4 v;
+    if (n == 1) {
+        float4 p = mem_pos[f];
+        v = make_float4(p.x, p.y, p.z, 0.f);
+    } else if (S > 0.0) {
+        v = make_float4(__double2float_rn(__ddiv_rn(Mx, S)), __double2float_rn(__ddiv_rn(My, S)),
+                        __double2float_rn(__ddiv_rn(Mz, S)), 0.f);
+    } else {
+        double l = cube[4 * (size_t)i + 3];
+        v = make_float4(__double2float_rn(__dadd_rn(cube[4 * (size_t)i + 0], __dmul_rn(0.5, l))),
+                        __double2float_rn(__dadd_rn(cube[4 * (size_t)i + 1], __dmul_rn(0.5, l))),
+                        __double2float_rn(__dadd_rn(cube[4 * (size_t)i + 2], __dmul_rn(0.5, l))),
+                        0.f);
+    }
+    v.w = __double2float_rn(__ddiv_rn(S, L_unit));
+    vsrc[i] = v;
+}
+
+int tree_moments(start_ctx *c, Tree &t, const float4 *mem_pos, const double *mem_L, double L_unit)
+{
+    if (t.n == 0) return START_OK;
+    if (ensure(t.L, t.n * sizeof(double)) || ensure(t.M, t.n * 3 * sizeof(double)) ||
+        ensure(t.vsrc, t.n * sizeof(float4)))
+        return set_err(c, START_ENOMEM, "out of device memory (moments)");
+    for (int l = t.depth; l >= 0; --l) {
+        long long o = t.lvl_off[l], mm = t.lvl_off[l + 1] - o;
+        k_moments_level<<<grid_for(mm, 256), 256, 0, c->stream>>>(
+            t.bfs_first.as<u32>(), t.bfs_count.as<u32>(), t.bfs_cb.as<u32>(), t.bfs_nc.as<u32>(),
+            t.bfs2dfs.as<u32>(), o, mm, mem_pos, mem_L, t.cube.as<double>(), L_unit,
+            t.L.as<double>(), t.M.as<double>(), t.vsrc.as<float4>()); ++c->launches;
+    }
+    return cuda_check(c, cudaGetLastError(), "k_moments_level");
+}
+
+void tree_release(Tree &t)
+{
+    DBuf *all[] = {&t.box, &t.meta, &t.cube, &t.level, &t.vsrc, &t.L, &t.M, &t.bfs2dfs,
+                   &t.bfs_first, &t.bfs_count, &t.bfs_cb, &t.bfs_nc};
+    for (DBuf *b : all) release(*b);
+    t.n = 0;
+    t.lvl_off.clear();
+}
+
+}  // namespace st

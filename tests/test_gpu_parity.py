@@ -1,0 +1,353 @@
+"""GPU path vs the FP64 oracle on the same seeded inputs.
+
+Bit-exact: frame, Morton keys, sort permutations, octrees (structure, FP64
+cubes, FP64 luminosities, float32 centres), neighbour sets, interaction
+lists and the number of rays and hops (every upstream choice agrees).
+Within tolerance: Gamma (|dG| <= 1e-4 G_ref + G_abs, G_abs = 1e-8 / (sigma
+dt), i.e. a flux whose k dt is 1e-8 for dt = 1 Myr) and x_HII (abs 1e-3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from start_inputs import (ALPHA_A, ALPHA_B, KPC_CM, MYR_S, SIGMA_CM2, config1, config2,
+                          jittered_lattice, lattice_workload, smoothing_lengths)
+
+pytestmark = pytest.mark.gpu
+
+DT = MYR_S
+G_ABS = 1e-8 / (SIGMA_CM2 * DT)
+G_REL = 1e-4
+X_ABS = 1e-3
+PTREE_LEAF = 16
+PHYS = dict(sigma_cm2=SIGMA_CM2, len_unit_cm=KPC_CM, alpha_A=ALPHA_A, alpha_B=ALPHA_B)
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1005_5312_gb300 as S
+    S.build()
+    S.lib()
+    return S
+
+
+def make_pair(S, w, tau_cut=1e30, **over):
+    """GPU context and oracle over one workload (same inputs)."""
+    ctx = S.Context(tau_cut=tau_cut, ptree_leaf=PTREE_LEAF, **over)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L, w.V if w.diffuse else None, diffuse=w.diffuse)
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=PTREE_LEAF,
+                                      src_leaf=over.get("src_leaf", 1))
+    return ctx, orc
+
+
+def gamma_close(g, ref):
+    g = np.asarray(g, np.float64)
+    err = np.abs(g - ref)
+    tol = G_REL * np.abs(ref) + G_ABS
+    bad = np.nonzero(err > tol)[0]
+    assert len(bad) == 0, (f"{len(bad)} targets off; worst i={bad[np.argmax(err[bad] / tol[bad])]}",
+                           g[bad[:5]], ref[bad[:5]])
+
+
+def decode(ent):
+    ent = np.asarray(ent, np.int64)
+    src = (ent & 0x80000000) != 0
+    emit = (ent & 0x40000000) != 0
+    ident = ent & 0x3FFFFFFF
+    return np.where(src, -(1 + ident), ident), emit
+
+
+def random_workload(n_p, n_s, seed, box=3.0, dups=0, diffuse=False):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0, box, size=(3, n_p)).astype(np.float32)
+    for d in range(dups):
+        pos[:, 2 * d + 1] = pos[:, 2 * d]
+    h = smoothing_lengths(pos)
+    w = lattice_workload("tmp", 2, 1.0, 0, seed)   # container for the fields
+    w.pos, w.h = pos, h
+    w.src_pos = rng.uniform(0, box, size=(3, n_s)).astype(np.float32)
+    w.src_L = rng.lognormal(np.log(1e48), 1.0, size=n_s)
+    w.n_H = np.full(n_p, 1e-3, np.float32)
+    w.y0 = rng.uniform(0.0, 1.0, n_p)
+    w.V = np.full(n_p, box ** 3 / n_p)
+    w.diffuse = diffuse
+    w.params["diffuse"] = diffuse
+    return w
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return config1()
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    # not a multiple of any tile; two pairs of identical positions
+    return random_workload(5003, 77, 11, dups=2)
+
+
+# ------------------------------------------------------------------ structure
+@pytest.mark.parametrize("which_w", ["cfg1", "ragged"])
+def test_frame_keys_perm_trees_neighbours_bitexact(S, which_w, request):
+    w = request.getfixturevalue(which_w)
+    ctx, orc = make_pair(S, w)
+    lo_g, side_g = ctx.frame()
+    lo_o, side_o = orc.frame()
+    assert np.array_equal(lo_g, lo_o) and side_g == side_o
+    for which in (0, 1):
+        assert np.array_equal(ctx.keys(which), orc.keys(which))
+        assert np.array_equal(ctx.perm(which).astype(np.int64), orc.perm(which))
+    for which in (0, 1):
+        tg, to = ctx.tree(which), orc.tree(which)
+        assert len(tg["level"]) == len(to["level"])
+        for k in ("level", "first", "count", "skip", "leaf"):
+            assert np.array_equal(tg[k].astype(np.int64), to[k].astype(np.int64)), k
+        assert np.array_equal(tg["cube"], to["cube"])
+        if which == 1:
+            assert np.array_equal(tg["L"], to["L"])
+            assert np.array_equal(tg["cen"], to["cen"])
+    og, ig = ctx.neighbors()
+    oo, io = orc.neighbours()
+    assert np.array_equal(og.astype(np.int64), oo)
+    for i in range(w.n_p):
+        assert sorted(ig[og[i]:og[i + 1]].tolist()) == io[oo[i]:oo[i + 1]].tolist()
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 1.0])
+def test_lists_bitexact(S, cfg1, theta):
+    ctx, orc = make_pair(S, cfg1)
+    off, ent = ctx.lists(theta)
+    dec, emit = decode(ent)
+    assert not emit.any()
+    for i in range(0, cfg1.n_p, 97):
+        assert dec[off[i]:off[i + 1]].tolist() == orc.list(theta, i).tolist()
+
+
+# ------------------------------------------------------------------ Gamma
+@pytest.mark.parametrize("theta", [0.0, 0.5, 1.0])
+def test_gamma_parity_config1(S, cfg1, theta):
+    ctx, orc = make_pair(S, cfg1)
+    nHI = cfg1.n_HI()
+    g = np.zeros(cfg1.n_p, np.float32)
+    ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
+    ref = orc.gamma(nHI, theta)
+    gamma_close(g, ref)
+    st = ctx.stats()
+    assert st["rays"] == orc.last_stats["rays"]
+    assert st["hops"] == orc.last_stats["hops"]
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.7])
+def test_gamma_parity_ragged_nonuniform(S, ragged, theta):
+    ctx, orc = make_pair(S, ragged)
+    nHI = (ragged.y0 * 1e-3).astype(np.float32)
+    g = np.zeros(ragged.n_p, np.float32)
+    ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
+    ref = orc.gamma(nHI, theta)
+    gamma_close(g, ref)
+    st = ctx.stats()
+    assert st["rays"] == orc.last_stats["rays"]
+    assert st["hops"] == orc.last_stats["hops"]
+
+
+@pytest.mark.parametrize("group", [8, 16, 32])
+def test_march_group_is_result_neutral(S, cfg1, group):
+    ctx = S.Context(march_group=group, ptree_leaf=PTREE_LEAF)
+    ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    ref_ctx = S.Context(march_group=8, ptree_leaf=PTREE_LEAF)
+    ref_ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    nHI = cfg1.n_HI()
+    a = np.zeros(cfg1.n_p, np.float32)
+    b = np.zeros(cfg1.n_p, np.float32)
+    ctx.rt_solve(0.5, n_HI=nHI, gamma_out=a)
+    ref_ctx.rt_solve(0.5, n_HI=nHI, gamma_out=b)
+    assert np.array_equal(a, b)
+
+
+def test_single_source_theta_independent_on_gpu(S):
+    w = lattice_workload("one", 12, 2.0, 1, 5)
+    ctx = S.Context()
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    nHI = np.random.default_rng(0).uniform(0, 2e-3, w.n_p).astype(np.float32)
+    outs = []
+    for th in (0.0, 0.5, 1.0, 3.0):
+        g = np.zeros(w.n_p, np.float32)
+        ctx.rt_solve(th, n_HI=nHI, gamma_out=g)
+        outs.append(g)
+    for g in outs[1:]:
+        assert np.array_equal(g, outs[0])
+
+
+def test_device_and_host_pointers_agree(S, cfg1):
+    import torch
+    ctx = S.Context()
+    ctx.build_trees(torch.from_numpy(cfg1.pos).cuda(), torch.from_numpy(cfg1.h).cuda(),
+                    torch.from_numpy(cfg1.src_pos).cuda(), torch.from_numpy(cfg1.src_L).cuda())
+    nHI = cfg1.n_HI()
+    gd = torch.zeros(cfg1.n_p, dtype=torch.float32, device="cuda")
+    ctx.rt_solve(0.5, n_HI=torch.from_numpy(nHI).cuda(), gamma_out=gd)
+    torch.cuda.synchronize()
+    ctx2 = S.Context()
+    ctx2.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    gh = np.zeros(cfg1.n_p, np.float32)
+    ctx2.rt_solve(0.5, n_HI=nHI, gamma_out=gh)
+    assert np.array_equal(gd.cpu().numpy(), gh)
+
+
+def test_oneshot_matches_context(S, cfg1):
+    nHI = cfg1.n_HI()
+    a = np.zeros(cfg1.n_p, np.float32)
+    S.start_rt_solve_oneshot(cfg1.pos, cfg1.h, cfg1.n_p, nHI, cfg1.src_pos, cfg1.src_L,
+                             cfg1.n_s, 0.5, a)
+    ctx = S.Context()
+    ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    b = np.zeros(cfg1.n_p, np.float32)
+    ctx.rt_solve(0.5, n_HI=nHI, gamma_out=b)
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ ionisation
+def test_ionize_parity_and_coupled_steps(S, cfg1):
+    ctx, orc = make_pair(S, cfg1)
+    ctx.set_state(cfg1.n_H, cfg1.y0)
+    y_ref = cfg1.y0.copy()
+    y_gpu = np.zeros(cfg1.n_p)
+    for step in range(4):
+        g = np.zeros(cfg1.n_p, np.float32)
+        ctx.rt_solve(0.5, gamma_out=g)
+        ctx.ionize(DT, y_out=y_gpu)
+        g_ref, y_ref = orc.step(y_ref, cfg1.n_H, 0.5, DT)
+        assert np.max(np.abs(y_gpu - y_ref)) <= X_ABS, step
+    # open loop: the same Gamma gives the same update to rounding
+    y_o, _ = orc.ionize(g.astype(np.float64), cfg1.n_H, cfg1.y0, DT)
+    ctx.set_state(cfg1.n_H, cfg1.y0)
+    ctx.rt_solve(0.5, gamma_out=g)
+    ctx.ionize(DT, y_out=y_gpu)
+    assert np.max(np.abs(y_gpu - y_o)) < 1e-12
+
+
+# ------------------------------------------------------------------ diffuse
+@pytest.fixture(scope="module")
+def diffuse_w():
+    w = lattice_workload("diffuse-12^3", 12, 2.0, 2, 17, L=3e50, diffuse=True)
+    rng = np.random.default_rng(4)
+    w.y0 = rng.uniform(0.0, 1.0, w.n_p)
+    w.n_H = (10 ** rng.uniform(-3.5, -1.5, w.n_p)).astype(np.float32)
+    return w
+
+
+def test_diffuse_emitters_tree_and_gamma(S, diffuse_w):
+    w = diffuse_w
+    ctx, orc = make_pair(S, w)
+    ctx.set_state(w.n_H, w.y0)
+    orc.set_emitters(w.y0, w.n_H)
+    eL = orc.emitter_L()
+    assert np.array_equal(ctx.emitter_L(), (eL / 1e48).astype(np.float32))
+    tg, to = ctx.tree(2), orc.tree(2)
+    for k in ("level", "first", "count", "skip", "leaf"):
+        assert np.array_equal(tg[k].astype(np.int64), to[k].astype(np.int64)), k
+    assert np.array_equal(tg["L"], to["L"])
+    assert np.array_equal(tg["cen"], to["cen"])
+    nHI = w.n_HI()
+    for theta in (0.0, 0.7):
+        off, ent = ctx.lists(theta)
+        dec, emit = decode(ent)
+        for i in range(0, w.n_p, 53):
+            row = slice(int(off[i]), int(off[i + 1]))
+            d, e = dec[row], emit[row]
+            assert d[~e].tolist() == orc.list(theta, i, which=1).tolist()
+            assert d[e].tolist() == orc.list(theta, i, which=2).tolist()
+        g = np.zeros(w.n_p, np.float32)
+        ctx.rt_solve(theta, gamma_out=g)
+        gamma_close(g, orc.gamma(nHI, theta))
+    y = np.zeros(w.n_p)
+    ctx.ionize(DT, y_out=y)
+    y_ref, _ = orc.ionize(orc.gamma(nHI, 0.7), w.n_H, w.y0, DT)
+    assert np.max(np.abs(y - y_ref)) <= X_ABS
+
+
+# ------------------------------------------------------------------ edge cases
+def test_edge_sizes(S):
+    rng = np.random.default_rng(9)
+    for n_p, n_s in ((1, 1), (2, 0), (33, 1), (40, 3)):
+        pos = rng.uniform(0, 1, size=(3, n_p)).astype(np.float32)
+        h = np.full(n_p, 0.4, np.float32)
+        src = rng.uniform(0, 1, size=(3, n_s)).astype(np.float32)
+        L = np.full(n_s, 1e48)
+        ctx = S.Context(tau_cut=1e30)
+        ctx.build_trees(pos, h, src, L)
+        orc = oracle.Oracle(pos, h, src, L, ptree_leaf=PTREE_LEAF, **PHYS)
+        nHI = np.full(n_p, 1e-3, np.float32)
+        g = np.full(n_p, -1.0, np.float32)
+        ctx.rt_solve(0.5, n_HI=nHI, gamma_out=g)
+        gamma_close(g, orc.gamma(nHI, 0.5))
+    # empty problem
+    ctx = S.Context()
+    ctx.build_trees(np.zeros((3, 0), np.float32), np.zeros(0, np.float32),
+                    np.zeros((3, 0), np.float32), np.zeros(0))
+    ctx.rt_solve(0.5, n_HI=np.zeros(0, np.float32), gamma_out=np.zeros(0, np.float32))
+
+
+def test_invalid_inputs_are_rejected(S, cfg1):
+    ctx = S.Context()
+    with pytest.raises(S.StartError) as e:
+        ctx.rt_solve(0.5, n_HI=cfg1.n_HI(), gamma_out=np.zeros(cfg1.n_p, np.float32))
+    assert e.value.code == S.START_ENOTBUILT
+    bad = cfg1.pos.copy()
+    bad[1, 7] = np.nan
+    with pytest.raises(S.StartError) as e:
+        ctx.build_trees(bad, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    assert e.value.code == S.START_EINVAL
+    hb = cfg1.h.copy()
+    hb[3] = 0.0
+    with pytest.raises(S.StartError) as e:
+        ctx.build_trees(cfg1.pos, hb, cfg1.src_pos, cfg1.src_L)
+    assert e.value.code == S.START_EINVAL
+    ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    with pytest.raises(S.StartError) as e:
+        ctx.rt_solve(-0.1, n_HI=cfg1.n_HI(), gamma_out=np.zeros(cfg1.n_p, np.float32))
+    assert e.value.code == S.START_EINVAL
+    nb = cfg1.n_HI()
+    nb[0] = -1.0
+    with pytest.raises(S.StartError) as e:
+        ctx.rt_solve(0.5, n_HI=nb, gamma_out=np.zeros(cfg1.n_p, np.float32))
+    assert e.value.code == S.START_EINVAL
+    # the context stays usable after rejected calls
+    g = np.zeros(cfg1.n_p, np.float32)
+    ctx.rt_solve(0.5, n_HI=cfg1.n_HI(), gamma_out=g)
+    assert np.all(np.isfinite(g)) and g.max() > 0
+
+
+def test_hop_cap_reports_echain(S, cfg1):
+    ctx = S.Context(hop_cap=2, tau_cut=1e30)
+    ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    with pytest.raises(S.StartError) as e:
+        ctx.rt_solve(0.5, n_HI=cfg1.n_HI(), gamma_out=np.zeros(cfg1.n_p, np.float32))
+    assert e.value.code == S.START_ECHAIN
+
+
+# ------------------------------------------------------------------ full size, sampled
+def test_config2_full_size_sampled_targets(S):
+    """64^3 particles and 1024 sources at theta = 0.5 in the launch
+    configuration the benchmark uses; the oracle evaluates 48 sampled
+    targets one by one."""
+    w = config2()
+    ctx = S.Context(tau_cut=1e30)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    nHI = w.n_HI()
+    g = np.zeros(w.n_p, np.float32)
+    ctx.rt_solve(0.5, n_HI=nHI, gamma_out=g)
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=PTREE_LEAF)
+    idx = np.random.default_rng(1).choice(w.n_p, 48, replace=False)
+    gamma_close(g[idx], orc.gamma(nHI, 0.5, targets=idx))
+    # and with the default early stop of opaque rays
+    ctx2 = S.Context()
+    ctx2.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    g2 = np.zeros(w.n_p, np.float32)
+    ctx2.rt_solve(0.5, n_HI=nHI, gamma_out=g2)
+    gamma_close(g2[idx], orc.gamma(nHI, 0.5, targets=idx))
