@@ -45,7 +45,11 @@ def parse():
     ap.add_argument("--march-group", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-targets", type=int, default=192)
+    ap.add_argument("--no-theta2", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="oracle work per CPU-baseline measurement")
+    ap.add_argument("--ref-targets", type=int, default=16384,
+                    help="targets per step of the reference arm")
     return ap.parse_args()
 
 
@@ -143,7 +147,7 @@ def run_reference(args, w):
     orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
     nHI = w.n_HI()
     rng = np.random.default_rng(7)
-    per_step = max(8, args.cpu_targets // 4)
+    per_step = min(w.n_p, args.ref_targets)
     times, rays = [], []
     for s in range(args.warmup + args.steps):
         idx = rng.choice(w.n_p, per_step, replace=False)
@@ -166,6 +170,29 @@ def run_reference(args, w):
                              "sample": f"{per_step} random targets of {w.n_p} per step"},
             "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline(w, theta, seconds):
+    """The oracle as it stands on the host cores: Gamma at random targets of
+    the same workload (neutral start), in chunks until `seconds` of work."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
+    order = np.random.default_rng(5).permutation(w.n_p)
+    nHI = w.n_HI()
+    done, rays, t = 0, 0, 0.0
+    chunk = 1024
+    while t < seconds and done < w.n_p:
+        idx = order[done:done + chunk]
+        t0 = time.perf_counter()
+        orc.gamma(nHI, theta, targets=idx)
+        t += time.perf_counter() - t0
+        rays += orc.last_stats["rays"]
+        done += len(idx)
+    return {"value": rays / t, "unit": "rays/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"Gamma at {done} random targets of {w.n_p} (theta={theta}, neutral "
+                      f"start): {rays} rays in {t:.1f} s"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -233,7 +260,7 @@ def run_gpu(args, w):
 
     with ClockSampler(local) as clk:
         r1 = timed(args.theta, args.steps, args.warmup)
-    r2 = timed(args.theta2, max(2, args.steps // 2), 1)
+    r2 = None if args.no_theta2 else timed(args.theta2, max(2, args.steps // 2), 1)
 
     tot_ms = sum(r1["step_ms"])
     rays = sum(r1["rays"])
@@ -272,11 +299,12 @@ def run_gpu(args, w):
            "march_fallbacks_per_step": sum(r1["fbs"]) / args.steps,
            "gpu_launches": r1["launches"],
            "roofline": roof, "clocks": clk.summary()}
-    t2 = sum(r2["step_ms"])
-    out[f"theta_{args.theta2}"] = {"value": sum(r2["rays"]) / (t2 * 1e-3), "unit": "rays/s",
-                                   "ms_per_step": t2 / len(r2["step_ms"]),
-                                   "rays_per_step": sum(r2["rays"]) / len(r2["rays"]),
-                                   "march_ms": sum(r2["march_ms"]) / len(r2["march_ms"])}
+    if r2 is not None:
+        t2 = sum(r2["step_ms"])
+        out[f"theta_{args.theta2}"] = {"value": sum(r2["rays"]) / (t2 * 1e-3), "unit": "rays/s",
+                                       "ms_per_step": t2 / len(r2["step_ms"]),
+                                       "rays_per_step": sum(r2["rays"]) / len(r2["rays"]),
+                                       "march_ms": sum(r2["march_ms"]) / len(r2["march_ms"])}
     phases = ctx.timings()
     out["phase_ms_last_step"] = phases
 
@@ -318,19 +346,7 @@ def run_gpu(args, w):
         ctx_h.close()
 
     if rank == 0 and ws == 1 and not args.no_cpu:
-        import numpy as np2
-        import oracle
-        oracle.build()
-        orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
-        idx = np2.random.default_rng(5).choice(w.n_p, args.cpu_targets, replace=False)
-        nHI = w.n_HI()
-        t0 = time.perf_counter()
-        orc.gamma(nHI, args.theta, targets=idx)
-        tc = time.perf_counter() - t0
-        out["cpu_baseline"] = {"value": orc.last_stats["rays"] / tc, "unit": "rays/s",
-                               "cores": oracle.threads(), "kind": "oracle",
-                               "sample": f"Gamma at {args.cpu_targets} random targets of {w.n_p}, "
-                                         f"theta={args.theta}, neutral start ({tc:.1f} s)"}
+        out["cpu_baseline"] = cpu_baseline(w, args.theta, args.cpu_seconds)
     ctx.close()
     if ws > 1:
         import torch.distributed as dist

@@ -483,6 +483,8 @@ int finish_gamma(start_ctx *c, float *gout_dev)
     k_gamma<<<grid_for(c->np, 256), 256, 0, c->stream>>>(c->pcon.as<float>(), c->loff.as<u64>(),
                                                           c->np, conv, c->porig.as<u32>(),
                                                           c->gam.as<float>(), gout_dev);
+    ++c->launches;
+    phase_mark(c, START_PHASE_GAMMA, true);
     return cuda_check(c, cudaGetLastError(), "k_gamma");
 }
 

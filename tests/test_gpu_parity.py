@@ -224,10 +224,10 @@ def test_ionize_parity_and_coupled_steps(S, cfg1):
         g_ref, y_ref = orc.step(y_ref, cfg1.n_H, 0.5, DT)
         assert np.max(np.abs(y_gpu - y_ref)) <= X_ABS, step
     # open loop: the same Gamma gives the same update to rounding
-    y_o, _ = orc.ionize(g.astype(np.float64), cfg1.n_H, cfg1.y0, DT)
     ctx.set_state(cfg1.n_H, cfg1.y0)
     ctx.rt_solve(0.5, gamma_out=g)
     ctx.ionize(DT, y_out=y_gpu)
+    y_o, _ = orc.ionize(g.astype(np.float64), cfg1.n_H, cfg1.y0, DT)
     assert np.max(np.abs(y_gpu - y_o)) < 1e-12
 
 
