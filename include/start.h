@@ -227,6 +227,34 @@ const char *start_last_error(const start_ctx *c);
 /* Name of a status code. */
 const char *start_status_string(int status);
 
+/* ---- allocation-free Morton ordering (no counterpart in the paper) ----
+ *
+ * For callers that cannot let the library allocate device memory: codes
+ * that hand out all GPU memory from their own pool or a budget fixed at
+ * start-up, and codes that must not stall mid-step (cudaMalloc/cudaFree
+ * synchronise the whole device).  Computes what start_build_trees computes
+ * for a particle set with no sources -- the root frame, the 63-bit Morton
+ * key of every particle and the stable order by (key, input index) -- but
+ * calls no allocating routine: its scratch is a fixed array compiled into
+ * the library, START_NOALLOC_MAX_N particles at most (about 20.5 MB, kept
+ * by every GPU that loads this code until the process exits).
+ *   pos       [3 * n] float32 SoA positions, device memory
+ *   n         0 <= n <= START_NOALLOC_MAX_N (larger: START_ERANGE)
+ *   keys_out  [n] Morton keys in input order, device memory
+ *   perm_out  [n] input index of each sorted rank, device memory
+ *   frame_out [4] lower corner x, y, z and side, device memory or NULL
+ *   stream    cudaStream_t to issue the work on (NULL = default stream)
+ * Host pointers are refused with START_EINVAL; non-finite positions give
+ * START_EINVAL.  The call returns after its work on `stream` has finished.
+ * The first call on a device looks up the scratch array's device address
+ * (and may load the library's GPU code there): make it before any stream
+ * capture begins.  All calls share the one scratch array, so calls that
+ * overlap on the GPU (other streams, other host threads) race; serialise
+ * them. */
+#define START_NOALLOC_MAX_N (1LL << 20)
+int start_morton_order_noalloc(const float *pos, long long n, unsigned long long *keys_out,
+                               unsigned *perm_out, double *frame_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ def lib():
             "start_get_timings": (i, [vp, P(d), i]),
             "start_last_error": (C.c_char_p, [vp]),
             "start_status_string": (C.c_char_p, [i]),
+            "start_morton_order_noalloc": (i, [vp, ll, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -160,6 +161,13 @@ def start_rt_solve_oneshot(pos, h, n_p, n_HI, src_pos, src_L, n_s, theta, gamma_
     return _check(None, lib().start_rt_solve_oneshot(
         C.byref(params) if params is not None else None, _ptr(pos), _ptr(h), int(n_p),
         _ptr(n_HI), _ptr(src_pos), _ptr(src_L), int(n_s), float(theta), _ptr(gamma_out)))
+
+
+def start_morton_order_noalloc(pos, n, keys_out, perm_out, frame_out=None, stream=None):
+    """Allocation-free Morton ordering (device arrays only); see start.h."""
+    st = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    return _check(None, lib().start_morton_order_noalloc(_ptr(pos), int(n), _ptr(keys_out),
+                                                         _ptr(perm_out), _ptr(frame_out), st))
 
 
 # ---------------------------------------------------------------- convenience
