@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 ALGO_BYTES_PER_HOP = 516     # 32 u32 neighbour indices + 32 float3 positions + 1 float n_HI
 ALGO_BYTES_PER_RAY = 16      # virtual source record
 ALGO_BYTES_PER_TARGET = 8    # Gamma out, target record
+# memoised march, per evaluated chain link: the neighbour list (516 B) plus
+# the link's source record (16 B), its hash-table entry (16 B) and its slot
+# state (virtual source, particle, next, tau, links: 16 B)
+ALGO_BYTES_PER_LINK = 516 + 16 + 16 + 16
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -43,6 +47,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--theta2", type=float, default=1.0)
     ap.add_argument("--march-group", type=int, default=8)
+    ap.add_argument("--march-mode", type=int, default=1, choices=[0, 1],
+                    help="1 memoised march (default), 0 per-ray march")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-theta2", action="store_true")
@@ -209,7 +215,8 @@ def run_gpu(args, w):
         dist.init_process_group("nccl")
     S.build()
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream)
+    ctx = S.Context(timing=1, march_group=args.march_group, march_mode=args.march_mode,
+                    stream=stream)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     pos, h, spos, sL = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L)
     nH, y0 = T(w.n_H), T(w.y0)
@@ -236,7 +243,7 @@ def run_gpu(args, w):
         torch.cuda.synchronize(dev)
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        march_ms, rays, hops, fbs = [], [], [], []
+        march_ms, hop_ms, rays, hops, evals, fbs = [], [], [], [], [], []
         l0 = ctx.stats()["launches"]
         barrier()
         t_wall = time.perf_counter()
@@ -248,15 +255,17 @@ def run_gpu(args, w):
             tm = ctx.timings()
             st = ctx.stats()
             march_ms.append(tm["march"])
+            hop_ms.append(tm["hops"])
             rays.append(st["rays"])
             hops.append(st["hops"])
+            evals.append(st["evals"])
             fbs.append(st["march_fallbacks"])
         barrier()
         t_wall = time.perf_counter() - t_wall
         launches = ctx.stats()["launches"] - l0
         step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-        return dict(step_ms=step_ms, march_ms=march_ms, rays=rays, hops=hops, fbs=fbs,
-                    launches=launches, wall=t_wall)
+        return dict(step_ms=step_ms, march_ms=march_ms, hop_ms=hop_ms, rays=rays, hops=hops,
+                    evals=evals, fbs=fbs, launches=launches, wall=t_wall)
 
     with ClockSampler(local) as clk:
         r1 = timed(args.theta, args.steps, args.warmup)
@@ -272,19 +281,28 @@ def run_gpu(args, w):
         rays = sum(x[1] for x in gathered)
     value = rays / (tot_ms * 1e-3)
 
-    # roofline of the march kernel (the dominant launch)
+    # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
-    mk = [(m, r, hp) for m, r, hp in zip(r1["march_ms"], r1["rays"], r1["hops"]) if m > 0]
-    algo = [ALGO_BYTES_PER_HOP * hp + ALGO_BYTES_PER_RAY * r + ALGO_BYTES_PER_TARGET * w.n_p
-            for _, r, hp in mk]
-    avg_ms = sum(m for m, _, _ in mk) / len(mk)
-    achieved = (sum(algo) / len(algo)) / (avg_ms * 1e-3) / 1e9
-    tr = traffic_record("k_march")
+    if args.march_mode == 1:
+        # memoised march: its hop kernel, summed over the frontier launches
+        kern = "k_memo_hop"
+        t_ms = sum(r1["hop_ms"])
+        algo = ALGO_BYTES_PER_LINK * sum(r1["evals"])
+        per_launch = algo / args.steps
+        avg_ms = t_ms / args.steps
+    else:
+        kern = "k_march"
+        algo_l = [ALGO_BYTES_PER_HOP * hp + ALGO_BYTES_PER_RAY * r + ALGO_BYTES_PER_TARGET * w.n_p
+                  for r, hp in zip(r1["rays"], r1["evals"])]
+        per_launch = sum(algo_l) / len(algo_l)
+        avg_ms = sum(r1["march_ms"]) / len(r1["march_ms"])
+    achieved = per_launch / (avg_ms * 1e-3) / 1e9
+    tr = traffic_record(kern)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "kernel": "k_march", "kernel_ms": avg_ms,
-            "algorithmic_bytes_per_launch": sum(algo) / len(algo)}
+            "kernel": kern, "kernel_ms_per_step": avg_ms,
+            "algorithmic_bytes_per_step": per_launch}
 
     out = {"metric": f"RT rays/s at theta_crit={args.theta}", "value": value, "unit": "rays/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -292,10 +310,13 @@ def run_gpu(args, w):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "theta": args.theta,
                       "dt_s": w.dt_s, "march_group": args.march_group,
+                      "march": "memoised" if args.march_mode == 1 else "per-ray",
                       "l2": "512 MB buffer written between timed steps",
                       "step": "build_trees + set_state + rt_solve + ionize, coupled"},
            "rays_per_step": rays / args.steps / ws,
-           "hops_per_ray": sum(r1["hops"]) / max(1, sum(r1["rays"])),
+           "chain_links_per_ray": sum(r1["hops"]) / max(1, sum(r1["rays"])),
+           "evaluations_per_ray": sum(r1["evals"]) / max(1, sum(r1["rays"])),
+           "march_ms_per_step": sum(r1["march_ms"]) / len(r1["march_ms"]),
            "march_fallbacks_per_step": sum(r1["fbs"]) / args.steps,
            "gpu_launches": r1["launches"],
            "roofline": roof, "clocks": clk.summary()}
@@ -315,7 +336,7 @@ def run_gpu(args, w):
         hnH = w.n_H
         hy = w.y0.copy()
         hg = np.zeros(w.n_p, np.float32)
-        ctx_h = S.Context(march_group=args.march_group)
+        ctx_h = S.Context(march_group=args.march_group, march_mode=args.march_mode)
 
         def hstep():
             ctx_h.build_trees(hpos, hh, hsp, hsL)

@@ -84,14 +84,21 @@ typedef struct start_params {
                               (0 = default); does not change any result */
     int timing;            /* 1: record CUDA events around each phase (see
                               start_get_timings); 0: none */
+    int march_mode;        /* 1: memoised march, every chain link (virtual
+                              source, particle) evaluated once and shared by
+                              the rays through it (default); 0: per-ray
+                              march, each chain followed from its target.
+                              Same upstream choices; tau differs only in the
+                              order of the additions */
+    int reserved1;
     double sigma_cm2;      /* HI photoionisation cross-section (6.3e-18) */
     double len_unit_cm;    /* length unit of positions (kpc = 3.0857e21) */
     double L_unit;         /* internal luminosity scale, photons/s (1e48) */
     double alpha_A;        /* case-A recombination coefficient, cm^3/s */
     double alpha_B;        /* case-B recombination coefficient, cm^3/s */
-    double tau_cut;        /* rays stop once tau exceeds this (default 110;
-                              e^-110 is below float32's smallest subnormal
-                              relative to any representable flux) */
+    double tau_cut;        /* per-ray march: rays stop once tau exceeds this
+                              (default 110; e^-110 is below float32's smallest
+                              subnormal relative to any representable flux) */
     long long hop_cap;     /* max upstream steps per ray (0 = N_p + 1) */
     long long spin_cap;    /* max iterations of any device wait (reserved) */
     void *stream;          /* cudaStream_t to issue work on (NULL = default) */
@@ -100,7 +107,7 @@ typedef struct start_params {
 /* Counters of the last start_rt_solve. */
 typedef struct start_stats {
     long long rays;             /* (target, virtual source) pairs evaluated */
-    long long hops;             /* neighbour-list evaluations over all rays */
+    long long hops;             /* chain links over all rays (sum of chain lengths) */
     long long march_fallbacks;  /* upstream choices decided in FP64 */
     long long walk_fallbacks;   /* opening tests decided in FP64 */
     long long nbr_fallbacks;    /* neighbour tests decided in FP64 (last build) */
@@ -110,6 +117,8 @@ typedef struct start_stats {
     long long nbr_total;        /* neighbour-list entries */
     long long max_hops;         /* longest chain of the last solve */
     long long launches;         /* kernels launched by this context so far */
+    long long evals;            /* neighbour-list evaluations performed */
+    long long links;            /* distinct chain links (memoised march) */
 } start_stats;
 
 /* Phases timed when start_params.timing = 1 (milliseconds of the last
@@ -120,7 +129,8 @@ typedef struct start_stats {
 #define START_PHASE_GAMMA 3   /* Gamma reduction */
 #define START_PHASE_IONIZE 4  /* implicit update */
 #define START_PHASE_EMIT 5    /* diffuse emitters and their moments */
-#define START_NPHASES 6
+#define START_PHASE_HOPS 6    /* memoised march: sum of its hop kernels */
+#define START_NPHASES 7
 
 typedef struct start_ctx start_ctx;
 

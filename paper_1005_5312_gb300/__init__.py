@@ -33,7 +33,8 @@ START_ENTRY_EMITTER = 0x40000000
 
 class StartParams(C.Structure):
     _fields_ = [("src_leaf", C.c_int), ("ptree_leaf", C.c_int), ("march_group", C.c_int),
-                ("timing", C.c_int), ("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
+                ("timing", C.c_int), ("march_mode", C.c_int), ("reserved1", C.c_int),
+                ("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
                 ("L_unit", C.c_double), ("alpha_A", C.c_double), ("alpha_B", C.c_double),
                 ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("spin_cap", C.c_longlong),
                 ("stream", C.c_void_p)]
@@ -42,7 +43,7 @@ class StartParams(C.Structure):
 class StartStats(C.Structure):
     _fields_ = [(n, C.c_longlong) for n in (
         "rays", "hops", "march_fallbacks", "walk_fallbacks", "nbr_fallbacks", "nodes_src",
-        "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches")]
+        "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches", "evals", "links")]
 
 
 class StartError(RuntimeError):
@@ -261,9 +262,9 @@ class Context:
     def timings(self) -> dict:
         """Milliseconds of the last build / walk / march / gamma / ionize /
         emitter phase (needs timing=1)."""
-        ms = (C.c_double * 6)()
-        _check(self.h, lib().start_get_timings(self.h, ms, 6))
-        return dict(zip(("build", "walk", "march", "gamma", "ionize", "emit"), list(ms)))
+        ms = (C.c_double * 7)()
+        _check(self.h, lib().start_get_timings(self.h, ms, 7))
+        return dict(zip(("build", "walk", "march", "gamma", "ionize", "emit", "hops"), list(ms)))
 
     def stats(self) -> dict:
         s = StartStats()

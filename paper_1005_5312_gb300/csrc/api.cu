@@ -261,6 +261,8 @@ static void release_all(start_ctx *c)
     if (c->ev_init)
         for (int k = 0; k < 2 * START_NPHASES; ++k) cudaEventDestroy(c->ev[k]);
     c->ev_init = false;
+    for (int k = 0; k < 2; ++k)
+        if (c->hev[k]) cudaEventDestroy(c->hev[k]);
 }
 
 }  // namespace st
@@ -291,6 +293,7 @@ int start_default_params(start_params *p)
     p->src_leaf = 1;
     p->ptree_leaf = 16;
     p->march_group = 8;
+    p->march_mode = 1;
     p->sigma_cm2 = 6.3e-18;
     p->len_unit_cm = 3.0857e21;
     p->L_unit = 1e48;
@@ -316,6 +319,7 @@ int start_create(start_ctx **out, const start_params *p)
     if (d.march_group != 0 && d.march_group != 8 && d.march_group != 16 && d.march_group != 32)
         return START_EINVAL;
     if (d.march_group == 0) d.march_group = 8;
+    if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
     start_ctx *c = new (std::nothrow) start_ctx();
     if (!c) return START_ENOMEM;
     c->p = d;
@@ -702,6 +706,8 @@ int start_get_stats(start_ctx *c, start_stats *out)
     out->nodes_part = c->pt.n;
     out->nbr_total = c->nb_total;
     out->launches = (long long)c->launches;
+    out->evals = (long long)v[C_EVALS];
+    out->links = (long long)(c->p.march_mode == 1 ? v[C_SLOTS] : 0);
     return START_OK;
 }
 
@@ -712,6 +718,10 @@ int start_get_timings(start_ctx *c, double *ms, int n)
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int k = 0; k < n; ++k) {
         ms[k] = -1.0;
+        if (k == START_PHASE_HOPS) {
+            ms[k] = c->p.march_mode == 1 ? c->hop_ms : -1.0;
+            continue;
+        }
         if (c->ev_init && c->ev_rec[k]) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, c->ev[2 * k], c->ev[2 * k + 1]) == cudaSuccess) ms[k] = t;

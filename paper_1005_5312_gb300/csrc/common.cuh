@@ -111,6 +111,9 @@ struct start_ctx {
     st::DBuf pcon;    // float contribution per pair
     long long npairs = 0;
 
+    // memoised march: per chain link (virtual source, particle)
+    st::DBuf m_vid, m_j, m_nxt[2], m_acc[2], m_links[2], m_fr[2], m_table;
+
     // generic scratch
     st::DBuf tk[2], tv[2], hist, scan_tmp, stage, flags;
     st::DBuf counters; // u64[16]
@@ -120,6 +123,8 @@ struct start_ctx {
     cudaEvent_t ev[2 * START_NPHASES] = {};  // phase begin/end events (timing = 1)
     bool ev_init = false;
     bool ev_rec[START_NPHASES] = {};
+    double hop_ms = -1.0;                    // summed memo hop kernels (timing = 1)
+    cudaEvent_t hev[2] = {};
 };
 
 namespace st {
@@ -128,6 +133,10 @@ namespace st {
 enum Counter {
     C_RAYS = 0, C_HOPS, C_MARCH_FB, C_WALK_FB, C_NBR_FB, C_MAX_HOPS, C_BAD_INPUT, C_CHAIN_OVF,
     C_INTERNAL,   // count/fill disagreement or an out-of-range index (never expected)
+    C_EVALS,      // neighbour-list evaluations performed
+    C_SLOTS,      // memoised chain links (virtual source, particle)
+    C_MEMO_OVF,   // memo slot capacity exceeded (the host retries larger)
+    C_FRONTIER,   // size of the next memo frontier
     C_COUNT = 16
 };
 

@@ -1,0 +1,164 @@
+// One step of the upstream search of Eq. tau (Section 2.2.1), shared by the
+// per-ray march and the memoised march.
+//
+// A group of G lanes evaluates the neighbour list of particle j for a source
+// at r_s: lane l reads neighbour slots l, l+G, ...; each candidate k is
+// tested for "strictly closer to r_s than j" and scored by
+// c_k = (r_s - r_j).(r_k - r_j) / |r_k - r_j| (the cosine of the angle phi
+// times |r_s - r_j|).  The group argmax is taken by shuffles.  Both the
+// candidate test and the argmax are FP32 with a certified error bound; when
+// any margin is inside its bound the group re-decides the whole step with the
+// FP64 expressions of the definition (upstream_64), so the chosen upstream
+// particle is always the one the FP64 definition picks.
+#pragma once
+
+#include "common.cuh"
+
+namespace st {
+
+constexpr u32 kNone = 0xffffffffu;
+
+struct MarchArgs {
+    const u32 *pent, *ptgt;
+    long long npairs;
+    u32 np, n_svs, n_ssrc, n_evs;   // bounds of every index the march dereferences
+    const float4 *pq;
+    const u32 *nb_off, *nb_idx, *porig;
+    const float4 *svsrc;   // source-tree virtual sources (centre, L / L_unit)
+    const float4 *ssrc;    // individual sources (position, L / L_unit), sorted
+    const float4 *evsrc;   // emitter-tree virtual sources
+    const float *eLs;      // individual emitters' L / L_unit, Morton order
+    float sig;             // sigma * len_unit (per length unit per cm^-3)
+    float rfloor2;         // squared dilution floor
+    float tau_cut;
+    long long hop_cap;
+    float *pcon;           // per-pair contribution L e^-tau / (4 pi r^2), scaled units
+    unsigned long long *counters;
+};
+
+// FP64 upstream choice with the definition's operation order; the group's
+// lanes share the neighbour slots and reduce with (c desc, input index asc).
+template <int G>
+__device__ u32 upstream_64(const MarchArgs &a, float4 pj, float4 src, u32 s0, u32 s1, int gl,
+                           unsigned gmask)
+{
+    double jx = pj.x, jy = pj.y, jz = pj.z, sx = src.x, sy = src.y, sz = src.z;
+    double Dj = d2_64(jx, jy, jz, sx, sy, sz);
+    double bx = __dsub_rn(sx, jx), by = __dsub_rn(sy, jy), bz = __dsub_rn(sz, jz);
+    double bc = 0.0;
+    u32 bo = kNone, bk = kNone;
+    for (u32 s = s0 + gl; s < s1; s += G) {
+        u32 k = a.nb_idx[s];
+        if (k >= a.np) continue;
+        float4 pk = a.pq[k];
+        double kx = pk.x, ky = pk.y, kz = pk.z;
+        double Dk = d2_64(kx, ky, kz, sx, sy, sz);
+        if (!(Dk < Dj)) continue;
+        double ax = __dsub_rn(kx, jx), ay = __dsub_rn(ky, jy), az = __dsub_rn(kz, jz);
+        double dot = __dadd_rn(__dadd_rn(__dmul_rn(bx, ax), __dmul_rn(by, ay)), __dmul_rn(bz, az));
+        double cval = __ddiv_rn(dot, __dsqrt_rn(d2_64(kx, ky, kz, jx, jy, jz)));
+        u32 o = a.porig[k];
+        if (bk == kNone || cval > bc || (cval == bc && o < bo)) {
+            bk = k;
+            bc = cval;
+            bo = o;
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off; off >>= 1) {
+        double oc = __shfl_xor_sync(gmask, bc, off, G);
+        u32 oo = __shfl_xor_sync(gmask, bo, off, G);
+        u32 ok = __shfl_xor_sync(gmask, bk, off, G);
+        bool take = ok != kNone && (bk == kNone || oc > bc || (oc == bc && oo < bo));
+        if (take) {
+            bc = oc;
+            bo = oo;
+            bk = ok;
+        }
+    }
+    return bk;
+}
+
+// One neighbour-list evaluation at particle j (record pj) toward src.
+// Returns the upstream particle (kNone at the end of the chain) and the
+// optical-depth increment dt: sigma (n_j + n_up)/2 dl with the radial
+// difference dl = (|b|^2 - |c|^2) / (|b| + |c|) evaluated as
+// (r_j - r_up).((r_j - r_s) + (r_up - r_s)) / (|b| + |c|) to avoid
+// cancellation, or sigma n_j |r_j - r_s| at the chain end.  Every lane of the
+// group returns the same values; fbs counts FP64 re-decisions.
+template <int G>
+__device__ __forceinline__ u32 hop(const MarchArgs &a, u32 j, float4 pj, float4 src, int gl,
+                                   unsigned gmask, float &dt, unsigned long long &fbs)
+{
+    const float two_eps = 32.f * kU32;   // 2 x the 16u|b| bound on each score
+    const float eps_q = 16.f * kU32;
+    float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
+    float bn = sqrtf(bx * bx + by * by + bz * bz);
+    u32 s0 = a.nb_off[j], s1 = a.nb_off[j + 1];
+    float bc = -1.f, sc = -1.f;
+    u32 bk = kNone;
+    bool unsure = false;
+#pragma unroll 4
+    for (u32 s = s0 + gl; s < s1; s += G) {
+        u32 k = a.nb_idx[s];
+        if (k >= a.np) continue;   // cannot happen: lists hold particle indices
+        float4 pk = a.pq[k];
+        float ax = pk.x - pj.x, ay = pk.y - pj.y, az = pk.z - pj.z;
+        float a2 = ax * ax + ay * ay + az * az;
+        if (a2 == 0.f) {
+            // same position as j: never strictly closer; a nonzero offset that
+            // underflowed is left to the FP64 decision
+            if (pk.x != pj.x || pk.y != pj.y || pk.z != pj.z) unsure = true;
+            continue;
+        }
+        float dot = bx * ax + by * ay + bz * az;
+        // |score error| <= 16u|b|: dot carries <= 5u|a||b|, rsqrtf <= 2 ulp
+        float ra = rsqrtf(a2);
+        float an = a2 * ra;
+        float q = 2.f * dot - a2;   // > 0 iff |r_k - r_s| < |r_j - r_s|
+        float eq = eps_q * (2.f * an * bn + a2) + 1e-37f;
+        if (q > eq) {
+            float cv = dot * ra;
+            if (cv > bc) {
+                sc = bc;
+                bc = cv;
+                bk = k;
+            } else if (cv > sc) {
+                sc = cv;
+            }
+        } else if (q >= -eq) {
+            unsure = true;
+        }
+    }
+    float mc = bc;
+    u32 mk = bk;
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) {
+        float oc = __shfl_xor_sync(gmask, mc, o, G);
+        u32 ok = __shfl_xor_sync(gmask, mk, o, G);
+        if (oc > mc || (oc == mc && ok < mk)) {
+            mc = oc;
+            mk = ok;
+        }
+    }
+    // every certified candidate scores > 0; -1 marks "none"
+    float lim = mc - two_eps * bn;
+    bool amb = unsure || (bk != mk && bc > 0.f && bc > lim) || (sc > 0.f && sc > lim);
+    if (__any_sync(gmask, amb)) {
+        mk = upstream_64<G>(a, pj, src, s0, s1, gl, gmask);
+        ++fbs;
+    }
+    if (mk == kNone) {
+        dt = a.sig * pj.w * bn;
+        return kNone;
+    }
+    float4 pu = a.pq[mk];
+    float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
+    float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
+    float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+    float dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
+    dt = a.sig * 0.5f * (pj.w + pu.w) * dl;
+    return mk;
+}
+
+}  // namespace st

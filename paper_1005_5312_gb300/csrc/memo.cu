@@ -1,0 +1,421 @@
+// Memoised march (the distance-ordered reuse of Section 2.2.1 and the
+// per-list evaluation of Section 2.2.2): the optical depth from a virtual
+// source v to a particle k is tau(v, k) = d_tau(k -> up_v(k)) + tau(v, up_v(k)),
+// so every chain link (v, k) needs one neighbour-list evaluation, shared by
+// all rays whose chains pass through it, instead of one per ray step.
+//
+// The same upstream choices are made as by the per-ray march (hop<G>), so
+// the chains -- and therefore tau up to the order of the additions -- are
+// those of the definition; the paper's "boundary" particles, whose upstream
+// particle is not in the list, simply continue the chain with links (v, k)
+// outside the list.
+//
+// Work is level-synchronous:
+//   1. every interaction pair (v, target) becomes slot p of a hash table
+//      keyed by (v, particle);
+//   2. each frontier slot takes one hop; its upstream link (v, up) is found
+//      in the table or claimed as a new slot, which joins the next frontier;
+//      links claimed by another group in the same launch are resolved by a
+//      second kernel, after the launch boundary;
+//   3. tau of every slot follows by compensated pointer jumping over the
+//      link forest (log2 of the longest chain rounds, double-buffered, so the
+//      sum order depends only on the chain);
+//   4. each pair contributes L e^-tau / (4 pi r^2).
+// Count-1 source cells and their single member are the same source and
+// share one chain forest.
+#include <math.h>
+
+#include "common.cuh"
+#include "march.cuh"
+
+namespace st {
+
+constexpr u32 kPending = 0x80000000u;
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+struct __align__(16) HEntry {
+    unsigned long long key;
+    unsigned int val;
+    unsigned int pad;
+};
+
+struct MemoArgs {
+    MarchArgs m;
+    u32 SN, NS, EN;                 // source-tree nodes, sources, emitter-tree nodes
+    const uint4 *smeta, *emeta;     // (skip, first, count, leaf) of the two trees
+    u32 *svid, *sj;                 // slot: virtual source id, particle
+    u32 *nxt;                       // slot: next slot (kNone = chain end)
+    float2 *acc;                    // slot: (hi, lo) optical depth of its link
+    u32 *links;                     // slot: links from it to the chain end
+    unsigned long long *nslots;     // slots allocated so far
+    const u32 *fr_in;               // frontier (NULL: slots [0, nf))
+    long long nf;
+    u32 *fr_out;
+    unsigned long long *nf_out;
+    u32 cap;                        // slot capacity
+    HEntry *table;
+    unsigned long long hmask;
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x)
+{
+    x ^= x >> 31;
+    x *= 0x7fb5d329728ea185ull;
+    x ^= x >> 27;
+    x *= 0x81dadef4bc2dd44dull;
+    x ^= x >> 33;
+    return x;
+}
+
+// Canonical virtual-source id of a list entry: tree nodes first, then
+// individual sources; a single-member leaf maps to its member.
+__device__ __forceinline__ u32 canon(const MemoArgs &a, u32 e)
+{
+    u32 id = e & kEntryIdMask;
+    bool src = (e & kEntrySrc) != 0;
+    if (!(e & kEntryEmit)) {
+        if (src) return a.SN + id;
+        uint4 mt = a.smeta[id];
+        return (mt.w && mt.z == 1u) ? a.SN + mt.y : id;
+    }
+    u32 base = a.SN + a.NS;
+    if (src) return base + a.EN + id;
+    uint4 mt = a.emeta[id];
+    return (mt.w && mt.z == 1u) ? base + a.EN + mt.y : base + id;
+}
+
+__device__ __forceinline__ float4 vsource(const MemoArgs &a, u32 vid)
+{
+    if (vid < a.SN) return a.m.svsrc[vid];
+    vid -= a.SN;
+    if (vid < a.NS) return a.m.ssrc[vid];
+    vid -= a.NS;
+    if (vid < a.EN) return a.m.evsrc[vid];
+    vid -= a.EN;
+    float4 q = a.m.pq[vid];
+    return make_float4(q.x, q.y, q.z, a.m.eLs[vid]);
+}
+
+__device__ __forceinline__ unsigned long long link_key(u32 vid, u32 k)
+{
+    return ((unsigned long long)vid << 32) | k;
+}
+
+// 1. every pair is a slot and a table entry
+__global__ void k_memo_init(MemoArgs a)
+{
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.m.npairs) return;
+    u32 vid = canon(a, a.m.pent[p]);
+    u32 t = a.m.ptgt[p];
+    if (t >= a.m.np) {
+        atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+        t = 0;
+    }
+    a.svid[p] = vid;
+    a.sj[p] = t;
+    unsigned long long key = link_key(vid, t);
+    unsigned long long h = mix64(key) & a.hmask;
+    for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+        unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, key);
+        if (prev == kEmptyKey) {
+            a.table[h].val = (u32)p;
+            return;
+        }
+        if (prev == key) break;   // a duplicate pair: never expected
+        h = (h + 1) & a.hmask;
+    }
+    atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+}
+
+// 2. one hop for every frontier slot, G lanes per slot
+template <int G>
+__global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const int gbase = lane - gl;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const long long ngroups = ((long long)gridDim.x * blockDim.x) / G;
+    unsigned long long fbs = 0;
+    for (long long it = gid; it < a.nf; it += ngroups) {
+        u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
+        u32 vid = a.svid[s];
+        u32 j = a.sj[s];
+        float4 src = vsource(a, vid);
+        float4 pj = a.m.pq[j];
+        float dt;
+        u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs);
+        if (gl != 0) continue;
+        a.acc[s] = make_float2(dt, 0.f);
+        a.links[s] = 1u;
+        if (up == kNone) {
+            a.nxt[s] = kNone;
+            continue;
+        }
+        unsigned long long key = link_key(vid, up);
+        unsigned long long h = mix64(key) & a.hmask;
+        u32 nx = kNone;
+        bool placed = false;
+        for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+            unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
+            if (k == kEmptyKey) {
+                unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, key);
+                if (prev == kEmptyKey) {
+                    unsigned long long ns = atomicAdd(a.nslots, 1ull);
+                    if (ns >= a.cap) {
+                        atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
+                        nx = kNone;
+                    } else {
+                        a.svid[ns] = vid;
+                        a.sj[ns] = up;
+                        *(volatile unsigned int *)&a.table[h].val = (u32)ns;
+                        a.fr_out[atomicAdd(a.nf_out, 1ull)] = (u32)ns;
+                        nx = (u32)ns;
+                    }
+                    placed = true;
+                    break;
+                }
+                k = prev;
+            }
+            if (k == key) {
+                u32 v = *(volatile unsigned int *)&a.table[h].val;
+                nx = (v != kNone) ? v : (kPending | (u32)h);
+                placed = true;
+                break;
+            }
+            h = (h + 1) & a.hmask;
+        }
+        if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+        a.nxt[s] = nx;
+    }
+    if (gl != 0) fbs = 0;
+    for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
+    if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
+}
+
+// Links claimed by another group during the same launch: read the slot the
+// claimant wrote (visible after the launch boundary).
+__global__ void k_memo_resolve(MemoArgs a)
+{
+    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= a.nf) return;
+    u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
+    u32 nx = a.nxt[s];
+    if (nx != kNone && (nx & kPending)) {
+        u32 v = a.table[nx & ~kPending].val;
+        if (v == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+        a.nxt[s] = v;
+    }
+}
+
+// Compensated (double-float) addition: TwoSum of the high parts, then the
+// low parts and the rounding error, renormalised.
+__device__ __forceinline__ float2 cadd(float2 x, float2 y)
+{
+    float s = x.x + y.x;
+    float bb = s - x.x;
+    float err = (x.x - (s - bb)) + (y.x - bb);
+    float lo = x.y + y.y + err;
+    float hi = s + lo;
+    lo = lo - (hi - s);
+    return make_float2(hi, lo);
+}
+
+// 3. one synchronous round of pointer jumping
+__global__ void k_memo_jump(long long n, const u32 *nxt, const float2 *acc, const u32 *links,
+                            u32 *nxt2, float2 *acc2, u32 *links2, unsigned *active)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = false;
+    if (s < n) {
+        u32 nx = nxt[s];
+        if (nx == kNone) {
+            nxt2[s] = kNone;
+            acc2[s] = acc[s];
+            links2[s] = links[s];
+        } else {
+            u32 nn = nxt[nx];
+            acc2[s] = cadd(acc[s], acc[nx]);
+            links2[s] = links[s] + links[nx];
+            nxt2[s] = nn;
+            act = nn != kNone;
+        }
+    }
+    if (__any_sync(0xffffffffu, act) && (threadIdx.x & 31) == 0) *active = 1u;
+}
+
+// 4. contribution of every pair
+__global__ void k_memo_contrib(MemoArgs a)
+{
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long hops = 0, ovf = 0, rays = 0;
+    u32 maxh = 0;
+    if (p < a.m.npairs) {
+        float2 t = a.acc[p];
+        float tau = t.x + t.y;
+        float4 src = vsource(a, a.svid[p]);
+        float4 pt = a.m.pq[a.sj[p]];
+        float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
+        float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
+        a.m.pcon[p] = src.w * expf(-tau) / (12.566370614359172f * r2);
+        u32 l = a.links[p];
+        hops = l;
+        maxh = l;
+        rays = 1;
+        if ((long long)l > a.m.hop_cap) ovf = 1;
+    }
+    for (int o = 16; o; o >>= 1) {
+        hops += __shfl_xor_sync(0xffffffffu, hops, o);
+        rays += __shfl_xor_sync(0xffffffffu, rays, o);
+        ovf += __shfl_xor_sync(0xffffffffu, ovf, o);
+        maxh = max(maxh, __shfl_xor_sync(0xffffffffu, maxh, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (rays) atomicAdd(&a.m.counters[C_RAYS], rays);
+        if (hops) atomicAdd(&a.m.counters[C_HOPS], hops);
+        if (ovf) atomicAdd(&a.m.counters[C_CHAIN_OVF], ovf);
+        if (maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
+    }
+}
+
+template <int G>
+static void launch_memo_hop(const MemoArgs &a, cudaStream_t s, int nsm)
+{
+    long long blocks = (a.nf * G + 255) / 256;
+    long long cap = (long long)nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_memo_hop<G><<<(unsigned)blocks, 256, 0, s>>>(a);
+}
+
+static unsigned long long read_u64(start_ctx *c, const unsigned long long *d)
+{
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return v;
+}
+
+static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &overflow)
+{
+    cudaStream_t s = c->stream;
+    overflow = false;
+    size_t hsize = 1;
+    while (hsize < 2 * cap) hsize <<= 1;
+    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_nxt[0], cap * 4) ||
+        ensure(c->m_nxt[1], cap * 4) || ensure(c->m_acc[0], cap * 8) ||
+        ensure(c->m_acc[1], cap * 8) || ensure(c->m_links[0], cap * 4) ||
+        ensure(c->m_links[1], cap * 4) || ensure(c->m_fr[0], cap * 4) ||
+        ensure(c->m_fr[1], cap * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
+        return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    ST_CUDA(c, cudaMemsetAsync(c->m_table.p, 0xff, hsize * sizeof(HEntry), s));
+    ST_CUDA(c, cudaMemsetAsync(ctr + C_MEMO_OVF, 0, sizeof(unsigned long long), s));
+    ST_CUDA(c, cudaMemcpyAsync(ctr + C_SLOTS, &m.npairs, sizeof(unsigned long long),
+                               cudaMemcpyHostToDevice, s));
+    MemoArgs a;
+    a.m = m;
+    a.SN = (u32)c->stree.n;
+    a.NS = (u32)c->ns;
+    a.EN = (u32)(c->diffuse ? c->et.n : 0);
+    a.smeta = c->stree.meta.as<uint4>();
+    a.emeta = c->et.meta.as<uint4>();
+    a.svid = c->m_vid.as<u32>();
+    a.sj = c->m_j.as<u32>();
+    a.nxt = c->m_nxt[0].as<u32>();
+    a.acc = c->m_acc[0].as<float2>();
+    a.links = c->m_links[0].as<u32>();
+    a.nslots = ctr + C_SLOTS;
+    a.cap = (u32)cap;
+    a.table = c->m_table.as<HEntry>();
+    a.hmask = hsize - 1;
+    a.fr_in = nullptr;
+    a.nf = m.npairs;
+    a.nf_out = ctr + C_FRONTIER;
+    k_memo_init<<<grid_for(m.npairs, 256), 256, 0, s>>>(a);
+    ++c->launches;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (nsm <= 0) nsm = 1;
+    int cur = 0;
+    long long iter = 0;
+    bool timing = c->p.timing != 0;
+    if (timing && !c->hev[0]) {
+        cudaEventCreate(&c->hev[0]);
+        cudaEventCreate(&c->hev[1]);
+    }
+    double hop_ms = 0.0;
+    long long max_iter = m.hop_cap + 1;
+    while (a.nf > 0) {
+        a.fr_out = c->m_fr[cur].as<u32>();
+        ST_CUDA(c, cudaMemsetAsync(a.nf_out, 0, sizeof(unsigned long long), s));
+        if (timing) cudaEventRecord(c->hev[0], s);
+        switch (c->p.march_group) {
+        case 32: launch_memo_hop<32>(a, s, nsm); break;
+        case 16: launch_memo_hop<16>(a, s, nsm); break;
+        default: launch_memo_hop<8>(a, s, nsm); break;
+        }
+        if (timing) cudaEventRecord(c->hev[1], s);
+        k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
+        c->launches += 2;
+        ST_CUDA(c, cudaGetLastError());
+        unsigned long long nf = read_u64(c, a.nf_out);
+        if (timing) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
+            else cudaGetLastError();
+        }
+        if (read_u64(c, ctr + C_MEMO_OVF)) {
+            overflow = true;
+            return START_OK;
+        }
+        a.fr_in = c->m_fr[cur].as<u32>();
+        a.nf = (long long)nf;
+        cur ^= 1;
+        if (++iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
+    }
+    if (timing) c->hop_ms = hop_ms;
+    long long nslots = (long long)read_u64(c, ctr + C_SLOTS);
+    ST_CUDA(c, cudaMemcpyAsync(ctr + C_EVALS, &nslots, sizeof(nslots), cudaMemcpyHostToDevice, s));
+    // pointer jumping
+    int b = 0;
+    unsigned *active = c->flags.as<unsigned>() + 12;
+    for (int round = 0; round < 40; ++round) {
+        ST_CUDA(c, cudaMemsetAsync(active, 0, sizeof(unsigned), s));
+        k_memo_jump<<<grid_for(nslots, 256), 256, 0, s>>>(
+            nslots, c->m_nxt[b].as<u32>(), c->m_acc[b].as<float2>(), c->m_links[b].as<u32>(),
+            c->m_nxt[b ^ 1].as<u32>(), c->m_acc[b ^ 1].as<float2>(),
+            c->m_links[b ^ 1].as<u32>(), active);
+        ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+        b ^= 1;
+        unsigned act = 0;
+        ST_CUDA(c, cudaMemcpyAsync(&act, active, sizeof(act), cudaMemcpyDeviceToHost, s));
+        ST_CUDA(c, cudaStreamSynchronize(s));
+        if (!act) break;
+    }
+    a.acc = c->m_acc[b].as<float2>();
+    a.links = c->m_links[b].as<u32>();
+    k_memo_contrib<<<grid_for(m.npairs, 256), 256, 0, s>>>(a);
+    ++c->launches;
+    return cuda_check(c, cudaGetLastError(), "k_memo_contrib");
+}
+
+int run_memo(start_ctx *c, const MarchArgs &m)
+{
+    if (m.npairs == 0) return START_OK;
+    size_t cap = (size_t)m.npairs + (size_t)(m.npairs / 2) + (size_t)c->np + 4096;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        // slot ids and table indices must stay below the pending flag (2^31)
+        if (cap >= (1ull << 30)) return set_err(c, START_ERANGE, "too many chain links");
+        bool overflow = false;
+        ST_TRY(memo_attempt(c, m, cap, overflow));
+        if (!overflow) return START_OK;
+        cap *= 2;
+    }
+    return set_err(c, START_ENOMEM, "memoised march: slot capacity");
+}
+
+}  // namespace st

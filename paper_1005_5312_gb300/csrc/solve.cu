@@ -13,10 +13,12 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "march.cuh"
 
 namespace st {
 
-constexpr u32 kNone = 0xffffffffu;
+int run_memo(start_ctx *c, const MarchArgs &m);
+
 
 // ---------------------------------------------------------------- walk
 struct TreeView {
@@ -91,24 +93,6 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long np, Tr
 }
 
 // ---------------------------------------------------------------- march
-struct MarchArgs {
-    const u32 *pent, *ptgt;
-    long long npairs;
-    u32 np, n_svs, n_ssrc, n_evs;   // bounds of every index the march dereferences
-    const float4 *pq;
-    const u32 *nb_off, *nb_idx, *porig;
-    const float4 *svsrc;   // source-tree virtual sources (centre, L / L_unit)
-    const float4 *ssrc;    // individual sources (position, L / L_unit), sorted
-    const float4 *evsrc;   // emitter-tree virtual sources
-    const float *eLs;      // individual emitters' L / L_unit, Morton order
-    float sig;             // sigma * len_unit (per length unit per cm^-3)
-    float rfloor2;         // squared dilution floor
-    float tau_cut;
-    long long hop_cap;
-    float *pcon;           // per-pair contribution L e^-tau / (4 pi r^2), scaled units
-    unsigned long long *counters;
-};
-
 // Position and L / L_unit of a pair's source; an out-of-range entry (never
 // expected) yields a dark source and raises the internal-error counter.
 __device__ __forceinline__ float4 pair_source(const MarchArgs &a, u32 e)
@@ -138,51 +122,9 @@ __device__ __forceinline__ u32 pair_target(const MarchArgs &a, long long p)
     return t;
 }
 
-// FP64 upstream choice with the definition's operation order; the group's
-// lanes share the neighbour slots and reduce with (c desc, input index asc).
-template <int G>
-__device__ u32 upstream_64(const MarchArgs &a, float4 pj, float4 src, u32 s0, u32 s1, int gl,
-                           unsigned gmask)
-{
-    double jx = pj.x, jy = pj.y, jz = pj.z, sx = src.x, sy = src.y, sz = src.z;
-    double Dj = d2_64(jx, jy, jz, sx, sy, sz);
-    double bx = __dsub_rn(sx, jx), by = __dsub_rn(sy, jy), bz = __dsub_rn(sz, jz);
-    double bc = 0.0;
-    u32 bo = kNone, bk = kNone;
-    for (u32 s = s0 + gl; s < s1; s += G) {
-        u32 k = a.nb_idx[s];
-        if (k >= a.np) continue;
-        float4 pk = a.pq[k];
-        double kx = pk.x, ky = pk.y, kz = pk.z;
-        double Dk = d2_64(kx, ky, kz, sx, sy, sz);
-        if (!(Dk < Dj)) continue;
-        double ax = __dsub_rn(kx, jx), ay = __dsub_rn(ky, jy), az = __dsub_rn(kz, jz);
-        double dot = __dadd_rn(__dadd_rn(__dmul_rn(bx, ax), __dmul_rn(by, ay)), __dmul_rn(bz, az));
-        double cval = __ddiv_rn(dot, __dsqrt_rn(d2_64(kx, ky, kz, jx, jy, jz)));
-        u32 o = a.porig[k];
-        if (bk == kNone || cval > bc || (cval == bc && o < bo)) {
-            bk = k;
-            bc = cval;
-            bo = o;
-        }
-    }
-#pragma unroll
-    for (int off = G / 2; off; off >>= 1) {
-        double oc = __shfl_xor_sync(gmask, bc, off, G);
-        u32 oo = __shfl_xor_sync(gmask, bo, off, G);
-        u32 ok = __shfl_xor_sync(gmask, bk, off, G);
-        bool take = ok != kNone && (bk == kNone || oc > bc || (oc == bc && oo < bo));
-        if (take) {
-            bc = oc;
-            bo = oo;
-            bk = ok;
-        }
-    }
-    return bk;
-}
-
-// One ray per group of G lanes; groups refill independently so that the
-// warp stays converged on the hop body.
+// Per-ray march (Section 2.2.1 integration along the ray): one ray per group
+// of G lanes, the chain followed to its end with a compensated FP32 sum.
+// Groups refill independently so that the warp stays converged on the hop.
 template <int G>
 __global__ void __launch_bounds__(256) k_march(MarchArgs a)
 {
@@ -192,8 +134,6 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
     const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const long long ngroups = ((long long)gridDim.x * blockDim.x) / G;
-    const float two_eps = 32.f * kU32;
-    const float eps_q = 16.f * kU32;
 
     unsigned long long rays = 0, hops = 0, fbs = 0, ovf = 0;
     u32 maxh = 0;
@@ -211,69 +151,11 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
     while (__any_sync(0xffffffffu, have)) {
         if (have) {
             float4 pj = a.pq[j];
-            float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
-            float bn = sqrtf(bx * bx + by * by + bz * bz);
-            u32 s0 = a.nb_off[j], s1 = a.nb_off[j + 1];
-            float bc = -1.f, sc = -1.f;
-            u32 bk = kNone;
-            bool unsure = false;
-#pragma unroll 4
-            for (u32 s = s0 + gl; s < s1; s += G) {
-                u32 k = a.nb_idx[s];
-                if (k >= a.np) continue;   // cannot happen: lists hold particle indices
-                float4 pk = a.pq[k];
-                float ax = pk.x - pj.x, ay = pk.y - pj.y, az = pk.z - pj.z;
-                float dot = bx * ax + by * ay + bz * az;
-                float a2 = ax * ax + ay * ay + az * az;
-                float an = sqrtf(a2);
-                float q = 2.f * dot - a2;
-                float eq = eps_q * (2.f * an * bn + a2) + 1e-37f;
-                if (q > eq) {
-                    float cv = __fdiv_rn(dot, an);
-                    if (cv > bc) {
-                        sc = bc;
-                        bc = cv;
-                        bk = k;
-                    } else if (cv > sc) {
-                        sc = cv;
-                    }
-                } else if (q >= -eq) {
-                    unsure = true;
-                }
-            }
-            float mc = bc;
-            u32 mk = bk;
-#pragma unroll
-            for (int o = G / 2; o; o >>= 1) {
-                float oc = __shfl_xor_sync(gmask, mc, o, G);
-                u32 ok = __shfl_xor_sync(gmask, mk, o, G);
-                if (oc > mc || (oc == mc && ok < mk)) {
-                    mc = oc;
-                    mk = ok;
-                }
-            }
-            // every certified candidate has c > 0; -1 marks "none"
-            float lim = mc - two_eps * bn;
-            bool amb = unsure || (bk != mk && bc > 0.f && bc > lim) || (sc > 0.f && sc > lim);
-            if (__any_sync(gmask, amb)) {
-                mk = upstream_64<G>(a, pj, src, s0, s1, gl, gmask);
-                ++fbs;
-            }
-            ++nh;
-            bool done = false;
             float dt;
-            if (mk == kNone) {
-                dt = a.sig * pj.w * bn;
-                done = true;
-            } else {
-                float4 pu = a.pq[mk];
-                float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
-                float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
-                float cn = sqrtf(cx * cx + cy * cy + cz * cz);
-                float dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
-                dt = a.sig * 0.5f * (pj.w + pu.w) * dl;
-                j = mk;
-            }
+            u32 up = hop<G>(a, j, pj, src, gl, gmask, dt, fbs);
+            ++nh;
+            bool done = up == kNone;
+            if (!done) j = up;
             float yk = dt - comp;
             float tk = tau + yk;
             comp = (tk - tau) - yk;
@@ -315,7 +197,10 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
     }
     if (lane == 0) {
         if (rays) atomicAdd(&a.counters[C_RAYS], rays);
-        if (hops) atomicAdd(&a.counters[C_HOPS], hops);
+        if (hops) {
+            atomicAdd(&a.counters[C_HOPS], hops);
+            atomicAdd(&a.counters[C_EVALS], hops);
+        }
         if (fbs) atomicAdd(&a.counters[C_MARCH_FB], fbs);
         if (ovf) atomicAdd(&a.counters[C_CHAIN_OVF], ovf);
         if (maxh) atomicMax(&a.counters[C_MAX_HOPS], (unsigned long long)maxh);
@@ -458,18 +343,22 @@ int run_solve(start_ctx *c, float theta, bool /*keep_lists*/)
     a.pcon = c->pcon.as<float>();
     a.counters = ctr;
     if (c->npairs > 0) {
-        int nsm = 0;
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-        if (nsm <= 0) nsm = 1;
         phase_mark(c, START_PHASE_MARCH, false);
-        switch (c->p.march_group) {
-        case 32: launch_march<32>(a, s, nsm); break;
-        case 16: launch_march<16>(a, s, nsm); break;
-        default: launch_march<8>(a, s, nsm); break;
+        if (c->p.march_mode == 1) {
+            ST_TRY(run_memo(c, a));
+        } else {
+            int nsm = 0;
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+            if (nsm <= 0) nsm = 1;
+            switch (c->p.march_group) {
+            case 32: launch_march<32>(a, s, nsm); break;
+            case 16: launch_march<16>(a, s, nsm); break;
+            default: launch_march<8>(a, s, nsm); break;
+            }
+            ++c->launches;
+            ST_CUDA(c, cudaGetLastError());
         }
-        ++c->launches;
         phase_mark(c, START_PHASE_MARCH, true);
-        ST_CUDA(c, cudaGetLastError());
     }
     return START_OK;
 }

@@ -129,9 +129,10 @@ def test_lists_bitexact(S, cfg1, theta):
 
 
 # ------------------------------------------------------------------ Gamma
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("theta", [0.0, 0.5, 1.0])
-def test_gamma_parity_config1(S, cfg1, theta):
-    ctx, orc = make_pair(S, cfg1)
+def test_gamma_parity_config1(S, cfg1, theta, mode):
+    ctx, orc = make_pair(S, cfg1, march_mode=mode)
     nHI = cfg1.n_HI()
     g = np.zeros(cfg1.n_p, np.float32)
     ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
@@ -142,9 +143,10 @@ def test_gamma_parity_config1(S, cfg1, theta):
     assert st["hops"] == orc.last_stats["hops"]
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("theta", [0.0, 0.7])
-def test_gamma_parity_ragged_nonuniform(S, ragged, theta):
-    ctx, orc = make_pair(S, ragged)
+def test_gamma_parity_ragged_nonuniform(S, ragged, theta, mode):
+    ctx, orc = make_pair(S, ragged, march_mode=mode)
     nHI = (ragged.y0 * 1e-3).astype(np.float32)
     g = np.zeros(ragged.n_p, np.float32)
     ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
@@ -155,11 +157,12 @@ def test_gamma_parity_ragged_nonuniform(S, ragged, theta):
     assert st["hops"] == orc.last_stats["hops"]
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("group", [8, 16, 32])
-def test_march_group_is_result_neutral(S, cfg1, group):
-    ctx = S.Context(march_group=group, ptree_leaf=PTREE_LEAF)
+def test_march_group_is_result_neutral(S, cfg1, group, mode):
+    ctx = S.Context(march_group=group, ptree_leaf=PTREE_LEAF, march_mode=mode)
     ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
-    ref_ctx = S.Context(march_group=8, ptree_leaf=PTREE_LEAF)
+    ref_ctx = S.Context(march_group=8, ptree_leaf=PTREE_LEAF, march_mode=mode)
     ref_ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
     nHI = cfg1.n_HI()
     a = np.zeros(cfg1.n_p, np.float32)
@@ -167,6 +170,23 @@ def test_march_group_is_result_neutral(S, cfg1, group):
     ctx.rt_solve(0.5, n_HI=nHI, gamma_out=a)
     ref_ctx.rt_solve(0.5, n_HI=nHI, gamma_out=b)
     assert np.array_equal(a, b)
+
+
+def test_memoised_and_per_ray_march_agree(S, cfg1):
+    """Same chains, so the same rays and chain links; tau differs only in the
+    order of the additions."""
+    nHI = cfg1.n_HI()
+    out = {}
+    for mode in (0, 1):
+        ctx = S.Context(march_mode=mode, tau_cut=1e30)
+        ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+        g = np.zeros(cfg1.n_p, np.float32)
+        ctx.rt_solve(0.5, n_HI=nHI, gamma_out=g)
+        out[mode] = (g.astype(np.float64), ctx.stats())
+    (g0, s0), (g1, s1) = out[0], out[1]
+    assert s0["rays"] == s1["rays"] and s0["hops"] == s1["hops"]
+    assert s1["evals"] < s0["evals"] / 5          # the links are shared
+    assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
 
 
 def test_single_source_theta_independent_on_gpu(S):
@@ -323,8 +343,9 @@ def test_invalid_inputs_are_rejected(S, cfg1):
     assert np.all(np.isfinite(g)) and g.max() > 0
 
 
-def test_hop_cap_reports_echain(S, cfg1):
-    ctx = S.Context(hop_cap=2, tau_cut=1e30)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_hop_cap_reports_echain(S, cfg1, mode):
+    ctx = S.Context(hop_cap=2, tau_cut=1e30, march_mode=mode)
     ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
     with pytest.raises(S.StartError) as e:
         ctx.rt_solve(0.5, n_HI=cfg1.n_HI(), gamma_out=np.zeros(cfg1.n_p, np.float32))
@@ -345,8 +366,8 @@ def test_config2_full_size_sampled_targets(S):
     orc = oracle.Oracle.from_workload(w, ptree_leaf=PTREE_LEAF)
     idx = np.random.default_rng(1).choice(w.n_p, 48, replace=False)
     gamma_close(g[idx], orc.gamma(nHI, 0.5, targets=idx))
-    # and with the default early stop of opaque rays
-    ctx2 = S.Context()
+    # the per-ray march, with its early stop of opaque rays
+    ctx2 = S.Context(march_mode=0)
     ctx2.build_trees(w.pos, w.h, w.src_pos, w.src_L)
     g2 = np.zeros(w.n_p, np.float32)
     ctx2.rt_solve(0.5, n_HI=nHI, gamma_out=g2)
