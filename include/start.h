@@ -80,8 +80,9 @@ typedef struct start_params {
                               "each cell contains only one radiation source" */
     int ptree_leaf;        /* max particles per particle-tree leaf (neighbour
                               search only; does not change any result) */
-    int march_group;       /* lanes cooperating on one ray: 8, 16 or 32
-                              (0 = default); does not change any result */
+    int march_group;       /* lanes cooperating on one neighbour-list
+                              evaluation: 1, 2, 4, 8, 16 or 32 (0 = default);
+                              does not change any result */
     int timing;            /* 1: record CUDA events around each phase (see
                               start_get_timings); 0: none */
     int march_mode;        /* 1: memoised march, every chain link (virtual

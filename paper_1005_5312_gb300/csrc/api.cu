@@ -253,7 +253,8 @@ static void release_all(start_ctx *c)
                    &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
                    &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,
                    &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
-                   &c->scan_tmp, &c->stage, &c->flags, &c->counters};
+                   &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j,
+                   &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr[0], &c->m_fr[1], &c->m_table};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);
@@ -316,7 +317,8 @@ int start_create(start_ctx **out, const start_params *p)
     if (d.src_leaf < 1 || d.ptree_leaf < 1 || !(d.sigma_cm2 > 0) || !(d.len_unit_cm > 0) ||
         !(d.L_unit > 0) || !(d.alpha_A >= 0) || !(d.alpha_B >= 0) || !(d.tau_cut > 0))
         return START_EINVAL;
-    if (d.march_group != 0 && d.march_group != 8 && d.march_group != 16 && d.march_group != 32)
+    if (d.march_group != 0 && d.march_group != 1 && d.march_group != 2 && d.march_group != 4 &&
+        d.march_group != 8 && d.march_group != 16 && d.march_group != 32)
         return START_EINVAL;
     if (d.march_group == 0) d.march_group = 8;
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;

@@ -112,7 +112,7 @@ struct start_ctx {
     long long npairs = 0;
 
     // memoised march: per chain link (virtual source, particle)
-    st::DBuf m_vid, m_j, m_nxt[2], m_acc[2], m_links[2], m_fr[2], m_table;
+    st::DBuf m_vid, m_j, m_st[2], m_ups, m_fr[2], m_table;
 
     // generic scratch
     st::DBuf tk[2], tv[2], hist, scan_tmp, stage, flags;

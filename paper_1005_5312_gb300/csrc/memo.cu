@@ -44,9 +44,8 @@ struct MemoArgs {
     u32 SN, NS, EN;                 // source-tree nodes, sources, emitter-tree nodes
     const uint4 *smeta, *emeta;     // (skip, first, count, leaf) of the two trees
     u32 *svid, *sj;                 // slot: virtual source id, particle
-    u32 *nxt;                       // slot: next slot (kNone = chain end)
-    float2 *acc;                    // slot: (hi, lo) optical depth of its link
-    u32 *links;                     // slot: links from it to the chain end
+    uint4 *state;                   // slot: (next slot, links to the end, tau hi, tau lo)
+    u32 *ups;                       // frontier item: upstream particle of its hop
     unsigned long long *nslots;     // slots allocated so far
     const u32 *fr_in;               // frontier (NULL: slots [0, nf))
     long long nf;
@@ -128,7 +127,27 @@ __global__ void k_memo_init(MemoArgs a)
     atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
 }
 
-// 2. one hop for every frontier slot, G lanes per slot
+// Sums counters of a block and adds them once per block.
+__device__ __forceinline__ void block_add(unsigned long long *ctr, unsigned long long v)
+{
+    __shared__ unsigned long long part[32];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) part[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        unsigned long long x = l < nw ? part[l] : 0ull;
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (l == 0 && x) atomicAdd(ctr, x);
+    }
+}
+
+// 2a. one hop for every frontier slot, G lanes per slot.  Only the gathers
+// of the neighbour search touch memory here (particle records and lists,
+// L2-resident); the table lookups run in k_memo_link so that their random
+// traffic does not evict that working set.
 template <int G>
 __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
 {
@@ -147,66 +166,74 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
         float4 pj = a.m.pq[j];
         float dt;
         u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs);
-        if (gl != 0) continue;
-        a.acc[s] = make_float2(dt, 0.f);
-        a.links[s] = 1u;
-        if (up == kNone) {
-            a.nxt[s] = kNone;
-            continue;
+        if (gl == 0) {
+            a.ups[it] = up;
+            a.state[s] = make_uint4(kNone, 1u, __float_as_uint(dt), 0u);
         }
-        unsigned long long key = link_key(vid, up);
-        unsigned long long h = mix64(key) & a.hmask;
-        u32 nx = kNone;
-        bool placed = false;
-        for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
-            unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
-            if (k == kEmptyKey) {
-                unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, key);
-                if (prev == kEmptyKey) {
-                    unsigned long long ns = atomicAdd(a.nslots, 1ull);
-                    if (ns >= a.cap) {
-                        atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
-                        nx = kNone;
-                    } else {
-                        a.svid[ns] = vid;
-                        a.sj[ns] = up;
-                        *(volatile unsigned int *)&a.table[h].val = (u32)ns;
-                        a.fr_out[atomicAdd(a.nf_out, 1ull)] = (u32)ns;
-                        nx = (u32)ns;
-                    }
-                    placed = true;
-                    break;
-                }
-                k = prev;
-            }
-            if (k == key) {
-                u32 v = *(volatile unsigned int *)&a.table[h].val;
-                nx = (v != kNone) ? v : (kPending | (u32)h);
-                placed = true;
-                break;
-            }
-            h = (h + 1) & a.hmask;
-        }
-        if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
-        a.nxt[s] = nx;
     }
     if (gl != 0) fbs = 0;
     for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
     if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
 }
 
-// Links claimed by another group during the same launch: read the slot the
+// 2b. the upstream link of every frontier slot: found in the table, or
+// claimed as a new slot that joins the next frontier.
+__global__ void k_memo_link(MemoArgs a)
+{
+    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= a.nf) return;
+    u32 up = a.ups[it];
+    if (up == kNone) return;              // chain end: next stays kNone
+    u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
+    u32 vid = a.svid[s];
+    unsigned long long key = link_key(vid, up);
+    unsigned long long h = mix64(key) & a.hmask;
+    u32 nx = kNone;
+    bool placed = false;
+    for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+        unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
+        if (k == kEmptyKey) {
+            unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                unsigned long long ns = atomicAdd(a.nslots, 1ull);
+                if (ns >= a.cap) {
+                    atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
+                } else {
+                    a.svid[ns] = vid;
+                    a.sj[ns] = up;
+                    *(volatile unsigned int *)&a.table[h].val = (u32)ns;
+                    a.fr_out[atomicAdd(a.nf_out, 1ull)] = (u32)ns;
+                    nx = (u32)ns;
+                }
+                placed = true;
+                break;
+            }
+            k = prev;
+        }
+        if (k == key) {
+            u32 v = *(volatile unsigned int *)&a.table[h].val;
+            nx = (v != kNone) ? v : (kPending | (u32)h);
+            placed = true;
+            break;
+        }
+        h = (h + 1) & a.hmask;
+    }
+    if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+    a.state[s].x = nx;
+}
+
+// Links claimed by another thread during the same launch: read the slot the
 // claimant wrote (visible after the launch boundary).
 __global__ void k_memo_resolve(MemoArgs a)
 {
     long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= a.nf) return;
     u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
-    u32 nx = a.nxt[s];
+    u32 nx = a.state[s].x;
     if (nx != kNone && (nx & kPending)) {
         u32 v = a.table[nx & ~kPending].val;
         if (v == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
-        a.nxt[s] = v;
+        a.state[s].x = v;
     }
 }
 
@@ -223,61 +250,49 @@ __device__ __forceinline__ float2 cadd(float2 x, float2 y)
     return make_float2(hi, lo);
 }
 
-// 3. one synchronous round of pointer jumping
-__global__ void k_memo_jump(long long n, const u32 *nxt, const float2 *acc, const u32 *links,
-                            u32 *nxt2, float2 *acc2, u32 *links2, unsigned *active)
+// 3. one synchronous round of pointer jumping over the packed link state
+__global__ void k_memo_jump(long long n, const uint4 *st, uint4 *st2, unsigned *active)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
     if (s < n) {
-        u32 nx = nxt[s];
-        if (nx == kNone) {
-            nxt2[s] = kNone;
-            acc2[s] = acc[s];
-            links2[s] = links[s];
-        } else {
-            u32 nn = nxt[nx];
-            acc2[s] = cadd(acc[s], acc[nx]);
-            links2[s] = links[s] + links[nx];
-            nxt2[s] = nn;
-            act = nn != kNone;
+        uint4 me = st[s];
+        if (me.x != kNone) {
+            uint4 nx = st[me.x];
+            float2 t = cadd(make_float2(__uint_as_float(me.z), __uint_as_float(me.w)),
+                            make_float2(__uint_as_float(nx.z), __uint_as_float(nx.w)));
+            me = make_uint4(nx.x, me.y + nx.y, __float_as_uint(t.x), __float_as_uint(t.y));
+            act = nx.x != kNone;
         }
+        st2[s] = me;
     }
     if (__any_sync(0xffffffffu, act) && (threadIdx.x & 31) == 0) *active = 1u;
 }
 
 // 4. contribution of every pair
-__global__ void k_memo_contrib(MemoArgs a)
+__global__ void __launch_bounds__(256) k_memo_contrib(MemoArgs a)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long hops = 0, ovf = 0, rays = 0;
     u32 maxh = 0;
     if (p < a.m.npairs) {
-        float2 t = a.acc[p];
-        float tau = t.x + t.y;
+        uint4 st = a.state[p];
+        float tau = __uint_as_float(st.z) + __uint_as_float(st.w);
         float4 src = vsource(a, a.svid[p]);
         float4 pt = a.m.pq[a.sj[p]];
         float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
         float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
         a.m.pcon[p] = src.w * expf(-tau) / (12.566370614359172f * r2);
-        u32 l = a.links[p];
-        hops = l;
-        maxh = l;
+        hops = st.y;
+        maxh = st.y;
         rays = 1;
-        if ((long long)l > a.m.hop_cap) ovf = 1;
+        if ((long long)st.y > a.m.hop_cap) ovf = 1;
     }
-    for (int o = 16; o; o >>= 1) {
-        hops += __shfl_xor_sync(0xffffffffu, hops, o);
-        rays += __shfl_xor_sync(0xffffffffu, rays, o);
-        ovf += __shfl_xor_sync(0xffffffffu, ovf, o);
-        maxh = max(maxh, __shfl_xor_sync(0xffffffffu, maxh, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (rays) atomicAdd(&a.m.counters[C_RAYS], rays);
-        if (hops) atomicAdd(&a.m.counters[C_HOPS], hops);
-        if (ovf) atomicAdd(&a.m.counters[C_CHAIN_OVF], ovf);
-        if (maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
-    }
+    block_add(&a.m.counters[C_RAYS], rays);
+    block_add(&a.m.counters[C_HOPS], hops);
+    block_add(&a.m.counters[C_CHAIN_OVF], ovf);
+    for (int o = 16; o; o >>= 1) maxh = max(maxh, __shfl_xor_sync(0xffffffffu, maxh, o));
+    if ((threadIdx.x & 31) == 0 && maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
 }
 
 template <int G>
@@ -304,10 +319,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     overflow = false;
     size_t hsize = 1;
     while (hsize < 2 * cap) hsize <<= 1;
-    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_nxt[0], cap * 4) ||
-        ensure(c->m_nxt[1], cap * 4) || ensure(c->m_acc[0], cap * 8) ||
-        ensure(c->m_acc[1], cap * 8) || ensure(c->m_links[0], cap * 4) ||
-        ensure(c->m_links[1], cap * 4) || ensure(c->m_fr[0], cap * 4) ||
+    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_st[0], cap * 16) ||
+        ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) || ensure(c->m_fr[0], cap * 4) ||
         ensure(c->m_fr[1], cap * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned long long *ctr = c->counters.as<unsigned long long>();
@@ -324,9 +337,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.emeta = c->et.meta.as<uint4>();
     a.svid = c->m_vid.as<u32>();
     a.sj = c->m_j.as<u32>();
-    a.nxt = c->m_nxt[0].as<u32>();
-    a.acc = c->m_acc[0].as<float2>();
-    a.links = c->m_links[0].as<u32>();
+    a.state = c->m_st[0].as<uint4>();
+    a.ups = c->m_ups.as<u32>();
     a.nslots = ctr + C_SLOTS;
     a.cap = (u32)cap;
     a.table = c->m_table.as<HEntry>();
@@ -355,24 +367,32 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         switch (c->p.march_group) {
         case 32: launch_memo_hop<32>(a, s, nsm); break;
         case 16: launch_memo_hop<16>(a, s, nsm); break;
+        case 4: launch_memo_hop<4>(a, s, nsm); break;
+        case 2: launch_memo_hop<2>(a, s, nsm); break;
+        case 1: launch_memo_hop<1>(a, s, nsm); break;
         default: launch_memo_hop<8>(a, s, nsm); break;
         }
         if (timing) cudaEventRecord(c->hev[1], s);
+        k_memo_link<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
         k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
-        c->launches += 2;
+        c->launches += 3;
         ST_CUDA(c, cudaGetLastError());
-        unsigned long long nf = read_u64(c, a.nf_out);
+        // the overflow flag and the next frontier size are adjacent counters
+        unsigned long long both[2] = {0, 0};
+        static_assert(C_FRONTIER == C_MEMO_OVF + 1, "adjacent counters");
+        ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_MEMO_OVF, sizeof(both), cudaMemcpyDeviceToHost, s));
+        ST_CUDA(c, cudaStreamSynchronize(s));
         if (timing) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
             else cudaGetLastError();
         }
-        if (read_u64(c, ctr + C_MEMO_OVF)) {
+        if (both[0]) {
             overflow = true;
             return START_OK;
         }
         a.fr_in = c->m_fr[cur].as<u32>();
-        a.nf = (long long)nf;
+        a.nf = (long long)both[1];
         cur ^= 1;
         if (++iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
     }
@@ -384,10 +404,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     unsigned *active = c->flags.as<unsigned>() + 12;
     for (int round = 0; round < 40; ++round) {
         ST_CUDA(c, cudaMemsetAsync(active, 0, sizeof(unsigned), s));
-        k_memo_jump<<<grid_for(nslots, 256), 256, 0, s>>>(
-            nslots, c->m_nxt[b].as<u32>(), c->m_acc[b].as<float2>(), c->m_links[b].as<u32>(),
-            c->m_nxt[b ^ 1].as<u32>(), c->m_acc[b ^ 1].as<float2>(),
-            c->m_links[b ^ 1].as<u32>(), active);
+        k_memo_jump<<<grid_for(nslots, 256), 256, 0, s>>>(nslots, c->m_st[b].as<uint4>(),
+                                                          c->m_st[b ^ 1].as<uint4>(), active);
         ++c->launches;
         ST_CUDA(c, cudaGetLastError());
         b ^= 1;
@@ -396,8 +414,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         ST_CUDA(c, cudaStreamSynchronize(s));
         if (!act) break;
     }
-    a.acc = c->m_acc[b].as<float2>();
-    a.links = c->m_links[b].as<u32>();
+    a.state = c->m_st[b].as<uint4>();
     k_memo_contrib<<<grid_for(m.npairs, 256), 256, 0, s>>>(a);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_memo_contrib");

@@ -353,6 +353,9 @@ int run_solve(start_ctx *c, float theta, bool /*keep_lists*/)
             switch (c->p.march_group) {
             case 32: launch_march<32>(a, s, nsm); break;
             case 16: launch_march<16>(a, s, nsm); break;
+            case 4: launch_march<4>(a, s, nsm); break;
+            case 2: launch_march<2>(a, s, nsm); break;
+            case 1: launch_march<1>(a, s, nsm); break;
             default: launch_march<8>(a, s, nsm); break;
             }
             ++c->launches;

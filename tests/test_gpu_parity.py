@@ -158,7 +158,7 @@ def test_gamma_parity_ragged_nonuniform(S, ragged, theta, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("group", [8, 16, 32])
+@pytest.mark.parametrize("group", [1, 4, 16, 32])
 def test_march_group_is_result_neutral(S, cfg1, group, mode):
     ctx = S.Context(march_group=group, ptree_leaf=PTREE_LEAF, march_mode=mode)
     ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
