@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--theta2", type=float, default=1.0)
-    ap.add_argument("--march-group", type=int, default=8)
+    ap.add_argument("--march-group", type=int, default=2)
     ap.add_argument("--march-mode", type=int, default=1, choices=[0, 1],
                     help="1 memoised march (default), 0 per-ray march")
     ap.add_argument("--no-e2e", action="store_true")

@@ -293,7 +293,7 @@ int start_default_params(start_params *p)
     memset(p, 0, sizeof(*p));
     p->src_leaf = 1;
     p->ptree_leaf = 16;
-    p->march_group = 8;
+    p->march_group = 2;
     p->march_mode = 1;
     p->sigma_cm2 = 6.3e-18;
     p->len_unit_cm = 3.0857e21;
@@ -320,7 +320,7 @@ int start_create(start_ctx **out, const start_params *p)
     if (d.march_group != 0 && d.march_group != 1 && d.march_group != 2 && d.march_group != 4 &&
         d.march_group != 8 && d.march_group != 16 && d.march_group != 32)
         return START_EINVAL;
-    if (d.march_group == 0) d.march_group = 8;
+    if (d.march_group == 0) d.march_group = 2;
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
     start_ctx *c = new (std::nothrow) start_ctx();
     if (!c) return START_ENOMEM;

@@ -39,7 +39,7 @@ def test_default_params_and_status_strings(libstart):
     import paper_1005_5312_gb300 as S
     p = S.default_params()
     assert p.src_leaf == 1 and p.sigma_cm2 == 6.3e-18 and p.len_unit_cm == 3.0857e21
-    assert p.tau_cut == 110.0 and p.march_group == 8
+    assert p.tau_cut == 110.0 and p.march_group == 2 and p.march_mode == 1
     L = S.lib()
     assert L.start_status_string(S.START_EINVAL) == b"START_EINVAL"
     assert L.start_status_string(S.START_ECHAIN) == b"START_ECHAIN"
