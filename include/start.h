@@ -101,6 +101,10 @@ typedef struct start_params {
                               (default 110; e^-110 is below float32's smallest
                               subnormal relative to any representable flux) */
     long long hop_cap;     /* max upstream steps per ray (0 = N_p + 1) */
+    long long max_pairs;   /* targets are solved in Morton-contiguous chunks of
+                              at most this many interaction pairs (bounds the
+                              device memory of a solve; 0 = 2^27).  Chains are
+                              shared only within a chunk */
     long long spin_cap;    /* max iterations of any device wait (reserved) */
     void *stream;          /* cudaStream_t to issue work on (NULL = default) */
 } start_params;
@@ -120,6 +124,7 @@ typedef struct start_stats {
     long long launches;         /* kernels launched by this context so far */
     long long evals;            /* neighbour-list evaluations performed */
     long long links;            /* distinct chain links (memoised march) */
+    long long chunks;           /* target chunks of the last solve */
 } start_stats;
 
 /* Phases timed when start_params.timing = 1 (milliseconds of the last
@@ -237,6 +242,11 @@ const char *start_last_error(const start_ctx *c);
 
 /* Name of a status code. */
 const char *start_status_string(int status);
+
+/* Device bytes currently held by all contexts of this process (buffers
+ * come from a library-owned stream-ordered pool; a server admits work
+ * against a budget with it). */
+long long start_memory_in_use(void);
 
 /* ---- allocation-free Morton ordering (no counterpart in the paper) ----
  *

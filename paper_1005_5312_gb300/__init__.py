@@ -36,14 +36,15 @@ class StartParams(C.Structure):
                 ("timing", C.c_int), ("march_mode", C.c_int), ("reserved1", C.c_int),
                 ("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
                 ("L_unit", C.c_double), ("alpha_A", C.c_double), ("alpha_B", C.c_double),
-                ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("spin_cap", C.c_longlong),
+                ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("max_pairs", C.c_longlong),
+                ("spin_cap", C.c_longlong),
                 ("stream", C.c_void_p)]
 
 
 class StartStats(C.Structure):
     _fields_ = [(n, C.c_longlong) for n in (
         "rays", "hops", "march_fallbacks", "walk_fallbacks", "nbr_fallbacks", "nodes_src",
-        "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches", "evals", "links")]
+        "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches", "evals", "links", "chunks")]
 
 
 class StartError(RuntimeError):
@@ -87,6 +88,7 @@ def lib():
             "start_last_error": (C.c_char_p, [vp]),
             "start_status_string": (C.c_char_p, [i]),
             "start_morton_order_noalloc": (i, [vp, ll, vp, vp, vp, vp]),
+            "start_memory_in_use": (ll, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -12,49 +14,99 @@
 
 namespace st {
 
-int finish_gamma(start_ctx *c, float *gout_dev);
-int run_walk(start_ctx *c, float theta);
 
 // ---------------------------------------------------------------- buffers and errors
+// Device buffers come from a library-owned, stream-ordered memory pool (one
+// per device, memory kept reserved after a free): growing a buffer never
+// synchronises the device, so contexts on different streams -- concurrent
+// requests of a server -- do not stall each other.  Allocations and frees
+// are ordered on the stream of the context being served (thread-local,
+// set on entry to every public call).
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+std::atomic<long long> g_bytes{0};
+thread_local cudaStream_t tl_stream = nullptr;
+
+cudaMemPool_t device_pool()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+}  // namespace
+
+void set_thread_stream(cudaStream_t s) { tl_stream = s; }
+cudaStream_t thread_stream() { return tl_stream; }
+
 int ensure(DBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (bytes <= b.cap) return START_OK;
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.cap = 0;
+    release(b);
     size_t want = bytes + bytes / 8 + 256;
-    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaMemPool_t pool = device_pool();
+    void *p = nullptr;
+    if (!pool || cudaMallocFromPoolAsync(&p, want, pool, tl_stream) != cudaSuccess) {
         cudaGetLastError();
-        b.p = nullptr;
         return START_ENOMEM;
     }
+    b.p = p;
     b.cap = want;
+    g_bytes += (long long)want;
     return START_OK;
 }
 
 int ensure_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s)
 {
     if (bytes <= b.cap) return START_OK;
+    cudaMemPool_t pool = device_pool();
     void *q = nullptr;
-    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    if (!pool || cudaMallocFromPoolAsync(&q, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
         return START_ENOMEM;
     }
     if (b.p && used) cudaMemcpyAsync(q, b.p, std::min(used, b.cap), cudaMemcpyDeviceToDevice, s);
-    cudaStreamSynchronize(s);
-    if (b.p) cudaFree(b.p);
+    if (b.p) {
+        cudaFreeAsync(b.p, s);
+        g_bytes -= (long long)b.cap;
+    }
     b.p = q;
     b.cap = bytes;
+    g_bytes += (long long)bytes;
     return START_OK;
 }
 
 void release(DBuf &b)
 {
-    if (b.p) cudaFree(b.p);
+    if (b.p) {
+        cudaFreeAsync(b.p, tl_stream);
+        g_bytes -= (long long)b.cap;
+    }
     b.p = nullptr;
     b.cap = 0;
 }
+
+long long bytes_in_use() { return g_bytes.load(); }
 
 void phase_mark(start_ctx *c, int phase, bool end)
 {
@@ -109,18 +161,24 @@ static int copy_out(start_ctx *c, void *dst, const void *src, size_t n)
     return START_OK;
 }
 
+// Makes the context's device current and its stream the thread's allocation
+// stream for the duration of a public call; restores both on exit.
 struct DeviceGuard {
     int prev = -1;
-    explicit DeviceGuard(int dev)
+    cudaStream_t prev_stream = nullptr;
+    explicit DeviceGuard(const start_ctx *c)
     {
         if (cudaGetDevice(&prev) != cudaSuccess) {
             cudaGetLastError();
             prev = -1;
         }
-        if (prev != dev) cudaSetDevice(dev);
+        if (prev != c->device) cudaSetDevice(c->device);
+        prev_stream = thread_stream();
+        set_thread_stream(c->stream);
     }
     ~DeviceGuard()
     {
+        set_thread_stream(prev_stream);
         int cur = -1;
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
@@ -331,6 +389,7 @@ int start_create(start_ctx **out, const start_params *p)
         delete c;
         return START_ECUDA;
     }
+    DeviceGuard g(c);
     if (ensure(c->counters, C_COUNT * sizeof(unsigned long long)) ||
         cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), c->stream) !=
             cudaSuccess) {
@@ -346,9 +405,10 @@ int start_create(start_ctx **out, const start_params *p)
 int start_destroy(start_ctx *c)
 {
     if (!c) return START_EINVAL;
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     cudaStreamSynchronize(c->stream);
     release_all(c);
+    cudaStreamSynchronize(c->stream);
     delete c;
     return START_OK;
 }
@@ -358,7 +418,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
                       unsigned flags)
 {
     if (!c) return START_EINVAL;
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     c->built = c->has_state = c->solved = false;
     if (n_p < 0 || n_s < 0) return set_err(c, START_EINVAL, "negative size");
     if (n_p >= START_MAX_N || n_s >= START_MAX_N)
@@ -445,7 +505,7 @@ int start_set_state(start_ctx *c, const float *n_H, const double *y)
 {
     if (!c) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     long long n = c->np;
     if (n && !n_H) return set_err(c, START_EINVAL, "NULL n_H");
     if (n == 0) {
@@ -473,7 +533,7 @@ int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_ou
     if (!c) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
     if (!(theta >= 0.f) || !isfinite(theta)) return set_err(c, START_EINVAL, "theta must be >= 0");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     long long n = c->np;
     if (n_HI && n) {
         Staged in;
@@ -487,10 +547,9 @@ int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_ou
     } else if (!n_HI && c->diffuse && !c->has_state && n) {
         return set_err(c, START_ENOTBUILT, "diffuse mode needs start_set_state");
     }
-    ST_TRY(run_solve(c, theta, false));
     bool dev_out = gamma_out && is_device_ptr(gamma_out);
     if (gamma_out && !dev_out) ST_TRY(ensure(c->stage, (n ? n : 1) * sizeof(float)));
-    ST_TRY(finish_gamma(c, dev_out ? gamma_out : (gamma_out ? c->stage.as<float>() : nullptr)));
+    ST_TRY(run_solve(c, theta, dev_out ? gamma_out : (gamma_out ? c->stage.as<float>() : nullptr)));
     if (gamma_out && !dev_out) ST_TRY(copy_out(c, gamma_out, c->stage.p, n * sizeof(float)));
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency (interaction lists)");
@@ -504,7 +563,7 @@ int start_ionize(start_ctx *c, double dt_s, double *y_out)
     if (!c) return START_EINVAL;
     if (!c->built || !c->solved) return set_err(c, START_ENOTBUILT, "start_rt_solve first");
     if (!(dt_s >= 0.0) || !isfinite(dt_s)) return set_err(c, START_EINVAL, "dt must be >= 0");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     ST_TRY(run_ionize(c, dt_s));
     if (y_out && c->np) {
         bool dev = is_device_ptr(y_out);
@@ -549,7 +608,7 @@ int start_get_perm(start_ctx *c, int which, unsigned *perm)
 {
     if (!c || !perm || (which != 0 && which != 1)) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     long long n = which ? c->ns : c->np;
     return copy_out(c, perm, which ? c->sorig.p : c->porig.p, n * sizeof(u32));
 }
@@ -558,7 +617,7 @@ int start_get_keys(start_ctx *c, int which, unsigned long long *keys)
 {
     if (!c || !keys || (which != 0 && which != 1)) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     long long n = which ? c->ns : c->np;
     return copy_out(c, keys, which ? c->skey.p : c->pkey.p, n * sizeof(u64));
 }
@@ -581,7 +640,7 @@ int start_get_tree(start_ctx *c, int which, int *level, unsigned *first, unsigne
     Tree *t = c ? pick_tree(c, which) : nullptr;
     if (!t) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     long long n = t->n;
     if (n == 0) return START_OK;
     if (which == 2 && c->diffuse && c->has_state) ST_TRY(refresh_emitters(c));
@@ -598,6 +657,7 @@ int start_get_tree(start_ctx *c, int which, int *level, unsigned *first, unsigne
         lf[i] = (int)meta[i].w;
     }
     ST_TRY(copy_out(c, level, t->level.p, n * sizeof(int)));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
     if (first) ST_CUDA(c, cudaMemcpy(first, a.data(), n * 4, cudaMemcpyDefault));
     if (count) ST_CUDA(c, cudaMemcpy(count, b.data(), n * 4, cudaMemcpyDefault));
     if (skip) ST_CUDA(c, cudaMemcpy(skip, d.data(), n * 4, cudaMemcpyDefault));
@@ -639,8 +699,9 @@ int start_get_neighbors(start_ctx *c, unsigned long long *off, unsigned *idx)
 {
     if (!c || !off) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     long long n = c->np;
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
     std::vector<u32> moff(n + 1), mval(c->nb_total), porig(n);
     ST_CUDA(c, cudaMemcpy(moff.data(), c->nb_off.p, (n + 1) * 4, cudaMemcpyDeviceToHost));
     if (c->nb_total) ST_CUDA(c, cudaMemcpy(mval.data(), c->nb_idx.p, c->nb_total * 4, cudaMemcpyDeviceToHost));
@@ -658,10 +719,11 @@ int start_get_lists(start_ctx *c, float theta, unsigned long long *off, unsigned
     if (!c || !off) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
     if (!(theta >= 0.f) || !isfinite(theta)) return set_err(c, START_EINVAL, "theta must be >= 0");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     long long n = c->np;
     if (c->diffuse && c->has_state) ST_TRY(refresh_emitters(c));
     ST_TRY(run_walk(c, theta));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
     std::vector<u64> moff(n + 1);
     std::vector<u32> mval(c->npairs), porig(n);
     ST_CUDA(c, cudaMemcpy(moff.data(), c->loff.p, (n + 1) * 8, cudaMemcpyDeviceToHost));
@@ -679,7 +741,7 @@ int start_get_emitter_L(start_ctx *c, float *out)
 {
     if (!c || !out) return START_EINVAL;
     if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     if (c->np == 0) return START_OK;
     if (c->diffuse && c->has_state) ST_TRY(refresh_emitters(c));
     ST_TRY(ensure(c->stage, c->np * sizeof(float)));
@@ -692,7 +754,7 @@ int start_get_emitter_L(start_ctx *c, float *out)
 int start_get_stats(start_ctx *c, start_stats *out)
 {
     if (!c || !out) return START_EINVAL;
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     unsigned long long v[C_COUNT];
     ST_CUDA(c, cudaMemcpyAsync(v, c->counters.p, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -710,13 +772,14 @@ int start_get_stats(start_ctx *c, start_stats *out)
     out->launches = (long long)c->launches;
     out->evals = (long long)v[C_EVALS];
     out->links = (long long)(c->p.march_mode == 1 ? v[C_SLOTS] : 0);
+    out->chunks = c->chunks;
     return START_OK;
 }
 
 int start_get_timings(start_ctx *c, double *ms, int n)
 {
     if (!c || !ms || n < 0 || n > START_NPHASES) return START_EINVAL;
-    DeviceGuard g(c->device);
+    DeviceGuard g(c);
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int k = 0; k < n; ++k) {
         ms[k] = -1.0;
@@ -738,6 +801,8 @@ const char *start_last_error(const start_ctx *c)
     if (!c) return "NULL context";
     return c->err.c_str();
 }
+
+long long start_memory_in_use(void) { return bytes_in_use(); }
 
 const char *start_status_string(int s)
 {

@@ -37,9 +37,13 @@ struct DBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
-// Grow-only device buffer; returns a START_* status.
+// Grow-only device buffer from the library's stream-ordered pool, ordered on
+// the calling thread's context stream; returns a START_* status.
 int ensure(DBuf &b, size_t bytes);
 void release(DBuf &b);
+void set_thread_stream(cudaStream_t s);
+cudaStream_t thread_stream();
+long long bytes_in_use();
 
 // ---------------------------------------------------------------- trees
 // Octree in depth-first pre-order (children in octant order).
@@ -124,6 +128,8 @@ struct start_ctx {
     bool ev_init = false;
     bool ev_rec[START_NPHASES] = {};
     double hop_ms = -1.0;                    // summed memo hop kernels (timing = 1)
+    unsigned long long memo_evals = 0, memo_links = 0;   // over the chunks of a solve
+    long long chunks = 0;                    // target chunks of the last solve
     cudaEvent_t hev[2] = {};
 };
 
@@ -186,7 +192,8 @@ void tree_release(Tree &t);
 int build_neighbours(start_ctx *c);
 
 // solve.cu
-int run_solve(start_ctx *c, float theta, bool keep_lists);
+int run_solve(start_ctx *c, float theta, float *gout_dev);
+int run_walk(start_ctx *c, float theta);
 int run_ionize(start_ctx *c, double dt);
 int refresh_emitters(start_ctx *c);
 

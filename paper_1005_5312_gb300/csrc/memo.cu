@@ -250,7 +250,12 @@ __device__ __forceinline__ float2 cadd(float2 x, float2 y)
     return make_float2(hi, lo);
 }
 
-// 3. one synchronous round of pointer jumping over the packed link state
+// 3. one synchronous round of pointer jumping over the packed link state.
+// A slot whose chain is resolved (next = kNone) is copied once more so that
+// both buffers hold it, then marked stable (bit 31 of its link count) and
+// never rewritten or re-read.
+constexpr u32 kStable = 0x80000000u;
+
 __global__ void k_memo_jump(long long n, const uint4 *st, uint4 *st2, unsigned *active)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,10 +266,14 @@ __global__ void k_memo_jump(long long n, const uint4 *st, uint4 *st2, unsigned *
             uint4 nx = st[me.x];
             float2 t = cadd(make_float2(__uint_as_float(me.z), __uint_as_float(me.w)),
                             make_float2(__uint_as_float(nx.z), __uint_as_float(nx.w)));
-            me = make_uint4(nx.x, me.y + nx.y, __float_as_uint(t.x), __float_as_uint(t.y));
+            me = make_uint4(nx.x, (me.y & ~kStable) + (nx.y & ~kStable), __float_as_uint(t.x),
+                            __float_as_uint(t.y));
             act = nx.x != kNone;
+            st2[s] = me;
+        } else if (!(me.y & kStable)) {
+            me.y |= kStable;
+            st2[s] = me;
         }
-        st2[s] = me;
     }
     if (__any_sync(0xffffffffu, act) && (threadIdx.x & 31) == 0) *active = 1u;
 }
@@ -283,10 +292,11 @@ __global__ void __launch_bounds__(256) k_memo_contrib(MemoArgs a)
         float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
         float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
         a.m.pcon[p] = src.w * expf(-tau) / (12.566370614359172f * r2);
-        hops = st.y;
-        maxh = st.y;
+        u32 l = st.y & ~kStable;
+        hops = l;
+        maxh = l;
         rays = 1;
-        if ((long long)st.y > a.m.hop_cap) ovf = 1;
+        if ((long long)l > a.m.hop_cap) ovf = 1;
     }
     block_add(&a.m.counters[C_RAYS], rays);
     block_add(&a.m.counters[C_HOPS], hops);
@@ -396,9 +406,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         cur ^= 1;
         if (++iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
     }
-    if (timing) c->hop_ms = hop_ms;
+    if (timing) c->hop_ms += hop_ms;
     long long nslots = (long long)read_u64(c, ctr + C_SLOTS);
-    ST_CUDA(c, cudaMemcpyAsync(ctr + C_EVALS, &nslots, sizeof(nslots), cudaMemcpyHostToDevice, s));
+    c->memo_evals += (unsigned long long)nslots;
+    c->memo_links += (unsigned long long)nslots;
     // pointer jumping
     int b = 0;
     unsigned *active = c->flags.as<unsigned>() + 12;

@@ -12,6 +12,9 @@
 // per step), and a per-target pass sums the contributions in list order.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "march.cuh"
 
@@ -68,18 +71,18 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
 }
 
 template <bool FILL>
-__global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long np, TreeView st_,
-                                              TreeView et_, float th2f, double th2d, float cmag,
-                                              u32 *cnt, const u64 *off, u32 *ent, u32 *tgt,
-                                              unsigned long long *fb_total)
+__global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, long long t1,
+                                              TreeView st_, TreeView et_, float th2f, double th2d,
+                                              float cmag, u32 *cnt, const u64 *off, u64 base,
+                                              u32 *ent, u32 *tgt, unsigned long long *fb_total)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long i = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned fb = 0;
-    if (i < np) {
+    if (i < t1) {
         float4 p = pq[i];
         u32 c = 0;
-        u64 w = FILL ? off[i] : 0ull;
-        const u64 wend = FILL ? off[i + 1] : 0ull;
+        u64 w = FILL ? off[i] - base : 0ull;
+        const u64 wend = FILL ? off[i + 1] - base : 0ull;
         walk_tree<FILL>(st_, p, th2f, th2d, cmag, kNone, 0u, (u32)i, c, w, wend, ent, tgt, fb);
         walk_tree<FILL>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, (u32)i, c, w, wend, ent, tgt,
                         fb);
@@ -210,13 +213,13 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
 // ---------------------------------------------------------------- Gamma
 // Per target: compensated sum of its contributions in list order, converted
 // to photons cm^-2 s^-1.
-__global__ void k_gamma(const float *pcon, const u64 *off, long long np, float conv,
-                        const u32 *porig, float *gam, float *gout)
+__global__ void k_gamma(const float *pcon, const u64 *off, long long t0, long long t1, u64 base,
+                        float conv, const u32 *porig, float *gam, float *gout)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
+    long long i = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= t1) return;
     float s = 0.f, cmp = 0.f;
-    for (u64 e = off[i]; e < off[i + 1]; ++e) {
+    for (u64 e = off[i] - base; e < off[i + 1] - base; ++e) {
         float yk = pcon[e] - cmp;
         float tk = s + yk;
         cmp = (tk - s) - yk;
@@ -270,60 +273,82 @@ static void launch_march(const MarchArgs &a, cudaStream_t s, int nsm)
     k_march<G><<<(unsigned)blocks, 256, 0, s>>>(a);
 }
 
-// Interaction lists of every target: count, scan, fill.
-int run_walk(start_ctx *c, float theta)
+// Interaction-list counts of every target and their exclusive scan (loff).
+static int walk_count(start_ctx *c, float theta, const TreeView &sv, const TreeView &ev,
+                      unsigned long long *total)
 {
     long long np = c->np;
     cudaStream_t s = c->stream;
-    c->npairs = 0;
     unsigned long long *ctr = c->counters.as<unsigned long long>();
-    if (np == 0) return START_OK;
-    phase_mark(c, START_PHASE_WALK, false);
-    TreeView sv{c->stree.box.as<float4>(), c->stree.meta.as<uint4>(), c->stree.cube.as<double>(),
-                (u32)c->stree.n};
-    TreeView ev{c->et.box.as<float4>(), c->et.meta.as<uint4>(), c->et.cube.as<double>(),
-                (u32)(c->diffuse ? c->et.n : 0)};
-    float th2f = theta * theta;
-    double th2d = (double)theta * (double)theta;
     ST_TRY(ensure(c->lcount, np * sizeof(u32)));
     ST_TRY(ensure(c->loff, (np + 1) * sizeof(u64)));
-    k_walk<false><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), np, sv, ev, th2f, th2d,
-                                                    c->fr.cmag, c->lcount.as<u32>(), nullptr,
-                                                    nullptr, nullptr, ctr + C_WALK_FB); ++c->launches;
+    k_walk<false><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), 0, np, sv, ev,
+                                                    theta * theta, (double)theta * (double)theta,
+                                                    c->fr.cmag, c->lcount.as<u32>(), nullptr, 0ull,
+                                                    nullptr, nullptr, ctr + C_WALK_FB);
+    ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_TRY(exclusive_scan_u32_to_u64(c, c->lcount.as<u32>(), c->loff.as<u64>(), np));
-    unsigned long long total = 0;
-    ST_CUDA(c, cudaMemcpyAsync(&total, c->loff.as<u64>() + np, sizeof(total),
+    ST_CUDA(c, cudaMemcpyAsync(total, c->loff.as<u64>() + np, sizeof(*total),
                                cudaMemcpyDeviceToHost, s));
     ST_CUDA(c, cudaStreamSynchronize(s));
-    c->npairs = (long long)total;
-    size_t np2 = total ? total : 1;
-    if (ensure(c->pent, np2 * sizeof(u32)) || ensure(c->ptgt, np2 * sizeof(u32)) ||
-        ensure(c->pcon, np2 * sizeof(float)))
-        return set_err(c, START_ENOMEM, "out of device memory (interaction lists)");
-    k_walk<true><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), np, sv, ev, th2f, th2d,
-                                                   c->fr.cmag, nullptr, c->loff.as<u64>(),
-                                                   c->pent.as<u32>(), c->ptgt.as<u32>(), ctr + C_INTERNAL); ++c->launches;
-    phase_mark(c, START_PHASE_WALK, true);
+    return START_OK;
+}
+
+// Pairs of targets [t0, t1) written from index 0 of the pair buffers.
+static int walk_fill(start_ctx *c, float theta, const TreeView &sv, const TreeView &ev,
+                     long long t0, long long t1, u64 base)
+{
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    k_walk<true><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
+        c->pq.as<float4>(), t0, t1, sv, ev, theta * theta, (double)theta * (double)theta,
+        c->fr.cmag, nullptr, c->loff.as<u64>(), base, c->pent.as<u32>(), c->ptgt.as<u32>(),
+        ctr + C_INTERNAL);
+    ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_walk");
 }
 
-int run_solve(start_ctx *c, float theta, bool /*keep_lists*/)
+static int ensure_pairs(start_ctx *c, unsigned long long n)
 {
-    long long np = c->np;
-    cudaStream_t s = c->stream;
-    c->npairs = 0;
-    ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));
-    unsigned long long *ctr = c->counters.as<unsigned long long>();
-    if (np == 0) return START_OK;
-    if (c->diffuse) ST_TRY(refresh_emitters(c));
-    ST_TRY(run_walk(c, theta));
+    size_t m = n ? n : 1;
+    if (ensure(c->pent, m * sizeof(u32)) || ensure(c->ptgt, m * sizeof(u32)) ||
+        ensure(c->pcon, m * sizeof(float)))
+        return set_err(c, START_ENOMEM, "out of device memory (interaction lists)");
+    return START_OK;
+}
 
+static TreeView source_view(start_ctx *c)
+{
+    return TreeView{c->stree.box.as<float4>(), c->stree.meta.as<uint4>(),
+                    c->stree.cube.as<double>(), (u32)c->stree.n};
+}
+
+static TreeView emitter_view(start_ctx *c)
+{
+    return TreeView{c->et.box.as<float4>(), c->et.meta.as<uint4>(), c->et.cube.as<double>(),
+                    (u32)(c->diffuse ? c->et.n : 0)};
+}
+
+// Interaction lists of every target (all pairs at once; introspection).
+int run_walk(start_ctx *c, float theta)
+{
+    c->npairs = 0;
+    if (c->np == 0) return START_OK;
+    TreeView sv = source_view(c), ev = emitter_view(c);
+    unsigned long long total = 0;
+    ST_TRY(walk_count(c, theta, sv, ev, &total));
+    c->npairs = (long long)total;
+    ST_TRY(ensure_pairs(c, total));
+    return walk_fill(c, theta, sv, ev, 0, c->np, 0ull);
+}
+
+static MarchArgs march_args(start_ctx *c, long long npairs)
+{
     MarchArgs a;
     a.pent = c->pent.as<u32>();
     a.ptgt = c->ptgt.as<u32>();
-    a.npairs = c->npairs;
-    a.np = (u32)np;
+    a.npairs = npairs;
+    a.np = (u32)c->np;
     a.n_svs = (u32)c->stree.n;
     a.n_ssrc = (u32)c->ns;
     a.n_evs = (u32)(c->diffuse ? c->et.n : 0);
@@ -339,45 +364,113 @@ int run_solve(start_ctx *c, float theta, bool /*keep_lists*/)
     double rf = 1e-6 * c->fr.side;
     a.rfloor2 = (float)(rf * rf);
     a.tau_cut = (float)c->p.tau_cut;
-    a.hop_cap = c->p.hop_cap > 0 ? c->p.hop_cap : np + 1;
+    a.hop_cap = c->p.hop_cap > 0 ? c->p.hop_cap : c->np + 1;
     a.pcon = c->pcon.as<float>();
-    a.counters = ctr;
-    if (c->npairs > 0) {
-        phase_mark(c, START_PHASE_MARCH, false);
-        if (c->p.march_mode == 1) {
-            ST_TRY(run_memo(c, a));
-        } else {
-            int nsm = 0;
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-            if (nsm <= 0) nsm = 1;
-            switch (c->p.march_group) {
-            case 32: launch_march<32>(a, s, nsm); break;
-            case 16: launch_march<16>(a, s, nsm); break;
-            case 4: launch_march<4>(a, s, nsm); break;
-            case 2: launch_march<2>(a, s, nsm); break;
-            case 1: launch_march<1>(a, s, nsm); break;
-            default: launch_march<8>(a, s, nsm); break;
-            }
-            ++c->launches;
-            ST_CUDA(c, cudaGetLastError());
-        }
-        phase_mark(c, START_PHASE_MARCH, true);
-    }
-    return START_OK;
+    a.counters = c->counters.as<unsigned long long>();
+    return a;
 }
 
-// Writes Gamma (Morton, resident) and optionally the input-order copy.
-int finish_gamma(start_ctx *c, float *gout_dev)
+// Targets are processed in Morton-contiguous chunks of at most max_pairs
+// interaction pairs; each chunk is walked, marched and reduced on its own.
+int run_solve(start_ctx *c, float theta, float *gout_dev)
 {
-    if (c->np == 0) return START_OK;
+    long long np = c->np;
+    cudaStream_t s = c->stream;
+    c->npairs = 0;
+    c->memo_evals = c->memo_links = 0;
+    c->hop_ms = c->p.timing ? 0.0 : -1.0;
+    ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));
+    if (np == 0) return START_OK;
+    if (c->diffuse) ST_TRY(refresh_emitters(c));
+    TreeView sv = source_view(c), ev = emitter_view(c);
+    phase_mark(c, START_PHASE_WALK, false);
+    unsigned long long total = 0;
+    ST_TRY(walk_count(c, theta, sv, ev, &total));
+    c->npairs = (long long)total;
+    long long maxp = c->p.max_pairs > 0 ? c->p.max_pairs : (1LL << 27);
+    std::vector<long long> cut;      // chunk boundaries (targets)
+    cut.push_back(0);
+    if ((long long)total > maxp) {
+        std::vector<unsigned long long> off(np + 1);
+        ST_CUDA(c, cudaMemcpy(off.data(), c->loff.p, (np + 1) * sizeof(u64),
+                              cudaMemcpyDeviceToHost));
+        long long t0 = 0;
+        while (t0 < np) {
+            // largest t1 with off[t1] - off[t0] <= maxp, at least one target
+            long long lo = t0 + 1, hi = np;
+            while (lo < hi) {
+                long long mid = (lo + hi + 1) / 2;
+                if ((long long)(off[mid] - off[t0]) <= maxp) lo = mid;
+                else hi = mid - 1;
+            }
+            cut.push_back(lo);
+            t0 = lo;
+        }
+    } else {
+        cut.push_back(np);
+    }
+    unsigned long long chunk_max = 0;
+    if (cut.size() > 2) {
+        std::vector<unsigned long long> off(np + 1);
+        ST_CUDA(c, cudaMemcpy(off.data(), c->loff.p, (np + 1) * sizeof(u64),
+                              cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k + 1 < cut.size(); ++k)
+            chunk_max = std::max(chunk_max, off[cut[k + 1]] - off[cut[k]]);
+    } else {
+        chunk_max = total;
+    }
+    ST_TRY(ensure_pairs(c, chunk_max));
+    std::vector<unsigned long long> offh;
+    if (cut.size() > 2) {
+        offh.resize(np + 1);
+        ST_CUDA(c, cudaMemcpy(offh.data(), c->loff.p, (np + 1) * sizeof(u64),
+                              cudaMemcpyDeviceToHost));
+    }
+    phase_mark(c, START_PHASE_WALK, true);
+    c->chunks = (long long)cut.size() - 1;
     float conv = (float)(c->p.L_unit / (c->p.len_unit_cm * c->p.len_unit_cm));
-    phase_mark(c, START_PHASE_GAMMA, false);
-    k_gamma<<<grid_for(c->np, 256), 256, 0, c->stream>>>(c->pcon.as<float>(), c->loff.as<u64>(),
-                                                          c->np, conv, c->porig.as<u32>(),
-                                                          c->gam.as<float>(), gout_dev);
-    ++c->launches;
-    phase_mark(c, START_PHASE_GAMMA, true);
-    return cuda_check(c, cudaGetLastError(), "k_gamma");
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        long long t0 = cut[k], t1 = cut[k + 1];
+        u64 base = cut.size() > 2 ? offh[t0] : 0ull;
+        long long n = cut.size() > 2 ? (long long)(offh[t1] - offh[t0]) : (long long)total;
+        ST_TRY(walk_fill(c, theta, sv, ev, t0, t1, base));
+        MarchArgs a = march_args(c, n);
+        if (n > 0) {
+            phase_mark(c, START_PHASE_MARCH, false);
+            if (c->p.march_mode == 1) {
+                ST_TRY(run_memo(c, a));
+            } else {
+                int nsm = 0;
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+                if (nsm <= 0) nsm = 1;
+                switch (c->p.march_group) {
+                case 32: launch_march<32>(a, s, nsm); break;
+                case 16: launch_march<16>(a, s, nsm); break;
+                case 4: launch_march<4>(a, s, nsm); break;
+                case 2: launch_march<2>(a, s, nsm); break;
+                case 1: launch_march<1>(a, s, nsm); break;
+                default: launch_march<8>(a, s, nsm); break;
+                }
+                ++c->launches;
+                ST_CUDA(c, cudaGetLastError());
+            }
+            phase_mark(c, START_PHASE_MARCH, true);
+        }
+        phase_mark(c, START_PHASE_GAMMA, false);
+        k_gamma<<<grid_for(t1 - t0, 256), 256, 0, s>>>(c->pcon.as<float>(), c->loff.as<u64>(), t0,
+                                                       t1, base, conv, c->porig.as<u32>(),
+                                                       c->gam.as<float>(), gout_dev);
+        ++c->launches;
+        phase_mark(c, START_PHASE_GAMMA, true);
+        ST_CUDA(c, cudaGetLastError());
+    }
+    if (c->p.march_mode == 1) {
+        unsigned long long v[2] = {c->memo_evals, c->memo_links};
+        ST_CUDA(c, cudaMemcpyAsync(c->counters.as<unsigned long long>() + C_EVALS, v, sizeof(v),
+                                   cudaMemcpyHostToDevice, s));
+        ST_CUDA(c, cudaStreamSynchronize(s));
+    }
+    return START_OK;
 }
 
 // ---------------------------------------------------------------- ionise

@@ -189,6 +189,23 @@ def test_memoised_and_per_ray_march_agree(S, cfg1):
     assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_target_chunks_are_result_neutral(S, cfg1, mode):
+    """Chunking the targets changes which chains are shared, never a chain:
+    Gamma is bitwise the same."""
+    nHI = cfg1.n_HI()
+    out = []
+    for max_pairs in (0, 20000):
+        ctx = S.Context(march_mode=mode, max_pairs=max_pairs)
+        ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+        g = np.zeros(cfg1.n_p, np.float32)
+        ctx.rt_solve(0.5, n_HI=nHI, gamma_out=g)
+        out.append((g, ctx.stats()))
+    assert out[0][1]["chunks"] == 1 and out[1][1]["chunks"] > 10
+    assert out[0][1]["rays"] == out[1][1]["rays"] and out[0][1]["hops"] == out[1][1]["hops"]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
 def test_single_source_theta_independent_on_gpu(S):
     w = lattice_workload("one", 12, 2.0, 1, 5)
     ctx = S.Context()
