@@ -17,6 +17,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import math
 import os
 import statistics
@@ -56,6 +58,11 @@ def parse():
                     help="oracle work per CPU-baseline measurement")
     ap.add_argument("--ref-targets", type=int, default=16384,
                     help="targets per step of the reference arm")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-log2np", default="15,21")
     return ap.parse_args()
 
 
@@ -199,6 +206,29 @@ def cpu_baseline(w, theta, seconds):
     return {"value": rays / t, "unit": "rays/s", "cores": oracle.threads(), "kind": "oracle",
             "sample": f"Gamma at {done} random targets of {w.n_p} (theta={theta}, neutral "
                       f"start): {rays} rays in {t:.1f} s"}
+
+
+def serving(args):
+    """Continuous batching vs one solve at a time on the same Poisson stream
+    of requests of mixed size (real-time replay, 150 GB budget)."""
+    from paper_1005_5312_gb300.serve import Server, make_requests, summarize
+    lo, hi = (float(x) for x in args.serve_log2np.split(","))
+    reqs = make_requests(args.serve_requests, rate_hz=args.serve_rate, log2_np=(lo, hi))
+    res = {}
+    for name, workers in (("plain", 1), ("served", args.serve_workers)):
+        srv = Server(workers=workers, budget_bytes=150e9)
+        # warm the workers' contexts and pools on a small request
+        srv.serve(make_requests(workers, rate_hz=1e9, log2_np=(14, 14), seed=1), realtime=False)
+        r = srv.serve(reqs, realtime=True)
+        srv.close()
+        res[name] = summarize(r)
+    sp = res["served"]["solves_per_s"] / res["plain"]["solves_per_s"]
+    n_p = [r.n_p for r in reqs]
+    return {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, N_p=2^U({lo:g},{hi:g}),"
+                        " N_s=e^U(0,ln N_p), uniform|clumpy, theta in {0.5,1}, 1 step each",
+            "workers": args.serve_workers, "budget_gb": 150, "mean_n_p": float(np.mean(n_p)),
+            "served": res["served"], "plain": res["plain"],
+            "solves_per_s_vs_plain": sp}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -365,6 +395,9 @@ def run_gpu(args, w):
         out["e2e"] = {"value": e_rays / te, "unit": "rays/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * te / args.steps}
         ctx_h.close()
+
+    if ws == 1 and not args.no_serve:
+        out["serving"] = serving(args)
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, args.theta, args.cpu_seconds)
