@@ -311,7 +311,7 @@ static void release_all(start_ctx *c)
                    &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
                    &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,
                    &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
-                   &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j,
+                   &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr[0], &c->m_fr[1], &c->m_table};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);

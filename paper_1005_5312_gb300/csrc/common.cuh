@@ -112,11 +112,12 @@ struct start_ctx {
     st::DBuf loff;    // u64 [np + 1]
     st::DBuf pent;    // u32 entry per pair
     st::DBuf ptgt;    // u32 target per pair
+    st::DBuf pord;    // u32 order key per pair (tree tag, node of the entry)
     st::DBuf pcon;    // float contribution per pair
     long long npairs = 0;
 
     // memoised march: per chain link (virtual source, particle)
-    st::DBuf m_vid, m_j, m_st[2], m_ups, m_fr[2], m_table;
+    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr[2], m_table;
 
     // generic scratch
     st::DBuf tk[2], tv[2], hist, scan_tmp, stage, flags;
@@ -130,6 +131,7 @@ struct start_ctx {
     double hop_ms = -1.0;                    // summed memo hop kernels (timing = 1)
     unsigned long long memo_evals = 0, memo_links = 0;   // over the chunks of a solve
     long long chunks = 0;                    // target chunks of the last solve
+    int memo_final = 0;                      // buffer holding the final chain sums
     cudaEvent_t hev[2] = {};
 };
 

@@ -44,6 +44,11 @@ struct MemoArgs {
     u32 SN, NS, EN;                 // source-tree nodes, sources, emitter-tree nodes
     const uint4 *smeta, *emeta;     // (skip, first, count, leaf) of the two trees
     u32 *svid, *sj;                 // slot: virtual source id, particle
+    u32 *sord;                      // slot: order key of its virtual source
+    const u32 *pord;                // pair: order key (rows are sorted by it)
+    const u64 *off;                 // row offsets of the chunk's targets (minus base)
+    long long t0, t1;               // the chunk's targets
+    unsigned long long base;
     uint4 *state;                   // slot: (next slot, links to the end, tau hi, tau lo)
     u32 *ups;                       // frontier item: upstream particle of its hop
     unsigned long long *nslots;     // slots allocated so far
@@ -100,7 +105,7 @@ __device__ __forceinline__ unsigned long long link_key(u32 vid, u32 k)
     return ((unsigned long long)vid << 32) | k;
 }
 
-// 1. every pair is a slot and a table entry
+// 1. every pair is a slot (its links are found in the rows of the pairs)
 __global__ void k_memo_init(MemoArgs a)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,18 +118,7 @@ __global__ void k_memo_init(MemoArgs a)
     }
     a.svid[p] = vid;
     a.sj[p] = t;
-    unsigned long long key = link_key(vid, t);
-    unsigned long long h = mix64(key) & a.hmask;
-    for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
-        unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, key);
-        if (prev == kEmptyKey) {
-            a.table[h].val = (u32)p;
-            return;
-        }
-        if (prev == key) break;   // a duplicate pair: never expected
-        h = (h + 1) & a.hmask;
-    }
-    atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+    a.sord[p] = a.pord[p];
 }
 
 // Sums counters of a block and adds them once per block.
@@ -176,8 +170,39 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
     if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
 }
 
-// 2b. the upstream link of every frontier slot: found in the table, or
-// claimed as a new slot that joins the next frontier.
+// Pair slot of (vid, k) in the row of target k, or kNone.  Neighbouring
+// targets have nearly the same lists, so the pair usually sits at the same
+// offset as in the row it comes from (guess) or a few entries away; else a
+// binary search on the order key finds the run of entries of the same cell.
+__device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u32 key, u32 raw,
+                                           long long guess_pos)
+{
+    if ((long long)k < a.t0 || (long long)k >= a.t1) return kNone;   // row not in this chunk
+    u64 r0 = a.off[k] - a.base, r1 = a.off[k + 1] - a.base;
+    if (r1 <= r0) return kNone;
+    if (guess_pos >= 0) {
+        u64 g = r0 + (u64)guess_pos;
+        if (g >= r1) g = r1 - 1;
+        if (a.m.pent[g] == raw) return (u32)g;
+        for (u64 d = 1; d <= 8; ++d) {
+            if (g + d < r1 && a.m.pent[g + d] == raw) return (u32)(g + d);
+            if (g >= r0 + d && a.m.pent[g - d] == raw) return (u32)(g - d);
+        }
+    }
+    u64 lo = r0, hi = r1;
+    while (lo < hi) {
+        u64 mid = lo + ((hi - lo) >> 1);
+        if (a.pord[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    for (u64 e = lo; e < r1 && a.pord[e] == key; ++e)
+        if (canon(a, a.m.pent[e]) == vid) return (u32)e;
+    return kNone;
+}
+
+// 2b. the upstream link of every frontier slot: the pair (v, up) when it is
+// in the row of up, else a slot outside the lists, found in the table or
+// claimed (it joins the next frontier).
 __global__ void k_memo_link(MemoArgs a)
 {
     long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -186,39 +211,49 @@ __global__ void k_memo_link(MemoArgs a)
     if (up == kNone) return;              // chain end: next stays kNone
     u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
     u32 vid = a.svid[s];
-    unsigned long long key = link_key(vid, up);
-    unsigned long long h = mix64(key) & a.hmask;
-    u32 nx = kNone;
-    bool placed = false;
-    for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
-        unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
-        if (k == kEmptyKey) {
-            unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, key);
-            if (prev == kEmptyKey) {
-                unsigned long long ns = atomicAdd(a.nslots, 1ull);
-                if (ns >= a.cap) {
-                    atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
-                } else {
-                    a.svid[ns] = vid;
-                    a.sj[ns] = up;
-                    *(volatile unsigned int *)&a.table[h].val = (u32)ns;
-                    a.fr_out[atomicAdd(a.nf_out, 1ull)] = (u32)ns;
-                    nx = (u32)ns;
+    u32 key = a.sord[s];
+    long long gpos = -1;
+    u32 raw = 0;
+    if ((long long)s < a.m.npairs) {
+        raw = a.m.pent[s];
+        gpos = (long long)(s - (a.off[a.sj[s]] - a.base));
+    }
+    u32 nx = find_in_row(a, up, vid, key, raw, gpos);
+    if (nx == kNone) {
+        unsigned long long lk = link_key(vid, up);
+        unsigned long long h = mix64(lk) & a.hmask;
+        bool placed = false;
+        for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+            unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
+            if (k == kEmptyKey) {
+                unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
+                if (prev == kEmptyKey) {
+                    unsigned long long ns = atomicAdd(a.nslots, 1ull);
+                    if (ns >= a.cap) {
+                        atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
+                    } else {
+                        a.svid[ns] = vid;
+                        a.sj[ns] = up;
+                        a.sord[ns] = key;
+                        *(volatile unsigned int *)&a.table[h].val = (u32)ns;
+                        a.fr_out[atomicAdd(a.nf_out, 1ull)] = (u32)ns;
+                        nx = (u32)ns;
+                    }
+                    placed = true;
+                    break;
                 }
+                k = prev;
+            }
+            if (k == lk) {
+                u32 v = *(volatile unsigned int *)&a.table[h].val;
+                nx = (v != kNone) ? v : (kPending | (u32)h);
                 placed = true;
                 break;
             }
-            k = prev;
+            h = (h + 1) & a.hmask;
         }
-        if (k == key) {
-            u32 v = *(volatile unsigned int *)&a.table[h].val;
-            nx = (v != kNone) ? v : (kPending | (u32)h);
-            placed = true;
-            break;
-        }
-        h = (h + 1) & a.hmask;
+        if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
     }
-    if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
     a.state[s].x = nx;
 }
 
@@ -278,31 +313,56 @@ __global__ void k_memo_jump(long long n, const uint4 *st, uint4 *st2, unsigned *
     if (__any_sync(0xffffffffu, act) && (threadIdx.x & 31) == 0) *active = 1u;
 }
 
-// 4. contribution of every pair
-__global__ void __launch_bounds__(256) k_memo_contrib(MemoArgs a)
+// 4. Gamma of every target from its pairs' chain sums, one warp per target:
+// each lane evaluates L e^-tau / (4 pi r^2) for one pair of a 32-pair chunk,
+// the chunk is summed by a fixed butterfly and the chunks are accumulated in
+// list order with compensation -- a deterministic order, so a target's
+// Gamma does not depend on which other targets share its chains.
+__global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, long long t0,
+                                                     long long t1, u64 base, float conv,
+                                                     const u32 *porig, float *gam, float *gout)
 {
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    long long i = t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     unsigned long long hops = 0, ovf = 0, rays = 0;
     u32 maxh = 0;
-    if (p < a.m.npairs) {
-        uint4 st = a.state[p];
-        float tau = __uint_as_float(st.z) + __uint_as_float(st.w);
-        float4 src = vsource(a, a.svid[p]);
-        float4 pt = a.m.pq[a.sj[p]];
-        float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
-        float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
-        a.m.pcon[p] = src.w * expf(-tau) / (12.566370614359172f * r2);
-        u32 l = st.y & ~kStable;
-        hops = l;
-        maxh = l;
-        rays = 1;
-        if ((long long)l > a.m.hop_cap) ovf = 1;
+    if (i < t1) {
+        u64 e0 = off[i] - base, e1 = off[i + 1] - base;
+        float4 pt = a.m.pq[i];
+        float sum = 0.f, cmp = 0.f;
+        for (u64 e = e0; e < e1; e += 32) {
+            u64 p = e + lane;
+            float v = 0.f;
+            if (p < e1) {
+                uint4 st = a.state[p];
+                float tau = __uint_as_float(st.z) + __uint_as_float(st.w);
+                float4 src = vsource(a, a.svid[p]);
+                float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
+                float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
+                v = src.w * expf(-tau) / (12.566370614359172f * r2);
+                u32 l = st.y & ~kStable;
+                hops += l;
+                maxh = max(maxh, l);
+                rays += 1;
+                if ((long long)l > a.m.hop_cap) ovf += 1;
+            }
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            float yk = v - cmp;
+            float tk = sum + yk;
+            cmp = (tk - sum) - yk;
+            sum = tk;
+        }
+        if (lane == 0) {
+            float g = sum * conv;
+            gam[i] = g;
+            if (gout) gout[porig[i]] = g;
+        }
     }
     block_add(&a.m.counters[C_RAYS], rays);
     block_add(&a.m.counters[C_HOPS], hops);
     block_add(&a.m.counters[C_CHAIN_OVF], ovf);
     for (int o = 16; o; o >>= 1) maxh = max(maxh, __shfl_xor_sync(0xffffffffu, maxh, o));
-    if ((threadIdx.x & 31) == 0 && maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
+    if (lane == 0 && maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
 }
 
 template <int G>
@@ -323,13 +383,16 @@ static unsigned long long read_u64(start_ctx *c, const unsigned long long *d)
     return v;
 }
 
-static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &overflow)
+static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &overflow,
+                        long long t0, long long t1, u64 base)
 {
     cudaStream_t s = c->stream;
     overflow = false;
+    // the table holds only the links outside the lists
     size_t hsize = 1;
-    while (hsize < 2 * cap) hsize <<= 1;
-    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_st[0], cap * 16) ||
+    while (hsize < 2 * (cap - (size_t)m.npairs) + 1024) hsize <<= 1;
+    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_ord, cap * 4) ||
+        ensure(c->m_st[0], cap * 16) ||
         ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) || ensure(c->m_fr[0], cap * 4) ||
         ensure(c->m_fr[1], cap * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
@@ -347,6 +410,12 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.emeta = c->et.meta.as<uint4>();
     a.svid = c->m_vid.as<u32>();
     a.sj = c->m_j.as<u32>();
+    a.sord = c->m_ord.as<u32>();
+    a.pord = c->pord.as<u32>();
+    a.off = c->loff.as<u64>();
+    a.t0 = t0;
+    a.t1 = t1;
+    a.base = base;
     a.state = c->m_st[0].as<uint4>();
     a.ups = c->m_ups.as<u32>();
     a.nslots = ctr + C_SLOTS;
@@ -425,21 +494,37 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         ST_CUDA(c, cudaStreamSynchronize(s));
         if (!act) break;
     }
-    a.state = c->m_st[b].as<uint4>();
-    k_memo_contrib<<<grid_for(m.npairs, 256), 256, 0, s>>>(a);
-    ++c->launches;
-    return cuda_check(c, cudaGetLastError(), "k_memo_contrib");
+    c->memo_final = b;
+    return START_OK;
 }
 
-int run_memo(start_ctx *c, const MarchArgs &m)
+// Gamma of targets [t0, t1) from the chain sums of the last run_memo.
+int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base,
+               float conv, float *gout)
+{
+    MemoArgs a;
+    a.m = m;
+    a.SN = (u32)c->stree.n;
+    a.NS = (u32)c->ns;
+    a.EN = (u32)(c->diffuse ? c->et.n : 0);
+    a.svid = c->m_vid.as<u32>();
+    a.state = c->m_st[c->memo_final].as<uint4>();
+    long long threads = (t1 - t0) * 32;
+    k_memo_gamma<<<grid_for(threads, 256), 256, 0, c->stream>>>(
+        a, c->loff.as<u64>(), t0, t1, base, conv, c->porig.as<u32>(), c->gam.as<float>(), gout);
+    ++c->launches;
+    return cuda_check(c, cudaGetLastError(), "k_memo_gamma");
+}
+
+int run_memo(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base)
 {
     if (m.npairs == 0) return START_OK;
-    size_t cap = (size_t)m.npairs + (size_t)(m.npairs / 2) + (size_t)c->np + 4096;
+    size_t cap = (size_t)m.npairs + (size_t)(m.npairs / 4) + (size_t)c->np + 4096;
     for (int attempt = 0; attempt < 4; ++attempt) {
         // slot ids and table indices must stay below the pending flag (2^31)
         if (cap >= (1ull << 30)) return set_err(c, START_ERANGE, "too many chain links");
         bool overflow = false;
-        ST_TRY(memo_attempt(c, m, cap, overflow));
+        ST_TRY(memo_attempt(c, m, cap, overflow, t0, t1, base));
         if (!overflow) return START_OK;
         cap *= 2;
     }

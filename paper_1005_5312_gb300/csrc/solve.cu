@@ -20,7 +20,9 @@
 
 namespace st {
 
-int run_memo(start_ctx *c, const MarchArgs &m);
+int run_memo(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base);
+int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base,
+               float conv, float *gout);
 
 
 // ---------------------------------------------------------------- walk
@@ -31,10 +33,13 @@ struct TreeView {
     u32 n;
 };
 
+// Entries are emitted in depth-first order; the order key of an entry is
+// (tree tag, node id of the accepted cell or of the leaf holding the member),
+// so every target's row is sorted by it.
 template <bool FILL>
 __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2f, double th2d,
                                           float cmag, u32 self, u32 tag, u32 i, u32 &c, u64 &w,
-                                          u64 wend, u32 *ent, u32 *tgt, unsigned &fb)
+                                          u64 wend, u32 *ent, u32 *tgt, u32 *ord, unsigned &fb)
 {
     u32 n = 0;
     while (n < t.n) {
@@ -47,7 +52,11 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
         }
         if (a) {
             if (FILL) {
-                if (w < wend) { ent[w] = n | tag; tgt[w] = i; }   // never past this row
+                if (w < wend) {   // never past this row
+                    ent[w] = n | tag;
+                    tgt[w] = i;
+                    ord[w] = (tag ? 0x80000000u : 0u) | n;
+                }
                 ++w;
             } else {
                 ++c;
@@ -57,7 +66,11 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
             for (u32 r = mt.y; r < mt.y + mt.z; ++r) {
                 if (r == self) continue;
                 if (FILL) {
-                    if (w < wend) { ent[w] = kEntrySrc | tag | r; tgt[w] = i; }
+                    if (w < wend) {
+                        ent[w] = kEntrySrc | tag | r;
+                        tgt[w] = i;
+                        ord[w] = (tag ? 0x80000000u : 0u) | n;
+                    }
                     ++w;
                 } else {
                     ++c;
@@ -74,7 +87,8 @@ template <bool FILL>
 __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, long long t1,
                                               TreeView st_, TreeView et_, float th2f, double th2d,
                                               float cmag, u32 *cnt, const u64 *off, u64 base,
-                                              u32 *ent, u32 *tgt, unsigned long long *fb_total)
+                                              u32 *ent, u32 *tgt, u32 *ord,
+                                              unsigned long long *fb_total)
 {
     long long i = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned fb = 0;
@@ -83,9 +97,9 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
         u32 c = 0;
         u64 w = FILL ? off[i] - base : 0ull;
         const u64 wend = FILL ? off[i + 1] - base : 0ull;
-        walk_tree<FILL>(st_, p, th2f, th2d, cmag, kNone, 0u, (u32)i, c, w, wend, ent, tgt, fb);
+        walk_tree<FILL>(st_, p, th2f, th2d, cmag, kNone, 0u, (u32)i, c, w, wend, ent, tgt, ord, fb);
         walk_tree<FILL>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, (u32)i, c, w, wend, ent, tgt,
-                        fb);
+                        ord, fb);
         if (!FILL) cnt[i] = c;
         else if (w != wend) atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
     }
@@ -285,7 +299,7 @@ static int walk_count(start_ctx *c, float theta, const TreeView &sv, const TreeV
     k_walk<false><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), 0, np, sv, ev,
                                                     theta * theta, (double)theta * (double)theta,
                                                     c->fr.cmag, c->lcount.as<u32>(), nullptr, 0ull,
-                                                    nullptr, nullptr, ctr + C_WALK_FB);
+                                                    nullptr, nullptr, nullptr, ctr + C_WALK_FB);
     ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_TRY(exclusive_scan_u32_to_u64(c, c->lcount.as<u32>(), c->loff.as<u64>(), np));
@@ -303,7 +317,7 @@ static int walk_fill(start_ctx *c, float theta, const TreeView &sv, const TreeVi
     k_walk<true><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), t0, t1, sv, ev, theta * theta, (double)theta * (double)theta,
         c->fr.cmag, nullptr, c->loff.as<u64>(), base, c->pent.as<u32>(), c->ptgt.as<u32>(),
-        ctr + C_INTERNAL);
+        c->pord.as<u32>(), ctr + C_INTERNAL);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_walk");
 }
@@ -312,7 +326,7 @@ static int ensure_pairs(start_ctx *c, unsigned long long n)
 {
     size_t m = n ? n : 1;
     if (ensure(c->pent, m * sizeof(u32)) || ensure(c->ptgt, m * sizeof(u32)) ||
-        ensure(c->pcon, m * sizeof(float)))
+        ensure(c->pord, m * sizeof(u32)) || ensure(c->pcon, m * sizeof(float)))
         return set_err(c, START_ENOMEM, "out of device memory (interaction lists)");
     return START_OK;
 }
@@ -438,7 +452,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         if (n > 0) {
             phase_mark(c, START_PHASE_MARCH, false);
             if (c->p.march_mode == 1) {
-                ST_TRY(run_memo(c, a));
+                ST_TRY(run_memo(c, a, t0, t1, base));
             } else {
                 int nsm = 0;
                 cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
@@ -457,10 +471,14 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
             phase_mark(c, START_PHASE_MARCH, true);
         }
         phase_mark(c, START_PHASE_GAMMA, false);
-        k_gamma<<<grid_for(t1 - t0, 256), 256, 0, s>>>(c->pcon.as<float>(), c->loff.as<u64>(), t0,
-                                                       t1, base, conv, c->porig.as<u32>(),
-                                                       c->gam.as<float>(), gout_dev);
-        ++c->launches;
+        if (c->p.march_mode == 1 && n > 0) {
+            ST_TRY(memo_gamma(c, a, t0, t1, base, conv, gout_dev));
+        } else {
+            k_gamma<<<grid_for(t1 - t0, 256), 256, 0, s>>>(c->pcon.as<float>(), c->loff.as<u64>(),
+                                                           t0, t1, base, conv, c->porig.as<u32>(),
+                                                           c->gam.as<float>(), gout_dev);
+            ++c->launches;
+        }
         phase_mark(c, START_PHASE_GAMMA, true);
         ST_CUDA(c, cudaGetLastError());
     }
