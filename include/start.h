@@ -91,7 +91,17 @@ typedef struct start_params {
                               march, each chain followed from its target.
                               Same upstream choices; tau differs only in the
                               order of the additions */
-    int reserved1;
+    int reuse_chains;      /* 1: keep the chain links of a solve resident and,
+                              while the particles, sources and theta stay the
+                              same, solve later steps from them: only d_tau
+                              is recomputed from the current n_HI, the links
+                              are summed in chain order, and the step runs as
+                              one replayed CUDA graph.  The upstream choices
+                              depend on positions only, so the links are
+                              those a full solve would find.  Used with the
+                              memoised march, without diffuse emitters (whose
+                              centres move as x changes) and when the solve
+                              fits one target chunk; otherwise ignored */
     double sigma_cm2;      /* HI photoionisation cross-section (6.3e-18) */
     double len_unit_cm;    /* length unit of positions (kpc = 3.0857e21) */
     double L_unit;         /* internal luminosity scale, photons/s (1e48) */

@@ -33,7 +33,7 @@ START_ENTRY_EMITTER = 0x40000000
 
 class StartParams(C.Structure):
     _fields_ = [("src_leaf", C.c_int), ("ptree_leaf", C.c_int), ("march_group", C.c_int),
-                ("timing", C.c_int), ("march_mode", C.c_int), ("reserved1", C.c_int),
+                ("timing", C.c_int), ("march_mode", C.c_int), ("reuse_chains", C.c_int),
                 ("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
                 ("L_unit", C.c_double), ("alpha_A", C.c_double), ("alpha_B", C.c_double),
                 ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("max_pairs", C.c_longlong),

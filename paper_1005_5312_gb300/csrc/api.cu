@@ -307,11 +307,13 @@ static void csr_to_input(long long n, const std::vector<O> &moff, const std::vec
 
 static void release_all(start_ctx *c)
 {
+    resident_reset(c);
     DBuf *all[] = {&c->pq, &c->ph, &c->porig, &c->pinv, &c->pkey, &c->nH, &c->y, &c->V,
                    &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
                    &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,
                    &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
-                   &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord,
+                   &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord, &c->m_nx0, &c->m_dl,
+                   &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr[0], &c->m_fr[1], &c->m_table};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
@@ -420,6 +422,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
     if (!c) return START_EINVAL;
     DeviceGuard g(c);
     c->built = c->has_state = c->solved = false;
+    resident_reset(c);
     if (n_p < 0 || n_s < 0) return set_err(c, START_EINVAL, "negative size");
     if (n_p >= START_MAX_N || n_s >= START_MAX_N)
         return set_err(c, START_ERANGE, "n_p and n_s must be below 2^30");
@@ -549,7 +552,21 @@ int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_ou
     }
     bool dev_out = gamma_out && is_device_ptr(gamma_out);
     if (gamma_out && !dev_out) ST_TRY(ensure(c->stage, (n ? n : 1) * sizeof(float)));
-    ST_TRY(run_solve(c, theta, dev_out ? gamma_out : (gamma_out ? c->stage.as<float>() : nullptr)));
+    float *gdst = dev_out ? gamma_out : (gamma_out ? c->stage.as<float>() : nullptr);
+    if (c->p.reuse_chains && c->r_valid && c->r_theta == theta && !c->diffuse) {
+        phase_mark(c, START_PHASE_GAMMA, false);   // the whole step on resident chains
+        ST_TRY(resident_solve(c));
+        if (gdst && n) {
+            k_to_input_order<float><<<grid_for(n, 256), 256, 0, c->stream>>>(
+                c->gam.as<float>(), c->porig.as<u32>(), n, gdst);
+            ++c->launches;
+            ST_CUDA(c, cudaGetLastError());
+        }
+        phase_mark(c, START_PHASE_GAMMA, true);
+    } else {
+        ST_TRY(run_solve(c, theta, gdst));
+        if (resident_eligible(c)) ST_TRY(resident_build(c, theta));
+    }
     if (gamma_out && !dev_out) ST_TRY(copy_out(c, gamma_out, c->stage.p, n * sizeof(float)));
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency (interaction lists)");

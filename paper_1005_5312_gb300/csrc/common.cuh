@@ -117,7 +117,19 @@ struct start_ctx {
     long long npairs = 0;
 
     // memoised march: per chain link (virtual source, particle)
-    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr[2], m_table;
+    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr[2], m_table, m_nx0, m_dl;
+    long long memo_slots = 0;          // slots of the last memoised chunk
+
+    // resident chains (reuse_chains = 1): the link forest of the last full
+    // solve in chain-end-first level order, replayed as a CUDA graph
+    st::DBuf r_j, r_up, r_dl, r_next, r_tau, r_pos, r_lvl, r_vid;
+    std::vector<long long> r_lvl_off;  // first position of each depth level
+    bool r_valid = false;
+    float r_theta = -1.f;
+    long long r_slots = 0, r_pairs = 0;
+    unsigned long long r_rays = 0, r_hops = 0, r_maxh = 0;
+    cudaGraph_t r_graph = nullptr;
+    cudaGraphExec_t r_exec = nullptr;
 
     // generic scratch
     st::DBuf tk[2], tv[2], hist, scan_tmp, stage, flags;
@@ -192,6 +204,12 @@ void tree_release(Tree &t);
 
 // neighbors.cu
 int build_neighbours(start_ctx *c);
+
+// resident.cu
+void resident_reset(start_ctx *c);
+bool resident_eligible(const start_ctx *c);
+int resident_build(start_ctx *c, float theta);
+int resident_solve(start_ctx *c);
 
 // solve.cu
 int run_solve(start_ctx *c, float theta, float *gout_dev);

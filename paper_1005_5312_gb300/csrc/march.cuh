@@ -88,7 +88,8 @@ __device__ u32 upstream_64(const MarchArgs &a, float4 pj, float4 src, u32 s0, u3
 // group returns the same values; fbs counts FP64 re-decisions.
 template <int G>
 __device__ __forceinline__ u32 hop(const MarchArgs &a, u32 j, float4 pj, float4 src, int gl,
-                                   unsigned gmask, float &dt, unsigned long long &fbs)
+                                   unsigned gmask, float &dt, unsigned long long &fbs,
+                                   float *dl_out = nullptr)
 {
     const float two_eps = 32.f * kU32;   // 2 x the 16u|b| bound on each score
     const float eps_q = 16.f * kU32;
@@ -150,6 +151,7 @@ __device__ __forceinline__ u32 hop(const MarchArgs &a, u32 j, float4 pj, float4 
     }
     if (mk == kNone) {
         dt = a.sig * pj.w * bn;
+        if (dl_out) *dl_out = bn;
         return kNone;
     }
     float4 pu = a.pq[mk];
@@ -158,6 +160,7 @@ __device__ __forceinline__ u32 hop(const MarchArgs &a, u32 j, float4 pj, float4 
     float cn = sqrtf(cx * cx + cy * cy + cz * cz);
     float dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
     dt = a.sig * 0.5f * (pj.w + pu.w) * dl;
+    if (dl_out) *dl_out = dl;
     return mk;
 }
 

@@ -50,6 +50,8 @@ struct MemoArgs {
     long long t0, t1;               // the chunk's targets
     unsigned long long base;
     uint4 *state;                   // slot: (next slot, links to the end, tau hi, tau lo)
+    u32 *nx0;                       // slot: next slot before pointer jumping
+    float *dl;                      // slot: geometric length of its link
     u32 *ups;                       // frontier item: upstream particle of its hop
     unsigned long long *nslots;     // slots allocated so far
     const u32 *fr_in;               // frontier (NULL: slots [0, nf))
@@ -158,11 +160,13 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
         u32 j = a.sj[s];
         float4 src = vsource(a, vid);
         float4 pj = a.m.pq[j];
-        float dt;
-        u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs);
+        float dt, dl;
+        u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs, &dl);
         if (gl == 0) {
             a.ups[it] = up;
             a.state[s] = make_uint4(kNone, 1u, __float_as_uint(dt), 0u);
+            a.dl[s] = dl;
+            if (up == kNone) a.nx0[s] = kNone;
         }
     }
     if (gl != 0) fbs = 0;
@@ -255,6 +259,7 @@ __global__ void k_memo_link(MemoArgs a)
         if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
     }
     a.state[s].x = nx;
+    a.nx0[s] = nx;
 }
 
 // Links claimed by another thread during the same launch: read the slot the
@@ -269,6 +274,7 @@ __global__ void k_memo_resolve(MemoArgs a)
         u32 v = a.table[nx & ~kPending].val;
         if (v == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
         a.state[s].x = v;
+        a.nx0[s] = v;
     }
 }
 
@@ -392,7 +398,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     size_t hsize = 1;
     while (hsize < 2 * (cap - (size_t)m.npairs) + 1024) hsize <<= 1;
     if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_ord, cap * 4) ||
-        ensure(c->m_st[0], cap * 16) ||
+        ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
         ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) || ensure(c->m_fr[0], cap * 4) ||
         ensure(c->m_fr[1], cap * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
@@ -417,6 +423,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.t1 = t1;
     a.base = base;
     a.state = c->m_st[0].as<uint4>();
+    a.nx0 = c->m_nx0.as<u32>();
+    a.dl = c->m_dl.as<float>();
     a.ups = c->m_ups.as<u32>();
     a.nslots = ctr + C_SLOTS;
     a.cap = (u32)cap;
@@ -477,6 +485,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     }
     if (timing) c->hop_ms += hop_ms;
     long long nslots = (long long)read_u64(c, ctr + C_SLOTS);
+    c->memo_slots = nslots;
     c->memo_evals += (unsigned long long)nslots;
     c->memo_links += (unsigned long long)nslots;
     // pointer jumping

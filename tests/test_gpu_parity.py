@@ -206,6 +206,50 @@ def test_target_chunks_are_result_neutral(S, cfg1, mode):
     assert np.array_equal(out[0][0], out[1][0])
 
 
+def test_resident_chains_reproduce_full_solves(S, cfg1):
+    """With static particles the links are reused: a resident step gives the
+    Gamma of a full solve (same rays and links; tau summed in chain order)."""
+    rng = np.random.default_rng(6)
+    full = S.Context()
+    full.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    res = S.Context(reuse_chains=1)
+    res.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    for step in range(3):
+        nHI = (cfg1.n_H * rng.uniform(0.0, 1.0, cfg1.n_p)).astype(np.float32)
+        a = np.zeros(cfg1.n_p, np.float32)
+        b = np.zeros(cfg1.n_p, np.float32)
+        full.rt_solve(0.5, n_HI=nHI, gamma_out=a)
+        res.rt_solve(0.5, n_HI=nHI, gamma_out=b)
+        sf, sr = full.stats(), res.stats()
+        assert sf["rays"] == sr["rays"] and sf["hops"] == sr["hops"]
+        if step > 0:
+            assert sr["evals"] == 0          # no neighbour list evaluated
+        assert np.all(np.abs(b.astype(np.float64) - a) <= 2e-5 * np.abs(a) + G_ABS), step
+    # a different theta, then new geometry: full solves again, still right
+    g = np.zeros(cfg1.n_p, np.float32)
+    res.rt_solve(1.0, n_HI=cfg1.n_HI(), gamma_out=g)
+    assert res.stats()["evals"] > 0
+    w2 = lattice_workload("other", 16, 3.0, 5, 31)
+    res.build_trees(w2.pos, w2.h, w2.src_pos, w2.src_L)
+    orc = oracle.Oracle.from_workload(w2, ptree_leaf=PTREE_LEAF)
+    for _ in range(2):
+        g2 = np.zeros(w2.n_p, np.float32)
+        res.rt_solve(0.5, n_HI=w2.n_HI(), gamma_out=g2)
+        gamma_close(g2, orc.gamma(w2.n_HI(), 0.5))
+
+
+def test_resident_coupled_steps_match_oracle(S, cfg1):
+    ctx, orc = make_pair(S, cfg1, reuse_chains=1)
+    ctx.set_state(cfg1.n_H, cfg1.y0)
+    y_ref = cfg1.y0.copy()
+    y_gpu = np.zeros(cfg1.n_p)
+    for step in range(5):
+        ctx.rt_solve(0.5)
+        ctx.ionize(DT, y_out=y_gpu)
+        _, y_ref = orc.step(y_ref, cfg1.n_H, 0.5, DT)
+        assert np.max(np.abs(y_gpu - y_ref)) <= X_ABS, step
+
+
 def test_single_source_theta_independent_on_gpu(S):
     w = lattice_workload("one", 12, 2.0, 1, 5)
     ctx = S.Context()
