@@ -308,6 +308,8 @@ static void csr_to_input(long long n, const std::vector<O> &moff, const std::vec
 static void release_all(start_ctx *c)
 {
     resident_reset(c);
+    if (c->r_cap) cudaStreamDestroy(c->r_cap);
+    c->r_cap = nullptr;
     DBuf *all[] = {&c->pq, &c->ph, &c->porig, &c->pinv, &c->pkey, &c->nH, &c->y, &c->V,
                    &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
                    &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,

@@ -130,6 +130,7 @@ struct start_ctx {
     unsigned long long r_rays = 0, r_hops = 0, r_maxh = 0;
     cudaGraph_t r_graph = nullptr;
     cudaGraphExec_t r_exec = nullptr;
+    cudaStream_t r_cap = nullptr;      // private stream the graph is captured on
 
     // generic scratch
     st::DBuf tk[2], tv[2], hist, scan_tmp, stage, flags;

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256) k_res_gamma(long long np, const u64 *off,
 
 void resident_reset(start_ctx *c)
 {
+    if (c->r_exec || c->r_graph) cudaStreamSynchronize(c->stream);
     if (c->r_exec) cudaGraphExecDestroy(c->r_exec);
     if (c->r_graph) cudaGraphDestroy(c->r_graph);
     c->r_exec = nullptr;
@@ -196,9 +197,8 @@ int resident_build(start_ctx *c, float theta)
     return START_OK;
 }
 
-static void resident_launches(start_ctx *c)
+static void resident_launches(start_ctx *c, cudaStream_t s)
 {
-    cudaStream_t s = c->stream;
     long long S = c->r_slots;
     float sig = (float)(c->p.sigma_cm2 * c->p.len_unit_cm);
     float2 *tau = c->r_tau.as<float2>();
@@ -223,10 +223,13 @@ int resident_solve(start_ctx *c)
 {
     cudaStream_t s = c->stream;
     if (!c->r_exec) {
+        // captured on a private stream (the legacy default stream cannot be
+        // captured), replayed on the context's stream
+        if (!c->r_cap) ST_CUDA(c, cudaStreamCreateWithFlags(&c->r_cap, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
-        ST_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        resident_launches(c);
-        cudaError_t e = cudaStreamEndCapture(s, &g);
+        ST_CUDA(c, cudaStreamBeginCapture(c->r_cap, cudaStreamCaptureModeThreadLocal));
+        resident_launches(c, c->r_cap);
+        cudaError_t e = cudaStreamEndCapture(c->r_cap, &g);
         if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
         ST_CUDA(c, cudaGraphInstantiate(&c->r_exec, g, 0));
         c->r_graph = g;
