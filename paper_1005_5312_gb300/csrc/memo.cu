@@ -174,32 +174,34 @@ __device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u3
 struct QueueCtl {
     unsigned long long ihead;     // next interaction pair to claim
     unsigned long long qhead;     // next queue index to claim
-    unsigned long long qtail;     // queue entries allocated
-    unsigned long long pending;   // items created and not yet finished
+    unsigned long long qtail;     // queue indices reserved (slot = npairs + index)
+    unsigned long long pending;   // work not yet accounted as finished
     unsigned long long timeout;   // waits that hit the iteration cap
 };
 
-constexpr int kClaim = 8;         // queue items claimed per group at a time
-constexpr int kClaimPairs = 64;   // interaction pairs claimed per group at a time
+constexpr int kClaimPairs = 128;  // interaction pairs claimed per group at a time
+constexpr int kClaim = 16;        // queue entries claimed per group at a time
+constexpr int kReserve = 32;      // queue indices (= new slots) reserved at a time
+constexpr unsigned long long kSkip = ~1ull;   // reserved queue entry left unused
 
 // Hop + link of one slot (every lane of the group enters; lane 0 links).
-// Returns the slot it created (or kNone).
+// A link outside the lists is claimed in the table with the next reserved
+// slot id *ns_next* (consumed only when the claim succeeds); returns true
+// when it was.
 template <int G>
-__device__ __forceinline__ u32 process_slot(const MemoArgs &a, u32 s, int gl, unsigned gmask,
-                                            unsigned long long &fbs)
+__device__ __forceinline__ bool process_slot(const MemoArgs &a, u32 s, u32 vid, u32 j, u32 key,
+                                             u32 ns_next, int gl, unsigned gmask,
+                                             unsigned long long &fbs)
 {
-    u32 vid = a.svid[s];
-    u32 j = a.sj[s];
     float4 src = vsource(a, vid);
     float4 pj = a.m.pq[j];
     float dt, dl;
     u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs, &dl);
-    u32 created = kNone;
+    bool created = false;
     if (gl == 0) {
         a.dl[s] = dl;
         u32 nx = kNone;
         if (up != kNone) {
-            u32 key = a.sord[s];
             long long gpos = -1;
             u32 raw = 0;
             if ((long long)s < a.m.npairs) {
@@ -216,17 +218,16 @@ __device__ __forceinline__ u32 process_slot(const MemoArgs &a, u32 s, int gl, un
                     if (k == kEmptyKey) {
                         unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
                         if (prev == kEmptyKey) {
-                            unsigned long long ns = atomicAdd(a.nslots, 1ull);
-                            if (ns >= a.cap) {
-                                atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
-                            } else {
-                                a.svid[ns] = vid;
-                                a.sj[ns] = up;
-                                a.sord[ns] = key;
-                                *(volatile unsigned int *)&a.table[h].val = (u32)ns;
-                                nx = (u32)ns;
-                                created = (u32)ns;
+                            // ns_next = kNone: out of capacity; the caller
+                            // reports it and the host retries larger
+                            if (ns_next != kNone) {
+                                a.svid[ns_next] = vid;
+                                a.sj[ns_next] = up;
+                                a.sord[ns_next] = key;
+                                *(volatile unsigned int *)&a.table[h].val = ns_next;
                             }
+                            nx = ns_next;
+                            created = true;
                             placed = true;
                             break;
                         }
@@ -252,11 +253,16 @@ __device__ __forceinline__ u32 process_slot(const MemoArgs &a, u32 s, int gl, un
 // 2. The whole frontier in one launch.  Groups claim the interaction pairs
 // (kClaimPairs at a time) and then the links outside the lists that the
 // processing publishes to the queue, in creation order (kClaim at a time).
-// Only running groups ever hold claimed work, and an entry is published by
-// whoever creates it while processing an earlier item, so a group waiting
-// for an entry always waits on running work.  It stops when no item is
-// pending (nothing can be published any more) or when its wait exceeds
-// spin_cap iterations (the timeout counter tells the host).
+// A new link's slot is npairs + its queue index; indices are reserved
+// kReserve at a time and unused reserved ones are published as kSkip (with a
+// benign slot) before the group waits, so no waiter stalls on a hole.
+// Finished and created counts are kept per group and added to `pending`
+// before any wait: `pending` then never undercounts the work left, and it
+// reaches 0 only when all work is done and every group has flushed.  Only
+// running groups hold claimed work, and an entry is published by whoever
+// creates it while processing an earlier item, so a waiting group always
+// waits on running work.  A wait gives up after spin_cap iterations (the
+// timeout counter tells the host).
 template <int G>
 __global__ void __launch_bounds__(256) k_memo_persist(MemoArgs a, QueueCtl *qc,
                                                       unsigned long long *q,
@@ -266,19 +272,58 @@ __global__ void __launch_bounds__(256) k_memo_persist(MemoArgs a, QueueCtl *qc,
     const int gl = lane % G;
     const int gbase = lane - gl;
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const unsigned long long npairs = (unsigned long long)a.m.npairs;
     unsigned long long fbs = 0;
+    // leader-local accounting
+    long long made = 0, done = 0;
+    unsigned long long rn = 0, re = 0;   // reserved queue indices [rn, re)
 
-    auto finish = [&](u32 created) {
-        if (gl == 0) {
-            if (created != kNone) {
-                atomicAdd(&qc->pending, 1ull);
-                unsigned long long t = atomicAdd(&qc->qtail, 1ull);
-                __threadfence();
-                if (t < qcap) atomicExch(&q[t], (unsigned long long)created);
-                else atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
-            }
+    auto next_index = [&]() -> unsigned long long {   // leader only
+        if (rn == re) {
+            rn = atomicAdd(&qc->qtail, (unsigned long long)kReserve);
+            re = rn + kReserve;
+        }
+        return rn;
+    };
+    auto flush = [&]() {   // leader only
+        for (; rn < re; ++rn) {
+            if (rn >= qcap) continue;
+            u32 hs = (u32)(npairs + rn);
+            a.svid[hs] = 0u;
+            a.sj[hs] = 0u;
+            a.sord[hs] = 0u;
+            a.dl[hs] = 0.f;
+            a.nx0[hs] = kNone;
+            a.state[hs] = make_uint4(kNone, 1u, 0u, 0u);
             __threadfence();
-            atomicAdd(&qc->pending, ~0ull);   // this item is done
+            atomicExch(&q[rn], kSkip);
+        }
+        long long d = made - done;
+        if (d) atomicAdd(&qc->pending, (unsigned long long)d);
+        made = done = 0;
+    };
+    // one item: process, publish what it created, count it
+    auto run_item = [&](u32 s, u32 vid, u32 j, u32 key) {
+        unsigned long long t = 0;
+        u32 ns = kNone;
+        if (gl == 0) {
+            t = next_index();
+            ns = t < qcap ? (u32)(npairs + t) : kNone;
+        }
+        ns = __shfl_sync(gmask, ns, 0, G);
+        bool created = process_slot<G>(a, s, vid, j, key, ns, gl, gmask, fbs);
+        if (gl == 0) {
+            if (created) {
+                if (ns == kNone) {
+                    atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
+                } else {
+                    __threadfence();
+                    atomicExch(&q[t], (unsigned long long)ns);
+                    ++rn;
+                    ++made;
+                }
+            }
+            ++done;
         }
     };
 
@@ -286,11 +331,10 @@ __global__ void __launch_bounds__(256) k_memo_persist(MemoArgs a, QueueCtl *qc,
         unsigned long long b0 = 0;
         if (gl == 0) b0 = atomicAdd(&qc->ihead, (unsigned long long)kClaimPairs);
         b0 = __shfl_sync(gmask, b0, 0, G);
-        if (b0 >= (unsigned long long)a.m.npairs) break;
-        unsigned long long b1 = b0 + kClaimPairs;
-        if (b1 > (unsigned long long)a.m.npairs) b1 = (unsigned long long)a.m.npairs;
+        if (b0 >= npairs) break;
+        unsigned long long b1 = b0 + kClaimPairs < npairs ? b0 + kClaimPairs : npairs;
         for (unsigned long long it = b0; it < b1; ++it)
-            finish(process_slot<G>(a, (u32)it, gl, gmask, fbs));
+            run_item((u32)it, a.svid[it], a.sj[it], a.sord[it]);
     }
 
     bool quit = false;
@@ -300,38 +344,56 @@ __global__ void __launch_bounds__(256) k_memo_persist(MemoArgs a, QueueCtl *qc,
         b0 = __shfl_sync(gmask, b0, 0, G);
         for (int k = 0; k < kClaim && !quit; ++k) {
             unsigned long long qi = b0 + k;
-            u32 s = kNone;
-            int stop = 0;
+            u32 s = kNone, vid = 0, j = 0, key = 0;
+            int stop = 0, skip = 0;
             if (gl == 0) {
-                for (long long w = 0;; ++w) {
-                    unsigned long long e =
-                        qi < qcap ? *(volatile unsigned long long *)&q[qi] : ~0ull;
-                    if (e != kEmptyKey) {
-                        s = (u32)e;
-                        break;
+                unsigned long long e =
+                    qi < qcap ? *(volatile unsigned long long *)&q[qi] : ~0ull;
+                if (e == kEmptyKey) {
+                    flush();   // account for our work before waiting on others
+                    for (long long w = 0;; ++w) {
+                        e = qi < qcap ? *(volatile unsigned long long *)&q[qi] : ~0ull;
+                        if (e != kEmptyKey) break;
+                        if (*(volatile unsigned long long *)&qc->pending == 0ull) {
+                            stop = 1;
+                            break;
+                        }
+                        if (w > spin_cap) {
+                            atomicAdd(&qc->timeout, 1ull);
+                            stop = 1;
+                            break;
+                        }
+                        __nanosleep(64);
                     }
-                    if (*(volatile unsigned long long *)&qc->pending == 0ull) {
-                        stop = 1;
-                        break;
-                    }
-                    if (w > spin_cap) {
-                        atomicAdd(&qc->timeout, 1ull);
-                        stop = 1;
-                        break;
-                    }
-                    __nanosleep(64);
                 }
                 __threadfence();
+                if (!stop) {
+                    if (e == kSkip) {
+                        skip = 1;
+                    } else {
+                        s = (u32)e;
+                        // written by another group in this launch: read past L1
+                        vid = __ldcg(a.svid + s);
+                        j = __ldcg(a.sj + s);
+                        key = __ldcg(a.sord + s);
+                    }
+                }
             }
             stop = __shfl_sync(gmask, stop, 0, G);
-            s = __shfl_sync(gmask, s, 0, G);
+            skip = __shfl_sync(gmask, skip, 0, G);
             if (stop) {
                 quit = true;
                 break;
             }
-            finish(process_slot<G>(a, s, gl, gmask, fbs));
+            if (skip) continue;
+            s = __shfl_sync(gmask, s, 0, G);
+            vid = __shfl_sync(gmask, vid, 0, G);
+            j = __shfl_sync(gmask, j, 0, G);
+            key = __shfl_sync(gmask, key, 0, G);
+            run_item(s, vid, j, key);
         }
     }
+    if (gl == 0) flush();
     if (gl != 0) fbs = 0;
     for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
     if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
@@ -530,10 +592,9 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     QueueCtl qh;
-    unsigned long long ovf = 0, nsl = 0;
+    unsigned long long ovf = 0;
     ST_CUDA(c, cudaMemcpyAsync(&qh, qc, sizeof(qh), cudaMemcpyDeviceToHost, s));
     ST_CUDA(c, cudaMemcpyAsync(&ovf, ctr + C_MEMO_OVF, sizeof(ovf), cudaMemcpyDeviceToHost, s));
-    ST_CUDA(c, cudaMemcpyAsync(&nsl, ctr + C_SLOTS, sizeof(nsl), cudaMemcpyDeviceToHost, s));
     ST_CUDA(c, cudaStreamSynchronize(s));
     if (timing) {
         float ms = 0.f;
@@ -545,8 +606,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         overflow = true;
         return START_OK;
     }
-    long long nslots = (long long)nsl;
-    if (nslots > (long long)cap) nslots = (long long)cap;
+    unsigned long long used = qh.qtail < (unsigned long long)qcap ? qh.qtail : (unsigned long long)qcap;
+    long long nslots = m.npairs + (long long)used;
     k_memo_resolve_all<<<grid_for(nslots, 256), 256, 0, s>>>(a, nslots);
     ++c->launches;
     ST_CUDA(c, cudaGetLastError());

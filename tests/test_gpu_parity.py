@@ -413,6 +413,23 @@ def test_hop_cap_reports_echain(S, cfg1, mode):
     assert e.value.code == S.START_ECHAIN
 
 
+def test_queue_wait_limit_reports_etimeout_and_context_survives(S, cfg1):
+    """A persistent-kernel wait that runs out (spin_cap = 1 iteration) ends
+    the launch with START_ETIMEOUT instead of hanging; the context and the
+    device stay usable (a solve with no queued work then succeeds)."""
+    ctx = S.Context(spin_cap=1)
+    ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+    with pytest.raises(S.StartError) as e:
+        ctx.rt_solve(0.5, n_HI=cfg1.n_HI(), gamma_out=np.zeros(cfg1.n_p, np.float32))
+    assert e.value.code == S.START_ETIMEOUT
+    assert ctx.stats()["nodes_src"] > 0
+    g = np.zeros(cfg1.n_p, np.float32)
+    ctx.rt_solve(0.0, n_HI=cfg1.n_HI(), gamma_out=g)      # theta = 0: every link in a list
+    orc = oracle.Oracle.from_workload(cfg1, ptree_leaf=PTREE_LEAF)
+    idx = np.arange(0, cfg1.n_p, 257)
+    gamma_close(g[idx], orc.gamma(cfg1.n_HI(), 0.0, targets=idx))
+
+
 # ------------------------------------------------------------------ full size, sampled
 def test_config2_full_size_sampled_targets(S):
     """64^3 particles and 1024 sources at theta = 0.5 in the launch
