@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(256) k_memo_persist(MemoArgs a, QueueCtl *qc,
         }
         long long d = made - done;
         if (d) atomicAdd(&qc->pending, (unsigned long long)d);
+        if (made) atomicAdd(a.nslots, (unsigned long long)made);   // links evaluated
         made = done = 0;
     };
     // one item: process, publish what it created, count it
@@ -611,6 +612,14 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     k_memo_resolve_all<<<grid_for(nslots, 256), 256, 0, s>>>(a, nslots);
     ++c->launches;
     ST_CUDA(c, cudaGetLastError());
+    // slots = pairs + reserved queue indices (unused ones hold benign links);
+    // evaluations = pairs + links created
+    unsigned long long evaluated = 0;
+    ST_CUDA(c, cudaMemcpyAsync(&evaluated, ctr + C_SLOTS, sizeof(evaluated), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(c, cudaStreamSynchronize(s));
+    c->memo_slots = nslots;
+    c->memo_evals += evaluated;
+    c->memo_links += evaluated;
     // pointer jumping
     int b = 0;
     unsigned *active = c->flags.as<unsigned>() + 12;
