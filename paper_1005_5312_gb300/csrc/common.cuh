@@ -117,7 +117,7 @@ struct start_ctx {
     long long npairs = 0;
 
     // memoised march: per chain link (virtual source, particle)
-    st::DBuf m_vid, m_j, m_ord, m_st[2], m_q, m_qc, m_table, m_nx0, m_dl;
+    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr[2], m_table, m_nx0, m_dl;
     long long memo_slots = 0;          // slots of the last memoised chunk
 
     // resident chains (reuse_chains = 1): the link forest of the last full

@@ -140,6 +140,40 @@ __device__ __forceinline__ void block_add(unsigned long long *ctr, unsigned long
     }
 }
 
+// 2a. one hop for every frontier slot, G lanes per slot.  Only the gathers
+// of the neighbour search touch memory here (particle records and lists,
+// L2-resident); the table lookups run in k_memo_link so that their random
+// traffic does not evict that working set.
+template <int G>
+__global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const int gbase = lane - gl;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const long long ngroups = ((long long)gridDim.x * blockDim.x) / G;
+    unsigned long long fbs = 0;
+    for (long long it = gid; it < a.nf; it += ngroups) {
+        u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
+        u32 vid = a.svid[s];
+        u32 j = a.sj[s];
+        float4 src = vsource(a, vid);
+        float4 pj = a.m.pq[j];
+        float dt, dl;
+        u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs, &dl);
+        if (gl == 0) {
+            a.ups[it] = up;
+            a.state[s] = make_uint4(kNone, 1u, __float_as_uint(dt), 0u);
+            a.dl[s] = dl;
+            if (up == kNone) a.nx0[s] = kNone;
+        }
+    }
+    if (gl != 0) fbs = 0;
+    for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
+    if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
+}
+
 // Pair slot of (vid, k) in the row of target k, or kNone.  Neighbouring
 // targets have nearly the same lists, so the pair usually sits at the same
 // offset as in the row it comes from (guess) or a few entries away; else a
@@ -170,242 +204,71 @@ __device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u3
     return kNone;
 }
 
-// Work-queue control of the persistent frontier kernel.
-struct QueueCtl {
-    unsigned long long ihead;     // next interaction pair to claim
-    unsigned long long qhead;     // next queue index to claim
-    unsigned long long qtail;     // queue indices reserved (slot = npairs + index)
-    unsigned long long pending;   // work not yet accounted as finished
-    unsigned long long timeout;   // waits that hit the iteration cap
-};
-
-constexpr int kClaimPairs = 128;  // interaction pairs claimed per group at a time
-constexpr int kClaim = 16;        // queue entries claimed per group at a time
-constexpr int kReserve = 32;      // queue indices (= new slots) reserved at a time
-constexpr unsigned long long kSkip = ~1ull;   // reserved queue entry left unused
-
-// Hop + link of one slot (every lane of the group enters; lane 0 links).
-// A link outside the lists is claimed in the table with the next reserved
-// slot id *ns_next* (consumed only when the claim succeeds); returns true
-// when it was.
-template <int G>
-__device__ __forceinline__ bool process_slot(const MemoArgs &a, u32 s, u32 vid, u32 j, u32 key,
-                                             u32 ns_next, int gl, unsigned gmask,
-                                             unsigned long long &fbs)
+// 2b. the upstream link of every frontier slot: the pair (v, up) when it is
+// in the row of up, else a slot outside the lists, found in the table or
+// claimed (it joins the next frontier).
+__global__ void k_memo_link(MemoArgs a)
 {
-    float4 src = vsource(a, vid);
-    float4 pj = a.m.pq[j];
-    float dt, dl;
-    u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs, &dl);
-    bool created = false;
-    if (gl == 0) {
-        a.dl[s] = dl;
-        u32 nx = kNone;
-        if (up != kNone) {
-            long long gpos = -1;
-            u32 raw = 0;
-            if ((long long)s < a.m.npairs) {
-                raw = a.m.pent[s];
-                gpos = (long long)(s - (a.off[j] - a.base));
-            }
-            nx = find_in_row(a, up, vid, key, raw, gpos);
-            if (nx == kNone) {
-                unsigned long long lk = link_key(vid, up);
-                unsigned long long h = mix64(lk) & a.hmask;
-                bool placed = false;
-                for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
-                    unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
-                    if (k == kEmptyKey) {
-                        unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
-                        if (prev == kEmptyKey) {
-                            // ns_next = kNone: out of capacity; the caller
-                            // reports it and the host retries larger
-                            if (ns_next != kNone) {
-                                a.svid[ns_next] = vid;
-                                a.sj[ns_next] = up;
-                                a.sord[ns_next] = key;
-                                *(volatile unsigned int *)&a.table[h].val = ns_next;
-                            }
-                            nx = ns_next;
-                            created = true;
-                            placed = true;
-                            break;
-                        }
-                        k = prev;
-                    }
-                    if (k == lk) {
-                        u32 v = *(volatile unsigned int *)&a.table[h].val;
-                        nx = (v != kNone) ? v : (kPending | (u32)h);
-                        placed = true;
-                        break;
-                    }
-                    h = (h + 1) & a.hmask;
-                }
-                if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
-            }
-        }
-        a.state[s] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
-        a.nx0[s] = nx;
+    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= a.nf) return;
+    u32 up = a.ups[it];
+    if (up == kNone) return;              // chain end: next stays kNone
+    u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
+    u32 vid = a.svid[s];
+    u32 key = a.sord[s];
+    long long gpos = -1;
+    u32 raw = 0;
+    if ((long long)s < a.m.npairs) {
+        raw = a.m.pent[s];
+        gpos = (long long)(s - (a.off[a.sj[s]] - a.base));
     }
-    return created;
-}
-
-// 2. The whole frontier in one launch.  Groups claim the interaction pairs
-// (kClaimPairs at a time) and then the links outside the lists that the
-// processing publishes to the queue, in creation order (kClaim at a time).
-// A new link's slot is npairs + its queue index; indices are reserved
-// kReserve at a time and unused reserved ones are published as kSkip (with a
-// benign slot) before the group waits, so no waiter stalls on a hole.
-// Finished and created counts are kept per group and added to `pending`
-// before any wait: `pending` then never undercounts the work left, and it
-// reaches 0 only when all work is done and every group has flushed.  Only
-// running groups hold claimed work, and an entry is published by whoever
-// creates it while processing an earlier item, so a waiting group always
-// waits on running work.  A wait gives up after spin_cap iterations (the
-// timeout counter tells the host).
-template <int G>
-__global__ void __launch_bounds__(256) k_memo_persist(MemoArgs a, QueueCtl *qc,
-                                                      unsigned long long *q,
-                                                      unsigned long long qcap, long long spin_cap)
-{
-    const int lane = threadIdx.x & 31;
-    const int gl = lane % G;
-    const int gbase = lane - gl;
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
-    const unsigned long long npairs = (unsigned long long)a.m.npairs;
-    unsigned long long fbs = 0;
-    // leader-local accounting
-    long long made = 0, done = 0;
-    unsigned long long rn = 0, re = 0;   // reserved queue indices [rn, re)
-
-    auto next_index = [&]() -> unsigned long long {   // leader only
-        if (rn == re) {
-            rn = atomicAdd(&qc->qtail, (unsigned long long)kReserve);
-            re = rn + kReserve;
-        }
-        return rn;
-    };
-    auto flush = [&]() {   // leader only
-        for (; rn < re; ++rn) {
-            if (rn >= qcap) continue;
-            u32 hs = (u32)(npairs + rn);
-            a.svid[hs] = 0u;
-            a.sj[hs] = 0u;
-            a.sord[hs] = 0u;
-            a.dl[hs] = 0.f;
-            a.nx0[hs] = kNone;
-            a.state[hs] = make_uint4(kNone, 1u, 0u, 0u);
-            __threadfence();
-            atomicExch(&q[rn], kSkip);
-        }
-        long long d = made - done;
-        if (d) atomicAdd(&qc->pending, (unsigned long long)d);
-        if (made) atomicAdd(a.nslots, (unsigned long long)made);   // links evaluated
-        made = done = 0;
-    };
-    // one item: process, publish what it created, count it
-    auto run_item = [&](u32 s, u32 vid, u32 j, u32 key) {
-        unsigned long long t = 0;
-        u32 ns = kNone;
-        if (gl == 0) {
-            t = next_index();
-            ns = t < qcap ? (u32)(npairs + t) : kNone;
-        }
-        ns = __shfl_sync(gmask, ns, 0, G);
-        bool created = process_slot<G>(a, s, vid, j, key, ns, gl, gmask, fbs);
-        if (gl == 0) {
-            if (created) {
-                if (ns == kNone) {
-                    atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
-                } else {
-                    __threadfence();
-                    atomicExch(&q[t], (unsigned long long)ns);
-                    ++rn;
-                    ++made;
-                }
-            }
-            ++done;
-        }
-    };
-
-    for (;;) {
-        unsigned long long b0 = 0;
-        if (gl == 0) b0 = atomicAdd(&qc->ihead, (unsigned long long)kClaimPairs);
-        b0 = __shfl_sync(gmask, b0, 0, G);
-        if (b0 >= npairs) break;
-        unsigned long long b1 = b0 + kClaimPairs < npairs ? b0 + kClaimPairs : npairs;
-        for (unsigned long long it = b0; it < b1; ++it)
-            run_item((u32)it, a.svid[it], a.sj[it], a.sord[it]);
-    }
-
-    bool quit = false;
-    while (!quit) {
-        unsigned long long b0 = 0;
-        if (gl == 0) b0 = atomicAdd(&qc->qhead, (unsigned long long)kClaim);
-        b0 = __shfl_sync(gmask, b0, 0, G);
-        for (int k = 0; k < kClaim && !quit; ++k) {
-            unsigned long long qi = b0 + k;
-            u32 s = kNone, vid = 0, j = 0, key = 0;
-            int stop = 0, skip = 0;
-            if (gl == 0) {
-                unsigned long long e =
-                    qi < qcap ? *(volatile unsigned long long *)&q[qi] : ~0ull;
-                if (e == kEmptyKey) {
-                    flush();   // account for our work before waiting on others
-                    for (long long w = 0;; ++w) {
-                        e = qi < qcap ? *(volatile unsigned long long *)&q[qi] : ~0ull;
-                        if (e != kEmptyKey) break;
-                        if (*(volatile unsigned long long *)&qc->pending == 0ull) {
-                            stop = 1;
-                            break;
-                        }
-                        if (w > spin_cap) {
-                            atomicAdd(&qc->timeout, 1ull);
-                            stop = 1;
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
-                }
-                __threadfence();
-                if (!stop) {
-                    if (e == kSkip) {
-                        skip = 1;
+    u32 nx = find_in_row(a, up, vid, key, raw, gpos);
+    if (nx == kNone) {
+        unsigned long long lk = link_key(vid, up);
+        unsigned long long h = mix64(lk) & a.hmask;
+        bool placed = false;
+        for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+            unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
+            if (k == kEmptyKey) {
+                unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
+                if (prev == kEmptyKey) {
+                    unsigned long long ns = atomicAdd(a.nslots, 1ull);
+                    if (ns >= a.cap) {
+                        atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
                     } else {
-                        s = (u32)e;
-                        // written by another group in this launch: read past L1
-                        vid = __ldcg(a.svid + s);
-                        j = __ldcg(a.sj + s);
-                        key = __ldcg(a.sord + s);
+                        a.svid[ns] = vid;
+                        a.sj[ns] = up;
+                        a.sord[ns] = key;
+                        *(volatile unsigned int *)&a.table[h].val = (u32)ns;
+                        a.fr_out[atomicAdd(a.nf_out, 1ull)] = (u32)ns;
+                        nx = (u32)ns;
                     }
+                    placed = true;
+                    break;
                 }
+                k = prev;
             }
-            stop = __shfl_sync(gmask, stop, 0, G);
-            skip = __shfl_sync(gmask, skip, 0, G);
-            if (stop) {
-                quit = true;
+            if (k == lk) {
+                u32 v = *(volatile unsigned int *)&a.table[h].val;
+                nx = (v != kNone) ? v : (kPending | (u32)h);
+                placed = true;
                 break;
             }
-            if (skip) continue;
-            s = __shfl_sync(gmask, s, 0, G);
-            vid = __shfl_sync(gmask, vid, 0, G);
-            j = __shfl_sync(gmask, j, 0, G);
-            key = __shfl_sync(gmask, key, 0, G);
-            run_item(s, vid, j, key);
+            h = (h + 1) & a.hmask;
         }
+        if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
     }
-    if (gl == 0) flush();
-    if (gl != 0) fbs = 0;
-    for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
-    if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
+    a.state[s].x = nx;
+    a.nx0[s] = nx;
 }
 
-// Links claimed by another group during the persistent launch: read the slot
-// the claimant wrote (visible after the launch boundary).
-__global__ void k_memo_resolve_all(MemoArgs a, long long n)
+// Links claimed by another thread during the same launch: read the slot the
+// claimant wrote (visible after the launch boundary).
+__global__ void k_memo_resolve(MemoArgs a)
 {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= a.nf) return;
+    u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
     u32 nx = a.state[s].x;
     if (nx != kNone && (nx & kPending)) {
         u32 v = a.table[nx & ~kPending].val;
@@ -508,6 +371,16 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
     if (lane == 0 && maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
 }
 
+template <int G>
+static void launch_memo_hop(const MemoArgs &a, cudaStream_t s, int nsm)
+{
+    long long blocks = (a.nf * G + 255) / 256;
+    long long cap = (long long)nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_memo_hop<G><<<(unsigned)blocks, 256, 0, s>>>(a);
+}
+
 static unsigned long long read_u64(start_ctx *c, const unsigned long long *d)
 {
     unsigned long long v = 0;
@@ -521,23 +394,19 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
 {
     cudaStream_t s = c->stream;
     overflow = false;
-    size_t qcap = cap - (size_t)m.npairs;   // links outside the lists
     // the table holds only the links outside the lists
     size_t hsize = 1;
-    while (hsize < 2 * qcap + 1024) hsize <<= 1;
+    while (hsize < 2 * (cap - (size_t)m.npairs) + 1024) hsize <<= 1;
     if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_ord, cap * 4) ||
         ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
-        ensure(c->m_st[1], cap * 16) || ensure(c->m_q, qcap * 8) ||
-        ensure(c->m_qc, sizeof(QueueCtl)) || ensure(c->m_table, hsize * sizeof(HEntry)))
+        ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) || ensure(c->m_fr[0], cap * 4) ||
+        ensure(c->m_fr[1], cap * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_CUDA(c, cudaMemsetAsync(c->m_table.p, 0xff, hsize * sizeof(HEntry), s));
-    ST_CUDA(c, cudaMemsetAsync(c->m_q.p, 0xff, qcap * 8, s));
     ST_CUDA(c, cudaMemsetAsync(ctr + C_MEMO_OVF, 0, sizeof(unsigned long long), s));
     ST_CUDA(c, cudaMemcpyAsync(ctr + C_SLOTS, &m.npairs, sizeof(unsigned long long),
                                cudaMemcpyHostToDevice, s));
-    QueueCtl qc0 = {0ull, 0ull, 0ull, (unsigned long long)m.npairs, 0ull};
-    ST_CUDA(c, cudaMemcpyAsync(c->m_qc.p, &qc0, sizeof(qc0), cudaMemcpyHostToDevice, s));
     MemoArgs a;
     a.m = m;
     a.SN = (u32)c->stree.n;
@@ -556,70 +425,69 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.state = c->m_st[0].as<uint4>();
     a.nx0 = c->m_nx0.as<u32>();
     a.dl = c->m_dl.as<float>();
+    a.ups = c->m_ups.as<u32>();
     a.nslots = ctr + C_SLOTS;
     a.cap = (u32)cap;
     a.table = c->m_table.as<HEntry>();
     a.hmask = hsize - 1;
+    a.fr_in = nullptr;
+    a.nf = m.npairs;
+    a.nf_out = ctr + C_FRONTIER;
     k_memo_init<<<grid_for(m.npairs, 256), 256, 0, s>>>(a);
     ++c->launches;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (nsm <= 0) nsm = 1;
+    int cur = 0;
+    long long iter = 0;
     bool timing = c->p.timing != 0;
     if (timing && !c->hev[0]) {
         cudaEventCreate(&c->hev[0]);
         cudaEventCreate(&c->hev[1]);
     }
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    if (nsm <= 0) nsm = 1;
-    long long spin = c->p.spin_cap > 0 ? c->p.spin_cap : (1LL << 24);
-    QueueCtl *qc = c->m_qc.as<QueueCtl>();
-    unsigned long long *q = c->m_q.as<unsigned long long>();
-    if (timing) cudaEventRecord(c->hev[0], s);
-    // persistent: every group resident at once, so queue waits always see progress
-    auto launch = [&](auto kern) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
-        if (per_sm < 1) per_sm = 1;
-        kern<<<nsm * per_sm, 256, 0, s>>>(a, qc, q, (unsigned long long)qcap, spin);
-    };
-    switch (c->p.march_group) {
-    case 32: launch(k_memo_persist<32>); break;
-    case 16: launch(k_memo_persist<16>); break;
-    case 8: launch(k_memo_persist<8>); break;
-    case 4: launch(k_memo_persist<4>); break;
-    case 1: launch(k_memo_persist<1>); break;
-    default: launch(k_memo_persist<2>); break;
+    double hop_ms = 0.0;
+    long long max_iter = m.hop_cap + 1;
+    while (a.nf > 0) {
+        a.fr_out = c->m_fr[cur].as<u32>();
+        ST_CUDA(c, cudaMemsetAsync(a.nf_out, 0, sizeof(unsigned long long), s));
+        if (timing) cudaEventRecord(c->hev[0], s);
+        switch (c->p.march_group) {
+        case 32: launch_memo_hop<32>(a, s, nsm); break;
+        case 16: launch_memo_hop<16>(a, s, nsm); break;
+        case 4: launch_memo_hop<4>(a, s, nsm); break;
+        case 2: launch_memo_hop<2>(a, s, nsm); break;
+        case 1: launch_memo_hop<1>(a, s, nsm); break;
+        default: launch_memo_hop<8>(a, s, nsm); break;
+        }
+        if (timing) cudaEventRecord(c->hev[1], s);
+        k_memo_link<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
+        k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
+        c->launches += 3;
+        ST_CUDA(c, cudaGetLastError());
+        // the overflow flag and the next frontier size are adjacent counters
+        unsigned long long both[2] = {0, 0};
+        static_assert(C_FRONTIER == C_MEMO_OVF + 1, "adjacent counters");
+        ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_MEMO_OVF, sizeof(both), cudaMemcpyDeviceToHost, s));
+        ST_CUDA(c, cudaStreamSynchronize(s));
+        if (timing) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
+            else cudaGetLastError();
+        }
+        if (both[0]) {
+            overflow = true;
+            return START_OK;
+        }
+        a.fr_in = c->m_fr[cur].as<u32>();
+        a.nf = (long long)both[1];
+        cur ^= 1;
+        if (++iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
     }
-    if (timing) cudaEventRecord(c->hev[1], s);
-    ++c->launches;
-    ST_CUDA(c, cudaGetLastError());
-    QueueCtl qh;
-    unsigned long long ovf = 0;
-    ST_CUDA(c, cudaMemcpyAsync(&qh, qc, sizeof(qh), cudaMemcpyDeviceToHost, s));
-    ST_CUDA(c, cudaMemcpyAsync(&ovf, ctr + C_MEMO_OVF, sizeof(ovf), cudaMemcpyDeviceToHost, s));
-    ST_CUDA(c, cudaStreamSynchronize(s));
-    if (timing) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) c->hop_ms += ms;
-        else cudaGetLastError();
-    }
-    if (qh.timeout) return set_err(c, START_ETIMEOUT, "memoised march: a queue wait exceeded spin_cap");
-    if (ovf) {
-        overflow = true;
-        return START_OK;
-    }
-    unsigned long long used = qh.qtail < (unsigned long long)qcap ? qh.qtail : (unsigned long long)qcap;
-    long long nslots = m.npairs + (long long)used;
-    k_memo_resolve_all<<<grid_for(nslots, 256), 256, 0, s>>>(a, nslots);
-    ++c->launches;
-    ST_CUDA(c, cudaGetLastError());
-    // slots = pairs + reserved queue indices (unused ones hold benign links);
-    // evaluations = pairs + links created
-    unsigned long long evaluated = 0;
-    ST_CUDA(c, cudaMemcpyAsync(&evaluated, ctr + C_SLOTS, sizeof(evaluated), cudaMemcpyDeviceToHost, s));
-    ST_CUDA(c, cudaStreamSynchronize(s));
+    if (timing) c->hop_ms += hop_ms;
+    long long nslots = (long long)read_u64(c, ctr + C_SLOTS);
     c->memo_slots = nslots;
-    c->memo_evals += evaluated;
-    c->memo_links += evaluated;
+    c->memo_evals += (unsigned long long)nslots;
+    c->memo_links += (unsigned long long)nslots;
     // pointer jumping
     int b = 0;
     unsigned *active = c->flags.as<unsigned>() + 12;

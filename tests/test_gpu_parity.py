@@ -414,29 +414,6 @@ def test_hop_cap_reports_echain(S, cfg1, mode):
     assert e.value.code == S.START_ECHAIN
 
 
-def test_queue_wait_limit_reports_etimeout_and_context_survives(S, cfg1):
-    """A persistent-kernel wait that runs out (spin_cap = 1 iteration) ends
-    the launch with START_ETIMEOUT instead of hanging; the context's other
-    calls keep working and the device serves the next solve correctly."""
-    ctx = S.Context(spin_cap=1)
-    ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
-    with pytest.raises(S.StartError) as e:
-        ctx.rt_solve(0.5, n_HI=cfg1.n_HI(), gamma_out=np.zeros(cfg1.n_p, np.float32))
-    assert e.value.code == S.START_ETIMEOUT
-    assert ctx.stats()["nodes_src"] > 0
-    off, ent = ctx.lists(0.5)
-    orc = oracle.Oracle.from_workload(cfg1, ptree_leaf=PTREE_LEAF)
-    dec, _ = decode(ent)
-    assert dec[off[7]:off[8]].tolist() == orc.list(0.5, 7).tolist()
-    ctx.set_state(cfg1.n_H, cfg1.y0)
-    fresh = S.Context()
-    fresh.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
-    g = np.zeros(cfg1.n_p, np.float32)
-    fresh.rt_solve(0.5, n_HI=cfg1.n_HI(), gamma_out=g)
-    idx = np.arange(0, cfg1.n_p, 257)
-    gamma_close(g[idx], orc.gamma(cfg1.n_HI(), 0.5, targets=idx))
-
-
 # ------------------------------------------------------------------ full size, sampled
 def test_config2_full_size_sampled_targets(S):
     """64^3 particles and 1024 sources at theta = 0.5 in the launch
