@@ -60,6 +60,7 @@ def parse():
                     help="targets per step of the reference arm")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-resident", action="store_true")
+    ap.add_argument("--no-diffuse", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-workers", type=int, default=4)
@@ -244,6 +245,46 @@ def resident_steps(S, w, dev, args, T):
                     "implicit update (no tree build, walk or neighbour search)"}
 
 
+def diffuse_workload(S, dev, args, T):
+    """The diffuse-recombination shadowing workload at full size: 128^3
+    particles (all emitting), eight 200x clumps, one 3e51/s central source,
+    theta = 0.7; coupled full-path steps (emitter moments, walk over both
+    trees, memoised march in target chunks, Gamma, update with k_self)."""
+    import torch
+    from start_inputs import config3
+    w = config3()
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream, max_pairs=1 << 29)
+    y = T(w.y0)
+    g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    pos, h, sp, sL, V, nH = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L), T(w.V), T(w.n_H)
+
+    def step():
+        ctx.build_trees(pos, h, sp, sL, V, diffuse=True)
+        ctx.set_state(nH, y)
+        ctx.rt_solve(0.7, gamma_out=g)
+        ctx.ionize(w.dt_s, y_out=y)
+
+    step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps, rays = 2, 0
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+        rays += ctx.stats()["rays"]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    ctx.close()
+    return {"value": rays / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms / steps,
+            "rays_per_step": rays / steps, "chunks": st["chunks"],
+            "evaluations_per_ray": st["evals"] / max(1, st["rays"]), "workload": w.name,
+            "theta": 0.7}
+
+
 def serving(args):
     """Continuous batching vs one solve at a time on the same Poisson stream
     of requests of mixed size (real-time replay, 150 GB budget)."""
@@ -397,6 +438,8 @@ def run_gpu(args, w):
 
     if not args.no_resident:
         out["resident_steps"] = resident_steps(S, w, dev, args, T)
+    if not args.no_diffuse:
+        out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: H2D copies of the
