@@ -160,6 +160,12 @@ int start_create(start_ctx **out, const start_params *p);
 /* Release the context and its device buffers (synchronises its stream). */
 int start_destroy(start_ctx *c);
 
+/* Replace the parameters of a context (e.g. tuned knobs between requests).
+ * The stream and the physical constants may change too; src_leaf and
+ * ptree_leaf take effect at the next start_build_trees.  Invalid values give
+ * START_EINVAL and leave the context unchanged. */
+int start_set_params(start_ctx *c, const start_params *p);
+
 /* Steps 1-4 (and the emitter tree in diffuse mode): frame, keys, sorts,
  * source tree + moments, particle tree, neighbour lists.
  *   pos    [3 * n_p] float32 SoA particle positions

@@ -69,6 +69,7 @@ def lib():
             "start_default_params": (i, [P(StartParams)]),
             "start_create": (i, [P(vp), P(StartParams)]),
             "start_destroy": (i, [vp]),
+            "start_set_params": (i, [vp, P(StartParams)]),
             "start_build_trees": (i, [vp, vp, vp, ll, vp, vp, ll, vp, C.c_uint]),
             "start_set_state": (i, [vp, vp, vp]),
             "start_rt_solve": (i, [vp, vp, f, vp]),
@@ -182,6 +183,17 @@ class Context:
         self.h = start_create(self.params)
         self.n_p = 0
         self.n_s = 0
+
+    def set_params(self, **over):
+        """Change knobs of this context (the others keep their values)."""
+        p = StartParams()
+        C.memmove(C.byref(p), C.byref(self.params), C.sizeof(StartParams))
+        for k, v in over.items():
+            if k == "stream" and v is not None and not isinstance(v, int):
+                v = int(v.cuda_stream)
+            setattr(p, k, v)
+        _check(self.h, lib().start_set_params(self.h, C.byref(p)))
+        self.params = p
 
     def close(self):
         if getattr(self, "h", None):

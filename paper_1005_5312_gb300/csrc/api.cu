@@ -369,13 +369,8 @@ int start_default_params(start_params *p)
     return START_OK;
 }
 
-int start_create(start_ctx **out, const start_params *p)
+static int check_params(start_params &d)
 {
-    if (!out) return START_EINVAL;
-    *out = nullptr;
-    start_params d;
-    start_default_params(&d);
-    if (p) d = *p;
     if (d.src_leaf < 1 || d.ptree_leaf < 1 || !(d.sigma_cm2 > 0) || !(d.len_unit_cm > 0) ||
         !(d.L_unit > 0) || !(d.alpha_A >= 0) || !(d.alpha_B >= 0) || !(d.tau_cut > 0))
         return START_EINVAL;
@@ -384,6 +379,18 @@ int start_create(start_ctx **out, const start_params *p)
         return START_EINVAL;
     if (d.march_group == 0) d.march_group = 2;
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
+    if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
+    return START_OK;
+}
+
+int start_create(start_ctx **out, const start_params *p)
+{
+    if (!out) return START_EINVAL;
+    *out = nullptr;
+    start_params d;
+    start_default_params(&d);
+    if (p) d = *p;
+    if (check_params(d) != START_OK) return START_EINVAL;
     start_ctx *c = new (std::nothrow) start_ctx();
     if (!c) return START_ENOMEM;
     c->p = d;
@@ -403,6 +410,24 @@ int start_create(start_ctx **out, const start_params *p)
         return START_ENOMEM;
     }
     *out = c;
+    return START_OK;
+}
+
+int start_set_params(start_ctx *c, const start_params *p)
+{
+    if (!c || !p) return START_EINVAL;
+    start_params d = *p;
+    if (check_params(d) != START_OK) return set_err(c, START_EINVAL, "invalid parameters");
+    DeviceGuard g(c);
+    if ((cudaStream_t)d.stream != c->stream) {
+        cudaStreamSynchronize(c->stream);
+        resident_reset(c);   // the captured graph belongs to the old stream's sequence
+    }
+    if (d.reuse_chains != c->p.reuse_chains || d.sigma_cm2 != c->p.sigma_cm2 ||
+        d.len_unit_cm != c->p.len_unit_cm || d.L_unit != c->p.L_unit)
+        resident_reset(c);
+    c->p = d;
+    c->stream = (cudaStream_t)d.stream;
     return START_OK;
 }
 

@@ -94,7 +94,7 @@ class Server:
     """FIFO admission by worker slots and a device-memory budget."""
 
     def __init__(self, workers: int = 4, budget_bytes: float = 150e9, max_pairs: int = 1 << 27,
-                 **params):
+                 tuner=None, **params):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
@@ -104,6 +104,7 @@ class Server:
         for _ in range(max(1, workers)):
             st = torch.cuda.Stream()
             self.workers.append(_Worker(Context(stream=st, **self.params), st))
+        self.tuner = tuner
         self.cv = threading.Condition()
         self.reserved = 0.0
         self.results = []
@@ -116,6 +117,10 @@ class Server:
     def _solve(self, w: _Worker, req: SolveRequest, t0: float, t_admit: float, est: int):
         try:
             ctx = w.ctx
+            if self.tuner is not None:
+                knobs = self.tuner.params_for(req.n_p, req.n_s, req.theta)
+                knobs["max_pairs"] = min(knobs["max_pairs"], self.max_pairs)
+                ctx.set_params(**knobs)
             ctx.build_trees(req.pos, req.h, req.src_pos, req.src_L)
             y = np.ascontiguousarray(req.y0, dtype=np.float64).copy()
             g = np.zeros(req.n_p, np.float32)
