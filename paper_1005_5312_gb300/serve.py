@@ -99,7 +99,7 @@ class Server:
         self.torch = torch
         self.budget = float(budget_bytes)
         self.max_pairs = int(max_pairs)
-        self.params = dict(params, max_pairs=self.max_pairs)
+        self.params = dict(dict(reuse_chains=1), **params, max_pairs=self.max_pairs)
         self.workers = []
         for _ in range(max(1, workers)):
             st = torch.cuda.Stream()
