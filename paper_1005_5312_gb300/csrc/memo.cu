@@ -528,8 +528,18 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
 int run_memo(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base)
 {
     if (m.npairs == 0) return START_OK;
-    size_t cap = (size_t)m.npairs + (size_t)(m.npairs / 4) + (size_t)c->np + 4096;
+    // a chunk that does not cover every target cuts chains: more links leave its lists
+    bool partial = t0 > 0 || t1 < c->np;
+    size_t cap = (size_t)m.npairs + (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
+    // an attempt that runs out of slots leaves artefacts (table keys without
+    // slots) in the error and fallback counters: restore them before retrying
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    unsigned long long saved[C_COUNT];
+    ST_CUDA(c, cudaMemcpyAsync(saved, ctr, sizeof(saved), cudaMemcpyDeviceToHost, c->stream));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int attempt = 0; attempt < 4; ++attempt) {
+        if (attempt > 0)
+            ST_CUDA(c, cudaMemcpyAsync(ctr, saved, sizeof(saved), cudaMemcpyHostToDevice, c->stream));
         // slot ids and table indices must stay below the pending flag (2^31)
         if (cap >= (1ull << 30)) return set_err(c, START_ERANGE, "too many chain links");
         bool overflow = false;

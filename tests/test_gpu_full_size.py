@@ -45,3 +45,34 @@ def test_config3_diffuse_full_size_sampled_targets():
     assert np.all(err <= 1e-4 * np.abs(ref) + G_ABS), (err, ref)
     print(f"config3: gen {t_gen:.1f}s solve {t_solve:.2f}s rays {st['rays']} chunks {st['chunks']} "
           f"evals {st['evals']}")
+
+
+def test_multi_chunk_request_memoised_matches_per_ray_and_oracle():
+    """A served request whose pairs need several target chunks (609,707
+    particles, 20,002 sources, theta = 0.5): chunks cut chains, so many links
+    leave the lists and the slot capacity is retried larger; the memoised
+    solve must still agree with the per-ray march and the oracle."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1005_5312_gb300 as S
+    from paper_1005_5312_gb300.serve import make_requests
+    S.build()
+    r = make_requests(2, rate_hz=50.0, log2_np=(15, 21))[1]
+    assert r.n_p == 609707 and r.n_s == 20002
+    out = {}
+    for mode in (1, 0):
+        ctx = S.Context(march_mode=mode, tau_cut=1e30)
+        ctx.build_trees(r.pos, r.h, r.src_pos, r.src_L)
+        g = np.zeros(r.n_p, np.float32)
+        ctx.rt_solve(r.theta, n_HI=r.n_H, gamma_out=g)
+        out[mode] = (g.astype(np.float64), ctx.stats())
+        ctx.close()
+    (g1, s1), (g0, s0) = out[1], out[0]
+    assert s1["chunks"] > 1 and s1["rays"] == s0["rays"] and s1["hops"] == s0["hops"]
+    assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
+    orc = oracle.Oracle(r.pos, r.h, r.src_pos, r.src_L, ptree_leaf=16, sigma_cm2=6.3e-18,
+                        len_unit_cm=3.0857e21, alpha_A=4.18e-13, alpha_B=2.59e-13)
+    idx = np.random.default_rng(4).choice(r.n_p, 12, replace=False)
+    ref = orc.gamma(r.n_H, r.theta, targets=idx)
+    assert np.all(np.abs(g1[idx] - ref) <= 1e-4 * np.abs(ref) + G_ABS)
