@@ -185,40 +185,48 @@ def summarize(results, t_first_arrival: float = 0.0) -> dict:
             "rays_per_s": sum(r.rays for r in results) / span, "n": len(results)}
 
 
+def make_request(rid: int, n_p: int, n_s: int, clumpy: bool, theta: float, t_arrive: float = 0.0,
+                 seed: int = 53124, steps: int = 1, dt: float = 3.15576e13) -> SolveRequest:
+    """One request: particles on a jittered lattice of the requested size in
+    a 6.6 kpc box with 2h = 2.04 spacings (about 33 neighbours), uniform
+    n_H = 1e-3 or eight 200x clumps on 2e-4, sources uniform with
+    L = 1e48 exp(N(0, 1)).  The arrays depend only on (seed, rid)."""
+    rng = np.random.default_rng((seed, rid))
+    box = 6.6
+    nside = int(math.ceil(n_p ** (1.0 / 3.0) - 1e-9))
+    dx = box / nside
+    keep = np.sort(rng.choice(nside ** 3, size=n_p, replace=False))
+    ijk = np.stack(np.unravel_index(keep, (nside, nside, nside))).astype(np.float64)
+    pos = ((ijk + 0.5 + rng.uniform(-0.25, 0.25, size=ijk.shape)) * dx).astype(np.float32)
+    h = np.full(n_p, 1.02 * dx, np.float32)
+    if clumpy:
+        n_H = np.full(n_p, 2e-4)
+        for c in rng.uniform(0.8, box - 0.8, size=(8, 3)):
+            inside = np.sum((pos.T.astype(np.float64) - c) ** 2, axis=1) < 0.64
+            n_H[inside] = 0.04
+        n_H = n_H.astype(np.float32)
+    else:
+        n_H = np.full(n_p, 1e-3, np.float32)
+    src = rng.uniform(0.0, box, size=(3, n_s)).astype(np.float32)
+    src_L = 1e48 * np.exp(rng.normal(0.0, 1.0, size=n_s))
+    return SolveRequest(rid, float(t_arrive), np.ascontiguousarray(pos), h, src, src_L, n_H,
+                        np.ones(n_p), float(theta), dt, steps)
+
+
 def make_requests(n_req: int = 256, rate_hz: float = 50.0, log2_np=(15.0, 21.0), seed: int = 53124,
                   steps: int = 1, dt: float = 3.15576e13) -> list:
     """Config-4-shaped stream: exponential inter-arrivals, N_p = 2^U(a, b),
-    N_s = exp(U(0, ln N_p)), uniform or clumpy (eight 200x clumps) density,
-    theta in {0.5, 1}.  Particles on a jittered lattice of the requested
-    size in a 6.6 kpc box with 2h = 2.04 spacings (about 33 neighbours);
-    sources uniform, L = 1e48 exp(N(0, 1))."""
-    rng = np.random.default_rng(seed)
-    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_req))
+    N_s = exp(U(0, ln N_p)), uniform or clumpy density (coin flip), theta in
+    {0.5, 1}; request r's recipe and arrays do not depend on n_req."""
+    t = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate_hz, size=n_req))
     out = []
-    box = 6.6
     for r in range(n_req):
+        rng = np.random.default_rng((seed, r, 1))
         n_p = int(round(2.0 ** rng.uniform(*log2_np)))
         n_s = max(1, int(round(math.exp(rng.uniform(0.0, math.log(n_p))))))
         clumpy = bool(rng.integers(0, 2))
         theta = float(rng.choice([0.5, 1.0]))
-        nside = int(math.ceil(n_p ** (1.0 / 3.0) - 1e-9))
-        dx = box / nside
-        keep = np.sort(rng.choice(nside ** 3, size=n_p, replace=False))
-        ijk = np.stack(np.unravel_index(keep, (nside, nside, nside))).astype(np.float64)
-        pos = ((ijk + 0.5 + rng.uniform(-0.25, 0.25, size=ijk.shape)) * dx).astype(np.float32)
-        h = np.full(n_p, 1.02 * dx, np.float32)
-        if clumpy:
-            n_H = np.full(n_p, 2e-4)
-            for c in rng.uniform(0.8, box - 0.8, size=(8, 3)):
-                inside = np.sum((pos.T.astype(np.float64) - c) ** 2, axis=1) < 0.64
-                n_H[inside] = 0.04
-            n_H = n_H.astype(np.float32)
-        else:
-            n_H = np.full(n_p, 1e-3, np.float32)
-        src = rng.uniform(0.0, box, size=(3, n_s)).astype(np.float32)
-        src_L = 1e48 * np.exp(rng.normal(0.0, 1.0, size=n_s))
-        out.append(SolveRequest(r, float(t[r]), np.ascontiguousarray(pos), h, src, src_L, n_H,
-                                np.ones(n_p), theta, dt, steps))
+        out.append(make_request(r, n_p, n_s, clumpy, theta, float(t[r]), seed, steps, dt))
     return out
 
 

@@ -56,10 +56,9 @@ def test_multi_chunk_request_memoised_matches_per_ray_and_oracle():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1005_5312_gb300 as S
-    from paper_1005_5312_gb300.serve import make_requests
+    from paper_1005_5312_gb300.serve import make_request
     S.build()
-    r = make_requests(2, rate_hz=50.0, log2_np=(15, 21))[1]
-    assert r.n_p == 609707 and r.n_s == 20002
+    r = make_request(1, 609707, 20002, clumpy=False, theta=0.5)
     out = {}
     for mode in (1, 0):
         ctx = S.Context(march_mode=mode, tau_cut=1e30)
