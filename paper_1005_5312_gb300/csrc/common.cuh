@@ -157,8 +157,7 @@ enum Counter {
     C_EVALS,      // neighbour-list evaluations performed
     C_SLOTS,      // memoised chain links (virtual source, particle)
     C_MEMO_OVF,   // memo slot capacity exceeded (the host retries larger)
-    C_FRONTIER,   // size of the next memo frontier (also a level counter)
-    C_LEVEL,      // second level counter of the breadth-first tau pass
+    C_FRONTIER,   // size of the next memo frontier
     C_COUNT = 16
 };
 

@@ -291,66 +291,32 @@ __device__ __forceinline__ float2 cadd(float2 x, float2 y)
     return make_float2(hi, lo);
 }
 
-// 3. tau of every slot, breadth-first from the chain ends.  Each slot has
-// one successor (its upstream link), so the predecessors of every slot are
-// gathered once into reverse lists; then the chain ends start level 1 and
-// level d + 1 is every predecessor of level d, whose tau is its own d_tau
-// plus its successor's complete tau (compensated).  Every slot is written
-// once, after its successor, and its sum runs from the source end in chain
-// order -- an order that depends only on the chain.  The level of a slot is
-// its number of links to the end of its chain.
-constexpr u32 kStable = 0x80000000u;   // reserved bit of the link count (never set)
+// 3. one synchronous round of pointer jumping over the packed link state.
+// A slot whose chain is resolved (next = kNone) is copied once more so that
+// both buffers hold it, then marked stable (bit 31 of its link count) and
+// never rewritten or re-read.
+constexpr u32 kStable = 0x80000000u;
 
-__global__ void k_pred_count(long long n, const u32 *nx0, u32 *pc)
+__global__ void k_memo_jump(long long n, const uint4 *st, uint4 *st2, unsigned *active)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    u32 nx = nx0[s];
-    if (nx != kNone) atomicAdd(&pc[nx], 1u);
-}
-
-__global__ void k_pred_fill(long long n, const u32 *nx0, const u32 *poff, u32 *cur, u32 *pred)
-{
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    u32 nx = nx0[s];
-    if (nx != kNone) pred[poff[nx] + atomicAdd(&cur[nx], 1u)] = (u32)s;
-}
-
-__global__ void k_chain_ends(long long n, const u32 *nx0, u32 *lvl, unsigned long long *cnt)
-{
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool end = s < n && nx0[s] == kNone;
-    unsigned m = __ballot_sync(0xffffffffu, end);
-    if (!m) return;
-    unsigned long long base = 0;
-    int lane = threadIdx.x & 31;
-    if (lane == __ffs(m) - 1) base = atomicAdd(cnt, (unsigned long long)__popc(m));
-    base = __shfl_sync(m, base, __ffs(m) - 1);
-    if (end) lvl[base + __popc(m & ((1u << lane) - 1))] = (u32)s;
-}
-
-// Level d -> d + 1; the level size is read on the device (grid-stride), so
-// several levels go back to back without a host round trip.
-__global__ void k_chain_level(const u32 *lvl_in, const unsigned long long *n_in, u32 *lvl_out,
-                              unsigned long long *n_out, const u32 *poff, const u32 *pred,
-                              uint4 *st)
-{
-    long long n = (long long)*n_in;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        u32 s = lvl_in[i];
+    bool act = false;
+    if (s < n) {
         uint4 me = st[s];
-        float2 t = make_float2(__uint_as_float(me.z), __uint_as_float(me.w));
-        u32 p0 = poff[s], p1 = poff[s + 1];
-        for (u32 e = p0; e < p1; ++e) {
-            u32 p = pred[e];
-            uint4 q = st[p];
-            float2 u = cadd(make_float2(__uint_as_float(q.z), 0.f), t);
-            st[p] = make_uint4(s, me.y + 1u, __float_as_uint(u.x), __float_as_uint(u.y));
-            lvl_out[atomicAdd(n_out, 1ull)] = p;
+        if (me.x != kNone) {
+            uint4 nx = st[me.x];
+            float2 t = cadd(make_float2(__uint_as_float(me.z), __uint_as_float(me.w)),
+                            make_float2(__uint_as_float(nx.z), __uint_as_float(nx.w)));
+            me = make_uint4(nx.x, (me.y & ~kStable) + (nx.y & ~kStable), __float_as_uint(t.x),
+                            __float_as_uint(t.y));
+            act = nx.x != kNone;
+            st2[s] = me;
+        } else if (!(me.y & kStable)) {
+            me.y |= kStable;
+            st2[s] = me;
         }
     }
+    if (__any_sync(0xffffffffu, act) && (threadIdx.x & 31) == 0) *active = 1u;
 }
 
 // 4. Gamma of every target from its pairs' chain sums, one warp per target:
@@ -522,51 +488,22 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     c->memo_slots = nslots;
     c->memo_evals += (unsigned long long)nslots;
     c->memo_links += (unsigned long long)nslots;
-    // tau by levels from the chain ends (the successor of every slot is final
-    // in state.x after the resolve; links = 1, tau = (d_tau, 0))
-    long long S = nslots;
-    if (ensure(c->m_ups, (size_t)(S + 1) * 4)) return set_err(c, START_ENOMEM, "out of device memory");
-    u32 *scratch = c->m_st[1].as<u32>();          // 4 x S words: count, pred, two levels
-    u32 *pc = scratch, *pred = scratch + S, *lv0 = scratch + 2 * S, *lv1 = scratch + 3 * S;
-    u32 *poff = c->m_ups.as<u32>();
-    unsigned long long *cnt = c->counters.as<unsigned long long>() + C_FRONTIER;
-    unsigned long long *cnt2 = c->counters.as<unsigned long long>() + C_LEVEL;
-    ST_CUDA(c, cudaMemsetAsync(pc, 0, S * 4, s));
-    k_pred_count<<<grid_for(S, 256), 256, 0, s>>>(S, a.nx0, pc);
-    ++c->launches;
-    ST_TRY(exclusive_scan_u32(c, pc, poff, S, poff + S));
-    ST_CUDA(c, cudaMemsetAsync(pc, 0, S * 4, s));  // reused as fill cursors
-    k_pred_fill<<<grid_for(S, 256), 256, 0, s>>>(S, a.nx0, poff, pc, pred);
-    ST_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
-    k_chain_ends<<<grid_for(S, 256), 256, 0, s>>>(S, a.nx0, lv0, cnt);
-    c->launches += 2;
-    ST_CUDA(c, cudaGetLastError());
-    int nsm2 = 0;
-    cudaDeviceGetAttribute(&nsm2, cudaDevAttrMultiProcessorCount, c->device);
-    if (nsm2 <= 0) nsm2 = 1;
-    unsigned long long *cnts[2] = {cnt, cnt2};
-    u32 *lvls[2] = {lv0, lv1};
-    int lc = 0;
-    long long levels = 0;
-    for (;;) {
-        // a few levels per host round trip; empty levels cost one short launch
-        for (int k = 0; k < 8; ++k) {
-            ST_CUDA(c, cudaMemsetAsync(cnts[lc ^ 1], 0, sizeof(unsigned long long), s));
-            k_chain_level<<<nsm2 * 8, 256, 0, s>>>(lvls[lc], cnts[lc], lvls[lc ^ 1],
-                                                   cnts[lc ^ 1], poff, pred, a.state);
-            ++c->launches;
-            lc ^= 1;
-            ++levels;
-        }
+    // pointer jumping
+    int b = 0;
+    unsigned *active = c->flags.as<unsigned>() + 12;
+    for (int round = 0; round < 40; ++round) {
+        ST_CUDA(c, cudaMemsetAsync(active, 0, sizeof(unsigned), s));
+        k_memo_jump<<<grid_for(nslots, 256), 256, 0, s>>>(nslots, c->m_st[b].as<uint4>(),
+                                                          c->m_st[b ^ 1].as<uint4>(), active);
+        ++c->launches;
         ST_CUDA(c, cudaGetLastError());
-        unsigned long long left = 0;
-        ST_CUDA(c, cudaMemcpyAsync(&left, cnts[lc], sizeof(left), cudaMemcpyDeviceToHost, s));
+        b ^= 1;
+        unsigned act = 0;
+        ST_CUDA(c, cudaMemcpyAsync(&act, active, sizeof(act), cudaMemcpyDeviceToHost, s));
         ST_CUDA(c, cudaStreamSynchronize(s));
-        if (!left) break;
-        if (levels > m.hop_cap + 8) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
+        if (!act) break;
     }
-    ST_CUDA(c, cudaMemsetAsync(cnt2, 0, sizeof(unsigned long long), s));
-    c->memo_final = 0;
+    c->memo_final = b;
     return START_OK;
 }
 
