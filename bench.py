@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--march-group", type=int, default=2)
     ap.add_argument("--march-mode", type=int, default=1, choices=[0, 1],
                     help="1 memoised march (default), 0 per-ray march")
+    ap.add_argument("--nside", type=int, default=64,
+                    help="lattice side of the multiple-source workload (64: the benchmark; "
+                         "smaller: profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-theta2", action="store_true")
@@ -493,7 +496,7 @@ def run_gpu(args, w):
 def main():
     args = parse()
     from start_inputs import config2
-    w = config2()
+    w = config2(nside=args.nside)
     res = run_reference(args, w) if args.impl == "reference" else run_gpu(args, w)
     if res is not None:
         print(json.dumps(res), flush=True)

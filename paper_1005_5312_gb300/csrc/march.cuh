@@ -79,13 +79,31 @@ __device__ u32 upstream_64(const MarchArgs &a, float4 pj, float4 src, u32 s0, u3
     return bk;
 }
 
+// Optical-depth increment of the link from particle j (record pj) to its
+// upstream particle mk, with b = r_s - r_j and bn = |b|: the trapezoid
+// sigma (n_j + n_up)/2 dl of Eq. tau with the radial difference
+// dl = (|b|^2 - |c|^2) / (|b| + |c|), c = r_up - r_s, evaluated as
+// (r_j - r_up).((r_j - r_s) + (r_up - r_s)) / (|b| + |c|) to avoid
+// cancellation; at the chain end (mk = kNone) sigma n_j |r_j - r_s|.
+__device__ __forceinline__ float link_dt(const MarchArgs &a, float4 pj, float4 src, float bx,
+                                         float by, float bz, float bn, u32 mk, float &dl)
+{
+    if (mk == kNone) {
+        dl = bn;
+        return a.sig * pj.w * bn;
+    }
+    float4 pu = a.pq[mk];
+    float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
+    float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
+    float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+    dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
+    return a.sig * 0.5f * (pj.w + pu.w) * dl;
+}
+
 // One neighbour-list evaluation at particle j (record pj) toward src.
 // Returns the upstream particle (kNone at the end of the chain) and the
-// optical-depth increment dt: sigma (n_j + n_up)/2 dl with the radial
-// difference dl = (|b|^2 - |c|^2) / (|b| + |c|) evaluated as
-// (r_j - r_up).((r_j - r_s) + (r_up - r_s)) / (|b| + |c|) to avoid
-// cancellation, or sigma n_j |r_j - r_s| at the chain end.  Every lane of the
-// group returns the same values; fbs counts FP64 re-decisions.
+// optical-depth increment dt of the link (link_dt).  Every lane of the group
+// returns the same values; fbs counts FP64 re-decisions.
 template <int G>
 __device__ __forceinline__ u32 hop(const MarchArgs &a, u32 j, float4 pj, float4 src, int gl,
                                    unsigned gmask, float &dt, unsigned long long &fbs,
@@ -149,17 +167,8 @@ __device__ __forceinline__ u32 hop(const MarchArgs &a, u32 j, float4 pj, float4 
         mk = upstream_64<G>(a, pj, src, s0, s1, gl, gmask);
         ++fbs;
     }
-    if (mk == kNone) {
-        dt = a.sig * pj.w * bn;
-        if (dl_out) *dl_out = bn;
-        return kNone;
-    }
-    float4 pu = a.pq[mk];
-    float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
-    float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
-    float cn = sqrtf(cx * cx + cy * cy + cz * cz);
-    float dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
-    dt = a.sig * 0.5f * (pj.w + pu.w) * dl;
+    float dl;
+    dt = link_dt(a, pj, src, bx, by, bz, bn, mk, dl);
     if (dl_out) *dl_out = dl;
     return mk;
 }

@@ -11,8 +11,8 @@
 // outside the list.
 //
 // Work is level-synchronous:
-//   1. every interaction pair (v, target) becomes slot p of a hash table
-//      keyed by (v, particle);
+//   1. every interaction pair (v, target) is slot p; links outside the lists
+//      get slots through a hash table keyed by (v, particle);
 //   2. each frontier slot takes one hop; its upstream link (v, up) is found
 //      in the table or claimed as a new slot, which joins the next frontier;
 //      links claimed by another group in the same launch are resolved by a
@@ -30,7 +30,11 @@
 
 namespace st {
 
+int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base);
+int ensure_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s);
+
 constexpr u32 kPending = 0x80000000u;
+constexpr u32 kRowMiss = 0x80000000u;   // frontier item: upstream not in its row
 constexpr unsigned long long kEmptyKey = ~0ull;
 
 struct __align__(16) HEntry {
@@ -42,10 +46,9 @@ struct __align__(16) HEntry {
 struct MemoArgs {
     MarchArgs m;
     u32 SN, NS, EN;                 // source-tree nodes, sources, emitter-tree nodes
-    const uint4 *smeta, *emeta;     // (skip, first, count, leaf) of the two trees
     u32 *svid, *sj;                 // slot: virtual source id, particle
-    u32 *sord;                      // slot: order key of its virtual source
-    const u32 *pord;                // pair: order key (rows are sorted by it)
+    u32 *sord;                      // slot: order key of its virtual source (rows are
+                                    // sorted by it)
     const u64 *off;                 // row offsets of the chunk's targets (minus base)
     long long t0, t1;               // the chunk's targets
     unsigned long long base;
@@ -73,23 +76,6 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
     return x;
 }
 
-// Canonical virtual-source id of a list entry: tree nodes first, then
-// individual sources; a single-member leaf maps to its member.
-__device__ __forceinline__ u32 canon(const MemoArgs &a, u32 e)
-{
-    u32 id = e & kEntryIdMask;
-    bool src = (e & kEntrySrc) != 0;
-    if (!(e & kEntryEmit)) {
-        if (src) return a.SN + id;
-        uint4 mt = a.smeta[id];
-        return (mt.w && mt.z == 1u) ? a.SN + mt.y : id;
-    }
-    u32 base = a.SN + a.NS;
-    if (src) return base + a.EN + id;
-    uint4 mt = a.emeta[id];
-    return (mt.w && mt.z == 1u) ? base + a.EN + mt.y : base + id;
-}
-
 __device__ __forceinline__ float4 vsource(const MemoArgs &a, u32 vid)
 {
     if (vid < a.SN) return a.m.svsrc[vid];
@@ -105,22 +91,6 @@ __device__ __forceinline__ float4 vsource(const MemoArgs &a, u32 vid)
 __device__ __forceinline__ unsigned long long link_key(u32 vid, u32 k)
 {
     return ((unsigned long long)vid << 32) | k;
-}
-
-// 1. every pair is a slot (its links are found in the rows of the pairs)
-__global__ void k_memo_init(MemoArgs a)
-{
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.m.npairs) return;
-    u32 vid = canon(a, a.m.pent[p]);
-    u32 t = a.m.ptgt[p];
-    if (t >= a.m.np) {
-        atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
-        t = 0;
-    }
-    a.svid[p] = vid;
-    a.sj[p] = t;
-    a.sord[p] = a.pord[p];
 }
 
 // Sums counters of a block and adds them once per block.
@@ -178,7 +148,9 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
 // targets have nearly the same lists, so the pair usually sits at the same
 // offset as in the row it comes from (guess) or a few entries away; else a
 // binary search on the order key finds the run of entries of the same cell.
-__device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u32 key, u32 raw,
+// Within a row the canonical ids are distinct (a row holds a count-1 cell or
+// its member, never both).
+__device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u32 key,
                                            long long guess_pos)
 {
     if ((long long)k < a.t0 || (long long)k >= a.t1) return kNone;   // row not in this chunk
@@ -187,21 +159,142 @@ __device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u3
     if (guess_pos >= 0) {
         u64 g = r0 + (u64)guess_pos;
         if (g >= r1) g = r1 - 1;
-        if (a.m.pent[g] == raw) return (u32)g;
+        if (a.svid[g] == vid) return (u32)g;
         for (u64 d = 1; d <= 8; ++d) {
-            if (g + d < r1 && a.m.pent[g + d] == raw) return (u32)(g + d);
-            if (g >= r0 + d && a.m.pent[g - d] == raw) return (u32)(g - d);
+            if (g + d < r1 && a.svid[g + d] == vid) return (u32)(g + d);
+            if (g >= r0 + d && a.svid[g - d] == vid) return (u32)(g - d);
         }
     }
     u64 lo = r0, hi = r1;
     while (lo < hi) {
         u64 mid = lo + ((hi - lo) >> 1);
-        if (a.pord[mid] < key) lo = mid + 1;
+        if (a.sord[mid] < key) lo = mid + 1;
         else hi = mid;
     }
-    for (u64 e = lo; e < r1 && a.pord[e] == key; ++e)
-        if (canon(a, a.m.pent[e]) == vid) return (u32)e;
+    for (u64 e = lo; e < r1 && a.sord[e] == key; ++e)
+        if (a.svid[e] == vid) return (u32)e;
     return kNone;
+}
+
+// 2a'. the first hop of every pair, one warp per target row: the pairs of
+// target j all evaluate j's neighbour list, so the list is read once, its
+// source-independent terms (r_k - r_j, |r_k - r_j|^2, its rsqrt and root) are
+// staged in shared memory, and each lane takes one pair, scanning the staged
+// candidates (every lane reads the same entry: a broadcast).  The decision
+// is the certified one of hop<G> -- the same FP32 terms and error bounds and
+// the same FP64 re-decision -- so the upstream particle is the same.  Rows
+// with more neighbours than the stage holds take hop<1> from global memory.
+// The walk wrote the pair slots' virtual source, particle and order key.
+constexpr int kRowNB = 64;      // staged neighbours per target
+constexpr int kRowWarps = 8;    // targets per block
+
+__global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
+{
+    __shared__ float4 nba[kRowWarps][kRowNB];   // (r_k - r_j, rsqrt |r_k - r_j|^2)
+    __shared__ uint4 nbb[kRowWarps][kRowNB];    // (|r_k - r_j|^2, |r_k - r_j|, k, -)
+    const float two_eps = 32.f * kU32;
+    const float eps_q = 16.f * kU32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned me = 1u << lane;
+    const long long i = a.t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    unsigned long long fbs = 0;
+    if (i < a.t1) {
+        const u64 r0 = a.off[i] - a.base, r1 = a.off[i + 1] - a.base;
+        const float4 pj = a.m.pq[i];
+        const u32 s0 = a.m.nb_off[i], s1 = a.m.nb_off[i + 1];
+        const bool staged = s1 - s0 <= (u32)kRowNB;
+        int nst = 0;
+        bool odd = false;   // a distinct neighbour whose FP32 offset underflowed
+        if (staged && r1 > r0) {
+            for (u32 b = s0; b < s1; b += 32) {
+                u32 s = b + lane;
+                bool ok = false;
+                float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint4 B = make_uint4(0u, 0u, 0u, 0u);
+                if (s < s1) {
+                    u32 k = a.m.nb_idx[s];
+                    if (k < a.m.np) {
+                        float4 pk = a.m.pq[k];
+                        float ax = pk.x - pj.x, ay = pk.y - pj.y, az = pk.z - pj.z;
+                        float a2 = ax * ax + ay * ay + az * az;
+                        if (a2 == 0.f) {
+                            if (pk.x != pj.x || pk.y != pj.y || pk.z != pj.z) odd = true;
+                        } else {
+                            float ra = rsqrtf(a2);
+                            A = make_float4(ax, ay, az, ra);
+                            B = make_uint4(__float_as_uint(a2), __float_as_uint(a2 * ra), k, 0u);
+                            ok = true;
+                        }
+                    }
+                }
+                unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    int q = nst + __popc(m & (me - 1u));
+                    nba[w][q] = A;
+                    nbb[w][q] = B;
+                }
+                nst += __popc(m);
+            }
+            odd = __any_sync(0xffffffffu, odd);
+            __syncwarp();
+        }
+        for (u64 p = r0 + lane; p < r1; p += 32) {
+            u32 vid = a.svid[p];
+            float4 src = vsource(a, vid);
+            float dt, dl;
+            u32 up;
+            if (staged) {
+                float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
+                float bn = sqrtf(bx * bx + by * by + bz * bz);
+                float bc = -1.f, sc = -1.f;
+                u32 bk = kNone;
+                bool unsure = odd;
+                for (int q = 0; q < nst; ++q) {
+                    float4 A = nba[w][q];
+                    uint4 B = nbb[w][q];
+                    float a2 = __uint_as_float(B.x), an = __uint_as_float(B.y);
+                    float dot = bx * A.x + by * A.y + bz * A.z;
+                    float qv = 2.f * dot - a2;
+                    float eq = eps_q * (2.f * an * bn + a2) + 1e-37f;
+                    if (qv > eq) {
+                        float cv = dot * A.w;
+                        if (cv > bc) {
+                            sc = bc;
+                            bc = cv;
+                            bk = B.z;
+                        } else if (cv > sc) {
+                            sc = cv;
+                        }
+                    } else if (qv >= -eq) {
+                        unsure = true;
+                    }
+                }
+                if (unsure || (sc > 0.f && sc > bc - two_eps * bn)) {
+                    bk = upstream_64<1>(a.m, pj, src, s0, s1, 0, me);
+                    ++fbs;
+                }
+                dt = link_dt(a.m, pj, src, bx, by, bz, bn, bk, dl);
+                up = bk;
+            } else {
+                up = hop<1>(a.m, (u32)i, pj, src, 0, me, dt, fbs, &dl);
+            }
+            // the upstream link is usually the pair (vid, up) of up's row --
+            // a neighbour's row, near this one; only the others go on to
+            // k_memo_link, marked so that it skips the row search
+            u32 nx = kNone;
+            if (up != kNone) {
+                nx = find_in_row(a, up, vid, a.sord[p], (long long)(p - r0));
+                a.ups[p] = (nx == kNone) ? (up | kRowMiss) : kNone;
+            } else {
+                a.ups[p] = kNone;
+            }
+            a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
+            a.dl[p] = dl;
+            a.nx0[p] = nx;
+        }
+    }
+    for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
+    if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
 }
 
 // 2b. the upstream link of every frontier slot: the pair (v, up) when it is
@@ -212,17 +305,18 @@ __global__ void k_memo_link(MemoArgs a)
     long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= a.nf) return;
     u32 up = a.ups[it];
-    if (up == kNone) return;              // chain end: next stays kNone
+    if (up == kNone) return;   // chain end, or a link the first-level kernel found
+    bool searched = (up & kRowMiss) != 0;
+    up &= ~kRowMiss;
     u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
     u32 vid = a.svid[s];
     u32 key = a.sord[s];
-    long long gpos = -1;
-    u32 raw = 0;
-    if ((long long)s < a.m.npairs) {
-        raw = a.m.pent[s];
-        gpos = (long long)(s - (a.off[a.sj[s]] - a.base));
+    u32 nx = kNone;
+    if (!searched) {
+        long long gpos = -1;
+        if ((long long)s < a.m.npairs) gpos = (long long)(s - (a.off[a.sj[s]] - a.base));
+        nx = find_in_row(a, up, vid, key, gpos);
     }
-    u32 nx = find_in_row(a, up, vid, key, raw, gpos);
     if (nx == kNone) {
         unsigned long long lk = link_key(vid, up);
         unsigned long long h = mix64(lk) & a.hmask;
@@ -297,23 +391,40 @@ __device__ __forceinline__ float2 cadd(float2 x, float2 y)
 // never rewritten or re-read.
 constexpr u32 kStable = 0x80000000u;
 
-__global__ void k_memo_jump(long long n, const uint4 *st, uint4 *st2, unsigned *active)
+constexpr int kJumpR = 4;   // slots per thread (independent loads in flight)
+
+__global__ void __launch_bounds__(256) k_memo_jump(long long n, const uint4 *__restrict__ st,
+                                                    uint4 *__restrict__ st2, unsigned *active,
+                                                    unsigned long long *internal)
 {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s0 = (long long)blockIdx.x * (256 * kJumpR) + threadIdx.x;
+    uint4 me[kJumpR], nx[kJumpR];
+#pragma unroll
+    for (int r = 0; r < kJumpR; ++r) {
+        long long s = s0 + 256 * r;
+        me[r] = s < n ? st[s] : make_uint4(kNone, kStable, 0u, 0u);
+        if (me[r].x != kNone && (long long)me[r].x >= n) {   // never expected
+            atomicAdd(internal, 1ull);
+            me[r].x = kNone;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kJumpR; ++r)
+        nx[r] = me[r].x != kNone ? st[me[r].x] : make_uint4(kNone, 0u, 0u, 0u);
     bool act = false;
-    if (s < n) {
-        uint4 me = st[s];
-        if (me.x != kNone) {
-            uint4 nx = st[me.x];
-            float2 t = cadd(make_float2(__uint_as_float(me.z), __uint_as_float(me.w)),
-                            make_float2(__uint_as_float(nx.z), __uint_as_float(nx.w)));
-            me = make_uint4(nx.x, (me.y & ~kStable) + (nx.y & ~kStable), __float_as_uint(t.x),
-                            __float_as_uint(t.y));
-            act = nx.x != kNone;
-            st2[s] = me;
-        } else if (!(me.y & kStable)) {
-            me.y |= kStable;
-            st2[s] = me;
+#pragma unroll
+    for (int r = 0; r < kJumpR; ++r) {
+        long long s = s0 + 256 * r;
+        if (s >= n) continue;
+        if (me[r].x != kNone) {
+            float2 t = cadd(make_float2(__uint_as_float(me[r].z), __uint_as_float(me[r].w)),
+                            make_float2(__uint_as_float(nx[r].z), __uint_as_float(nx[r].w)));
+            st2[s] = make_uint4(nx[r].x, (me[r].y & ~kStable) + (nx[r].y & ~kStable),
+                                __float_as_uint(t.x), __float_as_uint(t.y));
+            act |= nx[r].x != kNone;
+        } else if (!(me[r].y & kStable)) {
+            me[r].y |= kStable;
+            st2[s] = me[r];
         }
     }
     if (__any_sync(0xffffffffu, act) && (threadIdx.x & 31) == 0) *active = 1u;
@@ -397,8 +508,9 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     // the table holds only the links outside the lists
     size_t hsize = 1;
     while (hsize < 2 * (cap - (size_t)m.npairs) + 1024) hsize <<= 1;
-    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_ord, cap * 4) ||
-        ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
+    const size_t walked = (size_t)m.npairs * 4;   // the pair slots the walk wrote
+    if (ensure_keep(c->m_vid, cap * 4, walked, s) || ensure_keep(c->m_j, cap * 4, walked, s) ||
+        ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
         ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) || ensure(c->m_fr[0], cap * 4) ||
         ensure(c->m_fr[1], cap * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
@@ -412,12 +524,9 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.SN = (u32)c->stree.n;
     a.NS = (u32)c->ns;
     a.EN = (u32)(c->diffuse ? c->et.n : 0);
-    a.smeta = c->stree.meta.as<uint4>();
-    a.emeta = c->et.meta.as<uint4>();
     a.svid = c->m_vid.as<u32>();
     a.sj = c->m_j.as<u32>();
     a.sord = c->m_ord.as<u32>();
-    a.pord = c->pord.as<u32>();
     a.off = c->loff.as<u64>();
     a.t0 = t0;
     a.t1 = t1;
@@ -433,8 +542,6 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.fr_in = nullptr;
     a.nf = m.npairs;
     a.nf_out = ctr + C_FRONTIER;
-    k_memo_init<<<grid_for(m.npairs, 256), 256, 0, s>>>(a);
-    ++c->launches;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm <= 0) nsm = 1;
@@ -451,13 +558,19 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         a.fr_out = c->m_fr[cur].as<u32>();
         ST_CUDA(c, cudaMemsetAsync(a.nf_out, 0, sizeof(unsigned long long), s));
         if (timing) cudaEventRecord(c->hev[0], s);
-        switch (c->p.march_group) {
-        case 32: launch_memo_hop<32>(a, s, nsm); break;
-        case 16: launch_memo_hop<16>(a, s, nsm); break;
-        case 4: launch_memo_hop<4>(a, s, nsm); break;
-        case 2: launch_memo_hop<2>(a, s, nsm); break;
-        case 1: launch_memo_hop<1>(a, s, nsm); break;
-        default: launch_memo_hop<8>(a, s, nsm); break;
+        if (!a.fr_in) {   // first level: every pair, row by row
+            long long rows = t1 - t0;
+            k_memo_hop_rows<<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0,
+                              s>>>(a);
+        } else {
+            switch (c->p.march_group) {
+            case 32: launch_memo_hop<32>(a, s, nsm); break;
+            case 16: launch_memo_hop<16>(a, s, nsm); break;
+            case 4: launch_memo_hop<4>(a, s, nsm); break;
+            case 2: launch_memo_hop<2>(a, s, nsm); break;
+            case 1: launch_memo_hop<1>(a, s, nsm); break;
+            default: launch_memo_hop<8>(a, s, nsm); break;
+            }
         }
         if (timing) cudaEventRecord(c->hev[1], s);
         k_memo_link<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
@@ -493,8 +606,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     unsigned *active = c->flags.as<unsigned>() + 12;
     for (int round = 0; round < 40; ++round) {
         ST_CUDA(c, cudaMemsetAsync(active, 0, sizeof(unsigned), s));
-        k_memo_jump<<<grid_for(nslots, 256), 256, 0, s>>>(nslots, c->m_st[b].as<uint4>(),
-                                                          c->m_st[b ^ 1].as<uint4>(), active);
+        k_memo_jump<<<grid_for(nslots, 256 * kJumpR), 256, 0, s>>>(
+            nslots, c->m_st[b].as<uint4>(), c->m_st[b ^ 1].as<uint4>(), active, ctr + C_INTERNAL);
         ++c->launches;
         ST_CUDA(c, cudaGetLastError());
         b ^= 1;
@@ -525,12 +638,16 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     return cuda_check(c, cudaGetLastError(), "k_memo_gamma");
 }
 
-int run_memo(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base)
+int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long long t1,
+             u64 base)
 {
     if (m.npairs == 0) return START_OK;
     // a chunk that does not cover every target cuts chains: more links leave its lists
     bool partial = t0 > 0 || t1 < c->np;
     size_t cap = (size_t)m.npairs + (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
+    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_ord, cap * 4))
+        return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
+    ST_TRY(walk_fill_slots(c, theta, t0, t1, base));
     // an attempt that runs out of slots leaves artefacts (table keys without
     // slots) in the error and fallback counters: restore them before retrying
     unsigned long long *ctr = c->counters.as<unsigned long long>();

@@ -20,7 +20,8 @@
 
 namespace st {
 
-int run_memo(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base);
+int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long long t1,
+             u64 base);
 int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base,
                float conv, float *gout);
 
@@ -33,14 +34,25 @@ struct TreeView {
     u32 n;
 };
 
+// Canonical virtual-source ids (the memoised march's numbering): source-tree
+// nodes, then sources, then emitter-tree nodes, then emitters; a count-1 leaf
+// is its member.  node0 / memb0 are the first ids of this tree's nodes and
+// members.
+struct CanonBase {
+    u32 node0, memb0;
+};
+
 // Entries are emitted in depth-first order; the order key of an entry is
 // (tree tag, node id of the accepted cell or of the leaf holding the member),
-// so every target's row is sorted by it.
-template <bool FILL>
+// so every target's row is sorted by it.  MODE 0 counts, 1 writes raw
+// entries (tree tag | member flag | id), 2 writes canonical ids.
+template <int MODE>
 __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2f, double th2d,
-                                          float cmag, u32 self, u32 tag, u32 i, u32 &c, u64 &w,
-                                          u64 wend, u32 *ent, u32 *tgt, u32 *ord, unsigned &fb)
+                                          float cmag, u32 self, u32 tag, CanonBase cb, u32 i,
+                                          u32 &c, u64 &w, u64 wend, u32 *ent, u32 *tgt, u32 *ord,
+                                          unsigned &fb)
 {
+    constexpr bool FILL = MODE != 0;
     u32 n = 0;
     while (n < t.n) {
         float4 b = t.box[n];
@@ -53,7 +65,10 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
         if (a) {
             if (FILL) {
                 if (w < wend) {   // never past this row
-                    ent[w] = n | tag;
+                    if (MODE == 2)
+                        ent[w] = (mt.w && mt.z == 1u) ? cb.memb0 + mt.y : cb.node0 + n;
+                    else
+                        ent[w] = n | tag;
                     tgt[w] = i;
                     ord[w] = (tag ? 0x80000000u : 0u) | n;
                 }
@@ -67,7 +82,7 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
                 if (r == self) continue;
                 if (FILL) {
                     if (w < wend) {
-                        ent[w] = kEntrySrc | tag | r;
+                        ent[w] = (MODE == 2) ? cb.memb0 + r : (kEntrySrc | tag | r);
                         tgt[w] = i;
                         ord[w] = (tag ? 0x80000000u : 0u) | n;
                     }
@@ -83,13 +98,15 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
     }
 }
 
-template <bool FILL>
+template <int MODE>
 __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, long long t1,
-                                              TreeView st_, TreeView et_, float th2f, double th2d,
+                                              TreeView st_, TreeView et_, CanonBase scb,
+                                              CanonBase ecb, float th2f, double th2d,
                                               float cmag, u32 *cnt, const u64 *off, u64 base,
                                               u32 *ent, u32 *tgt, u32 *ord,
                                               unsigned long long *fb_total)
 {
+    constexpr bool FILL = MODE != 0;
     long long i = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned fb = 0;
     if (i < t1) {
@@ -97,9 +114,10 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
         u32 c = 0;
         u64 w = FILL ? off[i] - base : 0ull;
         const u64 wend = FILL ? off[i + 1] - base : 0ull;
-        walk_tree<FILL>(st_, p, th2f, th2d, cmag, kNone, 0u, (u32)i, c, w, wend, ent, tgt, ord, fb);
-        walk_tree<FILL>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, (u32)i, c, w, wend, ent, tgt,
+        walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, (u32)i, c, w, wend, ent, tgt,
                         ord, fb);
+        walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, (u32)i, c, w, wend,
+                        ent, tgt, ord, fb);
         if (!FILL) cnt[i] = c;
         else if (w != wend) atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
     }
@@ -296,8 +314,9 @@ static int walk_count(start_ctx *c, float theta, const TreeView &sv, const TreeV
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_TRY(ensure(c->lcount, np * sizeof(u32)));
     ST_TRY(ensure(c->loff, (np + 1) * sizeof(u64)));
-    k_walk<false><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), 0, np, sv, ev,
-                                                    theta * theta, (double)theta * (double)theta,
+    k_walk<0><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), 0, np, sv, ev, CanonBase{},
+                                                CanonBase{}, theta * theta,
+                                                (double)theta * (double)theta,
                                                     c->fr.cmag, c->lcount.as<u32>(), nullptr, 0ull,
                                                     nullptr, nullptr, nullptr, ctr + C_WALK_FB);
     ++c->launches;
@@ -314,10 +333,29 @@ static int walk_fill(start_ctx *c, float theta, const TreeView &sv, const TreeVi
                      long long t0, long long t1, u64 base)
 {
     unsigned long long *ctr = c->counters.as<unsigned long long>();
-    k_walk<true><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
-        c->pq.as<float4>(), t0, t1, sv, ev, theta * theta, (double)theta * (double)theta,
-        c->fr.cmag, nullptr, c->loff.as<u64>(), base, c->pent.as<u32>(), c->ptgt.as<u32>(),
-        c->pord.as<u32>(), ctr + C_INTERNAL);
+    k_walk<1><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
+        c->pq.as<float4>(), t0, t1, sv, ev, CanonBase{}, CanonBase{}, theta * theta,
+        (double)theta * (double)theta, c->fr.cmag, nullptr, c->loff.as<u64>(), base,
+        c->pent.as<u32>(), c->ptgt.as<u32>(), c->pord.as<u32>(), ctr + C_INTERNAL);
+    ++c->launches;
+    return cuda_check(c, cudaGetLastError(), "k_walk");
+}
+
+static TreeView source_view(start_ctx *c);
+static TreeView emitter_view(start_ctx *c);
+
+// The memoised march's pair slots of targets [t0, t1): canonical virtual
+// source, target and order key of every pair, written straight into the
+// first slots (vid, j, ord buffers, which the caller sized).
+int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base)
+{
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    u32 SN = (u32)c->stree.n, NS = (u32)c->ns, EN = (u32)(c->diffuse ? c->et.n : 0);
+    CanonBase scb{0u, SN}, ecb{SN + NS, SN + NS + EN};
+    k_walk<2><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
+        c->pq.as<float4>(), t0, t1, source_view(c), emitter_view(c), scb, ecb, theta * theta,
+        (double)theta * (double)theta, c->fr.cmag, nullptr, c->loff.as<u64>(), base,
+        c->m_vid.as<u32>(), c->m_j.as<u32>(), c->m_ord.as<u32>(), ctr + C_INTERNAL);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_walk");
 }
@@ -433,7 +471,8 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     } else {
         chunk_max = total;
     }
-    ST_TRY(ensure_pairs(c, chunk_max));
+    // the memoised march keeps its pairs in its own slot arrays
+    if (c->p.march_mode != 1) ST_TRY(ensure_pairs(c, chunk_max));
     std::vector<unsigned long long> offh;
     if (cut.size() > 2) {
         offh.resize(np + 1);
@@ -447,12 +486,12 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         long long t0 = cut[k], t1 = cut[k + 1];
         u64 base = cut.size() > 2 ? offh[t0] : 0ull;
         long long n = cut.size() > 2 ? (long long)(offh[t1] - offh[t0]) : (long long)total;
-        ST_TRY(walk_fill(c, theta, sv, ev, t0, t1, base));
+        if (c->p.march_mode != 1) ST_TRY(walk_fill(c, theta, sv, ev, t0, t1, base));
         MarchArgs a = march_args(c, n);
         if (n > 0) {
             phase_mark(c, START_PHASE_MARCH, false);
             if (c->p.march_mode == 1) {
-                ST_TRY(run_memo(c, a, t0, t1, base));
+                ST_TRY(run_memo(c, a, theta, t0, t1, base));   // walks the chunk itself
             } else {
                 int nsm = 0;
                 cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);

@@ -158,6 +158,28 @@ def test_gamma_parity_ragged_nonuniform(S, ragged, theta, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+def test_gamma_parity_mixed_neighbour_counts(S, mode):
+    """Every other particle has a 1.8x smoothing length (about 190 neighbours
+    instead of 32), so the first hop of the memoised march takes both its
+    staged path and its global-memory path; two pairs of particles coincide."""
+    w = random_workload(3001, 40, 12, dups=2)
+    w.h = w.h.copy()
+    w.h[::2] *= np.float32(1.8)
+    ctx, orc = make_pair(S, w, march_mode=mode)
+    og, _ = ctx.neighbors()
+    cnt = np.diff(og.astype(np.int64))
+    assert cnt.max() > 64 and cnt.min() <= 64
+    nHI = (w.y0 * 1e-3).astype(np.float32)
+    g = np.zeros(w.n_p, np.float32)
+    ctx.rt_solve(0.6, n_HI=nHI, gamma_out=g)
+    ref = orc.gamma(nHI, 0.6)
+    gamma_close(g, ref)
+    st = ctx.stats()
+    assert st["rays"] == orc.last_stats["rays"]
+    assert st["hops"] == orc.last_stats["hops"]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("group", [1, 4, 16, 32])
 def test_march_group_is_result_neutral(S, cfg1, group, mode):
     ctx = S.Context(march_group=group, ptree_leaf=PTREE_LEAF, march_mode=mode)
