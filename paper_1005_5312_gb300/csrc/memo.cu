@@ -46,7 +46,8 @@ struct __align__(16) HEntry {
 struct MemoArgs {
     MarchArgs m;
     u32 SN, NS, EN;                 // source-tree nodes, sources, emitter-tree nodes
-    u32 *svid, *sj;                 // slot: virtual source id, particle
+    u32 *svid, *sj;                 // slot: virtual source id, particle (the particle of
+                                    // a pair slot is its row's target; not stored)
     u32 *sord;                      // slot: order key of its virtual source (rows are
                                     // sorted by it)
     const u64 *off;                 // row offsets of the chunk's targets (minus base)
@@ -57,10 +58,8 @@ struct MemoArgs {
     float *dl;                      // slot: geometric length of its link
     u32 *ups;                       // frontier item: upstream particle of its hop
     unsigned long long *nslots;     // slots allocated so far
-    const u32 *fr_in;               // frontier (NULL: slots [0, nf))
-    long long nf;
-    u32 *fr_out;
-    unsigned long long *nf_out;
+    u32 fbase;                      // frontier: slots [fbase, fbase + nf) (the links
+    long long nf;                   // claimed by the previous level are contiguous)
     u32 cap;                        // slot capacity
     HEntry *table;
     unsigned long long hmask;
@@ -125,7 +124,7 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
     const long long ngroups = ((long long)gridDim.x * blockDim.x) / G;
     unsigned long long fbs = 0;
     for (long long it = gid; it < a.nf; it += ngroups) {
-        u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
+        u32 s = a.fbase + (u32)it;
         u32 vid = a.svid[s];
         u32 j = a.sj[s];
         float4 src = vsource(a, vid);
@@ -144,26 +143,37 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
     if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
 }
 
-// Pair slot of (vid, k) in the row of target k, or kNone.  Neighbouring
-// targets have nearly the same lists, so the pair usually sits at the same
-// offset as in the row it comes from (guess) or a few entries away; else a
-// binary search on the order key finds the run of entries of the same cell.
-// Within a row the canonical ids are distinct (a row holds a count-1 cell or
-// its member, never both).
-__device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u32 key,
-                                           long long guess_pos)
+// Pair slot of vid in the row [r0, r1) (slot indices), or kNone.  Rows of
+// neighbouring targets hold nearly the same cells in the same order, so the
+// entry sits close to the caller's guess g (the same relative position in the
+// row, scaled by the two rows' lengths: within 8 entries for ~90 % of the
+// links on a uniform 64^3 workload); the 20 entries around g are read at
+// once as five aligned 16-byte vectors, and only a miss falls back to a
+// binary search on the order key (key of the cell holding vid).  Canonical
+// ids within a row are distinct (a row holds a count-1 cell or its member,
+// never both), so a match is the slot.  Reads stay below r1 + 12, inside the
+// slot arrays (their capacity exceeds the pair count by more than that).
+__device__ __forceinline__ u32 find_in_bounds(const MemoArgs &a, u64 r0, u64 r1, u32 vid, u32 key,
+                                              long long g)
 {
-    if ((long long)k < a.t0 || (long long)k >= a.t1) return kNone;   // row not in this chunk
-    u64 r0 = a.off[k] - a.base, r1 = a.off[k + 1] - a.base;
     if (r1 <= r0) return kNone;
-    if (guess_pos >= 0) {
-        u64 g = r0 + (u64)guess_pos;
-        if (g >= r1) g = r1 - 1;
-        if (a.svid[g] == vid) return (u32)g;
-        for (u64 d = 1; d <= 8; ++d) {
-            if (g + d < r1 && a.svid[g + d] == vid) return (u32)(g + d);
-            if (g >= r0 + d && a.svid[g - d] == vid) return (u32)(g - d);
+    if (g >= 0) {
+        long long b = (g - 8) & ~3ll;
+        if (b < 0) b = 0;
+        const uint4 *v4 = reinterpret_cast<const uint4 *>(a.svid + b);
+        uint4 q[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q[k] = v4[k];
+        u32 found = kNone;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            u64 e = (u64)b + 4 * k;
+            if (q[k].x == vid && e >= r0 && e < r1) found = (u32)e;
+            if (q[k].y == vid && e + 1 >= r0 && e + 1 < r1) found = (u32)(e + 1);
+            if (q[k].z == vid && e + 2 >= r0 && e + 2 < r1) found = (u32)(e + 2);
+            if (q[k].w == vid && e + 3 >= r0 && e + 3 < r1) found = (u32)(e + 3);
         }
+        if (found != kNone) return found;
     }
     u64 lo = r0, hi = r1;
     while (lo < hi) {
@@ -176,22 +186,45 @@ __device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u3
     return kNone;
 }
 
+// Guess for the entry at position pos of a row of length len, in a row
+// [r0, r1): the same relative position.
+__device__ __forceinline__ long long row_guess(u64 r0, u64 r1, u64 pos, u64 len)
+{
+    if (r1 <= r0 || len == 0) return -1;
+    u64 g = r0 + (u64)((float)pos * ((float)(r1 - r0) / (float)len));
+    return (long long)(g < r1 ? g : r1 - 1);
+}
+
+// Pair slot of (vid, k) in the row of target k (a row of this chunk), or
+// kNone; pos / len locate the link's own pair in its row (len 0: no guess).
+__device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u32 key, u64 pos,
+                                           u64 len)
+{
+    if ((long long)k < a.t0 || (long long)k >= a.t1) return kNone;   // row not in this chunk
+    u64 r0 = a.off[k] - a.base, r1 = a.off[k + 1] - a.base;
+    return find_in_bounds(a, r0, r1, vid, key, row_guess(r0, r1, pos, len));
+}
+
 // 2a'. the first hop of every pair, one warp per target row: the pairs of
-// target j all evaluate j's neighbour list, so the list is read once, its
-// source-independent terms (r_k - r_j, |r_k - r_j|^2, its rsqrt and root) are
-// staged in shared memory, and each lane takes one pair, scanning the staged
-// candidates (every lane reads the same entry: a broadcast).  The decision
-// is the certified one of hop<G> -- the same FP32 terms and error bounds and
-// the same FP64 re-decision -- so the upstream particle is the same.  Rows
-// with more neighbours than the stage holds take hop<1> from global memory.
-// The walk wrote the pair slots' virtual source, particle and order key.
+// target j all evaluate j's neighbour list, so the list is read once and
+// staged in shared memory with its source-independent terms (r_k - r_j,
+// |r_k - r_j|^2, its rsqrt, the two error-bound coefficients), each
+// neighbour's record and the bounds of its row; each lane takes one pair and
+// scans the staged candidates (every lane reads the same entry: a
+// broadcast).  The decision is hop<G>'s: the same FP32 terms, the same error
+// bounds (their per-neighbour factors folded once), the same FP64
+// re-decision, so the upstream particle is the same.  Rows with more
+// neighbours than the stage holds take hop<1> from global memory.  The walk
+// wrote the pair slots' virtual source, particle and order key.
 constexpr int kRowNB = 64;      // staged neighbours per target
 constexpr int kRowWarps = 8;    // targets per block
 
 __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
 {
     __shared__ float4 nba[kRowWarps][kRowNB];   // (r_k - r_j, rsqrt |r_k - r_j|^2)
-    __shared__ uint4 nbb[kRowWarps][kRowNB];    // (|r_k - r_j|^2, |r_k - r_j|, k, -)
+    __shared__ float4 nbb[kRowWarps][kRowNB];   // (|r_k - r_j|^2, e1, e0, -): bound e1 |b| + e0
+    __shared__ float4 nbp[kRowWarps][kRowNB];   // record of k
+    __shared__ uint4 nbr[kRowWarps][kRowNB];    // (k, row start, row end, -), slot indices
     const float two_eps = 32.f * kU32;
     const float eps_q = 16.f * kU32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -209,20 +242,26 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
             for (u32 b = s0; b < s1; b += 32) {
                 u32 s = b + lane;
                 bool ok = false;
-                float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
-                uint4 B = make_uint4(0u, 0u, 0u, 0u);
+                float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, P = A;
+                uint4 R = make_uint4(0u, 0u, 0u, 0u);
                 if (s < s1) {
                     u32 k = a.m.nb_idx[s];
                     if (k < a.m.np) {
-                        float4 pk = a.m.pq[k];
-                        float ax = pk.x - pj.x, ay = pk.y - pj.y, az = pk.z - pj.z;
+                        P = a.m.pq[k];
+                        float ax = P.x - pj.x, ay = P.y - pj.y, az = P.z - pj.z;
                         float a2 = ax * ax + ay * ay + az * az;
                         if (a2 == 0.f) {
-                            if (pk.x != pj.x || pk.y != pj.y || pk.z != pj.z) odd = true;
+                            if (P.x != pj.x || P.y != pj.y || P.z != pj.z) odd = true;
                         } else {
                             float ra = rsqrtf(a2);
+                            float an = a2 * ra;
                             A = make_float4(ax, ay, az, ra);
-                            B = make_uint4(__float_as_uint(a2), __float_as_uint(a2 * ra), k, 0u);
+                            B = make_float4(a2, eps_q * 2.f * an, eps_q * a2 + 1e-37f, 0.f);
+                            R.x = k;
+                            if ((long long)k >= a.t0 && (long long)k < a.t1) {
+                                R.y = (u32)(a.off[k] - a.base);
+                                R.z = (u32)(a.off[k + 1] - a.base);
+                            }
                             ok = true;
                         }
                     }
@@ -232,6 +271,8 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
                     int q = nst + __popc(m & (me - 1u));
                     nba[w][q] = A;
                     nbb[w][q] = B;
+                    nbp[w][q] = P;
+                    nbr[w][q] = R;
                 }
                 nst += __popc(m);
             }
@@ -239,55 +280,68 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
             __syncwarp();
         }
         for (u64 p = r0 + lane; p < r1; p += 32) {
-            u32 vid = a.svid[p];
-            float4 src = vsource(a, vid);
+            const u32 vid = a.svid[p];
+            const float4 src = vsource(a, vid);
             float dt, dl;
-            u32 up;
+            u32 up, nx = kNone;
             if (staged) {
                 float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
                 float bn = sqrtf(bx * bx + by * by + bz * bz);
                 float bc = -1.f, sc = -1.f;
-                u32 bk = kNone;
+                int bq = -1;
                 bool unsure = odd;
+#pragma unroll 4
                 for (int q = 0; q < nst; ++q) {
                     float4 A = nba[w][q];
-                    uint4 B = nbb[w][q];
-                    float a2 = __uint_as_float(B.x), an = __uint_as_float(B.y);
+                    float4 B = nbb[w][q];
                     float dot = bx * A.x + by * A.y + bz * A.z;
-                    float qv = 2.f * dot - a2;
-                    float eq = eps_q * (2.f * an * bn + a2) + 1e-37f;
-                    if (qv > eq) {
-                        float cv = dot * A.w;
-                        if (cv > bc) {
-                            sc = bc;
-                            bc = cv;
-                            bk = B.z;
-                        } else if (cv > sc) {
-                            sc = cv;
-                        }
-                    } else if (qv >= -eq) {
-                        unsure = true;
-                    }
+                    float qv = 2.f * dot - B.x;
+                    float eq = B.y * bn + B.z;
+                    bool pass = qv > eq;
+                    unsure |= !pass && qv >= -eq;
+                    float cv = pass ? dot * A.w : -2.f;
+                    bool better = cv > bc;
+                    sc = better ? bc : fmaxf(sc, cv);
+                    bc = better ? cv : bc;
+                    bq = better ? q : bq;
                 }
+                u32 mk_global = kNone;   // an FP64 choice that was not staged
                 if (unsure || (sc > 0.f && sc > bc - two_eps * bn)) {
-                    bk = upstream_64<1>(a.m, pj, src, s0, s1, 0, me);
+                    u32 mk = upstream_64<1>(a.m, pj, src, s0, s1, 0, me);
                     ++fbs;
+                    bq = -1;
+                    for (int q = 0; q < nst && mk != kNone; ++q)
+                        if (nbr[w][q].x == mk) bq = q;
+                    if (bq < 0) mk_global = mk;
                 }
-                dt = link_dt(a.m, pj, src, bx, by, bz, bn, bk, dl);
-                up = bk;
+                if (bq < 0 && mk_global != kNone) {
+                    dt = link_dt(a.m, pj, src, bx, by, bz, bn, mk_global, dl);
+                    up = mk_global;
+                    nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
+                } else if (bq < 0) {
+                    dl = bn;
+                    dt = a.m.sig * pj.w * bn;
+                    up = kNone;
+                } else {
+                    // link_dt with the staged record of the upstream particle
+                    float4 pu = nbp[w][bq];
+                    float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
+                    float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
+                    float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+                    dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
+                    dt = a.m.sig * 0.5f * (pj.w + pu.w) * dl;
+                    uint4 R = nbr[w][bq];
+                    up = R.x;
+                    nx = find_in_bounds(a, R.y, R.z, vid, a.sord[p],
+                                        row_guess(R.y, R.z, p - r0, r1 - r0));
+                }
             } else {
                 up = hop<1>(a.m, (u32)i, pj, src, 0, me, dt, fbs, &dl);
+                if (up != kNone) nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
             }
-            // the upstream link is usually the pair (vid, up) of up's row --
-            // a neighbour's row, near this one; only the others go on to
+            // links found in up's row are done; the others go on to
             // k_memo_link, marked so that it skips the row search
-            u32 nx = kNone;
-            if (up != kNone) {
-                nx = find_in_row(a, up, vid, a.sord[p], (long long)(p - r0));
-                a.ups[p] = (nx == kNone) ? (up | kRowMiss) : kNone;
-            } else {
-                a.ups[p] = kNone;
-            }
+            a.ups[p] = (up == kNone || nx != kNone) ? kNone : (up | kRowMiss);
             a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
             a.dl[p] = dl;
             a.nx0[p] = nx;
@@ -299,61 +353,76 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
 
 // 2b. the upstream link of every frontier slot: the pair (v, up) when it is
 // in the row of up, else a slot outside the lists, found in the table or
-// claimed (it joins the next frontier).
-__global__ void k_memo_link(MemoArgs a)
+// claimed (it joins the next frontier).  Slots claimed in a warp take
+// consecutive ids from one counter update.
+__global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
 {
-    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= a.nf) return;
-    u32 up = a.ups[it];
-    if (up == kNone) return;   // chain end, or a link the first-level kernel found
-    bool searched = (up & kRowMiss) != 0;
-    up &= ~kRowMiss;
-    u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
-    u32 vid = a.svid[s];
-    u32 key = a.sord[s];
-    u32 nx = kNone;
-    if (!searched) {
-        long long gpos = -1;
-        if ((long long)s < a.m.npairs) gpos = (long long)(s - (a.off[a.sj[s]] - a.base));
-        nx = find_in_row(a, up, vid, key, gpos);
-    }
-    if (nx == kNone) {
-        unsigned long long lk = link_key(vid, up);
-        unsigned long long h = mix64(lk) & a.hmask;
-        bool placed = false;
-        for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
-            unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
-            if (k == kEmptyKey) {
-                unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
-                if (prev == kEmptyKey) {
-                    unsigned long long ns = atomicAdd(a.nslots, 1ull);
-                    if (ns >= a.cap) {
-                        atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
-                    } else {
-                        a.svid[ns] = vid;
-                        a.sj[ns] = up;
-                        a.sord[ns] = key;
-                        *(volatile unsigned int *)&a.table[h].val = (u32)ns;
-                        a.fr_out[atomicAdd(a.nf_out, 1ull)] = (u32)ns;
-                        nx = (u32)ns;
+    const int lane = threadIdx.x & 31;
+    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    u32 up = it < a.nf ? a.ups[it] : kNone;
+    const bool act = up != kNone;   // else a chain end, or a link the first level found
+    u32 s = 0, vid = 0, key = 0, nx = kNone;
+    unsigned long long hc = 0;      // table entry this thread claimed
+    bool claimed = false;
+    if (act) {
+        bool searched = (up & kRowMiss) != 0;
+        up &= ~kRowMiss;
+        s = a.fbase + (u32)it;
+        vid = a.svid[s];
+        key = a.sord[s];
+        // links of the first level were searched there; later slots sit
+        // in no row, so their search has no guess
+        if (!searched) nx = find_in_row(a, up, vid, key, 0, 0);
+        if (nx == kNone) {
+            unsigned long long lk = link_key(vid, up);
+            unsigned long long h = mix64(lk) & a.hmask;
+            bool placed = false;
+            for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+                unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
+                if (k == kEmptyKey) {
+                    unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
+                    if (prev == kEmptyKey) {
+                        claimed = true;
+                        hc = h;
+                        placed = true;
+                        break;
                     }
+                    k = prev;
+                }
+                if (k == lk) {
+                    u32 v = *(volatile unsigned int *)&a.table[h].val;
+                    nx = (v != kNone) ? v : (kPending | (u32)h);
                     placed = true;
                     break;
                 }
-                k = prev;
+                h = (h + 1) & a.hmask;
             }
-            if (k == lk) {
-                u32 v = *(volatile unsigned int *)&a.table[h].val;
-                nx = (v != kNone) ? v : (kPending | (u32)h);
-                placed = true;
-                break;
-            }
-            h = (h + 1) & a.hmask;
+            if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
         }
-        if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
     }
-    a.state[s].x = nx;
-    a.nx0[s] = nx;
+    const unsigned cm = __ballot_sync(0xffffffffu, claimed);
+    if (cm) {
+        const int leader = __ffs(cm) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(a.nslots, (unsigned long long)__popc(cm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (claimed) {
+            unsigned long long ns = base + __popc(cm & ((1u << lane) - 1u));
+            if (ns >= a.cap) {
+                atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
+            } else {
+                a.svid[ns] = vid;
+                a.sj[ns] = up;
+                a.sord[ns] = key;
+                *(volatile unsigned int *)&a.table[hc].val = (u32)ns;
+                nx = (u32)ns;
+            }
+        }
+    }
+    if (act) {
+        a.state[s].x = nx;
+        a.nx0[s] = nx;
+    }
 }
 
 // Links claimed by another thread during the same launch: read the slot the
@@ -362,7 +431,7 @@ __global__ void k_memo_resolve(MemoArgs a)
 {
     long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= a.nf) return;
-    u32 s = a.fr_in ? a.fr_in[it] : (u32)it;
+    u32 s = a.fbase + (u32)it;
     u32 nx = a.state[s].x;
     if (nx != kNone && (nx & kPending)) {
         u32 v = a.table[nx & ~kPending].val;
@@ -509,10 +578,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     size_t hsize = 1;
     while (hsize < 2 * (cap - (size_t)m.npairs) + 1024) hsize <<= 1;
     const size_t walked = (size_t)m.npairs * 4;   // the pair slots the walk wrote
-    if (ensure_keep(c->m_vid, cap * 4, walked, s) || ensure_keep(c->m_j, cap * 4, walked, s) ||
+    if (ensure_keep(c->m_vid, cap * 4, walked, s) || ensure(c->m_j, cap * 4) ||
         ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
-        ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) || ensure(c->m_fr[0], cap * 4) ||
-        ensure(c->m_fr[1], cap * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
+        ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) ||
+        ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_CUDA(c, cudaMemsetAsync(c->m_table.p, 0xff, hsize * sizeof(HEntry), s));
@@ -539,13 +608,11 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.cap = (u32)cap;
     a.table = c->m_table.as<HEntry>();
     a.hmask = hsize - 1;
-    a.fr_in = nullptr;
+    a.fbase = 0;
     a.nf = m.npairs;
-    a.nf_out = ctr + C_FRONTIER;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm <= 0) nsm = 1;
-    int cur = 0;
     long long iter = 0;
     bool timing = c->p.timing != 0;
     if (timing && !c->hev[0]) {
@@ -554,11 +621,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     }
     double hop_ms = 0.0;
     long long max_iter = m.hop_cap + 1;
+    unsigned long long total = (unsigned long long)m.npairs;   // slots so far
     while (a.nf > 0) {
-        a.fr_out = c->m_fr[cur].as<u32>();
-        ST_CUDA(c, cudaMemsetAsync(a.nf_out, 0, sizeof(unsigned long long), s));
         if (timing) cudaEventRecord(c->hev[0], s);
-        if (!a.fr_in) {   // first level: every pair, row by row
+        if (iter == 0) {   // first level: every pair, row by row
             long long rows = t1 - t0;
             k_memo_hop_rows<<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0,
                               s>>>(a);
@@ -577,23 +643,24 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
         c->launches += 3;
         ST_CUDA(c, cudaGetLastError());
-        // the overflow flag and the next frontier size are adjacent counters
+        // the slot count and the overflow flag are adjacent counters
         unsigned long long both[2] = {0, 0};
-        static_assert(C_FRONTIER == C_MEMO_OVF + 1, "adjacent counters");
-        ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_MEMO_OVF, sizeof(both), cudaMemcpyDeviceToHost, s));
+        static_assert(C_MEMO_OVF == C_SLOTS + 1, "adjacent counters");
+        ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_SLOTS, sizeof(both), cudaMemcpyDeviceToHost, s));
         ST_CUDA(c, cudaStreamSynchronize(s));
         if (timing) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
             else cudaGetLastError();
         }
-        if (both[0]) {
+        if (both[1]) {
             overflow = true;
             return START_OK;
         }
-        a.fr_in = c->m_fr[cur].as<u32>();
-        a.nf = (long long)both[1];
-        cur ^= 1;
+        // the next frontier: the slots this level claimed
+        a.fbase = (u32)total;
+        a.nf = (long long)(both[0] - total);
+        total = both[0];
         if (++iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
     }
     if (timing) c->hop_ms += hop_ms;
@@ -645,7 +712,7 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     // a chunk that does not cover every target cuts chains: more links leave its lists
     bool partial = t0 > 0 || t1 < c->np;
     size_t cap = (size_t)m.npairs + (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
-    if (ensure(c->m_vid, cap * 4) || ensure(c->m_j, cap * 4) || ensure(c->m_ord, cap * 4))
+    if (ensure(c->m_vid, cap * 4) || ensure(c->m_ord, cap * 4))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     ST_TRY(walk_fill_slots(c, theta, t0, t1, base));
     // an attempt that runs out of slots leaves artefacts (table keys without

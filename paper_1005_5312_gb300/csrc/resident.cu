@@ -62,6 +62,15 @@ __global__ void k_res_fill(long long n, const u32 *pos, const u32 *sj, const u32
     rdl[k] = dl[s];
 }
 
+// The particle of every pair slot is the target of its row (one warp per
+// target, coalesced writes); the march does not store it.
+__global__ void k_res_pair_targets(long long np_, const u64 *off, u32 *sj)
+{
+    long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= np_) return;
+    for (u64 e = off[i] + (threadIdx.x & 31); e < off[i + 1]; e += 32) sj[e] = (u32)i;
+}
+
 __global__ void k_res_pairs(long long np_, const u32 *pos, const u32 *svid, u32 *rpos, u32 *rvid)
 {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -177,6 +186,9 @@ int resident_build(start_ctx *c, float theta)
     if (run != S || hh[0] != 0) return set_err(c, START_ECUDA, "internal inconsistency (chain depths)");
     ST_CUDA(c, cudaMemcpyAsync(cursor, start.data(), (D + 2) * sizeof(u32), cudaMemcpyHostToDevice, s));
     k_res_place<<<grid_for(S, 256), 256, 0, s>>>(st, S, cursor, pos.as<u32>());
+    k_res_pair_targets<<<grid_for(c->np * 32, 256), 256, 0, s>>>(c->np, c->loff.as<u64>(),
+                                                                 c->m_j.as<u32>());
+    ++c->launches;
     k_res_fill<<<grid_for(S, 256), 256, 0, s>>>(S, pos.as<u32>(), c->m_j.as<u32>(),
                                                 c->m_nx0.as<u32>(), c->m_dl.as<float>(),
                                                 c->r_j.as<u32>(), c->r_up.as<u32>(),

@@ -42,17 +42,72 @@ struct CanonBase {
     u32 node0, memb0;
 };
 
+// Writers of one target's row.  RawRows stores (raw entry, target, order
+// key) per pair; SlotRows stores (canonical id, order key) and gathers each
+// aligned group of four consecutive entries into one 16-byte store per array
+// (a thread writes its own row, so scalar stores of a warp would touch 32
+// different rows' sectors at once).  Entries arrive in order w = r0, r0+1, ...
+struct RawRows {
+    u32 *ent, *tgt, *ord;
+    u32 i;
+    __device__ __forceinline__ void put(u64 w, u32 e, u32 o)
+    {
+        ent[w] = e;
+        tgt[w] = i;
+        ord[w] = o;
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+struct SlotRows {
+    u32 *ent, *ord;
+    u64 g = 0;            // group (w / 4) of the buffered entries
+    int lo = 0, hi = 0;   // buffered positions [lo, hi) of the group
+    u32 e0 = 0, e1 = 0, e2 = 0, e3 = 0, o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+    __device__ __forceinline__ void flush()
+    {
+        if (hi <= lo) return;
+        u64 b = g * 4;
+        if (lo == 0 && hi == 4) {
+            *reinterpret_cast<uint4 *>(ent + b) = make_uint4(e0, e1, e2, e3);
+            *reinterpret_cast<uint4 *>(ord + b) = make_uint4(o0, o1, o2, o3);
+        } else {
+            if (lo <= 0 && 0 < hi) { ent[b] = e0; ord[b] = o0; }
+            if (lo <= 1 && 1 < hi) { ent[b + 1] = e1; ord[b + 1] = o1; }
+            if (lo <= 2 && 2 < hi) { ent[b + 2] = e2; ord[b + 2] = o2; }
+            if (lo <= 3 && 3 < hi) { ent[b + 3] = e3; ord[b + 3] = o3; }
+        }
+        lo = hi = 0;
+    }
+    __device__ __forceinline__ void put(u64 w, u32 e, u32 o)
+    {
+        u64 gw = w >> 2;
+        int k = (int)(w & 3);
+        if (hi > lo && gw != g) flush();
+        if (hi <= lo) {
+            g = gw;
+            lo = k;
+        }
+        if (k == 0) { e0 = e; o0 = o; }
+        if (k == 1) { e1 = e; o1 = o; }
+        if (k == 2) { e2 = e; o2 = o; }
+        if (k == 3) { e3 = e; o3 = o; }
+        hi = k + 1;
+        if (hi == 4) flush();
+    }
+};
+
 // Entries are emitted in depth-first order; the order key of an entry is
 // (tree tag, node id of the accepted cell or of the leaf holding the member),
 // so every target's row is sorted by it.  MODE 0 counts, 1 writes raw
 // entries (tree tag | member flag | id), 2 writes canonical ids.
-template <int MODE>
+template <int MODE, class Rows>
 __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2f, double th2d,
-                                          float cmag, u32 self, u32 tag, CanonBase cb, u32 i,
-                                          u32 &c, u64 &w, u64 wend, u32 *ent, u32 *tgt, u32 *ord,
-                                          unsigned &fb)
+                                          float cmag, u32 self, u32 tag, CanonBase cb, u32 &c,
+                                          u64 &w, u64 wend, Rows &rows, unsigned &fb)
 {
     constexpr bool FILL = MODE != 0;
+    const u32 okey = tag ? 0x80000000u : 0u;
     u32 n = 0;
     while (n < t.n) {
         float4 b = t.box[n];
@@ -65,12 +120,9 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
         if (a) {
             if (FILL) {
                 if (w < wend) {   // never past this row
-                    if (MODE == 2)
-                        ent[w] = (mt.w && mt.z == 1u) ? cb.memb0 + mt.y : cb.node0 + n;
-                    else
-                        ent[w] = n | tag;
-                    tgt[w] = i;
-                    ord[w] = (tag ? 0x80000000u : 0u) | n;
+                    u32 e = (MODE == 2) ? ((mt.w && mt.z == 1u) ? cb.memb0 + mt.y : cb.node0 + n)
+                                        : (n | tag);
+                    rows.put(w, e, okey | n);
                 }
                 ++w;
             } else {
@@ -81,11 +133,8 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
             for (u32 r = mt.y; r < mt.y + mt.z; ++r) {
                 if (r == self) continue;
                 if (FILL) {
-                    if (w < wend) {
-                        ent[w] = (MODE == 2) ? cb.memb0 + r : (kEntrySrc | tag | r);
-                        tgt[w] = i;
-                        ord[w] = (tag ? 0x80000000u : 0u) | n;
-                    }
+                    if (w < wend)
+                        rows.put(w, (MODE == 2) ? cb.memb0 + r : (kEntrySrc | tag | r), okey | n);
                     ++w;
                 } else {
                     ++c;
@@ -114,10 +163,18 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
         u32 c = 0;
         u64 w = FILL ? off[i] - base : 0ull;
         const u64 wend = FILL ? off[i + 1] - base : 0ull;
-        walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, (u32)i, c, w, wend, ent, tgt,
-                        ord, fb);
-        walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, (u32)i, c, w, wend,
-                        ent, tgt, ord, fb);
+        if (MODE == 2) {
+            SlotRows rows{ent, ord};
+            walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
+            walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, c, w, wend, rows,
+                            fb);
+            rows.flush();
+        } else {
+            RawRows rows{ent, tgt, ord, (u32)i};
+            walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
+            walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, c, w, wend, rows,
+                            fb);
+        }
         if (!FILL) cnt[i] = c;
         else if (w != wend) atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
     }
@@ -345,8 +402,9 @@ static TreeView source_view(start_ctx *c);
 static TreeView emitter_view(start_ctx *c);
 
 // The memoised march's pair slots of targets [t0, t1): canonical virtual
-// source, target and order key of every pair, written straight into the
-// first slots (vid, j, ord buffers, which the caller sized).
+// source and order key of every pair, written straight into the first slots
+// (vid and ord buffers, which the caller sized; the first hop knows each
+// row's target, so the pair slots' particle is not stored).
 int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base)
 {
     unsigned long long *ctr = c->counters.as<unsigned long long>();
@@ -355,7 +413,7 @@ int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 b
     k_walk<2><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), t0, t1, source_view(c), emitter_view(c), scb, ecb, theta * theta,
         (double)theta * (double)theta, c->fr.cmag, nullptr, c->loff.as<u64>(), base,
-        c->m_vid.as<u32>(), c->m_j.as<u32>(), c->m_ord.as<u32>(), ctr + C_INTERNAL);
+        c->m_vid.as<u32>(), nullptr, c->m_ord.as<u32>(), ctr + C_INTERNAL);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_walk");
 }
