@@ -117,7 +117,7 @@ struct start_ctx {
     long long npairs = 0;
 
     // memoised march: per chain link (virtual source, particle)
-    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_table, m_nx0, m_dl;
+    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_table, m_nx0, m_dl;
     long long memo_slots = 0;          // slots of the last memoised chunk
 
     // resident chains (reuse_chains = 1): the link forest of the last full
@@ -157,6 +157,7 @@ enum Counter {
     C_EVALS,      // neighbour-list evaluations performed
     C_SLOTS,      // memoised chain links (virtual source, particle)
     C_MEMO_OVF,   // memo slot capacity exceeded (the host retries larger)
+    C_MISS,       // first-level links not found in their upstream row
     C_COUNT = 16
 };
 

@@ -59,7 +59,10 @@ struct MemoArgs {
     u32 *ups;                       // frontier item: upstream particle of its hop
     unsigned long long *nslots;     // slots allocated so far
     u32 fbase;                      // frontier: slots [fbase, fbase + nf) (the links
-    long long nf;                   // claimed by the previous level are contiguous)
+    long long nf;                   // claimed by the previous level are contiguous),
+    const u32 *fr;                  // or the listed slots fr[0, nf) (first level)
+    u32 *miss;                      // the first level's list of links not found in
+    unsigned long long *nmiss;      // their upstream row, and its length
     u32 cap;                        // slot capacity
     HEntry *table;
     unsigned long long hmask;
@@ -279,72 +282,88 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
             odd = __any_sync(0xffffffffu, odd);
             __syncwarp();
         }
-        for (u64 p = r0 + lane; p < r1; p += 32) {
-            const u32 vid = a.svid[p];
-            const float4 src = vsource(a, vid);
-            float dt, dl;
-            u32 up, nx = kNone;
-            if (staged) {
-                float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
-                float bn = sqrtf(bx * bx + by * by + bz * bz);
-                float bc = -1.f, sc = -1.f;
-                int bq = -1;
-                bool unsure = odd;
-#pragma unroll 4
-                for (int q = 0; q < nst; ++q) {
-                    float4 A = nba[w][q];
-                    float4 B = nbb[w][q];
-                    float dot = bx * A.x + by * A.y + bz * A.z;
-                    float qv = 2.f * dot - B.x;
-                    float eq = B.y * bn + B.z;
-                    bool pass = qv > eq;
-                    unsure |= !pass && qv >= -eq;
-                    float cv = pass ? dot * A.w : -2.f;
-                    bool better = cv > bc;
-                    sc = better ? bc : fmaxf(sc, cv);
-                    bc = better ? cv : bc;
-                    bq = better ? q : bq;
-                }
-                u32 mk_global = kNone;   // an FP64 choice that was not staged
-                if (unsure || (sc > 0.f && sc > bc - two_eps * bn)) {
-                    u32 mk = upstream_64<1>(a.m, pj, src, s0, s1, 0, me);
-                    ++fbs;
-                    bq = -1;
-                    for (int q = 0; q < nst && mk != kNone; ++q)
-                        if (nbr[w][q].x == mk) bq = q;
-                    if (bq < 0) mk_global = mk;
-                }
-                if (bq < 0 && mk_global != kNone) {
-                    dt = link_dt(a.m, pj, src, bx, by, bz, bn, mk_global, dl);
-                    up = mk_global;
-                    nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
-                } else if (bq < 0) {
-                    dl = bn;
-                    dt = a.m.sig * pj.w * bn;
-                    up = kNone;
+        for (u64 p0 = r0; p0 < r1; p0 += 32) {   // warp-uniform: the list append below
+            const u64 p = p0 + lane;
+            const bool valid = p < r1;
+            u32 up = kNone, nx = kNone;
+            if (valid) {
+                const u32 vid = a.svid[p];
+                const float4 src = vsource(a, vid);
+                float dt, dl;
+                if (staged) {
+                    float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
+                    float bn = sqrtf(bx * bx + by * by + bz * bz);
+                    float bc = -1.f, sc = -1.f;
+                    int bq = -1;
+                    bool unsure = odd;
+    #pragma unroll 4
+                    for (int q = 0; q < nst; ++q) {
+                        float4 A = nba[w][q];
+                        float4 B = nbb[w][q];
+                        float dot = bx * A.x + by * A.y + bz * A.z;
+                        float qv = 2.f * dot - B.x;
+                        float eq = B.y * bn + B.z;
+                        bool pass = qv > eq;
+                        unsure |= !pass && qv >= -eq;
+                        float cv = pass ? dot * A.w : -2.f;
+                        bool better = cv > bc;
+                        sc = better ? bc : fmaxf(sc, cv);
+                        bc = better ? cv : bc;
+                        bq = better ? q : bq;
+                    }
+                    u32 mk_global = kNone;   // an FP64 choice that was not staged
+                    if (unsure || (sc > 0.f && sc > bc - two_eps * bn)) {
+                        u32 mk = upstream_64<1>(a.m, pj, src, s0, s1, 0, me);
+                        ++fbs;
+                        bq = -1;
+                        for (int q = 0; q < nst && mk != kNone; ++q)
+                            if (nbr[w][q].x == mk) bq = q;
+                        if (bq < 0) mk_global = mk;
+                    }
+                    if (bq < 0 && mk_global != kNone) {
+                        dt = link_dt(a.m, pj, src, bx, by, bz, bn, mk_global, dl);
+                        up = mk_global;
+                        nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
+                    } else if (bq < 0) {
+                        dl = bn;
+                        dt = a.m.sig * pj.w * bn;
+                        up = kNone;
+                    } else {
+                        // link_dt with the staged record of the upstream particle
+                        float4 pu = nbp[w][bq];
+                        float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
+                        float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
+                        float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+                        dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
+                        dt = a.m.sig * 0.5f * (pj.w + pu.w) * dl;
+                        uint4 R = nbr[w][bq];
+                        up = R.x;
+                        nx = find_in_bounds(a, R.y, R.z, vid, a.sord[p],
+                                            row_guess(R.y, R.z, p - r0, r1 - r0));
+                    }
                 } else {
-                    // link_dt with the staged record of the upstream particle
-                    float4 pu = nbp[w][bq];
-                    float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
-                    float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
-                    float cn = sqrtf(cx * cx + cy * cy + cz * cz);
-                    dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
-                    dt = a.m.sig * 0.5f * (pj.w + pu.w) * dl;
-                    uint4 R = nbr[w][bq];
-                    up = R.x;
-                    nx = find_in_bounds(a, R.y, R.z, vid, a.sord[p],
-                                        row_guess(R.y, R.z, p - r0, r1 - r0));
+                    up = hop<1>(a.m, (u32)i, pj, src, 0, me, dt, fbs, &dl);
+                    if (up != kNone) nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
                 }
-            } else {
-                up = hop<1>(a.m, (u32)i, pj, src, 0, me, dt, fbs, &dl);
-                if (up != kNone) nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
+                a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
+                a.dl[p] = dl;
+                a.nx0[p] = nx;
             }
-            // links found in up's row are done; the others go on to
+            // links found in up's row are done; the others are listed for
             // k_memo_link, marked so that it skips the row search
-            a.ups[p] = (up == kNone || nx != kNone) ? kNone : (up | kRowMiss);
-            a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
-            a.dl[p] = dl;
-            a.nx0[p] = nx;
+            const bool miss = valid && up != kNone && nx == kNone;
+            const unsigned mm = __ballot_sync(0xffffffffu, miss);
+            if (mm) {
+                const int leader = __ffs(mm) - 1;
+                unsigned long long b = 0;
+                if (lane == leader) b = atomicAdd(a.nmiss, (unsigned long long)__popc(mm));
+                b = __shfl_sync(0xffffffffu, b, leader);
+                if (miss) {
+                    unsigned long long q = b + __popc(mm & (me - 1u));
+                    a.miss[q] = (u32)p;
+                    a.ups[q] = up | kRowMiss;
+                }
+            }
         }
     }
     for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
@@ -367,7 +386,7 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
     if (act) {
         bool searched = (up & kRowMiss) != 0;
         up &= ~kRowMiss;
-        s = a.fbase + (u32)it;
+        s = a.fr ? a.fr[it] : a.fbase + (u32)it;
         vid = a.svid[s];
         key = a.sord[s];
         // links of the first level were searched there; later slots sit
@@ -431,7 +450,7 @@ __global__ void k_memo_resolve(MemoArgs a)
 {
     long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= a.nf) return;
-    u32 s = a.fbase + (u32)it;
+    u32 s = a.fr ? a.fr[it] : a.fbase + (u32)it;
     u32 nx = a.state[s].x;
     if (nx != kNone && (nx & kPending)) {
         u32 v = a.table[nx & ~kPending].val;
@@ -581,7 +600,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     if (ensure_keep(c->m_vid, cap * 4, walked, s) || ensure(c->m_j, cap * 4) ||
         ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
         ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) ||
-        ensure(c->m_table, hsize * sizeof(HEntry)))
+        ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_CUDA(c, cudaMemsetAsync(c->m_table.p, 0xff, hsize * sizeof(HEntry), s));
@@ -610,6 +629,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.hmask = hsize - 1;
     a.fbase = 0;
     a.nf = m.npairs;
+    a.fr = nullptr;
+    a.miss = c->m_fr.as<u32>();
+    a.nmiss = ctr + C_MISS;
+    ST_CUDA(c, cudaMemsetAsync(a.nmiss, 0, sizeof(unsigned long long), s));
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm <= 0) nsm = 1;
@@ -639,9 +662,17 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
             }
         }
         if (timing) cudaEventRecord(c->hev[1], s);
-        k_memo_link<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
-        k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
-        c->launches += 3;
+        if (iter == 0) {   // the first level's unresolved links were listed
+            a.fr = a.miss;
+            a.nf = (long long)read_u64(c, a.nmiss);
+        }
+        if (a.nf > 0) {
+            k_memo_link<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
+            k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
+            c->launches += 2;
+        }
+        ++c->launches;
+        a.fr = nullptr;
         ST_CUDA(c, cudaGetLastError());
         // the slot count and the overflow flag are adjacent counters
         unsigned long long both[2] = {0, 0};
