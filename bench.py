@@ -36,7 +36,6 @@ ALGO_BYTES_PER_TARGET = 8    # Gamma out, target record
 # memoised march, per evaluated chain link: the neighbour list (516 B) plus
 # the link's source record (16 B), its hash-table entry (16 B) and its slot
 # state (virtual source, particle, next, tau, links: 16 B)
-ALGO_BYTES_PER_LINK = 516 + 16 + 16 + 16
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -138,10 +137,27 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha(source: str, kernel: str) -> str:
+    """sha256 (16 hex digits) of a kernel's definition text: from its
+    `__global__` line to the matching closing brace."""
+    import hashlib
+    import re
+    text = open(os.path.join(ROOT, "paper_1005_5312_gb300", "csrc", source)).read()
+    m = re.search(r"__global__[^;{]*?\b" + re.escape(kernel) + r"\s*\(", text)
+    if not m:
+        return ""
+    i = text.index("{", m.end())
+    depth = 0
+    for j in range(i, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[j], 0)
+        if depth == 0:
+            return hashlib.sha256(text[m.start():j + 1].encode()).hexdigest()[:16]
+    return ""
+
+
 def traffic_record(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (else None)."""
-    import hashlib
+    the kernel's current definition (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -149,9 +165,7 @@ def traffic_record(kernel: str):
         d = json.load(f).get(kernel)
     if not d:
         return None
-    src = os.path.join(ROOT, "paper_1005_5312_gb300", "csrc", d["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return d if d.get("source_sha") == h else None
+    return d if d.get("kernel_sha") == kernel_source_sha(d["source"], kernel) else None
 
 
 # ---------------------------------------------------------------- reference arm
@@ -354,6 +368,7 @@ def run_gpu(args, w):
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         march_ms, hop_ms, rays, hops, evals, fbs = [], [], [], [], [], []
+        link_ms, jump_ms, jump_bytes, jump_rounds = [], [], [], []
         l0 = ctx.stats()["launches"]
         barrier()
         t_wall = time.perf_counter()
@@ -366,6 +381,10 @@ def run_gpu(args, w):
             st = ctx.stats()
             march_ms.append(tm["march"])
             hop_ms.append(tm["hops"])
+            link_ms.append(tm["link"])
+            jump_ms.append(tm["jump"])
+            jump_bytes.append(st["jump_bytes"])
+            jump_rounds.append(st["jump_rounds"])
             rays.append(st["rays"])
             hops.append(st["hops"])
             evals.append(st["evals"])
@@ -375,7 +394,8 @@ def run_gpu(args, w):
         launches = ctx.stats()["launches"] - l0
         step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
         return dict(step_ms=step_ms, march_ms=march_ms, hop_ms=hop_ms, rays=rays, hops=hops,
-                    evals=evals, fbs=fbs, launches=launches, wall=t_wall)
+                    evals=evals, fbs=fbs, launches=launches, wall=t_wall, link_ms=link_ms,
+                    jump_ms=jump_ms, jump_bytes=jump_bytes, jump_rounds=jump_rounds)
 
     with ClockSampler(local) as clk:
         r1 = timed(args.theta, args.steps, args.warmup)
@@ -394,12 +414,12 @@ def run_gpu(args, w):
     # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
     if args.march_mode == 1:
-        # memoised march: its hop kernel, summed over the frontier launches
-        kern = "k_memo_hop"
-        t_ms = sum(r1["hop_ms"])
-        algo = ALGO_BYTES_PER_LINK * sum(r1["evals"])
-        per_launch = algo / args.steps
-        avg_ms = t_ms / args.steps
+        # memoised march: the pointer-jumping rounds (its largest share of a
+        # step); bytes and durations summed over the timed steps' rounds
+        kern = "k_memo_jump"
+        n_launch = sum(r1["jump_rounds"])
+        per_launch = sum(r1["jump_bytes"]) / n_launch
+        avg_ms = sum(r1["jump_ms"]) / n_launch
     else:
         kern = "k_march"
         algo_l = [ALGO_BYTES_PER_HOP * hp + ALGO_BYTES_PER_RAY * r + ALGO_BYTES_PER_TARGET * w.n_p
@@ -411,8 +431,9 @@ def run_gpu(args, w):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind,
             "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "kernel": kern, "kernel_ms_per_step": avg_ms,
-            "algorithmic_bytes_per_step": per_launch}
+            "kernel": kern, "launch_ms": avg_ms, "algorithmic_bytes_per_launch": per_launch}
+    if args.march_mode == 1:
+        roof["launches_per_step"] = sum(r1["jump_rounds"]) / args.steps
 
     out = {"metric": f"RT rays/s at theta_crit={args.theta}", "value": value, "unit": "rays/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -428,6 +449,9 @@ def run_gpu(args, w):
            "evaluations_per_ray": sum(r1["evals"]) / max(1, sum(r1["rays"])),
            "march_ms_per_step": sum(r1["march_ms"]) / len(r1["march_ms"]),
            "march_fallbacks_per_step": sum(r1["fbs"]) / args.steps,
+           "memo_kernels_ms_per_step": ({
+               "hops": sum(r1["hop_ms"]) / args.steps, "link": sum(r1["link_ms"]) / args.steps,
+               "jump": sum(r1["jump_ms"]) / args.steps} if args.march_mode == 1 else None),
            "gpu_launches": r1["launches"],
            "roofline": roof, "clocks": clk.summary()}
     if r2 is not None:

@@ -135,6 +135,11 @@ typedef struct start_stats {
     long long evals;            /* neighbour-list evaluations performed */
     long long links;            /* distinct chain links (memoised march) */
     long long chunks;           /* target chunks of the last solve */
+    long long jump_rounds;      /* pointer-jumping rounds of the last solve (memoised) */
+    long long jump_bytes;       /* bytes those rounds read and wrote: 16 per slot and
+                                   round (own state), 32 per slot that advanced
+                                   (successor read, write), 16 per slot copied once
+                                   when its chain closed */
 } start_stats;
 
 /* Phases timed when start_params.timing = 1 (milliseconds of the last
@@ -146,7 +151,9 @@ typedef struct start_stats {
 #define START_PHASE_IONIZE 4  /* implicit update */
 #define START_PHASE_EMIT 5    /* diffuse emitters and their moments */
 #define START_PHASE_HOPS 6    /* memoised march: sum of its hop kernels */
-#define START_NPHASES 7
+#define START_PHASE_LINK 7    /* memoised march: sum of its link-resolution kernels */
+#define START_PHASE_JUMP 8    /* memoised march: sum of its pointer-jumping rounds */
+#define START_NPHASES 9
 
 typedef struct start_ctx start_ctx;
 

@@ -44,7 +44,8 @@ class StartParams(C.Structure):
 class StartStats(C.Structure):
     _fields_ = [(n, C.c_longlong) for n in (
         "rays", "hops", "march_fallbacks", "walk_fallbacks", "nbr_fallbacks", "nodes_src",
-        "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches", "evals", "links", "chunks")]
+        "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches", "evals", "links", "chunks",
+        "jump_rounds", "jump_bytes")]
 
 
 class StartError(RuntimeError):
@@ -273,12 +274,16 @@ class Context:
         _check(self.h, lib().start_get_emitter_L(self.h, out.ctypes.data))
         return out[:self.n_p]
 
+    PHASES = ("build", "walk", "march", "gamma", "ionize", "emit", "hops", "link", "jump")
+
     def timings(self) -> dict:
         """Milliseconds of the last build / walk / march / gamma / ionize /
-        emitter phase (needs timing=1)."""
-        ms = (C.c_double * 7)()
-        _check(self.h, lib().start_get_timings(self.h, ms, 7))
-        return dict(zip(("build", "walk", "march", "gamma", "ionize", "emit", "hops"), list(ms)))
+        emitter phase, and of the memoised march's hop, link-resolution and
+        pointer-jumping kernels summed over the last solve (needs timing=1)."""
+        n = len(self.PHASES)
+        ms = (C.c_double * n)()
+        _check(self.h, lib().start_get_timings(self.h, ms, n))
+        return dict(zip(self.PHASES, list(ms)))
 
     def stats(self) -> dict:
         s = StartStats()

@@ -316,7 +316,7 @@ static void release_all(start_ctx *c)
                    &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
                    &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord, &c->m_nx0, &c->m_dl,
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
-                   &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_table};
+                   &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_part, &c->m_table};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);
@@ -324,7 +324,7 @@ static void release_all(start_ctx *c)
     if (c->ev_init)
         for (int k = 0; k < 2 * START_NPHASES; ++k) cudaEventDestroy(c->ev[k]);
     c->ev_init = false;
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 4; ++k)
         if (c->hev[k]) cudaEventDestroy(c->hev[k]);
 }
 
@@ -817,6 +817,8 @@ int start_get_stats(start_ctx *c, start_stats *out)
     out->evals = (long long)v[C_EVALS];
     out->links = (long long)(c->p.march_mode == 1 ? v[C_SLOTS] : 0);
     out->chunks = c->chunks;
+    out->jump_rounds = c->jump_rounds;
+    out->jump_bytes = (long long)c->jump_bytes;
     return START_OK;
 }
 
@@ -827,8 +829,10 @@ int start_get_timings(start_ctx *c, double *ms, int n)
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int k = 0; k < n; ++k) {
         ms[k] = -1.0;
-        if (k == START_PHASE_HOPS) {
-            ms[k] = c->p.march_mode == 1 ? c->hop_ms : -1.0;
+        if (k == START_PHASE_HOPS || k == START_PHASE_LINK || k == START_PHASE_JUMP) {
+            double v = k == START_PHASE_HOPS ? c->hop_ms
+                       : k == START_PHASE_LINK ? c->link_ms : c->jump_ms;
+            ms[k] = c->p.march_mode == 1 ? v : -1.0;
             continue;
         }
         if (c->ev_init && c->ev_rec[k]) {

@@ -117,7 +117,7 @@ struct start_ctx {
     long long npairs = 0;
 
     // memoised march: per chain link (virtual source, particle)
-    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_table, m_nx0, m_dl;
+    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_part, m_table, m_nx0, m_dl;
     long long memo_slots = 0;          // slots of the last memoised chunk
 
     // resident chains (reuse_chains = 1): the link forest of the last full
@@ -142,10 +142,14 @@ struct start_ctx {
     bool ev_init = false;
     bool ev_rec[START_NPHASES] = {};
     double hop_ms = -1.0;                    // summed memo hop kernels (timing = 1)
+    double link_ms = -1.0;                   // summed memo link + resolve kernels
+    double jump_ms = -1.0;                   // summed pointer-jumping rounds
+    long long jump_rounds = 0;               // rounds and algorithmic bytes of the
+    unsigned long long jump_bytes = 0;       // last solve's pointer jumping
     unsigned long long memo_evals = 0, memo_links = 0;   // over the chunks of a solve
     long long chunks = 0;                    // target chunks of the last solve
     int memo_final = 0;                      // buffer holding the final chain sums
-    cudaEvent_t hev[2] = {};
+    cudaEvent_t hev[4] = {};
 };
 
 namespace st {
@@ -158,6 +162,8 @@ enum Counter {
     C_SLOTS,      // memoised chain links (virtual source, particle)
     C_MEMO_OVF,   // memo slot capacity exceeded (the host retries larger)
     C_MISS,       // first-level links not found in their upstream row
+    C_JUMP_ADV,   // pointer jumping: slot updates that read a successor
+    C_JUMP_COPY,  // pointer jumping: closed chains copied to the other buffer
     C_COUNT = 16
 };
 

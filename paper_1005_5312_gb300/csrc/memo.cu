@@ -481,9 +481,13 @@ constexpr u32 kStable = 0x80000000u;
 
 constexpr int kJumpR = 4;   // slots per thread (independent loads in flight)
 
+// part[2 b], part[2 b + 1] accumulate block b's advancing updates and copies
+// over the rounds (plain stores: a block index is unique within a launch and
+// the rounds are stream-ordered), summed once after the last round.
 __global__ void __launch_bounds__(256) k_memo_jump(long long n, const uint4 *__restrict__ st,
                                                     uint4 *__restrict__ st2, unsigned *active,
-                                                    unsigned long long *internal)
+                                                    unsigned long long *ctr,
+                                                    unsigned long long *part)
 {
     const long long s0 = (long long)blockIdx.x * (256 * kJumpR) + threadIdx.x;
     uint4 me[kJumpR], nx[kJumpR];
@@ -492,7 +496,7 @@ __global__ void __launch_bounds__(256) k_memo_jump(long long n, const uint4 *__r
         long long s = s0 + 256 * r;
         me[r] = s < n ? st[s] : make_uint4(kNone, kStable, 0u, 0u);
         if (me[r].x != kNone && (long long)me[r].x >= n) {   // never expected
-            atomicAdd(internal, 1ull);
+            atomicAdd(&ctr[C_INTERNAL], 1ull);
             me[r].x = kNone;
         }
     }
@@ -500,6 +504,7 @@ __global__ void __launch_bounds__(256) k_memo_jump(long long n, const uint4 *__r
     for (int r = 0; r < kJumpR; ++r)
         nx[r] = me[r].x != kNone ? st[me[r].x] : make_uint4(kNone, 0u, 0u, 0u);
     bool act = false;
+    unsigned adv = 0, cpy = 0;
 #pragma unroll
     for (int r = 0; r < kJumpR; ++r) {
         long long s = s0 + 256 * r;
@@ -510,12 +515,64 @@ __global__ void __launch_bounds__(256) k_memo_jump(long long n, const uint4 *__r
             st2[s] = make_uint4(nx[r].x, (me[r].y & ~kStable) + (nx[r].y & ~kStable),
                                 __float_as_uint(t.x), __float_as_uint(t.y));
             act |= nx[r].x != kNone;
+            ++adv;
         } else if (!(me[r].y & kStable)) {
             me[r].y |= kStable;
             st2[s] = me[r];
+            ++cpy;
         }
     }
-    if (__any_sync(0xffffffffu, act) && (threadIdx.x & 31) == 0) *active = 1u;
+    for (int o = 16; o; o >>= 1) {
+        adv += __shfl_xor_sync(0xffffffffu, adv, o);
+        cpy += __shfl_xor_sync(0xffffffffu, cpy, o);
+    }
+    __shared__ unsigned wadv[8], wcpy[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        wadv[wid] = adv;
+        wcpy[wid] = cpy;
+    }
+    if (__any_sync(0xffffffffu, act) && lane == 0) *active = 1u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ba = 0, bc = 0;
+        for (int k = 0; k < 8; ++k) {
+            ba += wadv[k];
+            bc += wcpy[k];
+        }
+        part[2 * blockIdx.x] += ba;
+        part[2 * blockIdx.x + 1] += bc;
+    }
+}
+
+// Sums the per-block pointer-jumping counts into the two counters.
+__global__ void k_memo_jump_sum(const unsigned long long *part, long long nblocks,
+                                unsigned long long *ctr)
+{
+    unsigned long long a = 0, b = 0;
+    for (long long k = threadIdx.x; k < nblocks; k += blockDim.x) {
+        a += part[2 * k];
+        b += part[2 * k + 1];
+    }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    __shared__ unsigned long long sa[32], sb[32];
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ta = 0, tb = 0;
+        for (unsigned k = 0; k < blockDim.x / 32; ++k) {
+            ta += sa[k];
+            tb += sb[k];
+        }
+        ctr[C_JUMP_ADV] = ta;
+        ctr[C_JUMP_COPY] = tb;
+    }
 }
 
 // 4. Gamma of every target from its pairs' chain sums, one warp per target:
@@ -638,11 +695,9 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     if (nsm <= 0) nsm = 1;
     long long iter = 0;
     bool timing = c->p.timing != 0;
-    if (timing && !c->hev[0]) {
-        cudaEventCreate(&c->hev[0]);
-        cudaEventCreate(&c->hev[1]);
-    }
-    double hop_ms = 0.0;
+    if (timing && !c->hev[0])
+        for (int k = 0; k < 4; ++k) cudaEventCreate(&c->hev[k]);
+    double hop_ms = 0.0, link_ms = 0.0, jump_ms = 0.0;
     long long max_iter = m.hop_cap + 1;
     unsigned long long total = (unsigned long long)m.npairs;   // slots so far
     while (a.nf > 0) {
@@ -667,8 +722,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
             a.nf = (long long)read_u64(c, a.nmiss);
         }
         if (a.nf > 0) {
+            if (timing) cudaEventRecord(c->hev[2], s);
             k_memo_link<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
             k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
+            if (timing) cudaEventRecord(c->hev[3], s);
             c->launches += 2;
         }
         ++c->launches;
@@ -683,6 +740,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
             else cudaGetLastError();
+            if (a.nf > 0) {
+                if (cudaEventElapsedTime(&ms, c->hev[2], c->hev[3]) == cudaSuccess) link_ms += ms;
+                else cudaGetLastError();
+            }
         }
         if (both[1]) {
             overflow = true;
@@ -694,7 +755,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         total = both[0];
         if (++iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
     }
-    if (timing) c->hop_ms += hop_ms;
+    if (timing) {
+        c->hop_ms += hop_ms;
+        c->link_ms += link_ms;
+    }
     long long nslots = (long long)read_u64(c, ctr + C_SLOTS);
     c->memo_slots = nslots;
     c->memo_evals += (unsigned long long)nslots;
@@ -702,18 +766,42 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     // pointer jumping
     int b = 0;
     unsigned *active = c->flags.as<unsigned>() + 12;
+    unsigned long long jc[2] = {0, 0};
+    static_assert(C_JUMP_COPY == C_JUMP_ADV + 1, "adjacent counters");
+    const long long jblocks = (long long)grid_for(nslots, 256 * kJumpR);
+    if (ensure(c->m_part, (size_t)jblocks * 16))
+        return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
+    ST_CUDA(c, cudaMemsetAsync(c->m_part.p, 0, (size_t)jblocks * 16, s));
+    long long rounds = 0;
     for (int round = 0; round < 40; ++round) {
         ST_CUDA(c, cudaMemsetAsync(active, 0, sizeof(unsigned), s));
-        k_memo_jump<<<grid_for(nslots, 256 * kJumpR), 256, 0, s>>>(
-            nslots, c->m_st[b].as<uint4>(), c->m_st[b ^ 1].as<uint4>(), active, ctr + C_INTERNAL);
+        if (timing) cudaEventRecord(c->hev[0], s);
+        k_memo_jump<<<(unsigned)jblocks, 256, 0, s>>>(nslots, c->m_st[b].as<uint4>(),
+                                                       c->m_st[b ^ 1].as<uint4>(), active, ctr,
+                                                       c->m_part.as<unsigned long long>());
+        if (timing) cudaEventRecord(c->hev[1], s);
         ++c->launches;
+        ++rounds;
         ST_CUDA(c, cudaGetLastError());
         b ^= 1;
         unsigned act = 0;
         ST_CUDA(c, cudaMemcpyAsync(&act, active, sizeof(act), cudaMemcpyDeviceToHost, s));
         ST_CUDA(c, cudaStreamSynchronize(s));
+        if (timing) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) jump_ms += ms;
+            else cudaGetLastError();
+        }
         if (!act) break;
     }
+    k_memo_jump_sum<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), jblocks, ctr);
+    ++c->launches;
+    ST_CUDA(c, cudaMemcpyAsync(jc, ctr + C_JUMP_ADV, sizeof(jc), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(c, cudaStreamSynchronize(s));
+    c->jump_rounds += rounds;
+    c->jump_bytes += 16ull * (unsigned long long)nslots * (unsigned long long)rounds +
+                     32ull * jc[0] + 16ull * jc[1];
+    if (timing) c->jump_ms += jump_ms;
     c->memo_final = b;
     return START_OK;
 }

@@ -488,7 +488,9 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     cudaStream_t s = c->stream;
     c->npairs = 0;
     c->memo_evals = c->memo_links = 0;
-    c->hop_ms = c->p.timing ? 0.0 : -1.0;
+    c->hop_ms = c->link_ms = c->jump_ms = c->p.timing ? 0.0 : -1.0;
+    c->jump_rounds = 0;
+    c->jump_bytes = 0;
     ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));
     if (np == 0) return START_OK;
     if (c->diffuse) ST_TRY(refresh_emitters(c));

@@ -66,3 +66,14 @@ def test_params_struct_layout_matches_header():
     body = src[src.index("typedef struct start_params"):src.index("} start_params;")]
     fields = re.findall(r"\b(?:int|double|long long|void \*)\s*\**\s*([a-zA-Z_0-9]+);", body)
     assert [f for f, _ in S.StartParams._fields_] == fields
+
+
+def test_stats_struct_layout_and_phases_match_header():
+    import paper_1005_5312_gb300 as S
+    src = open(HEADER).read()
+    body = src[src.index("typedef struct start_stats"):src.index("} start_stats;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\blong long\s+([a-zA-Z_0-9]+);", body)
+    assert [f for f, _ in S.StartStats._fields_] == fields
+    n = int(re.search(r"#define START_NPHASES (\d+)", src).group(1))
+    assert len(S.Context.PHASES) == n
