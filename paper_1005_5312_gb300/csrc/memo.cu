@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(256) k_memo_jump(long long n, const uint4 *__r
 }
 
 // Sums the per-block pointer-jumping counts into the two counters.
-__global__ void k_memo_jump_sum(const unsigned long long *part, long long nblocks,
+__global__ void k_sum_jump_counts(const unsigned long long *part, long long nblocks,
                                 unsigned long long *ctr)
 {
     unsigned long long a = 0, b = 0;
@@ -794,7 +794,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         }
         if (!act) break;
     }
-    k_memo_jump_sum<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), jblocks, ctr);
+    k_sum_jump_counts<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), jblocks, ctr);
     ++c->launches;
     ST_CUDA(c, cudaMemcpyAsync(jc, ctr + C_JUMP_ADV, sizeof(jc), cudaMemcpyDeviceToHost, s));
     ST_CUDA(c, cudaStreamSynchronize(s));
