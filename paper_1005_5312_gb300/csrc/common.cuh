@@ -164,6 +164,7 @@ enum Counter {
     C_MISS,       // first-level links not found in their upstream row
     C_JUMP_ADV,   // pointer jumping: slot updates that read a successor
     C_JUMP_COPY,  // pointer jumping: closed chains copied to the other buffer
+    C_TAIL_CAP,   // memo tail kernel: a chain exceeded the iteration cap
     C_COUNT = 16
 };
 

@@ -444,6 +444,80 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
     }
 }
 
+// 2c. the last levels, once the frontier is small: each thread takes one
+// frontier slot and follows its chain itself -- the hop, then the upstream
+// link in its row or the table; a link it claims becomes its next slot -- so
+// the remaining levels need no launch and no host round trip each.  Links
+// another thread claimed in this launch stay pending and are resolved after
+// it (k_memo_resolve over every slot from fbase on).  A chain longer than
+// max_iter links raises C_TAIL_CAP and stops.
+constexpr long long kTailMax = 1 << 18;   // frontier size that switches to the tail kernel
+
+__global__ void __launch_bounds__(128) k_memo_tail(MemoArgs a, long long max_iter)
+{
+    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= a.nf) return;
+    const unsigned me = 1u << (threadIdx.x & 31);
+    unsigned long long fbs = 0;
+    u32 s = a.fbase + (u32)it;
+    for (long long n = 0;; ++n) {
+        if (n > max_iter) {
+            atomicAdd(&a.m.counters[C_TAIL_CAP], 1ull);
+            break;
+        }
+        const u32 vid = a.svid[s], j = a.sj[s], key = a.sord[s];
+        const float4 src = vsource(a, vid);
+        float dt, dl;
+        const u32 up = hop<1>(a.m, j, a.m.pq[j], src, 0, me, dt, fbs, &dl);
+        u32 nx = kNone;
+        bool claimed = false;
+        if (up != kNone) {
+            nx = find_in_row(a, up, vid, key, 0, 0);
+            if (nx == kNone) {
+                unsigned long long lk = link_key(vid, up);
+                unsigned long long h = mix64(lk) & a.hmask;
+                bool placed = false;
+                for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+                    unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
+                    if (k == kEmptyKey) {
+                        unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
+                        if (prev == kEmptyKey) {
+                            unsigned long long ns = atomicAdd(a.nslots, 1ull);
+                            if (ns >= a.cap) {
+                                atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
+                            } else {
+                                a.svid[ns] = vid;
+                                a.sj[ns] = up;
+                                a.sord[ns] = key;
+                                *(volatile unsigned int *)&a.table[h].val = (u32)ns;
+                                nx = (u32)ns;
+                                claimed = true;
+                            }
+                            placed = true;
+                            break;
+                        }
+                        k = prev;
+                    }
+                    if (k == lk) {
+                        u32 v = *(volatile unsigned int *)&a.table[h].val;
+                        nx = (v != kNone) ? v : (kPending | (u32)h);
+                        placed = true;
+                        break;
+                    }
+                    h = (h + 1) & a.hmask;
+                }
+                if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+            }
+        }
+        a.state[s] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
+        a.dl[s] = dl;
+        a.nx0[s] = nx;
+        if (!claimed) break;
+        s = nx;
+    }
+    if (fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
+}
+
 // Links claimed by another thread during the same launch: read the slot the
 // claimant wrote (visible after the launch boundary).
 __global__ void k_memo_resolve(MemoArgs a)
@@ -701,6 +775,38 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     long long max_iter = m.hop_cap + 1;
     unsigned long long total = (unsigned long long)m.npairs;   // slots so far
     while (a.nf > 0) {
+        if (iter > 0 && a.nf <= kTailMax) {
+            // the remaining levels in one launch, then the pending links
+            if (timing) cudaEventRecord(c->hev[0], s);
+            k_memo_tail<<<grid_for(a.nf, 128), 128, 0, s>>>(a, max_iter);
+            if (timing) cudaEventRecord(c->hev[1], s);
+            ++c->launches;
+            ST_CUDA(c, cudaGetLastError());
+            unsigned long long both[2] = {0, 0};
+            ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_SLOTS, sizeof(both), cudaMemcpyDeviceToHost,
+                                       s));
+            ST_CUDA(c, cudaStreamSynchronize(s));
+            if (both[1]) {
+                overflow = true;
+                return START_OK;
+            }
+            a.nf = (long long)(both[0] - a.fbase);
+            if (timing) cudaEventRecord(c->hev[2], s);
+            k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
+            if (timing) cudaEventRecord(c->hev[3], s);
+            ++c->launches;
+            if (read_u64(c, ctr + C_TAIL_CAP))
+                return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
+            if (timing) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
+                else cudaGetLastError();
+                if (cudaEventElapsedTime(&ms, c->hev[2], c->hev[3]) == cudaSuccess) link_ms += ms;
+                else cudaGetLastError();
+            }
+            total = both[0];
+            break;
+        }
         if (timing) cudaEventRecord(c->hev[0], s);
         if (iter == 0) {   // first level: every pair, row by row
             long long rows = t1 - t0;
