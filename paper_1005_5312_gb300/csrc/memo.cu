@@ -156,55 +156,55 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
 // ids within a row are distinct (a row holds a count-1 cell or its member,
 // never both), so a match is the slot.  Reads stay below r1 + 12, inside the
 // slot arrays (their capacity exceeds the pair count by more than that).
-__device__ __forceinline__ u32 find_in_bounds(const MemoArgs &a, u64 r0, u64 r1, u32 vid, u32 key,
+__device__ __forceinline__ u32 find_in_bounds(const MemoArgs &a, u32 r0, u32 r1, u32 vid, u32 key,
                                               long long g)
 {
     if (r1 <= r0) return kNone;
     if (g >= 0) {
-        long long b = (g - 8) & ~3ll;
-        if (b < 0) b = 0;
+        long long bb = (g - 8) & ~3ll;
+        const u32 b = bb < 0 ? 0u : (u32)bb;
         const uint4 *v4 = reinterpret_cast<const uint4 *>(a.svid + b);
         uint4 q[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) q[k] = v4[k];
-        u32 found = kNone;
+        // matches among the 20 entries, restricted to those inside the row
+        u32 m = 0;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            u64 e = (u64)b + 4 * k;
-            if (q[k].x == vid && e >= r0 && e < r1) found = (u32)e;
-            if (q[k].y == vid && e + 1 >= r0 && e + 1 < r1) found = (u32)(e + 1);
-            if (q[k].z == vid && e + 2 >= r0 && e + 2 < r1) found = (u32)(e + 2);
-            if (q[k].w == vid && e + 3 >= r0 && e + 3 < r1) found = (u32)(e + 3);
-        }
-        if (found != kNone) return found;
+        for (int k = 0; k < 5; ++k)
+            m |= ((u32)(q[k].x == vid) | (u32)(q[k].y == vid) << 1 | (u32)(q[k].z == vid) << 2 |
+                  (u32)(q[k].w == vid) << 3) << (4 * k);
+        const u32 lo = r0 > b ? r0 - b : 0u;                 // < 20 when g >= r0
+        const u32 hi = r1 - b < 20u ? r1 - b : 20u;           // > 0 when g < r1
+        m &= ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+        if (m) return b + (u32)(__ffs(m) - 1);
     }
-    u64 lo = r0, hi = r1;
+    u32 lo = r0, hi = r1;
     while (lo < hi) {
-        u64 mid = lo + ((hi - lo) >> 1);
+        u32 mid = lo + ((hi - lo) >> 1);
         if (a.sord[mid] < key) lo = mid + 1;
         else hi = mid;
     }
-    for (u64 e = lo; e < r1 && a.sord[e] == key; ++e)
-        if (a.svid[e] == vid) return (u32)e;
+    for (u32 e = lo; e < r1 && a.sord[e] == key; ++e)
+        if (a.svid[e] == vid) return e;
     return kNone;
 }
 
 // Guess for the entry at position pos of a row of length len, in a row
 // [r0, r1): the same relative position.
-__device__ __forceinline__ long long row_guess(u64 r0, u64 r1, u64 pos, u64 len)
+__device__ __forceinline__ long long row_guess(u32 r0, u32 r1, u32 pos, u32 len)
 {
     if (r1 <= r0 || len == 0) return -1;
-    u64 g = r0 + (u64)((float)pos * ((float)(r1 - r0) / (float)len));
+    u32 g = r0 + (u32)((float)pos * ((float)(r1 - r0) / (float)len));
     return (long long)(g < r1 ? g : r1 - 1);
 }
 
 // Pair slot of (vid, k) in the row of target k (a row of this chunk), or
 // kNone; pos / len locate the link's own pair in its row (len 0: no guess).
-__device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u32 key, u64 pos,
-                                           u64 len)
+__device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u32 key, u32 pos,
+                                           u32 len)
 {
     if ((long long)k < a.t0 || (long long)k >= a.t1) return kNone;   // row not in this chunk
-    u64 r0 = a.off[k] - a.base, r1 = a.off[k + 1] - a.base;
+    u32 r0 = (u32)(a.off[k] - a.base), r1 = (u32)(a.off[k + 1] - a.base);
     return find_in_bounds(a, r0, r1, vid, key, row_guess(r0, r1, pos, len));
 }
 
@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
                     float bn = sqrtf(bx * bx + by * by + bz * bz);
                     float bc = -1.f, sc = -1.f;
                     int bq = -1;
-                    bool unsure = odd;
-    #pragma unroll 4
+                    float margin = 1.f;   // min |q| - bound: <= 0 when a test is unsure
+#pragma unroll 4
                     for (int q = 0; q < nst; ++q) {
                         float4 A = nba[w][q];
                         float4 B = nbb[w][q];
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
                         float qv = 2.f * dot - B.x;
                         float eq = B.y * bn + B.z;
                         bool pass = qv > eq;
-                        unsure |= !pass && qv >= -eq;
+                        margin = fminf(margin, fabsf(qv) - eq);
                         float cv = pass ? dot * A.w : -2.f;
                         bool better = cv > bc;
                         sc = better ? bc : fmaxf(sc, cv);
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
                         bq = better ? q : bq;
                     }
                     u32 mk_global = kNone;   // an FP64 choice that was not staged
-                    if (unsure || (sc > 0.f && sc > bc - two_eps * bn)) {
+                    if (odd || !(margin > 0.f) || (sc > 0.f && sc > bc - two_eps * bn)) {
                         u32 mk = upstream_64<1>(a.m, pj, src, s0, s1, 0, me);
                         ++fbs;
                         bq = -1;
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
                     if (bq < 0 && mk_global != kNone) {
                         dt = link_dt(a.m, pj, src, bx, by, bz, bn, mk_global, dl);
                         up = mk_global;
-                        nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
+                        nx = find_in_row(a, up, vid, a.sord[p], (u32)(p - r0), (u32)(r1 - r0));
                     } else if (bq < 0) {
                         dl = bn;
                         dt = a.m.sig * pj.w * bn;
@@ -339,11 +339,12 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
                         uint4 R = nbr[w][bq];
                         up = R.x;
                         nx = find_in_bounds(a, R.y, R.z, vid, a.sord[p],
-                                            row_guess(R.y, R.z, p - r0, r1 - r0));
+                                            row_guess(R.y, R.z, (u32)(p - r0), (u32)(r1 - r0)));
                     }
                 } else {
                     up = hop<1>(a.m, (u32)i, pj, src, 0, me, dt, fbs, &dl);
-                    if (up != kNone) nx = find_in_row(a, up, vid, a.sord[p], p - r0, r1 - r0);
+                    if (up != kNone)
+                        nx = find_in_row(a, up, vid, a.sord[p], (u32)(p - r0), (u32)(r1 - r0));
                 }
                 a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
                 a.dl[p] = dl;
@@ -729,7 +730,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     while (hsize < 2 * (cap - (size_t)m.npairs) + 1024) hsize <<= 1;
     const size_t walked = (size_t)m.npairs * 4;   // the pair slots the walk wrote
     if (ensure_keep(c->m_vid, cap * 4, walked, s) || ensure(c->m_j, cap * 4) ||
-        ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
+        ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) ||
+        ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
         ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) ||
         ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
@@ -948,7 +950,8 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int attempt = 0; attempt < 4; ++attempt) {
         if (attempt > 0)
-            ST_CUDA(c, cudaMemcpyAsync(ctr, saved, sizeof(saved), cudaMemcpyHostToDevice, c->stream));
+            ST_CUDA(c, cudaMemcpyAsync(ctr, saved, sizeof(saved), cudaMemcpyHostToDevice,
+                                       c->stream));
         // slot ids and table indices must stay below the pending flag (2^31)
         if (cap >= (1ull << 30)) return set_err(c, START_ERANGE, "too many chain links");
         bool overflow = false;
