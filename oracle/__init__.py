@@ -74,6 +74,9 @@ def _load():
         lib.orc_gamma.restype = ip
         lib.orc_gamma.argtypes = [vp, vp, fp, vp, lp, vp, vp]
         lib.orc_ionize.argtypes = [vp, vp, vp, vp, dp, lp, vp, vp]
+        lib.orc_spline_w.restype = dp
+        lib.orc_spline_w.argtypes = [dp, dp]
+        lib.orc_sph_density.argtypes = [vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -224,6 +227,13 @@ class Oracle:
         self.lib.orc_ionize(self.h_, _p(gamma), _p(n_H), _p(y0), float(dt), n, _p(y1), _p(nHI))
         return y1, nHI
 
+    def sph_density(self, mass):
+        """rho_i = sum_j m_j W(r_ij, h_i) (Section 2.1), input order."""
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+        rho = np.zeros(self.np_)
+        self.lib.orc_sph_density(self.h_, _p(mass), _p(rho))
+        return rho
+
     def step(self, y, n_H, theta: float, dt: float):
         """One operator-split step: Gamma from the step-start state, then the
         implicit update.  Returns (gamma, y1)."""
@@ -233,3 +243,8 @@ class Oracle:
         g = self.gamma(nHI, theta)
         y1, _ = self.ionize(g, n_H, y, dt)
         return g, y1
+
+
+def spline_w(r: float, h: float) -> float:
+    """The oracle's cubic spline kernel W(r, h) (Section 2.1)."""
+    return float(_load().orc_spline_w(float(r), float(h)))

@@ -27,6 +27,9 @@
  *                         ray (Eq. tau), d_tau = sigma dl (n_t + n_up)/2
  *   Gamma                 sum L exp(-tau) / (4 pi r^2) (Eq. solution2 with
  *                         geometric dilution, Eq. ksum / Appendix A)
+ *   SPH density           rho_i = sum_j m_j W(r_ij, h_i) with the standard
+ *                         cubic spline kernel (Section 2.1), over the particle
+ *                         itself and its neighbours (the kernel's support)
  *   ionisation            implicit (backward Euler) hydrogen update
  *                         (Appendix A), with alpha_B on the spot or alpha_A
  *                         plus the self term k_self (Eq. kself1) in the
@@ -703,5 +706,41 @@ void orc_ionize(const orc *o, const double *gamma, const float *nH, const double
         double y = 2.0 * c / (b + sqrt(disc));
         y1[i] = y;
         if (nHI_out) nHI_out[i] = (float)(y * nh);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* SPH density (Section 2.1)                                           */
+
+/* The standard cubic spline of SPH (Monaghan 1992) in three dimensions,
+ * support 2h:  W = 1/(pi h^3) * (1 - 3/2 q^2 + 3/4 q^3)  for 0 <= q < 1,
+ *                  1/(pi h^3) * (2 - q)^3 / 4             for 1 <= q < 2,
+ *                  0 beyond, with q = r / h. */
+double orc_spline_w(double r, double h)
+{
+    double q = r / h;
+    double norm = 1.0 / (ORC_PI * h * h * h);
+    if (q < 1.0) return norm * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+    if (q < 2.0) {
+        double t = 2.0 - q;
+        return norm * 0.25 * t * t * t;
+    }
+    return 0.0;
+}
+
+/* rho_i = sum_j m_j W(|r_i - r_j|, h_i) (Section 2.1): the particle itself
+ * (r = 0) and its neighbours, which are exactly the particles inside the
+ * kernel's support 2 h_i.  mass and rho in input order. */
+void orc_sph_density(const orc *o, const double *mass, double *rho)
+{
+    for (long i = 0; i < o->np; ++i) {
+        double hi = o->h[i];
+        double s = mass[i] * orc_spline_w(0.0, hi);
+        for (long e = o->nb_off[i]; e < o->nb_off[i + 1]; ++e) {
+            long k = o->nb_idx[e];
+            double r = sqrt(d2_64(o->px[k], o->py[k], o->pz[k], o->px[i], o->py[i], o->pz[i]));
+            s += mass[k] * orc_spline_w(r, hi);
+        }
+        rho[i] = s;
     }
 }

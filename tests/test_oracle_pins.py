@@ -527,3 +527,67 @@ def test_stromgren_sphere_and_ifront_law():
     assert abs(r_ion / R_s - 1) < 0.03
     rec = np.sum(ALPHA_B * (n_H * (1 - y)) ** 2 * V * KPC_CM ** 3)
     assert abs(rec / (L / 8) - 1) < 0.06
+
+
+# ---------------------------------------------------------------- SPH density (Section 2.1)
+def test_spline_kernel_is_normalised_with_support_2h():
+    """Any SPH kernel integrates to one over its support; the cubic spline's
+    support is 2h.  Checked by quadrature for two smoothing lengths."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    for h in (1.0, 0.37):
+        val, err = quad(lambda r: oracle.spline_w(r, h) * 4.0 * math.pi * r * r, 0.0, 2.0 * h,
+                        points=[h], epsabs=1e-13, epsrel=1e-13)
+        assert abs(val - 1.0) < 1e-10
+        assert oracle.spline_w(2.0 * h, h) == 0.0 and oracle.spline_w(3.0 * h, h) == 0.0
+
+
+def test_spline_kernel_shape():
+    """The cubic spline's defining values: W(0) = 1/(pi h^3), W(h) = W(0)/4,
+    and W, dW/dq and d2W/dq2 continuous at q = 1 (one-sided differences),
+    dW/dq = 0 at q = 0 and q = 2."""
+    h = 0.8
+    w0 = oracle.spline_w(0.0, h)
+    assert w0 == pytest.approx(1.0 / (math.pi * h ** 3), rel=1e-15)
+    assert oracle.spline_w(h, h) == pytest.approx(0.25 * w0, rel=1e-15)
+    f = lambda q: oracle.spline_w(q * h, h) / w0
+    e = 1e-5
+    d_lo = (f(1.0 - e) - f(1.0 - 2 * e)) / e
+    d_hi = (f(1.0 + 2 * e) - f(1.0 + e)) / e
+    assert d_lo == pytest.approx(-0.75, abs=1e-4) and d_hi == pytest.approx(-0.75, abs=1e-4)
+    c_lo = (f(1.0 - e) - 2 * f(1.0 - 2 * e) + f(1.0 - 3 * e)) / e ** 2
+    c_hi = (f(1.0 + 3 * e) - 2 * f(1.0 + 2 * e) + f(1.0 + e)) / e ** 2
+    assert c_lo == pytest.approx(1.5, abs=1e-3) and c_hi == pytest.approx(1.5, abs=1e-3)
+    assert abs(f(e) - f(0.0)) < 1e-9 and abs(f(2.0 - e)) < 1e-13
+
+
+def test_sph_density_isolated_and_pair():
+    """One particle alone: rho = m W(0).  Two particles closer than 2h: each
+    sees itself and the other, weighted by its own h (Section 2.1)."""
+    pos = np.array([[0.1, 0.9], [0.2, 0.2], [0.3, 0.3]], np.float32)
+    h = np.array([0.5, 0.2], np.float32)   # 2 h_0 = 1.0 > 0.8 = r; 2 h_1 = 0.4 < r
+    o = oracle.Oracle(pos, h, np.zeros((3, 0), np.float32), np.zeros(0), **PHYS)
+    m = np.array([2.0, 3.0])
+    rho = o.sph_density(m)
+    r = float(pos[0, 1]) - float(pos[0, 0])
+    q = r / float(h[0])
+    w = 0.25 * (2.0 - q) ** 3 / (math.pi * float(h[0]) ** 3)
+    assert rho[0] == pytest.approx(2.0 / (math.pi * float(h[0]) ** 3) + 3.0 * w, rel=1e-12)
+    assert rho[1] == pytest.approx(3.0 / (math.pi * float(h[1]) ** 3), rel=1e-15)
+
+
+def test_sph_density_of_a_regular_lattice():
+    """On a regular cubic lattice of spacing dx with about 32 neighbours per
+    kernel (h ~ 1.06 dx), the SPH estimate reproduces the mean density
+    m / dx^3 to well under one per cent away from the edges."""
+    pos = jittered_lattice(16, 1.0, np.random.default_rng(0), 0.0)
+    h = smoothing_lengths(pos)
+    o = oracle.Oracle(pos, h, np.zeros((3, 0), np.float32), np.zeros(0), **PHYS)
+    rho = o.sph_density(np.full(pos.shape[1], 1.5))
+    dx = 1.0 / 16
+    inner = np.all((pos > 3 * dx) & (pos < 1.0 - 3 * dx), axis=0)
+    ratio = rho[inner] * dx ** 3 / 1.5
+    assert inner.sum() == 1000
+    assert np.all(np.abs(ratio - 1.0) < 0.01)
+    # mass enters linearly
+    rho2 = o.sph_density(np.full(pos.shape[1], 3.0))
+    assert np.allclose(rho2, 2.0 * rho, rtol=1e-15)
