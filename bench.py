@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-resident", action="store_true")
     ap.add_argument("--no-diffuse", action="store_true")
+    ap.add_argument("--no-density", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-workers", type=int, default=4)
@@ -260,6 +261,43 @@ def resident_steps(S, w, dev, args, T):
     return {"value": rays / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms / args.steps,
             "note": "links of the first full solve reused; per step: d_tau, chain sums, Gamma, "
                     "implicit update (no tree build, walk or neighbour search)"}
+
+
+# algorithmic bytes of one particle's SPH density: its record, h and CSR
+# offsets, then per neighbour its index, record and mass (33 neighbours in
+# this recipe), the mass gather and the scattered result
+DENSITY_BYTES_PER_NEIGHBOUR = 4 + 16 + 4
+DENSITY_BYTES_PER_PARTICLE = 16 + 4 + 8 + 4 + 4 + 4 + 4
+
+
+def sph_density(S, w, dev, args, T, flush):
+    """SPH density (Section 2.1) of the benchmark particles from device masses,
+    L2 flushed before every timed call."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(stream=stream)
+    ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
+    m = torch.ones(w.n_p, dtype=torch.float32, device=dev)
+    rho = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.sph_density(m, rho)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        ctx.sph_density(m, rho)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    nbr = ctx.stats()["nbr_total"]
+    ctx.close()
+    algo = DENSITY_BYTES_PER_PARTICLE * w.n_p + DENSITY_BYTES_PER_NEIGHBOUR * nbr
+    return {"value": w.n_p / (ms * 1e-3), "unit": "particles/s", "ms_per_call": ms,
+            "neighbours_per_particle": nbr / w.n_p,
+            "algorithmic_GB_per_s": algo / (ms * 1e-3) / 1e9,
+            "note": "two kernels (mass gather to Morton order, density); gathers L2-served"}
 
 
 def diffuse_workload(S, dev, args, T):
@@ -465,6 +503,8 @@ def run_gpu(args, w):
 
     if not args.no_resident:
         out["resident_steps"] = resident_steps(S, w, dev, args, T)
+    if not args.no_density:
+        out["sph_density"] = sph_density(S, w, dev, args, T, flush)
     if not args.no_diffuse:
         out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
 

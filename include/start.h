@@ -208,6 +208,21 @@ int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_ou
  * resident n_HI, and copy y to y_out [n_p] (input order) when not NULL. */
 int start_ionize(start_ctx *c, double dt_s, double *y_out);
 
+/* SPH density of Sec. 2.1 (the step before the path when the density
+ * changes between solves): rho_i = sum_j m_j W(|r_i - r_j|, h_i) over the
+ * particle itself and its neighbours (the particles within 2 h_i of the last
+ * start_build_trees, the support of the kernel), with the standard cubic
+ * spline W(r, h) = 1/(pi h^3) (1 - 3/2 q^2 + 3/4 q^3) for q = r/h < 1,
+ * 1/(pi h^3) (2 - q)^3 / 4 for 1 <= q < 2, 0 beyond.
+ *   mass    [n_p] float32 particle masses (>= 0, finite), input order, host
+ *           or device; read only
+ *   rho_out [n_p] float32, input order, host or device (host: the call
+ *           synchronises); mass units per cubed position unit
+ * FP32 arithmetic (relative error a few 1e-6).  START_ENOTBUILT before
+ * start_build_trees, START_EINVAL for NULL pointers (n_p > 0) or a negative
+ * or non-finite mass. */
+int start_sph_density(start_ctx *c, const float *mass, float *rho_out);
+
 /* Stateless form: build + set_state(n_H = n_HI, y = 1) + solve on a
  * temporary context.  Equivalent to the calls above; p may be NULL. */
 int start_rt_solve_oneshot(const start_params *p, const float *pos, const float *h,

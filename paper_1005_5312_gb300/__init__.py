@@ -75,6 +75,7 @@ def lib():
             "start_set_state": (i, [vp, vp, vp]),
             "start_rt_solve": (i, [vp, vp, f, vp]),
             "start_ionize": (i, [vp, d, vp]),
+            "start_sph_density": (i, [vp, vp, vp]),
             "start_rt_solve_oneshot": (i, [P(StartParams), vp, vp, ll, vp, vp, vp, ll, f, vp]),
             "start_get_frame": (i, [vp, vp]),
             "start_get_perm": (i, [vp, i, vp]),
@@ -161,6 +162,10 @@ def start_ionize(ctx, dt, y_out=None):
     return _check(ctx, lib().start_ionize(ctx, float(dt), _ptr(y_out)))
 
 
+def start_sph_density(ctx, mass, rho_out):
+    return _check(ctx, lib().start_sph_density(ctx, _ptr(mass), _ptr(rho_out)))
+
+
 def start_rt_solve_oneshot(pos, h, n_p, n_HI, src_pos, src_L, n_s, theta, gamma_out,
                            params: StartParams | None = None):
     return _check(None, lib().start_rt_solve_oneshot(
@@ -223,6 +228,21 @@ class Context:
     def ionize(self, dt, y_out=None):
         start_ionize(self.h, dt, y_out)
         return y_out
+
+    def sph_density(self, mass, rho_out=None):
+        """SPH density of every particle (Section 2.1) from float32 masses
+        (input order, host or device); returns rho_out (a new numpy array
+        when None)."""
+        if isinstance(mass, np.ndarray):
+            mass = np.ascontiguousarray(mass, dtype=np.float32)
+        elif hasattr(mass, "dtype") and str(mass.dtype) != "torch.float32":
+            raise TypeError("mass must be float32")
+        if rho_out is None:
+            rho_out = np.zeros(max(self.n_p, 1), np.float32)
+            start_sph_density(self.h, mass, rho_out)
+            return rho_out[:self.n_p]
+        start_sph_density(self.h, mass, rho_out)
+        return rho_out
 
     # introspection (numpy on the host)
     def frame(self):

@@ -310,7 +310,8 @@ static void release_all(start_ctx *c)
     resident_reset(c);
     if (c->r_cap) cudaStreamDestroy(c->r_cap);
     c->r_cap = nullptr;
-    DBuf *all[] = {&c->pq, &c->ph, &c->porig, &c->pinv, &c->pkey, &c->nH, &c->y, &c->V,
+    DBuf *all[] = {&c->pq, &c->ph, &c->porig, &c->pinv, &c->pkey, &c->nH, &c->mass_in,
+                   &c->mass_s, &c->y, &c->V,
                    &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
                    &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,
                    &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
@@ -621,6 +622,32 @@ int start_ionize(start_ctx *c, double dt_s, double *y_out)
         ST_CUDA(c, cudaGetLastError());
         if (!dev) ST_TRY(copy_out(c, y_out, dst, c->np * sizeof(double)));
     }
+    return START_OK;
+}
+
+int start_sph_density(start_ctx *c, const float *mass, float *rho_out)
+{
+    if (!c) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    long long n = c->np;
+    if (n && (!mass || !rho_out)) return set_err(c, START_EINVAL, "NULL mass or rho_out");
+    if (n == 0) return START_OK;
+    DeviceGuard g(c);
+    const float *md = mass;
+    if (!is_device_ptr(mass)) {
+        ST_TRY(stage_in(c, c->mass_in, mass, n * sizeof(float)));
+        md = c->mass_in.as<float>();
+    }
+    bool dev_out = is_device_ptr(rho_out);
+    float *dst = rho_out;
+    if (!dev_out) {
+        ST_TRY(ensure(c->stage, n * sizeof(float)));
+        dst = c->stage.as<float>();
+    }
+    ST_TRY(run_sph_density(c, md, dst));
+    if (read_counter(c, C_BAD_INPUT))
+        return set_err(c, START_EINVAL, "mass must be finite and >= 0");
+    if (!dev_out) ST_TRY(copy_out(c, rho_out, dst, n * sizeof(float)));
     return START_OK;
 }
 

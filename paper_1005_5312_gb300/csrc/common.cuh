@@ -89,6 +89,8 @@ struct start_ctx {
     st::DBuf pinv;    // u32 input index -> sorted rank
     st::DBuf pkey;    // u64 Morton key, input order
     st::DBuf nH;      // float n_H
+    st::DBuf mass_in; // float SPH masses as given (input order), staged
+    st::DBuf mass_s;  // float SPH masses, Morton order
     st::DBuf y;       // double neutral fraction
     st::DBuf V;       // double volume (len_unit^3)
     st::DBuf gam;     // float Gamma (cgs)
@@ -212,6 +214,9 @@ void tree_release(Tree &t);
 
 // neighbors.cu
 int build_neighbours(start_ctx *c);
+
+// density.cu
+int run_sph_density(start_ctx *c, const float *mass_dev, float *rho_dev);
 
 // resident.cu
 void resident_reset(start_ctx *c);
