@@ -77,6 +77,10 @@ def _load():
         lib.orc_spline_w.restype = dp
         lib.orc_spline_w.argtypes = [dp, dp]
         lib.orc_sph_density.argtypes = [vp, vp, vp]
+        lib.orc_h2_fsh.restype = dp
+        lib.orc_h2_fsh.argtypes = [dp]
+        lib.orc_h2_dissociation.restype = ip
+        lib.orc_h2_dissociation.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp]
         _lib = lib
     return _lib
 
@@ -234,6 +238,22 @@ class Oracle:
         self.lib.orc_sph_density(self.h_, _p(mass), _p(rho))
         return rho
 
+    def h2_dissociation(self, nH2, theta: float, kappa: float, targets=None):
+        """k_dis (s^-1) of Appendix B at the targets (input indices, or all);
+        self.last_stats = {rays, hops}."""
+        nH2 = np.ascontiguousarray(nH2, dtype=np.float32)
+        if targets is None:
+            nt, tp = self.np_, None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            nt, tp = len(targets), _p(targets)
+        out = np.zeros(max(nt, 1))
+        st = np.zeros(2, np.int64)
+        self.lib.orc_h2_dissociation(self.h_, _p(nH2), float(theta), float(kappa), tp, nt,
+                                     _p(out), _p(st))
+        self.last_stats = {"rays": int(st[0]), "hops": int(st[1])}
+        return out[:nt]
+
     def step(self, y, n_H, theta: float, dt: float):
         """One operator-split step: Gamma from the step-start state, then the
         implicit update.  Returns (gamma, y1)."""
@@ -248,3 +268,8 @@ class Oracle:
 def spline_w(r: float, h: float) -> float:
     """The oracle's cubic spline kernel W(r, h) (Section 2.1)."""
     return float(_load().orc_spline_w(float(r), float(h)))
+
+
+def h2_fsh(x: float) -> float:
+    """The oracle's H2 self-shielding function f_sh(x) (Appendix B)."""
+    return float(_load().orc_h2_fsh(float(x)))

@@ -385,10 +385,13 @@ static void walk_node(const otree *t, long n, double px, double py, double pz, d
 /* ------------------------------------------------------------------ */
 /* march: Eq. tau and the trapezoidal d_tau (Section 2.2.1)             */
 
-static double march(const orc *o, long i, const double rs[3], const float *nHI, long *hops,
-                    lvec *chain)
+/* Column of the density field `dens` from rs to particle i along the chain,
+ * times `scale`: scale = sigma * len_unit gives tau (Eq. tau, dens = n_HI),
+ * scale = len_unit gives a column density in cm^-2 (Eq. NH2, dens = n_H2). */
+static double march_column(const orc *o, long i, const double rs[3], const float *dens,
+                           double sig, long *hops, lvec *chain)
 {
-    double sig = o->p.sigma_cm2 * o->p.len_unit_cm;   /* per length unit per cm^-3 */
+    const float *nHI = dens;
     long j = i;
     double tau = 0.0;
     long nh = 0;
@@ -422,6 +425,13 @@ static double march(const orc *o, long i, const double rs[3], const float *nHI, 
     }
     if (hops) *hops += nh;
     return tau;
+}
+
+static double march(const orc *o, long i, const double rs[3], const float *nHI, long *hops,
+                    lvec *chain)
+{
+    /* per length unit per cm^-3 */
+    return march_column(o, i, rs, nHI, o->p.sigma_cm2 * o->p.len_unit_cm, hops, chain);
 }
 
 /* ------------------------------------------------------------------ */
@@ -743,4 +753,65 @@ void orc_sph_density(const orc *o, const double *mass, double *rho)
         }
         rho[i] = s;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* H2 photodissociation (Appendix B)                                   */
+
+/* Self-shielding function f_sh(x) = 1 for x <= 1, x^(-3/4) beyond, with
+ * x = N_H2 / 1e14 cm^-2 (Eq. H2ss). */
+double orc_h2_fsh(double x)
+{
+    return x <= 1.0 ? 1.0 : pow(x, -0.75);
+}
+
+/* k_dis (s^-1) at the given targets (input indices; NULL = all): over the
+ * interaction list of the point-source tree, sum 1.13e8 F_LW,0 f_sh(N_H2 /
+ * 1e14 cm^-2) with F_LW,0 = kappa L / (4 pi r^2) (no absorption by H atoms
+ * in the Lyman-Werner band) and N_H2 = N_H2,up + dl (n_H2,up + n_H2,tar)/2
+ * along the same chain as tau (Eq. NH2), closed by n_H2 |r_j - r_s| at the
+ * chain end.  kappa converts a source's ionising photon rate into its LW
+ * specific luminosity.  nH2 in input order; stats = {rays, hops}. */
+int orc_h2_dissociation(const orc *o, const float *nH2, float theta, double kappa,
+                        const long *targets, long nt, double *out, long long *stats)
+{
+    long n = targets ? nt : o->np;
+    long long rays = 0, hops = 0;
+    double th = theta;
+    const otree *t = &o->st;
+    double lu = o->p.len_unit_cm;
+    double rfloor = 1e-6 * o->side;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : rays, hops)
+    for (long q = 0; q < n; ++q) {
+        long i = targets ? targets[q] : q;
+        double k = 0.0;
+        if (t->n) {
+            lvec v = {0};
+            walk_node(t, 0, o->px[i], o->py[i], o->pz[i], th * th, -1, &v);
+            for (long e = 0; e < v.n; ++e) {
+                double rs[3], L;
+                long ent = v.v[e];
+                if (ent >= 0) {
+                    rs[0] = t->cen[3 * ent]; rs[1] = t->cen[3 * ent + 1]; rs[2] = t->cen[3 * ent + 2];
+                    L = t->L[ent];
+                } else {
+                    long j = o->sperm[-ent - 1];
+                    rs[0] = o->sx[j]; rs[1] = o->sy[j]; rs[2] = o->sz[j];
+                    L = o->sL[j];
+                }
+                long nh = 0;
+                double col = march_column(o, i, rs, nH2, lu, &nh, NULL);
+                double r2 = d2_64(o->px[i], o->py[i], o->pz[i], rs[0], rs[1], rs[2]);
+                if (r2 < rfloor * rfloor) r2 = rfloor * rfloor;
+                double F = kappa * L / (4.0 * ORC_PI * r2 * lu * lu);
+                k += 1.13e8 * F * orc_h2_fsh(col / 1e14);
+                rays += 1;
+                hops += nh;
+            }
+            free(v.v);
+        }
+        out[q] = k;
+    }
+    if (stats) { stats[0] = rays; stats[1] = hops; }
+    return 0;
 }

@@ -591,3 +591,67 @@ def test_sph_density_of_a_regular_lattice():
     # mass enters linearly
     rho2 = o.sph_density(np.full(pos.shape[1], 3.0))
     assert np.allclose(rho2, 2.0 * rho, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- H2 photodissociation (Appendix B)
+KDIS_COEF = 1.13e8
+
+
+def test_h2_self_shielding_function():
+    """f_sh(x) = 1 for x <= 1 and x^(-3/4) beyond (Eq. H2ss): continuous at 1."""
+    for x, f in ((0.0, 1.0), (0.3, 1.0), (1.0, 1.0), (16.0, 0.125), (1e4, 1e-3), (81.0, 1.0 / 27.0)):
+        assert oracle.h2_fsh(x) == pytest.approx(f, rel=1e-15)
+    assert oracle.h2_fsh(1.0 + 1e-12) == pytest.approx(1.0, abs=1e-11)
+
+
+def test_h2_column_is_the_trapezoid_along_a_line():
+    """Ten particles on a line at x = 0..9 (2h = 1.5: each sees only its two
+    neighbours), a source at x = -0.5: the chain of particle j is j, j-1, ...,
+    0, so N_H2 = sum_k (n_k + n_(k-1))/2 + n_0 / 2 in length units (Eq. NH2 and
+    the chain-end segment), and k_dis follows from Eq. H2ss."""
+    n = 10
+    pos = np.zeros((3, n), np.float32)
+    pos[0] = np.arange(n, dtype=np.float32)
+    h = np.full(n, 0.75, np.float32)
+    src = np.array([[-0.5], [0.0], [0.0]], np.float32)
+    L = np.array([3e49])
+    o = oracle.Oracle(pos, h, src, L, **PHYS)
+    nH2 = (1e-7 * (1.0 + np.arange(n))).astype(np.float32)
+    kappa = 2.0e-22
+    k = o.h2_dissociation(nH2, 0.5, kappa)
+    nd = nH2.astype(np.float64)
+    for j in range(n):
+        col = 0.5 * nd[0] + sum(0.5 * (nd[q] + nd[q - 1]) for q in range(1, j + 1))
+        N = col * KPC_CM
+        r = (j + 0.5) * KPC_CM
+        x = N / 1e14
+        f = 1.0 if x <= 1.0 else x ** -0.75
+        ref = KDIS_COEF * kappa * 3e49 / (4.0 * math.pi * r * r) * f
+        assert k[j] == pytest.approx(ref, rel=1e-12), j
+    assert o.last_stats["hops"] == sum(j + 1 for j in range(n))
+
+
+def test_h2_dissociation_in_a_uniform_medium_and_optically_thin():
+    """Uniform n_H2: every chain telescopes, N = n_H2 r (as tau = sigma n r), so
+    at theta = 0 k_dis is the direct sum over sources; with n_H2 = 0 there is no
+    shielding.  Both against the straight-line closed form."""
+    o, pos, h, src, L, V = _random_problem(300, 7, 31, box=2.0)
+    d = pos.astype(np.float64)[:, :, None] - src.astype(np.float64)[:, None, :]
+    r = np.sqrt((d ** 2).sum(axis=0)) * KPC_CM
+    kappa = 1e-21
+    for nval in (0.0, 3e-6):
+        nH2 = np.full(300, nval, np.float32)
+        x = np.float64(np.float32(nval)) * r / 1e14
+        f = np.where(x <= 1.0, 1.0, np.maximum(x, 1.0) ** -0.75)
+        ref = (KDIS_COEF * kappa * L[None, :] / (4.0 * math.pi * r * r) * f).sum(axis=1)
+        k = o.h2_dissociation(nH2, 0.0, kappa)
+        assert np.allclose(k, ref, rtol=1e-10, atol=0)
+        assert o.h2_dissociation(nH2, 0.0, 2 * kappa) == pytest.approx(2 * k, rel=1e-14)
+
+
+def test_h2_dissociation_single_source_is_theta_independent():
+    o, pos, h, src, L, V = _random_problem(400, 1, 32, box=2.0)
+    nH2 = np.random.default_rng(5).uniform(0, 1e-5, 400).astype(np.float32)
+    k0 = o.h2_dissociation(nH2, 0.0, 1e-21)
+    k1 = o.h2_dissociation(nH2, 1.0, 1e-21)
+    assert np.array_equal(k0, k1)
