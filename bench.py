@@ -300,6 +300,37 @@ def sph_density(S, w, dev, args, T, flush):
             "note": "two kernels (mass gather to Morton order, density); gathers L2-served"}
 
 
+def h2_dissociation(S, w, dev, args, T, flush):
+    """H2 photodissociation rates (Appendix B) of the benchmark particles: the
+    same walk and memoised chains as the Gamma solve, carrying the H2 column
+    (log-normal n_H2) and the self-shielding function; L2 flushed before every
+    timed call."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(stream=stream, march_group=args.march_group)
+    ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
+    nH2 = T(np.random.default_rng(5).lognormal(np.log(1e-4), 1.5, w.n_p).astype(np.float32))
+    k = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.h2_dissociation(nH2, args.theta, 1e-21, k)
+    torch.cuda.synchronize(dev)
+    ms, rays = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.h2_dissociation(nH2, args.theta, 1e-21, k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += e0.elapsed_time(e1)
+        rays += ctx.stats()["rays"]
+    ctx.close()
+    return {"value": rays / (ms * 1e-3), "unit": "rays/s", "ms_per_call": ms / args.steps,
+            "theta": args.theta, "note": "walk + memoised chains carrying N_H2 + self-shielded "
+                                         "LW flux per pair (no tree build)"}
+
+
 def diffuse_workload(S, dev, args, T):
     """The diffuse-recombination shadowing workload at full size: 128^3
     particles (all emitting), eight 200x clumps, one 3e51/s central source,
@@ -505,6 +536,7 @@ def run_gpu(args, w):
         out["resident_steps"] = resident_steps(S, w, dev, args, T)
     if not args.no_density:
         out["sph_density"] = sph_density(S, w, dev, args, T, flush)
+        out["h2_dissociation"] = h2_dissociation(S, w, dev, args, T, flush)
     if not args.no_diffuse:
         out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
 

@@ -223,6 +223,28 @@ int start_ionize(start_ctx *c, double dt_s, double *y_out);
  * or non-finite mass. */
 int start_sph_density(start_ctx *c, const float *mass, float *rho_out);
 
+/* H2 photodissociation rate of Appendix B for every particle:
+ *   k_dis,i = sum over the interaction list of i (point sources only, the
+ *             walk of start_rt_solve at theta) of
+ *             1.13e8 * F_LW,0 * f_sh(N_H2 / 1e14 cm^-2)  s^-1       (Eq. H2ss)
+ *   f_sh(x) = 1 for x <= 1, x^(-3/4) beyond
+ *   F_LW,0  = kappa_LW * L / (4 pi r^2): Lyman-Werner photons are not
+ *             absorbed by hydrogen atoms, the flux only dilutes
+ *   N_H2    = N_H2,up + dl (n_H2,up + n_H2,tar)/2 along the same upstream
+ *             chain as tau (Eq. NH2), closed by n_H2 |r_j - r_s| at the
+ *             chain end
+ *   n_H2     [n_p] float32 cm^-3 (>= 0, finite), input order, host or device
+ *   kappa_LW LW specific luminosity per ionising photon per second of a
+ *            source (erg s^-1 Hz^-1 per photon s^-1; >= 0): a virtual
+ *            source's LW luminosity is kappa_LW times its L
+ *   kdis_out [n_p] float32 s^-1, input order, host or device
+ * Always uses the memoised march.  The resident Gamma and chemistry state
+ * are unchanged; start_get_stats reports this solve.  START_ENOTBUILT before
+ * start_build_trees; START_EINVAL for NULL pointers, theta < 0, kappa_LW < 0
+ * or a negative or non-finite n_H2. */
+int start_h2_dissociation(start_ctx *c, const float *n_H2, float theta, double kappa_LW,
+                          float *kdis_out);
+
 /* Stateless form: build + set_state(n_H = n_HI, y = 1) + solve on a
  * temporary context.  Equivalent to the calls above; p may be NULL. */
 int start_rt_solve_oneshot(const start_params *p, const float *pos, const float *h,

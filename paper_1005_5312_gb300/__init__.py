@@ -76,6 +76,7 @@ def lib():
             "start_rt_solve": (i, [vp, vp, f, vp]),
             "start_ionize": (i, [vp, d, vp]),
             "start_sph_density": (i, [vp, vp, vp]),
+            "start_h2_dissociation": (i, [vp, vp, f, d, vp]),
             "start_rt_solve_oneshot": (i, [P(StartParams), vp, vp, ll, vp, vp, vp, ll, f, vp]),
             "start_get_frame": (i, [vp, vp]),
             "start_get_perm": (i, [vp, i, vp]),
@@ -166,6 +167,11 @@ def start_sph_density(ctx, mass, rho_out):
     return _check(ctx, lib().start_sph_density(ctx, _ptr(mass), _ptr(rho_out)))
 
 
+def start_h2_dissociation(ctx, n_H2, theta, kappa_LW, kdis_out):
+    return _check(ctx, lib().start_h2_dissociation(ctx, _ptr(n_H2), float(theta), float(kappa_LW),
+                                                   _ptr(kdis_out)))
+
+
 def start_rt_solve_oneshot(pos, h, n_p, n_HI, src_pos, src_L, n_s, theta, gamma_out,
                            params: StartParams | None = None):
     return _check(None, lib().start_rt_solve_oneshot(
@@ -243,6 +249,20 @@ class Context:
             return rho_out[:self.n_p]
         start_sph_density(self.h, mass, rho_out)
         return rho_out
+
+    def h2_dissociation(self, n_H2, theta, kappa_LW, kdis_out=None):
+        """H2 photodissociation rate k_dis (s^-1) of every particle
+        (Appendix B) from float32 n_H2 (input order, host or device)."""
+        if isinstance(n_H2, np.ndarray):
+            n_H2 = np.ascontiguousarray(n_H2, dtype=np.float32)
+        elif hasattr(n_H2, "dtype") and str(n_H2.dtype) != "torch.float32":
+            raise TypeError("n_H2 must be float32")
+        if kdis_out is None:
+            kdis_out = np.zeros(max(self.n_p, 1), np.float32)
+            start_h2_dissociation(self.h, n_H2, theta, kappa_LW, kdis_out)
+            return kdis_out[:self.n_p]
+        start_h2_dissociation(self.h, n_H2, theta, kappa_LW, kdis_out)
+        return kdis_out
 
     # introspection (numpy on the host)
     def frame(self):

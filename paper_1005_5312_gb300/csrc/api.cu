@@ -311,7 +311,7 @@ static void release_all(start_ctx *c)
     if (c->r_cap) cudaStreamDestroy(c->r_cap);
     c->r_cap = nullptr;
     DBuf *all[] = {&c->pq, &c->ph, &c->porig, &c->pinv, &c->pkey, &c->nH, &c->mass_in,
-                   &c->mass_s, &c->y, &c->V,
+                   &c->mass_s, &c->h2_in, &c->w_save, &c->y, &c->V,
                    &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
                    &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,
                    &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
@@ -645,9 +645,40 @@ int start_sph_density(start_ctx *c, const float *mass, float *rho_out)
         dst = c->stage.as<float>();
     }
     ST_TRY(run_sph_density(c, md, dst));
-    if (read_counter(c, C_BAD_INPUT))
-        return set_err(c, START_EINVAL, "mass must be finite and >= 0");
+    ST_TRY(check_bad(c, "mass (must be finite and >= 0)"));
     if (!dev_out) ST_TRY(copy_out(c, rho_out, dst, n * sizeof(float)));
+    return START_OK;
+}
+
+int start_h2_dissociation(start_ctx *c, const float *n_H2, float theta, double kappa_LW,
+                          float *kdis_out)
+{
+    if (!c) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    if (!(theta >= 0.f) || !isfinite(theta)) return set_err(c, START_EINVAL, "theta must be >= 0");
+    if (!(kappa_LW >= 0.0) || !isfinite(kappa_LW))
+        return set_err(c, START_EINVAL, "kappa_LW must be finite and >= 0");
+    long long n = c->np;
+    if (n && (!n_H2 || !kdis_out)) return set_err(c, START_EINVAL, "NULL n_H2 or kdis_out");
+    if (n == 0) return START_OK;
+    DeviceGuard g(c);
+    const float *nd = n_H2;
+    if (!is_device_ptr(n_H2)) {
+        ST_TRY(stage_in(c, c->h2_in, n_H2, n * sizeof(float)));
+        nd = c->h2_in.as<float>();
+    }
+    bool dev_out = is_device_ptr(kdis_out);
+    float *dst = kdis_out;
+    if (!dev_out) {
+        ST_TRY(ensure(c->stage, n * sizeof(float)));
+        dst = c->stage.as<float>();
+    }
+    c->kappa_LW = kappa_LW;
+    ST_TRY(run_h2_dissociation(c, nd, theta, dst));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency");
+    if (read_counter(c, C_CHAIN_OVF)) return set_err(c, START_ECHAIN, "a ray exceeded hop_cap");
+    if (!dev_out) ST_TRY(copy_out(c, kdis_out, dst, n * sizeof(float)));
     return START_OK;
 }
 

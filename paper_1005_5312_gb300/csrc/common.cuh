@@ -79,6 +79,13 @@ struct start_ctx {
     int device = 0;
     std::string err;
     bool built = false, has_state = false, solved = false, diffuse = false;
+    // what the current solve sums over its chains: 0 = Gamma (tau of n_HI,
+    // L e^-tau / 4 pi r^2), 1 = H2 photodissociation (column of n_H2 held
+    // in the records' density slot, self-shielded LW flux); walk_emit: the
+    // emitter tree is walked (diffuse Gamma only)
+    int solve_kind = 0;
+    bool walk_emit = false;
+    double kappa_LW = 0.0;
     long long np = 0, ns = 0;
     st::Frame fr;
 
@@ -91,6 +98,8 @@ struct start_ctx {
     st::DBuf nH;      // float n_H
     st::DBuf mass_in; // float SPH masses as given (input order), staged
     st::DBuf mass_s;  // float SPH masses, Morton order
+    st::DBuf h2_in;   // float n_H2 as given (input order), staged
+    st::DBuf w_save;  // float n_HI of the records while they hold n_H2
     st::DBuf y;       // double neutral fraction
     st::DBuf V;       // double volume (len_unit^3)
     st::DBuf gam;     // float Gamma (cgs)
@@ -217,6 +226,9 @@ int build_neighbours(start_ctx *c);
 
 // density.cu
 int run_sph_density(start_ctx *c, const float *mass_dev, float *rho_dev);
+
+// h2.cu
+int run_h2_dissociation(start_ctx *c, const float *nH2_dev, float theta, float *kdis_dev);
 
 // resident.cu
 void resident_reset(start_ctx *c);

@@ -655,6 +655,10 @@ __global__ void k_sum_jump_counts(const unsigned long long *part, long long nblo
 // the chunk is summed by a fixed butterfly and the chunks are accumulated in
 // list order with compensation -- a deterministic order, so a target's
 // Gamma does not depend on which other targets share its chains.
+// KDIS: the chain sums are H2 columns (cm^-2) and each pair adds
+// L f_sh(N_H2 / 1e14 cm^-2) / (4 pi r^2) (Eq. H2ss) instead of L e^-tau / (4 pi r^2);
+// the resident Gamma (gam) is then left alone.
+template <bool KDIS>
 __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, long long t0,
                                                      long long t1, u64 base, float conv,
                                                      const u32 *porig, float *gam, float *gout)
@@ -676,7 +680,14 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
                 float4 src = vsource(a, a.svid[p]);
                 float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
                 float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
-                v = src.w * expf(-tau) / (12.566370614359172f * r2);
+                float att;
+                if (KDIS) {
+                    float x = tau * 1e-14f;
+                    att = x <= 1.f ? 1.f : powf(x, -0.75f);
+                } else {
+                    att = expf(-tau);
+                }
+                v = src.w * att / (12.566370614359172f * r2);
                 u32 l = st.y & ~kStable;
                 hops += l;
                 maxh = max(maxh, l);
@@ -691,7 +702,7 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
         }
         if (lane == 0) {
             float g = sum * conv;
-            gam[i] = g;
+            if (!KDIS) gam[i] = g;
             if (gout) gout[porig[i]] = g;
         }
     }
@@ -744,7 +755,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.m = m;
     a.SN = (u32)c->stree.n;
     a.NS = (u32)c->ns;
-    a.EN = (u32)(c->diffuse ? c->et.n : 0);
+    a.EN = (u32)(c->walk_emit ? c->et.n : 0);
     a.svid = c->m_vid.as<u32>();
     a.sj = c->m_j.as<u32>();
     a.sord = c->m_ord.as<u32>();
@@ -922,12 +933,18 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     a.m = m;
     a.SN = (u32)c->stree.n;
     a.NS = (u32)c->ns;
-    a.EN = (u32)(c->diffuse ? c->et.n : 0);
+    a.EN = (u32)(c->walk_emit ? c->et.n : 0);
     a.svid = c->m_vid.as<u32>();
     a.state = c->m_st[c->memo_final].as<uint4>();
     long long threads = (t1 - t0) * 32;
-    k_memo_gamma<<<grid_for(threads, 256), 256, 0, c->stream>>>(
-        a, c->loff.as<u64>(), t0, t1, base, conv, c->porig.as<u32>(), c->gam.as<float>(), gout);
+    if (c->solve_kind == 1)
+        k_memo_gamma<true><<<grid_for(threads, 256), 256, 0, c->stream>>>(
+            a, c->loff.as<u64>(), t0, t1, base, conv, c->porig.as<u32>(), c->gam.as<float>(),
+            gout);
+    else
+        k_memo_gamma<false><<<grid_for(threads, 256), 256, 0, c->stream>>>(
+            a, c->loff.as<u64>(), t0, t1, base, conv, c->porig.as<u32>(), c->gam.as<float>(),
+            gout);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_memo_gamma");
 }

@@ -408,7 +408,7 @@ static TreeView emitter_view(start_ctx *c);
 int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base)
 {
     unsigned long long *ctr = c->counters.as<unsigned long long>();
-    u32 SN = (u32)c->stree.n, NS = (u32)c->ns, EN = (u32)(c->diffuse ? c->et.n : 0);
+    u32 SN = (u32)c->stree.n, NS = (u32)c->ns, EN = (u32)(c->walk_emit ? c->et.n : 0);
     CanonBase scb{0u, SN}, ecb{SN + NS, SN + NS + EN};
     k_walk<2><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), t0, t1, source_view(c), emitter_view(c), scb, ecb, theta * theta,
@@ -436,13 +436,14 @@ static TreeView source_view(start_ctx *c)
 static TreeView emitter_view(start_ctx *c)
 {
     return TreeView{c->et.box.as<float4>(), c->et.meta.as<uint4>(), c->et.cube.as<double>(),
-                    (u32)(c->diffuse ? c->et.n : 0)};
+                    (u32)(c->walk_emit ? c->et.n : 0)};
 }
 
 // Interaction lists of every target (all pairs at once; introspection).
 int run_walk(start_ctx *c, float theta)
 {
     c->npairs = 0;
+    c->walk_emit = c->diffuse;
     if (c->np == 0) return START_OK;
     TreeView sv = source_view(c), ev = emitter_view(c);
     unsigned long long total = 0;
@@ -461,7 +462,7 @@ static MarchArgs march_args(start_ctx *c, long long npairs)
     a.np = (u32)c->np;
     a.n_svs = (u32)c->stree.n;
     a.n_ssrc = (u32)c->ns;
-    a.n_evs = (u32)(c->diffuse ? c->et.n : 0);
+    a.n_evs = (u32)(c->walk_emit ? c->et.n : 0);
     a.pq = c->pq.as<float4>();
     a.nb_off = c->nb_off.as<u32>();
     a.nb_idx = c->nb_idx.as<u32>();
@@ -470,7 +471,8 @@ static MarchArgs march_args(start_ctx *c, long long npairs)
     a.ssrc = c->sq.as<float4>();
     a.evsrc = c->et.vsrc.as<float4>();
     a.eLs = c->eLs.as<float>();
-    a.sig = (float)(c->p.sigma_cm2 * c->p.len_unit_cm);
+    // tau (sigma per length unit per cm^-3) or a column in cm^-2
+    a.sig = (float)(c->solve_kind == 1 ? c->p.len_unit_cm : c->p.sigma_cm2 * c->p.len_unit_cm);
     double rf = 1e-6 * c->fr.side;
     a.rfloor2 = (float)(rf * rf);
     a.tau_cut = (float)c->p.tau_cut;
@@ -492,8 +494,11 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     c->jump_rounds = 0;
     c->jump_bytes = 0;
     ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));
+    const bool kdis = c->solve_kind == 1;
+    const bool memo = c->p.march_mode == 1 || kdis;   // k_dis always takes the memoised march
+    c->walk_emit = c->diffuse && !kdis;               // LW photons come from point sources
     if (np == 0) return START_OK;
-    if (c->diffuse) ST_TRY(refresh_emitters(c));
+    if (c->walk_emit) ST_TRY(refresh_emitters(c));
     TreeView sv = source_view(c), ev = emitter_view(c);
     phase_mark(c, START_PHASE_WALK, false);
     unsigned long long total = 0;
@@ -532,7 +537,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         chunk_max = total;
     }
     // the memoised march keeps its pairs in its own slot arrays
-    if (c->p.march_mode != 1) ST_TRY(ensure_pairs(c, chunk_max));
+    if (!memo) ST_TRY(ensure_pairs(c, chunk_max));
     std::vector<unsigned long long> offh;
     if (cut.size() > 2) {
         offh.resize(np + 1);
@@ -541,16 +546,20 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     }
     phase_mark(c, START_PHASE_WALK, true);
     c->chunks = (long long)cut.size() - 1;
-    float conv = (float)(c->p.L_unit / (c->p.len_unit_cm * c->p.len_unit_cm));
+    // L / L_unit / (4 pi r^2), r in length units -> photons cm^-2 s^-1; for
+    // k_dis times 1.13e8 kappa_LW (Eq. H2ss)
+    double conv_d = c->p.L_unit / (c->p.len_unit_cm * c->p.len_unit_cm);
+    if (kdis) conv_d *= 1.13e8 * c->kappa_LW;
+    float conv = (float)conv_d;
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
         long long t0 = cut[k], t1 = cut[k + 1];
         u64 base = cut.size() > 2 ? offh[t0] : 0ull;
         long long n = cut.size() > 2 ? (long long)(offh[t1] - offh[t0]) : (long long)total;
-        if (c->p.march_mode != 1) ST_TRY(walk_fill(c, theta, sv, ev, t0, t1, base));
+        if (!memo) ST_TRY(walk_fill(c, theta, sv, ev, t0, t1, base));
         MarchArgs a = march_args(c, n);
         if (n > 0) {
             phase_mark(c, START_PHASE_MARCH, false);
-            if (c->p.march_mode == 1) {
+            if (memo) {
                 ST_TRY(run_memo(c, a, theta, t0, t1, base));   // walks the chunk itself
             } else {
                 int nsm = 0;
@@ -570,7 +579,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
             phase_mark(c, START_PHASE_MARCH, true);
         }
         phase_mark(c, START_PHASE_GAMMA, false);
-        if (c->p.march_mode == 1 && n > 0) {
+        if (memo && n > 0) {
             ST_TRY(memo_gamma(c, a, t0, t1, base, conv, gout_dev));
         } else {
             k_gamma<<<grid_for(t1 - t0, 256), 256, 0, s>>>(c->pcon.as<float>(), c->loff.as<u64>(),
@@ -581,7 +590,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         phase_mark(c, START_PHASE_GAMMA, true);
         ST_CUDA(c, cudaGetLastError());
     }
-    if (c->p.march_mode == 1) {
+    if (memo) {
         unsigned long long v[2] = {c->memo_evals, c->memo_links};
         ST_CUDA(c, cudaMemcpyAsync(c->counters.as<unsigned long long>() + C_EVALS, v, sizeof(v),
                                    cudaMemcpyHostToDevice, s));

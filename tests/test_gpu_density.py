@@ -99,6 +99,7 @@ def test_density_rejects_bad_input(S):
         ctx.sph_density(m)
     m[5] = 1.0
     assert np.all(np.isfinite(ctx.sph_density(m)))      # usable after the errors
+    ctx.set_state(w.n_H, w.y0)                           # no stale input error left
 
 
 def test_density_full_size_multisource_workload(S):
