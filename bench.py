@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-resident", action="store_true")
     ap.add_argument("--no-diffuse", action="store_true")
     ap.add_argument("--no-density", action="store_true")
+    ap.add_argument("--no-method-error", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-workers", type=int, default=4)
@@ -331,6 +332,43 @@ def h2_dissociation(S, w, dev, args, T, flush):
                                          "LW flux per pair (no tree build)"}
 
 
+def method_error(S, w, dev, args, T):
+    """The method's own error (Section 2.2.2): Gamma at theta = 0.5 and 1.0
+    against theta = 0 (every source individually, the brute-force RSPH sum)
+    on the benchmark particles, for the neutral start and optically thin
+    (n_HI = 0); relative deviations over the particles whose brute-force Gamma
+    exceeds the absolute floor 1e-8 / (sigma dt)."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(stream=stream, march_group=args.march_group, reuse_chains=0)
+    ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
+    floor = 1e-8 / (w.params["sigma_cm2"] * w.dt_s)
+    out = {"floor": floor}
+    for name, nhi in (("neutral", w.n_HI()), ("thin", np.zeros(w.n_p, np.float32))):
+        n_t = T(nhi)
+        g = {}
+        for th in (0.0, 0.5, 1.0):
+            gd = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ctx.rt_solve(th, n_HI=n_t, gamma_out=gd)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            g[th] = gd.double().cpu().numpy()
+            if th == 0.0 and name == "neutral":
+                out["brute_force_rays_per_s"] = ctx.stats()["rays"] / dt
+        ok = g[0.0] > floor
+        res = {"particles": int(ok.sum())}
+        for th in (0.5, 1.0):
+            rel = np.abs(g[th][ok] / g[0.0][ok] - 1.0)
+            res[f"theta_{th}"] = {"median": float(np.median(rel)),
+                                  "p90": float(np.percentile(rel, 90)), "max": float(rel.max())}
+        out[name] = res
+    ctx.close()
+    return out
+
+
 def diffuse_workload(S, dev, args, T):
     """The diffuse-recombination shadowing workload at full size: 128^3
     particles (all emitting), eight 200x clumps, one 3e51/s central source,
@@ -534,6 +572,8 @@ def run_gpu(args, w):
 
     if not args.no_resident:
         out["resident_steps"] = resident_steps(S, w, dev, args, T)
+    if not args.no_method_error:
+        out["method_error"] = method_error(S, w, dev, args, T)
     if not args.no_density:
         out["sph_density"] = sph_density(S, w, dev, args, T, flush)
         out["h2_dissociation"] = h2_dissociation(S, w, dev, args, T, flush)

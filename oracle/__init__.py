@@ -79,6 +79,9 @@ def _load():
         lib.orc_sph_density.argtypes = [vp, vp, vp]
         lib.orc_h2_fsh.restype = dp
         lib.orc_h2_fsh.argtypes = [dp]
+        lib.orc_bb_integrals.argtypes = [dp, dp, vp, vp]
+        lib.orc_gamma_spectral.restype = ip
+        lib.orc_gamma_spectral.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp, vp]
         lib.orc_h2_dissociation.restype = ip
         lib.orc_h2_dissociation.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp]
         _lib = lib
@@ -238,6 +241,23 @@ class Oracle:
         self.lib.orc_sph_density(self.h_, _p(mass), _p(rho))
         return rho
 
+    def gamma_spectral(self, nHI, theta: float, T_eff: float, targets=None):
+        """(Gamma_eff, heating per neutral atom in erg/s) with blackbody point
+        sources at T_eff; self.last_stats = {rays, hops}."""
+        nHI = np.ascontiguousarray(nHI, dtype=np.float32)
+        if targets is None:
+            nt, tp = self.np_, None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            nt, tp = len(targets), _p(targets)
+        g = np.zeros(max(nt, 1))
+        hh = np.zeros(max(nt, 1))
+        st = np.zeros(2, np.int64)
+        self.lib.orc_gamma_spectral(self.h_, _p(nHI), float(theta), float(T_eff), tp, nt, _p(g),
+                                    _p(hh), _p(st))
+        self.last_stats = {"rays": int(st[0]), "hops": int(st[1])}
+        return g[:nt], hh[:nt]
+
     def h2_dissociation(self, nH2, theta: float, kappa: float, targets=None):
         """k_dis (s^-1) of Appendix B at the targets (input indices, or all);
         self.last_stats = {rays, hops}."""
@@ -273,3 +293,10 @@ def spline_w(r: float, h: float) -> float:
 def h2_fsh(x: float) -> float:
     """The oracle's H2 self-shielding function f_sh(x) (Appendix B)."""
     return float(_load().orc_h2_fsh(float(x)))
+
+
+def bb_integrals(tau: float, T_eff: float):
+    """The oracle's (F_ion, F_heat) of one ray at Lyman-limit depth tau."""
+    fi, fh = C.c_double(0.0), C.c_double(0.0)
+    _load().orc_bb_integrals(float(tau), float(T_eff), C.byref(fi), C.byref(fh))
+    return fi.value, fh.value

@@ -815,3 +815,106 @@ int orc_h2_dissociation(const orc *o, const float *nH2, float theta, double kapp
     if (stats) { stats[0] = rays; stats[1] = hops; }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Multi-frequency point sources: photoionisation and photoheating      */
+/* (Appendix A integrals with blackbody sources as in Section 3.1.1)    */
+
+#define ORC_HNU_L_ERG (13.6 * 1.602176634e-12)   /* h nu_L = 13.6 eV */
+#define ORC_KB_ERG 1.380649e-16                  /* Boltzmann constant, erg/K */
+
+/* The spectral integrals of one ray with Lyman-limit optical depth tau, per
+ * ionising photon emitted: with u = nu / nu_L, the blackbody photon spectrum
+ * w(u) = u^2 / (e^(a u) - 1), a = h nu_L / (k T_eff), normalised over u >= 1,
+ * and the hydrogenic cross-section sigma_nu = sigma_L u^-3 (so tau_nu = tau u^-3):
+ *   F_ion(tau)  = int w u^-3 e^(-tau u^-3) du / int w du
+ *   F_heat(tau) = int w u^-3 (u - 1) e^(-tau u^-3) du / int w du
+ * by composite Simpson over [1, 1 + 60/a] (the spectrum beyond is below e^-60
+ * of its peak) with 4096 intervals. */
+static void bb_integrals(double tau, double a, double *f_ion, double *f_heat)
+{
+    const int n = 4096;
+    double umax = 1.0 + 60.0 / a;
+    double du = (umax - 1.0) / n;
+    double z = 0.0, si = 0.0, sh = 0.0;
+    for (int k = 0; k <= n; ++k) {
+        double u = 1.0 + k * du;
+        double wgt = (k == 0 || k == n) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+        double w = u * u / expm1(a * u);
+        double u3 = 1.0 / (u * u * u);
+        double att = exp(-tau * u3);
+        z += wgt * w;
+        si += wgt * w * u3 * att;
+        sh += wgt * w * u3 * (u - 1.0) * att;
+    }
+    *f_ion = si / z;
+    *f_heat = sh / z;
+}
+
+void orc_bb_integrals(double tau, double T_eff, double *f_ion, double *f_heat)
+{
+    bb_integrals(tau, ORC_HNU_L_ERG / (ORC_KB_ERG * T_eff), f_ion, f_heat);
+}
+
+/* Gamma_eff = sum L F_ion(tau) / (4 pi r^2) (photons cm^-2 s^-1 at sigma_L:
+ * k_ion = sigma_L Gamma_eff per neutral atom) and the photoheating rate per
+ * neutral atom H = sigma_L h nu_L sum L F_heat(tau) / (4 pi r^2) (erg/s) over
+ * the point-source list, tau the Lyman-limit optical depth of Eq. tau.  In
+ * the diffuse case the recombination photons stay monochromatic at nu_L (the
+ * emitter tree adds L e^-tau / (4 pi r^2) to Gamma_eff and nothing to H).
+ * stats = {rays, hops}. */
+int orc_gamma_spectral(const orc *o, const float *nHI, float theta, double T_eff,
+                       const long *targets, long nt, double *gamma_out, double *heat_out,
+                       long long *stats)
+{
+    long n = targets ? nt : o->np;
+    long long rays = 0, hops = 0;
+    double th = theta;
+    double a = ORC_HNU_L_ERG / (ORC_KB_ERG * T_eff);
+    const otree *t = &o->st;
+    double lu = o->p.len_unit_cm;
+    double rfloor = 1e-6 * o->side;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : rays, hops)
+    for (long q = 0; q < n; ++q) {
+        long i = targets ? targets[q] : q;
+        double g = 0.0, hsum = 0.0;
+        if (t->n) {
+            lvec v = {0};
+            walk_node(t, 0, o->px[i], o->py[i], o->pz[i], th * th, -1, &v);
+            for (long e = 0; e < v.n; ++e) {
+                double rs[3], L;
+                long ent = v.v[e];
+                if (ent >= 0) {
+                    rs[0] = t->cen[3 * ent]; rs[1] = t->cen[3 * ent + 1]; rs[2] = t->cen[3 * ent + 2];
+                    L = t->L[ent];
+                } else {
+                    long j = o->sperm[-ent - 1];
+                    rs[0] = o->sx[j]; rs[1] = o->sy[j]; rs[2] = o->sz[j];
+                    L = o->sL[j];
+                }
+                long nh = 0;
+                double tau = march(o, i, rs, nHI, &nh, NULL);
+                double r2 = d2_64(o->px[i], o->py[i], o->pz[i], rs[0], rs[1], rs[2]);
+                if (r2 < rfloor * rfloor) r2 = rfloor * rfloor;
+                double fi, fh;
+                bb_integrals(tau, a, &fi, &fh);
+                double flux = L / (4.0 * ORC_PI * r2 * lu * lu);
+                g += flux * fi;
+                hsum += flux * fh;
+                rays += 1;
+                hops += nh;
+            }
+            free(v.v);
+        }
+        if (o->p.diffuse) {
+            long long r = 0, hc = 0;
+            g += gamma_tree(o, 2, i, th, nHI, &r, &hc);
+            rays += r;
+            hops += hc;
+        }
+        gamma_out[q] = g;
+        heat_out[q] = o->p.sigma_cm2 * ORC_HNU_L_ERG * hsum;
+    }
+    if (stats) { stats[0] = rays; stats[1] = hops; }
+    return 0;
+}

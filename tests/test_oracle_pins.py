@@ -655,3 +655,75 @@ def test_h2_dissociation_single_source_is_theta_independent():
     k0 = o.h2_dissociation(nH2, 0.0, 1e-21)
     k1 = o.h2_dissociation(nH2, 1.0, 1e-21)
     assert np.array_equal(k0, k1)
+
+
+# ---------------------------------------------------------------- multi-frequency sources
+HNU_L = 13.6 * 1.602176634e-12
+K_B = 1.380649e-16
+
+
+def _bb_quad(tau, T):
+    """F_ion, F_heat by adaptive quadrature (scipy), independent of the
+    oracle's fixed-grid rule: blackbody photon spectrum u^2/(e^(a u) - 1) over
+    u = nu/nu_L >= 1, cross-section u^-3."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    a = HNU_L / (K_B * T)
+    w = lambda u: u * u / math.expm1(a * u)
+    up = 1.0 + 80.0 / a
+    brk = [1.0 + k / a for k in (1, 3, 10, 30)] + [max(1.0, tau ** (1.0 / 3.0))]
+    brk = sorted(b for b in brk if 1.0 < b < up)
+    z = quad(w, 1.0, up, points=brk, limit=400, epsabs=0, epsrel=1e-12)[0]
+    fi = quad(lambda u: w(u) * u ** -3 * math.exp(-tau * u ** -3), 1.0, up, points=brk, limit=400,
+              epsabs=0, epsrel=1e-12)[0]
+    fh = quad(lambda u: w(u) * u ** -3 * (u - 1.0) * math.exp(-tau * u ** -3), 1.0, up,
+              points=brk, limit=400, epsabs=0, epsrel=1e-12)[0]
+    return fi / z, fh / z
+
+
+@pytest.mark.parametrize("T", [1e5, 3e4])
+def test_spectral_integrals_against_adaptive_quadrature(T):
+    for tau in (0.0, 0.3, 3.0, 30.0, 300.0):
+        fi, fh = oracle.bb_integrals(tau, T)
+        qi, qh = _bb_quad(tau, T)
+        assert fi == pytest.approx(qi, rel=1e-8) and fh == pytest.approx(qh, rel=1e-8), tau
+
+
+def test_spectral_limits_and_hardening():
+    """A cool source is nearly monochromatic just above the Lyman limit:
+    F_ion(0) = <u^-3> is close to (below) one and F_ion(tau) / F_ion(0) ~
+    exp(-tau <u^-3>) (first cumulant of a narrow spectrum); the mean excess
+    energy per absorbed photon, F_heat / F_ion, grows with depth (the
+    spectrum hardens)."""
+    f0 = oracle.bb_integrals(0.0, 2000.0)[0]
+    assert 0.9 < f0 < 1.0
+    for tau in (0.5, 1.0, 2.0):
+        assert oracle.bb_integrals(tau, 2000.0)[0] / f0 == pytest.approx(math.exp(-tau * f0),
+                                                                          rel=2e-3)
+    assert 0.0 < oracle.bb_integrals(0.0, 1e5)[0] < 1.0
+    e = [oracle.bb_integrals(t, 1e5) for t in (0.0, 1.0, 10.0, 100.0, 1000.0)]
+    ratio = [fh / fi for fi, fh in e]
+    assert all(b > a for a, b in zip(ratio, ratio[1:]))
+    assert all(b[0] < a[0] for a, b in zip(e, e[1:]))
+
+
+def test_spectral_gamma_in_a_uniform_medium():
+    """Uniform n_HI at theta = 0: tau_L = sigma n r on every chain, so
+    Gamma_eff = sum L F_ion(sigma n r) / (4 pi r^2) and the heating per neutral
+    atom sigma h nu_L sum L F_heat / (4 pi r^2), with F from adaptive quadrature."""
+    pos, h, src, L = _lattice_problem(8, 2.0, 41, n_s=4)
+    o = oracle.Oracle(pos, h, src, L, **PHYS)
+    n = np.float32(1e-3)
+    nHI = np.full(pos.shape[1], n, np.float32)
+    idx = np.array([0, 77, 300, 511])
+    g, hh = o.gamma_spectral(nHI, 0.0, 1e5, targets=idx)
+    for q, i in enumerate(idx):
+        rg, rh = 0.0, 0.0
+        for s in range(4):
+            r = math.sqrt(sum((float(pos[a, i]) - float(src[a, s])) ** 2 for a in range(3)))
+            tau = SIGMA_CM2 * KPC_CM * float(n) * r
+            fi, fh = _bb_quad(tau, 1e5)
+            flux = L[s] / (4 * math.pi * (r * KPC_CM) ** 2)
+            rg += flux * fi
+            rh += flux * fh
+        assert g[q] == pytest.approx(rg, rel=1e-7)
+        assert hh[q] == pytest.approx(SIGMA_CM2 * HNU_L * rh, rel=1e-7)
