@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-resident", action="store_true")
     ap.add_argument("--no-diffuse", action="store_true")
-    ap.add_argument("--no-density", action="store_true")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the SPH density, H2 photodissociation and blackbody-source lines")
     ap.add_argument("--no-method-error", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=50.0)
@@ -369,6 +370,35 @@ def method_error(S, w, dev, args, T):
     return out
 
 
+def blackbody_sources(S, w, dev, args, T, flush):
+    """The benchmark workload with blackbody point sources (T_eff = 1e5 K, as
+    in Test 1): full solves from built trees, Gamma_eff and the photoheating
+    rate per pair from the spectral tables; L2 flushed before every call."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(stream=stream, march_group=args.march_group, T_eff=1e5)
+    ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
+    ctx.set_state(T(w.n_H), T(w.y0))
+    g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.rt_solve(args.theta, gamma_out=g)
+    torch.cuda.synchronize(dev)
+    ms, rays = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.rt_solve(args.theta, gamma_out=g)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += e0.elapsed_time(e1)
+        rays += ctx.stats()["rays"]
+    ctx.close()
+    return {"value": rays / (ms * 1e-3), "unit": "rays/s", "ms_per_call": ms / args.steps,
+            "theta": args.theta, "T_eff": 1e5,
+            "note": "walk + memoised chains + spectral Gamma and heating per pair (no tree build)"}
+
+
 def diffuse_workload(S, dev, args, T):
     """The diffuse-recombination shadowing workload at full size: 128^3
     particles (all emitting), eight 200x clumps, one 3e51/s central source,
@@ -574,9 +604,10 @@ def run_gpu(args, w):
         out["resident_steps"] = resident_steps(S, w, dev, args, T)
     if not args.no_method_error:
         out["method_error"] = method_error(S, w, dev, args, T)
-    if not args.no_density:
+    if not args.no_next:
         out["sph_density"] = sph_density(S, w, dev, args, T, flush)
         out["h2_dissociation"] = h2_dissociation(S, w, dev, args, T, flush)
+        out["blackbody_sources"] = blackbody_sources(S, w, dev, args, T, flush)
     if not args.no_diffuse:
         out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
 

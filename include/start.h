@@ -117,6 +117,17 @@ typedef struct start_params {
                               shared only within a chunk */
     long long spin_cap;    /* max iterations of any device wait (reserved) */
     void *stream;          /* cudaStream_t to issue work on (NULL = default) */
+    double T_eff;          /* 0: monochromatic sources at the Lyman limit (sigma_cm2);
+                              else the point sources radiate blackbody spectra of
+                              this temperature (K, 500 to 1e7; Test 1 uses 1e5):
+                              Gamma becomes sum L F_ion(tau) / (4 pi r^2) and a
+                              photoheating rate is kept (start_get_heating) --
+                              the photoionisation and photoheating integrals of
+                              Appendix A with the hydrogenic cross-section
+                              sigma_nu = sigma_cm2 (nu/nu_L)^-3, tau the
+                              Lyman-limit depth of the chain.  L stays the
+                              ionising photon rate.  Uses the memoised march;
+                              reuse_chains is ignored */
 } start_params;
 
 /* Counters of the last start_rt_solve. */
@@ -222,6 +233,16 @@ int start_ionize(start_ctx *c, double dt_s, double *y_out);
  * start_build_trees, START_EINVAL for NULL pointers (n_p > 0) or a negative
  * or non-finite mass. */
 int start_sph_density(start_ctx *c, const float *mass, float *rho_out);
+
+/* Photoheating rate per neutral hydrogen atom (erg/s), input order, of the
+ * last start_rt_solve: sigma_L h nu_L sum L F_heat(tau) / (4 pi r^2) over the
+ * point sources with F_heat the spectral integral of the absorbed photons'
+ * excess energy h (nu - nu_L) (Appendix A), h nu_L = 13.6 eV.  Zero with
+ * monochromatic sources (T_eff = 0): their photons carry no excess energy.
+ * The diffuse recombination photons add none (their excess energy is kT,
+ * not modelled).  heat_out [n_p] float32, host or device.
+ * START_ENOTBUILT before the first solve. */
+int start_get_heating(start_ctx *c, float *heat_out);
 
 /* H2 photodissociation rate of Appendix B for every particle:
  *   k_dis,i = sum over the interaction list of i (point sources only, the

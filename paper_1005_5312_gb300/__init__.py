@@ -38,7 +38,8 @@ class StartParams(C.Structure):
                 ("L_unit", C.c_double), ("alpha_A", C.c_double), ("alpha_B", C.c_double),
                 ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("max_pairs", C.c_longlong),
                 ("spin_cap", C.c_longlong),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p),
+                ("T_eff", C.c_double)]
 
 
 class StartStats(C.Structure):
@@ -77,6 +78,7 @@ def lib():
             "start_ionize": (i, [vp, d, vp]),
             "start_sph_density": (i, [vp, vp, vp]),
             "start_h2_dissociation": (i, [vp, vp, f, d, vp]),
+            "start_get_heating": (i, [vp, vp]),
             "start_rt_solve_oneshot": (i, [P(StartParams), vp, vp, ll, vp, vp, vp, ll, f, vp]),
             "start_get_frame": (i, [vp, vp]),
             "start_get_perm": (i, [vp, i, vp]),
@@ -249,6 +251,16 @@ class Context:
             return rho_out[:self.n_p]
         start_sph_density(self.h, mass, rho_out)
         return rho_out
+
+    def heating(self, heat_out=None):
+        """Photoheating rate per neutral atom (erg/s) of the last solve
+        (blackbody sources; zeros when monochromatic)."""
+        if heat_out is None:
+            heat_out = np.zeros(max(self.n_p, 1), np.float32)
+            _check(self.h, lib().start_get_heating(self.h, _ptr(heat_out)))
+            return heat_out[:self.n_p]
+        _check(self.h, lib().start_get_heating(self.h, _ptr(heat_out)))
+        return heat_out
 
     def h2_dissociation(self, n_H2, theta, kappa_LW, kdis_out=None):
         """H2 photodissociation rate k_dis (s^-1) of every particle

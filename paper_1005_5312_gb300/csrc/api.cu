@@ -311,7 +311,7 @@ static void release_all(start_ctx *c)
     if (c->r_cap) cudaStreamDestroy(c->r_cap);
     c->r_cap = nullptr;
     DBuf *all[] = {&c->pq, &c->ph, &c->porig, &c->pinv, &c->pkey, &c->nH, &c->mass_in,
-                   &c->mass_s, &c->h2_in, &c->w_save, &c->y, &c->V,
+                   &c->mass_s, &c->h2_in, &c->w_save, &c->heat, &c->spec_tab, &c->y, &c->V,
                    &c->gam, &c->eL, &c->eLs, &c->sq, &c->sorig, &c->skey, &c->sL,
                    &c->nb_off, &c->nb_idx, &c->lcount, &c->loff, &c->pent, &c->ptgt,
                    &c->pcon, &c->tk[0], &c->tk[1], &c->tv[0], &c->tv[1], &c->hist,
@@ -381,6 +381,7 @@ static int check_params(start_params &d)
     if (d.march_group == 0) d.march_group = 2;
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
+    if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;
     return START_OK;
 }
 
@@ -425,7 +426,7 @@ int start_set_params(start_ctx *c, const start_params *p)
         resident_reset(c);   // the captured graph belongs to the old stream's sequence
     }
     if (d.reuse_chains != c->p.reuse_chains || d.sigma_cm2 != c->p.sigma_cm2 ||
-        d.len_unit_cm != c->p.len_unit_cm || d.L_unit != c->p.L_unit)
+        d.len_unit_cm != c->p.len_unit_cm || d.L_unit != c->p.L_unit || d.T_eff != c->p.T_eff)
         resident_reset(c);
     c->p = d;
     c->stream = (cudaStream_t)d.stream;
@@ -581,7 +582,9 @@ int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_ou
     bool dev_out = gamma_out && is_device_ptr(gamma_out);
     if (gamma_out && !dev_out) ST_TRY(ensure(c->stage, (n ? n : 1) * sizeof(float)));
     float *gdst = dev_out ? gamma_out : (gamma_out ? c->stage.as<float>() : nullptr);
-    if (c->p.reuse_chains && c->r_valid && c->r_theta == theta && !c->diffuse) {
+    if (c->p.reuse_chains && c->r_valid && c->r_theta == theta && !c->diffuse &&
+        c->p.T_eff == 0.0) {
+        c->heat_valid = false;
         phase_mark(c, START_PHASE_GAMMA, false);   // the whole step on resident chains
         ST_TRY(resident_solve(c));
         if (gdst && n) {
@@ -647,6 +650,32 @@ int start_sph_density(start_ctx *c, const float *mass, float *rho_out)
     ST_TRY(run_sph_density(c, md, dst));
     ST_TRY(check_bad(c, "mass (must be finite and >= 0)"));
     if (!dev_out) ST_TRY(copy_out(c, rho_out, dst, n * sizeof(float)));
+    return START_OK;
+}
+
+int start_get_heating(start_ctx *c, float *heat_out)
+{
+    if (!c) return START_EINVAL;
+    if (!c->solved) return set_err(c, START_ENOTBUILT, "start_rt_solve first");
+    long long n = c->np;
+    if (n && !heat_out) return set_err(c, START_EINVAL, "NULL heat_out");
+    if (n == 0) return START_OK;
+    DeviceGuard g(c);
+    bool dev = is_device_ptr(heat_out);
+    float *dst = heat_out;
+    if (!dev) {
+        ST_TRY(ensure(c->stage, n * sizeof(float)));
+        dst = c->stage.as<float>();
+    }
+    if (c->heat_valid) {
+        k_to_input_order<float><<<grid_for(n, 256), 256, 0, c->stream>>>(
+            c->heat.as<float>(), c->porig.as<u32>(), n, dst);
+        ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+    } else {
+        ST_CUDA(c, cudaMemsetAsync(dst, 0, n * sizeof(float), c->stream));
+    }
+    if (!dev) ST_TRY(copy_out(c, heat_out, dst, n * sizeof(float)));
     return START_OK;
 }
 

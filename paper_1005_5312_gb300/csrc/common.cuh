@@ -100,6 +100,10 @@ struct start_ctx {
     st::DBuf mass_s;  // float SPH masses, Morton order
     st::DBuf h2_in;   // float n_H2 as given (input order), staged
     st::DBuf w_save;  // float n_HI of the records while they hold n_H2
+    st::DBuf heat;    // float photoheating per neutral atom (erg/s), Morton order
+    bool heat_valid = false;           // heat holds the last solve's (blackbody sources)
+    st::DBuf spec_tab;                 // float ln F_ion, ln F_heat tables (blackbody)
+    double spec_T = 0.0;               // temperature spec_tab was built for
     st::DBuf y;       // double neutral fraction
     st::DBuf V;       // double volume (len_unit^3)
     st::DBuf gam;     // float Gamma (cgs)
@@ -229,6 +233,12 @@ int run_sph_density(start_ctx *c, const float *mass_dev, float *rho_dev);
 
 // h2.cu
 int run_h2_dissociation(start_ctx *c, const float *nH2_dev, float theta, float *kdis_dev);
+
+// spectral.cu
+constexpr int kSpecN = 8192;              // table points in s = ln(1 + tau / kSpecTau0)
+constexpr double kSpecTau0 = 1e-3;
+constexpr double kSpecTauMax = 1e6;       // F = 0 beyond
+int spectral_table(start_ctx *c);         // (re)builds spec_tab for p.T_eff
 
 // resident.cu
 void resident_reset(start_ctx *c);

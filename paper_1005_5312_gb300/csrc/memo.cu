@@ -650,18 +650,40 @@ __global__ void k_sum_jump_counts(const unsigned long long *part, long long nblo
     }
 }
 
-// 4. Gamma of every target from its pairs' chain sums, one warp per target:
-// each lane evaluates L e^-tau / (4 pi r^2) for one pair of a 32-pair chunk,
-// the chunk is summed by a fixed butterfly and the chunks are accumulated in
-// list order with compensation -- a deterministic order, so a target's
-// Gamma does not depend on which other targets share its chains.
-// KDIS: the chain sums are H2 columns (cm^-2) and each pair adds
-// L f_sh(N_H2 / 1e14 cm^-2) / (4 pi r^2) (Eq. H2ss) instead of L e^-tau / (4 pi r^2);
-// the resident Gamma (gam) is then left alone.
-template <bool KDIS>
+// What a pair adds to its target.  MODE 0: L e^-tau / (4 pi r^2).
+// MODE 1 (k_dis): the chain sums are H2 columns (cm^-2) and each pair adds
+// L f_sh(N_H2 / 1e14 cm^-2) / (4 pi r^2) (Eq. H2ss); the resident Gamma is
+// left alone.  MODE 2 (blackbody point sources): a point-source pair adds
+// L F_ion(tau) / (4 pi r^2) to Gamma and L F_heat(tau) / (4 pi r^2) to the
+// heating sum, F from the ln-tables of spectral.cu (linear in
+// s = ln(1 + tau / tau0)); emitter pairs stay monochromatic.
+struct GammaExtra {
+    const float *tab;      // ln F_ion [kSpecN], then ln F_heat [kSpecN]
+    float inv_tau0, inv_ds;
+    float *heat;           // heating per neutral atom, Morton order
+    float heat_conv;
+    u32 point_end;         // canonical ids below this are point sources
+};
+
+__device__ __forceinline__ float spec_lookup(const float *tab, float sidx)
+{
+    if (!(sidx < (float)(kSpecN - 1))) return 0.f;
+    int k = (int)sidx;
+    float f = sidx - (float)k;
+    float lo = tab[k], hi = tab[k + 1];
+    return expf(lo + f * (hi - lo));
+}
+
+// Gamma of every target from its pairs' chain sums, one warp per target:
+// each lane evaluates one pair of a 32-pair chunk, the chunk is summed by a
+// fixed butterfly and the chunks are accumulated in list order with
+// compensation -- a deterministic order, so a target's Gamma does not depend
+// on which other targets share its chains.
+template <int MODE>
 __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, long long t0,
                                                      long long t1, u64 base, float conv,
-                                                     const u32 *porig, float *gam, float *gout)
+                                                     const u32 *porig, float *gam, float *gout,
+                                                     GammaExtra x)
 {
     const int lane = threadIdx.x & 31;
     long long i = t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -670,24 +692,28 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
     if (i < t1) {
         u64 e0 = off[i] - base, e1 = off[i + 1] - base;
         float4 pt = a.m.pq[i];
-        float sum = 0.f, cmp = 0.f;
+        float sum = 0.f, cmp = 0.f, hsum = 0.f, hcmp = 0.f;
         for (u64 e = e0; e < e1; e += 32) {
             u64 p = e + lane;
-            float v = 0.f;
+            float v = 0.f, hv = 0.f;
             if (p < e1) {
                 uint4 st = a.state[p];
                 float tau = __uint_as_float(st.z) + __uint_as_float(st.w);
-                float4 src = vsource(a, a.svid[p]);
+                u32 vid = a.svid[p];
+                float4 src = vsource(a, vid);
                 float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
                 float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
-                float att;
-                if (KDIS) {
-                    float x = tau * 1e-14f;
-                    att = x <= 1.f ? 1.f : powf(x, -0.75f);
+                float dil = src.w / (12.566370614359172f * r2);
+                if (MODE == 1) {
+                    float xs = tau * 1e-14f;
+                    v = dil * (xs <= 1.f ? 1.f : powf(xs, -0.75f));
+                } else if (MODE == 2 && vid < x.point_end) {
+                    float sidx = log1pf(tau * x.inv_tau0) * x.inv_ds;
+                    v = dil * spec_lookup(x.tab, sidx);
+                    hv = dil * spec_lookup(x.tab + kSpecN, sidx);
                 } else {
-                    att = expf(-tau);
+                    v = dil * expf(-tau);
                 }
-                v = src.w * att / (12.566370614359172f * r2);
                 u32 l = st.y & ~kStable;
                 hops += l;
                 maxh = max(maxh, l);
@@ -699,10 +725,18 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
             float tk = sum + yk;
             cmp = (tk - sum) - yk;
             sum = tk;
+            if (MODE == 2) {
+                for (int o = 16; o; o >>= 1) hv += __shfl_xor_sync(0xffffffffu, hv, o);
+                float hy = hv - hcmp;
+                float ht = hsum + hy;
+                hcmp = (ht - hsum) - hy;
+                hsum = ht;
+            }
         }
         if (lane == 0) {
             float g = sum * conv;
-            if (!KDIS) gam[i] = g;
+            if (MODE != 1) gam[i] = g;
+            if (MODE == 2) x.heat[i] = hsum * x.heat_conv;
             if (gout) gout[porig[i]] = g;
         }
     }
@@ -937,14 +971,27 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     a.svid = c->m_vid.as<u32>();
     a.state = c->m_st[c->memo_final].as<uint4>();
     long long threads = (t1 - t0) * 32;
+    GammaExtra x{};
+    const bool spec = c->solve_kind == 0 && c->p.T_eff > 0.0;
+    if (spec) {
+        x.tab = c->spec_tab.as<float>();
+        x.inv_tau0 = (float)(1.0 / kSpecTau0);
+        x.inv_ds = (float)((kSpecN - 1) / log1p(kSpecTauMax / kSpecTau0));
+        x.heat = c->heat.as<float>();
+        // sigma_L h nu_L (erg cm^2) times the flux conversion
+        x.heat_conv = (float)(c->p.sigma_cm2 * 13.6 * 1.602176634e-12 * (double)conv);
+        x.point_end = a.SN + a.NS;
+    }
+    const unsigned grid = grid_for(threads, 256);
+    const u64 *lo = c->loff.as<u64>();
+    const u32 *po = c->porig.as<u32>();
+    float *gm = c->gam.as<float>();
     if (c->solve_kind == 1)
-        k_memo_gamma<true><<<grid_for(threads, 256), 256, 0, c->stream>>>(
-            a, c->loff.as<u64>(), t0, t1, base, conv, c->porig.as<u32>(), c->gam.as<float>(),
-            gout);
+        k_memo_gamma<1><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x);
+    else if (spec)
+        k_memo_gamma<2><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x);
     else
-        k_memo_gamma<false><<<grid_for(threads, 256), 256, 0, c->stream>>>(
-            a, c->loff.as<u64>(), t0, t1, base, conv, c->porig.as<u32>(), c->gam.as<float>(),
-            gout);
+        k_memo_gamma<0><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_memo_gamma");
 }

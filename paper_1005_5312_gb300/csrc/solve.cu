@@ -495,7 +495,14 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     c->jump_bytes = 0;
     ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));
     const bool kdis = c->solve_kind == 1;
-    const bool memo = c->p.march_mode == 1 || kdis;   // k_dis always takes the memoised march
+    const bool spec = !kdis && c->p.T_eff > 0.0;      // blackbody point sources
+    // k_dis and blackbody sources always take the memoised march
+    const bool memo = c->p.march_mode == 1 || kdis || spec;
+    if (spec) {
+        ST_TRY(spectral_table(c));
+        ST_TRY(ensure(c->heat, (np ? np : 1) * sizeof(float)));
+    }
+    if (!kdis) c->heat_valid = spec;
     c->walk_emit = c->diffuse && !kdis;               // LW photons come from point sources
     if (np == 0) return START_OK;
     if (c->walk_emit) ST_TRY(refresh_emitters(c));

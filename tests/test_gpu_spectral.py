@@ -1,0 +1,95 @@
+"""Blackbody point sources (T_eff, Appendix A integrals) through the C ABI
+against the FP64 oracle.
+
+The GPU interpolates ln F_ion and ln F_heat from a table (spacing 2.5e-3 in
+s = ln(1 + tau/1e-3): interpolation error below ~1e-5 relative where the
+contributions matter), on top of the float32 tau of the chains: Gamma_eff and
+the heating rate are compared at 1e-4 relative plus the absolute floors
+Gamma_abs = 1e-8/(sigma dt) and sigma h nu_L Gamma_abs.  Rays and chain links
+are exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from start_inputs import KPC_CM, MYR_S, SIGMA_CM2, lattice_workload
+
+pytestmark = pytest.mark.gpu
+G_ABS = 1e-8 / (SIGMA_CM2 * MYR_S)
+H_ABS = SIGMA_CM2 * 13.6 * 1.602176634e-12 * G_ABS
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1005_5312_gb300 as S
+    S.build()
+    return S
+
+
+def close(x, ref, floor):
+    x = np.asarray(x, np.float64)
+    bad = np.nonzero(np.abs(x - ref) > REL * np.abs(ref) + floor)[0]
+    assert len(bad) == 0, (len(bad), bad[:5], x[bad[:5]], ref[bad[:5]])
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.6])
+@pytest.mark.parametrize("T_eff", [1e5, 3e4])
+def test_spectral_gamma_and_heating_parity(S, theta, T_eff):
+    w = lattice_workload("bb-20^3", 20, 6.6, 16, 91, L=5e48)
+    y = np.random.default_rng(2).uniform(0.0, 1.0, w.n_p)
+    nHI = (y * w.n_H.astype(np.float64)).astype(np.float32)
+    ctx = S.Context(T_eff=T_eff, ptree_leaf=16)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    g = np.zeros(w.n_p, np.float32)
+    ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
+    heat = ctx.heating()
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
+    gref, href = orc.gamma_spectral(nHI, theta, T_eff)
+    close(g, gref, G_ABS)
+    close(heat, href, H_ABS)
+    st = ctx.stats()
+    assert st["rays"] == orc.last_stats["rays"] and st["hops"] == orc.last_stats["hops"]
+    assert np.all(heat >= 0) and heat.max() > 0
+
+
+def test_monochromatic_sources_heat_nothing(S):
+    w = lattice_workload("mono-16^3", 16, 6.6, 4, 92)
+    ctx = S.Context(reuse_chains=1)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    ctx.set_state(w.n_H, w.y0)
+    g = np.zeros(w.n_p, np.float32)
+    for _ in range(2):                       # full solve, then the resident form
+        ctx.rt_solve(0.5, gamma_out=g)
+        assert not np.any(ctx.heating())
+    # switching to blackbody sources takes the full path and heats
+    ctx.set_params(T_eff=1e5, reuse_chains=1)
+    ctx.rt_solve(0.5, gamma_out=g)
+    assert ctx.heating().max() > 0
+
+
+def test_spectral_sources_with_diffuse_emitters(S):
+    """Emitters stay monochromatic at the Lyman limit and add no heating."""
+    w = lattice_workload("bb-diffuse-14^3", 14, 4.0, 3, 93, L=1e49, diffuse=True)
+    y = np.full(w.n_p, 0.3)
+    ctx = S.Context(T_eff=1e5, ptree_leaf=16)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L, w.V, diffuse=True)
+    ctx.set_state(w.n_H, y)
+    g = np.zeros(w.n_p, np.float32)
+    ctx.rt_solve(0.7, gamma_out=g)
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
+    orc.set_emitters(y, w.n_H)
+    nHI = (y * w.n_H.astype(np.float64)).astype(np.float32)
+    gref, href = orc.gamma_spectral(nHI, 0.7, 1e5)
+    close(g, gref, G_ABS)
+    close(ctx.heating(), href, H_ABS)
+
+
+def test_invalid_temperature_is_rejected(S):
+    with pytest.raises(S.StartError):
+        S.Context(T_eff=100.0)
+    with pytest.raises(S.StartError):
+        S.Context(T_eff=-1.0)
