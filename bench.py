@@ -80,6 +80,18 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(seconds, units):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the units all ranks processed (an initialised process group, any backend;
+    one rank: unchanged)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, units
+    gathered = [None] * dist.get_world_size()
+    dist.all_gather_object(gathered, (seconds, units))
+    return max(x[0] for x in gathered), sum(x[1] for x in gathered)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
 
@@ -538,14 +550,7 @@ def run_gpu(args, w):
         r1 = timed(args.theta, args.steps, args.warmup)
     r2 = None if args.no_theta2 else timed(args.theta2, max(2, args.steps // 2), 1)
 
-    tot_ms = sum(r1["step_ms"])
-    rays = sum(r1["rays"])
-    if ws > 1:
-        import torch.distributed as dist
-        gathered = [None] * ws
-        dist.all_gather_object(gathered, (tot_ms, rays))
-        tot_ms = max(x[0] for x in gathered)
-        rays = sum(x[1] for x in gathered)
+    tot_ms, rays = reduce_over_ranks(sum(r1["step_ms"]), sum(r1["rays"]))
     value = rays / (tot_ms * 1e-3)
 
     # roofline of the dominant kernel
@@ -635,13 +640,7 @@ def run_gpu(args, w):
         for _ in range(args.steps):
             hstep()
             e_rays += ctx_h.stats()["rays"]
-        te = time.perf_counter() - t0
-        if ws > 1:
-            import torch.distributed as dist
-            gathered = [None] * ws
-            dist.all_gather_object(gathered, (te, e_rays))
-            te = max(x[0] for x in gathered)
-            e_rays = sum(x[1] for x in gathered)
+        te, e_rays = reduce_over_ranks(time.perf_counter() - t0, e_rays)
         h2d = hpos.nbytes + hh.nbytes + hsp.nbytes + hsL.nbytes + hnH.nbytes + hy.nbytes
         d2h = hg.nbytes + hy.nbytes
         out["e2e"] = {"value": e_rays / te, "unit": "rays/s", "h2d_bytes_per_step": h2d,
