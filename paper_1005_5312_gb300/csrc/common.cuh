@@ -132,7 +132,7 @@ struct start_ctx {
     long long npairs = 0;
 
     // memoised march: per chain link (virtual source, particle)
-    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_part, m_table, m_nx0, m_dl;
+    st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_hard, m_part, m_table, m_nx0, m_dl;
     long long memo_slots = 0;          // slots of the last memoised chunk
 
     // resident chains (reuse_chains = 1): the link forest of the last full
@@ -149,7 +149,7 @@ struct start_ctx {
 
     // generic scratch
     st::DBuf tk[2], tv[2], hist, scan_tmp, stage, flags;
-    st::DBuf counters; // u64[16]
+    st::DBuf counters; // u64[C_COUNT]
 
     start_stats stats{};
     unsigned long long launches = 0;        // kernels launched by this context
@@ -180,7 +180,8 @@ enum Counter {
     C_JUMP_ADV,   // pointer jumping: slot updates that read a successor
     C_JUMP_COPY,  // pointer jumping: closed chains copied to the other buffer
     C_TAIL_CAP,   // memo tail kernel: a chain exceeded the iteration cap
-    C_COUNT = 16
+    C_HARD,       // first hops listed for the FP64 kernel
+    C_COUNT = 24
 };
 
 // ---------------------------------------------------------------- error helpers

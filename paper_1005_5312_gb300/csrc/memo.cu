@@ -63,6 +63,8 @@ struct MemoArgs {
     const u32 *fr;                  // or the listed slots fr[0, nf) (first level)
     u32 *miss;                      // the first level's list of links not found in
     unsigned long long *nmiss;      // their upstream row, and its length
+    uint2 *hard;                    // first hops left to the FP64 kernel: (slot, target)
+    unsigned long long *nhard;
     u32 cap;                        // slot capacity
     HEntry *table;
     unsigned long long hmask;
@@ -215,14 +217,30 @@ __device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u3
 // neighbour's record and the bounds of its row; each lane takes one pair and
 // scans the staged candidates (every lane reads the same entry: a
 // broadcast).  The decision is hop<G>'s: the same FP32 terms, the same error
-// bounds (their per-neighbour factors folded once), the same FP64
-// re-decision, so the upstream particle is the same.  Rows with more
-// neighbours than the stage holds take hop<1> from global memory.  The walk
-// wrote the pair slots' virtual source, particle and order key.
+// bounds (their per-neighbour factors folded once).  The rare pairs whose
+// decision falls inside the bounds, and the rows with more neighbours than
+// the stage holds, are listed for k_memo_hop_hard (FP64 re-decision, lists
+// read from global memory), which keeps this kernel small.  The walk wrote
+// the pair slots' virtual source, particle and order key.
 constexpr int kRowNB = 64;      // staged neighbours per target
 constexpr int kRowWarps = 8;    // targets per block
 
-__global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
+// Appends the flagged lanes' (slot, target) to a list with one counter
+// update per warp; every lane of the warp calls it.
+__device__ __forceinline__ void warp_append(bool flag, u32 slot, u32 tgt, uint2 *list,
+                                            unsigned long long *count)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    unsigned long long b = 0;
+    if (lane == leader) b = atomicAdd(count, (unsigned long long)__popc(m));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (flag) list[b + __popc(m & ((1u << lane) - 1u))] = make_uint2(slot, tgt);
+}
+
+__global__ void __launch_bounds__(32 * kRowWarps, 4) k_memo_hop_rows(MemoArgs a)
 {
     __shared__ float4 nba[kRowWarps][kRowNB];   // (r_k - r_j, rsqrt |r_k - r_j|^2)
     __shared__ float4 nbb[kRowWarps][kRowNB];   // (|r_k - r_j|^2, e1, e0, -): bound e1 |b| + e0
@@ -233,142 +251,160 @@ __global__ void __launch_bounds__(32 * kRowWarps, 3) k_memo_hop_rows(MemoArgs a)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned me = 1u << lane;
     const long long i = a.t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    unsigned long long fbs = 0;
-    if (i < a.t1) {
-        const u64 r0 = a.off[i] - a.base, r1 = a.off[i + 1] - a.base;
-        const float4 pj = a.m.pq[i];
-        const u32 s0 = a.m.nb_off[i], s1 = a.m.nb_off[i + 1];
-        const bool staged = s1 - s0 <= (u32)kRowNB;
-        int nst = 0;
-        bool odd = false;   // a distinct neighbour whose FP32 offset underflowed
-        if (staged && r1 > r0) {
-            for (u32 b = s0; b < s1; b += 32) {
-                u32 s = b + lane;
-                bool ok = false;
-                float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, P = A;
-                uint4 R = make_uint4(0u, 0u, 0u, 0u);
-                if (s < s1) {
-                    u32 k = a.m.nb_idx[s];
-                    if (k < a.m.np) {
-                        P = a.m.pq[k];
-                        float ax = P.x - pj.x, ay = P.y - pj.y, az = P.z - pj.z;
-                        float a2 = ax * ax + ay * ay + az * az;
-                        if (a2 == 0.f) {
-                            if (P.x != pj.x || P.y != pj.y || P.z != pj.z) odd = true;
-                        } else {
-                            float ra = rsqrtf(a2);
-                            float an = a2 * ra;
-                            A = make_float4(ax, ay, az, ra);
-                            B = make_float4(a2, eps_q * 2.f * an, eps_q * a2 + 1e-37f, 0.f);
-                            R.x = k;
-                            if ((long long)k >= a.t0 && (long long)k < a.t1) {
-                                R.y = (u32)(a.off[k] - a.base);
-                                R.z = (u32)(a.off[k + 1] - a.base);
-                            }
-                            ok = true;
-                        }
-                    }
-                }
-                unsigned m = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
-                    int q = nst + __popc(m & (me - 1u));
-                    nba[w][q] = A;
-                    nbb[w][q] = B;
-                    nbp[w][q] = P;
-                    nbr[w][q] = R;
-                }
-                nst += __popc(m);
-            }
-            odd = __any_sync(0xffffffffu, odd);
-            __syncwarp();
-        }
-        for (u64 p0 = r0; p0 < r1; p0 += 32) {   // warp-uniform: the list append below
-            const u64 p = p0 + lane;
-            const bool valid = p < r1;
-            u32 up = kNone, nx = kNone;
-            if (valid) {
-                const u32 vid = a.svid[p];
-                const float4 src = vsource(a, vid);
-                float dt, dl;
-                if (staged) {
-                    float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
-                    float bn = sqrtf(bx * bx + by * by + bz * bz);
-                    float bc = -1.f, sc = -1.f;
-                    int bq = -1;
-                    float margin = 1.f;   // min |q| - bound: <= 0 when a test is unsure
-#pragma unroll 4
-                    for (int q = 0; q < nst; ++q) {
-                        float4 A = nba[w][q];
-                        float4 B = nbb[w][q];
-                        float dot = bx * A.x + by * A.y + bz * A.z;
-                        float qv = 2.f * dot - B.x;
-                        float eq = B.y * bn + B.z;
-                        bool pass = qv > eq;
-                        margin = fminf(margin, fabsf(qv) - eq);
-                        float cv = pass ? dot * A.w : -2.f;
-                        bool better = cv > bc;
-                        sc = better ? bc : fmaxf(sc, cv);
-                        bc = better ? cv : bc;
-                        bq = better ? q : bq;
-                    }
-                    u32 mk_global = kNone;   // an FP64 choice that was not staged
-                    if (odd || !(margin > 0.f) || (sc > 0.f && sc > bc - two_eps * bn)) {
-                        u32 mk = upstream_64<1>(a.m, pj, src, s0, s1, 0, me);
-                        ++fbs;
-                        bq = -1;
-                        for (int q = 0; q < nst && mk != kNone; ++q)
-                            if (nbr[w][q].x == mk) bq = q;
-                        if (bq < 0) mk_global = mk;
-                    }
-                    if (bq < 0 && mk_global != kNone) {
-                        dt = link_dt(a.m, pj, src, bx, by, bz, bn, mk_global, dl);
-                        up = mk_global;
-                        nx = find_in_row(a, up, vid, a.sord[p], (u32)(p - r0), (u32)(r1 - r0));
-                    } else if (bq < 0) {
-                        dl = bn;
-                        dt = a.m.sig * pj.w * bn;
-                        up = kNone;
-                    } else {
-                        // link_dt with the staged record of the upstream particle
-                        float4 pu = nbp[w][bq];
-                        float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
-                        float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
-                        float cn = sqrtf(cx * cx + cy * cy + cz * cz);
-                        dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
-                        dt = a.m.sig * 0.5f * (pj.w + pu.w) * dl;
-                        uint4 R = nbr[w][bq];
-                        up = R.x;
-                        nx = find_in_bounds(a, R.y, R.z, vid, a.sord[p],
-                                            row_guess(R.y, R.z, (u32)(p - r0), (u32)(r1 - r0)));
-                    }
+    if (i >= a.t1) return;   // warp-uniform
+    const u64 r0 = a.off[i] - a.base, r1 = a.off[i + 1] - a.base;
+    if (r1 <= r0) return;
+    const float4 pj = a.m.pq[i];
+    const u32 s0 = a.m.nb_off[i], s1 = a.m.nb_off[i + 1];
+    if (s1 - s0 > (u32)kRowNB) {   // the whole row takes the global-memory path
+        for (u64 p0 = r0; p0 < r1; p0 += 32)
+            warp_append(p0 + lane < r1, (u32)(p0 + lane), (u32)i, a.hard, a.nhard);
+        return;
+    }
+    int nst = 0;
+    bool odd = false;   // a distinct neighbour whose FP32 offset underflowed
+    for (u32 b = s0; b < s1; b += 32) {
+        u32 s = b + lane;
+        bool ok = false;
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, P = A;
+        uint4 R = make_uint4(0u, 0u, 0u, 0u);
+        if (s < s1) {
+            u32 k = a.m.nb_idx[s];
+            if (k < a.m.np) {
+                P = a.m.pq[k];
+                float ax = P.x - pj.x, ay = P.y - pj.y, az = P.z - pj.z;
+                float a2 = ax * ax + ay * ay + az * az;
+                if (a2 == 0.f) {
+                    if (P.x != pj.x || P.y != pj.y || P.z != pj.z) odd = true;
                 } else {
-                    up = hop<1>(a.m, (u32)i, pj, src, 0, me, dt, fbs, &dl);
-                    if (up != kNone)
-                        nx = find_in_row(a, up, vid, a.sord[p], (u32)(p - r0), (u32)(r1 - r0));
+                    float ra = rsqrtf(a2);
+                    float an = a2 * ra;
+                    A = make_float4(ax, ay, az, ra);
+                    B = make_float4(a2, eps_q * 2.f * an, eps_q * a2 + 1e-37f, 0.f);
+                    R.x = k;
+                    if ((long long)k >= a.t0 && (long long)k < a.t1) {
+                        R.y = (u32)(a.off[k] - a.base);
+                        R.z = (u32)(a.off[k + 1] - a.base);
+                    }
+                    ok = true;
+                }
+            }
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            int q = nst + __popc(m & (me - 1u));
+            nba[w][q] = A;
+            nbb[w][q] = B;
+            nbp[w][q] = P;
+            nbr[w][q] = R;
+        }
+        nst += __popc(m);
+    }
+    odd = __any_sync(0xffffffffu, odd);
+    __syncwarp();
+    for (u64 p0 = r0; p0 < r1; p0 += 32) {   // warp-uniform: the list appends below
+        const u64 p = p0 + lane;
+        const bool valid = p < r1;
+        u32 up = kNone, nx = kNone;
+        bool hard = false;
+        if (valid) {
+            const u32 vid = a.svid[p];
+            const float4 src = vsource(a, vid);
+            float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
+            float bn = sqrtf(bx * bx + by * by + bz * bz);
+            float bc = -1.f, sc = -1.f;
+            int bq = -1;
+            float margin = 1.f;   // min |q| - bound: <= 0 when a test is unsure
+#pragma unroll 4
+            for (int q = 0; q < nst; ++q) {
+                float4 A = nba[w][q];
+                float4 B = nbb[w][q];
+                float dot = bx * A.x + by * A.y + bz * A.z;
+                float qv = 2.f * dot - B.x;
+                float eq = B.y * bn + B.z;
+                bool pass = qv > eq;
+                margin = fminf(margin, fabsf(qv) - eq);
+                float cv = pass ? dot * A.w : -2.f;
+                bool better = cv > bc;
+                sc = better ? bc : fmaxf(sc, cv);
+                bc = better ? cv : bc;
+                bq = better ? q : bq;
+            }
+            if (odd || !(margin > 0.f) || (sc > 0.f && sc > bc - two_eps * bn)) {
+                hard = true;   // decided in FP64 by k_memo_hop_hard
+            } else {
+                float dt, dl;
+                if (bq < 0) {
+                    dl = bn;
+                    dt = a.m.sig * pj.w * bn;
+                } else {
+                    // link_dt with the staged record of the upstream particle
+                    float4 pu = nbp[w][bq];
+                    float ux = pj.x - pu.x, uy = pj.y - pu.y, uz = pj.z - pu.z;
+                    float cx = pu.x - src.x, cy = pu.y - src.y, cz = pu.z - src.z;
+                    float cn = sqrtf(cx * cx + cy * cy + cz * cz);
+                    dl = (ux * (cx - bx) + uy * (cy - by) + uz * (cz - bz)) / (bn + cn);
+                    dt = a.m.sig * 0.5f * (pj.w + pu.w) * dl;
+                    uint4 R = nbr[w][bq];
+                    up = R.x;
+                    nx = find_in_bounds(a, R.y, R.z, vid, a.sord[p],
+                                        row_guess(R.y, R.z, (u32)(p - r0), (u32)(r1 - r0)));
                 }
                 a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
                 a.dl[p] = dl;
                 a.nx0[p] = nx;
             }
-            // links found in up's row are done; the others are listed for
-            // k_memo_link, marked so that it skips the row search
-            const bool miss = valid && up != kNone && nx == kNone;
-            const unsigned mm = __ballot_sync(0xffffffffu, miss);
-            if (mm) {
-                const int leader = __ffs(mm) - 1;
-                unsigned long long b = 0;
-                if (lane == leader) b = atomicAdd(a.nmiss, (unsigned long long)__popc(mm));
-                b = __shfl_sync(0xffffffffu, b, leader);
-                if (miss) {
-                    unsigned long long q = b + __popc(mm & (me - 1u));
-                    a.miss[q] = (u32)p;
-                    a.ups[q] = up | kRowMiss;
-                }
+        }
+        warp_append(hard, (u32)p, (u32)i, a.hard, a.nhard);
+        // links found in up's row are done; the others are listed for
+        // k_memo_link, marked so that it skips the row search
+        const bool miss = valid && !hard && up != kNone && nx == kNone;
+        const unsigned mm = __ballot_sync(0xffffffffu, miss);
+        if (mm) {
+            const int leader = __ffs(mm) - 1;
+            unsigned long long b = 0;
+            if (lane == leader) b = atomicAdd(a.nmiss, (unsigned long long)__popc(mm));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (miss) {
+                unsigned long long q = b + __popc(mm & (me - 1u));
+                a.miss[q] = (u32)p;
+                a.ups[q] = up | kRowMiss;
             }
         }
     }
-    for (int o = 16; o; o >>= 1) fbs += __shfl_xor_sync(0xffffffffu, fbs, o);
-    if (lane == 0 && fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
+}
+
+// 2a''. the listed first hops: the FP64 re-decision of hop<1> (its neighbour
+// list from global memory), then the in-row search; links not in the row are
+// appended to the first level's miss list.
+__global__ void __launch_bounds__(256) k_memo_hop_hard(MemoArgs a)
+{
+    const long long n = (long long)*a.nhard;
+    const unsigned me = 1u << (threadIdx.x & 31);
+    unsigned long long fbs = 0;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < n;
+         it += (long long)gridDim.x * blockDim.x) {
+        const uint2 e = a.hard[it];
+        const u32 p = e.x, i = e.y;
+        const u32 vid = a.svid[p];
+        const float4 src = vsource(a, vid);
+        float dt, dl;
+        const u32 up = hop<1>(a.m, i, a.m.pq[i], src, 0, me, dt, fbs, &dl);
+        u32 nx = kNone;
+        if (up != kNone) {
+            const u64 r0 = a.off[i] - a.base, r1 = a.off[i + 1] - a.base;
+            nx = find_in_row(a, up, vid, a.sord[p], (u32)(p - r0), (u32)(r1 - r0));
+        }
+        a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
+        a.dl[p] = dl;
+        a.nx0[p] = nx;
+        if (up != kNone && nx == kNone) {
+            unsigned long long q = atomicAdd(a.nmiss, 1ull);
+            a.miss[q] = p;
+            a.ups[q] = up | kRowMiss;
+        }
+    }
+    if (fbs) atomicAdd(&a.m.counters[C_MARCH_FB], fbs);
 }
 
 // 2b. the upstream link of every frontier slot: the pair (v, up) when it is
@@ -778,7 +814,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) ||
         ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
         ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) ||
-        ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_table, hsize * sizeof(HEntry)))
+        ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_hard, (size_t)m.npairs * 8) || ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_CUDA(c, cudaMemsetAsync(c->m_table.p, 0xff, hsize * sizeof(HEntry), s));
@@ -810,7 +846,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.fr = nullptr;
     a.miss = c->m_fr.as<u32>();
     a.nmiss = ctr + C_MISS;
+    a.hard = c->m_hard.as<uint2>();
+    a.nhard = ctr + C_HARD;
     ST_CUDA(c, cudaMemsetAsync(a.nmiss, 0, sizeof(unsigned long long), s));
+    ST_CUDA(c, cudaMemsetAsync(a.nhard, 0, sizeof(unsigned long long), s));
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm <= 0) nsm = 1;
@@ -859,6 +898,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
             long long rows = t1 - t0;
             k_memo_hop_rows<<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0,
                               s>>>(a);
+            k_memo_hop_hard<<<(unsigned)(nsm * 4), 256, 0, s>>>(a);
+            ++c->launches;
         } else {
             switch (c->p.march_group) {
             case 32: launch_memo_hop<32>(a, s, nsm); break;
