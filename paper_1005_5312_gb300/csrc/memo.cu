@@ -240,7 +240,7 @@ __device__ __forceinline__ void warp_append(bool flag, u32 slot, u32 tgt, uint2 
     if (flag) list[b + __popc(m & ((1u << lane) - 1u))] = make_uint2(slot, tgt);
 }
 
-__global__ void __launch_bounds__(32 * kRowWarps, 4) k_memo_hop_rows(MemoArgs a)
+__global__ void __launch_bounds__(32 * kRowWarps, 5) k_memo_hop_rows(MemoArgs a)
 {
     __shared__ float4 nba[kRowWarps][kRowNB];   // (r_k - r_j, rsqrt |r_k - r_j|^2)
     __shared__ float4 nbb[kRowWarps][kRowNB];   // (|r_k - r_j|^2, e1, e0, -): bound e1 |b| + e0
