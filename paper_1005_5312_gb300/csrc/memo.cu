@@ -602,7 +602,7 @@ __device__ __forceinline__ float2 cadd(float2 x, float2 y)
 // never rewritten or re-read.
 constexpr u32 kStable = 0x80000000u;
 
-constexpr int kJumpR = 4;   // slots per thread (independent loads in flight)
+constexpr int kJumpR = 8;   // slots per thread (independent loads in flight)
 
 // part[2 b], part[2 b + 1] accumulate block b's advancing updates and copies
 // over the rounds (plain stores: a block index is unique within a launch and
