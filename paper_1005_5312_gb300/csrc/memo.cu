@@ -607,7 +607,7 @@ constexpr int kJumpR = 8;   // slots per thread (independent loads in flight)
 // part[2 b], part[2 b + 1] accumulate block b's advancing updates and copies
 // over the rounds (plain stores: a block index is unique within a launch and
 // the rounds are stream-ordered), summed once after the last round.
-__global__ void __launch_bounds__(256) k_memo_jump(long long n, const uint4 *__restrict__ st,
+__global__ void __launch_bounds__(256, 3) k_memo_jump(long long n, const uint4 *__restrict__ st,
                                                     uint4 *__restrict__ st2, unsigned *active,
                                                     unsigned long long *ctr,
                                                     unsigned long long *part)
