@@ -65,6 +65,17 @@ struct MemoArgs {
     unsigned long long *nmiss;      // their upstream row, and its length
     uint2 *hard;                    // first hops left to the FP64 kernel: (slot, target)
     unsigned long long *nhard;
+    // the walk's trees and opening angle, to tell whether a link (vid, up) is in
+    // the interaction row of up without searching it (in_row)
+    struct WalkTree {
+        const float4 *box;
+        const uint4 *meta;
+        const double *cube;
+        const u32 *parent;
+        u32 n;
+    } ts, te;
+    float th2f, cmag;
+    double th2d;
     u32 cap;                        // slot capacity
     HEntry *table;
     unsigned long long hmask;
@@ -189,6 +200,39 @@ __device__ __forceinline__ u32 find_in_bounds(const MemoArgs &a, u32 r0, u32 r1,
     for (u32 e = lo; e < r1 && a.sord[e] == key; ++e)
         if (a.svid[e] == vid) return e;
     return kNone;
+}
+
+// Whether the walk of target up lists the virtual source vid whose order key
+// (tree tag, cell) is key -- decided from the opening tests of Eqs. con1 and
+// con2 instead of a search of the row.  The walk reaches a cell iff its
+// parent is opened (a child of an accepted cell is accepted too: its edge
+// halves and its distance does not shrink); a cell entry is listed iff it is
+// then accepted; a count-1 cell is listed as itself or as its member either
+// way; members of a larger (level-21) leaf are listed iff the leaf is opened,
+// except the target itself among the emitters.  The tests are the walk's own
+// (certified FP32, FP64 inside the bound), so the answer is the walk's.
+__device__ __forceinline__ bool walk_accepts(const MemoArgs::WalkTree &t, u32 m, float4 p,
+                                             const MemoArgs &a)
+{
+    int r = accept_32(t.box[m], a.th2f, p.x, p.y, p.z, a.cmag);
+    if (r < 0) r = accept_64(t.cube + 4 * (size_t)m, a.th2d, p.x, p.y, p.z) ? 1 : 0;
+    return r != 0;
+}
+
+__device__ __forceinline__ bool in_row(const MemoArgs &a, u32 up, u32 vid, u32 key)
+{
+    const bool emit = (key >> 31) != 0;
+    const MemoArgs::WalkTree &t = emit ? a.te : a.ts;
+    const u32 n = key & 0x7fffffffu;
+    if (n >= t.n) return true;   // never expected: let the search decide
+    const float4 p = a.m.pq[up];
+    const u32 par = t.parent[n];
+    if (par != kNone && walk_accepts(t, par, p, a)) return false;   // n is not reached
+    const u32 memb0 = emit ? a.SN + a.NS + a.EN : a.SN;
+    if (vid < memb0) return walk_accepts(t, n, p, a);               // a cell entry
+    if (emit && vid - memb0 == up) return false;                    // the target itself
+    if (t.meta[n].z == 1u) return true;                              // count-1 cell
+    return !walk_accepts(t, n, p, a);                                // level-21 leaf
 }
 
 // Guess for the entry at position pos of a row of length len, in a row
@@ -430,9 +474,14 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
         s = a.fr ? a.fr[it] : a.fbase + (u32)it;
         vid = a.svid[s];
         key = a.sord[s];
-        // links of the first level were searched there; later slots sit
-        // in no row, so their search has no guess
-        if (!searched) nx = find_in_row(a, up, vid, key, 0, 0);
+        // links of the first level were searched there; later slots sit in
+        // no row, so their search has no guess, and the row is searched only
+        // when the walk lists vid for up
+        if (!searched && (long long)up >= a.t0 && (long long)up < a.t1 &&
+            in_row(a, up, vid, key)) {
+            nx = find_in_row(a, up, vid, key, 0, 0);
+            if (nx == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+        }
         if (nx == kNone) {
             unsigned long long lk = link_key(vid, up);
             unsigned long long h = mix64(lk) & a.hmask;
@@ -501,8 +550,11 @@ __device__ __forceinline__ u32 link_or_claim(const MemoArgs &a, u32 vid, u32 up,
                                              bool &claimed)
 {
     claimed = false;
-    u32 nx = find_in_row(a, up, vid, key, 0, 0);
-    if (nx != kNone) return nx;
+    if ((long long)up >= a.t0 && (long long)up < a.t1 && in_row(a, up, vid, key)) {
+        u32 nx = find_in_row(a, up, vid, key, 0, 0);
+        if (nx == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+        return nx;
+    }
     unsigned long long lk = link_key(vid, up);
     unsigned long long h = mix64(lk) & a.hmask;
     for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
@@ -813,8 +865,8 @@ static unsigned long long read_u64(start_ctx *c, const unsigned long long *d)
     return v;
 }
 
-static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &overflow,
-                        long long t0, long long t1, u64 base)
+static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t cap,
+                        bool &overflow, long long t0, long long t1, u64 base)
 {
     cudaStream_t s = c->stream;
     overflow = false;
@@ -826,7 +878,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
         ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) ||
         ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
         ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) ||
-        ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_hard, (size_t)m.npairs * 8) || ensure(c->m_table, hsize * sizeof(HEntry)))
+        ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_hard, (size_t)m.npairs * 8) ||
+        ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_CUDA(c, cudaMemsetAsync(c->m_table.p, 0xff, hsize * sizeof(HEntry), s));
@@ -838,6 +891,13 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, size_t cap, bool &over
     a.SN = (u32)c->stree.n;
     a.NS = (u32)c->ns;
     a.EN = (u32)(c->walk_emit ? c->et.n : 0);
+    a.ts = {c->stree.box.as<float4>(), c->stree.meta.as<uint4>(), c->stree.cube.as<double>(),
+            c->stree.parent.as<u32>(), a.SN};
+    a.te = {c->et.box.as<float4>(), c->et.meta.as<uint4>(), c->et.cube.as<double>(),
+            c->et.parent.as<u32>(), a.EN};
+    a.th2f = theta * theta;       // the walk's own values (k_walk)
+    a.th2d = (double)theta * (double)theta;
+    a.cmag = c->fr.cmag;
     a.svid = c->m_vid.as<u32>();
     a.sj = c->m_j.as<u32>();
     a.sord = c->m_ord.as<u32>();
@@ -1072,7 +1132,7 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
         // slot ids and table indices must stay below the pending flag (2^31)
         if (cap >= (1ull << 30)) return set_err(c, START_ERANGE, "too many chain links");
         bool overflow = false;
-        ST_TRY(memo_attempt(c, m, cap, overflow, t0, t1, base));
+        ST_TRY(memo_attempt(c, m, theta, cap, overflow, t0, t1, base));
         if (!overflow) return START_OK;
         cap *= 2;
     }

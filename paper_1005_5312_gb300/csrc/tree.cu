@@ -133,6 +133,16 @@ __global__ void k_finalize(const u64 *keys, const u32 *first, const u32 *count, 
     lev[i] = level;
 }
 
+// Parent (depth-first index) of every node; the root has none.
+__global__ void k_parents(const u32 *cb, const u32 *nc, const u32 *dfs, long long n, u32 *parent)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    if (b == 0) parent[dfs[0]] = 0xffffffffu;
+    u32 i = dfs[b];
+    for (u32 k = 0; k < nc[b]; ++k) parent[dfs[cb[b] + k]] = i;
+}
+
 __global__ void k_bfs2dfs(const u32 *dfs, long long n, u32 *out)
 {
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -217,7 +227,7 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
     ST_CUDA(c, cudaGetLastError());
     if (ensure(t.box, total * sizeof(float4)) || ensure(t.meta, total * sizeof(uint4)) ||
         ensure(t.cube, total * 4 * sizeof(double)) || ensure(t.level, total * sizeof(int)) ||
-        ensure(t.bfs2dfs, total * sizeof(u32)))
+        ensure(t.bfs2dfs, total * sizeof(u32)) || ensure(t.parent, total * sizeof(u32)))
         return set_err(c, START_ENOMEM, "out of device memory (octree)");
     for (int l = 0; l <= t.depth; ++l) {
         long long o = t.lvl_off[l], mm = t.lvl_off[l + 1] - o;
@@ -227,6 +237,9 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
             t.meta.as<uint4>(), t.cube.as<double>(), t.level.as<int>()); ++c->launches;
     }
     k_bfs2dfs<<<grid_for(total, 256), 256, 0, s>>>(dfs.as<u32>(), total, t.bfs2dfs.as<u32>()); ++c->launches;
+    k_parents<<<grid_for(total, 256), 256, 0, s>>>(t.bfs_cb.as<u32>(), t.bfs_nc.as<u32>(),
+                                                   dfs.as<u32>(), total, t.parent.as<u32>());
+    ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_CUDA(c, cudaStreamSynchronize(s));
     release(size);
@@ -308,7 +321,7 @@ int tree_moments(start_ctx *c, Tree &t, const float4 *mem_pos, const double *mem
 
 void tree_release(Tree &t)
 {
-    DBuf *all[] = {&t.box, &t.meta, &t.cube, &t.level, &t.vsrc, &t.L, &t.M, &t.bfs2dfs,
+    DBuf *all[] = {&t.box, &t.meta, &t.cube, &t.level, &t.parent, &t.vsrc, &t.L, &t.M, &t.bfs2dfs,
                    &t.bfs_first, &t.bfs_count, &t.bfs_cb, &t.bfs_nc};
     for (DBuf *b : all) release(*b);
     t.n = 0;
