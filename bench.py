@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-next", action="store_true",
                     help="skip the SPH density, H2 photodissociation and blackbody-source lines")
     ap.add_argument("--no-method-error", action="store_true")
+    ap.add_argument("--lognormal256", action="store_true",
+                    help="add the 256^3 log-normal diffuse workload (about a minute)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-workers", type=int, default=4)
@@ -451,6 +453,45 @@ def diffuse_workload(S, dev, args, T):
             "theta": 0.7}
 
 
+def lognormal_256(S, dev, args, T):
+    """The large diffuse run at full size (opt-in): 256^3 particles in a
+    log-normal field (sigma_ln = 1.5, P(k) ~ k^-3), every particle emitting
+    plus 64 sources of 1e50/s; per theta in {0.5, 1}: SPH density recompute
+    from masses, then a full coupled step (build, walk over both trees,
+    memoised march in target chunks, Gamma, implicit update)."""
+    import numpy as np
+    import torch
+    from start_inputs import config5
+    w = config5()
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream, max_pairs=1 << 29)
+    pos, h, sp, sL, V = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L), T(w.V)
+    mass = T((w.n_H.astype(np.float64) * w.V).astype(np.float32))
+    rho = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    y = T(w.y0)
+    g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    out = {"workload": w.name, "n_p": w.n_p}
+    for theta in (0.5, 1.0):
+        y.copy_(T(w.y0))
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.build_trees(pos, h, sp, sL, V, diffuse=True)
+        ctx.sph_density(mass, rho)
+        ctx.set_state(rho, y)
+        ctx.rt_solve(theta, gamma_out=g)
+        ctx.ionize(w.dt_s, y_out=y)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        st = ctx.stats()
+        out[f"theta_{theta}"] = {"value": st["rays"] / (ms * 1e-3), "unit": "rays/s",
+                                 "ms_per_step": ms, "rays_per_step": st["rays"],
+                                 "chunks": st["chunks"]}
+    ctx.close()
+    return out
+
+
 def serving(args):
     """Continuous batching vs one solve at a time on the same Poisson stream
     of requests of mixed size (real-time replay, 150 GB budget)."""
@@ -615,6 +656,8 @@ def run_gpu(args, w):
         out["blackbody_sources"] = blackbody_sources(S, w, dev, args, T, flush)
     if not args.no_diffuse:
         out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
+    if args.lognormal256:
+        out["lognormal_256cubed"] = lognormal_256(S, dev, args, T)
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: H2D copies of the
