@@ -182,6 +182,7 @@ enum Counter {
     C_JUMP_COPY,  // pointer jumping: closed chains copied to the other buffer
     C_TAIL_CAP,   // memo tail kernel: a chain exceeded the iteration cap
     C_HARD,       // first hops listed for the FP64 kernel
+    C_NB_OVER,    // targets with more neighbours than the counting walk keeps
     C_COUNT = 24
 };
 

@@ -6,7 +6,10 @@
 // (pre-order index + skip pointer), so the 32 targets of a warp are spatial
 // neighbours and read the same cells.  Cells are visited by a conservative
 // FP32 distance test; members are accepted by the FP32-filtered exact test
-// with an FP64 fallback.  Two passes: count, then fill at scanned offsets.
+// with an FP64 fallback.  One walk counts the neighbours and keeps the first
+// kNbCap of them in a padded scratch; after the scan of the counts the rows
+// are copied into the CSR, and only targets with more neighbours than that
+// walk again to fill their rows.
 #include "common.cuh"
 
 namespace st {
@@ -29,16 +32,23 @@ __device__ __forceinline__ bool member_in(float4 pk, float4 pi, float two_h, dou
     return d2e < __dmul_rn(two_h64, two_h64);
 }
 
+constexpr u32 kNbCap = 48;   // neighbours kept per target by the counting walk
+
+// FILL = false: count into cnt[i] and keep the first kNbCap in scratch[i *
+// kNbCap ..], counting the targets that have more into n_over.  FILL = true:
+// write the rows of the targets listed in only[0, n) (all when NULL) at off.
 template <bool FILL>
 __global__ void __launch_bounds__(128) k_neighbours(const float4 *pq, const float *h, long long np,
                                                     const float4 *box, const uint4 *meta,
                                                     long long nn, float cmag, u32 *cnt,
                                                     const u32 *off, u32 *idx,
-                                                    unsigned long long *fb_total)
+                                                    unsigned long long *fb_total, u32 *scratch,
+                                                    unsigned long long *n_over, const u32 *only)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned fb = 0;
-    if (i < np) {
+    if (t < np) {
+        const long long i = only ? (long long)only[t] : t;
         float4 pi = pq[i];
         float two_h = __fmul_rn(2.f, h[i]);
         double two_h64 = 2.0 * (double)h[i];
@@ -67,6 +77,7 @@ __global__ void __launch_bounds__(128) k_neighbours(const float4 *pq, const floa
                             if (w < wend) idx[w] = r;   // never past this row
                             ++w;
                         } else {
+                            if (c < kNbCap) scratch[(size_t)i * kNbCap + c] = r;
                             ++c;
                         }
                     }
@@ -76,13 +87,34 @@ __global__ void __launch_bounds__(128) k_neighbours(const float4 *pq, const floa
                 n = n + 1;
             }
         }
-        if (!FILL) cnt[i] = c;
-        else if (w != wend) atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
+        if (!FILL) {
+            cnt[i] = c;
+            if (c > kNbCap) atomicAdd(n_over, 1ull);
+        } else if (w != wend) {
+            atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
+        }
     }
     if (!FILL) {
         for (int o = 16; o; o >>= 1) fb += __shfl_xor_sync(0xffffffffu, fb, o);
         if ((threadIdx.x & 31) == 0 && fb) atomicAdd(fb_total, (unsigned long long)fb);
     }
+}
+
+// Rows of at most kNbCap neighbours copied from the scratch into the CSR, one
+// warp per target; the others are listed for the filling walk.
+__global__ void k_nb_compact(long long np, const u32 *cnt, const u32 *off, const u32 *scratch,
+                             u32 *idx, u32 *over, unsigned long long *n_over)
+{
+    long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    int lane = threadIdx.x & 31;
+    if (i >= np) return;
+    u32 c = cnt[i];
+    if (c > kNbCap) {
+        if (lane == 0) over[atomicAdd(n_over, 1ull)] = (u32)i;
+        return;
+    }
+    u32 o = off[i];
+    for (u32 k = lane; k < c; k += 32) idx[o + k] = scratch[(size_t)i * kNbCap + k];
 }
 
 int build_neighbours(start_ctx *c)
@@ -95,27 +127,48 @@ int build_neighbours(start_ctx *c)
         return START_OK;
     }
     ST_TRY(ensure(c->lcount, np * sizeof(u32)));
-    unsigned long long *fb = c->counters.as<unsigned long long>() + C_NBR_FB;
+    struct Scratch {   // released on every return
+        DBuf b;
+        ~Scratch() { release(b); }
+    } scr, ol;
+    DBuf &scratch = scr.b, &olist = ol.b;
+    if (ensure(scratch, (size_t)np * kNbCap * sizeof(u32)))
+        return set_err(c, START_ENOMEM, "out of device memory (neighbour lists)");
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    unsigned long long *fb = ctr + C_NBR_FB;
+    unsigned long long *n_over = ctr + C_NB_OVER;
+    ST_CUDA(c, cudaMemsetAsync(n_over, 0, sizeof(unsigned long long), c->stream));
     const Tree &t = c->pt;
     k_neighbours<false><<<grid_for(np, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), c->ph.as<float>(), np, t.box.as<float4>(), t.meta.as<uint4>(), t.n,
-        c->fr.cmag, c->lcount.as<u32>(), nullptr, nullptr, fb); ++c->launches;
+        c->fr.cmag, c->lcount.as<u32>(), nullptr, nullptr, fb, scratch.as<u32>(), n_over,
+        nullptr); ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     // offsets in u64 first to detect overflow of the u32 CSR
     ST_TRY(ensure(c->loff, (np + 1) * sizeof(u64)));
     ST_TRY(exclusive_scan_u32_to_u64(c, c->lcount.as<u32>(), c->loff.as<u64>(), np));
-    unsigned long long total = 0;
+    unsigned long long total = 0, over = 0;
     ST_CUDA(c, cudaMemcpyAsync(&total, c->loff.as<u64>() + np, sizeof(total),
                                cudaMemcpyDeviceToHost, c->stream));
+    ST_CUDA(c, cudaMemcpyAsync(&over, n_over, sizeof(over), cudaMemcpyDeviceToHost, c->stream));
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     if (total >= 0xffffffffull) return set_err(c, START_ERANGE, "more than 2^32 neighbour entries");
     ST_TRY(exclusive_scan_u32(c, c->lcount.as<u32>(), c->nb_off.as<u32>(), np,
                               c->nb_off.as<u32>() + np));
     ST_TRY(ensure(c->nb_idx, (total ? total : 1) * sizeof(u32)));
-    k_neighbours<true><<<grid_for(np, 128), 128, 0, c->stream>>>(
-        c->pq.as<float4>(), c->ph.as<float>(), np, t.box.as<float4>(), t.meta.as<uint4>(), t.n,
-        c->fr.cmag, nullptr, c->nb_off.as<u32>(), c->nb_idx.as<u32>(),
-        c->counters.as<unsigned long long>() + C_INTERNAL); ++c->launches;
+    if (over && ensure(olist, over * sizeof(u32)))
+        return set_err(c, START_ENOMEM, "out of device memory (neighbour lists)");
+    ST_CUDA(c, cudaMemsetAsync(n_over, 0, sizeof(unsigned long long), c->stream));
+    k_nb_compact<<<grid_for(np * 32, 256), 256, 0, c->stream>>>(
+        np, c->lcount.as<u32>(), c->nb_off.as<u32>(), scratch.as<u32>(), c->nb_idx.as<u32>(),
+        over ? olist.as<u32>() : nullptr, n_over); ++c->launches;
+    if (over) {
+        k_neighbours<true><<<grid_for((long long)over, 128), 128, 0, c->stream>>>(
+            c->pq.as<float4>(), c->ph.as<float>(), (long long)over, t.box.as<float4>(),
+            t.meta.as<uint4>(), t.n, c->fr.cmag, nullptr, c->nb_off.as<u32>(),
+            c->nb_idx.as<u32>(), ctr + C_INTERNAL, nullptr, nullptr, olist.as<u32>());
+        ++c->launches;
+    }
     ST_CUDA(c, cudaGetLastError());
     c->nb_total = (long long)total;
     return START_OK;
