@@ -55,6 +55,7 @@ struct Tree {
     DBuf cube;                 // double4-like: lower corner x,y,z, edge (exact frame values)
     DBuf level;                // int
     DBuf parent;               // u32 depth-first index of the parent (root: none)
+    DBuf leafof;               // u32 per member: the leaf holding it
     DBuf vsrc;                 // float4: luminosity centre, L / L_unit
     DBuf L;                    // double summed luminosity (photons/s)
     DBuf M;                    // double[3] summed L * r

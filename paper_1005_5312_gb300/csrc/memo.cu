@@ -30,7 +30,8 @@
 
 namespace st {
 
-int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base);
+int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base,
+                    long long npairs);
 int ensure_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s);
 
 constexpr u32 kPending = 0x80000000u;
@@ -1118,7 +1119,7 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     size_t cap = (size_t)m.npairs + (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
     if (ensure(c->m_vid, cap * 4) || ensure(c->m_ord, cap * 4))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
-    ST_TRY(walk_fill_slots(c, theta, t0, t1, base));
+    ST_TRY(walk_fill_slots(c, theta, t0, t1, base, m.npairs));
     // an attempt that runs out of slots leaves artefacts (table keys without
     // slots) in the error and fallback counters: restore them before retrying
     unsigned long long *ctr = c->counters.as<unsigned long long>();

@@ -60,26 +60,25 @@ struct RawRows {
 };
 
 struct SlotRows {
-    u32 *ent, *ord;
+    u32 *ent;             // canonical ids only: the order key is a function of the id
     u64 g = 0;            // group (w / 4) of the buffered entries
     int lo = 0, hi = 0;   // buffered positions [lo, hi) of the group
-    u32 e0 = 0, e1 = 0, e2 = 0, e3 = 0, o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+    u32 e0 = 0, e1 = 0, e2 = 0, e3 = 0;
     __device__ __forceinline__ void flush()
     {
         if (hi <= lo) return;
         u64 b = g * 4;
         if (lo == 0 && hi == 4) {
             *reinterpret_cast<uint4 *>(ent + b) = make_uint4(e0, e1, e2, e3);
-            *reinterpret_cast<uint4 *>(ord + b) = make_uint4(o0, o1, o2, o3);
         } else {
-            if (lo <= 0 && 0 < hi) { ent[b] = e0; ord[b] = o0; }
-            if (lo <= 1 && 1 < hi) { ent[b + 1] = e1; ord[b + 1] = o1; }
-            if (lo <= 2 && 2 < hi) { ent[b + 2] = e2; ord[b + 2] = o2; }
-            if (lo <= 3 && 3 < hi) { ent[b + 3] = e3; ord[b + 3] = o3; }
+            if (lo <= 0 && 0 < hi) ent[b] = e0;
+            if (lo <= 1 && 1 < hi) ent[b + 1] = e1;
+            if (lo <= 2 && 2 < hi) ent[b + 2] = e2;
+            if (lo <= 3 && 3 < hi) ent[b + 3] = e3;
         }
         lo = hi = 0;
     }
-    __device__ __forceinline__ void put(u64 w, u32 e, u32 o)
+    __device__ __forceinline__ void put(u64 w, u32 e, u32)
     {
         u64 gw = w >> 2;
         int k = (int)(w & 3);
@@ -88,10 +87,10 @@ struct SlotRows {
             g = gw;
             lo = k;
         }
-        if (k == 0) { e0 = e; o0 = o; }
-        if (k == 1) { e1 = e; o1 = o; }
-        if (k == 2) { e2 = e; o2 = o; }
-        if (k == 3) { e3 = e; o3 = o; }
+        if (k == 0) e0 = e;
+        if (k == 1) e1 = e;
+        if (k == 2) e2 = e;
+        if (k == 3) e3 = e;
         hi = k + 1;
         if (hi == 4) flush();
     }
@@ -164,7 +163,7 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
         u64 w = FILL ? off[i] - base : 0ull;
         const u64 wend = FILL ? off[i + 1] - base : 0ull;
         if (MODE == 2) {
-            SlotRows rows{ent, ord};
+            SlotRows rows{ent};
             walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
             walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, c, w, wend, rows,
                             fb);
@@ -401,11 +400,30 @@ static int walk_fill(start_ctx *c, float theta, const TreeView &sv, const TreeVi
 static TreeView source_view(start_ctx *c);
 static TreeView emitter_view(start_ctx *c);
 
+// Order key (tree tag, cell) of a canonical virtual-source id: the cell
+// itself, or the leaf holding a member (a count-1 cell's id is its member's,
+// and its key is that leaf either way) -- the key the walk orders rows by.
+__global__ void k_order_keys(long long n, const u32 *vid, u32 SN, u32 NS, u32 EN,
+                             const u32 *leaf_s, const u32 *leaf_e, u32 *key)
+{
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    u32 v = vid[p];
+    u32 k;
+    if (v < SN) k = v;
+    else if ((v -= SN) < NS) k = leaf_s[v];
+    else if ((v -= NS) < EN) k = 0x80000000u | v;
+    else k = 0x80000000u | leaf_e[v - EN];
+    key[p] = k;
+}
+
 // The memoised march's pair slots of targets [t0, t1): canonical virtual
-// source and order key of every pair, written straight into the first slots
-// (vid and ord buffers, which the caller sized; the first hop knows each
-// row's target, so the pair slots' particle is not stored).
-int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base)
+// source of every pair written straight into the first slots (the vid
+// buffer, which the caller sized), then its order key (ord buffer) by one
+// coalesced pass; the first hop knows each row's target, so the pair slots'
+// particle is not stored.
+int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base,
+                    long long n)
 {
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     u32 SN = (u32)c->stree.n, NS = (u32)c->ns, EN = (u32)(c->walk_emit ? c->et.n : 0);
@@ -413,8 +431,11 @@ int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 b
     k_walk<2><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), t0, t1, source_view(c), emitter_view(c), scb, ecb, theta * theta,
         (double)theta * (double)theta, c->fr.cmag, nullptr, c->loff.as<u64>(), base,
-        c->m_vid.as<u32>(), nullptr, c->m_ord.as<u32>(), ctr + C_INTERNAL);
-    ++c->launches;
+        c->m_vid.as<u32>(), nullptr, nullptr, ctr + C_INTERNAL);
+    k_order_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(
+        n, c->m_vid.as<u32>(), SN, NS, EN, c->stree.leafof.as<u32>(), c->et.leafof.as<u32>(),
+        c->m_ord.as<u32>());
+    c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "k_walk");
 }
 

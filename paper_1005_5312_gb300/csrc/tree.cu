@@ -133,6 +133,16 @@ __global__ void k_finalize(const u64 *keys, const u32 *first, const u32 *count, 
     lev[i] = level;
 }
 
+// The leaf holding every member (members in sorted order).
+__global__ void k_leafof(const uint4 *meta, long long nn, u32 *leafof)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    uint4 mt = meta[i];
+    if (!mt.w) return;
+    for (u32 r = mt.y; r < mt.y + mt.z; ++r) leafof[r] = (u32)i;
+}
+
 // Parent (depth-first index) of every node; the root has none.
 __global__ void k_parents(const u32 *cb, const u32 *nc, const u32 *dfs, long long n, u32 *parent)
 {
@@ -227,7 +237,8 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
     ST_CUDA(c, cudaGetLastError());
     if (ensure(t.box, total * sizeof(float4)) || ensure(t.meta, total * sizeof(uint4)) ||
         ensure(t.cube, total * 4 * sizeof(double)) || ensure(t.level, total * sizeof(int)) ||
-        ensure(t.bfs2dfs, total * sizeof(u32)) || ensure(t.parent, total * sizeof(u32)))
+        ensure(t.bfs2dfs, total * sizeof(u32)) || ensure(t.parent, total * sizeof(u32)) ||
+        ensure(t.leafof, n * sizeof(u32)))
         return set_err(c, START_ENOMEM, "out of device memory (octree)");
     for (int l = 0; l <= t.depth; ++l) {
         long long o = t.lvl_off[l], mm = t.lvl_off[l + 1] - o;
@@ -239,7 +250,8 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
     k_bfs2dfs<<<grid_for(total, 256), 256, 0, s>>>(dfs.as<u32>(), total, t.bfs2dfs.as<u32>()); ++c->launches;
     k_parents<<<grid_for(total, 256), 256, 0, s>>>(t.bfs_cb.as<u32>(), t.bfs_nc.as<u32>(),
                                                    dfs.as<u32>(), total, t.parent.as<u32>());
-    ++c->launches;
+    k_leafof<<<grid_for(total, 256), 256, 0, s>>>(t.meta.as<uint4>(), total, t.leafof.as<u32>());
+    c->launches += 2;
     ST_CUDA(c, cudaGetLastError());
     ST_CUDA(c, cudaStreamSynchronize(s));
     release(size);
@@ -321,7 +333,8 @@ int tree_moments(start_ctx *c, Tree &t, const float4 *mem_pos, const double *mem
 
 void tree_release(Tree &t)
 {
-    DBuf *all[] = {&t.box, &t.meta, &t.cube, &t.level, &t.parent, &t.vsrc, &t.L, &t.M, &t.bfs2dfs,
+    DBuf *all[] = {&t.box,     &t.meta,      &t.cube,      &t.level,  &t.parent,
+                   &t.leafof,  &t.vsrc,      &t.L,         &t.M,      &t.bfs2dfs,
                    &t.bfs_first, &t.bfs_count, &t.bfs_cb, &t.bfs_nc};
     for (DBuf *b : all) release(*b);
     t.n = 0;
