@@ -522,6 +522,8 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     if (spec) {
         ST_TRY(spectral_table(c));
         ST_TRY(ensure(c->heat, (np ? np : 1) * sizeof(float)));
+        // targets of chunks without pairs keep zero heating
+        ST_CUDA(c, cudaMemsetAsync(c->heat.p, 0, (np ? np : 1) * sizeof(float), s));
     }
     if (!kdis) c->heat_valid = spec;
     c->walk_emit = c->diffuse && !kdis;               // LW photons come from point sources

@@ -108,3 +108,10 @@ def test_density_full_size_multisource_workload(S):
     ctx, orc = pair(S, w.pos, w.h, w.src_pos, w.src_L)
     m = np.random.default_rng(4).uniform(0.5, 1.5, w.n_p).astype(np.float32)
     close(ctx.sph_density(m), orc.sph_density(m.astype(np.float64)))
+
+
+def test_density_without_particles(S):
+    ctx = S.Context()
+    ctx.build_trees(np.zeros((3, 0), np.float32), np.zeros(0, np.float32),
+                    np.zeros((3, 1), np.float32), np.ones(1))
+    assert ctx.sph_density(np.zeros(0, np.float32)).size == 0

@@ -116,3 +116,15 @@ def test_kdis_full_size_sampled_targets(S):
     orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
     idx = np.random.default_rng(9).choice(w.n_p, 400, replace=False)
     close(k[idx], orc.h2_dissociation(nH2, 0.5, KAPPA, targets=idx))
+
+
+def test_kdis_edge_cases(S):
+    """No sources: k_dis = 0 everywhere; no particles: nothing to do."""
+    w = lattice_workload("h2-nosrc-8^3", 8, 2.0, 0, 79)
+    ctx = S.Context()
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    k = ctx.h2_dissociation(np.full(w.n_p, 1e-3, np.float32), 0.5, KAPPA)
+    assert not np.any(k)
+    c0 = S.Context()
+    c0.build_trees(np.zeros((3, 0), np.float32), np.zeros(0, np.float32), w.src_pos, w.src_L)
+    assert c0.h2_dissociation(np.zeros(0, np.float32), 0.5, KAPPA).size == 0

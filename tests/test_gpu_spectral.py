@@ -93,3 +93,17 @@ def test_invalid_temperature_is_rejected(S):
         S.Context(T_eff=100.0)
     with pytest.raises(S.StartError):
         S.Context(T_eff=-1.0)
+
+
+def test_spectral_edge_cases(S):
+    """Heating before any solve is an error; without sources Gamma and the
+    heating are zero."""
+    w = lattice_workload("bb-nosrc-8^3", 8, 2.0, 0, 94)
+    ctx = S.Context(T_eff=1e5)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    with pytest.raises(S.StartError):
+        ctx.heating()
+    ctx.set_state(w.n_H, w.y0)
+    g = np.ones(w.n_p, np.float32)
+    ctx.rt_solve(0.5, gamma_out=g)
+    assert not np.any(g) and not np.any(ctx.heating())
