@@ -506,6 +506,8 @@ def serving(args):
         r = srv.serve(reqs, realtime=True)
         srv.close()
         res[name] = summarize(r)
+        res[name]["context_trims"] = srv.trims
+        res[name]["oom_retries"] = srv.retries
     sp = res["served"]["solves_per_s"] / res["plain"]["solves_per_s"]
     n_p = [r.n_p for r in reqs]
     return {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, N_p=2^U({lo:g},{hi:g}),"

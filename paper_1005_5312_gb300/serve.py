@@ -7,7 +7,10 @@ library context on its own CUDA stream, so the kernels of admitted requests
 overlap on the GPU while their host threads wait in the library (ctypes
 releases the GIL).  Library buffers come from a stream-ordered pool, so one
 request growing its buffers never synchronises the others.  A worker keeps
-its context (and therefore its grown buffers) from request to request.
+its context (and therefore its grown buffers) from request to request,
+unless the library's memory in use then exceeds the trim threshold: the
+worker's context is then recreated, returning its buffers.  A request that
+runs out of device memory is retried once on a fresh context.
 
 `serve(requests, workers=1)` is the plain baseline: one solve at a time.
 Every request's results are the same whether it runs alone or in a mix
@@ -94,10 +97,13 @@ class Server:
     """FIFO admission by worker slots and a device-memory budget."""
 
     def __init__(self, workers: int = 4, budget_bytes: float = 150e9, max_pairs: int = 1 << 27,
-                 tuner=None, **params):
+                 tuner=None, trim_bytes: float = None, **params):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
+        self.trim_bytes = 0.5 * self.budget if trim_bytes is None else float(trim_bytes)
+        self.retries = 0
+        self.trims = 0
         self.max_pairs = int(max_pairs)
         self.params = dict(dict(reuse_chains=1), **params, max_pairs=self.max_pairs)
         self.workers = []
@@ -114,26 +120,47 @@ class Server:
         for w in self.workers:
             w.ctx.close()
 
+    def _fresh_context(self, w: _Worker):
+        """Recreate a worker's context: its grown buffers go back to the pool."""
+        w.ctx.close()
+        w.ctx = Context(stream=w.stream, **self.params)
+
+    def _run(self, ctx, req: SolveRequest):
+        if self.tuner is not None:
+            knobs = self.tuner.params_for(req.n_p, req.n_s, req.theta)
+            knobs["max_pairs"] = min(knobs["max_pairs"], self.max_pairs)
+            ctx.set_params(**knobs)
+        ctx.build_trees(req.pos, req.h, req.src_pos, req.src_L)
+        y = np.ascontiguousarray(req.y0, dtype=np.float64).copy()
+        g = np.zeros(req.n_p, np.float32)
+        rays = 0
+        for _ in range(req.steps):
+            ctx.set_state(req.n_H, y)
+            ctx.rt_solve(req.theta, gamma_out=g)
+            ctx.ionize(req.dt, y_out=y)
+            rays += ctx.stats()["rays"]
+        return g, y, rays
+
     def _solve(self, w: _Worker, req: SolveRequest, t0: float, t_admit: float, est: int):
+        from . import START_ENOMEM, StartError
         try:
-            ctx = w.ctx
-            if self.tuner is not None:
-                knobs = self.tuner.params_for(req.n_p, req.n_s, req.theta)
-                knobs["max_pairs"] = min(knobs["max_pairs"], self.max_pairs)
-                ctx.set_params(**knobs)
-            ctx.build_trees(req.pos, req.h, req.src_pos, req.src_L)
-            y = np.ascontiguousarray(req.y0, dtype=np.float64).copy()
-            g = np.zeros(req.n_p, np.float32)
-            rays = 0
-            for _ in range(req.steps):
-                ctx.set_state(req.n_H, y)
-                ctx.rt_solve(req.theta, gamma_out=g)
-                ctx.ionize(req.dt, y_out=y)
-                rays += ctx.stats()["rays"]
+            try:
+                g, y, rays = self._run(w.ctx, req)
+            except StartError as e:
+                if e.code != START_ENOMEM:
+                    raise
+                self._fresh_context(w)            # out of memory: once more, from scratch
+                with self.cv:
+                    self.retries += 1
+                g, y, rays = self._run(w.ctx, req)
             res = SolveResult(req.rid, req.t_arrive, t_admit, time.perf_counter() - t0, g, y, rays,
                               est)
             with self.cv:
                 self.results.append(res)
+            if memory_in_use() > self.trim_bytes:
+                self._fresh_context(w)
+                with self.cv:
+                    self.trims += 1
         except Exception as e:  # reported by serve()
             with self.cv:
                 self.errors.append((req.rid, repr(e)))

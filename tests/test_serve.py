@@ -59,3 +59,10 @@ def test_results_identical_alone_and_in_a_mix():
     tight.close()
     for a, b in zip(r1[:3], r3):
         assert np.array_equal(a.gamma, b.gamma)
+    # workers whose contexts are recreated after every request (trim threshold 0)
+    trimmed = Server(workers=2, trim_bytes=0.0)
+    r4 = trimmed.serve(reqs, realtime=False)
+    assert trimmed.trims == len(reqs)
+    trimmed.close()
+    for a, b in zip(r1, r4):
+        assert np.array_equal(a.gamma, b.gamma) and np.array_equal(a.y, b.y)
