@@ -37,7 +37,7 @@ class OrcParams(C.Structure):
     _fields_ = [("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
                 ("alpha_A", C.c_double), ("alpha_B", C.c_double),
                 ("src_leaf", C.c_int), ("ptree_leaf", C.c_int),
-                ("diffuse", C.c_int), ("pad_", C.c_int)]
+                ("diffuse", C.c_int), ("pad_", C.c_int), ("T_rec", C.c_double)]
 
 
 _lib = None
@@ -80,6 +80,8 @@ def _load():
         lib.orc_h2_fsh.restype = dp
         lib.orc_h2_fsh.argtypes = [dp]
         lib.orc_bb_integrals.argtypes = [dp, dp, vp, vp]
+        lib.orc_rec_band_integrals.argtypes = [dp, dp, vp, vp]
+        lib.orc_self_terms.argtypes = [vp, vp, vp, lp, vp, vp]
         lib.orc_gamma_spectral.restype = ip
         lib.orc_gamma_spectral.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp, vp]
         lib.orc_h2_dissociation.restype = ip
@@ -105,10 +107,11 @@ class Oracle:
     """
 
     def __init__(self, pos, h, src_pos, src_L, V=None, *, sigma_cm2, len_unit_cm,
-                 alpha_A, alpha_B, diffuse=False, src_leaf=1, ptree_leaf=8):
+                 alpha_A, alpha_B, diffuse=False, src_leaf=1, ptree_leaf=8, T_rec=0.0):
         self.lib = _load()
         self.params = OrcParams(sigma_cm2, len_unit_cm, alpha_A, alpha_B,
-                                int(src_leaf), int(ptree_leaf), int(bool(diffuse)), 0)
+                                int(src_leaf), int(ptree_leaf), int(bool(diffuse)), 0,
+                                float(T_rec))
         self.h_ = self.lib.orc_create(C.byref(self.params))
         self.diffuse = bool(diffuse)
         self.pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(3, -1)
@@ -234,6 +237,17 @@ class Oracle:
         self.lib.orc_ionize(self.h_, _p(gamma), _p(n_H), _p(y0), float(dt), n, _p(y1), _p(nHI))
         return y1, nHI
 
+    def self_terms(self, n_H, y0):
+        """(k_self, self photoheating) per neutral atom of every particle
+        (input order; diffuse case, Eqs. kself1 and gself)."""
+        n_H = np.ascontiguousarray(n_H, dtype=np.float32)
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        n = len(y0)
+        ks = np.zeros(max(n, 1))
+        hs = np.zeros(max(n, 1))
+        self.lib.orc_self_terms(self.h_, _p(n_H), _p(y0), n, _p(ks), _p(hs))
+        return ks[:n], hs[:n]
+
     def sph_density(self, mass):
         """rho_i = sum_j m_j W(r_ij, h_i) (Section 2.1), input order."""
         mass = np.ascontiguousarray(mass, dtype=np.float64)
@@ -243,7 +257,9 @@ class Oracle:
 
     def gamma_spectral(self, nHI, theta: float, T_eff: float, targets=None):
         """(Gamma_eff, heating per neutral atom in erg/s) with blackbody point
-        sources at T_eff; self.last_stats = {rays, hops}."""
+        sources at T_eff (0: photons at the Lyman limit) and, in the diffuse
+        case, recombination photons in the band of T_rec (0: at the Lyman
+        limit), self terms excluded; self.last_stats = {rays, hops}."""
         nHI = np.ascontiguousarray(nHI, dtype=np.float32)
         if targets is None:
             nt, tp = self.np_, None
@@ -299,4 +315,12 @@ def bb_integrals(tau: float, T_eff: float):
     """The oracle's (F_ion, F_heat) of one ray at Lyman-limit depth tau."""
     fi, fh = C.c_double(0.0), C.c_double(0.0)
     _load().orc_bb_integrals(float(tau), float(T_eff), C.byref(fi), C.byref(fh))
+    return fi.value, fh.value
+
+
+def rec_band_integrals(tau: float, T_rec: float):
+    """The oracle's (R_ion, R_heat) of one ray of recombination photons in the
+    band of width k T_rec / h at Lyman-limit depth tau."""
+    fi, fh = C.c_double(0.0), C.c_double(0.0)
+    _load().orc_rec_band_integrals(float(tau), float(T_rec), C.byref(fi), C.byref(fh))
     return fi.value, fh.value

@@ -34,6 +34,12 @@
  *                         (Appendix A), with alpha_B on the spot or alpha_A
  *                         plus the self term k_self (Eq. kself1) in the
  *                         diffuse case (Section 4.1)
+ *   H2 photodissociation  k_dis with self-shielding over the H2 column along
+ *                         the same chains (Appendix B, Eqs. H2ss, NH2)
+ *   spectra               blackbody point sources (Appendix A integrals) and
+ *                         recombination photons in a band of width k T / h
+ *                         with their photoheating (Section 4.1, Eqs. gself,
+ *                         gother)
  *
  * Readings of points the paper leaves open (the same readings bind the GPU
  * path):
@@ -72,6 +78,9 @@ typedef struct {
     int ptree_leaf;      /* max particles per particle-tree leaf */
     int diffuse;         /* 1: every particle emits recombination photons */
     int pad_;
+    double T_rec;        /* 0: recombination photons at nu_L; else the gas
+                            temperature (K) that sets their band width k T / h
+                            (Section 4.1) */
 } orc_params;
 
 typedef struct {
@@ -621,9 +630,17 @@ double orc_march(const orc *o, long target, const float rs32[3], const float *nH
     return tau;
 }
 
-/* Gamma of one target from one tree: sum over its list in walk order. */
-static double gamma_tree(const orc *o, int which, long i, double th, const float *nHI,
-                         long long *rays, long long *hops)
+static void bb_integrals(double tau, double a, double *f_ion, double *f_heat);
+static void band_integrals(double tau, double D, double *r_ion, double *r_heat);
+
+/* Sum over the interaction list of target i on one tree, in walk order.
+ * spec 0: photons at nu_L, L e^-tau / (4 pi r^2), no heating; spec 1:
+ * blackbody with a = h nu_L / (k T_eff), L F_ion(tau) / (4 pi r^2) and the
+ * heating factor L F_heat(tau) / (4 pi r^2); spec 2: the recombination band of
+ * width D = k T_rec / (h nu_L), the same with R_ion and R_heat.  Returns the
+ * Gamma sum and adds the heating factors to *heat. */
+static double tree_sum(const orc *o, int which, long i, double th, const float *nHI, int spec,
+                       double par, double *heat, long long *rays, long long *hops)
 {
     const otree *t = pick_tree(o, which);
     if (!t->n) return 0.0;
@@ -654,12 +671,29 @@ static double gamma_tree(const orc *o, int which, long i, double th, const float
         double tau = march(o, i, rs, nHI, &nh, NULL);
         double r2 = d2_64(o->px[i], o->py[i], o->pz[i], rs[0], rs[1], rs[2]);
         if (r2 < rfloor * rfloor) r2 = rfloor * rfloor;
-        g += L * exp(-tau) / (4.0 * ORC_PI * r2 * lu * lu);
+        if (spec == 0) {
+            g += L * exp(-tau) / (4.0 * ORC_PI * r2 * lu * lu);
+        } else {
+            double fi, fh;
+            if (spec == 1) bb_integrals(tau, par, &fi, &fh);
+            else band_integrals(tau, par, &fi, &fh);
+            double flux = L / (4.0 * ORC_PI * r2 * lu * lu);
+            g += flux * fi;
+            *heat += flux * fh;
+        }
         *rays += 1;
         *hops += nh;
     }
     free(v.v);
     return g;
+}
+
+/* Gamma of one target from one tree: sum over its list in walk order. */
+static double gamma_tree(const orc *o, int which, long i, double th, const float *nHI,
+                         long long *rays, long long *hops)
+{
+    double unused = 0.0;
+    return tree_sum(o, which, i, th, nHI, 0, 0.0, &unused, rays, hops);
 }
 
 /* Photoionisation rate Gamma (photons cm^-2 s^-1) at the given targets
@@ -686,28 +720,77 @@ int orc_gamma(const orc *o, const float *nHI, float theta, const long *targets, 
     return 0;
 }
 
+#define ORC_HNU_L_ERG (13.6 * 1.602176634e-12)   /* h nu_L = 13.6 eV */
+#define ORC_KB_ERG 1.380649e-16                  /* Boltzmann constant, erg/K */
+
+/* Self terms of a particle per neutral atom, from its state (y0, n_H) and
+ * volume V: the photoionisation rate k_self of Eq. kself1 in its reduced form
+ * and the photoheating rate of Eq. gself divided by n_HI.  With
+ * n_e = n_p = x n_H, tau_s = sigma n_HI R, R = (3V/4pi)^(1/3) and
+ * phi(t) = (1 - e^-t)/t (the division by n_HI taken inside phi, so that a
+ * fully ionised particle is regular):
+ *   photons at nu_L (T_rec = 0): k_self = alpha_1 n_e n_p sigma R phi(tau_s),
+ *     no heating;
+ *   the band 1 <= u <= 1 + D, D = k T_rec / (h nu_L), sigma_nu = sigma u^-3:
+ *     k_self = alpha_1 n_e n_p sigma R (1/D) int u^-3 phi(tau_s u^-3) du
+ *     heat   = alpha_1 n_e n_p sigma R h nu_L (1/D) int (u-1) u^-3 phi(tau_s u^-3) du
+ *     by composite Simpson with 512 intervals. */
+static void self_terms(const orc *o, long i, double nh, double y0, double *k_self,
+                       double *h_self)
+{
+    double a1 = o->p.alpha_A - o->p.alpha_B;
+    double sig = o->p.sigma_cm2;
+    double x0 = 1.0 - y0;
+    double R = cbrt(3.0 * o->V[i] / (4.0 * ORC_PI)) * o->p.len_unit_cm;
+    double ts = sig * (y0 * nh) * R;
+    if (o->p.T_rec <= 0.0) {
+        double phi = ts > 0.0 ? -expm1(-ts) / ts : 1.0;
+        *k_self = a1 * x0 * x0 * nh * nh * sig * R * phi;
+        *h_self = 0.0;
+        return;
+    }
+    double D = ORC_KB_ERG * o->p.T_rec / ORC_HNU_L_ERG;
+    const int n = 512;
+    double du = D / n, si = 0.0, sh = 0.0;
+    for (int k = 0; k <= n; ++k) {
+        double u = 1.0 + k * du;
+        double wgt = (k == 0 || k == n) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+        double u3 = 1.0 / (u * u * u);
+        double t = ts * u3;
+        double phi = t > 0.0 ? -expm1(-t) / t : 1.0;
+        si += wgt * u3 * phi;
+        sh += wgt * (u - 1.0) * u3 * phi;
+    }
+    double pre = a1 * x0 * x0 * nh * nh * sig * R;
+    *k_self = pre * (si * du / (3.0 * D));
+    *h_self = pre * ORC_HNU_L_ERG * (sh * du / (3.0 * D));
+}
+
+/* Self terms of particles [0, n) (input order, diffuse case): k_self and the
+ * self photoheating, both per neutral atom. */
+void orc_self_terms(const orc *o, const float *nH, const double *y0, long n, double *k_self,
+                    double *h_self)
+{
+    for (long i = 0; i < n; ++i) self_terms(o, i, (double)nH[i], y0[i], &k_self[i], &h_self[i]);
+}
+
 /* Implicit hydrogen update over dt (Appendix A), hydrogen only, isothermal:
  * dy/dt = -k y + alpha n_H (1 - y)^2 for the neutral fraction y, solved by
  * one backward-Euler step.  k = sigma Gamma, plus in the diffuse case the
- * self term of Eq. kself1 per neutral atom, alpha_1 x^2 n_H^2 sigma R phi
- * (tau_s) with R = (3V/4pi)^(1/3), tau_s = sigma n_HI R and
- * phi(t) = (1 - e^-t)/t, taken from the step-start state.  Writes y1 and
- * the float32 neutral density y1 n_H. */
+ * self term of Eq. kself1 per neutral atom (self_terms), taken from the
+ * step-start state.  Writes y1 and the float32 neutral density y1 n_H. */
 void orc_ionize(const orc *o, const double *gamma, const float *nH, const double *y0, double dt,
                 long n, double *y1, float *nHI_out)
 {
     double alpha = o->p.diffuse ? o->p.alpha_A : o->p.alpha_B;
-    double a1 = o->p.alpha_A - o->p.alpha_B;
     double sig = o->p.sigma_cm2;
     for (long i = 0; i < n; ++i) {
         double nh = nH[i];
         double k = sig * gamma[i];
         if (o->p.diffuse) {
-            double x0 = 1.0 - y0[i];
-            double R = cbrt(3.0 * o->V[i] / (4.0 * ORC_PI)) * o->p.len_unit_cm;
-            double ts = sig * (y0[i] * nh) * R;
-            double phi = ts > 0.0 ? -expm1(-ts) / ts : 1.0;
-            k += a1 * x0 * x0 * nh * nh * sig * R * phi;
+            double ks, hs;
+            self_terms(o, i, nh, y0[i], &ks, &hs);
+            k += ks;
         }
         /* y1 - y0 = dt (-k y1 + alpha n_H (1 - y1)^2): A y1^2 - b y1 + c = 0 */
         double A = alpha * nh * dt, K = k * dt;
@@ -820,9 +903,6 @@ int orc_h2_dissociation(const orc *o, const float *nH2, float theta, double kapp
 /* Multi-frequency point sources: photoionisation and photoheating      */
 /* (Appendix A integrals with blackbody sources as in Section 3.1.1)    */
 
-#define ORC_HNU_L_ERG (13.6 * 1.602176634e-12)   /* h nu_L = 13.6 eV */
-#define ORC_KB_ERG 1.380649e-16                  /* Boltzmann constant, erg/K */
-
 /* The spectral integrals of one ray with Lyman-limit optical depth tau, per
  * ionising photon emitted: with u = nu / nu_L, the blackbody photon spectrum
  * w(u) = u^2 / (e^(a u) - 1), a = h nu_L / (k T_eff), normalised over u >= 1,
@@ -856,13 +936,46 @@ void orc_bb_integrals(double tau, double T_eff, double *f_ion, double *f_heat)
     bb_integrals(tau, ORC_HNU_L_ERG / (ORC_KB_ERG * T_eff), f_ion, f_heat);
 }
 
-/* Gamma_eff = sum L F_ion(tau) / (4 pi r^2) (photons cm^-2 s^-1 at sigma_L:
+/* Recombination photons in a band (Section 4.1): in an isothermal medium at
+ * T_rec an emitter spreads its photons evenly over nu_L <= nu <= nu_L + dnu,
+ * dnu = k T_rec / h (and a cell's luminosity-weighted width is the same).
+ * With u = nu / nu_L, D = dnu / nu_L and sigma_nu = sigma_L u^-3, a ray of
+ * Lyman-limit depth tau delivers per emitted photon
+ *   R_ion(tau)  = (1/D) int_1^{1+D} u^-3 e^(-tau u^-3) du
+ *   R_heat(tau) = (1/D) int_1^{1+D} (u - 1) u^-3 e^(-tau u^-3) du
+ * (k_alpha of Section 4.1 per neutral atom in units of sigma_L, and Eq.
+ * gother per neutral atom in units of sigma_L h nu_L), by composite Simpson
+ * with 512 intervals. */
+static void band_integrals(double tau, double D, double *r_ion, double *r_heat)
+{
+    const int n = 512;
+    double du = D / n, si = 0.0, sh = 0.0;
+    for (int k = 0; k <= n; ++k) {
+        double u = 1.0 + k * du;
+        double wgt = (k == 0 || k == n) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+        double u3 = 1.0 / (u * u * u);
+        double v = u3 * exp(-tau * u3);
+        si += wgt * v;
+        sh += wgt * (u - 1.0) * v;
+    }
+    *r_ion = si * du / (3.0 * D);
+    *r_heat = sh * du / (3.0 * D);
+}
+
+void orc_rec_band_integrals(double tau, double T_rec, double *r_ion, double *r_heat)
+{
+    band_integrals(tau, ORC_KB_ERG * T_rec / ORC_HNU_L_ERG, r_ion, r_heat);
+}
+
+/* Gamma_eff = sum L F(tau) / (4 pi r^2) (photons cm^-2 s^-1 at sigma_L:
  * k_ion = sigma_L Gamma_eff per neutral atom) and the photoheating rate per
- * neutral atom H = sigma_L h nu_L sum L F_heat(tau) / (4 pi r^2) (erg/s) over
- * the point-source list, tau the Lyman-limit optical depth of Eq. tau.  In
- * the diffuse case the recombination photons stay monochromatic at nu_L (the
- * emitter tree adds L e^-tau / (4 pi r^2) to Gamma_eff and nothing to H).
- * stats = {rays, hops}. */
+ * neutral atom H = sigma_L h nu_L sum L F_heat(tau) / (4 pi r^2) (erg/s),
+ * tau the Lyman-limit optical depth of Eq. tau.  Point sources: blackbody
+ * at T_eff (F_ion, F_heat), or photons at nu_L when T_eff = 0 (e^-tau, no
+ * heating).  In the diffuse case the emitter tree adds the recombination
+ * photons: in the band of width k T_rec / h when T_rec > 0 (R_ion, and
+ * R_heat: Eq. gother), else at nu_L.  The self terms (Eq. gself) are not
+ * included (orc_self_terms).  stats = {rays, hops}. */
 int orc_gamma_spectral(const orc *o, const float *nHI, float theta, double T_eff,
                        const long *targets, long nt, double *gamma_out, double *heat_out,
                        long long *stats)
@@ -870,50 +983,21 @@ int orc_gamma_spectral(const orc *o, const float *nHI, float theta, double T_eff
     long n = targets ? nt : o->np;
     long long rays = 0, hops = 0;
     double th = theta;
-    double a = ORC_HNU_L_ERG / (ORC_KB_ERG * T_eff);
-    const otree *t = &o->st;
-    double lu = o->p.len_unit_cm;
-    double rfloor = 1e-6 * o->side;
+    int pspec = T_eff > 0.0 ? 1 : 0;
+    double a = T_eff > 0.0 ? ORC_HNU_L_ERG / (ORC_KB_ERG * T_eff) : 0.0;
+    int espec = o->p.T_rec > 0.0 ? 2 : 0;
+    double D = ORC_KB_ERG * o->p.T_rec / ORC_HNU_L_ERG;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : rays, hops)
     for (long q = 0; q < n; ++q) {
         long i = targets ? targets[q] : q;
-        double g = 0.0, hsum = 0.0;
-        if (t->n) {
-            lvec v = {0};
-            walk_node(t, 0, o->px[i], o->py[i], o->pz[i], th * th, -1, &v);
-            for (long e = 0; e < v.n; ++e) {
-                double rs[3], L;
-                long ent = v.v[e];
-                if (ent >= 0) {
-                    rs[0] = t->cen[3 * ent]; rs[1] = t->cen[3 * ent + 1]; rs[2] = t->cen[3 * ent + 2];
-                    L = t->L[ent];
-                } else {
-                    long j = o->sperm[-ent - 1];
-                    rs[0] = o->sx[j]; rs[1] = o->sy[j]; rs[2] = o->sz[j];
-                    L = o->sL[j];
-                }
-                long nh = 0;
-                double tau = march(o, i, rs, nHI, &nh, NULL);
-                double r2 = d2_64(o->px[i], o->py[i], o->pz[i], rs[0], rs[1], rs[2]);
-                if (r2 < rfloor * rfloor) r2 = rfloor * rfloor;
-                double fi, fh;
-                bb_integrals(tau, a, &fi, &fh);
-                double flux = L / (4.0 * ORC_PI * r2 * lu * lu);
-                g += flux * fi;
-                hsum += flux * fh;
-                rays += 1;
-                hops += nh;
-            }
-            free(v.v);
-        }
-        if (o->p.diffuse) {
-            long long r = 0, hc = 0;
-            g += gamma_tree(o, 2, i, th, nHI, &r, &hc);
-            rays += r;
-            hops += hc;
-        }
+        long long r = 0, hc = 0;
+        double hsum = 0.0;
+        double g = tree_sum(o, 1, i, th, nHI, pspec, a, &hsum, &r, &hc);
+        if (o->p.diffuse) g += tree_sum(o, 2, i, th, nHI, espec, D, &hsum, &r, &hc);
         gamma_out[q] = g;
         heat_out[q] = o->p.sigma_cm2 * ORC_HNU_L_ERG * hsum;
+        rays += r;
+        hops += hc;
     }
     if (stats) { stats[0] = rays; stats[1] = hops; }
     return 0;

@@ -402,11 +402,12 @@ def test_gamma_theta_error_is_small_in_thin_limit():
 
 
 # ---------------------------------------------------------------- ionisation
-def _ionizer(diffuse=False, alpha_B=ALPHA_B, V=None):
+def _ionizer(diffuse=False, alpha_B=ALPHA_B, V=None, T_rec=0.0):
     pos = np.zeros((3, 1), np.float32)
     return oracle.Oracle(pos, np.ones(1, np.float32), np.zeros((3, 1), np.float32),
                          np.ones(1), V if V is not None else np.ones(1), sigma_cm2=SIGMA_CM2,
-                         len_unit_cm=KPC_CM, alpha_A=ALPHA_A, alpha_B=alpha_B, diffuse=diffuse)
+                         len_unit_cm=KPC_CM, alpha_A=ALPHA_A, alpha_B=alpha_B, diffuse=diffuse,
+                         T_rec=T_rec)
 
 
 def test_ionize_limits_and_residual():
@@ -451,13 +452,16 @@ def test_ionize_equilibrium_and_ode_convergence():
     assert abs((1 - yv[0]) / x_exact - 1) < 1e-3
 
 
-def test_diffuse_self_term_opaque_limit():
-    """Opaque particle: k_self per volume -> alpha_1 n_e n_p (Section 4.1)."""
+@pytest.mark.parametrize("T_rec", [0.0, 1e4])
+def test_diffuse_self_term_opaque_limit(T_rec):
+    """Opaque particle: k_self per volume -> alpha_1 n_e n_p (Section 4.1),
+    whether the recombination photons sit at the Lyman limit or fill the band
+    of width k T / h."""
     nH = np.float32(1.0)
     y0 = 0.5
     dt = 1e9
     V = np.array([1.0])            # 1 kpc^3: tau_self ~ 1e4
-    o = _ionizer(diffuse=True, V=V)
+    o = _ionizer(diffuse=True, V=V, T_rec=T_rec)
     y1, _ = o.ionize(np.zeros(1), np.array([nH]), np.array([y0]), dt)
     A = ALPHA_A * float(nH) * dt
     # back out k from the implicit equation
@@ -725,5 +729,123 @@ def test_spectral_gamma_in_a_uniform_medium():
             flux = L[s] / (4 * math.pi * (r * KPC_CM) ** 2)
             rg += flux * fi
             rh += flux * fh
+        assert g[q] == pytest.approx(rg, rel=1e-7)
+        assert hh[q] == pytest.approx(SIGMA_CM2 * HNU_L * rh, rel=1e-7)
+
+
+# ---------------------------------------------------------------- recombination band
+def _band_D(T):
+    return K_B * T / HNU_L
+
+
+def _band_quad(tau, T):
+    """R_ion, R_heat by adaptive quadrature (scipy): photons spread evenly
+    over u = nu/nu_L in [1, 1 + kT/(h nu_L)], cross-section u^-3."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    D = _band_D(T)
+    ri = quad(lambda u: u ** -3 * math.exp(-tau * u ** -3), 1.0, 1.0 + D, epsabs=0,
+              epsrel=1e-13, limit=200)[0]
+    rh = quad(lambda u: (u - 1.0) * u ** -3 * math.exp(-tau * u ** -3), 1.0, 1.0 + D, epsabs=0,
+              epsrel=1e-13, limit=200)[0]
+    return ri / D, rh / D
+
+
+@pytest.mark.parametrize("T", [1e3, 1e4, 3e4])
+def test_band_integrals_closed_forms_at_zero_depth(T):
+    """Unattenuated: (1/D) int u^-3 du = (1 - (1+D)^-2) / (2D) and
+    (1/D) int (u-1) u^-3 du = D / (2 (1+D)^2)."""
+    D = _band_D(T)
+    ri, rh = oracle.rec_band_integrals(0.0, T)
+    assert ri == pytest.approx((1 - (1 + D) ** -2) / (2 * D), rel=1e-12)
+    assert rh == pytest.approx(D / (2 * (1 + D) ** 2), rel=1e-10)
+
+
+@pytest.mark.parametrize("T", [1e4, 5e4])
+def test_band_integrals_against_adaptive_quadrature(T):
+    for tau in (0.1, 1.0, 10.0, 100.0):
+        ri, rh = oracle.rec_band_integrals(tau, T)
+        qi, qh = _band_quad(tau, T)
+        assert ri == pytest.approx(qi, rel=1e-8) and rh == pytest.approx(qh, rel=1e-8), tau
+
+
+def test_band_narrow_limit_is_the_lyman_limit_line():
+    """A band of vanishing width (T -> 0) is the line at nu_L: R_ion -> e^-tau
+    and the mean excess energy per photon R_heat / R_ion -> D / 2."""
+    T = 1.0
+    D = _band_D(T)
+    for tau in (0.0, 0.5, 2.0, 5.0):
+        ri, rh = oracle.rec_band_integrals(tau, T)
+        assert ri == pytest.approx(math.exp(-tau), rel=1e-4)
+        assert rh / ri == pytest.approx(D / 2, rel=1e-4)
+
+
+def test_band_self_terms_limits():
+    """Self terms per neutral atom (Eqs. kself1, gself): an opaque particle
+    absorbs its whole band, k_self n_HI -> alpha_1 n_e n_p and the heating
+    n_HI -> alpha_1 n_e n_p k T / 2 (the mean excess energy of the band); a
+    transparent one gives alpha_1 n_e n_p sigma R times the unattenuated
+    band integrals; a narrow band is the line at nu_L."""
+    a1 = ALPHA_A - ALPHA_B
+    T = 2e4
+    D = _band_D(T)
+    y0 = np.array([0.3])
+    # opaque: tau_s ~ sigma n_HI R = 6.3e-18 * 0.3 * 2e21 ~ 4e3
+    o = _ionizer(diffuse=True, V=np.array([1.0]), T_rec=T)
+    ks, hs = o.self_terms(np.array([1.0], np.float32), y0)
+    nenp = a1 * (0.7 * 1.0) ** 2
+    assert ks[0] * 0.3 == pytest.approx(nenp, rel=1e-6)
+    assert hs[0] * 0.3 == pytest.approx(nenp * K_B * T / 2, rel=1e-8)
+    # transparent: tau_s ~ 6.3e-18 * 0.3e-6 * 3e17 ~ 6e-7
+    V = 1e-12
+    o = _ionizer(diffuse=True, V=np.array([V]), T_rec=T)
+    nH = np.float32(1e-6)
+    ks, hs = o.self_terms(np.array([nH]), y0)
+    R = (3 * V / (4 * math.pi)) ** (1 / 3) * KPC_CM
+    pre = a1 * (0.7 * float(nH)) ** 2 * SIGMA_CM2 * R
+    assert ks[0] == pytest.approx(pre * (1 - (1 + D) ** -2) / (2 * D), rel=1e-5)
+    assert hs[0] == pytest.approx(pre * HNU_L * D / (2 * (1 + D) ** 2), rel=1e-5)
+    # narrow band = line
+    for V in (1e-3, 1e-1):
+        k0, h0 = _ionizer(diffuse=True, V=np.array([V])).self_terms(np.array([1e-2], np.float32),
+                                                                     y0)
+        k1, h1 = _ionizer(diffuse=True, V=np.array([V]), T_rec=1.0).self_terms(
+            np.array([1e-2], np.float32), y0)
+        assert k1[0] == pytest.approx(k0[0], rel=1e-4) and h0[0] == 0.0
+        assert 0 < h1[0] < 1e-4 * HNU_L * k1[0]
+
+
+def test_band_gamma_in_a_uniform_medium():
+    """Diffuse emitters with the band, uniform n_HI, theta = 0: every chain
+    has tau_L = sigma n r, so the emitters add sum L_j R_ion(sigma n r) /
+    (4 pi r^2) to Gamma_eff and sigma h nu_L sum L_j R_heat / (4 pi r^2) to the
+    heating (Eq. gother), with R from adaptive quadrature; point sources at
+    T_eff = 0 add L e^-tau / (4 pi r^2) and no heating."""
+    T = 1e4
+    pos, h, src, L = _lattice_problem(5, 1.0, 43, n_s=2)
+    n = pos.shape[1]
+    V = np.full(n, (1.0 / 5) ** 3)
+    o = oracle.Oracle(pos, h, src, L, V, diffuse=True, T_rec=T, **PHYS)
+    y = np.full(n, 0.4)
+    nH = np.full(n, 2e-2, np.float32)
+    o.set_emitters(y, nH)
+    eL = o.emitter_L()
+    nHI = (y * nH.astype(np.float64)).astype(np.float32)
+    nn = float(nHI[0])
+    idx = np.array([0, 62, 124])
+    g, hh = o.gamma_spectral(nHI, 0.0, 0.0, targets=idx)
+    p = pos.astype(np.float64)
+    for q, i in enumerate(idx):
+        rg, rh = 0.0, 0.0
+        for s in range(src.shape[1]):
+            r = math.sqrt(sum((p[a, i] - float(src[a, s])) ** 2 for a in range(3)))
+            rg += L[s] * math.exp(-SIGMA_CM2 * KPC_CM * nn * r) / (4 * math.pi * (r * KPC_CM) ** 2)
+        for j in range(n):
+            if j == i:
+                continue
+            r = math.sqrt(sum((p[a, i] - p[a, j]) ** 2 for a in range(3)))
+            ri, rhh = _band_quad(SIGMA_CM2 * KPC_CM * nn * r, T)
+            flux = eL[j] / (4 * math.pi * (r * KPC_CM) ** 2)
+            rg += flux * ri
+            rh += flux * rhh
         assert g[q] == pytest.approx(rg, rel=1e-7)
         assert hh[q] == pytest.approx(SIGMA_CM2 * HNU_L * rh, rel=1e-7)
