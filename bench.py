@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--no-resident", action="store_true")
     ap.add_argument("--no-diffuse", action="store_true")
     ap.add_argument("--no-next", action="store_true",
-                    help="skip the SPH density, H2 photodissociation and blackbody-source lines")
+                    help="skip the SPH density, H2 photodissociation, blackbody-source and "
+                         "recombination-band lines")
     ap.add_argument("--no-method-error", action="store_true")
     ap.add_argument("--lognormal256", action="store_true",
                     help="add the 256^3 log-normal diffuse workload (about a minute)")
@@ -413,16 +414,19 @@ def blackbody_sources(S, w, dev, args, T, flush):
             "note": "walk + memoised chains + spectral Gamma and heating per pair (no tree build)"}
 
 
-def diffuse_workload(S, dev, args, T):
+def diffuse_workload(S, dev, args, T, T_rec=0.0):
     """The diffuse-recombination shadowing workload at full size: 128^3
     particles (all emitting), eight 200x clumps, one 3e51/s central source,
     theta = 0.7; coupled full-path steps (emitter moments, walk over both
-    trees, memoised march in target chunks, Gamma, update with k_self)."""
+    trees, memoised march in target chunks, Gamma, update with k_self).
+    T_rec > 0: the recombination photons fill the band of width k T_rec / h
+    (band tables per emitter pair, photoheating with its self term)."""
     import torch
     from start_inputs import config3
     w = config3()
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream, max_pairs=1 << 29)
+    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream, max_pairs=1 << 29,
+                    T_rec=T_rec)
     y = T(w.y0)
     g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
     pos, h, sp, sL, V, nH = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L), T(w.V), T(w.n_H)
@@ -450,7 +454,7 @@ def diffuse_workload(S, dev, args, T):
     return {"value": rays / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms / steps,
             "rays_per_step": rays / steps, "chunks": st["chunks"],
             "evaluations_per_ray": st["evals"] / max(1, st["rays"]), "workload": w.name,
-            "theta": 0.7}
+            "theta": 0.7, "T_rec": T_rec}
 
 
 def lognormal_256(S, dev, args, T):
@@ -658,6 +662,9 @@ def run_gpu(args, w):
         out["blackbody_sources"] = blackbody_sources(S, w, dev, args, T, flush)
     if not args.no_diffuse:
         out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
+        if not args.no_next:
+            out["diffuse_128cubed_recombination_band"] = diffuse_workload(S, dev, args, T,
+                                                                           T_rec=1e4)
     if args.lognormal256:
         out["lognormal_256cubed"] = lognormal_256(S, dev, args, T)
 

@@ -128,6 +128,16 @@ typedef struct start_params {
                               Lyman-limit depth of the chain.  L stays the
                               ionising photon rate.  Uses the memoised march;
                               reuse_chains is ignored */
+    double T_rec;          /* diffuse case: 0 = recombination photons at the
+                              Lyman limit; else the (isothermal) gas temperature
+                              in K, 100 to 1e5, and the photons of every emitter
+                              fill the band nu_L <= nu <= nu_L + k T_rec / h
+                              evenly (Section 4.1): emitter rays add
+                              L R_ion(tau) / (4 pi r^2) to Gamma, the self term
+                              k_self becomes its band average, and the
+                              photoheating of the recombination photons (Eqs.
+                              gself, gother) joins start_get_heating.  Uses the
+                              memoised march */
 } start_params;
 
 /* Counters of the last start_rt_solve. */
@@ -237,11 +247,18 @@ int start_sph_density(start_ctx *c, const float *mass, float *rho_out);
 /* Photoheating rate per neutral hydrogen atom (erg/s), input order, of the
  * last start_rt_solve: sigma_L h nu_L sum L F_heat(tau) / (4 pi r^2) over the
  * point sources with F_heat the spectral integral of the absorbed photons'
- * excess energy h (nu - nu_L) (Appendix A), h nu_L = 13.6 eV.  Zero with
- * monochromatic sources (T_eff = 0): their photons carry no excess energy.
- * The diffuse recombination photons add none (their excess energy is kT,
- * not modelled).  heat_out [n_p] float32, host or device.
- * START_ENOTBUILT before the first solve. */
+ * excess energy h (nu - nu_L) (Appendix A), h nu_L = 13.6 eV.  Point sources
+ * at the Lyman limit (T_eff = 0) add nothing: their photons carry no excess
+ * energy.  In the diffuse case with the recombination band (T_rec > 0) the
+ * recombination photons add
+ *   sigma_L h nu_L sum L R_heat(tau) / (4 pi r^2) over the other emitters
+ *     (Eq. gother per neutral atom; R_heat the band average of
+ *     (nu/nu_L - 1) (nu/nu_L)^-3 e^(-tau (nu/nu_L)^-3)), and
+ *   the particle's own absorbed recombination photons (Eq. gself per neutral
+ *     atom, from the state of the solve),
+ * and nothing when T_rec = 0.  All zero after a solve without spectra.
+ * heat_out [n_p] float32, host or device.  START_ENOTBUILT before the first
+ * solve. */
 int start_get_heating(start_ctx *c, float *heat_out);
 
 /* H2 photodissociation rate of Appendix B for every particle:

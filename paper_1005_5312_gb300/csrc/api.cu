@@ -382,6 +382,7 @@ static int check_params(start_params &d)
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
     if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;
+    if (!(d.T_rec == 0.0 || (d.T_rec >= 100.0 && d.T_rec <= 1e5))) return START_EINVAL;
     return START_OK;
 }
 

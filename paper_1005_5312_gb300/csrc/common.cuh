@@ -104,8 +104,9 @@ struct start_ctx {
     st::DBuf w_save;  // float n_HI of the records while they hold n_H2
     st::DBuf heat;    // float photoheating per neutral atom (erg/s), Morton order
     bool heat_valid = false;           // heat holds the last solve's (blackbody sources)
-    st::DBuf spec_tab;                 // float ln F_ion, ln F_heat tables (blackbody)
-    double spec_T = 0.0;               // temperature spec_tab was built for
+    st::DBuf spec_tab;                 // float ln F tables: blackbody ion, heat; band ion, heat
+    double spec_T = -1.0;              // T_eff and T_rec spec_tab was built for
+    double spec_Trec = -1.0;
     st::DBuf y;       // double neutral fraction
     st::DBuf V;       // double volume (len_unit^3)
     st::DBuf gam;     // float Gamma (cgs)
@@ -242,7 +243,14 @@ int run_h2_dissociation(start_ctx *c, const float *nH2_dev, float theta, float *
 constexpr int kSpecN = 8192;              // table points in s = ln(1 + tau / kSpecTau0)
 constexpr double kSpecTau0 = 1e-3;
 constexpr double kSpecTauMax = 1e6;       // F = 0 beyond
-int spectral_table(start_ctx *c);         // (re)builds spec_tab for p.T_eff
+int spectral_table(start_ctx *c);         // (re)builds spec_tab for p.T_eff, p.T_rec
+// Gamma solves with blackbody point sources or diffuse emitters in a band
+inline bool spectral_mode(const start_ctx *c)
+{
+    return c->p.T_eff > 0.0 || (c->diffuse && c->p.T_rec > 0.0);
+}
+constexpr double kHnuLErg = 13.6 * 1.602176634e-12;   // h nu_L, erg
+constexpr double kBoltzErg = 1.380649e-16;            // k, erg / K
 
 // resident.cu
 void resident_reset(start_ctx *c);

@@ -754,16 +754,18 @@ __global__ void k_sum_jump_counts(const unsigned long long *part, long long nblo
 // What a pair adds to its target.  MODE 0: L e^-tau / (4 pi r^2).
 // MODE 1 (k_dis): the chain sums are H2 columns (cm^-2) and each pair adds
 // L f_sh(N_H2 / 1e14 cm^-2) / (4 pi r^2) (Eq. H2ss); the resident Gamma is
-// left alone.  MODE 2 (blackbody point sources): a point-source pair adds
-// L F_ion(tau) / (4 pi r^2) to Gamma and L F_heat(tau) / (4 pi r^2) to the
-// heating sum, F from the ln-tables of spectral.cu (linear in
-// s = ln(1 + tau / tau0)); emitter pairs stay monochromatic.
+// left alone.  MODE 2 (spectra): a point-source pair with blackbody sources,
+// or an emitter pair with the recombination band, adds L F_ion(tau) /
+// (4 pi r^2) to Gamma and L F_heat(tau) / (4 pi r^2) to the heating sum, F
+// from the ln-tables of spectral.cu (linear in s = ln(1 + tau / tau0)); the
+// other pairs add L e^-tau / (4 pi r^2) and no heating.
 struct GammaExtra {
-    const float *tab;      // ln F_ion [kSpecN], then ln F_heat [kSpecN]
+    const float *tab;      // ln F: blackbody ion, heat; band ion, heat [kSpecN each]
     float inv_tau0, inv_ds;
     float *heat;           // heating per neutral atom, Morton order
     float heat_conv;
     u32 point_end;         // canonical ids below this are point sources
+    int point_bb, emit_band;
 };
 
 __device__ __forceinline__ float spec_lookup(const float *tab, float sidx)
@@ -808,10 +810,11 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
                 if (MODE == 1) {
                     float xs = tau * 1e-14f;
                     v = dil * (xs <= 1.f ? 1.f : powf(xs, -0.75f));
-                } else if (MODE == 2 && vid < x.point_end) {
+                } else if (MODE == 2 && (vid < x.point_end ? x.point_bb : x.emit_band)) {
+                    const float *tb = x.tab + (vid < x.point_end ? 0 : 2 * kSpecN);
                     float sidx = log1pf(tau * x.inv_tau0) * x.inv_ds;
-                    v = dil * spec_lookup(x.tab, sidx);
-                    hv = dil * spec_lookup(x.tab + kSpecN, sidx);
+                    v = dil * spec_lookup(tb, sidx);
+                    hv = dil * spec_lookup(tb + kSpecN, sidx);
                 } else {
                     v = dil * expf(-tau);
                 }
@@ -1086,7 +1089,7 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     a.state = c->m_st[c->memo_final].as<uint4>();
     long long threads = (t1 - t0) * 32;
     GammaExtra x{};
-    const bool spec = c->solve_kind == 0 && c->p.T_eff > 0.0;
+    const bool spec = c->solve_kind == 0 && spectral_mode(c);
     if (spec) {
         x.tab = c->spec_tab.as<float>();
         x.inv_tau0 = (float)(1.0 / kSpecTau0);
@@ -1095,6 +1098,8 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
         // sigma_L h nu_L (erg cm^2) times the flux conversion
         x.heat_conv = (float)(c->p.sigma_cm2 * 13.6 * 1.602176634e-12 * (double)conv);
         x.point_end = a.SN + a.NS;
+        x.point_bb = c->p.T_eff > 0.0;
+        x.emit_band = c->walk_emit && c->p.T_rec > 0.0;
     }
     const unsigned grid = grid_for(threads, 256);
     const u64 *lo = c->loff.as<u64>();

@@ -503,6 +503,53 @@ static MarchArgs march_args(start_ctx *c, long long npairs)
     return a;
 }
 
+// ---------------------------------------------------------------- self terms
+// Self terms of an emitting particle per neutral atom (Section 4.1):
+// alpha_1 n_e n_p sigma R times
+//   photons at nu_L:  phi(tau_s)                       (Eq. kself1, reduced)
+//   band of width D:  (1/D) int u^-3 phi(tau_s u^-3) du over 1 <= u <= 1 + D
+// for k_self, and for the photoheating of Eq. gself the band's
+// h nu_L (1/D) int (u - 1) u^-3 phi(tau_s u^-3) du, with tau_s = sigma n_HI R,
+// R = (3V/4pi)^(1/3) and phi(t) = (1 - e^-t)/t (n_HI divided out inside phi,
+// so that a fully ionised particle stays regular).  The band integrals take
+// composite 6-point Gauss-Legendre over 4 panels (the integrands are smooth
+// and the band narrow).
+__device__ __forceinline__ double phi_self(double t) { return t > 0.0 ? -expm1(-t) / t : 1.0; }
+
+__device__ void band_self(double ts, double D, double &ik, double &ih)
+{
+    const double gx[3] = {0.2386191860831969, 0.6612093864662645, 0.9324695142031521};
+    const double gw[3] = {0.4679139345726910, 0.3607615730481386, 0.1713244923791704};
+    const double hw = 0.125 * D;   // half a panel
+    double sk = 0.0, sh = 0.0;
+    for (int p = 0; p < 4; ++p) {
+        const double mid = 1.0 + (2 * p + 1) * hw;
+        for (int k = 0; k < 6; ++k) {
+            const double u = mid + (k < 3 ? -hw : hw) * gx[k < 3 ? k : k - 3];
+            const double u3 = 1.0 / (u * u * u);
+            const double v = gw[k < 3 ? k : k - 3] * u3 * phi_self(ts * u3);
+            sk += v;
+            sh += v * (u - 1.0);
+        }
+    }
+    ik = sk * hw / D;
+    ih = sh * hw / D;
+}
+
+// heat[i] += the self photoheating per neutral atom (band only), Morton order
+__global__ void k_self_heat(float *heat, const double *y, const float *nH, const double *V,
+                            long long np, double a1, double sigma, double len_cm, double D)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const double y0 = y[i], nh = (double)nH[i], x0 = 1.0 - y0;
+    const double R = cbrt(3.0 * V[i] / (4.0 * 3.14159265358979323846)) * len_cm;
+    double ik, ih;
+    band_self(sigma * (y0 * nh) * R, D, ik, ih);
+    const double pre = a1 * x0 * x0 * nh * nh * sigma * R;
+    heat[i] = (float)((double)heat[i] + pre * kHnuLErg * ih);
+}
+
 // Targets are processed in Morton-contiguous chunks of at most max_pairs
 // interaction pairs; each chunk is walked, marched and reduced on its own.
 int run_solve(start_ctx *c, float theta, float *gout_dev)
@@ -516,8 +563,8 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     c->jump_bytes = 0;
     ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));
     const bool kdis = c->solve_kind == 1;
-    const bool spec = !kdis && c->p.T_eff > 0.0;      // blackbody point sources
-    // k_dis and blackbody sources always take the memoised march
+    const bool spec = !kdis && spectral_mode(c);      // blackbody sources or band
+    // k_dis and the spectra always take the memoised march
     const bool memo = c->p.march_mode == 1 || kdis || spec;
     if (spec) {
         ST_TRY(spectral_table(c));
@@ -620,6 +667,14 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         phase_mark(c, START_PHASE_GAMMA, true);
         ST_CUDA(c, cudaGetLastError());
     }
+    if (spec && c->walk_emit && c->p.T_rec > 0.0) {   // Eq. gself
+        k_self_heat<<<grid_for(np, 256), 256, 0, s>>>(
+            c->heat.as<float>(), c->y.as<double>(), c->nH.as<float>(), c->V.as<double>(), np,
+            c->p.alpha_A - c->p.alpha_B, c->p.sigma_cm2, c->p.len_unit_cm,
+            kBoltzErg * c->p.T_rec / kHnuLErg);
+        ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+    }
     if (memo) {
         unsigned long long v[2] = {c->memo_evals, c->memo_links};
         ST_CUDA(c, cudaMemcpyAsync(c->counters.as<unsigned long long>() + C_EVALS, v, sizeof(v),
@@ -633,9 +688,10 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
 // One backward-Euler step of dy/dt = -k y + alpha n_H (1 - y)^2 in the
 // neutral fraction y (hydrogen only, n_e = x n_H), solved with the
 // cancellation-free root 2c / (b + sqrt((K+1)^2 + 4A(K+1-y0))).
+// D > 0: the self term's band average (recombination photons in the band).
 __global__ void k_ionize(double *y, float4 *pq, const float *gam, const float *nH, const double *V,
                          long long np, double dt, double sigma, double alpha, double a1,
-                         double len_cm, int diffuse)
+                         double len_cm, int diffuse, double D)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
@@ -646,8 +702,13 @@ __global__ void k_ionize(double *y, float4 *pq, const float *gam, const float *n
         double x0 = 1.0 - y0;
         double R = cbrt(3.0 * V[i] / (4.0 * 3.14159265358979323846)) * len_cm;
         double ts = sigma * (y0 * nh) * R;
-        double phi = ts > 0.0 ? -expm1(-ts) / ts : 1.0;
-        k += a1 * x0 * x0 * nh * nh * sigma * R * phi;
+        if (D > 0.0) {
+            double ik, ih;
+            band_self(ts, D, ik, ih);
+            k += a1 * x0 * x0 * nh * nh * sigma * R * ik;
+        } else {
+            k += a1 * x0 * x0 * nh * nh * sigma * R * phi_self(ts);
+        }
     }
     double A = alpha * nh * dt, K = k * dt;
     double b = 2.0 * A + K + 1.0, cc = A + y0;
@@ -665,7 +726,8 @@ int run_ionize(start_ctx *c, double dt)
     k_ionize<<<grid_for(c->np, 256), 256, 0, c->stream>>>(
         c->y.as<double>(), c->pq.as<float4>(), c->gam.as<float>(), c->nH.as<float>(),
         c->V.as<double>(), c->np, dt, c->p.sigma_cm2, alpha, c->p.alpha_A - c->p.alpha_B,
-        c->p.len_unit_cm, c->diffuse ? 1 : 0); ++c->launches;
+        c->p.len_unit_cm, c->diffuse ? 1 : 0,
+        c->p.T_rec > 0.0 ? kBoltzErg * c->p.T_rec / kHnuLErg : 0.0); ++c->launches;
     phase_mark(c, START_PHASE_IONIZE, true);
     return cuda_check(c, cudaGetLastError(), "k_ionize");
 }

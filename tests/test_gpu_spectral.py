@@ -1,9 +1,10 @@
-"""Blackbody point sources (T_eff, Appendix A integrals) through the C ABI
+"""Blackbody point sources (T_eff, Appendix A integrals) and diffuse
+recombination photons in a band (T_rec, Section 4.1) through the C ABI
 against the FP64 oracle.
 
-The GPU interpolates ln F_ion and ln F_heat from a table (spacing 2.5e-3 in
-s = ln(1 + tau/1e-3): interpolation error below ~1e-5 relative where the
-contributions matter), on top of the float32 tau of the chains: Gamma_eff and
+The GPU interpolates ln F_ion and ln F_heat (ln R_ion, ln R_heat for the
+band) from a table (spacing 2.5e-3 in s = ln(1 + tau/1e-3): interpolation
+error below ~1e-5 relative where the contributions matter), on top of the float32 tau of the chains: Gamma_eff and
 the heating rate are compared at 1e-4 relative plus the absolute floors
 Gamma_abs = 1e-8/(sigma dt) and sigma h nu_L Gamma_abs.  Rays and chain links
 are exact.
@@ -107,3 +108,56 @@ def test_spectral_edge_cases(S):
     g = np.ones(w.n_p, np.float32)
     ctx.rt_solve(0.5, gamma_out=g)
     assert not np.any(g) and not np.any(ctx.heating())
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.7])
+@pytest.mark.parametrize("T_eff", [0.0, 1e5])
+def test_recombination_band_parity(S, theta, T_eff):
+    """Diffuse emitters radiating the band of width k T_rec / h (Section 4.1):
+    Gamma_eff, the photoheating (Eq. gother over the emitter lists plus the
+    self term of Eq. gself) and the implicit update with the band-averaged
+    k_self, against the oracle."""
+    T_rec = 1e4
+    w = lattice_workload("band-14^3", 14, 4.0, 3, 95, L=1e49, diffuse=True)
+    y = np.random.default_rng(5).uniform(0.0, 1.0, w.n_p)
+    ctx = S.Context(T_eff=T_eff, T_rec=T_rec, ptree_leaf=16)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L, w.V, diffuse=True)
+    ctx.set_state(w.n_H, y)
+    g = np.zeros(w.n_p, np.float32)
+    ctx.rt_solve(theta, gamma_out=g)
+    heat = ctx.heating()
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=16, T_rec=T_rec)
+    orc.set_emitters(y, w.n_H)
+    nHI = (y * w.n_H.astype(np.float64)).astype(np.float32)
+    gref, href = orc.gamma_spectral(nHI, theta, T_eff)
+    _, hself = orc.self_terms(w.n_H, y)
+    close(g, gref, G_ABS)
+    close(heat, href + hself, H_ABS)
+    st = ctx.stats()
+    assert st["rays"] == orc.last_stats["rays"] and st["hops"] == orc.last_stats["hops"]
+    assert np.all(heat > 0)
+    y1 = np.zeros(w.n_p)
+    ctx.ionize(w.dt_s, y_out=y1)
+    yref, _ = orc.ionize(gref, w.n_H, y, w.dt_s)
+    assert np.max(np.abs(y1 - yref)) <= 1e-4
+
+
+def test_recombination_band_needs_emitters(S):
+    """Without diffuse emitters T_rec changes nothing and nothing heats."""
+    w = lattice_workload("band-nodiffuse-12^3", 12, 4.0, 3, 96)
+    out = []
+    for T_rec in (0.0, 3e4):
+        ctx = S.Context(T_rec=T_rec)
+        ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+        ctx.set_state(w.n_H, w.y0)
+        g = np.zeros(w.n_p, np.float32)
+        ctx.rt_solve(0.5, gamma_out=g)
+        assert not np.any(ctx.heating())
+        out.append(g)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_invalid_band_temperature_is_rejected(S):
+    for T_rec in (50.0, 2e5, -1.0, float("nan")):
+        with pytest.raises(S.StartError):
+            S.Context(T_rec=T_rec)
