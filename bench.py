@@ -156,20 +156,22 @@ def measured_peaks():
 
 
 def kernel_source_sha(source: str, kernel: str) -> str:
-    """sha256 (16 hex digits) of a kernel's definition text: from its
-    `__global__` line to the matching closing brace."""
+    """sha256 (16 hex digits) of a kernel's definition text (from its
+    `__global__` line to the matching closing brace) together with the
+    file's constexpr definitions (tile shapes, template arguments)."""
     import hashlib
     import re
     text = open(os.path.join(ROOT, "paper_1005_5312_gb300", "csrc", source)).read()
     m = re.search(r"__global__[^;{]*?\b" + re.escape(kernel) + r"\s*\(", text)
     if not m:
         return ""
+    consts = "\n".join(re.findall(r"^constexpr [^\n]*;", text, flags=re.M))
     i = text.index("{", m.end())
     depth = 0
     for j in range(i, len(text)):
         depth += {"{": 1, "}": -1}.get(text[j], 0)
         if depth == 0:
-            return hashlib.sha256(text[m.start():j + 1].encode()).hexdigest()[:16]
+            return hashlib.sha256((consts + "\n" + text[m.start():j + 1]).encode()).hexdigest()[:16]
     return ""
 
 

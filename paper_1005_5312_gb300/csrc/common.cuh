@@ -185,6 +185,7 @@ enum Counter {
     C_TAIL_CAP,   // memo tail kernel: a chain exceeded the iteration cap
     C_HARD,       // first hops listed for the FP64 kernel
     C_NB_OVER,    // targets with more neighbours than the counting walk keeps
+    C_JUMP_EXTRA, // pointer jumping: successor reads beyond the first in a round
     C_COUNT = 24
 };
 

@@ -649,24 +649,32 @@ __device__ __forceinline__ float2 cadd(float2 x, float2 y)
     return make_float2(hi, lo);
 }
 
-// 3. one synchronous round of pointer jumping over the packed link state.
-// A slot whose chain is resolved (next = kNone) is copied once more so that
-// both buffers hold it, then marked stable (bit 31 of its link count) and
-// never rewritten or re-read.
+// 3. one synchronous round of pointer jumping over the packed link state,
+// double-buffered: a slot whose state covers c links reads the states of the
+// G slots c, 2c, ... links ahead in the old buffer and covers (G + 1) c
+// links afterwards (or reaches the end of its chain).  The additions
+// combine the covered segments from the slot outwards, so the sum order
+// depends only on the chain.  A slot whose chain is resolved (next = kNone)
+// is copied once more so that both buffers hold it, then marked stable (bit
+// 31 of its link count) and never rewritten or re-read.
 constexpr u32 kStable = 0x80000000u;
 
-constexpr int kJumpR = 8;   // slots per thread (independent loads in flight)
+constexpr int kJumpR = 6;   // slots per thread (independent loads in flight)
+constexpr int kJumpG = 3;   // successor reads per slot and round
 
-// part[2 b], part[2 b + 1] accumulate block b's advancing updates and copies
-// over the rounds (plain stores: a block index is unique within a launch and
-// the rounds are stream-ordered), summed once after the last round.
-__global__ void __launch_bounds__(256, 3) k_memo_jump(long long n, const uint4 *__restrict__ st,
+// part[3 b .. 3 b + 2] accumulate block b's advancing updates, extra
+// successor reads and copies over the rounds (plain stores: a block index is
+// unique within a launch and the rounds are stream-ordered), summed once
+// after the last round.
+template <int G>
+__global__ void __launch_bounds__(256, 2) k_memo_jump(long long n, const uint4 *__restrict__ st,
                                                     uint4 *__restrict__ st2, unsigned *active,
                                                     unsigned long long *ctr,
                                                     unsigned long long *part)
 {
     const long long s0 = (long long)blockIdx.x * (256 * kJumpR) + threadIdx.x;
-    uint4 me[kJumpR], nx[kJumpR];
+    uint4 me[kJumpR];
+    unsigned go = 0;   // bit r: slot r advances this round
 #pragma unroll
     for (int r = 0; r < kJumpR; ++r) {
         long long s = s0 + 256 * r;
@@ -675,23 +683,38 @@ __global__ void __launch_bounds__(256, 3) k_memo_jump(long long n, const uint4 *
             atomicAdd(&ctr[C_INTERNAL], 1ull);
             me[r].x = kNone;
         }
+        if (me[r].x != kNone) go |= 1u << r;
     }
+    unsigned adv = __popc(go), extra = 0, cpy = 0;
+    // successors are read only below n (kNone is above it); an index out of
+    // range ends the chain here and is counted when its own slot is loaded.
+    // A slot that does not advance has next = kNone throughout.
+    const u32 n32 = (u32)n;
 #pragma unroll
-    for (int r = 0; r < kJumpR; ++r)
-        nx[r] = me[r].x != kNone ? st[me[r].x] : make_uint4(kNone, 0u, 0u, 0u);
+    for (int g = 0; g < G; ++g) {
+        uint4 nx[kJumpR];
+#pragma unroll
+        for (int r = 0; r < kJumpR; ++r)
+            nx[r] = me[r].x < n32 ? st[me[r].x] : make_uint4(kNone, 0u, 0u, 0u);
+#pragma unroll
+        for (int r = 0; r < kJumpR; ++r) {
+            if (me[r].x >= n32) continue;
+            if (g > 0) ++extra;
+            float2 t = cadd(make_float2(__uint_as_float(me[r].z), __uint_as_float(me[r].w)),
+                            make_float2(__uint_as_float(nx[r].z), __uint_as_float(nx[r].w)));
+            me[r] = make_uint4(nx[r].x, (me[r].y & ~kStable) + (nx[r].y & ~kStable),
+                               __float_as_uint(t.x), __float_as_uint(t.y));
+        }
+    }
     bool act = false;
-    unsigned adv = 0, cpy = 0;
 #pragma unroll
     for (int r = 0; r < kJumpR; ++r) {
         long long s = s0 + 256 * r;
         if (s >= n) continue;
-        if (me[r].x != kNone) {
-            float2 t = cadd(make_float2(__uint_as_float(me[r].z), __uint_as_float(me[r].w)),
-                            make_float2(__uint_as_float(nx[r].z), __uint_as_float(nx[r].w)));
-            st2[s] = make_uint4(nx[r].x, (me[r].y & ~kStable) + (nx[r].y & ~kStable),
-                                __float_as_uint(t.x), __float_as_uint(t.y));
-            act |= nx[r].x != kNone;
-            ++adv;
+        if ((go >> r) & 1u) {
+            if (me[r].x >= n32) me[r].x = kNone;
+            st2[s] = me[r];
+            act |= me[r].x != kNone;
         } else if (!(me[r].y & kStable)) {
             me[r].y |= kStable;
             st2[s] = me[r];
@@ -700,54 +723,51 @@ __global__ void __launch_bounds__(256, 3) k_memo_jump(long long n, const uint4 *
     }
     for (int o = 16; o; o >>= 1) {
         adv += __shfl_xor_sync(0xffffffffu, adv, o);
+        extra += __shfl_xor_sync(0xffffffffu, extra, o);
         cpy += __shfl_xor_sync(0xffffffffu, cpy, o);
     }
-    __shared__ unsigned wadv[8], wcpy[8];
+    __shared__ unsigned wadv[8], wext[8], wcpy[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         wadv[wid] = adv;
+        wext[wid] = extra;
         wcpy[wid] = cpy;
     }
     if (__any_sync(0xffffffffu, act) && lane == 0) *active = 1u;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long ba = 0, bc = 0;
+        unsigned long long ba = 0, be = 0, bc = 0;
         for (int k = 0; k < 8; ++k) {
             ba += wadv[k];
+            be += wext[k];
             bc += wcpy[k];
         }
-        part[2 * blockIdx.x] += ba;
-        part[2 * blockIdx.x + 1] += bc;
+        part[3 * blockIdx.x] += ba;
+        part[3 * blockIdx.x + 1] += be;
+        part[3 * blockIdx.x + 2] += bc;
     }
 }
 
-// Sums the per-block pointer-jumping counts into the two counters.
+// Sums the per-block pointer-jumping counts into their counters.
 __global__ void k_sum_jump_counts(const unsigned long long *part, long long nblocks,
-                                unsigned long long *ctr)
+                                  unsigned long long *ctr)
 {
-    unsigned long long a = 0, b = 0;
-    for (long long k = threadIdx.x; k < nblocks; k += blockDim.x) {
-        a += part[2 * k];
-        b += part[2 * k + 1];
-    }
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    __shared__ unsigned long long sa[32], sb[32];
-    if ((threadIdx.x & 31) == 0) {
-        sa[threadIdx.x >> 5] = a;
-        sb[threadIdx.x >> 5] = b;
+    unsigned long long v[3] = {0, 0, 0};
+    for (long long k = threadIdx.x; k < nblocks; k += blockDim.x)
+        for (int q = 0; q < 3; ++q) v[q] += part[3 * k + q];
+    __shared__ unsigned long long sv[3][32];
+    for (int q = 0; q < 3; ++q) {
+        for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if ((threadIdx.x & 31) == 0) sv[q][threadIdx.x >> 5] = v[q];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long ta = 0, tb = 0;
-        for (unsigned k = 0; k < blockDim.x / 32; ++k) {
-            ta += sa[k];
-            tb += sb[k];
-        }
-        ctr[C_JUMP_ADV] = ta;
-        ctr[C_JUMP_COPY] = tb;
+        unsigned long long t[3] = {0, 0, 0};
+        for (unsigned k = 0; k < blockDim.x / 32; ++k)
+            for (int q = 0; q < 3; ++q) t[q] += sv[q][k];
+        ctr[C_JUMP_ADV] = t[0];
+        ctr[C_JUMP_EXTRA] = t[1];
+        ctr[C_JUMP_COPY] = t[2];
     }
 }
 
@@ -1036,17 +1056,15 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     // pointer jumping
     int b = 0;
     unsigned *active = c->flags.as<unsigned>() + 12;
-    unsigned long long jc[2] = {0, 0};
-    static_assert(C_JUMP_COPY == C_JUMP_ADV + 1, "adjacent counters");
     const long long jblocks = (long long)grid_for(nslots, 256 * kJumpR);
-    if (ensure(c->m_part, (size_t)jblocks * 16))
+    if (ensure(c->m_part, (size_t)jblocks * 24))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
-    ST_CUDA(c, cudaMemsetAsync(c->m_part.p, 0, (size_t)jblocks * 16, s));
+    ST_CUDA(c, cudaMemsetAsync(c->m_part.p, 0, (size_t)jblocks * 24, s));
     long long rounds = 0;
     for (int round = 0; round < 40; ++round) {
         ST_CUDA(c, cudaMemsetAsync(active, 0, sizeof(unsigned), s));
         if (timing) cudaEventRecord(c->hev[0], s);
-        k_memo_jump<<<(unsigned)jblocks, 256, 0, s>>>(nslots, c->m_st[b].as<uint4>(),
+        k_memo_jump<kJumpG><<<(unsigned)jblocks, 256, 0, s>>>(nslots, c->m_st[b].as<uint4>(),
                                                        c->m_st[b ^ 1].as<uint4>(), active, ctr,
                                                        c->m_part.as<unsigned long long>());
         if (timing) cudaEventRecord(c->hev[1], s);
@@ -1066,11 +1084,16 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     }
     k_sum_jump_counts<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), jblocks, ctr);
     ++c->launches;
-    ST_CUDA(c, cudaMemcpyAsync(jc, ctr + C_JUMP_ADV, sizeof(jc), cudaMemcpyDeviceToHost, s));
+    unsigned long long jc[3] = {0, 0, 0};
+    ST_CUDA(c, cudaMemcpyAsync(&jc[0], ctr + C_JUMP_ADV, 8, cudaMemcpyDeviceToHost, s));
+    ST_CUDA(c, cudaMemcpyAsync(&jc[1], ctr + C_JUMP_EXTRA, 8, cudaMemcpyDeviceToHost, s));
+    ST_CUDA(c, cudaMemcpyAsync(&jc[2], ctr + C_JUMP_COPY, 8, cudaMemcpyDeviceToHost, s));
     ST_CUDA(c, cudaStreamSynchronize(s));
     c->jump_rounds += rounds;
+    // own state read per slot and round; per advancing slot one successor read
+    // and the write, plus the extra successor reads; closed chains copied once
     c->jump_bytes += 16ull * (unsigned long long)nslots * (unsigned long long)rounds +
-                     32ull * jc[0] + 16ull * jc[1];
+                     32ull * jc[0] + 16ull * jc[1] + 16ull * jc[2];
     if (timing) c->jump_ms += jump_ms;
     c->memo_final = b;
     return START_OK;
