@@ -254,7 +254,8 @@ class Context:
 
     def heating(self, heat_out=None):
         """Photoheating rate per neutral atom (erg/s) of the last solve
-        (blackbody sources; zeros when monochromatic)."""
+        (blackbody point sources and the recombination band; zeros when
+        every photon is at the Lyman limit)."""
         if heat_out is None:
             heat_out = np.zeros(max(self.n_p, 1), np.float32)
             _check(self.h, lib().start_get_heating(self.h, _ptr(heat_out)))
