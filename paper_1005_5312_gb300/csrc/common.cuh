@@ -128,6 +128,9 @@ struct start_ctx {
     // solve workspace
     st::DBuf lcount;  // u32 per target
     st::DBuf loff;    // u64 [np + 1]
+    st::DBuf w_scratch, w_over;   // one-walk lists: kWalkRow ids per target; longer rows
+    bool walk_scratch = false;    // the last count walk also filled w_scratch
+    unsigned long long walk_nover = 0;
     st::DBuf pent;    // u32 entry per pair
     st::DBuf ptgt;    // u32 target per pair
     st::DBuf pord;    // u32 order key per pair (tree tag, node of the entry)
@@ -186,6 +189,7 @@ enum Counter {
     C_HARD,       // first hops listed for the FP64 kernel
     C_NB_OVER,    // targets with more neighbours than the counting walk keeps
     C_JUMP_EXTRA, // pointer jumping: successor reads beyond the first in a round
+    C_WALK_OVER,  // one-walk lists: targets whose row exceeds the scratch row
     C_COUNT = 24
 };
 

@@ -99,7 +99,8 @@ struct SlotRows {
 // Entries are emitted in depth-first order; the order key of an entry is
 // (tree tag, node id of the accepted cell or of the leaf holding the member),
 // so every target's row is sorted by it.  MODE 0 counts, 1 writes raw
-// entries (tree tag | member flag | id), 2 writes canonical ids.
+// entries (tree tag | member flag | id), 2 writes canonical ids, 3 counts and
+// writes the first kWalkRow canonical ids into a fixed-size scratch row.
 template <int MODE, class Rows>
 __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2f, double th2d,
                                           float cmag, u32 self, u32 tag, CanonBase cb, u32 &c,
@@ -119,7 +120,7 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
         if (a) {
             if (FILL) {
                 if (w < wend) {   // never past this row
-                    u32 e = (MODE == 2) ? ((mt.w && mt.z == 1u) ? cb.memb0 + mt.y : cb.node0 + n)
+                    u32 e = (MODE >= 2) ? ((mt.w && mt.z == 1u) ? cb.memb0 + mt.y : cb.node0 + n)
                                         : (n | tag);
                     rows.put(w, e, okey | n);
                 }
@@ -133,7 +134,7 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
                 if (r == self) continue;
                 if (FILL) {
                     if (w < wend)
-                        rows.put(w, (MODE == 2) ? cb.memb0 + r : (kEntrySrc | tag | r), okey | n);
+                        rows.put(w, (MODE >= 2) ? cb.memb0 + r : (kEntrySrc | tag | r), okey | n);
                     ++w;
                 } else {
                     ++c;
@@ -146,23 +147,41 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
     }
 }
 
+constexpr u32 kWalkRow = 1024;                 // scratch row of the one-walk lists
+constexpr size_t kWalkScratchMax = 1ull << 30;   // bytes: larger problems count first
+
+// Targets [t0, t1), or when only is set the listed targets only[0, t1 - t0)
+// that lie in [lo, hi) (MODE 2).  MODE 3: the row of target i goes to
+// ent[(i - t0) kWalkRow ...], its length to cnt[i], and targets with longer
+// rows are appended to over[].
 template <int MODE>
 __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, long long t1,
                                               TreeView st_, TreeView et_, CanonBase scb,
                                               CanonBase ecb, float th2f, double th2d,
                                               float cmag, u32 *cnt, const u64 *off, u64 base,
                                               u32 *ent, u32 *tgt, u32 *ord,
-                                              unsigned long long *fb_total)
+                                              unsigned long long *fb_total, const u32 *only,
+                                              long long lo, long long hi, u32 *over,
+                                              unsigned long long *n_over)
 {
     constexpr bool FILL = MODE != 0;
-    long long i = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr bool COUNT = MODE == 0 || MODE == 3;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long i = -1;
+    if (!only) {
+        if (t0 + t < t1) i = t0 + t;
+    } else if (t < t1 - t0) {
+        const long long k = (long long)only[t];
+        if (k >= lo && k < hi) i = k;
+    }
     unsigned fb = 0;
-    if (i < t1) {
+    if (i >= 0) {
         float4 p = pq[i];
         u32 c = 0;
-        u64 w = FILL ? off[i] - base : 0ull;
-        const u64 wend = FILL ? off[i + 1] - base : 0ull;
-        if (MODE == 2) {
+        const u64 w0 = MODE == 3 ? (u64)(i - t0) * kWalkRow : (FILL ? off[i] - base : 0ull);
+        u64 w = w0;
+        const u64 wend = MODE == 3 ? w0 + kWalkRow : (FILL ? off[i + 1] - base : 0ull);
+        if (MODE >= 2) {
             SlotRows rows{ent};
             walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
             walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, c, w, wend, rows,
@@ -174,10 +193,16 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
             walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, c, w, wend, rows,
                             fb);
         }
-        if (!FILL) cnt[i] = c;
-        else if (w != wend) atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
+        if (MODE == 0) {
+            cnt[i] = c;
+        } else if (MODE == 3) {
+            cnt[i] = (u32)(w - w0);
+            if (w - w0 > kWalkRow) over[atomicAdd(n_over, 1ull)] = (u32)i;
+        } else if (w != wend) {
+            atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
+        }
     }
-    if (!FILL) {
+    if (COUNT) {
         for (int o = 16; o; o >>= 1) fb += __shfl_xor_sync(0xffffffffu, fb, o);
         if ((threadIdx.x & 31) == 0 && fb) atomicAdd(fb_total, (unsigned long long)fb);
     }
@@ -362,25 +387,48 @@ static void launch_march(const MarchArgs &a, cudaStream_t s, int nsm)
 }
 
 // Interaction-list counts of every target and their exclusive scan (loff).
+// one_walk (memoised march, scratch within kWalkScratchMax): the counting
+// walk also writes the canonical ids into a scratch row per target, so the
+// slot fill becomes a copy (walk_fill_slots).
 static int walk_count(start_ctx *c, float theta, const TreeView &sv, const TreeView &ev,
-                      unsigned long long *total)
+                      unsigned long long *total, bool one_walk = false)
 {
     long long np = c->np;
     cudaStream_t s = c->stream;
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_TRY(ensure(c->lcount, np * sizeof(u32)));
     ST_TRY(ensure(c->loff, (np + 1) * sizeof(u64)));
-    k_walk<0><<<grid_for(np, 128), 128, 0, s>>>(c->pq.as<float4>(), 0, np, sv, ev, CanonBase{},
-                                                CanonBase{}, theta * theta,
-                                                (double)theta * (double)theta,
-                                                    c->fr.cmag, c->lcount.as<u32>(), nullptr, 0ull,
-                                                    nullptr, nullptr, nullptr, ctr + C_WALK_FB);
+    c->walk_scratch = false;
+    c->walk_nover = 0;
+    one_walk = one_walk && (size_t)np * kWalkRow * sizeof(u32) <= kWalkScratchMax;
+    if (one_walk && (ensure(c->w_scratch, (size_t)np * kWalkRow * sizeof(u32)) ||
+                     ensure(c->w_over, (size_t)np * sizeof(u32))))
+        one_walk = false;   // no room: count, then fill
+    if (one_walk) {
+        u32 SN = (u32)c->stree.n, NS = (u32)c->ns, EN = (u32)(c->walk_emit ? c->et.n : 0);
+        CanonBase scb{0u, SN}, ecb{SN + NS, SN + NS + EN};
+        ST_CUDA(c, cudaMemsetAsync(ctr + C_WALK_OVER, 0, sizeof(unsigned long long), s));
+        k_walk<3><<<grid_for(np, 128), 128, 0, s>>>(
+            c->pq.as<float4>(), 0, np, sv, ev, scb, ecb, theta * theta,
+            (double)theta * (double)theta, c->fr.cmag, c->lcount.as<u32>(), nullptr, 0ull,
+            c->w_scratch.as<u32>(), nullptr, nullptr, ctr + C_WALK_FB, nullptr, 0, 0,
+            c->w_over.as<u32>(), ctr + C_WALK_OVER);
+    } else {
+        k_walk<0><<<grid_for(np, 128), 128, 0, s>>>(
+            c->pq.as<float4>(), 0, np, sv, ev, CanonBase{}, CanonBase{}, theta * theta,
+            (double)theta * (double)theta, c->fr.cmag, c->lcount.as<u32>(), nullptr, 0ull,
+            nullptr, nullptr, nullptr, ctr + C_WALK_FB, nullptr, 0, 0, nullptr, nullptr);
+    }
     ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_TRY(exclusive_scan_u32_to_u64(c, c->lcount.as<u32>(), c->loff.as<u64>(), np));
     ST_CUDA(c, cudaMemcpyAsync(total, c->loff.as<u64>() + np, sizeof(*total),
                                cudaMemcpyDeviceToHost, s));
+    if (one_walk)
+        ST_CUDA(c, cudaMemcpyAsync(&c->walk_nover, ctr + C_WALK_OVER, sizeof(c->walk_nover),
+                                   cudaMemcpyDeviceToHost, s));
     ST_CUDA(c, cudaStreamSynchronize(s));
+    c->walk_scratch = one_walk;
     return START_OK;
 }
 
@@ -392,7 +440,8 @@ static int walk_fill(start_ctx *c, float theta, const TreeView &sv, const TreeVi
     k_walk<1><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), t0, t1, sv, ev, CanonBase{}, CanonBase{}, theta * theta,
         (double)theta * (double)theta, c->fr.cmag, nullptr, c->loff.as<u64>(), base,
-        c->pent.as<u32>(), c->ptgt.as<u32>(), c->pord.as<u32>(), ctr + C_INTERNAL);
+        c->pent.as<u32>(), c->ptgt.as<u32>(), c->pord.as<u32>(), ctr + C_INTERNAL, nullptr, 0, 0,
+        nullptr, nullptr);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_walk");
 }
@@ -422,16 +471,58 @@ __global__ void k_order_keys(long long n, const u32 *vid, u32 SN, u32 NS, u32 EN
 // buffer, which the caller sized), then its order key (ord buffer) by one
 // coalesced pass; the first hop knows each row's target, so the pair slots'
 // particle is not stored.
+// The rows of targets [t0, t1) from the one-walk scratch (rows of at most
+// kWalkRow ids; longer rows were filled in place by a second walk), copied
+// to their slots with their order keys, one warp per target.
+__global__ void k_walk_compact(long long t0, long long t1, u64 base, const u32 *cnt,
+                               const u64 *off, const u32 *scratch, u32 *vid, u32 SN, u32 NS,
+                               u32 EN, const u32 *leaf_s, const u32 *leaf_e, u32 *key)
+{
+    const long long i = t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x & 31;
+    if (i >= t1) return;
+    const u32 c = cnt[i];
+    const u64 o = off[i] - base;
+    const u32 *src = scratch + (size_t)i * kWalkRow;
+    for (u32 k = lane; k < c; k += 32) {
+        u32 v = c <= kWalkRow ? src[k] : vid[o + k];
+        if (c <= kWalkRow) vid[o + k] = v;
+        u32 q;
+        if (v < SN) q = v;
+        else if ((v -= SN) < NS) q = leaf_s[v];
+        else if ((v -= NS) < EN) q = 0x80000000u | v;
+        else q = 0x80000000u | leaf_e[v - EN];
+        key[o + k] = q;
+    }
+}
+
 int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 base,
                     long long n)
 {
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     u32 SN = (u32)c->stree.n, NS = (u32)c->ns, EN = (u32)(c->walk_emit ? c->et.n : 0);
     CanonBase scb{0u, SN}, ecb{SN + NS, SN + NS + EN};
+    if (c->walk_scratch) {
+        if (c->walk_nover) {   // the longer rows, walked again straight into their slots
+            long long m = (long long)c->walk_nover;
+            k_walk<2><<<grid_for(m, 128), 128, 0, c->stream>>>(
+                c->pq.as<float4>(), 0, m, source_view(c), emitter_view(c), scb, ecb,
+                theta * theta, (double)theta * (double)theta, c->fr.cmag, nullptr,
+                c->loff.as<u64>(), base, c->m_vid.as<u32>(), nullptr, nullptr, ctr + C_INTERNAL,
+                c->w_over.as<u32>(), t0, t1, nullptr, nullptr);
+            ++c->launches;
+        }
+        k_walk_compact<<<grid_for((t1 - t0) * 32, 256), 256, 0, c->stream>>>(
+            t0, t1, base, c->lcount.as<u32>(), c->loff.as<u64>(), c->w_scratch.as<u32>(),
+            c->m_vid.as<u32>(), SN, NS, EN, c->stree.leafof.as<u32>(), c->et.leafof.as<u32>(),
+            c->m_ord.as<u32>());
+        ++c->launches;
+        return cuda_check(c, cudaGetLastError(), "k_walk_compact");
+    }
     k_walk<2><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), t0, t1, source_view(c), emitter_view(c), scb, ecb, theta * theta,
         (double)theta * (double)theta, c->fr.cmag, nullptr, c->loff.as<u64>(), base,
-        c->m_vid.as<u32>(), nullptr, nullptr, ctr + C_INTERNAL);
+        c->m_vid.as<u32>(), nullptr, nullptr, ctr + C_INTERNAL, nullptr, 0, 0, nullptr, nullptr);
     k_order_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(
         n, c->m_vid.as<u32>(), SN, NS, EN, c->stree.leafof.as<u32>(), c->et.leafof.as<u32>(),
         c->m_ord.as<u32>());
@@ -579,7 +670,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     TreeView sv = source_view(c), ev = emitter_view(c);
     phase_mark(c, START_PHASE_WALK, false);
     unsigned long long total = 0;
-    ST_TRY(walk_count(c, theta, sv, ev, &total));
+    ST_TRY(walk_count(c, theta, sv, ev, &total, memo));
     c->npairs = (long long)total;
     long long maxp = c->p.max_pairs > 0 ? c->p.max_pairs : (1LL << 27);
     std::vector<long long> cut;      // chunk boundaries (targets)

@@ -212,6 +212,33 @@ def test_memoised_and_per_ray_march_agree(S, cfg1):
     assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
 
 
+@pytest.mark.parametrize("theta,max_pairs", [(0.0, 0), (0.0, 300000), (0.6, 0)])
+def test_one_walk_lists_match_the_per_ray_path(S, theta, max_pairs):
+    """The memoised march takes its lists from one walk into a scratch row of
+    1024 ids per target; longer rows (every row at theta = 0 with 1100
+    sources) are walked again into place.  Same rays and chain links as the
+    per-ray march (which counts, then fills), Gamma within the summation-order
+    tolerance, and the oracle on a few targets."""
+    w = lattice_workload("rows-10^3-1100src", 10, 2.0, 1100, 97, L=2e47)
+    nHI = w.n_HI()
+    out = {}
+    for mode in (0, 1):
+        ctx = S.Context(march_mode=mode, tau_cut=1e30, ptree_leaf=PTREE_LEAF,
+                        max_pairs=max_pairs)
+        ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+        g = np.zeros(w.n_p, np.float32)
+        ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
+        out[mode] = (g.astype(np.float64), ctx.stats())
+    (g0, s0), (g1, s1) = out[0], out[1]
+    assert s0["rays"] == s1["rays"] and s0["hops"] == s1["hops"]
+    if max_pairs:
+        assert s1["chunks"] > 1
+    assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=PTREE_LEAF)
+    idx = np.array([0, 333, 999])
+    gamma_close(g1[idx], orc.gamma(nHI, theta, targets=idx))
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_target_chunks_are_result_neutral(S, cfg1, mode):
     """Chunking the targets changes which chains are shared, never a chain:
