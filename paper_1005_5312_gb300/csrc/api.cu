@@ -475,6 +475,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
     ST_TRY(stage_in(c, in.spos, src_pos, 3 * n_s * sizeof(float)));
     ST_TRY(stage_in(c, in.L, src_L, n_s * sizeof(double)));
     if (diffuse) ST_TRY(stage_in(c, in.V, V, n_p * sizeof(double)));
+    ST_CUDA(c, cudaMemsetAsync(ctr + C_INTERNAL, 0, sizeof(unsigned long long), s));
     if (n_p) { k_check_pos_h<<<grid_for(n_p, 256), 256, 0, s>>>(in.h.as<float>(), n_p, ctr + C_BAD_INPUT); ++c->launches; }
     if (n_s) { k_check_nonneg_d<<<grid_for(n_s, 256), 256, 0, s>>>(in.L.as<double>(), n_s, ctr + C_BAD_INPUT, 0); ++c->launches; }
     if (diffuse && n_p)
@@ -530,7 +531,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
     phase_mark(c, START_PHASE_BUILD, true);
     ST_CUDA(c, cudaStreamSynchronize(s));
     ST_CUDA(c, cudaGetLastError());
-    if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency (neighbour lists)");
+    if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency (trees or neighbour lists)");
     c->built = true;
     return START_OK;
 }

@@ -6,9 +6,10 @@
 // Construction is level-synchronous: the children of every split cell of a
 // level are found by binary search of the octant digit in the sorted keys
 // (one thread per cell), compacted by a scan, and appended as the next
-// level.  Subtree sizes (bottom-up) then give every node its depth-first
-// pre-order index and skip pointer, which is the layout the stackless walks
-// read.
+// level.  The size of every level is counted beforehand from the keys alone
+// (k_level_census), so the levels are issued without waiting for the host.
+// Subtree sizes (bottom-up) then give every node its depth-first pre-order
+// index and skip pointer, which is the layout the stackless walks read.
 #include "common.cuh"
 
 namespace st {
@@ -31,6 +32,66 @@ __device__ __forceinline__ u32 lower_digit(const u64 *keys, u32 lo, u32 hi, int 
     return lo;
 }
 
+// first index in [lo, hi) whose key is >= v
+__device__ __forceinline__ u32 lower_key(const u64 *keys, u32 lo, u32 hi, u64 v)
+{
+    while (lo < hi) {
+        u32 mid = lo + ((hi - lo) >> 1);
+        if (keys[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Nodes per level, from the sorted keys: a cell of level l starts at key k
+// iff k is the first key of its level-l prefix and its parent holds more
+// than `leaf` keys (then every ancestor does too, so the parent exists and is
+// split); a cell of at most `leaf` keys, or of level kLevels, is a leaf.
+// One thread per key counts the cells that start there; hist[l] += counts.
+__global__ void k_level_census(const u64 *keys, long long n, int leaf, unsigned long long *hist)
+{
+    __shared__ unsigned sh[kLevels + 1];
+    if (threadIdx.x <= kLevels) sh[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        const u64 key = keys[k];
+        int l = 0;
+        if (k > 0) {
+            const u64 x = keys[k - 1] ^ key;   // keys hold 3 kLevels bits
+            const int lcp = x ? (__clzll((long long)x) - (64 - 3 * kLevels)) / 3 : kLevels;
+            l = lcp + 1;
+            if (l <= kLevels) {   // the level-lcp cell holding keys k - 1 and k
+                const int sh3 = 3 * (kLevels - lcp);
+                const u64 p = key >> sh3;
+                const u32 st = lower_key(keys, 0u, (u32)k, p << sh3);
+                const u32 en = lower_key(keys, (u32)k, (u32)n, (p + 1) << sh3);
+                if (en - st <= (u32)leaf) l = kLevels + 1;   // a leaf: nothing starts here
+            }
+        }
+        for (; l <= kLevels; ++l) {
+            atomicAdd(&sh[l], 1u);
+            u32 c = (u32)n;
+            if (l > 0) {
+                const int sh3 = 3 * (kLevels - l);
+                c = lower_key(keys, (u32)k, (u32)n, ((key >> sh3) + 1) << sh3) - (u32)k;
+            }
+            if (c <= (u32)leaf || l == kLevels) break;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x <= kLevels && sh[threadIdx.x])
+        atomicAdd(&hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
+}
+
+// The census agrees with the construction (never expected otherwise).
+__global__ void k_check_levels(const u32 *totals, const unsigned long long *hist, int depth,
+                               unsigned long long *bad)
+{
+    for (int l = 0; l <= depth; ++l)
+        if ((unsigned long long)totals[l] != (l < kLevels ? hist[l + 1] : 0ull)) atomicAdd(bad, 1ull);
+}
+
 __global__ void k_count_children(const u64 *keys, const u32 *first, const u32 *count, long long m,
                                  int level, int leaf, u32 *nc)
 {
@@ -49,7 +110,8 @@ __global__ void k_count_children(const u64 *keys, const u32 *first, const u32 *c
 
 __global__ void k_emit_children(const u64 *keys, u32 *first, u32 *count, long long off_cur,
                                 long long m, int level, const u32 *nc, const u32 *cpos,
-                                long long off_next, u32 *cb)
+                                long long off_next, u32 *cb, long long cap,
+                                unsigned long long *bad)
 {
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= m) return;
@@ -63,8 +125,12 @@ __global__ void k_emit_children(const u64 *keys, u32 *first, u32 *count, long lo
     for (int d = 1; d <= 8; ++d) {
         u32 bd = d < 8 ? lower_digit(keys, prev, e, level + 1, d) : e;
         if (bd > prev) {
-            first[pos] = prev;
-            count[pos] = bd - prev;
+            if (pos < cap) {   // the census sized the arrays (never exceeded)
+                first[pos] = prev;
+                count[pos] = bd - prev;
+            } else {
+                atomicAdd(bad, 1ull);
+            }
             ++pos;
         }
         prev = bd;
@@ -166,7 +232,23 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
     t.lvl_off.clear();
     if (n <= 0) return START_OK;
     cudaStream_t s = c->stream;
-    size_t cap = (size_t)(2 * n + 64);
+    // level sizes first (one wait), then every level without waiting
+    ST_TRY(ensure(c->flags, 64 + 2 * (kLevels + 1) * sizeof(unsigned long long)));
+    unsigned long long *hist = reinterpret_cast<unsigned long long *>(c->flags.as<char>() + 64);
+    u32 *totals = reinterpret_cast<u32 *>(hist + (kLevels + 1));
+    ST_CUDA(c, cudaMemsetAsync(hist, 0, (kLevels + 1) * sizeof(unsigned long long), s));
+    k_level_census<<<grid_for(n, 256), 256, 0, s>>>(keys, n, leaf, hist); ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    unsigned long long lv[kLevels + 1];
+    ST_CUDA(c, cudaMemcpyAsync(lv, hist, sizeof(lv), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(c, cudaStreamSynchronize(s));
+    long long cap = 0;
+    int depth = 0;
+    for (int l = 0; l <= kLevels && lv[l]; ++l) {
+        cap += (long long)lv[l];
+        depth = l;
+    }
+    if (lv[0] != 1ull) return set_err(c, START_ECUDA, "octree census");
     ST_TRY(ensure(t.bfs_first, cap * sizeof(u32)));
     ST_TRY(ensure(t.bfs_count, cap * sizeof(u32)));
     ST_TRY(ensure(t.bfs_cb, cap * sizeof(u32)));
@@ -174,46 +256,33 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
     u32 root[2] = {0u, (u32)n};
     ST_CUDA(c, cudaMemcpyAsync(t.bfs_first.p, &root[0], sizeof(u32), cudaMemcpyHostToDevice, s));
     ST_CUDA(c, cudaMemcpyAsync(t.bfs_count.p, &root[1], sizeof(u32), cudaMemcpyHostToDevice, s));
-    ST_TRY(ensure(c->flags, 64));
-    u32 *total_dev = c->flags.as<u32>() + 8;
     long long off = 0, m = 1;
-    int level = 0;
     DBuf cpos;
-    for (;;) {
+    int rc = ensure(cpos, (size_t)(cap > 1 ? cap : 1) * sizeof(u32));
+    if (rc) return set_err(c, rc, "out of device memory (octree)");
+    int level = 0;
+    for (;; ++level) {
         t.lvl_off.push_back(off);
-        // children counts of this level
-        size_t used = (size_t)(off + m);
-        if (cap < used) return set_err(c, START_ECUDA, "octree bookkeeping overflow");
         k_count_children<<<grid_for(m, 256), 256, 0, s>>>(keys, t.bfs_first.as<u32>() + off,
                                                            t.bfs_count.as<u32>() + off, m, level,
                                                            leaf, t.bfs_nc.as<u32>() + off); ++c->launches;
         ST_CUDA(c, cudaGetLastError());
-        int rc = ensure(cpos, (size_t)m * sizeof(u32));
-        if (rc) return set_err(c, rc, "out of device memory (octree)");
-        ST_TRY(exclusive_scan_u32(c, t.bfs_nc.as<u32>() + off, cpos.as<u32>(), m, total_dev));
-        u32 mnext = 0;
-        ST_CUDA(c, cudaMemcpyAsync(&mnext, total_dev, sizeof(u32), cudaMemcpyDeviceToHost, s));
-        ST_CUDA(c, cudaStreamSynchronize(s));
-        long long off_next = off + m;
-        size_t need = (size_t)(off_next + mnext);
-        if (need > cap) {
-            size_t nc = need + need / 2 + 64;
-            ST_TRY(ensure_keep(t.bfs_first, nc * sizeof(u32), used * sizeof(u32), s));
-            ST_TRY(ensure_keep(t.bfs_count, nc * sizeof(u32), used * sizeof(u32), s));
-            ST_TRY(ensure_keep(t.bfs_cb, nc * sizeof(u32), used * sizeof(u32), s));
-            ST_TRY(ensure_keep(t.bfs_nc, nc * sizeof(u32), used * sizeof(u32), s));
-            cap = nc;
-        }
+        ST_TRY(exclusive_scan_u32(c, t.bfs_nc.as<u32>() + off, cpos.as<u32>(), m, totals + level));
+        const long long off_next = off + m;
+        const long long mnext = level < depth ? (long long)lv[level + 1] : 0;
         k_emit_children<<<grid_for(m, 256), 256, 0, s>>>(keys, t.bfs_first.as<u32>(),
                                                           t.bfs_count.as<u32>(), off, m, level,
                                                           t.bfs_nc.as<u32>() + off, cpos.as<u32>(),
-                                                          off_next, t.bfs_cb.as<u32>()); ++c->launches;
+                                                          off_next, t.bfs_cb.as<u32>(), cap,
+                                                          c->counters.as<unsigned long long>() + C_INTERNAL);
+        ++c->launches;
         ST_CUDA(c, cudaGetLastError());
         if (mnext == 0) break;
         off = off_next;
         m = mnext;
-        ++level;
     }
+    k_check_levels<<<1, 1, 0, s>>>(totals, hist, level, c->counters.as<unsigned long long>() + C_INTERNAL);
+    ++c->launches;
     release(cpos);
     long long total = off + m;
     t.n = total;
@@ -253,8 +322,7 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
     k_leafof<<<grid_for(total, 256), 256, 0, s>>>(t.meta.as<uint4>(), total, t.leafof.as<u32>());
     c->launches += 2;
     ST_CUDA(c, cudaGetLastError());
-    ST_CUDA(c, cudaStreamSynchronize(s));
-    release(size);
+    release(size);   // stream-ordered
     release(dfs);
     return START_OK;
 }
