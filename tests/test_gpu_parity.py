@@ -91,8 +91,22 @@ def ragged():
     return random_workload(5003, 77, 11, dups=2)
 
 
+@pytest.fixture(scope="module")
+def clustered():
+    # sources in close pairs (1e-5 of the box apart: chains of single-child
+    # cells down to the deepest levels), particles in tight clumps
+    w = random_workload(3001, 64, 12, dups=3)
+    rng = np.random.default_rng(13)
+    w.src_pos[:, 1::2] = w.src_pos[:, 0::2] + np.float32(3e-5) * rng.uniform(
+        0.1, 1.0, size=(3, 32)).astype(np.float32)
+    w.pos[:, 1000:1200] = (w.pos[:, 1000:1001]
+                           + np.float32(1e-4) * rng.uniform(0, 1, (3, 200)).astype(np.float32))
+    w.h = smoothing_lengths(w.pos)
+    return w
+
+
 # ------------------------------------------------------------------ structure
-@pytest.mark.parametrize("which_w", ["cfg1", "ragged"])
+@pytest.mark.parametrize("which_w", ["cfg1", "ragged", "clustered"])
 def test_frame_keys_perm_trees_neighbours_bitexact(S, which_w, request):
     w = request.getfixturevalue(which_w)
     ctx, orc = make_pair(S, w)
