@@ -159,8 +159,9 @@ typedef struct start_stats {
     long long jump_rounds;      /* pointer-jumping rounds of the last solve (memoised) */
     long long jump_bytes;       /* bytes those rounds read and wrote: 16 per slot and
                                    round (own state), 32 per slot that advanced
-                                   (successor read, write), 16 per slot copied once
-                                   when its chain closed */
+                                   (first successor read, write), 16 per further
+                                   successor read, 16 per slot copied once when its
+                                   chain closed */
 } start_stats;
 
 /* Phases timed when start_params.timing = 1 (milliseconds of the last

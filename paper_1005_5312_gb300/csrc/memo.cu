@@ -18,8 +18,9 @@
 //      links claimed by another group in the same launch are resolved by a
 //      second kernel, after the launch boundary;
 //   3. tau of every slot follows by compensated pointer jumping over the
-//      link forest (log2 of the longest chain rounds, double-buffered, so the
-//      sum order depends only on the chain);
+//      link forest (each round reads three successors, so log4 of the longest
+//      chain rounds; double-buffered, so the sum order depends only on the
+//      chain);
 //   4. each pair contributes L e^-tau / (4 pi r^2).
 // Count-1 source cells and their single member are the same source and
 // share one chain forest.
