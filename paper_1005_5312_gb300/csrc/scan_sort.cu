@@ -221,10 +221,90 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const u64 *kin, const
     }
 }
 
+// One tile (n <= kRsTile): all eight passes in one block, the ranks as in
+// k_rs_scatter and the digit offsets from the block's own histogram; the
+// passes alternate between the caller's buffers and (tk, tv), global writes
+// made visible to the block by the barrier between passes.
+__global__ void __launch_bounds__(kRsThreads) k_rs_small(u64 *keys, u32 *vals, u64 *tk, u32 *tv,
+                                                         int n)
+{
+    __shared__ u32 wcnt[kRsWarps][256];
+    __shared__ u32 base[256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int wbase = warp * 32 * kRsIpt;
+    u64 *ka = keys, *kb = tk;
+    u32 *va = vals, *vb = tv;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        u64 k[kRsIpt];
+        u32 v[kRsIpt], rank[kRsIpt];
+        int dg[kRsIpt];
+#pragma unroll
+        for (int r = 0; r < kRsIpt; ++r) {
+            const int idx = wbase + r * 32 + lane;
+            const bool valid = idx < n;
+            k[r] = valid ? ka[idx] : 0ull;
+            v[r] = valid ? va[idx] : 0u;
+            const int d = valid ? (int)((k[r] >> shift) & 255u) : 256;
+            dg[r] = d;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            const u32 before = valid ? wcnt[warp][d] : 0u;
+            __syncwarp();
+            if (valid && lane == leader) wcnt[warp][d] = before + __popc(peers);
+            __syncwarp();
+            rank[r] = before + __popc(peers & lt);
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += kRsThreads) {   // per digit: warps in order
+            u32 run = 0;
+            for (int w = 0; w < kRsWarps; ++w) {
+                const u32 t = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += t;
+            }
+            base[d] = run;   // digit total, scanned below
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {   // exclusive scan of the 256 digit totals
+            u32 run = 0;
+            for (int d = 0; d < 256; ++d) {
+                const u32 t = base[d];
+                base[d] = run;
+                run += t;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRsIpt; ++r) {
+            if (dg[r] < 256) {
+                const u32 pos = base[dg[r]] + wcnt[warp][dg[r]] + rank[r];
+                kb[pos] = k[r];
+                vb[pos] = v[r];
+            }
+        }
+        __syncthreads();
+        u64 *t1 = ka; ka = kb; kb = t1;
+        u32 *t2 = va; va = vb; vb = t2;
+    }
+    // eight passes: the result is back in (keys, vals)
+}
+
 // Sorts (keys, vals) in place by key, stably (equal keys keep their order).
 int radix_sort_pairs(start_ctx *c, u64 *keys, u32 *vals, long long n)
 {
     if (n <= 1) return START_OK;
+    if (n <= kRsTile) {
+        ST_TRY(ensure(c->tk[0], n * sizeof(u64)));
+        ST_TRY(ensure(c->tv[0], n * sizeof(u32)));
+        k_rs_small<<<1, kRsThreads, 0, c->stream>>>(keys, vals, c->tk[0].as<u64>(),
+                                                    c->tv[0].as<u32>(), (int)n);
+        ++c->launches;
+        return cuda_check(c, cudaGetLastError(), "k_rs_small");
+    }
     int nblocks = (int)((n + kRsTile - 1) / kRsTile);
     ST_TRY(ensure(c->tk[0], n * sizeof(u64)));
     ST_TRY(ensure(c->tv[0], n * sizeof(u32)));
