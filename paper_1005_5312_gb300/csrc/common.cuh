@@ -64,6 +64,8 @@ struct Tree {
     DBuf bfs2dfs;              // u32
     DBuf bfs_first, bfs_count; // u32
     DBuf bfs_cb, bfs_nc;       // u32 first child (BFS index), child count
+    bool small = false;        // built by one block (k_octree_small)
+    DBuf lvl_dev;              // u32 [depth + 2] level offsets (small trees)
 };
 
 struct Frame {

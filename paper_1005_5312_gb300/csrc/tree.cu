@@ -92,36 +92,26 @@ __global__ void k_check_levels(const u32 *totals, const unsigned long long *hist
         if ((unsigned long long)totals[l] != (l < kLevels ? hist[l + 1] : 0ull)) atomicAdd(bad, 1ull);
 }
 
-__global__ void k_count_children(const u64 *keys, const u32 *first, const u32 *count, long long m,
-                                 int level, int leaf, u32 *nc)
+// Non-empty octants of the cell holding keys [f, f + n) at `level` (0 for a
+// leaf: at most `leaf` keys, or the deepest level).
+__device__ __forceinline__ u32 cell_children(const u64 *keys, u32 f, u32 n, int level, int leaf)
 {
-    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= m) return;
-    u32 f = first[b], n = count[b];
-    if (!(n > (u32)leaf && level < kLevels)) { nc[b] = 0; return; }
+    if (!(n > (u32)leaf && level < kLevels)) return 0u;
     u32 e = f + n, cnt = 0, prev = f;
     for (int d = 1; d <= 8; ++d) {
         u32 bd = d < 8 ? lower_digit(keys, prev, e, level + 1, d) : e;
         cnt += bd > prev;
         prev = bd;
     }
-    nc[b] = cnt;
+    return cnt;
 }
 
-__global__ void k_emit_children(const u64 *keys, u32 *first, u32 *count, long long off_cur,
-                                long long m, int level, const u32 *nc, const u32 *cpos,
-                                long long off_next, u32 *cb, long long cap,
-                                unsigned long long *bad)
+// Writes the children (first key, count) of that cell from BFS index pos on.
+__device__ __forceinline__ void cell_emit(const u64 *keys, u32 f, u32 n, int level, long long pos,
+                                          u32 *first, u32 *count, long long cap,
+                                          unsigned long long *bad)
 {
-    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= m) return;
-    long long gb = off_cur + b;
-    u32 k = nc[b];
-    cb[gb] = (u32)(off_next + cpos[b]);
-    if (!k) return;
-    u32 f = first[gb], e = f + count[gb];
-    long long pos = off_next + cpos[b];
-    u32 prev = f;
+    u32 e = f + n, prev = f;
     for (int d = 1; d <= 8; ++d) {
         u32 bd = d < 8 ? lower_digit(keys, prev, e, level + 1, d) : e;
         if (bd > prev) {
@@ -135,6 +125,28 @@ __global__ void k_emit_children(const u64 *keys, u32 *first, u32 *count, long lo
         }
         prev = bd;
     }
+}
+
+__global__ void k_count_children(const u64 *keys, const u32 *first, const u32 *count, long long m,
+                                 int level, int leaf, u32 *nc)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    nc[b] = cell_children(keys, first[b], count[b], level, leaf);
+}
+
+__global__ void k_emit_children(const u64 *keys, u32 *first, u32 *count, long long off_cur,
+                                long long m, int level, const u32 *nc, const u32 *cpos,
+                                long long off_next, u32 *cb, long long cap,
+                                unsigned long long *bad)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    long long gb = off_cur + b;
+    u32 k = nc[b];
+    cb[gb] = (u32)(off_next + cpos[b]);
+    if (!k) return;
+    cell_emit(keys, first[gb], count[gb], level, off_next + cpos[b], first, count, cap, bad);
 }
 
 __global__ void k_subtree_size(const u32 *cb, const u32 *nc, long long off, long long m, u32 *size)
@@ -172,15 +184,13 @@ __device__ __forceinline__ u32 compact3(u64 v)
     return (u32)v;
 }
 
-// Writes the depth-first arrays of one level's nodes.
-__global__ void k_finalize(const u64 *keys, const u32 *first, const u32 *count, const u32 *nc,
-                           const u32 *dfs, const u32 *size, long long off, long long m, int level,
-                           double lox, double loy, double loz, double side, float4 *box,
-                           uint4 *meta, double *cube, int *lev)
+// Writes the depth-first record of BFS node gb of `level`.
+__device__ __forceinline__ void node_finalize(const u64 *keys, const u32 *first, const u32 *count,
+                                              const u32 *nc, const u32 *dfs, const u32 *size,
+                                              long long gb, int level, double lox, double loy,
+                                              double loz, double side, float4 *box, uint4 *meta,
+                                              double *cube, int *lev)
 {
-    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= m) return;
-    long long gb = off + b;
     u32 i = dfs[gb];
     u32 f = first[gb];
     u64 prefix = level ? (keys[f] >> (3 * (kLevels - level))) : 0ull;
@@ -197,6 +207,18 @@ __global__ void k_finalize(const u64 *keys, const u32 *first, const u32 *count, 
                          __double2float_rn(l));
     meta[i] = make_uint4(i + size[gb], f, count[gb], nc[gb] == 0 ? 1u : 0u);
     lev[i] = level;
+}
+
+// Writes the depth-first arrays of one level's nodes.
+__global__ void k_finalize(const u64 *keys, const u32 *first, const u32 *count, const u32 *nc,
+                           const u32 *dfs, const u32 *size, long long off, long long m, int level,
+                           double lox, double loy, double loz, double side, float4 *box,
+                           uint4 *meta, double *cube, int *lev)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    node_finalize(keys, first, count, nc, dfs, size, off + b, level, lox, loy, loz, side, box, meta,
+                  cube, lev);
 }
 
 // The leaf holding every member (members in sorted order).
@@ -223,6 +245,117 @@ __global__ void k_bfs2dfs(const u32 *dfs, long long n, u32 *out)
 {
     long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (b < n) out[b] = dfs[b];
+}
+
+// ---------------------------------------------------------------- small trees
+// Trees of at most kSmallTree members (the sources, small problems) are built
+// by one block in one launch: the same level-synchronous steps (children,
+// scan, emission; subtree sizes; pre-order positions; records), separated by
+// block barriers instead of launches.
+constexpr long long kSmallTree = 4096;
+
+// Exclusive scan of in[0, m) into out[0, m) by one block of 256 threads;
+// returns the total to every thread.
+__device__ u32 block_scan(const u32 *in, u32 *out, u32 m)
+{
+    __shared__ u32 part[256];
+    __shared__ u32 tot;
+    const u32 t = threadIdx.x, per = (m + 255) / 256;
+    const u32 b0 = min(m, t * per), b1 = min(m, b0 + per);
+    u32 sum = 0;
+    for (u32 k = b0; k < b1; ++k) sum += in[k];
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        u32 run = 0;
+        for (int k = 0; k < 256; ++k) {
+            const u32 v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        tot = run;
+    }
+    __syncthreads();
+    u32 run = part[t];
+    for (u32 k = b0; k < b1; ++k) {
+        const u32 v = in[k];
+        out[k] = run;
+        run += v;
+    }
+    __syncthreads();
+    return tot;
+}
+
+// hist: the census (nodes per level); the level offsets are written to loff.
+__global__ void __launch_bounds__(256) k_octree_small(
+    const u64 *keys, u32 n, int leaf, const unsigned long long *hist, int depth, u32 *loff,
+    u32 *first, u32 *count, u32 *cb, u32 *nc, u32 *cpos, u32 *size, u32 *dfs, double lox,
+    double loy, double loz, double side, float4 *box, uint4 *meta, double *cube, int *lev,
+    u32 *b2d, u32 *parent, u32 *leafof, unsigned long long *bad)
+{
+    __shared__ u32 off[kLevels + 2];
+    const u32 t = threadIdx.x;
+    if (t == 0) {
+        off[0] = 0u;
+        for (int l = 0; l <= depth; ++l) off[l + 1] = off[l] + (u32)hist[l];
+        for (int l = 0; l <= depth + 1; ++l) loff[l] = off[l];
+        first[0] = 0u;
+        count[0] = n;
+    }
+    __syncthreads();
+    const u32 total = off[depth + 1];
+    for (int l = 0; l <= depth; ++l) {   // children, level by level
+        const u32 o = off[l], m = off[l + 1] - o, on = off[l + 1];
+        for (u32 b = t; b < m; b += 256)
+            nc[o + b] = cell_children(keys, first[o + b], count[o + b], l, leaf);
+        __syncthreads();
+        const u32 tot = block_scan(nc + o, cpos, m);
+        if (t == 0 && tot != (l < depth ? off[l + 2] - off[l + 1] : 0u)) atomicAdd(bad, 1ull);
+        for (u32 b = t; b < m; b += 256) {
+            cb[o + b] = on + cpos[b];
+            if (nc[o + b])
+                cell_emit(keys, first[o + b], count[o + b], l, (long long)(on + cpos[b]), first,
+                          count, (long long)total, bad);
+        }
+        __syncthreads();
+    }
+    for (int l = depth; l >= 0; --l) {   // subtree sizes, bottom-up
+        const u32 o = off[l], m = off[l + 1] - o;
+        for (u32 b = t; b < m; b += 256) {
+            const u32 gb = o + b, k = nc[gb], c0 = cb[gb];
+            u32 sz = 1;
+            for (u32 c = 0; c < k; ++c) sz += size[c0 + c];
+            size[gb] = sz;
+        }
+        __syncthreads();
+    }
+    if (t == 0) dfs[0] = 0u;
+    __syncthreads();
+    for (int l = 0; l <= depth; ++l) {   // pre-order positions, top-down
+        const u32 o = off[l], m = off[l + 1] - o;
+        for (u32 b = t; b < m; b += 256) {
+            const u32 gb = o + b, k = nc[gb], c0 = cb[gb];
+            u32 p = dfs[gb] + 1;
+            for (u32 c = 0; c < k; ++c) {
+                dfs[c0 + c] = p;
+                p += size[c0 + c];
+            }
+        }
+        __syncthreads();
+    }
+    for (int l = 0; l <= depth; ++l) {   // records, parents, member-to-leaf table
+        const u32 o = off[l], m = off[l + 1] - o;
+        for (u32 b = t; b < m; b += 256) {
+            const u32 gb = o + b, i = dfs[gb];
+            node_finalize(keys, first, count, nc, dfs, size, gb, l, lox, loy, loz, side, box, meta,
+                          cube, lev);
+            b2d[gb] = i;
+            if (gb == 0) parent[i] = 0xffffffffu;
+            for (u32 k = 0; k < nc[gb]; ++k) parent[dfs[cb[gb] + k]] = i;
+            if (nc[gb] == 0)
+                for (u32 r = first[gb]; r < first[gb] + count[gb]; ++r) leafof[r] = i;
+        }
+    }
 }
 
 int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, const Frame &fr)
@@ -253,6 +386,36 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
     ST_TRY(ensure(t.bfs_count, cap * sizeof(u32)));
     ST_TRY(ensure(t.bfs_cb, cap * sizeof(u32)));
     ST_TRY(ensure(t.bfs_nc, cap * sizeof(u32)));
+    t.small = n <= kSmallTree;
+    if (t.small) {
+        DBuf scr;   // cpos, size, dfs
+        if (ensure(scr, (size_t)3 * cap * sizeof(u32)) ||
+            ensure(t.box, cap * sizeof(float4)) || ensure(t.meta, cap * sizeof(uint4)) ||
+            ensure(t.cube, cap * 4 * sizeof(double)) || ensure(t.level, cap * sizeof(int)) ||
+            ensure(t.bfs2dfs, cap * sizeof(u32)) || ensure(t.parent, cap * sizeof(u32)) ||
+            ensure(t.leafof, n * sizeof(u32)) || ensure(t.lvl_dev, (kLevels + 2) * sizeof(u32))) {
+            release(scr);
+            return set_err(c, START_ENOMEM, "out of device memory (octree)");
+        }
+        u32 *sc = scr.as<u32>();
+        k_octree_small<<<1, 256, 0, s>>>(
+            keys, (u32)n, leaf, hist, depth, t.lvl_dev.as<u32>(), t.bfs_first.as<u32>(),
+            t.bfs_count.as<u32>(), t.bfs_cb.as<u32>(), t.bfs_nc.as<u32>(), sc, sc + cap,
+            sc + 2 * cap, fr.lo[0], fr.lo[1], fr.lo[2], fr.side, t.box.as<float4>(),
+            t.meta.as<uint4>(), t.cube.as<double>(), t.level.as<int>(), t.bfs2dfs.as<u32>(),
+            t.parent.as<u32>(), t.leafof.as<u32>(), c->counters.as<unsigned long long>() + C_INTERNAL);
+        ++c->launches;
+        release(scr);   // stream-ordered
+        long long o = 0;
+        for (int l = 0; l <= depth; ++l) {
+            t.lvl_off.push_back(o);
+            o += (long long)lv[l];
+        }
+        t.lvl_off.push_back(o);
+        t.n = cap;
+        t.depth = depth;
+        return cuda_check(c, cudaGetLastError(), "k_octree_small");
+    }
     u32 root[2] = {0u, (u32)n};
     ST_CUDA(c, cudaMemcpyAsync(t.bfs_first.p, &root[0], sizeof(u32), cudaMemcpyHostToDevice, s));
     ST_CUDA(c, cudaMemcpyAsync(t.bfs_count.p, &root[1], sizeof(u32), cudaMemcpyHostToDevice, s));
@@ -330,14 +493,12 @@ int build_octree(start_ctx *c, Tree &t, const u64 *keys, long long n, int leaf, 
 // ---------------------------------------------------------------- moments
 // One level, deepest first.  A leaf sums its members in sorted order; an
 // inner cell sums its children in octant order (FP64, never contracted).
-__global__ void k_moments_level(const u32 *first, const u32 *count, const u32 *cb, const u32 *nc,
-                                const u32 *b2d, long long off, long long m,
-                                const float4 *mem_pos, const double *mem_L, const double *cube,
-                                double L_unit, double *L, double *M, float4 *vsrc)
+__device__ __forceinline__ void node_moments(const u32 *first, const u32 *count, const u32 *cb,
+                                             const u32 *nc, const u32 *b2d, long long gb,
+                                             const float4 *mem_pos, const double *mem_L,
+                                             const double *cube, double L_unit, double *L,
+                                             double *M, float4 *vsrc)
 {
-    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= m) return;
-    long long gb = off + b;
     u32 i = b2d[gb];
     double S = 0.0, Mx = 0.0, My = 0.0, Mz = 0.0;
     u32 k = nc[gb];
@@ -383,12 +544,48 @@ __global__ void k_moments_level(const u32 *first, const u32 *count, const u32 *c
     vsrc[i] = v;
 }
 
+__global__ void k_moments_level(const u32 *first, const u32 *count, const u32 *cb, const u32 *nc,
+                                const u32 *b2d, long long off, long long m,
+                                const float4 *mem_pos, const double *mem_L, const double *cube,
+                                double L_unit, double *L, double *M, float4 *vsrc)
+{
+    long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m) return;
+    node_moments(first, count, cb, nc, b2d, off + b, mem_pos, mem_L, cube, L_unit, L, M, vsrc);
+}
+
+// All levels of a small tree by one block, deepest first.
+__global__ void __launch_bounds__(256) k_moments_small(const u32 *first, const u32 *count,
+                                                       const u32 *cb, const u32 *nc,
+                                                       const u32 *b2d, const u32 *loff, int depth,
+                                                       const float4 *mem_pos, const double *mem_L,
+                                                       const double *cube, double L_unit,
+                                                       double *L, double *M, float4 *vsrc)
+{
+    for (int l = depth; l >= 0; --l) {
+        const u32 o = loff[l], m = loff[l + 1] - o;
+        for (u32 b = threadIdx.x; b < m; b += blockDim.x)
+            node_moments(first, count, cb, nc, b2d, o + b, mem_pos, mem_L, cube, L_unit, L, M,
+                         vsrc);
+        __syncthreads();
+    }
+}
+
 int tree_moments(start_ctx *c, Tree &t, const float4 *mem_pos, const double *mem_L, double L_unit)
 {
     if (t.n == 0) return START_OK;
     if (ensure(t.L, t.n * sizeof(double)) || ensure(t.M, t.n * 3 * sizeof(double)) ||
         ensure(t.vsrc, t.n * sizeof(float4)))
         return set_err(c, START_ENOMEM, "out of device memory (moments)");
+    if (t.small) {
+        k_moments_small<<<1, 256, 0, c->stream>>>(
+            t.bfs_first.as<u32>(), t.bfs_count.as<u32>(), t.bfs_cb.as<u32>(), t.bfs_nc.as<u32>(),
+            t.bfs2dfs.as<u32>(), t.lvl_dev.as<u32>(), t.depth, mem_pos, mem_L,
+            t.cube.as<double>(), L_unit, t.L.as<double>(), t.M.as<double>(),
+            t.vsrc.as<float4>());
+        ++c->launches;
+        return cuda_check(c, cudaGetLastError(), "k_moments_small");
+    }
     for (int l = t.depth; l >= 0; --l) {
         long long o = t.lvl_off[l], mm = t.lvl_off[l + 1] - o;
         k_moments_level<<<grid_for(mm, 256), 256, 0, c->stream>>>(
@@ -403,7 +600,7 @@ void tree_release(Tree &t)
 {
     DBuf *all[] = {&t.box,     &t.meta,      &t.cube,      &t.level,  &t.parent,
                    &t.leafof,  &t.vsrc,      &t.L,         &t.M,      &t.bfs2dfs,
-                   &t.bfs_first, &t.bfs_count, &t.bfs_cb, &t.bfs_nc};
+                   &t.bfs_first, &t.bfs_count, &t.bfs_cb, &t.bfs_nc, &t.lvl_dev};
     for (DBuf *b : all) release(*b);
     t.n = 0;
     t.lvl_off.clear();
