@@ -328,6 +328,8 @@ static void release_all(start_ctx *c)
     c->ev_init = false;
     for (int k = 0; k < 4; ++k)
         if (c->hev[k]) cudaEventDestroy(c->hev[k]);
+    for (cudaEvent_t &e : c->lev_ev)
+        if (e) cudaEventDestroy(e);
 }
 
 }  // namespace st

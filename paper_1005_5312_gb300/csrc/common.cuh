@@ -173,6 +173,7 @@ struct start_ctx {
     long long chunks = 0;                    // target chunks of the last solve
     int memo_final = 0;                      // buffer holding the final chain sums
     cudaEvent_t hev[4] = {};
+    cudaEvent_t lev_ev[16] = {};      // memoised march: per-level events of a batch
 };
 
 namespace st {
@@ -192,6 +193,7 @@ enum Counter {
     C_NB_OVER,    // targets with more neighbours than the counting walk keeps
     C_JUMP_EXTRA, // pointer jumping: successor reads beyond the first in a round
     C_WALK_OVER,  // one-walk lists: targets whose row exceeds the scratch row
+    C_LEVEL,      // memoised march: device frontier {fbase, nf, total} (3 words)
     C_COUNT = 24
 };
 

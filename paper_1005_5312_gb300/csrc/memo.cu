@@ -63,6 +63,8 @@ struct MemoArgs {
     u32 fbase;                      // frontier: slots [fbase, fbase + nf) (the links
     long long nf;                   // claimed by the previous level are contiguous),
     const u32 *fr;                  // or the listed slots fr[0, nf) (first level)
+    const unsigned long long *dlv;  // when set, fbase = dlv[0] and nf = dlv[1] (device
+                                    // values: levels issued without a host round trip)
     u32 *miss;                      // the first level's list of links not found in
     unsigned long long *nmiss;      // their upstream row, and its length
     uint2 *hard;                    // first hops left to the FP64 kernel: (slot, target)
@@ -140,9 +142,11 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
     const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const long long ngroups = ((long long)gridDim.x * blockDim.x) / G;
+    const u32 fbase = a.dlv ? (u32)a.dlv[0] : a.fbase;
+    const long long nf = a.dlv ? (long long)a.dlv[1] : a.nf;
     unsigned long long fbs = 0;
-    for (long long it = gid; it < a.nf; it += ngroups) {
-        u32 s = a.fbase + (u32)it;
+    for (long long it = gid; it < nf; it += ngroups) {
+        u32 s = fbase + (u32)it;
         u32 vid = a.svid[s];
         u32 j = a.sj[s];
         float4 src = vsource(a, vid);
@@ -464,75 +468,82 @@ __global__ void __launch_bounds__(256) k_memo_hop_hard(MemoArgs a)
 __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    u32 up = it < a.nf ? a.ups[it] : kNone;
-    const bool act = up != kNone;   // else a chain end, or a link the first level found
-    u32 s = 0, vid = 0, key = 0, nx = kNone;
-    unsigned long long hc = 0;      // table entry this thread claimed
-    bool claimed = false;
-    if (act) {
-        bool searched = (up & kRowMiss) != 0;
-        up &= ~kRowMiss;
-        s = a.fr ? a.fr[it] : a.fbase + (u32)it;
-        vid = a.svid[s];
-        key = a.sord[s];
-        // links of the first level were searched there; later slots sit in
-        // no row, so their search has no guess, and the row is searched only
-        // when the walk lists vid for up
-        if (!searched && (long long)up >= a.t0 && (long long)up < a.t1 &&
-            in_row(a, up, vid, key)) {
-            nx = find_in_row(a, up, vid, key, 0, 0);
-            if (nx == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
-        }
-        if (nx == kNone) {
-            unsigned long long lk = link_key(vid, up);
-            unsigned long long h = mix64(lk) & a.hmask;
-            bool placed = false;
-            for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
-                unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
-                if (k == kEmptyKey) {
-                    unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
-                    if (prev == kEmptyKey) {
-                        claimed = true;
-                        hc = h;
+    const u32 fbase = a.dlv ? (u32)a.dlv[0] : a.fbase;
+    const long long nf = a.dlv ? (long long)a.dlv[1] : a.nf;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // warp-uniform trips: the claims below are aggregated per warp
+    for (long long w0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < nf;
+         w0 += stride) {
+        const long long it = w0 + lane;
+        u32 up = it < nf ? a.ups[it] : kNone;
+        const bool act = up != kNone;   // else a chain end, or a link the first level found
+        u32 s = 0, vid = 0, key = 0, nx = kNone;
+        unsigned long long hc = 0;      // table entry this thread claimed
+        bool claimed = false;
+        if (act) {
+            bool searched = (up & kRowMiss) != 0;
+            up &= ~kRowMiss;
+            s = a.fr ? a.fr[it] : fbase + (u32)it;
+            vid = a.svid[s];
+            key = a.sord[s];
+            // links of the first level were searched there; later slots sit in
+            // no row, so their search has no guess, and the row is searched only
+            // when the walk lists vid for up
+            if (!searched && (long long)up >= a.t0 && (long long)up < a.t1 &&
+                in_row(a, up, vid, key)) {
+                nx = find_in_row(a, up, vid, key, 0, 0);
+                if (nx == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+            }
+            if (nx == kNone) {
+                unsigned long long lk = link_key(vid, up);
+                unsigned long long h = mix64(lk) & a.hmask;
+                bool placed = false;
+                for (unsigned long long probe = 0; probe <= a.hmask; ++probe) {
+                    unsigned long long k = *(volatile unsigned long long *)&a.table[h].key;
+                    if (k == kEmptyKey) {
+                        unsigned long long prev = atomicCAS(&a.table[h].key, kEmptyKey, lk);
+                        if (prev == kEmptyKey) {
+                            claimed = true;
+                            hc = h;
+                            placed = true;
+                            break;
+                        }
+                        k = prev;
+                    }
+                    if (k == lk) {
+                        u32 v = *(volatile unsigned int *)&a.table[h].val;
+                        nx = (v != kNone) ? v : (kPending | (u32)h);
                         placed = true;
                         break;
                     }
-                    k = prev;
+                    h = (h + 1) & a.hmask;
                 }
-                if (k == lk) {
-                    u32 v = *(volatile unsigned int *)&a.table[h].val;
-                    nx = (v != kNone) ? v : (kPending | (u32)h);
-                    placed = true;
-                    break;
-                }
-                h = (h + 1) & a.hmask;
-            }
-            if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
-        }
-    }
-    const unsigned cm = __ballot_sync(0xffffffffu, claimed);
-    if (cm) {
-        const int leader = __ffs(cm) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(a.nslots, (unsigned long long)__popc(cm));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (claimed) {
-            unsigned long long ns = base + __popc(cm & ((1u << lane) - 1u));
-            if (ns >= a.cap) {
-                atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
-            } else {
-                a.svid[ns] = vid;
-                a.sj[ns] = up;
-                a.sord[ns] = key;
-                *(volatile unsigned int *)&a.table[hc].val = (u32)ns;
-                nx = (u32)ns;
+                if (!placed) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
             }
         }
-    }
-    if (act) {
-        a.state[s].x = nx;
-        a.nx0[s] = nx;
+        const unsigned cm = __ballot_sync(0xffffffffu, claimed);
+        if (cm) {
+            const int leader = __ffs(cm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.nslots, (unsigned long long)__popc(cm));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (claimed) {
+                unsigned long long ns = base + __popc(cm & ((1u << lane) - 1u));
+                if (ns >= a.cap) {
+                    atomicAdd(&a.m.counters[C_MEMO_OVF], 1ull);
+                } else {
+                    a.svid[ns] = vid;
+                    a.sj[ns] = up;
+                    a.sord[ns] = key;
+                    *(volatile unsigned int *)&a.table[hc].val = (u32)ns;
+                    nx = (u32)ns;
+                }
+            }
+        }
+        if (act) {
+            a.state[s].x = nx;
+            a.nx0[s] = nx;
+        }
     }
 }
 
@@ -544,6 +555,7 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
 // it (k_memo_resolve over every slot from fbase on).  A chain longer than
 // max_iter links raises C_TAIL_CAP and stops.
 constexpr long long kTailMax = 1 << 18;   // frontier size that switches to the tail kernel
+constexpr int kLevelBatch = 4;            // levels issued per host round trip
 
 // The upstream link (vid, up) of a chain: the pair in up's row, else a slot
 // of the table -- found (or pending when its claimant has not published it
@@ -625,16 +637,40 @@ __global__ void __launch_bounds__(128) k_memo_tail(MemoArgs a, long long max_ite
 // claimant wrote (visible after the launch boundary).
 __global__ void k_memo_resolve(MemoArgs a)
 {
-    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= a.nf) return;
-    u32 s = a.fr ? a.fr[it] : a.fbase + (u32)it;
-    u32 nx = a.state[s].x;
-    if (nx != kNone && (nx & kPending)) {
-        u32 v = a.table[nx & ~kPending].val;
-        if (v == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
-        a.state[s].x = v;
-        a.nx0[s] = v;
+    const u32 fbase = a.dlv ? (u32)a.dlv[0] : a.fbase;
+    const long long nf = a.dlv ? (long long)a.dlv[1] : a.nf;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < nf;
+         it += (long long)gridDim.x * blockDim.x) {
+        u32 s = a.fr ? a.fr[it] : fbase + (u32)it;
+        u32 nx = a.state[s].x;
+        if (nx != kNone && (nx & kPending)) {
+            u32 v = a.table[nx & ~kPending].val;
+            if (v == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
+            a.state[s].x = v;
+            a.nx0[s] = v;
+        }
     }
+}
+
+// Device-side frontier of the next level: the slots the last level claimed,
+// [total, min(nslots, cap)) (dlv = {fbase, nf, total}); the first level's
+// frontier is its miss list.
+__global__ void k_level_next(unsigned long long *dlv, const unsigned long long *nslots,
+                             unsigned long long cap)
+{
+    unsigned long long ns = *nslots;
+    if (ns > cap) ns = cap;   // overflow: raised by the claimant, retried larger
+    dlv[0] = dlv[2];
+    dlv[1] = ns - dlv[2];
+    dlv[2] = ns;
+}
+
+__global__ void k_level_miss(unsigned long long *dlv, const unsigned long long *nmiss,
+                             unsigned long long npairs)
+{
+    dlv[0] = 0ull;
+    dlv[1] = *nmiss;
+    dlv[2] = npairs;
 }
 
 // Compensated (double-float) addition: TwoSum of the high parts, then the
@@ -941,6 +977,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     a.fbase = 0;
     a.nf = m.npairs;
     a.fr = nullptr;
+    a.dlv = nullptr;
     a.miss = c->m_fr.as<u32>();
     a.nmiss = ctr + C_MISS;
     a.hard = c->m_hard.as<uint2>();
@@ -954,18 +991,76 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     bool timing = c->p.timing != 0;
     if (timing && !c->hev[0])
         for (int k = 0; k < 4; ++k) cudaEventCreate(&c->hev[k]);
+    if (timing && !c->lev_ev[0])
+        for (int k = 0; k < 4 * kLevelBatch; ++k) cudaEventCreate(&c->lev_ev[k]);
     double hop_ms = 0.0, link_ms = 0.0, jump_ms = 0.0;
     long long max_iter = m.hop_cap + 1;
-    unsigned long long total = (unsigned long long)m.npairs;   // slots so far
-    while (a.nf > 0) {
-        if (iter > 0 && a.nf <= kTailMax) {
+    // device frontier {fbase, nf, total} after the slot counters
+    unsigned long long *dlv = ctr + C_LEVEL;
+    static_assert(C_LEVEL + 3 <= C_COUNT, "level state inside the counters");
+    const unsigned fixed_grid = (unsigned)(nsm * 8);
+    auto ev = [&](int k) {
+        if (timing) cudaEventRecord(c->lev_ev[k], s);
+    };
+    // level 0: the first hop of every pair, row by row; its links not found
+    // in their upstream row are listed and resolved on the device
+    ev(0);
+    {
+        long long rows = t1 - t0;
+        k_memo_hop_rows<<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0, s>>>(
+            a);
+        k_memo_hop_hard<<<(unsigned)(nsm * 4), 256, 0, s>>>(a);
+    }
+    ev(1);
+    k_level_miss<<<1, 1, 0, s>>>(dlv, a.nmiss, (unsigned long long)m.npairs);
+    a.dlv = dlv;
+    a.fr = a.miss;
+    ev(2);
+    k_memo_link<<<fixed_grid, 256, 0, s>>>(a);
+    k_memo_resolve<<<fixed_grid, 256, 0, s>>>(a);
+    ev(3);
+    a.fr = nullptr;
+    k_level_next<<<1, 1, 0, s>>>(dlv, a.nslots, (unsigned long long)cap);
+    c->launches += 6;
+    ST_CUDA(c, cudaGetLastError());
+    iter = 1;
+    int pending = 1;   // levels whose events are not read yet
+    for (;;) {
+        // the slot count and the overflow flag are adjacent counters, then the level
+        static_assert(C_MEMO_OVF == C_SLOTS + 1, "adjacent counters");
+        unsigned long long both[2] = {0, 0}, lv[3] = {0, 0, 0};
+        ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_SLOTS, sizeof(both), cudaMemcpyDeviceToHost, s));
+        ST_CUDA(c, cudaMemcpyAsync(lv, dlv, sizeof(lv), cudaMemcpyDeviceToHost, s));
+        ST_CUDA(c, cudaStreamSynchronize(s));
+        if (timing) {
+            for (int q = 0; q < pending; ++q) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, c->lev_ev[4 * q], c->lev_ev[4 * q + 1]) == cudaSuccess)
+                    hop_ms += ms;
+                else cudaGetLastError();
+                if (cudaEventElapsedTime(&ms, c->lev_ev[4 * q + 2], c->lev_ev[4 * q + 3]) ==
+                    cudaSuccess)
+                    link_ms += ms;
+                else cudaGetLastError();
+            }
+        }
+        pending = 0;
+        if (both[1]) {
+            overflow = true;
+            return START_OK;
+        }
+        if (iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
+        a.fbase = (u32)lv[0];
+        a.nf = (long long)lv[1];
+        if (a.nf == 0) break;
+        if (a.nf <= kTailMax) {
             // the remaining levels in one launch, then the pending links
+            a.dlv = nullptr;
             if (timing) cudaEventRecord(c->hev[0], s);
             k_memo_tail<<<grid_for(a.nf, 128), 128, 0, s>>>(a, max_iter);
             if (timing) cudaEventRecord(c->hev[1], s);
             ++c->launches;
             ST_CUDA(c, cudaGetLastError());
-            unsigned long long both[2] = {0, 0};
             ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_SLOTS, sizeof(both), cudaMemcpyDeviceToHost,
                                        s));
             ST_CUDA(c, cudaStreamSynchronize(s));
@@ -987,17 +1082,13 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
                 if (cudaEventElapsedTime(&ms, c->hev[2], c->hev[3]) == cudaSuccess) link_ms += ms;
                 else cudaGetLastError();
             }
-            total = both[0];
             break;
         }
-        if (timing) cudaEventRecord(c->hev[0], s);
-        if (iter == 0) {   // first level: every pair, row by row
-            long long rows = t1 - t0;
-            k_memo_hop_rows<<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0,
-                              s>>>(a);
-            k_memo_hop_hard<<<(unsigned)(nsm * 4), 256, 0, s>>>(a);
-            ++c->launches;
-        } else {
+        // a batch of levels, each sized on the device by the one before
+        a.dlv = dlv;
+        a.nf = (long long)cap;   // launch sizes only: every kernel reads nf from dlv
+        for (int q = 0; q < kLevelBatch; ++q) {
+            ev(4 * q);
             switch (c->p.march_group) {
             case 32: launch_memo_hop<32>(a, s, nsm); break;
             case 16: launch_memo_hop<16>(a, s, nsm); break;
@@ -1006,45 +1097,17 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
             case 1: launch_memo_hop<1>(a, s, nsm); break;
             default: launch_memo_hop<8>(a, s, nsm); break;
             }
+            ev(4 * q + 1);
+            ev(4 * q + 2);
+            k_memo_link<<<fixed_grid, 256, 0, s>>>(a);
+            k_memo_resolve<<<fixed_grid, 256, 0, s>>>(a);
+            ev(4 * q + 3);
+            k_level_next<<<1, 1, 0, s>>>(dlv, a.nslots, (unsigned long long)cap);
+            c->launches += 4;
+            ++iter;
+            ++pending;
         }
-        if (timing) cudaEventRecord(c->hev[1], s);
-        if (iter == 0) {   // the first level's unresolved links were listed
-            a.fr = a.miss;
-            a.nf = (long long)read_u64(c, a.nmiss);
-        }
-        if (a.nf > 0) {
-            if (timing) cudaEventRecord(c->hev[2], s);
-            k_memo_link<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
-            k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
-            if (timing) cudaEventRecord(c->hev[3], s);
-            c->launches += 2;
-        }
-        ++c->launches;
-        a.fr = nullptr;
         ST_CUDA(c, cudaGetLastError());
-        // the slot count and the overflow flag are adjacent counters
-        unsigned long long both[2] = {0, 0};
-        static_assert(C_MEMO_OVF == C_SLOTS + 1, "adjacent counters");
-        ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_SLOTS, sizeof(both), cudaMemcpyDeviceToHost, s));
-        ST_CUDA(c, cudaStreamSynchronize(s));
-        if (timing) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
-            else cudaGetLastError();
-            if (a.nf > 0) {
-                if (cudaEventElapsedTime(&ms, c->hev[2], c->hev[3]) == cudaSuccess) link_ms += ms;
-                else cudaGetLastError();
-            }
-        }
-        if (both[1]) {
-            overflow = true;
-            return START_OK;
-        }
-        // the next frontier: the slots this level claimed
-        a.fbase = (u32)total;
-        a.nf = (long long)(both[0] - total);
-        total = both[0];
-        if (++iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
     }
     if (timing) {
         c->hop_ms += hop_ms;
@@ -1106,6 +1169,7 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
 {
     MemoArgs a;
     a.m = m;
+    a.dlv = nullptr;
     a.SN = (u32)c->stree.n;
     a.NS = (u32)c->ns;
     a.EN = (u32)(c->walk_emit ? c->et.n : 0);
