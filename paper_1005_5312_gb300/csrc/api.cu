@@ -318,7 +318,7 @@ static void release_all(start_ctx *c)
                    &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord, &c->m_nx0, &c->m_dl,
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_hard, &c->m_part, &c->m_table,
-                   &c->w_scratch, &c->w_over};
+                   &c->w_scratch, &c->w_over, &c->ctr_save};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);

@@ -131,6 +131,7 @@ struct start_ctx {
     st::DBuf lcount;  // u32 per target
     st::DBuf loff;    // u64 [np + 1]
     st::DBuf w_scratch, w_over;   // one-walk lists: kWalkRow ids per target; longer rows
+    st::DBuf ctr_save;            // counters before a memoised-march attempt (retries)
     bool walk_scratch = false;    // the last count walk also filled w_scratch
     unsigned long long walk_nover = 0;
     st::DBuf pent;    // u32 entry per pair

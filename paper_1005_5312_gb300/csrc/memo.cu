@@ -918,14 +918,6 @@ static void launch_memo_hop(const MemoArgs &a, cudaStream_t s, int nsm)
     k_memo_hop<G><<<(unsigned)blocks, 256, 0, s>>>(a);
 }
 
-static unsigned long long read_u64(start_ctx *c, const unsigned long long *d)
-{
-    unsigned long long v = 0;
-    cudaMemcpyAsync(&v, d, sizeof(v), cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
-    return v;
-}
-
 static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t cap,
                         bool &overflow, long long t0, long long t1, u64 base)
 {
@@ -995,6 +987,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
         for (int k = 0; k < 4 * kLevelBatch; ++k) cudaEventCreate(&c->lev_ev[k]);
     double hop_ms = 0.0, link_ms = 0.0, jump_ms = 0.0;
     long long max_iter = m.hop_cap + 1;
+    unsigned long long nslots_host = (unsigned long long)m.npairs;   // slots after the levels
     // device frontier {fbase, nf, total} after the slot counters
     unsigned long long *dlv = ctr + C_LEVEL;
     static_assert(C_LEVEL + 3 <= C_COUNT, "level state inside the counters");
@@ -1052,36 +1045,34 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
         if (iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
         a.fbase = (u32)lv[0];
         a.nf = (long long)lv[1];
+        nslots_host = lv[2];
         if (a.nf == 0) break;
         if (a.nf <= kTailMax) {
             // the remaining levels in one launch, then the pending links
             a.dlv = nullptr;
-            if (timing) cudaEventRecord(c->hev[0], s);
+            ev(0);
             k_memo_tail<<<grid_for(a.nf, 128), 128, 0, s>>>(a, max_iter);
-            if (timing) cudaEventRecord(c->hev[1], s);
+            ev(1);
             ++c->launches;
             ST_CUDA(c, cudaGetLastError());
+            unsigned long long tail_cap = 0;
             ST_CUDA(c, cudaMemcpyAsync(both, ctr + C_SLOTS, sizeof(both), cudaMemcpyDeviceToHost,
                                        s));
+            ST_CUDA(c, cudaMemcpyAsync(&tail_cap, ctr + C_TAIL_CAP, sizeof(tail_cap),
+                                       cudaMemcpyDeviceToHost, s));
             ST_CUDA(c, cudaStreamSynchronize(s));
             if (both[1]) {
                 overflow = true;
                 return START_OK;
             }
+            if (tail_cap) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
             a.nf = (long long)(both[0] - a.fbase);
-            if (timing) cudaEventRecord(c->hev[2], s);
+            ev(2);
             k_memo_resolve<<<grid_for(a.nf, 256), 256, 0, s>>>(a);
-            if (timing) cudaEventRecord(c->hev[3], s);
+            ev(3);
             ++c->launches;
-            if (read_u64(c, ctr + C_TAIL_CAP))
-                return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
-            if (timing) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, c->hev[0], c->hev[1]) == cudaSuccess) hop_ms += ms;
-                else cudaGetLastError();
-                if (cudaEventElapsedTime(&ms, c->hev[2], c->hev[3]) == cudaSuccess) link_ms += ms;
-                else cudaGetLastError();
-            }
+            nslots_host = both[0];
+            pending = 1;   // read after the first pointer-jumping round
             break;
         }
         // a batch of levels, each sized on the device by the one before
@@ -1113,7 +1104,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
         c->hop_ms += hop_ms;
         c->link_ms += link_ms;
     }
-    long long nslots = (long long)read_u64(c, ctr + C_SLOTS);
+    long long nslots = (long long)nslots_host;
     c->memo_slots = nslots;
     c->memo_evals += (unsigned long long)nslots;
     c->memo_links += (unsigned long long)nslots;
@@ -1145,6 +1136,13 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
             else cudaGetLastError();
         }
         if (!act) break;
+    }
+    if (timing && pending) {   // the tail's events (the rounds above waited on them)
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->lev_ev[0], c->lev_ev[1]) == cudaSuccess) c->hop_ms += ms;
+        else cudaGetLastError();
+        if (cudaEventElapsedTime(&ms, c->lev_ev[2], c->lev_ev[3]) == cudaSuccess) c->link_ms += ms;
+        else cudaGetLastError();
     }
     k_sum_jump_counts<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), jblocks, ctr);
     ++c->launches;
@@ -1216,13 +1214,16 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     // an attempt that runs out of slots leaves artefacts (table keys without
     // slots) in the error and fallback counters: restore them before retrying
     unsigned long long *ctr = c->counters.as<unsigned long long>();
-    unsigned long long saved[C_COUNT];
-    ST_CUDA(c, cudaMemcpyAsync(saved, ctr, sizeof(saved), cudaMemcpyDeviceToHost, c->stream));
-    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    // (a device copy: no wait)
+    if (ensure(c->ctr_save, C_COUNT * sizeof(unsigned long long)))
+        return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
+    unsigned long long *saved = c->ctr_save.as<unsigned long long>();
+    ST_CUDA(c, cudaMemcpyAsync(saved, ctr, C_COUNT * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToDevice, c->stream));
     for (int attempt = 0; attempt < 4; ++attempt) {
         if (attempt > 0)
-            ST_CUDA(c, cudaMemcpyAsync(ctr, saved, sizeof(saved), cudaMemcpyHostToDevice,
-                                       c->stream));
+            ST_CUDA(c, cudaMemcpyAsync(ctr, saved, C_COUNT * sizeof(unsigned long long),
+                                       cudaMemcpyDeviceToDevice, c->stream));
         // slot ids and table indices must stay below the pending flag (2^31)
         if (cap >= (1ull << 30)) return set_err(c, START_ERANGE, "too many chain links");
         bool overflow = false;

@@ -641,6 +641,15 @@ __global__ void k_self_heat(float *heat, const double *y, const float *nH, const
     heat[i] = (float)((double)heat[i] + pre * kHnuLErg * ih);
 }
 
+// The memoised march's evaluation and link counts into the counters (kernel
+// arguments: no host buffer to keep alive).
+__global__ void k_set_evals(unsigned long long *ctr, unsigned long long evals,
+                            unsigned long long links)
+{
+    ctr[0] = evals;
+    ctr[1] = links;
+}
+
 // Targets are processed in Morton-contiguous chunks of at most max_pairs
 // interaction pairs; each chunk is walked, marched and reduced on its own.
 int run_solve(start_ctx *c, float theta, float *gout_dev)
@@ -767,10 +776,10 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         ST_CUDA(c, cudaGetLastError());
     }
     if (memo) {
-        unsigned long long v[2] = {c->memo_evals, c->memo_links};
-        ST_CUDA(c, cudaMemcpyAsync(c->counters.as<unsigned long long>() + C_EVALS, v, sizeof(v),
-                                   cudaMemcpyHostToDevice, s));
-        ST_CUDA(c, cudaStreamSynchronize(s));
+        k_set_evals<<<1, 1, 0, s>>>(c->counters.as<unsigned long long>() + C_EVALS, c->memo_evals,
+                                    c->memo_links);
+        ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
     }
     return START_OK;
 }
