@@ -77,6 +77,8 @@ struct Frame {
 
 }  // namespace st
 
+constexpr int kLevelBatch = 4;   // memoised march: frontier levels issued per host round trip
+
 struct start_ctx {
     start_params p;
     cudaStream_t stream = nullptr;
@@ -174,7 +176,7 @@ struct start_ctx {
     long long chunks = 0;                    // target chunks of the last solve
     int memo_final = 0;                      // buffer holding the final chain sums
     cudaEvent_t hev[4] = {};
-    cudaEvent_t lev_ev[16] = {};      // memoised march: per-level events of a batch
+    cudaEvent_t lev_ev[4 * kLevelBatch] = {};   // memoised march: per-level events of a batch
 };
 
 namespace st {

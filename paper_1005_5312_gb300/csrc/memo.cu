@@ -555,7 +555,6 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
 // it (k_memo_resolve over every slot from fbase on).  A chain longer than
 // max_iter links raises C_TAIL_CAP and stops.
 constexpr long long kTailMax = 1 << 18;   // frontier size that switches to the tail kernel
-constexpr int kLevelBatch = 4;            // levels issued per host round trip
 
 // The upstream link (vid, up) of a chain: the pair in up's row, else a slot
 // of the table -- found (or pending when its claimant has not published it
