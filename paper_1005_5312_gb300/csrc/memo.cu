@@ -16,7 +16,9 @@
 //   2. each frontier slot takes one hop; its upstream link (v, up) is found
 //      in the table or claimed as a new slot, which joins the next frontier;
 //      links claimed by another group in the same launch are resolved by a
-//      second kernel, after the launch boundary;
+//      second kernel, after the launch boundary.  The frontier's size stays
+//      on the device, so several levels are issued per host round trip, and
+//      once it is small one kernel follows each remaining chain to its end;
 //   3. tau of every slot follows by compensated pointer jumping over the
 //      link forest (each round reads three successors, so log4 of the longest
 //      chain rounds; double-buffered, so the sum order depends only on the
