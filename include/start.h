@@ -365,12 +365,13 @@ long long start_memory_in_use(void);
  *   frame_out [4] lower corner x, y, z and side, device memory or NULL
  *   stream    cudaStream_t to issue the work on (NULL = default stream)
  * Host pointers are refused with START_EINVAL; non-finite positions give
- * START_EINVAL.  The call returns after its work on `stream` has finished.
- * The first call on a device looks up the scratch array's device address
- * (and may load the library's GPU code there): make it before any stream
- * capture begins.  All calls share the one scratch array, so calls that
- * overlap on the GPU (other streams, other host threads) race; serialise
- * them. */
+ * START_EINVAL.  The call synchronises `stream` (it reads back the count
+ * of non-finite positions) and returns after its work there has finished,
+ * so it cannot be issued on a stream that is being captured into a CUDA
+ * graph.  The first call on a device also looks up the scratch array's
+ * device address (and may load the library's GPU code there).  All calls
+ * share the one scratch array, so calls that overlap on the GPU (other
+ * streams, other host threads) race; serialise them. */
 #define START_NOALLOC_MAX_N (1LL << 20)
 int start_morton_order_noalloc(const float *pos, long long n, unsigned long long *keys_out,
                                unsigned *perm_out, double *frame_out, void *stream);

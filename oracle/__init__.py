@@ -46,48 +46,84 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        lib = C.CDLL(str(build()))
-        vp, lp, ip, dp, fp = C.c_void_p, C.c_long, C.c_int, C.c_double, C.c_float
-        P = C.POINTER
-        lib.orc_create.restype = vp
-        lib.orc_create.argtypes = [P(OrcParams)]
-        lib.orc_destroy.argtypes = [vp]
-        lib.orc_threads.restype = ip
-        lib.orc_build.restype = ip
-        lib.orc_build.argtypes = [vp, vp, vp, lp, vp, vp, lp, vp]
-        lib.orc_frame.argtypes = [vp, vp]
-        lib.orc_keys.argtypes = [vp, ip, vp]
-        lib.orc_perm.argtypes = [vp, ip, vp]
-        lib.orc_tree_size.restype = lp
-        lib.orc_tree_size.argtypes = [vp, ip]
-        lib.orc_tree_get.argtypes = [vp, ip] + [vp] * 9
-        lib.orc_nbr_total.restype = lp
-        lib.orc_nbr_total.argtypes = [vp]
-        lib.orc_nbr_get.argtypes = [vp, vp, vp]
-        lib.orc_set_emitters.argtypes = [vp, vp, vp]
-        lib.orc_emitter_L.restype = dp
-        lib.orc_emitter_L.argtypes = [vp, lp]
-        lib.orc_list.restype = lp
-        lib.orc_list.argtypes = [vp, ip, fp, lp, vp, lp]
-        lib.orc_march.restype = dp
-        lib.orc_march.argtypes = [vp, lp, vp, vp, vp, vp, lp, vp]
-        lib.orc_gamma.restype = ip
-        lib.orc_gamma.argtypes = [vp, vp, fp, vp, lp, vp, vp]
-        lib.orc_ionize.argtypes = [vp, vp, vp, vp, dp, lp, vp, vp]
-        lib.orc_spline_w.restype = dp
-        lib.orc_spline_w.argtypes = [dp, dp]
-        lib.orc_sph_density.argtypes = [vp, vp, vp]
-        lib.orc_h2_fsh.restype = dp
-        lib.orc_h2_fsh.argtypes = [dp]
-        lib.orc_bb_integrals.argtypes = [dp, dp, vp, vp]
-        lib.orc_rec_band_integrals.argtypes = [dp, dp, vp, vp]
-        lib.orc_self_terms.argtypes = [vp, vp, vp, lp, vp, vp]
-        lib.orc_gamma_spectral.restype = ip
-        lib.orc_gamma_spectral.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp, vp]
-        lib.orc_h2_dissociation.restype = ip
-        lib.orc_h2_dissociation.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp]
-        _lib = lib
+        _lib = _configure(C.CDLL(str(build())))
     return _lib
+
+
+def _configure(lib):
+    """Declares the argument and result types of the oracle's functions."""
+    vp, lp, ip, dp, fp = C.c_void_p, C.c_long, C.c_int, C.c_double, C.c_float
+    P = C.POINTER
+    lib.orc_create.restype = vp
+    lib.orc_create.argtypes = [P(OrcParams)]
+    lib.orc_destroy.argtypes = [vp]
+    lib.orc_threads.restype = ip
+    lib.orc_build.restype = ip
+    lib.orc_build.argtypes = [vp, vp, vp, lp, vp, vp, lp, vp]
+    lib.orc_frame.argtypes = [vp, vp]
+    lib.orc_keys.argtypes = [vp, ip, vp]
+    lib.orc_perm.argtypes = [vp, ip, vp]
+    lib.orc_tree_size.restype = lp
+    lib.orc_tree_size.argtypes = [vp, ip]
+    lib.orc_tree_get.argtypes = [vp, ip] + [vp] * 9
+    lib.orc_nbr_total.restype = lp
+    lib.orc_nbr_total.argtypes = [vp]
+    lib.orc_nbr_get.argtypes = [vp, vp, vp]
+    lib.orc_set_emitters.argtypes = [vp, vp, vp]
+    lib.orc_emitter_L.restype = dp
+    lib.orc_emitter_L.argtypes = [vp, lp]
+    lib.orc_list.restype = lp
+    lib.orc_list.argtypes = [vp, ip, fp, lp, vp, lp]
+    lib.orc_march.restype = dp
+    lib.orc_march.argtypes = [vp, lp, vp, vp, vp, vp, lp, vp]
+    lib.orc_gamma.restype = ip
+    lib.orc_gamma.argtypes = [vp, vp, fp, vp, lp, vp, vp]
+    lib.orc_ionize.argtypes = [vp, vp, vp, vp, dp, lp, vp, vp]
+    lib.orc_spline_w.restype = dp
+    lib.orc_spline_w.argtypes = [dp, dp]
+    lib.orc_sph_density.argtypes = [vp, vp, vp]
+    lib.orc_h2_fsh.restype = dp
+    lib.orc_h2_fsh.argtypes = [dp]
+    lib.orc_bb_integrals.argtypes = [dp, dp, vp, vp]
+    lib.orc_rec_band_integrals.argtypes = [dp, dp, vp, vp]
+    lib.orc_self_terms.argtypes = [vp, vp, vp, lp, vp, vp]
+    lib.orc_gamma_spectral.restype = ip
+    lib.orc_gamma_spectral.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp, vp]
+    lib.orc_h2_dissociation.restype = ip
+    lib.orc_h2_dissociation.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp]
+    return lib
+
+
+def build_variant(source_text: str, tag: str) -> Path:
+    """Compiles a modified copy of the oracle's source (the tests plant
+    mistakes in it to show that a pin catches them) into _build/."""
+    BUILD.mkdir(exist_ok=True)
+    src = BUILD / f"variant_{tag}.c"
+    src.write_text(source_text)
+    out = BUILD / f"libvariant_{tag}.so"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", str(src), "-o", str(out), "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+class use_library:
+    """Context manager: Oracle objects created inside it use the library at
+    `path` (a variant from build_variant) instead of the oracle's own."""
+
+    def __init__(self, path):
+        self.path = str(path)
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _configure(C.CDLL(self.path))
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
 
 
 def _p(a: np.ndarray):

@@ -554,8 +554,10 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
 // link in its row or the table; a link it claims becomes its next slot -- so
 // the remaining levels need no launch and no host round trip each.  Links
 // another thread claimed in this launch stay pending and are resolved after
-// it (k_memo_resolve over every slot from fbase on).  A chain longer than
-// max_iter links raises C_TAIL_CAP and stops.
+// it (k_memo_resolve over every slot from fbase on).  The frontier holds
+// level iter of the chains; a chain that needs more than max_iter further
+// links (the caller passes the levels left under the hop cap) raises
+// C_TAIL_CAP and stops.
 constexpr long long kTailMax = 1 << 18;   // frontier size that switches to the tail kernel
 
 // The upstream link (vid, up) of a chain: the pair in up's row, else a slot
@@ -1043,16 +1045,19 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
             overflow = true;
             return START_OK;
         }
-        if (iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
         a.fbase = (u32)lv[0];
         a.nf = (long long)lv[1];
         nslots_host = lv[2];
+        // every chain ended (possibly inside the last batch, whose later
+        // levels then launched over an empty frontier and did nothing)
         if (a.nf == 0) break;
+        // a non-empty frontier at level iter: its chains hold more than iter links
+        if (iter > max_iter) return set_err(c, START_ECHAIN, "a chain exceeded hop_cap");
         if (a.nf <= kTailMax) {
             // the remaining levels in one launch, then the pending links
             a.dlv = nullptr;
             ev(0);
-            k_memo_tail<<<grid_for(a.nf, 128), 128, 0, s>>>(a, max_iter);
+            k_memo_tail<<<grid_for(a.nf, 128), 128, 0, s>>>(a, max_iter - iter);
             ev(1);
             ++c->launches;
             ST_CUDA(c, cudaGetLastError());

@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
             comp = (tk - tau) - yk;
             tau = tk;
             if (tau > a.tau_cut) done = true;
-            if (!done && (long long)nh > a.hop_cap) {
+            // more than hop_cap links: the chain goes on after hop_cap hops
+            if (!done && (long long)nh >= a.hop_cap) {
                 done = true;
                 if (gl == 0) ++ovf;
             }

@@ -477,7 +477,42 @@ def test_hop_cap_reports_echain(S, cfg1, mode):
     assert e.value.code == S.START_ECHAIN
 
 
+def _depth_and_caps(S, w, mode, theta):
+    """Solve with no hop cap, then with hop_cap = the longest chain (must pass,
+    bitwise the same Gamma) and one less (must report START_ECHAIN)."""
+    nHI = w.n_HI()
+    ctx = S.Context(tau_cut=1e30, march_mode=mode, ptree_leaf=PTREE_LEAF)
+    ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
+    g = np.zeros(w.n_p, np.float32)
+    ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
+    depth = ctx.stats()["max_hops"]
+    assert depth > 2
+    ctx.set_params(hop_cap=depth)
+    g2 = np.zeros(w.n_p, np.float32)
+    ctx.rt_solve(theta, n_HI=nHI, gamma_out=g2)
+    assert np.array_equal(g, g2)
+    ctx.set_params(hop_cap=depth - 1)
+    with pytest.raises(S.StartError) as e:
+        ctx.rt_solve(theta, n_HI=nHI, gamma_out=g2)
+    assert e.value.code == S.START_ECHAIN
+    return depth
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_hop_cap_at_the_longest_chain(S, cfg1, mode):
+    """The limit falls where the memoised march follows chains one thread
+    each (its tail kernel); both march modes agree on where it lies."""
+    _depth_and_caps(S, cfg1, mode, 0.5)
+
+
 # ------------------------------------------------------------------ full size, sampled
+def test_config2_hop_cap_at_the_longest_chain(S):
+    """64^3 particles, 1024 sources: the memoised march issues batches of
+    frontier levels before its tail; hop_cap at the longest chain passes and
+    one less is reported."""
+    _depth_and_caps(S, config2(), 1, 1.0)
+
+
 def test_config2_full_size_sampled_targets(S):
     """64^3 particles and 1024 sources at theta = 0.5 in the launch
     configuration the benchmark uses; the oracle evaluates 48 sampled

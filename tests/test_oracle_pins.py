@@ -494,6 +494,64 @@ def test_diffuse_emitters_thin_theta0_bruteforce():
         assert abs(g[i] / ref - 1) < 1e-12
 
 
+def _escape_probability(pt, box, kappa, ndir=200000):
+    """(1/4 pi) int exp(-kappa l(Omega)) dOmega for a point inside the cube
+    [0, box]^3, l the distance to the cube's surface along Omega (Fibonacci
+    directions)."""
+    k = np.arange(ndir) + 0.5
+    z = 1.0 - 2.0 * k / ndir
+    ph = math.pi * (1.0 + 5.0 ** 0.5) * k
+    rxy = np.sqrt(1.0 - z * z)
+    d = np.stack([rxy * np.cos(ph), rxy * np.sin(ph), z], 1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(d > 0, (box - pt) / d, np.where(d < 0, -pt / d, np.inf))
+    return float(np.exp(-kappa * t.min(1)).mean())
+
+
+def diffuse_balance_ratios(nside=24, box=4.0, x=0.5, tau_dx=0.25, seed=41):
+    """Radiative equilibrium of a homogeneous emitting and absorbing medium
+    (Section 4.1's recombination photons, theta = 0): at an interior point the
+    photons absorbed per unit volume, n_HI (sigma Gamma + k_self), equal those
+    emitted per unit volume, alpha_1 n_e n_p, less the part that escapes
+    through the box's surface.  Returns absorbed / (emitted (1 - P_esc)) at the
+    eight particles nearest the centre, P_esc by angular quadrature."""
+    dx = box / nside
+    rng = np.random.default_rng(seed)
+    pos = jittered_lattice(nside, box, rng)
+    h = smoothing_lengths(pos)
+    n = pos.shape[1]
+    V = np.full(n, dx ** 3)
+    n_hi = tau_dx / (SIGMA_CM2 * dx * KPC_CM)
+    nH = np.full(n, n_hi / (1.0 - x), np.float32)
+    y = np.full(n, 1.0 - x)
+    o = oracle.Oracle(pos, h, np.zeros((3, 0), np.float32), np.zeros(0), V, diffuse=True, **PHYS)
+    o.set_emitters(y, nH)
+    d2 = ((pos.T.astype(np.float64) - box / 2) ** 2).sum(1)
+    idx = np.argsort(d2)[:8]
+    nHI = (y * nH.astype(np.float64)).astype(np.float32)
+    g = o.gamma(nHI, 0.0, targets=idx)
+    ks, _ = o.self_terms(nH, y)
+    n_hi_cm = float(nHI[0])
+    absorbed = n_hi_cm * (SIGMA_CM2 * g + ks[idx])
+    n_e = x * float(nH[0])
+    emitted = (ALPHA_A - ALPHA_B) * n_e * n_e          # per cm^3 and second
+    kappa = n_hi_cm * SIGMA_CM2 * KPC_CM               # per length unit
+    keep = np.array([1.0 - _escape_probability(pos[:, i].astype(np.float64), box, kappa)
+                     for i in idx])
+    return absorbed / (emitted * keep)
+
+
+def test_diffuse_emitters_radiative_equilibrium():
+    """Pins the emitters' luminosity N_rec = alpha_1 n_e n_p V (Section 4.1)
+    through the transfer itself: a wrong coefficient (alpha_A or alpha_B for
+    alpha_1), a missing volume unit, or x instead of x^2 moves the balance by
+    a factor of 1.6 or more.  The lattice sum stands for the volume integral
+    to about 3 % per target (one particle spacing has tau = 0.25)."""
+    rel = diffuse_balance_ratios()
+    assert np.all(np.abs(rel - 1.0) < 0.05), rel
+    assert abs(rel.mean() - 1.0) < 0.02, rel.mean()
+
+
 # ---------------------------------------------------------------- Stromgren
 @pytest.mark.slow
 def test_stromgren_sphere_and_ifront_law():

@@ -67,3 +67,53 @@ def test_noalloc_rejects_oversize_and_host_pointers():
     host = np.zeros(12, np.float32)
     assert L.start_morton_order_noalloc(C.c_void_p(host.ctypes.data), 4, C.c_void_p(k.data_ptr()),
                                         C.c_void_p(p.data_ptr()), None, None) == S.START_EINVAL
+
+
+def _noalloc(S, L, torch, pos, with_frame=True):
+    n = pos.shape[1]
+    d_pos = torch.from_numpy(pos).cuda()
+    d_keys = torch.zeros(max(n, 1), dtype=torch.uint64, device="cuda")
+    d_perm = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    d_frame = torch.zeros(4, dtype=torch.float64, device="cuda") if with_frame else None
+    rc = L.start_morton_order_noalloc(C.c_void_p(d_pos.data_ptr()), n,
+                                      C.c_void_p(d_keys.data_ptr()),
+                                      C.c_void_p(d_perm.data_ptr()),
+                                      C.c_void_p(d_frame.data_ptr()) if with_frame else None,
+                                      None)
+    torch.cuda.synchronize()
+    return rc, d_keys[:n].cpu().numpy().astype(np.uint64), \
+        d_perm[:n].cpu().numpy().astype(np.uint32), \
+        None if d_frame is None else d_frame.cpu().numpy()
+
+
+def test_noalloc_small_full_and_invalid_inputs():
+    """A set that the regular path sorts in one block (1000 particles), one
+    that fills the scratch exactly (2^20 particles), a call without a frame
+    output, and a non-finite position (START_EINVAL; the next call is still
+    correct)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1005_5312_gb300 as S
+    S.build()
+    L = S.lib()
+    rng = np.random.default_rng(22)
+    for n, box, with_frame in ((1000, 2.0, True), (1 << 20, 5.0, True), (3001, 1.0, False)):
+        pos = rng.uniform(-box, box, size=(3, n)).astype(np.float32)
+        pos[:, 7] = pos[:, 3]
+        rc, keys, perm, frame = _noalloc(S, L, torch, pos, with_frame)
+        assert rc == S.START_OK
+        k_ref, p_ref, f_ref = _regular(S, pos)
+        assert np.array_equal(keys, k_ref)
+        assert np.array_equal(perm, p_ref)
+        if with_frame:
+            assert np.array_equal(frame, f_ref)
+    bad = rng.uniform(-1, 1, size=(3, 500)).astype(np.float32)
+    bad[1, 123] = np.nan
+    rc, _, _, _ = _noalloc(S, L, torch, bad)
+    assert rc == S.START_EINVAL
+    pos = rng.uniform(-1, 1, size=(3, 777)).astype(np.float32)
+    rc, keys, perm, frame = _noalloc(S, L, torch, pos)
+    k_ref, p_ref, f_ref = _regular(S, pos)
+    assert rc == S.START_OK and np.array_equal(keys, k_ref) and np.array_equal(perm, p_ref)
+    assert np.array_equal(frame, f_ref)
