@@ -164,8 +164,10 @@ typedef struct start_stats {
                                    chain closed */
 } start_stats;
 
-/* Phases timed when start_params.timing = 1 (milliseconds of the last
- * occurrence of each, from CUDA events on the context's stream). */
+/* Phases timed when start_params.timing = 1 (milliseconds summed over every
+ * occurrence since the previous start_get_timings, from CUDA events on the
+ * context's stream; a solve in several target chunks runs the march and
+ * Gamma phases once per chunk). */
 #define START_PHASE_BUILD 0   /* start_build_trees */
 #define START_PHASE_WALK 1    /* interaction lists */
 #define START_PHASE_MARCH 2   /* ray march (the dominant kernel) */
@@ -175,7 +177,8 @@ typedef struct start_stats {
 #define START_PHASE_HOPS 6    /* memoised march: sum of its hop kernels */
 #define START_PHASE_LINK 7    /* memoised march: sum of its link-resolution kernels */
 #define START_PHASE_JUMP 8    /* memoised march: sum of its pointer-jumping rounds */
-#define START_NPHASES 9
+#define START_PHASE_DENSITY 9 /* start_sph_density */
+#define START_NPHASES 10
 
 typedef struct start_ctx start_ctx;
 
@@ -326,14 +329,26 @@ int start_get_neighbors(start_ctx *c, unsigned long long *off, unsigned *idx);
 #define START_ENTRY_EMITTER 0x40000000u
 int start_get_lists(start_ctx *c, float theta, unsigned long long *off, unsigned *entries);
 
+/* Checksums of the interaction lists at theta, for comparing them whole at
+ * sizes where the lists are too large to copy out: for every target i
+ * (input order) hash[i] = 64-bit FNV-1a (offset basis 14695981039346656037,
+ * prime 1099511628211) over the entries start_get_lists returns for i, in
+ * walk order, each entry fed as its four bytes, least significant first;
+ * count[i] = the number of entries.  hash and count are [n_p], host or
+ * device memory (count may be NULL).  The walk is the one every solve
+ * uses (Eqs. con1, con2). */
+int start_get_list_hashes(start_ctx *c, float theta, unsigned long long *hash,
+                          unsigned long long *count);
+
 /* Per-particle float32 luminosity of the emitters (input order), photons/s
  * divided by L_unit, as used by the last diffuse solve. */
 int start_get_emitter_L(start_ctx *c, float *out);
 
 int start_get_stats(start_ctx *c, start_stats *out);
 
-/* ms[k] = duration of the last phase k (START_PHASE_*), or -1 if it was not
- * recorded; n entries are written (n <= START_NPHASES).  Synchronises. */
+/* ms[k] = summed duration of phase k (START_PHASE_*) since the previous
+ * call, or -1 if it did not run (or timing is off); n entries are written
+ * (n <= START_NPHASES).  Resets the sums of every phase.  Synchronises. */
 int start_get_timings(start_ctx *c, double *ms, int n);
 
 /* Message of the last failure on c (never NULL). */

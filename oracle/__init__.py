@@ -74,6 +74,7 @@ def _configure(lib):
     lib.orc_emitter_L.argtypes = [vp, lp]
     lib.orc_list.restype = lp
     lib.orc_list.argtypes = [vp, ip, fp, lp, vp, lp]
+    lib.orc_list_hashes.argtypes = [vp, fp, vp, lp, vp, vp]
     lib.orc_march.restype = dp
     lib.orc_march.argtypes = [vp, lp, vp, vp, vp, vp, lp, vp]
     lib.orc_gamma.restype = ip
@@ -231,6 +232,19 @@ class Oracle:
             if n <= cap:
                 return out[:n].copy()
             cap = n
+
+    def list_hashes(self, theta: float, targets=None):
+        """(FNV-1a 64-bit checksum, length) of the interaction rows of the
+        targets (input indices, or all), source tree then emitter tree."""
+        if targets is None:
+            nt, tp = self.np_, None
+        else:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            nt, tp = len(targets), _p(targets)
+        h = np.zeros(max(nt, 1), np.uint64)
+        cnt = np.zeros(max(nt, 1), np.int64)
+        self.lib.orc_list_hashes(self.h_, C.c_float(theta), tp, nt, _p(h), _p(cnt))
+        return h[:nt], cnt[:nt]
 
     def march(self, target: int, rs, nHI, with_chain: bool = False):
         rs = np.ascontiguousarray(rs, dtype=np.float32)

@@ -612,6 +612,47 @@ long orc_list(const orc *o, int which, float theta, long target, long *out, long
     return n;
 }
 
+/* Whole-row checksums of the interaction lists (all trees walked by a
+ * solve: the sources, then in the diffuse case the emitters), for comparing
+ * them with a list computed elsewhere without copying every entry.  Each
+ * entry is encoded as an unsigned 32-bit word -- the cell's node id, or
+ * 0x80000000 | sorted rank for a member of a leaf that was not accepted,
+ * with 0x40000000 added on the emitter tree -- and fed to the 64-bit FNV-1a
+ * hash (offset basis 14695981039346656037, prime 1099511628211) as four
+ * bytes, least significant first, in walk order.  count = row length. */
+void orc_list_hashes(const orc *o, float theta, const long *targets, long nt, uint64_t *hash,
+                     long *count)
+{
+    long n = targets ? nt : o->np;
+    double th = theta;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long t = 0; t < n; ++t) {
+        long i = targets ? targets[t] : t;
+        uint64_t h = 14695981039346656037ull;
+        long len = 0;
+        for (int which = 1; which <= (o->p.diffuse ? 2 : 1); ++which) {
+            const otree *tr = pick_tree(o, which);
+            if (!tr->n) continue;
+            lvec v = {0};
+            walk_node(tr, 0, o->px[i], o->py[i], o->pz[i], th * th,
+                      which == 2 ? o->prank[i] : -1, &v);
+            for (long e = 0; e < v.n; ++e) {
+                long ent = v.v[e];
+                uint32_t w = ent >= 0 ? (uint32_t)ent : (0x80000000u | (uint32_t)(-ent - 1));
+                if (which == 2) w |= 0x40000000u;
+                for (int b = 0; b < 4; ++b) {
+                    h ^= (w >> (8 * b)) & 0xffu;
+                    h *= 1099511628211ull;
+                }
+            }
+            len += v.n;
+            free(v.v);
+        }
+        hash[t] = h;
+        if (count) count[t] = len;
+    }
+}
+
 /* Optical depth from a source at rs to particle `target`; the visited chain
  * (input indices, target first) goes to chain_out when given. */
 double orc_march(const orc *o, long target, const float rs32[3], const float *nHI, long *hops,

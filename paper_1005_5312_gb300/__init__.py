@@ -88,6 +88,7 @@ def lib():
             "start_nbr_total": (ll, [vp]),
             "start_get_neighbors": (i, [vp, vp, vp]),
             "start_get_lists": (i, [vp, f, vp, vp]),
+            "start_get_list_hashes": (i, [vp, f, vp, vp]),
             "start_get_emitter_L": (i, [vp, vp]),
             "start_get_stats": (i, [vp, P(StartStats)]),
             "start_get_timings": (i, [vp, P(d), i]),
@@ -322,17 +323,28 @@ class Context:
         _check(self.h, lib().start_get_lists(self.h, float(theta), off.ctypes.data, ent.ctypes.data))
         return off, ent[:int(off[-1])]
 
+    def list_hashes(self, theta):
+        """(FNV-1a 64-bit checksum, length) of every target's interaction row
+        at theta, input order (start_get_list_hashes)."""
+        hsh = np.zeros(max(self.n_p, 1), np.uint64)
+        cnt = np.zeros(max(self.n_p, 1), np.uint64)
+        _check(self.h, lib().start_get_list_hashes(self.h, float(theta), hsh.ctypes.data,
+                                                   cnt.ctypes.data))
+        return hsh[:self.n_p], cnt[:self.n_p]
+
     def emitter_L(self):
         out = np.zeros(max(self.n_p, 1), np.float32)
         _check(self.h, lib().start_get_emitter_L(self.h, out.ctypes.data))
         return out[:self.n_p]
 
-    PHASES = ("build", "walk", "march", "gamma", "ionize", "emit", "hops", "link", "jump")
+    PHASES = ("build", "walk", "march", "gamma", "ionize", "emit", "hops", "link", "jump",
+              "density")
 
     def timings(self) -> dict:
-        """Milliseconds of the last build / walk / march / gamma / ionize /
-        emitter phase, and of the memoised march's hop, link-resolution and
-        pointer-jumping kernels summed over the last solve (needs timing=1)."""
+        """Milliseconds of each phase (build, walk, march, gamma, ionize,
+        emitters, the memoised march's hop, link-resolution and
+        pointer-jumping kernels, SPH density) summed since the previous call,
+        -1 where a phase did not run (needs timing=1)."""
         n = len(self.PHASES)
         ms = (C.c_double * n)()
         _check(self.h, lib().start_get_timings(self.h, ms, n))

@@ -111,12 +111,18 @@ long long bytes_in_use() { return g_bytes.load(); }
 void phase_mark(start_ctx *c, int phase, bool end)
 {
     if (!c->p.timing) return;
-    if (!c->ev_init) {
-        for (int k = 0; k < 2 * START_NPHASES; ++k) cudaEventCreate(&c->ev[k]);
-        c->ev_init = true;
+    std::vector<cudaEvent_t> &v = c->pev[phase];
+    const size_t k = 2 * (size_t)c->pcount[phase] + (end ? 1 : 0);
+    while (v.size() <= k) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        v.push_back(e);
     }
-    cudaEventRecord(c->ev[2 * phase + (end ? 1 : 0)], c->stream);
-    if (end) c->ev_rec[phase] = true;
+    cudaEventRecord(v[k], c->stream);
+    if (end) ++c->pcount[phase];
 }
 
 int set_err(start_ctx *c, int code, const std::string &msg)
@@ -323,9 +329,11 @@ static void release_all(start_ctx *c)
     tree_release(c->pt);
     tree_release(c->stree);
     tree_release(c->et);
-    if (c->ev_init)
-        for (int k = 0; k < 2 * START_NPHASES; ++k) cudaEventDestroy(c->ev[k]);
-    c->ev_init = false;
+    for (int k = 0; k < START_NPHASES; ++k) {
+        for (cudaEvent_t e : c->pev[k]) cudaEventDestroy(e);
+        c->pev[k].clear();
+        c->pcount[k] = 0;
+    }
     for (int k = 0; k < 4; ++k)
         if (c->hev[k]) cudaEventDestroy(c->hev[k]);
     for (cudaEvent_t &e : c->lev_ev)
@@ -873,6 +881,24 @@ int start_get_lists(start_ctx *c, float theta, unsigned long long *off, unsigned
     return START_OK;
 }
 
+int start_get_list_hashes(start_ctx *c, float theta, unsigned long long *hash,
+                          unsigned long long *count)
+{
+    if (!c || (!hash && c->np > 0)) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    if (!(theta >= 0.f) || !isfinite(theta)) return set_err(c, START_EINVAL, "theta must be >= 0");
+    DeviceGuard g(c);
+    long long n = c->np;
+    if (n == 0) return START_OK;
+    if (c->diffuse && c->has_state) ST_TRY(refresh_emitters(c));
+    ST_TRY(ensure(c->stage, (size_t)n * 16));
+    unsigned long long *dh = c->stage.as<unsigned long long>();
+    ST_TRY(run_walk_hash(c, theta, dh, dh + n));
+    ST_TRY(copy_out(c, hash, dh, (size_t)n * 8));
+    if (count) ST_TRY(copy_out(c, count, dh + n, (size_t)n * 8));
+    return START_OK;
+}
+
 int start_get_emitter_L(start_ctx *c, float *out)
 {
     if (!c || !out) return START_EINVAL;
@@ -924,15 +950,22 @@ int start_get_timings(start_ctx *c, double *ms, int n)
         if (k == START_PHASE_HOPS || k == START_PHASE_LINK || k == START_PHASE_JUMP) {
             double v = k == START_PHASE_HOPS ? c->hop_ms
                        : k == START_PHASE_LINK ? c->link_ms : c->jump_ms;
-            ms[k] = c->p.march_mode == 1 ? v : -1.0;
+            if (c->p.timing && c->p.march_mode == 1) ms[k] = v;
             continue;
         }
-        if (c->ev_init && c->ev_rec[k]) {
+        if (c->pcount[k] == 0) continue;
+        double sum = 0.0;
+        for (int q = 0; q < c->pcount[k]; ++q) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, c->ev[2 * k], c->ev[2 * k + 1]) == cudaSuccess) ms[k] = t;
-            else cudaGetLastError();
+            if (cudaEventElapsedTime(&t, c->pev[k][2 * q], c->pev[k][2 * q + 1]) == cudaSuccess)
+                sum += t;
+            else
+                cudaGetLastError();
         }
+        ms[k] = sum;
     }
+    for (int k = 0; k < START_NPHASES; ++k) c->pcount[k] = 0;
+    c->hop_ms = c->link_ms = c->jump_ms = 0.0;
     return START_OK;
 }
 

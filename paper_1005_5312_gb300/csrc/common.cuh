@@ -164,12 +164,13 @@ struct start_ctx {
 
     start_stats stats{};
     unsigned long long launches = 0;        // kernels launched by this context
-    cudaEvent_t ev[2 * START_NPHASES] = {};  // phase begin/end events (timing = 1)
-    bool ev_init = false;
-    bool ev_rec[START_NPHASES] = {};
-    double hop_ms = -1.0;                    // summed memo hop kernels (timing = 1)
-    double link_ms = -1.0;                   // summed memo link + resolve kernels
-    double jump_ms = -1.0;                   // summed pointer-jumping rounds
+    // timing = 1: begin/end event pairs of every occurrence of each phase since
+    // the last start_get_timings (pcount pairs recorded)
+    std::vector<cudaEvent_t> pev[START_NPHASES];
+    int pcount[START_NPHASES] = {};
+    double hop_ms = 0.0;                     // summed memo hop kernels (timing = 1)
+    double link_ms = 0.0;                    // summed memo link + resolve kernels
+    double jump_ms = 0.0;                    // summed pointer-jumping rounds
     long long jump_rounds = 0;               // rounds and algorithmic bytes of the
     unsigned long long jump_bytes = 0;       // last solve's pointer jumping
     unsigned long long memo_evals = 0, memo_links = 0;   // over the chunks of a solve
@@ -273,6 +274,7 @@ int resident_solve(start_ctx *c);
 // solve.cu
 int run_solve(start_ctx *c, float theta, float *gout_dev);
 int run_walk(start_ctx *c, float theta);
+int run_walk_hash(start_ctx *c, float theta, unsigned long long *hash, unsigned long long *count);
 int run_ionize(start_ctx *c, double dt);
 int refresh_emitters(start_ctx *c);
 

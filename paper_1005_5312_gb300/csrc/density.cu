@@ -65,12 +65,14 @@ int run_sph_density(start_ctx *c, const float *mass_dev, float *rho_dev)
     unsigned long long *ctr = c->counters.as<unsigned long long>();
     ST_TRY(ensure(c->mass_s, n * sizeof(float)));
     ST_CUDA(c, cudaMemsetAsync(ctr + C_BAD_INPUT, 0, sizeof(unsigned long long), s));
+    phase_mark(c, START_PHASE_DENSITY, false);
     k_mass_to_morton<<<grid_for(n, 256), 256, 0, s>>>(mass_dev, c->porig.as<u32>(), n,
                                                       c->mass_s.as<float>(), ctr + C_BAD_INPUT);
     k_sph_density<<<grid_for(n, 256), 256, 0, s>>>(n, c->pq.as<float4>(), c->ph.as<float>(),
                                                    c->nb_off.as<u32>(), c->nb_idx.as<u32>(),
                                                    c->mass_s.as<float>(), c->porig.as<u32>(),
                                                    rho_dev);
+    phase_mark(c, START_PHASE_DENSITY, true);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "k_sph_density");
 }

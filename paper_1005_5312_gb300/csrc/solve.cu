@@ -208,6 +208,49 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
     }
 }
 
+// Whole-row checksum of the interaction lists (introspection): FNV-1a
+// (64-bit, offset basis 14695981039346656037, prime 1099511628211) over the
+// raw entries of the row in walk order, each as four bytes, least
+// significant first.  The decisions are walk_tree's own, so the rows are
+// those every solve walks.
+struct HashRows {
+    unsigned long long h = 14695981039346656037ull;
+    __device__ __forceinline__ void put(u64, u32 e, u32)
+    {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            h ^= (e >> (8 * b)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+__global__ void __launch_bounds__(128) k_walk_hash(const float4 *pq, long long np, TreeView st_,
+                                                   TreeView et_, float th2f, double th2d,
+                                                   float cmag, const u32 *porig,
+                                                   unsigned long long *hash,
+                                                   unsigned long long *count,
+                                                   unsigned long long *fb_total)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned fb = 0;
+    if (i < np) {
+        const float4 p = pq[i];
+        u32 c = 0;
+        u64 w = 0;
+        HashRows rows;
+        walk_tree<1>(st_, p, th2f, th2d, cmag, kNone, 0u, CanonBase{}, c, w, ~0ull, rows, fb);
+        walk_tree<1>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, CanonBase{}, c, w, ~0ull, rows,
+                     fb);
+        const u32 o = porig[i];
+        hash[o] = rows.h;
+        count[o] = w;
+    }
+    for (int k = 16; k; k >>= 1) fb += __shfl_xor_sync(0xffffffffu, fb, k);
+    if ((threadIdx.x & 31) == 0 && fb) atomicAdd(fb_total, (unsigned long long)fb);
+}
+
 // ---------------------------------------------------------------- march
 // Position and L / L_unit of a pair's source; an out-of-range entry (never
 // expected) yields a dark source and raises the internal-error counter.
@@ -566,6 +609,21 @@ int run_walk(start_ctx *c, float theta)
     return walk_fill(c, theta, sv, ev, 0, c->np, 0ull);
 }
 
+// Row checksums and lengths of every target's interaction list, input order,
+// into device buffers hash / count.
+int run_walk_hash(start_ctx *c, float theta, unsigned long long *hash, unsigned long long *count)
+{
+    c->walk_emit = c->diffuse;
+    if (c->np == 0) return START_OK;
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    k_walk_hash<<<grid_for(c->np, 128), 128, 0, c->stream>>>(
+        c->pq.as<float4>(), c->np, source_view(c), emitter_view(c), theta * theta,
+        (double)theta * (double)theta, c->fr.cmag, c->porig.as<u32>(), hash, count,
+        ctr + C_WALK_FB);
+    ++c->launches;
+    return cuda_check(c, cudaGetLastError(), "k_walk_hash");
+}
+
 static MarchArgs march_args(start_ctx *c, long long npairs)
 {
     MarchArgs a;
@@ -659,7 +717,6 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     cudaStream_t s = c->stream;
     c->npairs = 0;
     c->memo_evals = c->memo_links = 0;
-    c->hop_ms = c->link_ms = c->jump_ms = c->p.timing ? 0.0 : -1.0;
     c->jump_rounds = 0;
     c->jump_bytes = 0;
     ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));

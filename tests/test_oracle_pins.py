@@ -248,6 +248,40 @@ def _lattice_problem(nside, box, seed, n_s=4):
     return pos, h, src, L
 
 
+def _fnv1a64(data: bytes) -> int:
+    h = 14695981039346656037
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_list_hashes_are_fnv1a_of_the_lists():
+    """The oracle's whole-row checksums: the 64-bit FNV-1a of the published
+    test vectors, then of every row's entries (brute-force-pinned lists)
+    encoded as 32-bit words, source tree then emitter tree."""
+    assert _fnv1a64(b"") == 0xCBF29CE484222325
+    assert _fnv1a64(b"a") == 0xAF63DC4C8601EC8C
+    assert _fnv1a64(b"foobar") == 0x85944171F73967E8
+    pos, h, src, L = _lattice_problem(6, 2.0, 27, n_s=9)
+    n = pos.shape[1]
+    V = np.full(n, (2.0 / 6) ** 3)
+    for diffuse in (False, True):
+        o = oracle.Oracle(pos, h, src, L, V, diffuse=diffuse, **PHYS)
+        if diffuse:
+            o.set_emitters(np.full(n, 0.5), np.full(n, 1e-3, np.float32))
+        for theta in (0.0, 0.6):
+            hs, cnt = o.list_hashes(theta)
+            for i in range(0, n, 5):
+                words = []
+                for which in ((1, 2) if diffuse else (1,)):
+                    for e in o.list(theta, i, which=which).tolist():
+                        w = e if e >= 0 else (0x80000000 | (-e - 1))
+                        words.append(w | (0x40000000 if which == 2 else 0))
+                data = b"".join(int(w).to_bytes(4, "little") for w in words)
+                assert cnt[i] == len(words)
+                assert int(hs[i]) == _fnv1a64(data)
+
+
 def test_march_uniform_closed_form():
     """Uniform n_HI: the trapezoids telescope to tau = sigma n |r_i - r_s|."""
     pos, h, src, L = _lattice_problem(10, 3.0, 20)
