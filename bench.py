@@ -1,14 +1,19 @@
 #!/usr/bin/env python3
 """Benchmark of the START hot path on one GB300 (or N replicas under torchrun).
 
-A step is one pass of the whole path over the multiple-source workload
-(64^3 = 262144 particles on a jittered lattice, 1024 sources with
-log-normal luminosity, uniform n_H = 1e-3 in a 6.6 kpc box): frame, Morton
-keys, sorts, source and particle octrees, moments, neighbour lists, walk,
-ray march, Gamma and the implicit 1 Myr ionisation update, coupled from step
-to step.  The metric is rays per second (a ray is one (target, virtual
-source) pair whose optical depth is evaluated); theta_crit = 0.5 is the
-headline and 1.0 is reported beside it.
+The headline workload is the large diffuse run: 256^3 = 16777216 particles
+on a jittered lattice in a 6.6 kpc box, log n_H a Gaussian random field
+(P(k) ~ k^-3, sigma_ln = 1.5, mean 1e-3 cm^-3), every particle emitting
+recombination photons plus 64 point sources of 1e50 photons/s.  A step is
+one pass of the whole path: frame, Morton keys, sorts, source, particle and
+emitter octrees, moments, neighbour lists, the SPH density recompute from
+the particle masses (Section 2.1), the emitters' luminosities and moments,
+the walk, the memoised ray march, Gamma, and the implicit 1 Myr ionisation
+update with the diffuse self term, coupled from step to step.  The metric
+is rays per second (a ray is one (target, virtual source) pair whose
+optical depth is evaluated and added to Gamma); theta_crit = 0.5 is the
+headline and 1.0 is reported beside it.  The 64^3 multiple-source set, the
+128^3 diffuse set and the served request stream are reported as extra keys.
 
 Prints one JSON line.  --impl reference times the FP64 oracle on the host
 cores on a bounded sample of the same workload instead.
@@ -17,8 +22,6 @@ from __future__ import annotations
 
 import argparse
 import json
-
-import numpy as np
 import math
 import os
 import statistics
@@ -27,16 +30,19 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ALGO_BYTES_PER_HOP = 516     # 32 u32 neighbour indices + 32 float3 positions + 1 float n_HI
-ALGO_BYTES_PER_RAY = 16      # virtual source record
-ALGO_BYTES_PER_TARGET = 8    # Gamma out, target record
-# memoised march, per evaluated chain link: the neighbour list (516 B) plus
-# the link's source record (16 B), its hash-table entry (16 B) and its slot
-# state (virtual source, particle, next, tau, links: 16 B)
+# algorithmic bytes of the march (per neighbour-list evaluation: 32 u32
+# indices + 32 float3 positions + 1 float n_HI), per ray (virtual-source
+# record) and per target (Gamma out)
+ALGO_BYTES_PER_EVAL = 516
+ALGO_BYTES_PER_RAY = 16
+ALGO_BYTES_PER_TARGET = 8
 L2_FLUSH_BYTES = 512 << 20
+G_REL = 1e-4
 
 
 def parse():
@@ -48,18 +54,22 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--theta2", type=float, default=1.0)
     ap.add_argument("--march-group", type=int, default=2)
-    ap.add_argument("--march-mode", type=int, default=1, choices=[0, 1],
-                    help="1 memoised march (default), 0 per-ray march")
-    ap.add_argument("--nside", type=int, default=64,
-                    help="lattice side of the multiple-source workload (64: the benchmark; "
+    ap.add_argument("--max-pairs", type=int, default=1 << 29,
+                    help="interaction pairs per chunk of the large run")
+    ap.add_argument("--nside", type=int, default=256,
+                    help="lattice side of the headline workload (256: the benchmark; "
                          "smaller: profiling cases)")
+    ap.add_argument("--side-steps", type=int, default=3,
+                    help="timed steps of the theta2 and end-to-end lines")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-theta2", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="oracle work per CPU-baseline measurement")
-    ap.add_argument("--ref-targets", type=int, default=16384,
+    ap.add_argument("--ref-targets", type=int, default=256,
                     help="targets per step of the reference arm")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline workload (no 64^3, 128^3 or serving lines)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-resident", action="store_true")
     ap.add_argument("--no-diffuse", action="store_true")
@@ -67,10 +77,10 @@ def parse():
                     help="skip the SPH density, H2 photodissociation, blackbody-source and "
                          "recombination-band lines")
     ap.add_argument("--no-method-error", action="store_true")
-    ap.add_argument("--lognormal256", action="store_true",
-                    help="add the 256^3 log-normal diffuse workload (about a minute)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-low-rate", type=float, default=8.0)
+    ap.add_argument("--serve-low-requests", type=int, default=96)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-log2np", default="15,21")
     return ap.parse_args()
@@ -155,48 +165,63 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha(source: str, kernel: str) -> str:
-    """sha256 (16 hex digits) of a kernel's definition text (from its
-    `__global__` line to the matching closing brace) together with the
-    file's constexpr definitions (tile shapes, template arguments)."""
+def sources_sha() -> str:
+    """sha256 (16 hex digits) of every CUDA source of the library: recorded
+    DRAM traffic stays valid only while none of the kernels has changed."""
     import hashlib
-    import re
-    text = open(os.path.join(ROOT, "paper_1005_5312_gb300", "csrc", source)).read()
-    m = re.search(r"__global__[^;{]*?\b" + re.escape(kernel) + r"\s*\(", text)
-    if not m:
-        return ""
-    consts = "\n".join(re.findall(r"^constexpr [^\n]*;", text, flags=re.M))
-    i = text.index("{", m.end())
-    depth = 0
-    for j in range(i, len(text)):
-        depth += {"{": 1, "}": -1}.get(text[j], 0)
-        if depth == 0:
-            return hashlib.sha256((consts + "\n" + text[m.start():j + 1]).encode()).hexdigest()[:16]
-    return ""
+    d = os.path.join(ROOT, "paper_1005_5312_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
 
 
-def traffic_record(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the kernel's current definition (else None)."""
+def traffic_record(key: str):
+    """DRAM bytes per step from a committed ncu summary, if it was taken on
+    the current kernels (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f).get(kernel)
-    if not d:
+        d = json.load(f).get(key)
+    if not d or d.get("sources_sha") != sources_sha():
         return None
-    return d if d.get("kernel_sha") == kernel_source_sha(d["source"], kernel) else None
+    return d
+
+
+def rel_errors(g, ref, g_abs):
+    """Relative deviation of the GPU Gamma from the oracle's where the oracle
+    is above the absolute floor, and the count outside the tolerance."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    err = np.abs(g - ref)
+    over = int(np.sum(err > G_REL * np.abs(ref) + g_abs))
+    m = ref > g_abs
+    rel = err[m] / ref[m]
+    if rel.size == 0:
+        rel = np.zeros(1)
+    return {"targets": int(len(ref)), "above_floor": int(m.sum()),
+            "max_rel": float(rel.max()), "p99_rel": float(np.percentile(rel, 99)),
+            "median_rel": float(np.median(rel)), "outside_tolerance": over,
+            "tolerance": f"|dG| <= {G_REL:g} G_oracle + {g_abs:.3g}"}
 
 
 # ---------------------------------------------------------------- reference arm
-def run_reference(args, w):
-    import numpy as np
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the headline workload: Gamma at random targets each step (the trees and
+    neighbour lists built once, outside the timed steps)."""
     import oracle
+    from start_inputs import config5
     ws, rank, _ = dist_env()
     if rank != 0:
         return None
     oracle.build()
+    w = config5(nside=args.nside)
     orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
+    orc.set_emitters(w.y0, w.n_H)
     nHI = w.n_HI()
     rng = np.random.default_rng(7)
     per_step = min(w.n_p, args.ref_targets)
@@ -216,35 +241,206 @@ def run_reference(args, w):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "theta": args.theta,
-                       "sample": f"{per_step} random targets per step"},
+            "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "emitters": w.n_p,
+                       "theta": args.theta, "sample": f"{per_step} random targets per step"},
             "cpu_baseline": {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} random targets of {w.n_p} per step"},
+                             "sample": f"Gamma at {per_step} random targets of {w.n_p} per step "
+                                       f"(all emitters and point sources, neutral start)"},
             "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
-def cpu_baseline(w, theta, seconds):
+def oracle_sample(w, theta, seconds, seed=5, chunk=None):
     """The oracle as it stands on the host cores: Gamma at random targets of
-    the same workload (neutral start), in chunks until `seconds` of work."""
-    import numpy as np
+    the workload's starting state, in chunks until `seconds` of work.
+    Returns (targets, Gamma, rays, seconds, threads)."""
     import oracle
     oracle.build()
     orc = oracle.Oracle.from_workload(w, ptree_leaf=16)
-    order = np.random.default_rng(5).permutation(w.n_p)
+    if w.diffuse:
+        orc.set_emitters(w.y0, w.n_H)
     nHI = w.n_HI()
+    order = np.random.default_rng(seed).permutation(w.n_p)
+    chunk = chunk or max(64, 4 * oracle.threads())
     done, rays, t = 0, 0, 0.0
-    chunk = 1024
+    parts = []
     while t < seconds and done < w.n_p:
         idx = order[done:done + chunk]
         t0 = time.perf_counter()
-        orc.gamma(nHI, theta, targets=idx)
+        parts.append(orc.gamma(nHI, theta, targets=idx))
         t += time.perf_counter() - t0
         rays += orc.last_stats["rays"]
         done += len(idx)
-    return {"value": rays / t, "unit": "rays/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"Gamma at {done} random targets of {w.n_p} (theta={theta}, neutral "
-                      f"start): {rays} rays in {t:.1f} s"}
+    return order[:done], np.concatenate(parts), rays, t, oracle.threads()
+
+
+# Per-phase models of the algorithmic bytes of a step (each phase's
+# compulsory traffic: what its kernels must read and write once), from the
+# step's own counts.  st: summed counters of the step; w: the workload.
+def phase_models(st, n_p, n_s, diffuse, chunk_count):
+    rays, links = st["rays"], st["evals"]
+    off = max(0, links - rays)          # chain links outside the interaction lists
+    nb = st["nbr_total"]
+    nodes = st["nodes_part"] + st["nodes_src"] + (st["nodes_emit"] if diffuse else 0)
+    return {
+        # frame, keys, 8 radix passes (key + index in and out), octree records,
+        # neighbour search (its CSR written) and the records of the particles
+        "build": {"kernels": "k_bbox, k_morton, k_rs_*, k_level_census, octree levels, "
+                             "k_moments_*, k_neighbours, k_nb_compact",
+                  "bytes": n_p * (12 + 4 + 8 + 8 * 24 + 16 + 8) + nb * 4 + nodes * 64,
+                  "model": "per particle: position, h, key, 8 radix passes x 24 B, record, CSR "
+                           "offsets; 4 B per neighbour; 64 B per octree node"},
+        "density": {"kernels": "k_mass_to_morton, k_sph_density",
+                    "bytes": n_p * 36 + nb * 24,
+                    "model": "per particle 36 B (mass gather, record, h, offsets, result); "
+                             "per neighbour 24 B (index, record, mass)"},
+        "emit": {"kernels": "k_emitters, k_moments_level",
+                 "bytes": (n_p * 32 + st["nodes_emit"] * 64) if diffuse else 0,
+                 "model": "per particle 32 B (y, n_H, V, L out); 64 B per emitter-tree node"},
+        "walk": {"kernels": "k_walk (count, fill), k_order_keys, k_walk_compact",
+                 "bytes": rays * 12 + n_p * 16 * chunk_count,
+                 "model": "per pair 12 B (canonical id written, read, order key written); per "
+                          "target and walk its 16 B record"},
+        "hops": {"kernels": "k_memo_hop_rows, k_memo_hop_hard, k_memo_hop<G>, k_memo_tail",
+                 "bytes": links * 32 + off * ALGO_BYTES_PER_EVAL + n_p * chunk_count * 676,
+                 "model": "per chain link 32 B (id and order key read; state, length and next "
+                          "written); per link outside the lists its neighbour list (516 B); per "
+                          "target and chunk its staged neighbour list (33 x 20 B + 16 B)"},
+        "link": {"kernels": "k_memo_link, k_memo_resolve",
+                 "bytes": off * 56 + rays * 8,
+                 "model": "per link outside the lists 56 B (upstream, id, key, table entry, "
+                          "claimed slot, next written); per pair 8 B (row search)"},
+        "jump": {"kernels": "k_memo_jump<3>",
+                 "bytes": st["jump_bytes"],
+                 "model": "16 B own state per slot and round; 32 B per slot that advances "
+                          "(first successor read and the write); 16 B per further successor "
+                          "read; 16 B per closed chain copied once"},
+        "gamma": {"kernels": "k_memo_gamma",
+                  "bytes": rays * 20 + n_p * 8,
+                  "model": "per pair 20 B (chain state, id); per target 8 B"},
+        "ionize": {"kernels": "k_ionize",
+                   "bytes": n_p * (36 if diffuse else 28),
+                   "model": "per particle: y read and written (16), Gamma (4), n_H (4), n_HI "
+                            "(4), V (8, diffuse)"},
+    }
+
+
+def kernel_table(phase_ms, models, step_ms, peak):
+    rows = []
+    for name, m in models.items():
+        ms = phase_ms.get(name)
+        if ms is None or ms < 0:
+            continue
+        gbs = m["bytes"] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        rows.append({"phase": name, "kernels": m["kernels"], "ms_per_step": ms,
+                     "share_of_step": ms / step_ms, "algorithmic_bytes_per_step": m["bytes"],
+                     "achieved_GB_per_s": gbs, "frac_of_measured_hbm": gbs / peak,
+                     "bytes_model": m["model"]})
+    rows.sort(key=lambda r: -r["ms_per_step"])
+    return rows
+
+
+def headline(S, w, dev, args, T, clk_index):
+    """The headline workload: W untimed and K timed coupled steps at theta,
+    then the theta2 line; per-step CUDA events on the context's stream."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream,
+                    max_pairs=args.max_pairs)
+    pos, h, sp, sL, V = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L), T(w.V)
+    mass = T((w.n_H.astype(np.float64) * w.V).astype(np.float32))
+    rho = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    y0 = T(w.y0)
+    y = y0.clone()
+    g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+
+    def step(theta):
+        ctx.build_trees(pos, h, sp, sL, V, diffuse=True)
+        ctx.sph_density(mass, rho)
+        ctx.set_state(rho, y)
+        ctx.rt_solve(theta, gamma_out=g)
+        ctx.ionize(w.dt_s, y_out=y)
+
+    def run(theta, steps, warmup, clock=None):
+        y.copy_(y0)
+        for _ in range(warmup):
+            step(theta)
+        torch.cuda.synchronize(dev)
+        ctx.timings()                       # reset the phase sums
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stats, phases = [], []
+        l0 = ctx.stats()["launches"]
+        if args.gpus > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        if clock:
+            clock.__enter__()
+        t_wall = time.perf_counter()
+        for e0, e1 in ev:
+            e0.record(stream)
+            step(theta)
+            e1.record(stream)
+            phases.append(ctx.timings())     # synchronises
+            stats.append(ctx.stats())
+        if args.gpus > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+        if clock:
+            clock.__exit__()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        launches = ctx.stats()["launches"] - l0
+        return dict(step_ms=step_ms, stats=stats, phases=phases, launches=launches, wall=t_wall)
+
+    clk = ClockSampler(clk_index)
+    r1 = run(args.theta, args.steps, args.warmup, clk)
+    r2 = None if args.no_theta2 else run(args.theta2, args.side_steps, 1)
+    # the starting state once more, for the parity check against the oracle
+    ctx.build_trees(pos, h, sp, sL, V, diffuse=True)
+    ctx.set_state(T(w.n_H), y0)
+    g0 = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+    ctx.rt_solve(args.theta, gamma_out=g0)
+    g_start = g0.cpu().numpy()
+    ctx.close()
+    return r1, r2, clk.summary(), g_start
+
+
+def headline_e2e(S, w, args):
+    """The same step through the C ABI with host buffers (numpy arrays): every
+    step copies its inputs to the device and Gamma and y back."""
+    ctx = S.Context(march_group=args.march_group, max_pairs=args.max_pairs)
+    mass = (w.n_H.astype(np.float64) * w.V).astype(np.float32)
+    rho = np.zeros(w.n_p, np.float32)
+    y = w.y0.copy()
+    g = np.zeros(w.n_p, np.float32)
+
+    def step():
+        ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L, w.V, diffuse=True)
+        ctx.sph_density(mass, rho)
+        ctx.set_state(rho, y)
+        ctx.rt_solve(args.theta, gamma_out=g)
+        ctx.ionize(w.dt_s, y_out=y)
+
+    step()
+    y[:] = w.y0
+    rays = 0
+    t0 = time.perf_counter()
+    for _ in range(args.side_steps):
+        step()
+        rays += ctx.stats()["rays"]
+    te, rays = reduce_over_ranks(time.perf_counter() - t0, rays)
+    ctx.close()
+    h2d = w.pos.nbytes + w.h.nbytes + w.src_pos.nbytes + w.src_L.nbytes + w.V.nbytes + \
+        mass.nbytes + rho.nbytes + y.nbytes
+    d2h = rho.nbytes + g.nbytes + y.nbytes
+    return {"value": rays / te, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * te / args.side_steps,
+            "steps": args.side_steps,
+            "note": "numpy host buffers through the C ABI: positions, h, sources, V, masses "
+                    "and y copied in, the density, Gamma and y copied out, every step"}
 
 
 def resident_steps(S, w, dev, args, T):
@@ -459,75 +655,114 @@ def diffuse_workload(S, dev, args, T, T_rec=0.0):
             "theta": 0.7, "T_rec": T_rec}
 
 
-def lognormal_256(S, dev, args, T):
-    """The large diffuse run at full size (opt-in): 256^3 particles in a
-    log-normal field (sigma_ln = 1.5, P(k) ~ k^-3), every particle emitting
-    plus 64 sources of 1e50/s; per theta in {0.5, 1}: SPH density recompute
-    from masses, then a full coupled step (build, walk over both trees,
-    memoised march in target chunks, Gamma, implicit update)."""
-    import numpy as np
-    import torch
-    from start_inputs import config5
-    w = config5()
-    stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream, max_pairs=1 << 29)
-    pos, h, sp, sL, V = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L), T(w.V)
-    mass = T((w.n_H.astype(np.float64) * w.V).astype(np.float32))
-    rho = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
-    y = T(w.y0)
-    g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
-    out = {"workload": w.name, "n_p": w.n_p}
-    for theta in (0.5, 1.0):
-        y.copy_(T(w.y0))
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.build_trees(pos, h, sp, sL, V, diffuse=True)
-        ctx.sph_density(mass, rho)
-        ctx.set_state(rho, y)
-        ctx.rt_solve(theta, gamma_out=g)
-        ctx.ionize(w.dt_s, y_out=y)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
-        st = ctx.stats()
-        out[f"theta_{theta}"] = {"value": st["rays"] / (ms * 1e-3), "unit": "rays/s",
-                                 "ms_per_step": ms, "rays_per_step": st["rays"],
-                                 "chunks": st["chunks"]}
-    ctx.close()
+def serving(args):
+    """Continuous batching vs one solve at a time on the same Poisson stream
+    of requests of mixed size (real-time replay, 150 GB budget), at an
+    arrival rate above one GPU's capacity and at one below it."""
+    from paper_1005_5312_gb300.serve import Server, make_requests, summarize
+    lo, hi = (float(x) for x in args.serve_log2np.split(","))
+    out = {"workers": args.serve_workers, "budget_gb": 150}
+    for key, n_req, rate in (("saturated", args.serve_requests, args.serve_rate),
+                             ("below_capacity", args.serve_low_requests, args.serve_low_rate)):
+        reqs = make_requests(n_req, rate_hz=rate, log2_np=(lo, hi))
+        res = {}
+        for name, workers in (("plain", 1), ("served", args.serve_workers)):
+            srv = Server(workers=workers, budget_bytes=150e9)
+            # warm the workers' contexts and pools on a small request
+            srv.serve(make_requests(workers, rate_hz=1e9, log2_np=(14, 14), seed=1),
+                      realtime=False)
+            r = srv.serve(reqs, realtime=True)
+            srv.close()
+            res[name] = summarize(r)
+            res[name]["context_trims"] = srv.trims
+            res[name]["oom_retries"] = srv.retries
+        n_p = [r.n_p for r in reqs]
+        out[key] = {"workload": f"{len(reqs)} requests, Poisson {rate:g}/s, "
+                                f"N_p=2^U({lo:g},{hi:g}), N_s=e^U(0,ln N_p), uniform|clumpy, "
+                                f"theta in {{0.5,1}}, 1 step each",
+                    "mean_n_p": float(np.mean(n_p)), "served": res["served"],
+                    "plain": res["plain"],
+                    "solves_per_s_vs_plain": res["served"]["solves_per_s"] /
+                    res["plain"]["solves_per_s"]}
     return out
 
 
-def serving(args):
-    """Continuous batching vs one solve at a time on the same Poisson stream
-    of requests of mixed size (real-time replay, 150 GB budget)."""
-    from paper_1005_5312_gb300.serve import Server, make_requests, summarize
-    lo, hi = (float(x) for x in args.serve_log2np.split(","))
-    reqs = make_requests(args.serve_requests, rate_hz=args.serve_rate, log2_np=(lo, hi))
-    res = {}
-    for name, workers in (("plain", 1), ("served", args.serve_workers)):
-        srv = Server(workers=workers, budget_bytes=150e9)
-        # warm the workers' contexts and pools on a small request
-        srv.serve(make_requests(workers, rate_hz=1e9, log2_np=(14, 14), seed=1), realtime=False)
-        r = srv.serve(reqs, realtime=True)
-        srv.close()
-        res[name] = summarize(r)
-        res[name]["context_trims"] = srv.trims
-        res[name]["oom_retries"] = srv.retries
-    sp = res["served"]["solves_per_s"] / res["plain"]["solves_per_s"]
-    n_p = [r.n_p for r in reqs]
-    return {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, N_p=2^U({lo:g},{hi:g}),"
-                        " N_s=e^U(0,ln N_p), uniform|clumpy, theta in {0.5,1}, 1 step each",
-            "workers": args.serve_workers, "budget_gb": 150, "mean_n_p": float(np.mean(n_p)),
-            "served": res["served"], "plain": res["plain"],
-            "solves_per_s_vs_plain": sp}
+def multisource_lines(S, dev, args, T, flush, w2, peak):
+    """The 64^3 multiple-source workload (1024 point sources): coupled full
+    steps at theta and theta2 with L2 flushed between timed steps, the
+    resident-chain steps, the method's own error and the next-row lines."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream)
+    pos, h, spos, sL = T(w2.pos), T(w2.h), T(w2.src_pos), T(w2.src_L)
+    nH, y0 = T(w2.n_H), T(w2.y0)
+    y = y0.clone()
+    g = torch.zeros(w2.n_p, dtype=torch.float32, device=dev)
+
+    def step(theta):
+        ctx.build_trees(pos, h, spos, sL)
+        ctx.set_state(nH, y)
+        ctx.rt_solve(theta, gamma_out=g)
+        ctx.ionize(w2.dt_s, y_out=y)
+
+    out = {"workload": w2.name, "n_p": w2.n_p, "n_s": w2.n_s,
+           "l2": "512 MB buffer written between timed steps"}
+    steps = max(3, args.steps)
+    for theta in (args.theta, args.theta2):
+        y.copy_(y0)
+        for _ in range(3):
+            step(theta)
+        torch.cuda.synchronize(dev)
+        ctx.timings()
+        ms, rays, evals, phases = [], [], [], {}
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(theta)
+            e1.record(stream)
+            tm = ctx.timings()
+            st = ctx.stats()
+            ms.append(e0.elapsed_time(e1))
+            rays.append(st["rays"])
+            evals.append(st["evals"])
+            for k, v in tm.items():
+                if v is not None and v >= 0:
+                    phases[k] = phases.get(k, 0.0) + v / steps
+        t = sum(ms)
+        algo = (ALGO_BYTES_PER_EVAL * sum(evals) + ALGO_BYTES_PER_RAY * sum(rays) +
+                ALGO_BYTES_PER_TARGET * w2.n_p * steps) / steps
+        out[f"theta_{theta}"] = {
+            "value": sum(rays) / (t * 1e-3), "unit": "rays/s", "ms_per_step": t / steps,
+            "rays_per_step": sum(rays) / steps, "evaluations_per_ray": sum(evals) / sum(rays),
+            "phase_ms_per_step": phases,
+            "roofline_step": {"algorithmic_bytes_per_step": algo,
+                              "achieved_GB_per_s": algo / (t / steps * 1e-3) / 1e9,
+                              "frac_of_measured_hbm": algo / (t / steps * 1e-3) / 1e9 / peak}}
+    ctx.close()
+    if not args.no_resident:
+        out["resident_steps"] = resident_steps(S, w2, dev, args, T)
+    if not args.no_method_error:
+        out["method_error"] = method_error(S, w2, dev, args, T)
+    if not args.no_next:
+        out["sph_density"] = sph_density(S, w2, dev, args, T, flush)
+        out["h2_dissociation"] = h2_dissociation(S, w2, dev, args, T, flush)
+        out["blackbody_sources"] = blackbody_sources(S, w2, dev, args, T, flush)
+    # Gamma at the neutral start, for the parity check against the oracle
+    ctx = S.Context(march_group=args.march_group, stream=stream)
+    ctx.build_trees(pos, h, spos, sL)
+    g0 = torch.zeros(w2.n_p, dtype=torch.float32, device=dev)
+    ctx.rt_solve(args.theta, n_HI=T(w2.n_HI()), gamma_out=g0)
+    g_start = g0.cpu().numpy()
+    ctx.close()
+    return out, g_start
 
 
 # ---------------------------------------------------------------- GPU arm
-def run_gpu(args, w):
-    import numpy as np
+def run_gpu(args):
     import torch
     import paper_1005_5312_gb300 as S
+    from start_inputs import config2, config5
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -536,177 +771,103 @@ def run_gpu(args, w):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     S.build()
-    stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(timing=1, march_group=args.march_group, march_mode=args.march_mode,
-                    stream=stream)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    pos, h, spos, sL = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L)
-    nH, y0 = T(w.n_H), T(w.y0)
-    y = y0.clone()
-    g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def step(theta):
-        ctx.build_trees(pos, h, spos, sL)
-        ctx.set_state(nH, y)
-        ctx.rt_solve(theta, gamma_out=g)
-        ctx.ionize(w.dt_s, y_out=y)
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    def timed(theta, steps, warmup):
-        y.copy_(y0)
-        for _ in range(warmup):
-            step(theta)
-        torch.cuda.synchronize(dev)
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        march_ms, hop_ms, rays, hops, evals, fbs = [], [], [], [], [], []
-        link_ms, jump_ms, jump_bytes, jump_rounds = [], [], [], []
-        l0 = ctx.stats()["launches"]
-        barrier()
-        t_wall = time.perf_counter()
-        for k in range(steps):
-            flush.zero_()                      # evict L2 between timed steps
-            ev0[k].record(stream)
-            step(theta)
-            ev1[k].record(stream)
-            tm = ctx.timings()
-            st = ctx.stats()
-            march_ms.append(tm["march"])
-            hop_ms.append(tm["hops"])
-            link_ms.append(tm["link"])
-            jump_ms.append(tm["jump"])
-            jump_bytes.append(st["jump_bytes"])
-            jump_rounds.append(st["jump_rounds"])
-            rays.append(st["rays"])
-            hops.append(st["hops"])
-            evals.append(st["evals"])
-            fbs.append(st["march_fallbacks"])
-        barrier()
-        t_wall = time.perf_counter() - t_wall
-        launches = ctx.stats()["launches"] - l0
-        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-        return dict(step_ms=step_ms, march_ms=march_ms, hop_ms=hop_ms, rays=rays, hops=hops,
-                    evals=evals, fbs=fbs, launches=launches, wall=t_wall, link_ms=link_ms,
-                    jump_ms=jump_ms, jump_bytes=jump_bytes, jump_rounds=jump_rounds)
-
-    with ClockSampler(local) as clk:
-        r1 = timed(args.theta, args.steps, args.warmup)
-    r2 = None if args.no_theta2 else timed(args.theta2, max(2, args.steps // 2), 1)
-
-    tot_ms, rays = reduce_over_ranks(sum(r1["step_ms"]), sum(r1["rays"]))
-    value = rays / (tot_ms * 1e-3)
-
-    # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
-    if args.march_mode == 1:
-        # memoised march: the pointer-jumping rounds (its largest share of a
-        # step); bytes and durations summed over the timed steps' rounds
-        kern = "k_memo_jump"
-        n_launch = sum(r1["jump_rounds"])
-        per_launch = sum(r1["jump_bytes"]) / n_launch
-        avg_ms = sum(r1["jump_ms"]) / n_launch
-    else:
-        kern = "k_march"
-        algo_l = [ALGO_BYTES_PER_HOP * hp + ALGO_BYTES_PER_RAY * r + ALGO_BYTES_PER_TARGET * w.n_p
-                  for r, hp in zip(r1["rays"], r1["evals"])]
-        per_launch = sum(algo_l) / len(algo_l)
-        avg_ms = sum(r1["march_ms"]) / len(r1["march_ms"])
-    achieved = per_launch / (avg_ms * 1e-3) / 1e9
-    tr = traffic_record(kern)
+
+    w = config5(nside=args.nside)
+    r1, r2, clocks, g5_start = headline(S, w, dev, args, T, local)
+
+    tot_ms, rays = reduce_over_ranks(sum(r1["step_ms"]), sum(s["rays"] for s in r1["stats"]))
+    value = rays / (tot_ms * 1e-3)
+    K = args.steps
+    step_ms = tot_ms / K
+    st_sum = {k: sum(s[k] for s in r1["stats"]) / K
+              for k in ("rays", "evals", "hops", "jump_bytes", "march_fallbacks", "chunks")}
+    last = r1["stats"][-1]
+    for k in ("nbr_total", "nodes_part", "nodes_src", "nodes_emit"):
+        st_sum[k] = last[k]
+    phase_ms = {}
+    for ph in r1["phases"]:
+        for k, v in ph.items():
+            if v is not None and v >= 0:
+                phase_ms[k] = phase_ms.get(k, 0.0) + v / K
+    # the march phase holds the walk's fill, hops, link and jump; report the
+    # fill as part of the walk
+    if "march" in phase_ms:
+        rest = phase_ms["march"] - sum(phase_ms.get(k, 0.0) for k in ("hops", "link", "jump"))
+        phase_ms["walk"] = phase_ms.get("walk", 0.0) + max(0.0, rest)
+    models = phase_models(st_sum, w.n_p, w.n_s, True, max(1, round(st_sum["chunks"])))
+    kernels = kernel_table(phase_ms, models, step_ms, peak)
+
+    # whole-step roofline: the march's algorithmic traffic per step
+    algo = (ALGO_BYTES_PER_EVAL * st_sum["evals"] + ALGO_BYTES_PER_RAY * st_sum["rays"] +
+            ALGO_BYTES_PER_TARGET * w.n_p)
+    achieved = algo / (step_ms * 1e-3) / 1e9
+    tr = traffic_record("step_" + w.name)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind,
-            "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "kernel": kern, "launch_ms": avg_ms, "algorithmic_bytes_per_launch": per_launch}
-    if args.march_mode == 1:
-        roof["launches_per_step"] = sum(r1["jump_rounds"]) / args.steps
+            "frac": achieved / peak, "peak_source": f"{peak_kind} (copy bandwidth)",
+            "traffic": tr["dram_bytes_per_step"] if tr else None,
+            "kernel": "whole step (every kernel of build, density, walk, march, Gamma, update)",
+            "launch_ms": step_ms, "algorithmic_bytes_per_launch": algo,
+            "model": "516 B per neighbour-list evaluation (32 u32 indices, 32 float3 positions, "
+                     "one float n_HI) + 16 B per ray + 8 B per target",
+            "evaluations_per_step": st_sum["evals"], "rays_per_step": st_sum["rays"]}
 
     out = {"metric": f"RT rays/s at theta_crit={args.theta}", "value": value, "unit": "rays/s",
-           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "theta": args.theta,
-                      "dt_s": w.dt_s, "march_group": args.march_group,
-                      "march": "memoised" if args.march_mode == 1 else "per-ray",
-                      "l2": "512 MB buffer written between timed steps",
-                      "step": "build_trees + set_state + rt_solve + ionize, coupled"},
-           "rays_per_step": rays / args.steps / ws,
-           "chain_links_per_ray": sum(r1["hops"]) / max(1, sum(r1["rays"])),
-           "evaluations_per_ray": sum(r1["evals"]) / max(1, sum(r1["rays"])),
-           "march_ms_per_step": sum(r1["march_ms"]) / len(r1["march_ms"]),
-           "march_fallbacks_per_step": sum(r1["fbs"]) / args.steps,
-           "memo_kernels_ms_per_step": ({
-               "hops": sum(r1["hop_ms"]) / args.steps, "link": sum(r1["link_ms"]) / args.steps,
-               "jump": sum(r1["jump_ms"]) / args.steps} if args.march_mode == 1 else None),
+           "n_gpus": ws, "steps": K, "warmup": args.warmup, "ms_per_step": step_ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "emitters": w.n_p,
+                      "theta": args.theta, "dt_s": w.dt_s, "march_group": args.march_group,
+                      "max_pairs": args.max_pairs, "march": "memoised",
+                      "l2": "no flush: every step streams inputs and buffers far larger than "
+                            "L2 (particles 16.7M x 60 B, neighbour lists 2.1 GB, chain slots "
+                            "tens of GB)",
+                      "step": "build_trees + sph_density + set_state + rt_solve + ionize, "
+                              "coupled"},
            "gpu_launches": r1["launches"],
-           "roofline": roof, "clocks": clk.summary()}
+           "rays_per_step": st_sum["rays"] / 1.0,
+           "evaluations_per_ray": st_sum["evals"] / max(1.0, st_sum["rays"]),
+           "chain_links_per_ray": st_sum["hops"] / max(1.0, st_sum["rays"]),
+           "chunks_per_step": st_sum["chunks"],
+           "march_fallbacks_per_step": st_sum["march_fallbacks"],
+           "roofline": roof, "kernels": kernels, "clocks": clocks}
     if r2 is not None:
         t2 = sum(r2["step_ms"])
-        out[f"theta_{args.theta2}"] = {"value": sum(r2["rays"]) / (t2 * 1e-3), "unit": "rays/s",
-                                       "ms_per_step": t2 / len(r2["step_ms"]),
-                                       "rays_per_step": sum(r2["rays"]) / len(r2["rays"]),
-                                       "march_ms": sum(r2["march_ms"]) / len(r2["march_ms"])}
-    phases = ctx.timings()
-    out["phase_ms_last_step"] = phases
-
-    if not args.no_resident:
-        out["resident_steps"] = resident_steps(S, w, dev, args, T)
-    if not args.no_method_error:
-        out["method_error"] = method_error(S, w, dev, args, T)
-    if not args.no_next:
-        out["sph_density"] = sph_density(S, w, dev, args, T, flush)
-        out["h2_dissociation"] = h2_dissociation(S, w, dev, args, T, flush)
-        out["blackbody_sources"] = blackbody_sources(S, w, dev, args, T, flush)
-    if not args.no_diffuse:
-        out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
-        if not args.no_next:
-            out["diffuse_128cubed_recombination_band"] = diffuse_workload(S, dev, args, T,
-                                                                           T_rec=1e4)
-    if args.lognormal256:
-        out["lognormal_256cubed"] = lognormal_256(S, dev, args, T)
-
+        out[f"theta_{args.theta2}"] = {
+            "value": sum(s["rays"] for s in r2["stats"]) / (t2 * 1e-3), "unit": "rays/s",
+            "ms_per_step": t2 / len(r2["step_ms"]), "steps": len(r2["step_ms"]),
+            "rays_per_step": sum(s["rays"] for s in r2["stats"]) / len(r2["step_ms"])}
     if not args.no_e2e:
-        # end to end through the C ABI with host buffers: H2D copies of the
-        # step's inputs and D2H of Gamma and y inside the timed region
-        hpos, hh, hsp, hsL = w.pos, w.h, w.src_pos, w.src_L
-        hnH = w.n_H
-        hy = w.y0.copy()
-        hg = np.zeros(w.n_p, np.float32)
-        ctx_h = S.Context(march_group=args.march_group, march_mode=args.march_mode)
+        out["e2e"] = headline_e2e(S, w, args)
 
-        def hstep():
-            ctx_h.build_trees(hpos, hh, hsp, hsL)
-            ctx_h.set_state(hnH, hy)
-            ctx_h.rt_solve(args.theta, gamma_out=hg)
-            ctx_h.ionize(w.dt_s, y_out=hy)
-
-        for _ in range(args.warmup):
-            hstep()
-        hy[:] = w.y0
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        e_rays = 0
-        for _ in range(args.steps):
-            hstep()
-            e_rays += ctx_h.stats()["rays"]
-        te, e_rays = reduce_over_ranks(time.perf_counter() - t0, e_rays)
-        h2d = hpos.nbytes + hh.nbytes + hsp.nbytes + hsL.nbytes + hnH.nbytes + hy.nbytes
-        d2h = hg.nbytes + hy.nbytes
-        out["e2e"] = {"value": e_rays / te, "unit": "rays/s", "h2d_bytes_per_step": h2d,
-                      "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * te / args.steps}
-        ctx_h.close()
-
-    if ws == 1 and not args.no_serve:
-        out["serving"] = serving(args)
+    parity = {}
+    g2_start = None
+    if not args.no_extras:
+        w2 = config2()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        out["multisource_64cubed"], g2_start = multisource_lines(S, dev, args, T, flush, w2, peak)
+        if not args.no_diffuse:
+            out["diffuse_128cubed"] = diffuse_workload(S, dev, args, T)
+            if not args.no_next:
+                out["diffuse_128cubed_recombination_band"] = diffuse_workload(S, dev, args, T,
+                                                                               T_rec=1e4)
+        if ws == 1 and not args.no_serve:
+            out["serving"] = serving(args)
 
     if rank == 0 and ws == 1 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(w, args.theta, args.cpu_seconds)
-    ctx.close()
+        g_abs = 1e-8 / (w.params["sigma_cm2"] * w.dt_s)
+        idx, ref, orays, osec, cores = oracle_sample(w, args.theta, args.cpu_seconds)
+        out["cpu_baseline"] = {
+            "value": orays / osec, "unit": "rays/s", "cores": cores, "kind": "oracle",
+            "sample": f"Gamma at {len(idx)} random targets of {w.n_p} (theta={args.theta}, "
+                      f"starting state, all emitters and point sources): {orays} rays in "
+                      f"{osec:.1f} s"}
+        parity[f"{w.name}_theta{args.theta}"] = rel_errors(g5_start[idx], ref, g_abs)
+        if g2_start is not None:
+            idx2, ref2, _, _, _ = oracle_sample(w2, args.theta, 10.0)
+            parity[f"{w2.name}_theta{args.theta}"] = rel_errors(g2_start[idx2], ref2, g_abs)
+        out["parity"] = parity
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -715,9 +876,7 @@ def run_gpu(args, w):
 
 def main():
     args = parse()
-    from start_inputs import config2
-    w = config2(nside=args.nside)
-    res = run_reference(args, w) if args.impl == "reference" else run_gpu(args, w)
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:
         print(json.dumps(res), flush=True)
 
