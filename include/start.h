@@ -138,6 +138,9 @@ typedef struct start_params {
                               photoheating of the recombination photons (Eqs.
                               gself, gother) joins start_get_heating.  Uses the
                               memoised march */
+    int row_warps;         /* tile shape of the memoised march's first hop: target
+                              rows per thread block, 4 or 8 (0 = 8); does not
+                              change any result */
 } start_params;
 
 /* Counters of the last start_rt_solve. */

@@ -39,7 +39,7 @@ class StartParams(C.Structure):
                 ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("max_pairs", C.c_longlong),
                 ("spin_cap", C.c_longlong),
                 ("stream", C.c_void_p),
-                ("T_eff", C.c_double), ("T_rec", C.c_double)]
+                ("T_eff", C.c_double), ("T_rec", C.c_double), ("row_warps", C.c_int)]
 
 
 class StartStats(C.Structure):

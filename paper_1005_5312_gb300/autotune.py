@@ -1,12 +1,15 @@
 """Autotuner of the knobs that do not change any result.
 
 * ``ptree_leaf``  -- particle-tree leaf size (neighbour search),
-* ``march_group`` -- lanes cooperating on one neighbour-list evaluation,
-* ``max_pairs``   -- interaction pairs per target chunk (memory / sharing).
+* ``march_group`` -- lanes cooperating on one neighbour-list evaluation of
+  the later chain levels (the warp-per-target grouping of the march),
+* ``row_warps``   -- the first hop's tile shape: target rows per block.
 
 Each knob is varied in turn around the current best (coordinate descent),
 timing one full step (build + solve) per candidate with CUDA events, and the
-fastest setting is kept.  Results are cached per problem class (powers of
+fastest setting is kept.  The memory bound of a solve (max_pairs) is not a
+knob here: it decides how a large solve is split, which regroups Gamma's
+additions.  Results are cached per problem class (powers of
 two of N_p and N_s, theta, diffuse), so a server tunes a class once.  The
 source-tree leaf size is *not* tuned: it changes the method's result (one
 source per cell is the paper's choice).
@@ -18,9 +21,9 @@ import math
 SEARCH_SPACE = {
     "march_group": (1, 2, 4, 8),
     "ptree_leaf": (8, 16, 32),
-    "max_pairs": (1 << 26, 1 << 27, 1 << 28),
+    "row_warps": (4, 8),
 }
-DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "max_pairs": 1 << 27}
+DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "row_warps": 8}
 
 
 def problem_class(n_p: int, n_s: int, theta: float, diffuse: bool = False) -> tuple:

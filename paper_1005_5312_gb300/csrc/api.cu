@@ -324,7 +324,7 @@ static void release_all(start_ctx *c)
                    &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord, &c->m_nx0, &c->m_dl,
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_hard, &c->m_part, &c->m_table,
-                   &c->w_scratch, &c->w_over, &c->ctr_save};
+                   &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);
@@ -369,6 +369,7 @@ int start_default_params(start_params *p)
     p->ptree_leaf = 16;
     p->march_group = 2;
     p->march_mode = 1;
+    p->row_warps = 8;
     p->sigma_cm2 = 6.3e-18;
     p->len_unit_cm = 3.0857e21;
     p->L_unit = 1e48;
@@ -391,6 +392,8 @@ static int check_params(start_params &d)
         return START_EINVAL;
     if (d.march_group == 0) d.march_group = 2;
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
+    if (d.row_warps != 0 && d.row_warps != 4 && d.row_warps != 8) return START_EINVAL;
+    if (d.row_warps == 0) d.row_warps = 8;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
     if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;
     if (!(d.T_rec == 0.0 || (d.T_rec >= 100.0 && d.T_rec <= 1e5))) return START_EINVAL;

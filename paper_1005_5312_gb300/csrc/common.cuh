@@ -141,6 +141,12 @@ struct start_ctx {
     st::DBuf pord;    // u32 order key per pair (tree tag, node of the entry)
     st::DBuf pcon;    // float contribution per pair
     long long npairs = 0;
+    // a memoised solve split into groups of virtual sources (depth-first
+    // index ranges of the source and emitter trees): the ranges the walks of
+    // the current group emit (full otherwise), the sampled histogram the
+    // groups are planned from, and every target's running Gamma sums
+    unsigned grp_s[2] = {0u, 0xffffffffu}, grp_e[2] = {0u, 0xffffffffu};
+    st::DBuf g_hist, gacc;
 
     // memoised march: per chain link (virtual source, particle)
     st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_hard, m_part, m_table, m_nx0, m_dl;
@@ -198,6 +204,7 @@ enum Counter {
     C_JUMP_EXTRA, // pointer jumping: successor reads beyond the first in a round
     C_WALK_OVER,  // one-walk lists: targets whose row exceeds the scratch row
     C_LEVEL,      // memoised march: device frontier {fbase, nf, total} (3 words)
+    C_WALK_FB_GROUP = C_LEVEL + 3,   // opening tests re-decided by the walks of a group
     C_COUNT = 24
 };
 

@@ -28,6 +28,8 @@
 // share one chain forest.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "march.cuh"
 
@@ -275,7 +277,6 @@ __device__ __forceinline__ u32 find_in_row(const MemoArgs &a, u32 k, u32 vid, u3
 // read from global memory), which keeps this kernel small.  The walk wrote
 // the pair slots' virtual source, particle and order key.
 constexpr int kRowNB = 64;      // staged neighbours per target
-constexpr int kRowWarps = 8;    // targets per block
 
 // Appends the flagged lanes' (slot, target) to a list with one counter
 // update per warp; every lane of the warp calls it.
@@ -292,12 +293,15 @@ __device__ __forceinline__ void warp_append(bool flag, u32 slot, u32 tgt, uint2 
     if (flag) list[b + __popc(m & ((1u << lane) - 1u))] = make_uint2(slot, tgt);
 }
 
-__global__ void __launch_bounds__(32 * kRowWarps, 5) k_memo_hop_rows(MemoArgs a)
+// W target rows per block (the tile shape; 8 KB of stage per row): 40 warps
+// per SM either way.
+template <int W>
+__global__ void __launch_bounds__(32 * W, 40 / W) k_memo_hop_rows(MemoArgs a)
 {
-    __shared__ float4 nba[kRowWarps][kRowNB];   // (r_k - r_j, rsqrt |r_k - r_j|^2)
-    __shared__ float4 nbb[kRowWarps][kRowNB];   // (|r_k - r_j|^2, e1, e0, -): bound e1 |b| + e0
-    __shared__ float4 nbp[kRowWarps][kRowNB];   // record of k
-    __shared__ uint4 nbr[kRowWarps][kRowNB];    // (k, row start, row end, -), slot indices
+    __shared__ float4 nba[W][kRowNB];   // (r_k - r_j, rsqrt |r_k - r_j|^2)
+    __shared__ float4 nbb[W][kRowNB];   // (|r_k - r_j|^2, e1, e0, -): bound e1 |b| + e0
+    __shared__ float4 nbp[W][kRowNB];   // record of k
+    __shared__ uint4 nbr[W][kRowNB];    // (k, row start, row end, -), slot indices
     const float two_eps = 32.f * kU32;
     const float eps_q = 16.f * kU32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -842,11 +846,16 @@ __device__ __forceinline__ float spec_lookup(const float *tab, float sidx)
 // fixed butterfly and the chunks are accumulated in list order with
 // compensation -- a deterministic order, so a target's Gamma does not depend
 // on which other targets share its chains.
+// A solve split into groups of virtual sources visits every target once per
+// group, the groups in row order: acc carries each target's compensated sums
+// (sum, compensation, heating sum, its compensation) from one group to the
+// next; the first group starts from zero and the last one writes Gamma.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, long long t0,
                                                      long long t1, u64 base, float conv,
                                                      const u32 *porig, float *gam, float *gout,
-                                                     GammaExtra x)
+                                                     GammaExtra x, float4 *acc, int first,
+                                                     int last)
 {
     const int lane = threadIdx.x & 31;
     long long i = t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -856,6 +865,13 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
         u64 e0 = off[i] - base, e1 = off[i + 1] - base;
         float4 pt = a.m.pq[i];
         float sum = 0.f, cmp = 0.f, hsum = 0.f, hcmp = 0.f;
+        if (!first) {
+            const float4 q = acc[i];
+            sum = q.x;
+            cmp = q.y;
+            hsum = q.z;
+            hcmp = q.w;
+        }
         for (u64 e = e0; e < e1; e += 32) {
             u64 p = e + lane;
             float v = 0.f, hv = 0.f;
@@ -897,7 +913,9 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
                 hsum = ht;
             }
         }
-        if (lane == 0) {
+        if (lane == 0 && !last) {
+            acc[i] = make_float4(sum, cmp, hsum, hcmp);
+        } else if (lane == 0) {
             float g = sum * conv;
             if (MODE != 1) gam[i] = g;
             if (MODE == 2) x.heat[i] = hsum * x.heat_conv;
@@ -1003,8 +1021,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     ev(0);
     {
         long long rows = t1 - t0;
-        k_memo_hop_rows<<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0, s>>>(
-            a);
+        if (c->p.row_warps == 4)
+            k_memo_hop_rows<4><<<(unsigned)((rows + 3) / 4), 128, 0, s>>>(a);
+        else
+            k_memo_hop_rows<8><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(a);
         k_memo_hop_hard<<<(unsigned)(nsm * 4), 256, 0, s>>>(a);
     }
     ev(1);
@@ -1167,10 +1187,19 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     return START_OK;
 }
 
-// Gamma of targets [t0, t1) from the chain sums of the last run_memo.
+// Gamma of targets [t0, t1) from the chain sums of the last run_memo; first
+// / last: the group's place in a solve split into groups of virtual sources
+// (both set when it is not split).
 int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base,
-               float conv, float *gout)
+               float conv, float *gout, bool first, bool last)
 {
+    float4 *acc = nullptr;
+    if (!(first && last)) {
+        if (ensure(c->gacc, (size_t)(c->np ? c->np : 1) * sizeof(float4)))
+            return set_err(c, START_ENOMEM, "out of device memory (Gamma sums)");
+        acc = c->gacc.as<float4>();
+    }
+    const int f = first ? 1 : 0, l = last ? 1 : 0;
     MemoArgs a;
     a.m = m;
     a.dlv = nullptr;
@@ -1198,11 +1227,14 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     const u32 *po = c->porig.as<u32>();
     float *gm = c->gam.as<float>();
     if (c->solve_kind == 1)
-        k_memo_gamma<1><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x);
+        k_memo_gamma<1><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x,
+                                                     acc, f, l);
     else if (spec)
-        k_memo_gamma<2><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x);
+        k_memo_gamma<2><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x,
+                                                     acc, f, l);
     else
-        k_memo_gamma<0><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x);
+        k_memo_gamma<0><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x,
+                                                     acc, f, l);
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_memo_gamma");
 }
@@ -1226,16 +1258,19 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     unsigned long long *saved = c->ctr_save.as<unsigned long long>();
     ST_CUDA(c, cudaMemcpyAsync(saved, ctr, C_COUNT * sizeof(unsigned long long),
                                cudaMemcpyDeviceToDevice, c->stream));
-    for (int attempt = 0; attempt < 4; ++attempt) {
+    // slot ids and table indices must stay below the pending flag (2^31)
+    const size_t cap_max = (1ull << 30) - 1;
+    if ((size_t)m.npairs >= cap_max) return set_err(c, START_ERANGE, "too many chain links");
+    cap = std::min(cap, cap_max);
+    for (int attempt = 0; attempt < 5; ++attempt) {
         if (attempt > 0)
             ST_CUDA(c, cudaMemcpyAsync(ctr, saved, C_COUNT * sizeof(unsigned long long),
                                        cudaMemcpyDeviceToDevice, c->stream));
-        // slot ids and table indices must stay below the pending flag (2^31)
-        if (cap >= (1ull << 30)) return set_err(c, START_ERANGE, "too many chain links");
         bool overflow = false;
         ST_TRY(memo_attempt(c, m, theta, cap, overflow, t0, t1, base));
         if (!overflow) return START_OK;
-        cap *= 2;
+        if (cap == cap_max) break;
+        cap = std::min(cap + cap / 2, cap_max);
     }
     return set_err(c, START_ENOMEM, "memoised march: slot capacity");
 }

@@ -23,15 +23,20 @@ namespace st {
 int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long long t1,
              u64 base);
 int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64 base,
-               float conv, float *gout);
+               float conv, float *gout, bool first, bool last);
 
 
 // ---------------------------------------------------------------- walk
+// A tree as the walk sees it.  [lo, hi) restricts the entries a walk emits
+// to the cells (or leaves, for members) with depth-first index in that range:
+// the part of every row that belongs to one group of virtual sources.  Rows
+// are sorted by that index, so a group's part of a row is contiguous.
 struct TreeView {
     const float4 *box;
     const uint4 *meta;
     const double *cube;
     u32 n;
+    u32 lo = 0, hi = 0xffffffffu;
 };
 
 // Canonical virtual-source ids (the memoised march's numbering): source-tree
@@ -108,29 +113,35 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
 {
     constexpr bool FILL = MODE != 0;
     const u32 okey = tag ? 0x80000000u : 0u;
+    const u32 end = t.hi < t.n ? t.hi : t.n;   // depth-first order: nothing past hi is emitted
     u32 n = 0;
-    while (n < t.n) {
-        float4 b = t.box[n];
+    while (n < end) {
         uint4 mt = t.meta[n];
+        if (mt.x <= t.lo) {   // the whole subtree lies before the range
+            n = mt.x;
+            continue;
+        }
+        float4 b = t.box[n];
         int a = accept_32(b, th2f, p.x, p.y, p.z, cmag);
         if (a < 0) {
             a = accept_64(t.cube + 4 * (size_t)n, th2d, p.x, p.y, p.z) ? 1 : 0;
             ++fb;
         }
+        const bool in = n >= t.lo;
         if (a) {
-            if (FILL) {
+            if (in && FILL) {
                 if (w < wend) {   // never past this row
                     u32 e = (MODE >= 2) ? ((mt.w && mt.z == 1u) ? cb.memb0 + mt.y : cb.node0 + n)
                                         : (n | tag);
                     rows.put(w, e, okey | n);
                 }
                 ++w;
-            } else {
+            } else if (in) {
                 ++c;
             }
             n = mt.x;
         } else if (mt.w) {
-            for (u32 r = mt.y; r < mt.y + mt.z; ++r) {
+            for (u32 r = mt.y; in && r < mt.y + mt.z; ++r) {
                 if (r == self) continue;
                 if (FILL) {
                     if (w < wend)
@@ -583,16 +594,18 @@ static int ensure_pairs(start_ctx *c, unsigned long long n)
     return START_OK;
 }
 
+// The trees as the walks of the current solve see them: restricted to the
+// current group of virtual sources while a grouped solve runs.
 static TreeView source_view(start_ctx *c)
 {
     return TreeView{c->stree.box.as<float4>(), c->stree.meta.as<uint4>(),
-                    c->stree.cube.as<double>(), (u32)c->stree.n};
+                    c->stree.cube.as<double>(), (u32)c->stree.n, c->grp_s[0], c->grp_s[1]};
 }
 
 static TreeView emitter_view(start_ctx *c)
 {
     return TreeView{c->et.box.as<float4>(), c->et.meta.as<uint4>(), c->et.cube.as<double>(),
-                    (u32)(c->walk_emit ? c->et.n : 0)};
+                    (u32)(c->walk_emit ? c->et.n : 0), c->grp_e[0], c->grp_e[1]};
 }
 
 // Interaction lists of every target (all pairs at once; introspection).
@@ -709,8 +722,188 @@ __global__ void k_set_evals(unsigned long long *ctr, unsigned long long evals,
     ctr[1] = links;
 }
 
+// ---------------------------------------------------------------- groups
+// A memoised solve with more interaction pairs than max_pairs is split by
+// virtual source, not by target: each group is a range of depth-first cell
+// indices (the source tree's cells, then the emitter tree's), every target's
+// row is walked restricted to it (a contiguous part of the row, since rows
+// are sorted by that index), and the march runs over all targets at once.
+// Every chain link (v, k) of the group's sources then finds the pair (v, k)
+// whenever k's walk lists v, so only the method's own boundary links leave
+// the lists -- splitting by target would cut every chain at the edge of the
+// target range.  Groups are planned from a histogram of the pairs over
+// kGroupBins equal ranges of cell index, taken on every kGroupStride-th
+// target; each group's exact count comes from its own counting walk, and a
+// group that exceeds the plan by half is halved.
+constexpr int kGroupBins = 2048;
+constexpr int kGroupStride = 4;
+
+struct HistRows {
+    u32 *bins;
+    u32 SN;                     // cells of the source tree
+    unsigned long long NT;      // cells of both trees
+    int cur = -1;
+    u32 run = 0;
+    __device__ __forceinline__ void put(u64, u32, u32 key)
+    {
+        const unsigned long long pos =
+            (key & 0x80000000u) ? SN + (unsigned long long)(key & 0x7fffffffu) : key;
+        const int b = (int)(pos * kGroupBins / NT);
+        if (b != cur) {
+            if (run) atomicAdd(&bins[cur], run);
+            cur = b;
+            run = 0;
+        }
+        ++run;
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (run) atomicAdd(&bins[cur], run);
+        run = 0;
+    }
+};
+
+__global__ void __launch_bounds__(128) k_walk_hist(const float4 *pq, long long np, TreeView st_,
+                                                   TreeView et_, float th2f, double th2d,
+                                                   float cmag, u32 SN, unsigned long long NT,
+                                                   unsigned long long *hist)
+{
+    __shared__ u32 bins[kGroupBins];
+    for (int k = threadIdx.x; k < kGroupBins; k += blockDim.x) bins[k] = 0u;
+    __syncthreads();
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kGroupStride;
+    if (i < np) {
+        const float4 p = pq[i];
+        u32 c = 0;
+        u64 w = 0;
+        unsigned fb = 0;
+        HistRows rows{bins, SN, NT};
+        walk_tree<1>(st_, p, th2f, th2d, cmag, kNone, 0u, CanonBase{}, c, w, ~0ull, rows, fb);
+        walk_tree<1>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, CanonBase{}, c, w, ~0ull, rows,
+                     fb);
+        rows.flush();
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kGroupBins; k += blockDim.x)
+        if (bins[k]) atomicAdd(&hist[k], (unsigned long long)bins[k]);
+}
+
+// Restores the full trees for the walks when a grouped solve ends (also on
+// an error return).
+struct GroupViews {
+    start_ctx *c;
+    ~GroupViews()
+    {
+        c->grp_s[0] = c->grp_e[0] = 0u;
+        c->grp_s[1] = c->grp_e[1] = 0xffffffffu;
+    }
+};
+
+// Sampled pair histogram over the cell index ranges (kGroupBins values).
+static int group_histogram(start_ctx *c, float theta, std::vector<unsigned long long> &h)
+{
+    const u32 SN = (u32)c->stree.n, EN = (u32)(c->walk_emit ? c->et.n : 0);
+    h.assign(kGroupBins, 0ull);
+    if (SN + EN == 0) return START_OK;
+    ST_TRY(ensure(c->g_hist, kGroupBins * sizeof(unsigned long long)));
+    unsigned long long *d = c->g_hist.as<unsigned long long>();
+    ST_CUDA(c, cudaMemsetAsync(d, 0, kGroupBins * sizeof(unsigned long long), c->stream));
+    const long long ns = (c->np + kGroupStride - 1) / kGroupStride;
+    k_walk_hist<<<grid_for(ns, 128), 128, 0, c->stream>>>(
+        c->pq.as<float4>(), c->np, source_view(c), emitter_view(c), theta * theta,
+        (double)theta * (double)theta, c->fr.cmag, SN, (unsigned long long)SN + EN, d);
+    ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    ST_CUDA(c, cudaMemcpyAsync(h.data(), d, kGroupBins * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, c->stream));
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    return START_OK;
+}
+
+// The grouped memoised solve (see above): per group a counting walk and its
+// scan, the march over every target, and Gamma carried from group to group.
+static int run_grouped(start_ctx *c, float theta, float *gout_dev, long long maxp, float conv,
+                       std::vector<unsigned long long> &h)
+{
+    const long long np = c->np;
+    cudaStream_t s = c->stream;
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    if (h.empty()) ST_TRY(group_histogram(c, theta, h));
+    const unsigned long long SN = (unsigned long long)c->stree.n;
+    const unsigned long long NT = SN + (unsigned long long)(c->walk_emit ? c->et.n : 0);
+    // bins [b0, b1) of each group, about 0.8 max_pairs each by the sample
+    std::vector<std::pair<int, int>> groups;
+    {
+        const double target = 0.8 * (double)maxp / kGroupStride;
+        int b0 = 0;
+        double acc = 0.0;
+        for (int b = 0; b < kGroupBins; ++b) {
+            if (acc > 0.0 && acc + (double)h[b] > target) {
+                groups.push_back({b0, b});
+                b0 = b;
+                acc = 0.0;
+            }
+            acc += (double)h[b];
+        }
+        groups.push_back({b0, kGroupBins});
+    }
+    auto pos_of = [&](int b) -> unsigned long long {   // first cell index of bin b
+        return ((unsigned long long)b * NT + kGroupBins - 1) / kGroupBins;
+    };
+    GroupViews restore{c};
+    c->walk_scratch = false;
+    c->npairs = 0;
+    c->chunks = 0;
+    ST_TRY(ensure(c->lcount, np * sizeof(u32)));
+    ST_TRY(ensure(c->loff, (np + 1) * sizeof(u64)));
+    for (size_t q = 0; q < groups.size(); ++q) {
+        const unsigned long long P0 = pos_of(groups[q].first), P1 = pos_of(groups[q].second);
+        c->grp_s[0] = (u32)std::min(P0, SN);
+        c->grp_s[1] = (u32)std::min(P1, SN);
+        c->grp_e[0] = (u32)(std::max(P0, SN) - SN);
+        c->grp_e[1] = (u32)(std::max(P1, SN) - SN);
+        phase_mark(c, START_PHASE_WALK, false);
+        k_walk<0><<<grid_for(np, 128), 128, 0, s>>>(
+            c->pq.as<float4>(), 0, np, source_view(c), emitter_view(c), CanonBase{}, CanonBase{},
+            theta * theta, (double)theta * (double)theta, c->fr.cmag, c->lcount.as<u32>(),
+            nullptr, 0ull, nullptr, nullptr, nullptr, ctr + C_WALK_FB_GROUP, nullptr, 0, 0,
+            nullptr, nullptr);
+        ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+        ST_TRY(exclusive_scan_u32_to_u64(c, c->lcount.as<u32>(), c->loff.as<u64>(), np));
+        unsigned long long total = 0;
+        ST_CUDA(c, cudaMemcpyAsync(&total, c->loff.as<u64>() + np, sizeof(total),
+                                   cudaMemcpyDeviceToHost, s));
+        ST_CUDA(c, cudaStreamSynchronize(s));
+        phase_mark(c, START_PHASE_WALK, true);
+        if ((double)total > 1.5 * (double)maxp && groups[q].second - groups[q].first > 1) {
+            const int mid = (groups[q].first + groups[q].second) / 2;
+            groups.insert(groups.begin() + q + 1, {mid, groups[q].second});
+            groups[q].second = mid;
+            --q;
+            continue;
+        }
+        c->npairs += (long long)total;
+        MarchArgs a = march_args(c, (long long)total);
+        if (total > 0) {
+            phase_mark(c, START_PHASE_MARCH, false);
+            ST_TRY(run_memo(c, a, theta, 0, np, 0ull));
+            phase_mark(c, START_PHASE_MARCH, true);
+        }
+        phase_mark(c, START_PHASE_GAMMA, false);
+        ST_TRY(memo_gamma(c, a, 0, np, 0ull, conv, gout_dev, q == 0, q + 1 == groups.size()));
+        phase_mark(c, START_PHASE_GAMMA, true);
+        ++c->chunks;
+    }
+    return START_OK;
+}
+
+static int finish_solve(start_ctx *c, bool memo, bool spec);
+
 // Targets are processed in Morton-contiguous chunks of at most max_pairs
-// interaction pairs; each chunk is walked, marched and reduced on its own.
+// interaction pairs; each chunk is walked, marched and reduced on its own
+// (the memoised march splits a larger solve by virtual source instead:
+// run_grouped).
 int run_solve(start_ctx *c, float theta, float *gout_dev)
 {
     long long np = c->np;
@@ -734,12 +927,35 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     c->walk_emit = c->diffuse && !kdis;               // LW photons come from point sources
     if (np == 0) return START_OK;
     if (c->walk_emit) ST_TRY(refresh_emitters(c));
+    // L / L_unit / (4 pi r^2), r in length units -> photons cm^-2 s^-1; for
+    // k_dis times 1.13e8 kappa_LW (Eq. H2ss)
+    double conv_d = c->p.L_unit / (c->p.len_unit_cm * c->p.len_unit_cm);
+    if (kdis) conv_d *= 1.13e8 * c->kappa_LW;
+    const float conv = (float)conv_d;
+    const long long maxp = c->p.max_pairs > 0 ? c->p.max_pairs : (1LL << 27);
     TreeView sv = source_view(c), ev = emitter_view(c);
     phase_mark(c, START_PHASE_WALK, false);
+    std::vector<unsigned long long> hist;
+    bool grouped = false;
     unsigned long long total = 0;
-    ST_TRY(walk_count(c, theta, sv, ev, &total, memo));
-    c->npairs = (long long)total;
-    long long maxp = c->p.max_pairs > 0 ? c->p.max_pairs : (1LL << 27);
+    if (memo && (size_t)np * kWalkRow * sizeof(u32) > kWalkScratchMax) {
+        // a large problem: the sampled histogram first; a solve that clearly
+        // needs groups skips the counting walk over every target
+        ST_TRY(group_histogram(c, theta, hist));
+        double est = 0.0;
+        for (unsigned long long v : hist) est += (double)v * kGroupStride;
+        grouped = est > 1.25 * (double)maxp;
+    }
+    if (!grouped) {
+        ST_TRY(walk_count(c, theta, sv, ev, &total, memo));
+        c->npairs = (long long)total;
+        grouped = memo && (long long)total > maxp;
+    }
+    if (grouped) {
+        phase_mark(c, START_PHASE_WALK, true);
+        ST_TRY(run_grouped(c, theta, gout_dev, maxp, conv, hist));
+        return finish_solve(c, memo, spec);
+    }
     std::vector<long long> cut;      // chunk boundaries (targets)
     cut.push_back(0);
     if ((long long)total > maxp) {
@@ -781,11 +997,6 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     }
     phase_mark(c, START_PHASE_WALK, true);
     c->chunks = (long long)cut.size() - 1;
-    // L / L_unit / (4 pi r^2), r in length units -> photons cm^-2 s^-1; for
-    // k_dis times 1.13e8 kappa_LW (Eq. H2ss)
-    double conv_d = c->p.L_unit / (c->p.len_unit_cm * c->p.len_unit_cm);
-    if (kdis) conv_d *= 1.13e8 * c->kappa_LW;
-    float conv = (float)conv_d;
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
         long long t0 = cut[k], t1 = cut[k + 1];
         u64 base = cut.size() > 2 ? offh[t0] : 0ull;
@@ -815,7 +1026,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         }
         phase_mark(c, START_PHASE_GAMMA, false);
         if (memo && n > 0) {
-            ST_TRY(memo_gamma(c, a, t0, t1, base, conv, gout_dev));
+            ST_TRY(memo_gamma(c, a, t0, t1, base, conv, gout_dev, true, true));
         } else {
             k_gamma<<<grid_for(t1 - t0, 256), 256, 0, s>>>(c->pcon.as<float>(), c->loff.as<u64>(),
                                                            t0, t1, base, conv, c->porig.as<u32>(),
@@ -825,6 +1036,15 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         phase_mark(c, START_PHASE_GAMMA, true);
         ST_CUDA(c, cudaGetLastError());
     }
+    return finish_solve(c, memo, spec);
+}
+
+// The self photoheating of the recombination band and the evaluation counts,
+// after the chunks or groups of a solve.
+static int finish_solve(start_ctx *c, bool memo, bool spec)
+{
+    const long long np = c->np;
+    cudaStream_t s = c->stream;
     if (spec && c->walk_emit && c->p.T_rec > 0.0) {   // Eq. gself
         k_self_heat<<<grid_for(np, 256), 256, 0, s>>>(
             c->heat.as<float>(), c->y.as<double>(), c->nH.as<float>(), c->V.as<double>(), np,

@@ -127,9 +127,7 @@ class Server:
 
     def _run(self, ctx, req: SolveRequest):
         if self.tuner is not None:
-            knobs = self.tuner.params_for(req.n_p, req.n_s, req.theta)
-            knobs["max_pairs"] = min(knobs["max_pairs"], self.max_pairs)
-            ctx.set_params(**knobs)
+            ctx.set_params(**self.tuner.params_for(req.n_p, req.n_s, req.theta))
         ctx.build_trees(req.pos, req.h, req.src_pos, req.src_L)
         y = np.ascontiguousarray(req.y0, dtype=np.float64).copy()
         g = np.zeros(req.n_p, np.float32)

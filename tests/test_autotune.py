@@ -8,7 +8,7 @@ from paper_1005_5312_gb300.autotune import (DEFAULTS, SEARCH_SPACE, Tuner, coord
 
 
 def test_coordinate_descent_finds_the_separable_minimum():
-    target = {"march_group": 4, "ptree_leaf": 32, "max_pairs": 1 << 26}
+    target = {"march_group": 4, "ptree_leaf": 32, "row_warps": 4}
     calls = []
 
     def cost(p):
@@ -43,7 +43,7 @@ def test_tuned_knobs_are_result_neutral():
     best = tuner.tune(w.pos, w.h, w.src_pos, w.src_L, 0.5, nHI, repeats=1)
     assert set(best) == set(DEFAULTS)
     out = []
-    for p in (DEFAULTS, best, {"march_group": 8, "ptree_leaf": 8, "max_pairs": 4096}):
+    for p in (DEFAULTS, best, {"march_group": 8, "ptree_leaf": 8, "row_warps": 4}):
         ctx = S.Context(**p)
         ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
         g = np.zeros(w.n_p, np.float32)

@@ -254,9 +254,12 @@ def test_one_walk_lists_match_the_per_ray_path(S, theta, max_pairs):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-def test_target_chunks_are_result_neutral(S, cfg1, mode):
-    """Chunking the targets changes which chains are shared, never a chain:
-    Gamma is bitwise the same."""
+def test_split_solves_are_result_neutral(S, cfg1, mode):
+    """A solve larger than max_pairs is split: the per-ray march into chunks
+    of targets (Gamma bitwise the same), the memoised march into groups of
+    virtual sources, which share every chain link and leave only the
+    method's boundary links outside the lists (the same rays, chain links and
+    evaluations as one piece; Gamma's additions grouped differently)."""
     nHI = cfg1.n_HI()
     out = []
     for max_pairs in (0, 20000):
@@ -265,9 +268,51 @@ def test_target_chunks_are_result_neutral(S, cfg1, mode):
         g = np.zeros(cfg1.n_p, np.float32)
         ctx.rt_solve(0.5, n_HI=nHI, gamma_out=g)
         out.append((g, ctx.stats()))
-    assert out[0][1]["chunks"] == 1 and out[1][1]["chunks"] > 10
-    assert out[0][1]["rays"] == out[1][1]["rays"] and out[0][1]["hops"] == out[1][1]["hops"]
-    assert np.array_equal(out[0][0], out[1][0])
+    (g0, s0), (g1, s1) = out
+    assert s0["chunks"] == 1 and s1["chunks"] > 10
+    assert s0["rays"] == s1["rays"] and s0["hops"] == s1["hops"]
+    if mode == 0:
+        assert np.array_equal(g0, g1)
+    else:
+        assert s0["evals"] == s1["evals"]
+        assert np.all(np.abs(g1.astype(np.float64) - g0) <= 2e-5 * np.abs(g0) + G_ABS)
+        ctx = S.Context(march_mode=1, max_pairs=20000)      # deterministic
+        ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
+        g2 = np.zeros(cfg1.n_p, np.float32)
+        ctx.rt_solve(0.5, n_HI=nHI, gamma_out=g2)
+        assert np.array_equal(g1, g2)
+
+
+def test_grouped_diffuse_band_and_h2_match_one_piece(S):
+    """Groups of virtual sources over both trees (point sources and
+    emitters), with the recombination band and its photoheating carried from
+    group to group, and the H2 column solve: the same rays, links and
+    evaluations as one piece, results within the summation-order tolerance;
+    the oracle on sampled targets."""
+    w = random_workload(6001, 9, 14, diffuse=True)
+    out = {}
+    for max_pairs in (0, 40000):
+        ctx = S.Context(max_pairs=max_pairs, T_rec=1e4, T_eff=5e4, ptree_leaf=PTREE_LEAF)
+        ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L, w.V, diffuse=True)
+        ctx.set_state(w.n_H, w.y0)
+        g = np.zeros(w.n_p, np.float32)
+        ctx.rt_solve(0.6, gamma_out=g)
+        st = ctx.stats()
+        heat = ctx.heating()
+        k = np.zeros(w.n_p, np.float32)
+        ctx.h2_dissociation(np.full(w.n_p, 1e-4, np.float32), 0.6, 1e-21, k)
+        out[max_pairs] = (g.astype(np.float64), heat.astype(np.float64), k.astype(np.float64), st)
+    (g0, h0, k0, s0), (g1, h1, k1, s1) = out[0], out[40000]
+    assert s0["chunks"] == 1 and s1["chunks"] > 3
+    assert s0["rays"] == s1["rays"] and s0["hops"] == s1["hops"] and s0["evals"] == s1["evals"]
+    assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
+    assert np.all(np.abs(h1 - h0) <= 2e-5 * np.abs(h0) + 1e-30)
+    assert np.all(np.abs(k1 - k0) <= 2e-5 * np.abs(k0) + 1e-30)
+    orc = oracle.Oracle.from_workload(w, ptree_leaf=PTREE_LEAF, T_rec=1e4)
+    orc.set_emitters(w.y0, w.n_H)
+    idx = np.arange(0, w.n_p, 397)
+    gr, hr = orc.gamma_spectral(w.n_HI(), 0.6, 5e4, targets=idx)
+    gamma_close(g1[idx], gr)
 
 
 def test_resident_chains_reproduce_full_solves(S, cfg1):
