@@ -841,16 +841,17 @@ __device__ __forceinline__ float spec_lookup(const float *tab, float sidx)
     return expf(lo + f * (hi - lo));
 }
 
-// Gamma of every target from its pairs' chain sums, one warp per target:
-// each lane evaluates one pair of a 32-pair chunk, the chunk is summed by a
-// fixed butterfly and the chunks are accumulated in list order with
-// compensation -- a deterministic order, so a target's Gamma does not depend
-// on which other targets share its chains.
+// Gamma of every target from its pairs' chain sums, LANES lanes per target
+// (a warp for a whole row; eight for the short rows of one group of virtual
+// sources): each lane evaluates one pair of a LANES-pair chunk, the chunk is
+// summed by a fixed butterfly and the chunks are accumulated in list order
+// with compensation -- a deterministic order, so a target's Gamma does not
+// depend on which other targets share its chains.
 // A solve split into groups of virtual sources visits every target once per
 // group, the groups in row order: acc carries each target's compensated sums
 // (sum, compensation, heating sum, its compensation) from one group to the
 // next; the first group starts from zero and the last one writes Gamma.
-template <int MODE>
+template <int MODE, int LANES>
 __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, long long t0,
                                                      long long t1, u64 base, float conv,
                                                      const u32 *porig, float *gam, float *gout,
@@ -858,7 +859,9 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
                                                      int last)
 {
     const int lane = threadIdx.x & 31;
-    long long i = t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int gl = lane % LANES;
+    const unsigned gmask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << (lane - gl));
+    long long i = t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
     unsigned long long hops = 0, ovf = 0, rays = 0;
     u32 maxh = 0;
     if (i < t1) {
@@ -872,8 +875,8 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
             hsum = q.z;
             hcmp = q.w;
         }
-        for (u64 e = e0; e < e1; e += 32) {
-            u64 p = e + lane;
+        for (u64 e = e0; e < e1; e += LANES) {   // uniform within the lane group
+            u64 p = e + gl;
             float v = 0.f, hv = 0.f;
             if (p < e1) {
                 uint4 st = a.state[p];
@@ -900,22 +903,22 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
                 rays += 1;
                 if ((long long)l > a.m.hop_cap) ovf += 1;
             }
-            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            for (int o = LANES / 2; o; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
             float yk = v - cmp;
             float tk = sum + yk;
             cmp = (tk - sum) - yk;
             sum = tk;
             if (MODE == 2) {
-                for (int o = 16; o; o >>= 1) hv += __shfl_xor_sync(0xffffffffu, hv, o);
+                for (int o = LANES / 2; o; o >>= 1) hv += __shfl_xor_sync(gmask, hv, o);
                 float hy = hv - hcmp;
                 float ht = hsum + hy;
                 hcmp = (ht - hsum) - hy;
                 hsum = ht;
             }
         }
-        if (lane == 0 && !last) {
+        if (gl == 0 && !last) {
             acc[i] = make_float4(sum, cmp, hsum, hcmp);
-        } else if (lane == 0) {
+        } else if (gl == 0) {
             float g = sum * conv;
             if (MODE != 1) gam[i] = g;
             if (MODE == 2) x.heat[i] = hsum * x.heat_conv;
@@ -1208,7 +1211,10 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     a.EN = (u32)(c->walk_emit ? c->et.n : 0);
     a.svid = c->m_vid.as<u32>();
     a.state = c->m_st[c->memo_final].as<uint4>();
-    long long threads = (t1 - t0) * 32;
+    // a whole row per warp; the short rows of one group of a split solve eight
+    // lanes each
+    const int lanes = (first && last) ? 32 : 8;
+    long long threads = (t1 - t0) * lanes;
     GammaExtra x{};
     const bool spec = c->solve_kind == 0 && spectral_mode(c);
     if (spec) {
@@ -1226,15 +1232,17 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     const u64 *lo = c->loff.as<u64>();
     const u32 *po = c->porig.as<u32>();
     float *gm = c->gam.as<float>();
-    if (c->solve_kind == 1)
-        k_memo_gamma<1><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x,
-                                                     acc, f, l);
-    else if (spec)
-        k_memo_gamma<2><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x,
-                                                     acc, f, l);
-    else
-        k_memo_gamma<0><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x,
-                                                     acc, f, l);
+#define ST_GAMMA(M, LN)                                                                 \
+    k_memo_gamma<M, LN><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x, \
+                                                     acc, f, l)
+    if (c->solve_kind == 1) {
+        if (lanes == 32) ST_GAMMA(1, 32); else ST_GAMMA(1, 8);
+    } else if (spec) {
+        if (lanes == 32) ST_GAMMA(2, 32); else ST_GAMMA(2, 8);
+    } else {
+        if (lanes == 32) ST_GAMMA(0, 32); else ST_GAMMA(0, 8);
+    }
+#undef ST_GAMMA
     ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_memo_gamma");
 }

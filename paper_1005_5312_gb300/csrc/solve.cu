@@ -834,7 +834,7 @@ static int run_grouped(start_ctx *c, float theta, float *gout_dev, long long max
     // bins [b0, b1) of each group, about 0.8 max_pairs each by the sample
     std::vector<std::pair<int, int>> groups;
     {
-        const double target = 0.8 * (double)maxp / kGroupStride;
+        const double target = 0.9 * (double)maxp / kGroupStride;
         int b0 = 0;
         double acc = 0.0;
         for (int b = 0; b < kGroupBins; ++b) {
