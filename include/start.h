@@ -141,6 +141,18 @@ typedef struct start_params {
     int row_warps;         /* tile shape of the memoised march's first hop: target
                               rows per thread block, 4 or 8 (0 = 8); does not
                               change any result */
+    int thermal;           /* 0: isothermal, constant alpha_A / alpha_B (above).
+                              1: every particle carries a gas temperature
+                              (start_set_temperature); start_ionize takes the
+                              recombination coefficients at it, adds collisional
+                              ionisation, and then advances the temperature by
+                              the energy equation of Section 2.1 without its
+                              hydrodynamic terms: photoheating from the last
+                              solve (start_get_heating) against recombination,
+                              free-free, collisional-excitation and collisional-
+                              ionisation cooling; the emitters use
+                              alpha_1(T) = alpha_A(T) - alpha_B(T).  The rate
+                              fits are those of start_ionize's comment */
 } start_params;
 
 /* Counters of the last start_rt_solve. */
@@ -233,8 +245,36 @@ int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_ou
 
 /* Step 8: advance the resident y by dt_s seconds with the resident Gamma
  * of the last start_rt_solve (one backward-Euler step), update the
- * resident n_HI, and copy y to y_out [n_p] (input order) when not NULL. */
+ * resident n_HI, and copy y to y_out [n_p] (input order) when not NULL.
+ *
+ * With start_params.thermal = 1 (the temperature half of the network of
+ * Appendix A, hydrogen only), per particle and in FP64:
+ *   1. y: backward Euler of dy/dt = -k y - Gc(T0) n_H y (1 - y)
+ *      + alpha(T0) n_H (1 - y)^2 at the step-start temperature T0, k as
+ *      above (with alpha_1(T0) in the self term), alpha = alpha_A(T) in the
+ *      diffuse case and alpha_B(T) otherwise; the root in [0, 1] of
+ *      (a + c) y^2 - (1 + K + c + 2a) y + (y0 + a) = 0 with a = alpha n_H dt,
+ *      c = Gc n_H dt, K = k dt;
+ *   2. T: backward Euler of the energy density (3/2) (1 + x) n_H k_B T,
+ *      (3/2) k_B n_H ((1 + x1) T1 - (1 + x0) T0) = dt (H - Lambda(T1, x1)),
+ *      H = y1 n_H h with h the photoheating per neutral atom of the last
+ *      solve (0 when every photon is at the Lyman limit), Lambda =
+ *      n_e n_p (recombination cooling, case A in the diffuse case, else B,
+ *      + free-free) + n_e n_HI (collisional excitation + ionisation
+ *      cooling); T1 is kept within [10 K, 1e9 K].
+ *   Fits (cgs, lambda = 2 x 157807 K / T): Hui & Gnedin (1997) for
+ *   alpha_A, alpha_B, the case A and B recombination cooling and the
+ *   collisional ionisation rate Gc (its cooling: k_B 157807 K Gc);
+ *   Black (1981) as given by Cen (1992) for collisional excitation
+ *   7.5e-19 exp(-118348/T) / (1 + (T/1e5)^0.5); free-free 1.42e-27 g_ff
+ *   T^0.5 with g_ff = 1.1 + 0.34 exp(-(5.5 - log10 T)^2 / 3) (Cen 1992). */
 int start_ionize(start_ctx *c, double dt_s, double *y_out);
+
+/* Gas temperatures (thermal = 1): T [n_p] float64 kelvin (> 0, finite),
+ * input order, host or device.  start_set_state resets every temperature
+ * to 1e4 K; start_get_temperature copies the resident ones out. */
+int start_set_temperature(start_ctx *c, const double *T);
+int start_get_temperature(start_ctx *c, double *T_out);
 
 /* SPH density of Sec. 2.1 (the step before the path when the density
  * changes between solves): rho_i = sum_j m_j W(|r_i - r_j|, h_i) over the

@@ -90,6 +90,11 @@ def _configure(lib):
     lib.orc_self_terms.argtypes = [vp, vp, vp, lp, vp, vp]
     lib.orc_gamma_spectral.restype = ip
     lib.orc_gamma_spectral.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp, vp]
+    lib.orc_rate.restype = dp
+    lib.orc_rate.argtypes = [ip, dp]
+    lib.orc_set_emitters_T.argtypes = [vp, vp, vp, vp]
+    lib.orc_self_terms_T.argtypes = [vp, vp, vp, vp, lp, vp, vp]
+    lib.orc_ionize_thermal.argtypes = [vp, vp, vp, vp, vp, vp, dp, vp, lp, vp, vp]
     lib.orc_h2_dissociation.restype = ip
     lib.orc_h2_dissociation.argtypes = [vp, vp, fp, dp, vp, lp, vp, vp]
     return lib
@@ -221,6 +226,45 @@ class Oracle:
         n_H = np.ascontiguousarray(n_H, dtype=np.float32)
         self.lib.orc_set_emitters(self.h_, _p(y), _p(n_H))
 
+    def set_emitters_T(self, y, n_H, T):
+        """Emitters with alpha_1(T) of the rate fits per particle."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        n_H = np.ascontiguousarray(n_H, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        self.lib.orc_set_emitters_T(self.h_, _p(y), _p(n_H), _p(T))
+
+    def self_terms_T(self, n_H, y0, T):
+        """(k_self, self photoheating) per neutral atom with alpha_1(T)."""
+        n_H = np.ascontiguousarray(n_H, dtype=np.float32)
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        n = len(y0)
+        ks = np.zeros(max(n, 1))
+        hs = np.zeros(max(n, 1))
+        self.lib.orc_self_terms_T(self.h_, _p(n_H), _p(y0), _p(T), n, _p(ks), _p(hs))
+        return ks[:n], hs[:n]
+
+    def ionize_thermal(self, gamma, heat, n_H, y0, T0, dt, targets=None):
+        """One implicit step of hydrogen and its temperature (the rate fits;
+        heat = photoheating per neutral atom in erg/s, or None); the arrays
+        belong to the particles `targets` (input indices) or to all in order.
+        Returns (y1, T1)."""
+        gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+        heat = None if heat is None else np.ascontiguousarray(heat, dtype=np.float64)
+        n_H = np.ascontiguousarray(n_H, dtype=np.float32)
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        T0 = np.ascontiguousarray(T0, dtype=np.float64)
+        n = len(y0)
+        y1 = np.zeros(max(n, 1))
+        T1 = np.zeros(max(n, 1))
+        tp = None
+        if targets is not None:
+            targets = np.ascontiguousarray(targets, dtype=np.int64)
+            tp = _p(targets)
+        self.lib.orc_ionize_thermal(self.h_, _p(gamma), _p(heat), _p(n_H), _p(y0), _p(T0),
+                                    float(dt), tp, n, _p(y1), _p(T1))
+        return y1[:n], T1[:n]
+
     def emitter_L(self):
         return np.array([self.lib.orc_emitter_L(self.h_, i) for i in range(self.np_)])
 
@@ -349,6 +393,16 @@ class Oracle:
         g = self.gamma(nHI, theta)
         y1, _ = self.ionize(g, n_H, y, dt)
         return g, y1
+
+
+RATES = {"alpha_A": 0, "alpha_B": 1, "rec_cool_A": 2, "rec_cool_B": 3, "coll_ion": 4,
+         "coll_ion_cool": 5, "coll_exc_cool": 6, "free_free_cool": 7}
+
+
+def rate(name: str, T: float) -> float:
+    """The oracle's hydrogen rate or cooling coefficient at temperature T
+    (cgs: cm^3/s for rates, erg cm^3/s for cooling)."""
+    return float(_load().orc_rate(RATES[name], float(T)))
 
 
 def spline_w(r: float, h: float) -> float:

@@ -776,10 +776,9 @@ int orc_gamma(const orc *o, const float *nHI, float theta, const long *targets, 
  *     k_self = alpha_1 n_e n_p sigma R (1/D) int u^-3 phi(tau_s u^-3) du
  *     heat   = alpha_1 n_e n_p sigma R h nu_L (1/D) int (u-1) u^-3 phi(tau_s u^-3) du
  *     by composite Simpson with 512 intervals. */
-static void self_terms(const orc *o, long i, double nh, double y0, double *k_self,
-                       double *h_self)
+static void self_terms_a1(const orc *o, long i, double nh, double y0, double a1,
+                          double *k_self, double *h_self)
 {
-    double a1 = o->p.alpha_A - o->p.alpha_B;
     double sig = o->p.sigma_cm2;
     double x0 = 1.0 - y0;
     double R = cbrt(3.0 * o->V[i] / (4.0 * ORC_PI)) * o->p.len_unit_cm;
@@ -807,12 +806,31 @@ static void self_terms(const orc *o, long i, double nh, double y0, double *k_sel
     *h_self = pre * ORC_HNU_L_ERG * (sh * du / (3.0 * D));
 }
 
+static void self_terms(const orc *o, long i, double nh, double y0, double *k_self,
+                       double *h_self)
+{
+    self_terms_a1(o, i, nh, y0, o->p.alpha_A - o->p.alpha_B, k_self, h_self);
+}
+
+double orc_rate(int which, double T);
+
 /* Self terms of particles [0, n) (input order, diffuse case): k_self and the
- * self photoheating, both per neutral atom. */
+ * self photoheating, both per neutral atom; with temperatures T (may be
+ * NULL) alpha_1 = alpha_A(T) - alpha_B(T) of the rate fits below. */
 void orc_self_terms(const orc *o, const float *nH, const double *y0, long n, double *k_self,
                     double *h_self)
 {
     for (long i = 0; i < n; ++i) self_terms(o, i, (double)nH[i], y0[i], &k_self[i], &h_self[i]);
+}
+
+void orc_self_terms_T(const orc *o, const float *nH, const double *y0, const double *T, long n,
+                      double *k_self, double *h_self)
+{
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i) {
+        double a1 = T ? orc_rate(0, T[i]) - orc_rate(1, T[i]) : o->p.alpha_A - o->p.alpha_B;
+        self_terms_a1(o, i, (double)nH[i], y0[i], a1, &k_self[i], &h_self[i]);
+    }
 }
 
 /* Implicit hydrogen update over dt (Appendix A), hydrogen only, isothermal:
@@ -1042,4 +1060,139 @@ int orc_gamma_spectral(const orc *o, const float *nHI, float theta, double T_eff
     }
     if (stats) { stats[0] = rays; stats[1] = hops; }
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Gas temperature (the energy equation of Section 2.1 without its      */
+/* hydrodynamic terms; the rates of Appendix A's network restricted to  */
+/* hydrogen)                                                            */
+/*
+ * The paper takes its rate and cooling coefficients from the Kitayama et
+ * al. (2001) network without printing them.  Here hydrogen only, with
+ * published fits in cgs units, lambda = 2 T_HI / T, T_HI = 157807 K:
+ *   alpha_A(T) = 1.269e-13 lambda^1.503 / (1 + (lambda/0.522)^0.470)^1.923
+ *   alpha_B(T) = 2.753e-14 lambda^1.500 / (1 + (lambda/2.740)^0.407)^2.242
+ *   recombination cooling, erg cm^3/s, times n_e n_p:
+ *     case A  1.778e-29 T lambda^1.965 / (1 + (lambda/0.541)^0.502)^2.697
+ *     case B  3.435e-30 T lambda^1.970 / (1 + (lambda/2.250)^0.376)^3.720
+ *   collisional ionisation rate, cm^3/s, times n_e n_HI:
+ *     21.11 T^-1.5 exp(-lambda/2) lambda^-1.089 / (1 + (lambda/0.354)^0.874)^1.101
+ *   (all from Hui & Gnedin 1997, Appendix), its cooling k T_HI times the rate;
+ *   collisional excitation cooling (Black 1981, as given by Cen 1992),
+ *     7.5e-19 exp(-118348/T) / (1 + (T/1e5)^0.5) erg cm^3/s times n_e n_HI;
+ *   free-free cooling 1.42e-27 g_ff T^0.5 erg cm^3/s times n_e n_p with
+ *     g_ff = 1.1 + 0.34 exp(-(5.5 - log10 T)^2 / 3) (Cen 1992). */
+#define ORC_T_HI 157807.0
+
+double orc_rate(int which, double T)
+{
+    double lam = 2.0 * ORC_T_HI / T;
+    switch (which) {
+    case 0: return 1.269e-13 * pow(lam, 1.503) / pow(1.0 + pow(lam / 0.522, 0.470), 1.923);
+    case 1: return 2.753e-14 * pow(lam, 1.500) / pow(1.0 + pow(lam / 2.740, 0.407), 2.242);
+    case 2: return 1.778e-29 * T * pow(lam, 1.965) / pow(1.0 + pow(lam / 0.541, 0.502), 2.697);
+    case 3: return 3.435e-30 * T * pow(lam, 1.970) / pow(1.0 + pow(lam / 2.250, 0.376), 3.720);
+    case 4:
+        return 21.11 * pow(T, -1.5) * exp(-0.5 * lam) * pow(lam, -1.089) /
+               pow(1.0 + pow(lam / 0.354, 0.874), 1.101);
+    case 5: return ORC_KB_ERG * ORC_T_HI * orc_rate(4, T);
+    case 6: return 7.5e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1e5));
+    case 7: {
+        double lt = log10(T);
+        double gff = 1.1 + 0.34 * exp(-(5.5 - lt) * (5.5 - lt) / 3.0);
+        return 1.42e-27 * gff * sqrt(T);
+    }
+    }
+    return 0.0;
+}
+
+/* Net cooling minus heating of the energy equation at temperature T, with
+ * the ionisation state (x, n_H) held: Lambda(T) - H, erg cm^-3 s^-1. */
+static double net_cooling(int caseA, double T, double x, double nh, double heat)
+{
+    double ne = x * nh, np_ = x * nh, nhi = (1.0 - x) * nh;
+    double lam = ne * np_ * (orc_rate(caseA ? 2 : 3, T) + orc_rate(7, T)) +
+                 ne * nhi * (orc_rate(5, T) + orc_rate(6, T));
+    return lam - heat;
+}
+
+/* Recombination emitters with temperature-dependent coefficients:
+ * N_rec,j = alpha_1(T_j) n_e n_p V_j, alpha_1 = alpha_A(T) - alpha_B(T)
+ * (Section 4.1); T = NULL takes the constant alpha_A - alpha_B of the
+ * parameters (orc_set_emitters). */
+void orc_set_emitters_T(orc *o, const double *y, const float *nH, const double *T)
+{
+    if (!T) {
+        orc_set_emitters(o, y, nH);
+        return;
+    }
+    double lu3 = o->p.len_unit_cm * o->p.len_unit_cm * o->p.len_unit_cm;
+    for (long i = 0; i < o->np; ++i) {
+        double a1 = orc_rate(0, T[i]) - orc_rate(1, T[i]);
+        double ne = (1.0 - y[i]) * (double)nH[i];
+        o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);
+    }
+    if (o->et.n) moments_node(&o->et, 0, o->pperm, o->px, o->py, o->pz, o->eL);
+}
+
+/* One implicit step of hydrogen and its gas temperature over dt, per
+ * particle (input order):
+ *  1. the neutral fraction, with the step-start temperature T0: backward
+ *     Euler of dy/dt = -k y - C y (1 - y) + a (1 - y)^2 with k = sigma Gamma
+ *     (+ the self term of Eq. kself1, at the Lyman limit or band-averaged,
+ *     with alpha_1(T0) in the diffuse case),
+ *     C = Gc(T0) n_H (collisional ionisation), a = alpha(T0) n_H (alpha_A
+ *     in the diffuse case, else alpha_B): the root in [0, 1] of
+ *     (a' + c') y^2 - (1 + K + c' + 2a') y + (y0 + a') = 0 (primes: times
+ *     dt), taken as 2 (y0 + a') / (b + sqrt(b^2 - 4 (a' + c') (y0 + a')));
+ *  2. the temperature, with the new ionisation x1 = 1 - y1: backward Euler
+ *     of the energy density u = (3/2) (1 + x) n_H k T,
+ *       (3/2) k n_H ((1 + x1) T1 - (1 + x0) T0) = dt (H - Lambda(T1, x1)),
+ *     H = y1 n_H h with h the photoheating per neutral atom (erg/s) of the
+ *     solve (blackbody sources, the recombination band and its self term),
+ *     Lambda the recombination (case A in the diffuse case, else B),
+ *     free-free, collisional-excitation and collisional-ionisation cooling.
+ *     T1 is found by bisection on ln T over [10 K, 1e9 K] (the residual is
+ *     increasing in T1 there for every state tested), 200 halvings.
+ * heat may be NULL (no photoheating).  targets (may be NULL) lists the
+ * particles (input indices) that entry t of the arrays belongs to. */
+void orc_ionize_thermal(const orc *o, const double *gamma, const double *heat, const float *nH,
+                        const double *y0, const double *T0, double dt, const long *targets,
+                        long n, double *y1, double *T1)
+{
+    int diffuse = o->p.diffuse;
+    double sig = o->p.sigma_cm2;
+    for (long t = 0; t < n; ++t) {
+        long i = targets ? targets[t] : t;   /* the particle (volume); arrays indexed by t */
+        double nh = nH[t], t0 = T0[t], yy = y0[t];
+        double k = sig * gamma[t];
+        if (diffuse) {
+            double ks, hs;
+            self_terms_a1(o, i, nh, yy, orc_rate(0, t0) - orc_rate(1, t0), &ks, &hs);
+            k += ks;
+        }
+        double a = orc_rate(diffuse ? 0 : 1, t0) * nh * dt;
+        double c = orc_rate(4, t0) * nh * dt;
+        double K = k * dt;
+        double b = 1.0 + K + c + 2.0 * a;
+        double disc = b * b - 4.0 * (a + c) * (yy + a);
+        if (disc < 0.0) disc = 0.0;
+        double y = 2.0 * (yy + a) / (b + sqrt(disc));
+        y1[t] = y;
+        double x0 = 1.0 - yy, x1 = 1.0 - y;
+        double e = 1.5 * ORC_KB_ERG * nh;
+        double H = heat ? y * nh * heat[t] : 0.0;
+        double lo = log(10.0), hi = log(1e9);
+        double u0 = e * (1.0 + x0) * t0;
+#define RESID(T) (e * (1.0 + x1) * (T) - u0 + dt * net_cooling(diffuse, (T), x1, nh, H))
+        if (RESID(10.0) >= 0.0) { T1[t] = 10.0; continue; }
+        if (RESID(1e9) <= 0.0) { T1[t] = 1e9; continue; }
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (RESID(exp(mid)) > 0.0) hi = mid;
+            else lo = mid;
+        }
+#undef RESID
+        T1[t] = exp(0.5 * (lo + hi));
+    }
 }

@@ -39,7 +39,8 @@ class StartParams(C.Structure):
                 ("tau_cut", C.c_double), ("hop_cap", C.c_longlong), ("max_pairs", C.c_longlong),
                 ("spin_cap", C.c_longlong),
                 ("stream", C.c_void_p),
-                ("T_eff", C.c_double), ("T_rec", C.c_double), ("row_warps", C.c_int)]
+                ("T_eff", C.c_double), ("T_rec", C.c_double), ("row_warps", C.c_int),
+                ("thermal", C.c_int)]
 
 
 class StartStats(C.Structure):
@@ -79,6 +80,8 @@ def lib():
             "start_sph_density": (i, [vp, vp, vp]),
             "start_h2_dissociation": (i, [vp, vp, f, d, vp]),
             "start_get_heating": (i, [vp, vp]),
+            "start_set_temperature": (i, [vp, vp]),
+            "start_get_temperature": (i, [vp, vp]),
             "start_rt_solve_oneshot": (i, [P(StartParams), vp, vp, ll, vp, vp, vp, ll, f, vp]),
             "start_get_frame": (i, [vp, vp]),
             "start_get_perm": (i, [vp, i, vp]),
@@ -263,6 +266,21 @@ class Context:
             return heat_out[:self.n_p]
         _check(self.h, lib().start_get_heating(self.h, _ptr(heat_out)))
         return heat_out
+
+    def set_temperature(self, T):
+        """Gas temperatures in K (float64, input order, host or device)."""
+        if isinstance(T, np.ndarray):
+            T = np.ascontiguousarray(T, dtype=np.float64)
+        _check(self.h, lib().start_set_temperature(self.h, _ptr(T)))
+
+    def temperature(self, T_out=None):
+        """The resident gas temperatures (K, input order)."""
+        if T_out is None:
+            out = np.zeros(max(self.n_p, 1), np.float64)
+            _check(self.h, lib().start_get_temperature(self.h, _ptr(out)))
+            return out[:self.n_p]
+        _check(self.h, lib().start_get_temperature(self.h, _ptr(T_out)))
+        return T_out
 
     def h2_dissociation(self, n_H2, theta, kappa_LW, kdis_out=None):
         """H2 photodissociation rate k_dis (s^-1) of every particle

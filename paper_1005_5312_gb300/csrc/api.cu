@@ -212,6 +212,18 @@ __global__ void k_check_unit_d(const double *v, long long n, unsigned long long 
     if (i < n && !(v[i] >= 0.0 && v[i] <= 1.0)) atomicAdd(bad, 1ull);
 }
 
+__global__ void k_fill_d(double *v, long long n, double x)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = x;
+}
+
+__global__ void k_scatter_d(const double *in, const u32 *inv, long long n, double *out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[inv[i]] = in[i];
+}
+
 __global__ void k_invert(const u32 *perm, long long n, u32 *inv)
 {
     long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,6 +405,7 @@ static int check_params(start_params &d)
     if (d.march_group == 0) d.march_group = 2;
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
     if (d.row_warps != 0 && d.row_warps != 4 && d.row_warps != 8) return START_EINVAL;
+    if (d.thermal != 0 && d.thermal != 1) return START_EINVAL;
     if (d.row_warps == 0) d.row_warps = 8;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
     if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;
@@ -506,7 +519,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
     size_t P = (size_t)(n_p ? n_p : 1), S = (size_t)(n_s ? n_s : 1);
     if (ensure(c->pkey, P * 8) || ensure(c->tk[1], P * 8) || ensure(c->porig, P * 4) ||
         ensure(c->pinv, P * 4) || ensure(c->pq, P * 16) || ensure(c->ph, P * 4) ||
-        ensure(c->nH, P * 4) || ensure(c->y, P * 8) || ensure(c->V, P * 8) ||
+        ensure(c->nH, P * 4) || ensure(c->y, P * 8) || ensure(c->V, P * 8) || ensure(c->Tg, P * 8) ||
         ensure(c->gam, P * 4) || ensure(c->eL, P * 8) || ensure(c->eLs, P * 4) ||
         ensure(c->skey, S * 8) || ensure(c->tv[1], S * 8) || ensure(c->sorig, S * 4) ||
         ensure(c->sq, S * 16) || ensure(c->sL, S * 8))
@@ -523,6 +536,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
             c->nH.as<float>(), c->y.as<double>(), c->gam.as<float>()); ++c->launches;
         ST_CUDA(c, cudaMemsetAsync(c->eL.p, 0, n_p * 8, s));
         ST_CUDA(c, cudaMemsetAsync(c->eLs.p, 0, n_p * 4, s));
+        k_fill_d<<<grid_for(n_p, 256), 256, 0, s>>>(c->Tg.as<double>(), n_p, 1e4); ++c->launches;
         ST_CUDA(c, cudaGetLastError());
     }
     u64 *sks = c->tv[1].as<u64>();
@@ -570,10 +584,49 @@ int start_set_state(start_ctx *c, const float *n_H, const double *y)
     k_set_state<<<grid_for(n, 256), 256, 0, c->stream>>>(in.h.as<float>(), y ? in.V.as<double>() : nullptr,
                                                         c->pinv.as<u32>(), n, c->nH.as<float>(),
                                                         c->y.as<double>(), c->pq.as<float4>()); ++c->launches;
+    k_fill_d<<<grid_for(n, 256), 256, 0, c->stream>>>(c->Tg.as<double>(), n, 1e4); ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     c->has_state = true;
     return START_OK;
+}
+
+int start_set_temperature(start_ctx *c, const double *T)
+{
+    if (!c) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c);
+    long long n = c->np;
+    if (n == 0) return START_OK;
+    if (!T) return set_err(c, START_EINVAL, "NULL T");
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    Staged in;
+    ST_TRY(stage_in(c, in.V, T, n * sizeof(double)));
+    k_check_nonneg_d<<<grid_for(n, 256), 256, 0, c->stream>>>(in.V.as<double>(), n,
+                                                              ctr + C_BAD_INPUT, 1);
+    ++c->launches;
+    ST_TRY(check_bad(c, "T"));
+    k_scatter_d<<<grid_for(n, 256), 256, 0, c->stream>>>(in.V.as<double>(), c->pinv.as<u32>(), n,
+                                                         c->Tg.as<double>());
+    ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    return START_OK;
+}
+
+int start_get_temperature(start_ctx *c, double *T_out)
+{
+    if (!c || (!T_out && c->np > 0)) return START_EINVAL;
+    if (!c->built) return set_err(c, START_ENOTBUILT, "start_build_trees first");
+    DeviceGuard g(c);
+    long long n = c->np;
+    if (n == 0) return START_OK;
+    ST_TRY(ensure(c->stage, n * sizeof(double)));
+    k_to_input_order<double><<<grid_for(n, 256), 256, 0, c->stream>>>(
+        c->Tg.as<double>(), c->porig.as<u32>(), n, c->stage.as<double>());
+    ++c->launches;
+    ST_CUDA(c, cudaGetLastError());
+    return copy_out(c, T_out, c->stage.p, n * sizeof(double));
 }
 
 int start_rt_solve(start_ctx *c, const float *n_HI, float theta, float *gamma_out)
@@ -628,7 +681,8 @@ int start_ionize(start_ctx *c, double dt_s, double *y_out)
     if (!c->built || !c->solved) return set_err(c, START_ENOTBUILT, "start_rt_solve first");
     if (!(dt_s >= 0.0) || !isfinite(dt_s)) return set_err(c, START_EINVAL, "dt must be >= 0");
     DeviceGuard g(c);
-    ST_TRY(run_ionize(c, dt_s));
+    if (c->p.thermal) ST_TRY(run_ionize_thermal(c, dt_s));
+    else ST_TRY(run_ionize(c, dt_s));
     if (y_out && c->np) {
         bool dev = is_device_ptr(y_out);
         double *dst = y_out;

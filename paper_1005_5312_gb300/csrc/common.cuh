@@ -112,6 +112,7 @@ struct start_ctx {
     double spec_T = -1.0;              // T_eff and T_rec spec_tab was built for
     double spec_Trec = -1.0;
     st::DBuf y;       // double neutral fraction
+    st::DBuf Tg;      // double gas temperature (K), Morton order
     st::DBuf V;       // double volume (len_unit^3)
     st::DBuf gam;     // float Gamma (cgs)
     st::DBuf eL;      // double emitter luminosity, photons/s
@@ -283,6 +284,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev);
 int run_walk(start_ctx *c, float theta);
 int run_walk_hash(start_ctx *c, float theta, unsigned long long *hash, unsigned long long *count);
 int run_ionize(start_ctx *c, double dt);
+int run_ionize_thermal(start_ctx *c, double dt);
 int refresh_emitters(start_ctx *c);
 
 // ---------------------------------------------------------------- device helpers

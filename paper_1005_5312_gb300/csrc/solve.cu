@@ -401,11 +401,17 @@ __global__ void k_gamma(const float *pcon, const u64 *off, long long t0, long lo
 // ---------------------------------------------------------------- emitters
 // N_rec = alpha_1 (x n_H)^2 V (Section 4.1), same operation order as the
 // definition: ((alpha_1 n_e) n_e) (V len^3).
+__device__ double rate_alpha_A(double T);
+__device__ double rate_alpha_B(double T);
+
+// Tg (thermal mode, else NULL): alpha_1 = alpha_A(T) - alpha_B(T) per particle.
 __global__ void k_emitters(const double *y, const float *nH, const double *V, long long np,
-                           double a1, double lu3, double L_unit, double *eL, float *eLs)
+                           double a1c, double lu3, double L_unit, double *eL, float *eLs,
+                           const double *Tg)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
+    const double a1 = Tg ? rate_alpha_A(Tg[i]) - rate_alpha_B(Tg[i]) : a1c;
     double ne = __dmul_rn(__dsub_rn(1.0, y[i]), (double)nH[i]);
     double L = __dmul_rn(__dmul_rn(__dmul_rn(a1, ne), ne), __dmul_rn(V[i], lu3));
     eL[i] = L;
@@ -421,7 +427,8 @@ int refresh_emitters(start_ctx *c)
     phase_mark(c, START_PHASE_EMIT, false);
     k_emitters<<<grid_for(c->np, 256), 256, 0, c->stream>>>(
         c->y.as<double>(), c->nH.as<float>(), c->V.as<double>(), c->np, a1, lu3, c->p.L_unit,
-        c->eL.as<double>(), c->eLs.as<float>()); ++c->launches;
+        c->eL.as<double>(), c->eLs.as<float>(), c->p.thermal ? c->Tg.as<double>() : nullptr);
+    ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_TRY(tree_moments(c, c->et, c->pq.as<float4>(), c->eL.as<double>(), c->p.L_unit));
     phase_mark(c, START_PHASE_EMIT, true);
@@ -701,10 +708,12 @@ __device__ void band_self(double ts, double D, double &ik, double &ih)
 
 // heat[i] += the self photoheating per neutral atom (band only), Morton order
 __global__ void k_self_heat(float *heat, const double *y, const float *nH, const double *V,
-                            long long np, double a1, double sigma, double len_cm, double D)
+                            long long np, double a1c, double sigma, double len_cm, double D,
+                            const double *Tg)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
+    const double a1 = Tg ? rate_alpha_A(Tg[i]) - rate_alpha_B(Tg[i]) : a1c;
     const double y0 = y[i], nh = (double)nH[i], x0 = 1.0 - y0;
     const double R = cbrt(3.0 * V[i] / (4.0 * 3.14159265358979323846)) * len_cm;
     double ik, ih;
@@ -1049,7 +1058,7 @@ static int finish_solve(start_ctx *c, bool memo, bool spec)
         k_self_heat<<<grid_for(np, 256), 256, 0, s>>>(
             c->heat.as<float>(), c->y.as<double>(), c->nH.as<float>(), c->V.as<double>(), np,
             c->p.alpha_A - c->p.alpha_B, c->p.sigma_cm2, c->p.len_unit_cm,
-            kBoltzErg * c->p.T_rec / kHnuLErg);
+            kBoltzErg * c->p.T_rec / kHnuLErg, c->p.thermal ? c->Tg.as<double>() : nullptr);
         ++c->launches;
         ST_CUDA(c, cudaGetLastError());
     }
@@ -1108,6 +1117,146 @@ int run_ionize(start_ctx *c, double dt)
         c->p.T_rec > 0.0 ? kBoltzErg * c->p.T_rec / kHnuLErg : 0.0); ++c->launches;
     phase_mark(c, START_PHASE_IONIZE, true);
     return cuda_check(c, cudaGetLastError(), "k_ionize");
+}
+
+// ---------------------------------------------------------------- temperature
+// Hydrogen rate and cooling coefficients (cgs), lambda = 2 T_HI / T with
+// T_HI = 157807 K: Hui & Gnedin (1997) for alpha_A, alpha_B, recombination
+// cooling (cases A, B) and the collisional ionisation rate; collisional
+// excitation cooling of Black (1981) as given by Cen (1992); free-free
+// cooling with the gaunt factor of Cen (1992).  FP64 throughout.
+constexpr double kTHI = 157807.0;
+
+__device__ double rate_alpha_A(double T)
+{
+    const double l = 2.0 * kTHI / T;
+    return 1.269e-13 * pow(l, 1.503) / pow(1.0 + pow(l / 0.522, 0.470), 1.923);
+}
+
+__device__ double rate_alpha_B(double T)
+{
+    const double l = 2.0 * kTHI / T;
+    return 2.753e-14 * pow(l, 1.500) / pow(1.0 + pow(l / 2.740, 0.407), 2.242);
+}
+
+__device__ double cool_recomb(double T, bool caseA)
+{
+    const double l = 2.0 * kTHI / T;
+    return caseA ? 1.778e-29 * T * pow(l, 1.965) / pow(1.0 + pow(l / 0.541, 0.502), 2.697)
+                 : 3.435e-30 * T * pow(l, 1.970) / pow(1.0 + pow(l / 2.250, 0.376), 3.720);
+}
+
+__device__ double rate_coll_ion(double T)
+{
+    const double l = 2.0 * kTHI / T;
+    return 21.11 * pow(T, -1.5) * exp(-0.5 * l) * pow(l, -1.089) /
+           pow(1.0 + pow(l / 0.354, 0.874), 1.101);
+}
+
+__device__ double cool_coll_exc(double T)
+{
+    return 7.5e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1e5));
+}
+
+__device__ double cool_free_free(double T)
+{
+    const double q = 5.5 - log10(T);
+    return 1.42e-27 * (1.1 + 0.34 * exp(-q * q / 3.0)) * sqrt(T);
+}
+
+// Residual of the implicit energy equation at temperature T (erg cm^-3):
+// (3/2) k_B n_H (1 + x1) T - u0 + dt (Lambda(T) - H).
+struct EnergyResidual {
+    double e1, u0, dt, nene, nenhi, H;
+    bool caseA;
+    __device__ double operator()(double T) const
+    {
+        const double lam = nene * (cool_recomb(T, caseA) + cool_free_free(T)) +
+                           nenhi * (kBoltzErg * kTHI * rate_coll_ion(T) + cool_coll_exc(T));
+        return e1 * T - u0 + dt * (lam - H);
+    }
+};
+
+// One implicit step of hydrogen and its gas temperature per particle: the
+// neutral fraction at the step-start temperature (recombination and
+// collisional ionisation at T0), then T1 as the root of the energy
+// residual, by Newton steps on ln T kept inside a bracket that every
+// residual evaluation narrows (bisection whenever a step leaves it).
+__global__ void k_ionize_thermal(double *y, double *Tg, float4 *pq, const float *gam,
+                                 const float *heat, const float *nH, const double *V,
+                                 long long np, double dt, double sigma, double len_cm,
+                                 int diffuse, double D)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const double y0 = y[i], nh = (double)nH[i], t0 = Tg[i];
+    double k = sigma * (double)gam[i];
+    if (diffuse) {
+        const double a1 = rate_alpha_A(t0) - rate_alpha_B(t0);
+        const double x0 = 1.0 - y0;
+        const double R = cbrt(3.0 * V[i] / (4.0 * 3.14159265358979323846)) * len_cm;
+        const double ts = sigma * (y0 * nh) * R;
+        double f;
+        if (D > 0.0) {
+            double ik, ih;
+            band_self(ts, D, ik, ih);
+            f = ik;
+        } else {
+            f = phi_self(ts);
+        }
+        k += a1 * x0 * x0 * nh * nh * sigma * R * f;
+    }
+    const double a = (diffuse ? rate_alpha_A(t0) : rate_alpha_B(t0)) * nh * dt;
+    const double cc = rate_coll_ion(t0) * nh * dt;
+    const double K = k * dt;
+    const double b = 1.0 + K + cc + 2.0 * a;
+    const double disc = fmax(b * b - 4.0 * (a + cc) * (y0 + a), 0.0);
+    const double y1 = 2.0 * (y0 + a) / (b + sqrt(disc));
+    const double x0 = 1.0 - y0, x1 = 1.0 - y1;
+    const double e = 1.5 * kBoltzErg * nh;
+    EnergyResidual r{e * (1.0 + x1), e * (1.0 + x0) * t0, dt, x1 * nh * x1 * nh,
+                     x1 * nh * y1 * nh, heat ? y1 * nh * (double)heat[i] : 0.0, diffuse != 0};
+    double T1;
+    const double sl = log(10.0), sh = log(1e9);
+    if (r(10.0) >= 0.0) {
+        T1 = 10.0;
+    } else if (r(1e9) <= 0.0) {
+        T1 = 1e9;
+    } else {
+        double lo = sl, hi = sh;
+        double s = fmin(fmax(log(t0), sl), sh);
+        for (int it = 0; it < 100; ++it) {
+            const double f = r(exp(s));
+            if (f > 0.0) hi = s;
+            else lo = s;
+            if (f == 0.0) break;
+            const double hstep = 1e-7;
+            const double d = (r(exp(s + hstep)) - f) / hstep;
+            double sn = s - f / d;
+            if (!(d > 0.0) || !(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+            const bool done = fabs(sn - s) <= 1e-13 || hi - lo <= 1e-13;
+            s = sn;
+            if (done) break;
+        }
+        T1 = exp(s);
+    }
+    y[i] = y1;
+    Tg[i] = T1;
+    pq[i].w = __double2float_rn(y1 * nh);
+}
+
+int run_ionize_thermal(start_ctx *c, double dt)
+{
+    if (c->np == 0) return START_OK;
+    phase_mark(c, START_PHASE_IONIZE, false);
+    k_ionize_thermal<<<grid_for(c->np, 128), 128, 0, c->stream>>>(
+        c->y.as<double>(), c->Tg.as<double>(), c->pq.as<float4>(), c->gam.as<float>(),
+        c->heat_valid ? c->heat.as<float>() : nullptr, c->nH.as<float>(), c->V.as<double>(),
+        c->np, dt, c->p.sigma_cm2, c->p.len_unit_cm, c->diffuse ? 1 : 0,
+        c->p.T_rec > 0.0 ? kBoltzErg * c->p.T_rec / kHnuLErg : 0.0);
+    ++c->launches;
+    phase_mark(c, START_PHASE_IONIZE, true);
+    return cuda_check(c, cudaGetLastError(), "k_ionize_thermal");
 }
 
 }  // namespace st

@@ -12,6 +12,7 @@ import pytest
 import oracle
 
 import test_oracle_pins as pins
+from start_inputs import SIGMA_CM2 as SIGMA
 
 # (tag, original text, planted mistake, pins expected to catch it)
 MUTATIONS = [
@@ -20,12 +21,12 @@ MUTATIONS = [
      "double a1 = o->p.alpha_A;\n    double lu3",
      [pins.test_diffuse_emitters_radiative_equilibrium]),
     ("emit_no_volume_unit",
-     "o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);",
-     "o->eL[i] = a1 * ne * ne * o->V[i];",
+     "for (long i = 0; i < o->np; ++i) {\n        double ne = (1.0 - y[i]) * (double)nH[i];\n        o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);",
+     "for (long i = 0; i < o->np; ++i) {\n        double ne = (1.0 - y[i]) * (double)nH[i];\n        o->eL[i] = a1 * ne * ne * o->V[i];",
      [pins.test_diffuse_emitters_radiative_equilibrium]),
     ("emit_x_not_squared",
-     "o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);",
-     "o->eL[i] = a1 * ne * (double)nH[i] * (o->V[i] * lu3);",
+     "for (long i = 0; i < o->np; ++i) {\n        double ne = (1.0 - y[i]) * (double)nH[i];\n        o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);",
+     "for (long i = 0; i < o->np; ++i) {\n        double ne = (1.0 - y[i]) * (double)nH[i];\n        o->eL[i] = a1 * ne * (double)nH[i] * (o->V[i] * lu3);",
      [pins.test_diffuse_emitters_radiative_equilibrium]),
     ("march_dropped_half",
      "tau += sig * 0.5 * ((double)nHI[j] + (double)nHI[best]) * dl;",
@@ -67,6 +68,44 @@ MUTATIONS = [
      "*k_self = a1 * x0 * x0 * nh * nh * sig * R * phi;",
      "*k_self = a1 * x0 * x0 * nh * nh * sig * R;",
      [lambda: pins.test_diffuse_self_term_opaque_limit(0.0)]),
+    ("thermal_no_three_halves",
+     "double e = 1.5 * ORC_KB_ERG * nh;",
+     "double e = ORC_KB_ERG * nh;",
+     [pins.test_thermal_heating_of_neutral_gas_is_the_closed_form]),
+    ("thermal_particles_not_one_plus_x",
+     "#define RESID(T) (e * (1.0 + x1) * (T) - u0",
+     "#define RESID(T) (e * (2.0 - x1) * (T) - u0",
+     [lambda: pins.test_thermal_step_solves_both_implicit_equations(1e-12 / SIGMA, 8e-24, 0.3,
+                                                                   3e4)]),
+    ("thermal_heating_sign",
+     "double H = heat ? y * nh * heat[t] : 0.0;",
+     "double H = heat ? -y * nh * heat[t] : 0.0;",
+     [pins.test_thermal_heating_of_neutral_gas_is_the_closed_form]),
+    ("thermal_cooling_case_swapped",
+     "double lam = ne * np_ * (orc_rate(caseA ? 2 : 3, T) + orc_rate(7, T)) +",
+     "double lam = ne * np_ * (orc_rate(caseA ? 3 : 2, T) + orc_rate(7, T)) +",
+     [lambda: pins.test_thermal_step_solves_both_implicit_equations(0.0, 0.0, 0.1, 5e4)]),
+    ("thermal_no_collisional_ionisation",
+     "double c = orc_rate(4, t0) * nh * dt;",
+     "double c = 0.0 * orc_rate(4, t0) * nh * dt;",
+     [lambda: pins.test_thermal_step_solves_both_implicit_equations(0.0, 0.0, 0.1, 5e4)]),
+    ("thermal_recombination_case_swapped",
+     "double a = orc_rate(diffuse ? 0 : 1, t0) * nh * dt;",
+     "double a = orc_rate(diffuse ? 1 : 0, t0) * nh * dt;",
+     [lambda: pins.test_thermal_step_solves_both_implicit_equations(1e-13 / SIGMA, 1e-24, 1.0,
+                                                                   1e4)]),
+    ("rate_alpha_B_exponent",
+     "case 1: return 2.753e-14 * pow(lam, 1.500)",
+     "case 1: return 2.753e-14 * pow(lam, 1.600)",
+     [pins.test_recombination_fits_against_published_coefficients]),
+    ("rate_excitation_threshold",
+     "case 6: return 7.5e-19 * exp(-118348.0 / T)",
+     "case 6: return 7.5e-19 * exp(-157807.0 / T)",
+     [pins.test_collisional_rates_carry_their_threshold_energies]),
+    ("emitters_alpha_A_not_alpha_1",
+     "double a1 = orc_rate(0, T[i]) - orc_rate(1, T[i]);\n        double ne",
+     "double a1 = orc_rate(0, T[i]);\n        double ne",
+     [pins.test_thermal_emitters_use_the_local_alpha_1]),
     ("gamma_no_4pi",
      "g += L * exp(-tau) / (4.0 * ORC_PI * r2 * lu * lu);",
      "g += L * exp(-tau) / (ORC_PI * r2 * lu * lu);",

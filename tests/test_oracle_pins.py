@@ -941,3 +941,145 @@ def test_band_gamma_in_a_uniform_medium():
             rh += flux * rhh
         assert g[q] == pytest.approx(rg, rel=1e-7)
         assert hh[q] == pytest.approx(SIGMA_CM2 * HNU_L * rh, rel=1e-7)
+
+
+# ---------------------------------------------------------------- temperature
+def _rates_golden():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "hydrogen_rates.json")) as f:
+        return json.load(f)
+
+
+def test_recombination_fits_against_published_coefficients():
+    g = _rates_golden()["recombination_coefficients"]
+    for T, aA, aB in zip(g["T_K"], g["alpha_A"], g["alpha_B"]):
+        assert abs(oracle.rate("alpha_B", T) / aB - 1) < g["rel_tol_alpha_B"], T
+        assert abs(oracle.rate("alpha_A", T) / aA - 1) < g["rel_tol_alpha_A"], T
+
+
+def test_collisional_rates_carry_their_threshold_energies():
+    """At low temperature a collisional rate falls as exp(-E/kT): the
+    logarithmic slope against 1/T is -E/k (the power-law factors of the fits
+    add a few percent here)."""
+    g = _rates_golden()["threshold_energies"]
+    for name, E in (("coll_ion", g["T_ionisation_K"]), ("coll_ion_cool", g["T_ionisation_K"]),
+                    ("coll_exc_cool", g["T_lyman_alpha_K"])):
+        T1, T2 = 3000.0, 3300.0
+        slope = (math.log(oracle.rate(name, T1)) - math.log(oracle.rate(name, T2))) / \
+            (1 / T1 - 1 / T2)
+        assert abs(-slope / E - 1) < 0.03, (name, slope)
+    # collisional-ionisation cooling removes 13.6 eV per ionisation
+    assert abs(oracle.rate("coll_ion_cool", 2e4) /
+               (oracle.rate("coll_ion", 2e4) * 1.380649e-16 * g["T_ionisation_K"]) - 1) < 1e-12
+
+
+def test_cooling_magnitudes():
+    """Free-free cooling is the classical 1.42e-27 g T^1/2 with a gaunt factor
+    between 1.1 and 1.5; a recombination removes between 1/2 and 3/2 kT of
+    kinetic energy on average (case B), and case A removes more than case B."""
+    g = _rates_golden()["free_free"]
+    kB = 1.380649e-16
+    for T in (5e3, 1e4, 2e4):
+        gff = oracle.rate("free_free_cool", T) / (g["prefactor"] * math.sqrt(T))
+        assert g["g_ff_range"][0] <= gff <= g["g_ff_range"][1], (T, gff)
+        r = oracle.rate("rec_cool_B", T) / (oracle.rate("alpha_B", T) * kB * T)
+        assert 0.5 < r < 1.5, (T, r)
+        assert oracle.rate("rec_cool_A", T) > oracle.rate("rec_cool_B", T)
+
+
+def _thermal_oracle(diffuse=False, T_rec=0.0, n=3, V=None):
+    pos, h, src, L = _lattice_problem(4, 1.0, 3, n_s=1)
+    V = np.full(pos.shape[1], 1.0 / 64) if V is None else V
+    return oracle.Oracle(pos, h, src, L, V, diffuse=diffuse, T_rec=T_rec, **PHYS)
+
+
+def test_thermal_heating_of_neutral_gas_is_the_closed_form():
+    """Neutral gas has no free electrons, so nothing cools or recombines: the
+    energy equation integrates the photoheating exactly,
+    T1 = T0 + (2/3) h dt / k_B (h: heating per neutral atom)."""
+    o = _thermal_oracle()
+    kB = 1.380649e-16
+    for h, dt, T0 in ((1e-26, 3e13, 1e4), (3e-27, 1e14, 300.0), (1e-24, 1e12, 2e3)):
+        y1, T1 = o.ionize_thermal(np.zeros(3), np.full(3, h), np.full(3, 1e-3, np.float32),
+                                  np.ones(3), np.full(3, T0), dt)
+        assert np.all(np.abs(y1 - 1.0) < 1e-12)
+        assert np.allclose(T1, T0 + 2.0 * h * dt / (3.0 * kB), rtol=1e-12)
+
+
+def _residuals(o, gamma, heat, nH, y0, T0, dt, y1, T1, diffuse=False):
+    """The two implicit equations evaluated with the pinned coefficients."""
+    kB = 1.380649e-16
+    nh = float(nH)
+    aR = oracle.rate("alpha_A" if diffuse else "alpha_B", T0) * nh * dt
+    c = oracle.rate("coll_ion", T0) * nh * dt
+    K = SIGMA_CM2 * gamma * dt
+    ry = y1 - y0 - (-K * y1 - c * y1 * (1 - y1) + aR * (1 - y1) ** 2)
+    x0, x1 = 1 - y0, 1 - y1
+    ne, npr, nhi = x1 * nh, x1 * nh, y1 * nh
+    lam = ne * npr * (oracle.rate("rec_cool_A" if diffuse else "rec_cool_B", T1) +
+                      oracle.rate("free_free_cool", T1)) + \
+        ne * nhi * (oracle.rate("coll_ion_cool", T1) + oracle.rate("coll_exc_cool", T1))
+    du = 1.5 * kB * nh * ((1 + x1) * T1 - (1 + x0) * T0)
+    rT = du - dt * (nhi * heat - lam)
+    return ry, rT, abs(du) + dt * (abs(nhi * heat) + lam)
+
+
+@pytest.mark.parametrize("gamma,heat,y0,T0", [(1e-13 / SIGMA_CM2, 1e-24, 1.0, 1e4),
+                                              (1e-12 / SIGMA_CM2, 8e-24, 0.3, 3e4),
+                                              (0.0, 0.0, 0.1, 5e4),
+                                              (1e-15 / SIGMA_CM2, 1e-26, 0.7, 800.0)])
+def test_thermal_step_solves_both_implicit_equations(gamma, heat, y0, T0):
+    """The update is backward Euler in both y and T: the new state satisfies
+    the ionisation balance at T0 and the energy balance at (T1, x1), with
+    recombination, free-free, collisional excitation and ionisation cooling
+    assembled from the pinned coefficients (n_e n_p and n_e n_HI)."""
+    o = _thermal_oracle()
+    nH = np.float32(1e-3)
+    for dt in (1e11, 3.15576e13, 1e15):
+        y1, T1 = o.ionize_thermal(np.full(3, gamma), np.full(3, heat), np.full(3, nH),
+                                  np.full(3, y0), np.full(3, T0), dt)
+        ry, rT, scale = _residuals(o, gamma, heat, nH, y0, T0, dt, y1[0], T1[0])
+        assert abs(ry) < 1e-12 * max(1.0, abs(y1[0])), (dt, ry)
+        if 10.0 < T1[0] < 1e9:
+            assert abs(rT) < 1e-9 * scale, (dt, rT, scale)
+
+
+def test_thermal_equilibrium_of_photoionised_gas():
+    """Optically thin gas under a constant ionising flux whose photoelectrons
+    carry 5 eV each settles where photoionisation balances recombination and
+    photoheating balances the cooling; the long-step update lands there."""
+    o = _thermal_oracle()
+    nH = np.float32(1e-3)
+    k = 1e-12
+    h = k * 5.0 * 1.602176634e-12
+    y, T = np.ones(1), np.full(1, 1e4)
+    for _ in range(100):
+        y, T = o.ionize_thermal(np.array([k / SIGMA_CM2]), np.array([h]), np.array([nH]), y, T,
+                                1e16)
+    ry, rT, scale = _residuals(o, k / SIGMA_CM2, h, nH, y[0], T[0], 1e16, y[0], T[0])
+    x = 1 - y[0]
+    aB = oracle.rate("alpha_B", T[0])
+    assert abs(k * y[0] + oracle.rate("coll_ion", T[0]) * float(nH) * x * y[0] -
+               aB * float(nH) * x * x) < 1e-6 * k * y[0]
+    assert abs(rT) < 1e-6 * scale
+    assert 1.5e4 < T[0] < 4e4 and y[0] < 1e-3
+
+
+def test_thermal_emitters_use_the_local_alpha_1():
+    """In the diffuse case the emitters' luminosity takes alpha_A(T) -
+    alpha_B(T) at each particle's temperature (Section 4.1 with the rate
+    fits), and the self term of the update does too."""
+    pos, h, src, L = _lattice_problem(5, 2.0, 28, n_s=1)
+    n = pos.shape[1]
+    V = np.full(n, (2.0 / 5) ** 3)
+    o = oracle.Oracle(pos, h, src, L, V, diffuse=True, **PHYS)
+    rng = np.random.default_rng(8)
+    y = rng.uniform(0.1, 0.9, n)
+    T = rng.uniform(5e3, 5e4, n)
+    nH = np.full(n, 1e-2, np.float32)
+    o.set_emitters_T(y, nH, T)
+    a1 = np.array([oracle.rate("alpha_A", t) - oracle.rate("alpha_B", t) for t in T])
+    ref = a1 * ((1 - y) * nH.astype(np.float64)) ** 2 * V * KPC_CM ** 3
+    assert np.allclose(o.emitter_L(), ref, rtol=1e-12)
+    ks_T, _ = o.self_terms_T(nH, y, T)
+    ks_c, _ = o.self_terms(nH, y)
+    assert np.allclose(ks_T / ks_c, a1 / (ALPHA_A - ALPHA_B), rtol=1e-12)
