@@ -83,6 +83,11 @@ def parse():
     ap.add_argument("--serve-low-requests", type=int, default=96)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-log2np", default="15,21")
+    ap.add_argument("--serve-small-log2np", default="11,15",
+                    help="particle counts of the small-request stream (log2 range)")
+    ap.add_argument("--serve-small-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-small-requests", type=int, default=512)
+    ap.add_argument("--serve-small-workers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -658,16 +663,32 @@ def diffuse_workload(S, dev, args, T, T_rec=0.0):
 def serving(args):
     """Continuous batching vs one solve at a time on the same Poisson stream
     of requests of mixed size (real-time replay, 150 GB budget), at an
-    arrival rate above one GPU's capacity and at one below it."""
+    arrival rate above one GPU's capacity and at one below it; and a stream
+    of small requests, where a solve is bound by launches and host round
+    trips, served by more workers with the autotuned knobs of each problem
+    class (tuned before the stream starts)."""
+    from paper_1005_5312_gb300.autotune import Tuner
     from paper_1005_5312_gb300.serve import Server, make_requests, summarize
     lo, hi = (float(x) for x in args.serve_log2np.split(","))
+    slo, shi = (float(x) for x in args.serve_small_log2np.split(","))
     out = {"workers": args.serve_workers, "budget_gb": 150}
-    for key, n_req, rate in (("saturated", args.serve_requests, args.serve_rate),
-                             ("below_capacity", args.serve_low_requests, args.serve_low_rate)):
-        reqs = make_requests(n_req, rate_hz=rate, log2_np=(lo, hi))
+    small = make_requests(args.serve_small_requests, rate_hz=args.serve_small_rate,
+                          log2_np=(slo, shi), seed=53125)
+    tuner = Tuner()
+    t0 = time.perf_counter()
+    tuned = tuner.tune_requests(small, max_classes=24)
+    tune_s = time.perf_counter() - t0
+    for key, reqs, workers_served, tnr in (
+            ("saturated", make_requests(args.serve_requests, rate_hz=args.serve_rate,
+                                        log2_np=(lo, hi)), args.serve_workers, None),
+            ("below_capacity", make_requests(args.serve_low_requests,
+                                             rate_hz=args.serve_low_rate, log2_np=(lo, hi)),
+             args.serve_workers, None),
+            ("small_requests", small, args.serve_small_workers, tuner)):
         res = {}
-        for name, workers in (("plain", 1), ("served", args.serve_workers)):
-            srv = Server(workers=workers, budget_bytes=150e9)
+        for name, workers in (("plain", 1), ("served", workers_served)):
+            srv = Server(workers=workers, budget_bytes=150e9,
+                         tuner=tnr if name == "served" else None)
             # warm the workers' contexts and pools on a small request
             srv.serve(make_requests(workers, rate_hz=1e9, log2_np=(14, 14), seed=1),
                       realtime=False)
@@ -677,13 +698,18 @@ def serving(args):
             res[name]["context_trims"] = srv.trims
             res[name]["oom_retries"] = srv.retries
         n_p = [r.n_p for r in reqs]
-        out[key] = {"workload": f"{len(reqs)} requests, Poisson {rate:g}/s, "
-                                f"N_p=2^U({lo:g},{hi:g}), N_s=e^U(0,ln N_p), uniform|clumpy, "
+        rate = len(reqs) / max(r.t_arrive for r in reqs)
+        a, b = (slo, shi) if key == "small_requests" else (lo, hi)
+        out[key] = {"workload": f"{len(reqs)} requests, Poisson {rate:.3g}/s, "
+                                f"N_p=2^U({a:g},{b:g}), N_s=e^U(0,ln N_p), uniform|clumpy, "
                                 f"theta in {{0.5,1}}, 1 step each",
-                    "mean_n_p": float(np.mean(n_p)), "served": res["served"],
-                    "plain": res["plain"],
+                    "mean_n_p": float(np.mean(n_p)), "workers": workers_served,
+                    "served": res["served"], "plain": res["plain"],
                     "solves_per_s_vs_plain": res["served"]["solves_per_s"] /
                     res["plain"]["solves_per_s"]}
+    out["small_requests"]["autotuner"] = {"classes_tuned": len(tuned), "tuning_s": tune_s,
+                                          "knobs": "march_group, ptree_leaf, row_warps",
+                                          "tuned_outside_the_stream": True}
     return out
 
 

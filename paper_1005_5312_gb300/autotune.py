@@ -93,3 +93,23 @@ class Tuner:
         best, _, _ = coordinate_descent(time_fn)
         self.cache[problem_class(n_p, int(src_L.shape[0]), theta, diffuse)] = best
         return best
+
+    def tune_requests(self, requests, max_classes: int = 24, repeats: int = 2) -> list:
+        """Tune the problem classes of a request stream (the most frequent
+        first, at most max_classes), each on its first request; returns the
+        classes tuned."""
+        counts = {}
+        first = {}
+        for r in requests:
+            k = problem_class(r.n_p, r.n_s, r.theta)
+            counts[k] = counts.get(k, 0) + 1
+            first.setdefault(k, r)
+        done = []
+        for k in sorted(counts, key=lambda q: -counts[q])[:max_classes]:
+            if k in self.cache:
+                continue
+            r = first[k]
+            nHI = (r.y0 * r.n_H.astype("float64")).astype("float32")
+            self.tune(r.pos, r.h, r.src_pos, r.src_L, r.theta, nHI, repeats=repeats)
+            done.append(k)
+        return done
