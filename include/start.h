@@ -153,6 +153,17 @@ typedef struct start_params {
                               ionisation cooling; the emitters use
                               alpha_1(T) = alpha_A(T) - alpha_B(T).  The rate
                               fits are those of start_ionize's comment */
+    int lum_kernel;        /* diffuse case.  0: an emitter cell's luminosity is
+                              the sum of its members' (Section 2.2.2, Eq. ssum).
+                              1: the kernel-weighted form Section 2.2.2 offers as
+                              an alternative, read with the members' emissivity
+                              L_j / V_j in place of L_j and the cell's volume as
+                              the factor that makes it a luminosity:
+                              L = l^3 sum_j (L_j/V_j) W(|r - r_j|, l) / sum_j
+                              W(|r - r_j|, l) over the cell's members, r the
+                              cell's luminosity centre, W the cubic spline of
+                              start_sph_density with h = the cell's edge l; a
+                              cell of one member keeps its luminosity */
 } start_params;
 
 /* Counters of the last start_rt_solve. */

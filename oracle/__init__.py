@@ -37,7 +37,7 @@ class OrcParams(C.Structure):
     _fields_ = [("sigma_cm2", C.c_double), ("len_unit_cm", C.c_double),
                 ("alpha_A", C.c_double), ("alpha_B", C.c_double),
                 ("src_leaf", C.c_int), ("ptree_leaf", C.c_int),
-                ("diffuse", C.c_int), ("pad_", C.c_int), ("T_rec", C.c_double)]
+                ("diffuse", C.c_int), ("lum_kernel", C.c_int), ("T_rec", C.c_double)]
 
 
 _lib = None
@@ -149,11 +149,12 @@ class Oracle:
     """
 
     def __init__(self, pos, h, src_pos, src_L, V=None, *, sigma_cm2, len_unit_cm,
-                 alpha_A, alpha_B, diffuse=False, src_leaf=1, ptree_leaf=8, T_rec=0.0):
+                 alpha_A, alpha_B, diffuse=False, src_leaf=1, ptree_leaf=8, T_rec=0.0,
+                 lum_kernel=0):
         self.lib = _load()
         self.params = OrcParams(sigma_cm2, len_unit_cm, alpha_A, alpha_B,
-                                int(src_leaf), int(ptree_leaf), int(bool(diffuse)), 0,
-                                float(T_rec))
+                                int(src_leaf), int(ptree_leaf), int(bool(diffuse)),
+                                int(lum_kernel), float(T_rec))
         self.h_ = self.lib.orc_create(C.byref(self.params))
         self.diffuse = bool(diffuse)
         self.pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(3, -1)

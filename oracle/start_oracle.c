@@ -77,7 +77,8 @@ typedef struct {
     int src_leaf;        /* max sources per source-tree leaf (paper: 1) */
     int ptree_leaf;      /* max particles per particle-tree leaf */
     int diffuse;         /* 1: every particle emits recombination photons */
-    int pad_;
+    int lum_kernel;      /* 1: kernel-weighted emissivity for the emitter cells'
+                            luminosities (kernel_luminosities) */
     double T_rec;        /* 0: recombination photons at nu_L; else the gas
                             temperature (K) that sets their band width k T / h
                             (Section 4.1) */
@@ -581,6 +582,40 @@ void orc_nbr_get(const orc *o, long *off, long *idx)
     memcpy(idx, o->nb_idx, orc_nbr_total(o) * sizeof(long));
 }
 
+/* The kernel-weighted form of a virtual source's luminosity (Section 2.2.2
+ * offers L = sum_j L_j W(r - r_j) / sum_j W(r - r_j) as an alternative).
+ * Reading: the weighted quantity is the emissivity L_j / V_j (V_j = m_j /
+ * rho_j, the particle's volume), so the weighted mean is an emissivity and
+ * the cell's volume l^3 turns it into the cell's luminosity:
+ *   L_cell = l^3 sum_j (L_j / V_j) W(|r_c - r_j|, l) / sum_j W(|r_c - r_j|, l)
+ * over the cell's members j, r_c the cell's luminosity centre as stored
+ * (float32), W the cubic spline with smoothing length h = l (its support 2l
+ * reaches every member from any point of the cell), for every cell of more
+ * than one member; a single-member cell keeps its member's luminosity.  A
+ * uniform emissivity gives l^3 times it, the summed luminosity of a cell
+ * that its members fill.  Emitter tree only (its members are SPH particles
+ * with volumes); the centres keep the luminosity-weighted form. */
+double orc_spline_w(double r, double h);
+
+static void kernel_luminosities(orc *o)
+{
+    otree *t = &o->et;
+    for (long n = 0; n < t->n; ++n) {
+        if (t->count[n] < 2) continue;
+        double l = t->edge[n];
+        double cx = t->cen[3 * n], cy = t->cen[3 * n + 1], cz = t->cen[3 * n + 2];
+        double sw = 0.0, se = 0.0;
+        for (long r = t->first[n]; r < t->first[n] + t->count[n]; ++r) {
+            long j = o->pperm[r];
+            double d = sqrt(d2_64(o->px[j], o->py[j], o->pz[j], cx, cy, cz));
+            double w = orc_spline_w(d, l);
+            sw += w;
+            se += (o->eL[j] / o->V[j]) * w;
+        }
+        if (sw > 0.0) t->L[n] = l * l * l * (se / sw);
+    }
+}
+
 /* Recombination emitters (Section 4.1): N_rec,j = alpha_1 n_e n_p V_j with
  * n_e = n_p = x n_H (hydrogen only), alpha_1 = alpha_A - alpha_B; then the
  * emitter tree's moments.  y is the neutral fraction in input order. */
@@ -593,6 +628,7 @@ void orc_set_emitters(orc *o, const double *y, const float *nH)
         o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);
     }
     if (o->et.n) moments_node(&o->et, 0, o->pperm, o->px, o->py, o->pz, o->eL);
+    if (o->et.n && o->p.lum_kernel) kernel_luminosities(o);
 }
 
 double orc_emitter_L(const orc *o, long i) { return o->eL[i]; }
@@ -1133,6 +1169,7 @@ void orc_set_emitters_T(orc *o, const double *y, const float *nH, const double *
         o->eL[i] = a1 * ne * ne * (o->V[i] * lu3);
     }
     if (o->et.n) moments_node(&o->et, 0, o->pperm, o->px, o->py, o->pz, o->eL);
+    if (o->et.n && o->p.lum_kernel) kernel_luminosities(o);
 }
 
 /* One implicit step of hydrogen and its gas temperature over dt, per

@@ -336,7 +336,7 @@ static void release_all(start_ctx *c)
                    &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord, &c->m_nx0, &c->m_dl,
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_hard, &c->m_part, &c->m_table,
-                   &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc};
+                   &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc, &c->klum_big};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);
@@ -406,6 +406,7 @@ static int check_params(start_params &d)
     if (d.march_mode != 0 && d.march_mode != 1) return START_EINVAL;
     if (d.row_warps != 0 && d.row_warps != 4 && d.row_warps != 8) return START_EINVAL;
     if (d.thermal != 0 && d.thermal != 1) return START_EINVAL;
+    if (d.lum_kernel != 0 && d.lum_kernel != 1) return START_EINVAL;
     if (d.row_warps == 0) d.row_warps = 8;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
     if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;

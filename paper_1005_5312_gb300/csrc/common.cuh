@@ -148,6 +148,7 @@ struct start_ctx {
     // groups are planned from, and every target's running Gamma sums
     unsigned grp_s[2] = {0u, 0xffffffffu}, grp_e[2] = {0u, 0xffffffffu};
     st::DBuf g_hist, gacc;
+    st::DBuf klum_big;  // emitter cells whose kernel-weighted luminosity takes a block
 
     // memoised march: per chain link (virtual source, particle)
     st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_hard, m_part, m_table, m_nx0, m_dl;
@@ -206,7 +207,8 @@ enum Counter {
     C_WALK_OVER,  // one-walk lists: targets whose row exceeds the scratch row
     C_LEVEL,      // memoised march: device frontier {fbase, nf, total} (3 words)
     C_WALK_FB_GROUP = C_LEVEL + 3,   // opening tests re-decided by the walks of a group
-    C_COUNT = 24
+    C_KLUM_BIG,   // kernel-weighted cell luminosities: cells left to a block each
+    C_COUNT = 32
 };
 
 // ---------------------------------------------------------------- error helpers

@@ -418,6 +418,147 @@ __global__ void k_emitters(const double *y, const float *nH, const double *V, lo
     eLs[i] = __double2float_rn(__ddiv_rn(L, L_unit));
 }
 
+// The kernel-weighted luminosity of the emitter cells (start_params.
+// lum_kernel): L = l^3 sum_j e_j w_j / sum_j w_j over a cell's members, e_j =
+// L_j / V_j, w_j the cubic spline's shape at |r_c - r_j| / l (its
+// normalisation cancels), r_c the stored luminosity centre.  A warp per
+// cell, or a block per cell of more than kKernelLumWarp members; each
+// thread sums its members (strided, compensated FP32), the partial sums are
+// combined in a fixed order in FP64, so the result does not depend on the
+// schedule.  Single-member cells are left as they are.
+constexpr u32 kKernelLumWarp = 2048;
+
+__device__ __forceinline__ float spline_shape(float q)
+{
+    if (q < 1.f) return 1.f - 1.5f * q * q + 0.75f * q * q * q;
+    if (q < 2.f) {
+        const float t = 2.f - q;
+        return 0.25f * t * t * t;
+    }
+    return 0.f;
+}
+
+// Compensated sums (sum of w, sum of e w) of members [m0, m1) taken with
+// stride st from m0 + k.
+__device__ __forceinline__ void kernel_lum_part(const float4 *pq, const float *eLs,
+                                                const double *V, float4 cen, float inv_l, u32 m0,
+                                                u32 m1, u32 k, u32 st, double &sw, double &se)
+{
+    float a = 0.f, ca = 0.f, b = 0.f, cb = 0.f;
+    for (u32 r = m0 + k; r < m1; r += st) {
+        const float4 p = pq[r];
+        const float dx = p.x - cen.x, dy = p.y - cen.y, dz = p.z - cen.z;
+        const float w = spline_shape(sqrtf(dx * dx + dy * dy + dz * dz) * inv_l);
+        const float e = eLs[r] / (float)V[r];
+        float y = w - ca, t = a + y;
+        ca = (t - a) - y;
+        a = t;
+        y = e * w - cb;
+        t = b + y;
+        cb = (t - b) - y;
+        b = t;
+    }
+    sw = (double)a - (double)ca;
+    se = (double)b - (double)cb;
+}
+
+__global__ void __launch_bounds__(256) k_kernel_lum_warp(const uint4 *meta, const double *cube,
+                                                         float4 *vsrc, double *L, long long n,
+                                                         const float4 *pq, const float *eLs,
+                                                         const double *V, double L_unit,
+                                                         u32 *big, unsigned long long *nbig)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) / 32;
+    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; c < n; c += nw) {
+        const uint4 mt = meta[c];
+        if (mt.z < 2u) continue;                    // warp-uniform
+        if (mt.z > kKernelLumWarp) {
+            if (lane == 0) big[atomicAdd(nbig, 1ull)] = (u32)c;
+            continue;
+        }
+        const double l = cube[4 * (size_t)c + 3];
+        const float4 cen = vsrc[c];
+        double sw, se;
+        kernel_lum_part(pq, eLs, V, cen, (float)(1.0 / l), mt.y, mt.y + mt.z, (u32)lane, 32u, sw,
+                        se);
+        for (int o = 16; o; o >>= 1) {
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            se += __shfl_xor_sync(0xffffffffu, se, o);
+        }
+        if (lane == 0 && sw > 0.0) {
+            const double Ls = l * l * l * (se / sw);   // in units of L_unit
+            L[c] = Ls * L_unit;
+            vsrc[c].w = __double2float_rn(Ls);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_kernel_lum_block(const uint4 *meta, const double *cube,
+                                                          float4 *vsrc, double *L,
+                                                          const float4 *pq, const float *eLs,
+                                                          const double *V, double L_unit,
+                                                          const u32 *big,
+                                                          const unsigned long long *nbig)
+{
+    __shared__ double psw[8], pse[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long nb = (long long)*nbig;
+    for (long long q = blockIdx.x; q < nb; q += gridDim.x) {
+        const u32 c = big[q];
+        const uint4 mt = meta[c];
+        const double l = cube[4 * (size_t)c + 3];
+        const float4 cen = vsrc[c];
+        double sw, se;
+        kernel_lum_part(pq, eLs, V, cen, (float)(1.0 / l), mt.y, mt.y + mt.z, threadIdx.x,
+                        blockDim.x, sw, se);
+        for (int o = 16; o; o >>= 1) {
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            se += __shfl_xor_sync(0xffffffffu, se, o);
+        }
+        if (lane == 0) {
+            psw[w] = sw;
+            pse[w] = se;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                a += psw[k];
+                b += pse[k];
+            }
+            if (a > 0.0) {
+                const double Ls = l * l * l * (b / a);
+                L[c] = Ls * L_unit;
+                vsrc[c].w = __double2float_rn(Ls);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static int kernel_luminosities(start_ctx *c)
+{
+    Tree &t = c->et;
+    if (t.n == 0) return START_OK;
+    unsigned long long *ctr = c->counters.as<unsigned long long>();
+    ST_TRY(ensure(c->klum_big, (size_t)t.n * sizeof(u32)));
+    ST_CUDA(c, cudaMemsetAsync(ctr + C_KLUM_BIG, 0, sizeof(unsigned long long), c->stream));
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (nsm <= 0) nsm = 1;
+    k_kernel_lum_warp<<<grid_for(t.n * 32, 256, (long long)nsm * 64), 256, 0, c->stream>>>(
+        t.meta.as<uint4>(), t.cube.as<double>(), t.vsrc.as<float4>(), t.L.as<double>(), t.n,
+        c->pq.as<float4>(), c->eLs.as<float>(), c->V.as<double>(), c->p.L_unit,
+        c->klum_big.as<u32>(), ctr + C_KLUM_BIG);
+    k_kernel_lum_block<<<(unsigned)(nsm * 4), 256, 0, c->stream>>>(
+        t.meta.as<uint4>(), t.cube.as<double>(), t.vsrc.as<float4>(), t.L.as<double>(),
+        c->pq.as<float4>(), c->eLs.as<float>(), c->V.as<double>(), c->p.L_unit,
+        c->klum_big.as<u32>(), ctr + C_KLUM_BIG);
+    c->launches += 2;
+    return cuda_check(c, cudaGetLastError(), "k_kernel_lum");
+}
+
 int refresh_emitters(start_ctx *c)
 {
     if (!c->diffuse || c->np == 0) return START_OK;
@@ -431,6 +572,7 @@ int refresh_emitters(start_ctx *c)
     ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_TRY(tree_moments(c, c->et, c->pq.as<float4>(), c->eL.as<double>(), c->p.L_unit));
+    if (c->p.lum_kernel) ST_TRY(kernel_luminosities(c));
     phase_mark(c, START_PHASE_EMIT, true);
     return START_OK;
 }

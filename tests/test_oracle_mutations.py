@@ -106,6 +106,18 @@ MUTATIONS = [
      "double a1 = orc_rate(0, T[i]) - orc_rate(1, T[i]);\n        double ne",
      "double a1 = orc_rate(0, T[i]);\n        double ne",
      [pins.test_thermal_emitters_use_the_local_alpha_1]),
+    ("kernel_lum_no_cell_volume",
+     "if (sw > 0.0) t->L[n] = l * l * l * (se / sw);",
+     "if (sw > 0.0) t->L[n] = l * l * (se / sw);",
+     [pins.test_kernel_cell_luminosity_uniform_emissivity]),
+    ("kernel_lum_luminosity_not_emissivity",
+     "se += (o->eL[j] / o->V[j]) * w;",
+     "se += o->eL[j] * w;",
+     [pins.test_kernel_cell_luminosity_uniform_emissivity]),
+    ("kernel_lum_half_smoothing_length",
+     "double w = orc_spline_w(d, l);",
+     "double w = orc_spline_w(d, 0.5 * l);",
+     [pins.test_kernel_cell_luminosity_bruteforce]),
     ("gamma_no_4pi",
      "g += L * exp(-tau) / (4.0 * ORC_PI * r2 * lu * lu);",
      "g += L * exp(-tau) / (ORC_PI * r2 * lu * lu);",

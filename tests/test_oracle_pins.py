@@ -1083,3 +1083,75 @@ def test_thermal_emitters_use_the_local_alpha_1():
     ks_T, _ = o.self_terms_T(nH, y, T)
     ks_c, _ = o.self_terms(nH, y)
     assert np.allclose(ks_T / ks_c, a1 / (ALPHA_A - ALPHA_B), rtol=1e-12)
+
+
+
+# ---------------------------------------------------------------- kernel-weighted cells
+def _kernel_problem(nside=12, box=3.0, seed=33, eps=None):
+    pos, h, src, L = _lattice_problem(nside, box, seed, n_s=1)
+    n = pos.shape[1]
+    rng = np.random.default_rng(seed)
+    # volumes that fill the root cube (the frame: the particles' and the
+    # source's bounding cube), so that cells are filled by their members
+    p = np.concatenate([pos, src], axis=1).astype(np.float64)
+    side = (p.max(1) - p.min(1)).max()
+    V = side ** 3 / n * rng.uniform(0.9, 1.1, n)
+    nH = np.full(n, 1e-2, np.float32)
+    o = oracle.Oracle(pos, h, src, L, V, diffuse=True, lum_kernel=1, **PHYS)
+    if eps is None:        # the same ionisation: the same emissivity alpha_1 n_e n_p
+        y = np.full(n, 0.5)
+    else:
+        y = eps(pos, V)
+    o.set_emitters(y, nH)
+    return o, pos, V, y, nH
+
+
+def test_kernel_cell_luminosity_uniform_emissivity():
+    """Section 2.2.2's kernel-weighted form (emissivity reading): with a
+    uniform emissivity every cell of two or more members gets exactly l^3
+    times it, and over a level of cells that its members fill this is their
+    summed luminosity to within the lattice's discretisation; single-member
+    cells keep their member's luminosity."""
+    o, pos, V, y, nH = _kernel_problem()
+    eL = o.emitter_L()
+    e = eL / V
+    assert np.allclose(e, e[0], rtol=1e-12)
+    t = o.tree(2)
+    perm = o.perm(0)
+    for n in range(len(t["level"])):
+        members = perm[t["first"][n]:t["first"][n] + t["count"][n]]
+        if t["count"][n] == 1:
+            assert t["L"][n] == eL[members[0]]
+        else:
+            l = t["cube"][n, 3]
+            assert abs(t["L"][n] / (l ** 3 * e[0]) - 1) < 1e-12
+    for level in (1, 2):
+        sel = (t["level"] == level) & (t["count"] > 1)
+        tot = sum(eL[perm[t["first"][n]:t["first"][n] + t["count"][n]]].sum()
+                  for n in np.nonzero(sel)[0])
+        assert abs(t["L"][sel].sum() / tot - 1) < 0.05, level
+
+
+def test_kernel_cell_luminosity_bruteforce():
+    """Non-uniform emissivity: each cell's value is the definition evaluated
+    directly over its members (cubic spline with h = the cell's edge, the
+    stored float32 centre)."""
+    def eps(pos, V):
+        return np.clip(0.2 + 0.6 * pos[0].astype(np.float64) / 3.0, 0.0, 1.0)
+    o, pos, V, y, nH = _kernel_problem(eps=eps)
+    eL = o.emitter_L()
+    t = o.tree(2)
+    perm = o.perm(0)
+    p = pos.astype(np.float64)
+    checked = 0
+    for n in range(0, len(t["level"]), 7):
+        if t["count"][n] < 2:
+            continue
+        m = perm[t["first"][n]:t["first"][n] + t["count"][n]]
+        l = t["cube"][n, 3]
+        d = np.sqrt(((p[:, m] - t["cen"][n].astype(np.float64)[:, None]) ** 2).sum(0))
+        w = np.array([oracle.spline_w(di, l) for di in d])
+        ref = l ** 3 * (eL[m] / V[m] * w).sum() / w.sum()
+        assert abs(t["L"][n] / ref - 1) < 1e-12
+        checked += 1
+    assert checked > 20
