@@ -164,6 +164,10 @@ typedef struct start_params {
                               cell's luminosity centre, W the cubic spline of
                               start_sph_density with h = the cell's edge l; a
                               cell of one member keeps its luminosity */
+    int walk_warp;         /* 1: the 32 targets of a warp walk the trees together
+                              (one traversal, ballot masks per depth; default);
+                              0: one independent walk per thread.  Does not
+                              change any result */
 } start_params;
 
 /* Counters of the last start_rt_solve. */

@@ -3,7 +3,8 @@
 * ``ptree_leaf``  -- particle-tree leaf size (neighbour search),
 * ``march_group`` -- lanes cooperating on one neighbour-list evaluation of
   the later chain levels (the warp-per-target grouping of the march),
-* ``row_warps``   -- the first hop's tile shape: target rows per block.
+* ``row_warps``   -- the first hop's tile shape: target rows per block,
+* ``walk_warp``   -- one tree walk per warp of 32 targets, or per thread.
 
 Each knob is varied in turn around the current best (coordinate descent),
 timing one full step (build + solve) per candidate with CUDA events, and the
@@ -22,8 +23,9 @@ SEARCH_SPACE = {
     "march_group": (1, 2, 4, 8),
     "ptree_leaf": (8, 16, 32),
     "row_warps": (4, 8),
+    "walk_warp": (1, 0),
 }
-DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "row_warps": 8}
+DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "row_warps": 8, "walk_warp": 1}
 
 
 def problem_class(n_p: int, n_s: int, theta: float, diffuse: bool = False) -> tuple:

@@ -382,6 +382,7 @@ int start_default_params(start_params *p)
     p->march_group = 2;
     p->march_mode = 1;
     p->row_warps = 8;
+    p->walk_warp = 1;
     p->sigma_cm2 = 6.3e-18;
     p->len_unit_cm = 3.0857e21;
     p->L_unit = 1e48;
@@ -407,6 +408,7 @@ static int check_params(start_params &d)
     if (d.row_warps != 0 && d.row_warps != 4 && d.row_warps != 8) return START_EINVAL;
     if (d.thermal != 0 && d.thermal != 1) return START_EINVAL;
     if (d.lum_kernel != 0 && d.lum_kernel != 1) return START_EINVAL;
+    if (d.walk_warp != 0 && d.walk_warp != 1) return START_EINVAL;
     if (d.row_warps == 0) d.row_warps = 8;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
     if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;

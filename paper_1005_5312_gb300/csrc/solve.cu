@@ -37,6 +37,7 @@ struct TreeView {
     const double *cube;
     u32 n;
     u32 lo = 0, hi = 0xffffffffu;
+    const int *level = nullptr;   // depth of every cell (the warp-cooperative walk)
 };
 
 // Canonical virtual-source ids (the memoised march's numbering): source-tree
@@ -158,6 +159,83 @@ __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2
     }
 }
 
+// The same walk with the 32 targets of a warp sharing one traversal: the
+// warp visits, in depth-first order, every cell that any of its lanes
+// reaches; a lane takes part at a cell only if it opened every ancestor (the
+// lanes active at each depth are kept as ballot masks, indexed by the cell's
+// depth, so a jump along a skip pointer restores the mask of the level it
+// lands on).  Each lane still makes its own decisions in the same order, so
+// its row is exactly walk_tree's; the warp reads each cell record once (a
+// broadcast) instead of each lane at its own time.  live: this lane has a
+// target; every lane of the warp calls it.
+template <int MODE, class Rows>
+__device__ __forceinline__ void walk_tree_warp(const TreeView &t, float4 p, bool live, float th2f,
+                                               double th2d, float cmag, u32 self, u32 tag,
+                                               CanonBase cb, u32 &c, u64 &w, u64 wend,
+                                               Rows &rows, unsigned &fb)
+{
+    constexpr bool FILL = MODE != 0;
+    const u32 okey = tag ? 0x80000000u : 0u;
+    const u32 end = t.hi < t.n ? t.hi : t.n;
+    const unsigned me = 1u << (threadIdx.x & 31);
+    unsigned act[kLevels + 2];
+    act[0] = __ballot_sync(0xffffffffu, live);
+    u32 n = act[0] ? 0u : end;
+    while (n < end) {                               // warp-uniform
+        const uint4 mt = t.meta[n];
+        if (mt.x <= t.lo) {
+            n = mt.x;
+            continue;
+        }
+        const int lv = t.level[n];
+        const unsigned A = act[lv];
+        const bool mine = (A & me) != 0;
+        int a = 0;
+        if (mine) {
+            a = accept_32(t.box[n], th2f, p.x, p.y, p.z, cmag);
+            if (a < 0) {
+                a = accept_64(t.cube + 4 * (size_t)n, th2d, p.x, p.y, p.z) ? 1 : 0;
+                ++fb;
+            }
+        }
+        const bool in = n >= t.lo;
+        if (mine && in) {
+            if (a) {
+                if (FILL) {
+                    if (w < wend) {
+                        u32 e = (MODE >= 2) ? ((mt.w && mt.z == 1u) ? cb.memb0 + mt.y
+                                                                    : cb.node0 + n)
+                                            : (n | tag);
+                        rows.put(w, e, okey | n);
+                    }
+                    ++w;
+                } else {
+                    ++c;
+                }
+            } else if (mt.w) {
+                for (u32 r = mt.y; r < mt.y + mt.z; ++r) {
+                    if (r == self) continue;
+                    if (FILL) {
+                        if (w < wend)
+                            rows.put(w, (MODE >= 2) ? cb.memb0 + r : (kEntrySrc | tag | r),
+                                     okey | n);
+                        ++w;
+                    } else {
+                        ++c;
+                    }
+                }
+            }
+        }
+        const unsigned open = __ballot_sync(0xffffffffu, mine && !a && !mt.w);
+        if (open) {
+            act[lv + 1] = open;
+            n = n + 1;
+        } else {
+            n = mt.x;
+        }
+    }
+}
+
 constexpr u32 kWalkRow = 1024;                 // scratch row of the one-walk lists
 constexpr size_t kWalkScratchMax = 1ull << 30;   // bytes: larger problems count first
 
@@ -186,24 +264,45 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
         if (k >= lo && k < hi) i = k;
     }
     unsigned fb = 0;
-    if (i >= 0) {
-        float4 p = pq[i];
-        u32 c = 0;
-        const u64 w0 = MODE == 3 ? (u64)(i - t0) * kWalkRow : (FILL ? off[i] - base : 0ull);
-        u64 w = w0;
-        const u64 wend = MODE == 3 ? w0 + kWalkRow : (FILL ? off[i + 1] - base : 0ull);
+    const bool live = i >= 0;
+    const bool warp = st_.level != nullptr;   // the warp-cooperative walk (both trees or none)
+    u32 c = 0;
+    const u64 w0 = !live ? 0ull
+                         : (MODE == 3 ? (u64)(i - t0) * kWalkRow : (FILL ? off[i] - base : 0ull));
+    u64 w = w0;
+    const u64 wend = !live ? 0ull
+                           : (MODE == 3 ? w0 + kWalkRow : (FILL ? off[i + 1] - base : 0ull));
+    if (live || warp) {                         // warp: every lane takes part
+        float4 p = live ? pq[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const u32 self = live ? (u32)i : kNone;
         if (MODE >= 2) {
             SlotRows rows{ent};
-            walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
-            walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, c, w, wend, rows,
-                            fb);
+            if (warp) {
+                walk_tree_warp<MODE>(st_, p, live, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend,
+                                     rows, fb);
+                walk_tree_warp<MODE>(et_, p, live, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w,
+                                     wend, rows, fb);
+            } else {
+                walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
+                walk_tree<MODE>(et_, p, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w, wend,
+                                rows, fb);
+            }
             rows.flush();
         } else {
             RawRows rows{ent, tgt, ord, (u32)i};
-            walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
-            walk_tree<MODE>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, ecb, c, w, wend, rows,
-                            fb);
+            if (warp) {
+                walk_tree_warp<MODE>(st_, p, live, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend,
+                                     rows, fb);
+                walk_tree_warp<MODE>(et_, p, live, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w,
+                                     wend, rows, fb);
+            } else {
+                walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
+                walk_tree<MODE>(et_, p, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w, wend,
+                                rows, fb);
+            }
         }
+    }
+    if (live) {
         if (MODE == 0) {
             cnt[i] = c;
         } else if (MODE == 3) {
@@ -745,16 +844,20 @@ static int ensure_pairs(start_ctx *c, unsigned long long n)
 
 // The trees as the walks of the current solve see them: restricted to the
 // current group of virtual sources while a grouped solve runs.
+// start_params.walk_warp selects the warp-cooperative walk (the cell depths
+// are given) or one independent walk per thread.
 static TreeView source_view(start_ctx *c)
 {
     return TreeView{c->stree.box.as<float4>(), c->stree.meta.as<uint4>(),
-                    c->stree.cube.as<double>(), (u32)c->stree.n, c->grp_s[0], c->grp_s[1]};
+                    c->stree.cube.as<double>(), (u32)c->stree.n, c->grp_s[0], c->grp_s[1],
+                    c->p.walk_warp ? c->stree.level.as<int>() : nullptr};
 }
 
 static TreeView emitter_view(start_ctx *c)
 {
     return TreeView{c->et.box.as<float4>(), c->et.meta.as<uint4>(), c->et.cube.as<double>(),
-                    (u32)(c->walk_emit ? c->et.n : 0), c->grp_e[0], c->grp_e[1]};
+                    (u32)(c->walk_emit ? c->et.n : 0), c->grp_e[0], c->grp_e[1],
+                    c->p.walk_warp ? c->et.level.as<int>() : nullptr};
 }
 
 // Interaction lists of every target (all pairs at once; introspection).

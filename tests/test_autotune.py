@@ -8,12 +8,12 @@ from paper_1005_5312_gb300.autotune import (DEFAULTS, SEARCH_SPACE, Tuner, coord
 
 
 def test_coordinate_descent_finds_the_separable_minimum():
-    target = {"march_group": 4, "ptree_leaf": 32, "row_warps": 4}
+    target = {"march_group": 4, "ptree_leaf": 32, "row_warps": 4, "walk_warp": 1}
     calls = []
 
     def cost(p):
         calls.append(p)
-        return sum((np.log2(p[k]) - np.log2(target[k])) ** 2 for k in target) + 1.0
+        return sum((np.log2(p[k] + 1) - np.log2(target[k] + 1)) ** 2 for k in target) + 1.0
 
     best, t, tried = coordinate_descent(cost)
     assert best == target and t == 1.0
@@ -43,7 +43,8 @@ def test_tuned_knobs_are_result_neutral():
     best = tuner.tune(w.pos, w.h, w.src_pos, w.src_L, 0.5, nHI, repeats=1)
     assert set(best) == set(DEFAULTS)
     out = []
-    for p in (DEFAULTS, best, {"march_group": 8, "ptree_leaf": 8, "row_warps": 4}):
+    for p in (DEFAULTS, best, {"march_group": 8, "ptree_leaf": 8, "row_warps": 4,
+                               "walk_warp": 0}):
         ctx = S.Context(**p)
         ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
         g = np.zeros(w.n_p, np.float32)

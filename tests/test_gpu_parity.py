@@ -522,6 +522,30 @@ def test_hop_cap_reports_echain(S, cfg1, mode):
     assert e.value.code == S.START_ECHAIN
 
 
+@pytest.mark.parametrize("diffuse", [False, True])
+def test_warp_cooperative_walk_is_result_neutral(S, cfg1, diffuse):
+    """One traversal per warp of 32 targets (walk_warp = 1) and one per thread
+    give the same interaction lists (checksums), the same rays and chain
+    links and bitwise the same Gamma, also when a split solve restricts the
+    walks to groups of virtual sources."""
+    w = random_workload(4001, 33, 21, diffuse=True) if diffuse else cfg1
+    out = []
+    for ww in (0, 1):
+        for max_pairs in (0, 60000):
+            ctx = S.Context(walk_warp=ww, max_pairs=max_pairs, ptree_leaf=PTREE_LEAF)
+            ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L, w.V if diffuse else None,
+                            diffuse=diffuse)
+            ctx.set_state(w.n_H, w.y0)
+            g = np.zeros(w.n_p, np.float32)
+            ctx.rt_solve(0.6, gamma_out=g)
+            out.append((ww, max_pairs, g, ctx.stats(), ctx.list_hashes(0.6)))
+    for ww, mp, g, st, (hs, cnt) in out[2:]:
+        ref = out[0] if mp == 0 else out[1]
+        assert np.array_equal(hs, ref[4][0]) and np.array_equal(cnt, ref[4][1])
+        assert st["rays"] == ref[3]["rays"] and st["hops"] == ref[3]["hops"]
+        assert np.array_equal(g, ref[2])
+
+
 def _depth_and_caps(S, w, mode, theta):
     """Solve with no hop cap, then with hop_cap = the longest chain (must pass,
     bitwise the same Gamma) and one less (must report START_ECHAIN)."""
