@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--theta2", type=float, default=1.0)
     ap.add_argument("--march-group", type=int, default=2)
-    ap.add_argument("--max-pairs", type=int, default=3 << 28,
-                    help="interaction pairs per chunk of the large run")
+    ap.add_argument("--max-pairs", type=int, default=1_500_000_000,
+                    help="interaction pairs per group of the large run (device memory of the "
+                         "march about 90 B per pair)")
     ap.add_argument("--nside", type=int, default=256,
                     help="lattice side of the headline workload (256: the benchmark; "
                          "smaller: profiling cases)")

@@ -111,10 +111,14 @@ typedef struct start_params {
                               (default 110; e^-110 is below float32's smallest
                               subnormal relative to any representable flux) */
     long long hop_cap;     /* max upstream steps per ray (0 = N_p + 1) */
-    long long max_pairs;   /* targets are solved in Morton-contiguous chunks of
-                              at most this many interaction pairs (bounds the
-                              device memory of a solve; 0 = 2^27).  Chains are
-                              shared only within a chunk */
+    long long max_pairs;   /* interaction pairs solved at once (bounds the device
+                              memory of a solve, about 90 B per pair; 0 = 2^27).
+                              A larger memoised solve is split by virtual source:
+                              groups of cells (depth-first index ranges) whose
+                              rows are walked and marched over every target at
+                              once, so chains are never cut; Gamma's additions
+                              are then grouped by them.  The per-ray march splits
+                              by Morton-contiguous target chunks instead */
     long long spin_cap;    /* max iterations of any device wait (reserved) */
     void *stream;          /* cudaStream_t to issue work on (NULL = default) */
     double T_eff;          /* 0: monochromatic sources at the Lyman limit (sigma_cm2);
@@ -165,9 +169,11 @@ typedef struct start_params {
                               start_sph_density with h = the cell's edge l; a
                               cell of one member keeps its luminosity */
     int walk_warp;         /* 1: the 32 targets of a warp walk the trees together
-                              (one traversal, ballot masks per depth; default);
-                              0: one independent walk per thread.  Does not
-                              change any result */
+                              (one traversal, ballot masks per depth); 0: one
+                              independent walk per thread (default: Morton-
+                              adjacent targets already walk nearly the same
+                              cells, and the shared traversal measured 3 %
+                              slower).  Does not change any result */
 } start_params;
 
 /* Counters of the last start_rt_solve. */

@@ -23,9 +23,9 @@ SEARCH_SPACE = {
     "march_group": (1, 2, 4, 8),
     "ptree_leaf": (8, 16, 32),
     "row_warps": (4, 8),
-    "walk_warp": (1, 0),
+    "walk_warp": (0, 1),
 }
-DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "row_warps": 8, "walk_warp": 1}
+DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "row_warps": 8, "walk_warp": 0}
 
 
 def problem_class(n_p: int, n_s: int, theta: float, diffuse: bool = False) -> tuple:

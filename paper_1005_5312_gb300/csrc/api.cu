@@ -382,7 +382,7 @@ int start_default_params(start_params *p)
     p->march_group = 2;
     p->march_mode = 1;
     p->row_warps = 8;
-    p->walk_warp = 1;
+    p->walk_warp = 0;
     p->sigma_cm2 = 6.3e-18;
     p->len_unit_cm = 3.0857e21;
     p->L_unit = 1e48;

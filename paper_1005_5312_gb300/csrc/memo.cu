@@ -1267,7 +1267,7 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     ST_CUDA(c, cudaMemcpyAsync(saved, ctr, C_COUNT * sizeof(unsigned long long),
                                cudaMemcpyDeviceToDevice, c->stream));
     // slot ids and table indices must stay below the pending flag (2^31)
-    const size_t cap_max = (1ull << 30) - 1;
+    const size_t cap_max = (1ull << 31) - 1;
     if ((size_t)m.npairs >= cap_max) return set_err(c, START_ERANGE, "too many chain links");
     cap = std::min(cap, cap_max);
     for (int attempt = 0; attempt < 5; ++attempt) {

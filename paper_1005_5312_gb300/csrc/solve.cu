@@ -845,7 +845,7 @@ static int ensure_pairs(start_ctx *c, unsigned long long n)
 // The trees as the walks of the current solve see them: restricted to the
 // current group of virtual sources while a grouped solve runs.
 // start_params.walk_warp selects the warp-cooperative walk (the cell depths
-// are given) or one independent walk per thread.
+// are given) or one independent walk per thread (the default).
 static TreeView source_view(start_ctx *c)
 {
     return TreeView{c->stree.box.as<float4>(), c->stree.meta.as<uint4>(),

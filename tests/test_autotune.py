@@ -44,7 +44,7 @@ def test_tuned_knobs_are_result_neutral():
     assert set(best) == set(DEFAULTS)
     out = []
     for p in (DEFAULTS, best, {"march_group": 8, "ptree_leaf": 8, "row_warps": 4,
-                               "walk_warp": 0}):
+                               "walk_warp": 1}):
         ctx = S.Context(**p)
         ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
         g = np.zeros(w.n_p, np.float32)
