@@ -687,9 +687,13 @@ def serving(args):
              args.serve_workers, None),
             ("small_requests", small, args.serve_small_workers, tuner)):
         res = {}
-        for name, workers in (("plain", 1), ("served", workers_served)):
+        arms = [("plain", 1, 0), ("served", workers_served, 0)]
+        if key == "small_requests":
+            arms.append(("served_batched", workers_served, 16))
+        for name, workers, bsz in arms:
             srv = Server(workers=workers, budget_bytes=150e9,
-                         tuner=tnr if name == "served" else None)
+                         tuner=tnr if name != "plain" else None, batch_small=bsz,
+                         small_n_p=1 << 16)
             # warm the workers' contexts and pools on a small request
             srv.serve(make_requests(workers, rate_hz=1e9, log2_np=(14, 14), seed=1),
                       realtime=False)
@@ -698,6 +702,8 @@ def serving(args):
             res[name] = summarize(r)
             res[name]["context_trims"] = srv.trims
             res[name]["oom_retries"] = srv.retries
+            if bsz:
+                res[name]["batches"] = srv.batches
         n_p = [r.n_p for r in reqs]
         rate = len(reqs) / max(r.t_arrive for r in reqs)
         a, b = (slo, shi) if key == "small_requests" else (lo, hi)
@@ -708,6 +714,10 @@ def serving(args):
                     "served": res["served"], "plain": res["plain"],
                     "solves_per_s_vs_plain": res["served"]["solves_per_s"] /
                     res["plain"]["solves_per_s"]}
+        if "served_batched" in res:
+            out[key]["served_batched"] = res["served_batched"]
+            out[key]["batched_solves_per_s_vs_plain"] = (res["served_batched"]["solves_per_s"] /
+                                                         res["plain"]["solves_per_s"])
     out["small_requests"]["autotuner"] = {"classes_tuned": len(tuned), "tuning_s": tune_s,
                                           "knobs": "march_group, ptree_leaf, row_warps",
                                           "tuned_outside_the_stream": True}

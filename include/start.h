@@ -250,6 +250,26 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
                       const float *src_pos, const double *src_L, long long n_s,
                       const double *V, unsigned flags);
 
+/* A batch of independent problems in one context, solved with shared
+ * launches: problem b has n_p[b] particles and n_s[b] point sources, its
+ * arrays given by pos[b] (SoA 3 x n_p[b]), h[b], src_pos[b], src_L[b] (host or
+ * device memory; NULL allowed for empty arrays).  Each problem is built on its
+ * own (its frame, source octree and neighbour lists) and the parts are
+ * stacked: the context then behaves as one problem of sum n_p particles and
+ * sum n_s sources whose particle arrays (n_H, y, n_HI, Gamma, T, ...) are the
+ * problems' concatenated in order, and every later call (start_set_state,
+ * start_rt_solve, start_ionize, ...) runs one set of kernels over all of
+ * them.  A target walks only its own problem's tree and marches only through
+ * its own problem's particles, so each problem's results are bitwise those of
+ * the same calls on it alone (as long as the batch is not split by max_pairs).
+ * Point sources only (no diffuse emitters); resident chains are not kept for
+ * a batch; the introspection of the particle tree and of the frame refers to
+ * the parts (start_get_frame returns problem 0's).  Costs a context per
+ * problem, kept for reuse until start_destroy. */
+int start_build_batch(start_ctx *c, int n_problems, const long long *n_p, const long long *n_s,
+                      const float *const *pos, const float *const *h,
+                      const float *const *src_pos, const double *const *src_L);
+
 /* Resident chemistry state (input order): n_H [n_p] float32 cm^-3 (>= 0),
  * y [n_p] float64 neutral fraction in [0, 1].  Sets n_HI = y n_H. */
 int start_set_state(start_ctx *c, const float *n_H, const double *y);

@@ -81,6 +81,7 @@ def lib():
             "start_h2_dissociation": (i, [vp, vp, f, d, vp]),
             "start_get_heating": (i, [vp, vp]),
             "start_set_temperature": (i, [vp, vp]),
+            "start_build_batch": (i, [vp, i, vp, vp, vp, vp, vp, vp]),
             "start_get_temperature": (i, [vp, vp]),
             "start_rt_solve_oneshot": (i, [P(StartParams), vp, vp, ll, vp, vp, vp, ll, f, vp]),
             "start_get_frame": (i, [vp, vp]),
@@ -229,6 +230,32 @@ class Context:
         self.n_s = int(src_L.shape[0])
         start_build_trees(self.h, pos, h, self.n_p, src_pos, src_L, self.n_s, V,
                           START_DIFFUSE if diffuse else 0)
+
+    def build_batch(self, problems):
+        """Several independent problems in this context, solved together with
+        shared launches: problems = [(pos, h, src_pos, src_L), ...] (point
+        sources).  The particle arrays of later calls are the problems'
+        concatenated in order (start_build_batch)."""
+        nb = len(problems)
+        keep = []
+
+        def arr(x, dt):
+            if isinstance(x, np.ndarray):
+                x = np.ascontiguousarray(x, dtype=dt)
+            keep.append(x)
+            return _ptr(x) if (x.shape[-1] if hasattr(x, "shape") else len(x)) else None
+
+        n_p = (C.c_longlong * nb)(*[int(p[1].shape[0]) for p in problems])
+        n_s = (C.c_longlong * nb)(*[int(p[3].shape[0]) for p in problems])
+        ptrs = [(C.c_void_p * nb)() for _ in range(4)]
+        for b, (pos, h, sp, sL) in enumerate(problems):
+            ptrs[0][b] = arr(pos, np.float32)
+            ptrs[1][b] = arr(h, np.float32)
+            ptrs[2][b] = arr(sp, np.float32)
+            ptrs[3][b] = arr(sL, np.float64)
+        _check(self.h, lib().start_build_batch(self.h, nb, n_p, n_s, *ptrs))
+        self.n_p = int(sum(n_p))
+        self.n_s = int(sum(n_s))
 
     def set_state(self, n_H, y):
         start_set_state(self.h, n_H, y)

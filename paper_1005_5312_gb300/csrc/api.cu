@@ -323,8 +323,60 @@ static void csr_to_input(long long n, const std::vector<O> &moff, const std::vec
     }
 }
 
+// ---------------------------------------------------------------- batches
+// Merging one problem's structures into a batch's forest: plain copies, and
+// index arrays shifted by the problem's offsets (kNone kept).
+__global__ void k_shift_u32(const u32 *in, long long n, u32 add, u32 *out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] == 0xffffffffu ? 0xffffffffu : in[i] + add;   // "none" kept
+}
+
+__global__ void k_shift_meta(const uint4 *in, long long n, u32 node0, u32 memb0, uint4 *out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        uint4 m = in[i];
+        out[i] = make_uint4(m.x + node0, m.y + memb0, m.z, m.w);
+    }
+}
+
+__global__ void k_fill_range(uint2 *tr, float *rf2, long long n, uint2 r, float f)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        tr[i] = r;
+        rf2[i] = f;
+    }
+}
+
+extern "C" int start_destroy(start_ctx *c);
+
+int destroy_batch_parts(start_ctx *c)
+{
+    for (start_ctx *b : c->bsub) start_destroy(b);
+    c->bsub.clear();
+    return START_OK;
+}
+
+static int copy_dev(start_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    if (!bytes) return START_OK;
+    return cuda_check(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream),
+                      "batch copy");
+}
+
+static int shift_copy(start_ctx *c, u32 *dst, const u32 *src, long long n, u32 add)
+{
+    if (n <= 0) return START_OK;
+    k_shift_u32<<<grid_for(n, 256), 256, 0, c->stream>>>(src, n, add, dst);
+    ++c->launches;
+    return cuda_check(c, cudaGetLastError(), "k_shift_u32");
+}
+
 static void release_all(start_ctx *c)
 {
+    destroy_batch_parts(c);
     resident_reset(c);
     if (c->r_cap) cudaStreamDestroy(c->r_cap);
     c->r_cap = nullptr;
@@ -336,7 +388,7 @@ static void release_all(start_ctx *c)
                    &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord, &c->m_nx0, &c->m_dl,
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_hard, &c->m_part, &c->m_table,
-                   &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc, &c->klum_big};
+                   &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc, &c->klum_big, &c->trange, &c->trf2};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);
@@ -482,6 +534,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
     if (!c) return START_EINVAL;
     DeviceGuard g(c);
     c->built = c->has_state = c->solved = false;
+    c->nbatch = 0;
     resident_reset(c);
     if (n_p < 0 || n_s < 0) return set_err(c, START_EINVAL, "negative size");
     if (n_p >= START_MAX_N || n_s >= START_MAX_N)
@@ -562,6 +615,135 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
     ST_CUDA(c, cudaStreamSynchronize(s));
     ST_CUDA(c, cudaGetLastError());
     if (read_counter(c, C_INTERNAL)) return set_err(c, START_ECUDA, "internal inconsistency (trees or neighbour lists)");
+    c->built = true;
+    return START_OK;
+}
+
+int start_build_batch(start_ctx *c, int nb, const long long *n_p, const long long *n_s,
+                                 const float *const *pos, const float *const *h,
+                                 const float *const *src_pos, const double *const *src_L)
+{
+    if (!c) return START_EINVAL;
+    DeviceGuard g(c);
+    c->built = c->has_state = c->solved = false;
+    c->nbatch = 0;
+    resident_reset(c);
+    if (nb < 1 || !n_p || !n_s || !pos || !h || !src_pos || !src_L)
+        return set_err(c, START_EINVAL, "a batch needs n >= 1 problems and their arrays");
+    long long P = 0, S = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (n_p[b] < 0 || n_s[b] < 0) return set_err(c, START_EINVAL, "negative size");
+        P += n_p[b];
+        S += n_s[b];
+    }
+    if (P >= START_MAX_N || S >= START_MAX_N)
+        return set_err(c, START_ERANGE, "a batch holds below 2^30 particles and sources");
+    // every problem built on its own (its frame, trees and neighbour lists), in
+    // contexts that share this one's stream and parameters
+    while ((int)c->bsub.size() < nb) {
+        start_ctx *b = nullptr;
+        start_params q = c->p;
+        q.timing = 0;
+        int rc = start_create(&b, &q);
+        if (rc != START_OK) return set_err(c, rc, "batch: creating a part");
+        c->bsub.push_back(b);
+    }
+    long long N = 0, NB = 0;
+    float cmag = 0.f;
+    for (int b = 0; b < nb; ++b) {
+        start_ctx *q = c->bsub[b];
+        q->p = c->p;
+        q->p.timing = 0;
+        q->stream = c->stream;
+        int rc = start_build_trees(q, pos[b], h[b], n_p[b], src_pos[b], src_L[b], n_s[b], nullptr,
+                                   0u);
+        if (rc != START_OK) return set_err(c, rc, "batch part " + std::to_string(b) + ": " + q->err);
+        N += q->stree.n;
+        NB += q->nb_total;
+        if (q->np + q->ns > 0 && q->fr.cmag > cmag) cmag = q->fr.cmag;
+        c->launches += q->launches;
+        q->launches = 0;
+    }
+    if (N >= (1LL << 31)) return set_err(c, START_ERANGE, "a batch's forest is too large");
+    size_t Pz = (size_t)(P ? P : 1), Sz = (size_t)(S ? S : 1), Nz = (size_t)(N ? N : 1);
+    Tree &t = c->stree;
+    if (ensure(c->pq, Pz * 16) || ensure(c->ph, Pz * 4) || ensure(c->porig, Pz * 4) ||
+        ensure(c->pinv, Pz * 4) || ensure(c->pkey, Pz * 8) || ensure(c->nH, Pz * 4) ||
+        ensure(c->y, Pz * 8) || ensure(c->V, Pz * 8) || ensure(c->Tg, Pz * 8) ||
+        ensure(c->gam, Pz * 4) || ensure(c->eL, Pz * 8) || ensure(c->eLs, Pz * 4) ||
+        ensure(c->nb_off, (Pz + 1) * 4) || ensure(c->nb_idx, (size_t)(NB ? NB : 1) * 4) ||
+        ensure(c->sq, Sz * 16) || ensure(c->sL, Sz * 8) || ensure(c->sorig, Sz * 4) ||
+        ensure(c->skey, Sz * 8) || ensure(t.box, Nz * 16) || ensure(t.meta, Nz * 16) ||
+        ensure(t.cube, Nz * 32) || ensure(t.level, Nz * 4) || ensure(t.parent, Nz * 4) ||
+        ensure(t.leafof, Sz * 4) || ensure(t.vsrc, Nz * 16) || ensure(t.L, Nz * 8) ||
+        ensure(t.M, Nz * 24) || ensure(c->trange, Pz * 8) || ensure(c->trf2, Pz * 4))
+        return set_err(c, START_ENOMEM, "out of device memory (batch)");
+    long long p0 = 0, s0 = 0, n0 = 0, e0 = 0;
+    for (int b = 0; b < nb; ++b) {
+        start_ctx *q = c->bsub[b];
+        const long long np = q->np, ns = q->ns, nn = q->stree.n, ne = q->nb_total;
+        if (np) {
+            ST_TRY(copy_dev(c, c->pq.as<float4>() + p0, q->pq.p, np * 16));
+            ST_TRY(copy_dev(c, c->ph.as<float>() + p0, q->ph.p, np * 4));
+            ST_TRY(copy_dev(c, c->pkey.as<u64>() + p0, q->pkey.p, np * 8));
+            ST_TRY(copy_dev(c, c->V.as<double>() + p0, q->V.p, np * 8));
+            ST_TRY(copy_dev(c, c->nH.as<float>() + p0, q->nH.p, np * 4));
+            ST_TRY(copy_dev(c, c->y.as<double>() + p0, q->y.p, np * 8));
+            ST_TRY(copy_dev(c, c->gam.as<float>() + p0, q->gam.p, np * 4));
+            ST_TRY(copy_dev(c, c->Tg.as<double>() + p0, q->Tg.p, np * 8));
+            ST_TRY(shift_copy(c, c->porig.as<u32>() + p0, q->porig.as<u32>(), np, (u32)p0));
+            ST_TRY(shift_copy(c, c->pinv.as<u32>() + p0, q->pinv.as<u32>(), np, (u32)p0));
+            ST_TRY(shift_copy(c, c->nb_off.as<u32>() + p0, q->nb_off.as<u32>(), np, (u32)e0));
+            ST_TRY(shift_copy(c, c->nb_idx.as<u32>() + e0, q->nb_idx.as<u32>(), ne, (u32)p0));
+            const double rf = 1e-6 * q->fr.side;
+            k_fill_range<<<grid_for(np, 256), 256, 0, c->stream>>>(
+                c->trange.as<uint2>() + p0, c->trf2.as<float>() + p0, np,
+                make_uint2((u32)n0, (u32)(n0 + nn)), (float)(rf * rf));
+            ++c->launches;
+        }
+        if (ns) {
+            ST_TRY(copy_dev(c, c->sq.as<float4>() + s0, q->sq.p, ns * 16));
+            ST_TRY(copy_dev(c, c->sL.as<double>() + s0, q->sL.p, ns * 8));
+            ST_TRY(copy_dev(c, c->skey.as<u64>() + s0, q->skey.p, ns * 8));
+            ST_TRY(shift_copy(c, c->sorig.as<u32>() + s0, q->sorig.as<u32>(), ns, (u32)s0));
+            ST_TRY(shift_copy(c, t.leafof.as<u32>() + s0, q->stree.leafof.as<u32>(), ns, (u32)n0));
+        }
+        if (nn) {
+            const Tree &u = q->stree;
+            ST_TRY(copy_dev(c, t.box.as<float4>() + n0, u.box.p, nn * 16));
+            ST_TRY(copy_dev(c, t.cube.as<double>() + 4 * n0, u.cube.p, nn * 32));
+            ST_TRY(copy_dev(c, t.level.as<int>() + n0, u.level.p, nn * 4));
+            ST_TRY(copy_dev(c, t.vsrc.as<float4>() + n0, u.vsrc.p, nn * 16));
+            ST_TRY(copy_dev(c, t.L.as<double>() + n0, u.L.p, nn * 8));
+            ST_TRY(copy_dev(c, t.M.as<double>() + 3 * n0, u.M.p, nn * 24));
+            ST_TRY(shift_copy(c, t.parent.as<u32>() + n0, u.parent.as<u32>(), nn, (u32)n0));
+            k_shift_meta<<<grid_for(nn, 256), 256, 0, c->stream>>>(
+                u.meta.as<uint4>(), nn, (u32)n0, (u32)s0, t.meta.as<uint4>() + n0);
+            ++c->launches;
+        }
+        p0 += np;
+        s0 += ns;
+        n0 += nn;
+        e0 += ne;
+    }
+    u32 etot = (u32)NB;
+    ST_CUDA(c, cudaMemcpyAsync(c->nb_off.as<u32>() + P, &etot, 4, cudaMemcpyHostToDevice,
+                               c->stream));
+    if (P) {
+        ST_CUDA(c, cudaMemsetAsync(c->eL.p, 0, P * 8, c->stream));
+        ST_CUDA(c, cudaMemsetAsync(c->eLs.p, 0, P * 4, c->stream));
+    }
+    ST_CUDA(c, cudaStreamSynchronize(c->stream));   // the stacked values above are on the host
+    c->np = P;
+    c->ns = S;
+    c->nb_total = NB;
+    c->diffuse = false;
+    c->pt.n = 0;          // the problems' particle trees stay in their parts
+    c->et.n = 0;
+    t.n = N;
+    c->fr = c->bsub[0]->fr;
+    c->fr.cmag = cmag;    // the filters' magnitude bound covers every problem
+    c->nbatch = nb;
     c->built = true;
     return START_OK;
 }

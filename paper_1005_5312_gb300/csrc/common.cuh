@@ -149,6 +149,13 @@ struct start_ctx {
     unsigned grp_s[2] = {0u, 0xffffffffu}, grp_e[2] = {0u, 0xffffffffu};
     st::DBuf g_hist, gacc;
     st::DBuf klum_big;  // emitter cells whose kernel-weighted luminosity takes a block
+    // a batch of independent problems in one context (start_build_batch): each
+    // problem's own source tree is a range of the forest's cells, and every
+    // target walks only its problem's range (trange, uint2 per target) with its
+    // problem's dilution floor (trf2, float per target)
+    int nbatch = 0;
+    std::vector<start_ctx *> bsub;     // contexts the problems are built in
+    st::DBuf trange, trf2;
 
     // memoised march: per chain link (virtual source, particle)
     st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_hard, m_part, m_table, m_nx0, m_dl;

@@ -30,6 +30,7 @@ struct MarchArgs {
     const float *eLs;      // individual emitters' L / L_unit, Morton order
     float sig;             // sigma * len_unit (per length unit per cm^-3)
     float rfloor2;         // squared dilution floor
+    const float *rf2;      // per target (a batch of problems), or NULL: rfloor2
     float tau_cut;
     long long hop_cap;
     float *pcon;           // per-pair contribution L e^-tau / (4 pi r^2), scaled units

@@ -867,6 +867,7 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
     if (i < t1) {
         u64 e0 = off[i] - base, e1 = off[i + 1] - base;
         float4 pt = a.m.pq[i];
+        const float rf2 = a.m.rf2 ? a.m.rf2[i] : a.m.rfloor2;
         float sum = 0.f, cmp = 0.f, hsum = 0.f, hcmp = 0.f;
         if (!first) {
             const float4 q = acc[i];
@@ -884,7 +885,7 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
                 u32 vid = a.svid[p];
                 float4 src = vsource(a, vid);
                 float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
-                float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.m.rfloor2);
+                float r2 = fmaxf(rx * rx + ry * ry + rz * rz, rf2);
                 float dil = src.w / (12.566370614359172f * r2);
                 if (MODE == 1) {
                     float xs = tau * 1e-14f;
@@ -1137,8 +1138,11 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     c->memo_slots = nslots;
     c->memo_evals += (unsigned long long)nslots;
     c->memo_links += (unsigned long long)nslots;
-    // pointer jumping
+    // pointer jumping; its flag lives in the context's small scratch (allocated
+    // here too: a batch context never runs the builds that allocate it)
     int b = 0;
+    if (ensure(c->flags, 64 + 2 * (kLevels + 1) * sizeof(unsigned long long)))
+        return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned *active = c->flags.as<unsigned>() + 12;
     const long long jblocks = (long long)grid_for(nslots, 256 * kJumpR);
     if (ensure(c->m_part, (size_t)jblocks * 24))

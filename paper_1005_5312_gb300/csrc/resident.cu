@@ -145,6 +145,7 @@ void resident_reset(start_ctx *c)
 bool resident_eligible(const start_ctx *c)
 {
     return c->p.reuse_chains && c->p.march_mode == 1 && !c->diffuse && c->chunks == 1 &&
+           c->nbatch == 0 &&
            c->npairs > 0 && c->p.T_eff == 0.0;
 }
 

@@ -38,6 +38,8 @@ struct TreeView {
     u32 n;
     u32 lo = 0, hi = 0xffffffffu;
     const int *level = nullptr;   // depth of every cell (the warp-cooperative walk)
+    const uint2 *trange = nullptr;   // a batch of problems: the cells [x, y) of each
+                                     // target's own tree (Morton order of the targets)
 };
 
 // Canonical virtual-source ids (the memoised march's numbering): source-tree
@@ -110,12 +112,18 @@ struct SlotRows {
 template <int MODE, class Rows>
 __device__ __forceinline__ void walk_tree(const TreeView &t, float4 p, float th2f, double th2d,
                                           float cmag, u32 self, u32 tag, CanonBase cb, u32 &c,
-                                          u64 &w, u64 wend, Rows &rows, unsigned &fb)
+                                          u64 &w, u64 wend, Rows &rows, unsigned &fb,
+                                          long long tgt = -1)
 {
     constexpr bool FILL = MODE != 0;
     const u32 okey = tag ? 0x80000000u : 0u;
-    const u32 end = t.hi < t.n ? t.hi : t.n;   // depth-first order: nothing past hi is emitted
+    u32 end = t.hi < t.n ? t.hi : t.n;   // depth-first order: nothing past hi is emitted
     u32 n = 0;
+    if (t.trange && tgt >= 0) {          // the target's own tree of a batch
+        const uint2 r = t.trange[tgt];
+        n = r.x;
+        end = r.y < end ? r.y : end;
+    }
     while (n < end) {
         uint4 mt = t.meta[n];
         if (mt.x <= t.lo) {   // the whole subtree lies before the range
@@ -265,7 +273,8 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
     }
     unsigned fb = 0;
     const bool live = i >= 0;
-    const bool warp = st_.level != nullptr;   // the warp-cooperative walk (both trees or none)
+    // the warp-cooperative walk (both trees or none; not over a batch's forest)
+    const bool warp = st_.level != nullptr && st_.trange == nullptr;
     u32 c = 0;
     const u64 w0 = !live ? 0ull
                          : (MODE == 3 ? (u64)(i - t0) * kWalkRow : (FILL ? off[i] - base : 0ull));
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
                 walk_tree_warp<MODE>(et_, p, live, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w,
                                      wend, rows, fb);
             } else {
-                walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
+                walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb, i);
                 walk_tree<MODE>(et_, p, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w, wend,
                                 rows, fb);
             }
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
                 walk_tree_warp<MODE>(et_, p, live, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w,
                                      wend, rows, fb);
             } else {
-                walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb);
+                walk_tree<MODE>(st_, p, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend, rows, fb, i);
                 walk_tree<MODE>(et_, p, th2f, th2d, cmag, self, kEntryEmit, ecb, c, w, wend,
                                 rows, fb);
             }
@@ -350,7 +359,7 @@ __global__ void __launch_bounds__(128) k_walk_hash(const float4 *pq, long long n
         u32 c = 0;
         u64 w = 0;
         HashRows rows;
-        walk_tree<1>(st_, p, th2f, th2d, cmag, kNone, 0u, CanonBase{}, c, w, ~0ull, rows, fb);
+        walk_tree<1>(st_, p, th2f, th2d, cmag, kNone, 0u, CanonBase{}, c, w, ~0ull, rows, fb, i);
         walk_tree<1>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, CanonBase{}, c, w, ~0ull, rows,
                      fb);
         const u32 o = porig[i];
@@ -410,11 +419,11 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
     long long pidx = gid;
     bool have = pidx < a.npairs;
     float4 src = make_float4(0.f, 0.f, 0.f, 0.f), pt = src;
-    u32 j = 0, nh = 0;
+    u32 j = 0, j0 = 0, nh = 0;   // j0: the pair's target
     float tau = 0.f, comp = 0.f;
     if (have) {
         src = pair_source(a, a.pent[pidx]);
-        j = pair_target(a, pidx);
+        j = j0 = pair_target(a, pidx);
         pt = a.pq[j];
     }
     while (__any_sync(0xffffffffu, have)) {
@@ -438,7 +447,7 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
             if (done) {
                 if (gl == 0) {
                     float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
-                    float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.rfloor2);
+                    float r2 = fmaxf(rx * rx + ry * ry + rz * rz, a.rf2 ? a.rf2[j0] : a.rfloor2);
                     a.pcon[pidx] = src.w * expf(-tau) / (12.566370614359172f * r2);
                     ++rays;
                     hops += nh;
@@ -448,7 +457,7 @@ __global__ void __launch_bounds__(256) k_march(MarchArgs a)
                 have = pidx < a.npairs;
                 if (have) {
                     src = pair_source(a, a.pent[pidx]);
-                    j = pair_target(a, pidx);
+                    j = j0 = pair_target(a, pidx);
                     pt = a.pq[j];
                     tau = 0.f;
                     comp = 0.f;
@@ -850,7 +859,8 @@ static TreeView source_view(start_ctx *c)
 {
     return TreeView{c->stree.box.as<float4>(), c->stree.meta.as<uint4>(),
                     c->stree.cube.as<double>(), (u32)c->stree.n, c->grp_s[0], c->grp_s[1],
-                    c->p.walk_warp ? c->stree.level.as<int>() : nullptr};
+                    c->p.walk_warp ? c->stree.level.as<int>() : nullptr,
+                    c->nbatch ? c->trange.as<uint2>() : nullptr};
 }
 
 static TreeView emitter_view(start_ctx *c)
@@ -911,6 +921,7 @@ static MarchArgs march_args(start_ctx *c, long long npairs)
     a.sig = (float)(c->solve_kind == 1 ? c->p.len_unit_cm : c->p.sigma_cm2 * c->p.len_unit_cm);
     double rf = 1e-6 * c->fr.side;
     a.rfloor2 = (float)(rf * rf);
+    a.rf2 = c->nbatch ? c->trf2.as<float>() : nullptr;
     a.tau_cut = (float)c->p.tau_cut;
     a.hop_cap = c->p.hop_cap > 0 ? c->p.hop_cap : c->np + 1;
     a.pcon = c->pcon.as<float>();
@@ -1032,7 +1043,7 @@ __global__ void __launch_bounds__(128) k_walk_hist(const float4 *pq, long long n
         u64 w = 0;
         unsigned fb = 0;
         HistRows rows{bins, SN, NT};
-        walk_tree<1>(st_, p, th2f, th2d, cmag, kNone, 0u, CanonBase{}, c, w, ~0ull, rows, fb);
+        walk_tree<1>(st_, p, th2f, th2d, cmag, kNone, 0u, CanonBase{}, c, w, ~0ull, rows, fb, i);
         walk_tree<1>(et_, p, th2f, th2d, cmag, (u32)i, kEntryEmit, CanonBase{}, c, w, ~0ull, rows,
                      fb);
         rows.flush();

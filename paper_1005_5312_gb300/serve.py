@@ -15,6 +15,13 @@ runs out of device memory is retried once on a fresh context.
 `serve(requests, workers=1)` is the plain baseline: one solve at a time.
 Every request's results are the same whether it runs alone or in a mix
 (the solve is deterministic).
+
+With batch_small > 1, a worker that takes a small request (at most
+small_n_p particles) also takes the small requests that have already
+arrived and share its theta, time step and step count, up to batch_small of
+them, and solves them as one batch (start_build_batch): every kernel of the
+solve then runs once for the whole batch, and each request's results are
+bitwise those of solving it alone.
 """
 from __future__ import annotations
 
@@ -97,7 +104,8 @@ class Server:
     """FIFO admission by worker slots and a device-memory budget."""
 
     def __init__(self, workers: int = 4, budget_bytes: float = 150e9, max_pairs: int = 1 << 27,
-                 tuner=None, trim_bytes: float = None, **params):
+                 tuner=None, trim_bytes: float = None, batch_small: int = 0,
+                 small_n_p: int = 1 << 16, **params):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
@@ -111,6 +119,9 @@ class Server:
             st = torch.cuda.Stream()
             self.workers.append(_Worker(Context(stream=st, **self.params), st))
         self.tuner = tuner
+        self.batch_small = int(batch_small)
+        self.small_n_p = int(small_n_p)
+        self.batches = 0
         self.cv = threading.Condition()
         self.reserved = 0.0
         self.results = []
@@ -139,29 +150,56 @@ class Server:
             rays += ctx.stats()["rays"]
         return g, y, rays
 
-    def _solve(self, w: _Worker, req: SolveRequest, t0: float, t_admit: float, est: int):
+    def _run_batch(self, ctx, reqs):
+        """Several small requests as one batch; returns [(g, y, rays)] per request."""
+        r0 = reqs[0]
+        ctx.build_batch([(r.pos, r.h, r.src_pos, r.src_L) for r in reqs])
+        off = np.cumsum([0] + [r.n_p for r in reqs])
+        nH = np.concatenate([np.asarray(r.n_H, np.float32) for r in reqs])
+        y = np.concatenate([np.asarray(r.y0, np.float64) for r in reqs])
+        g = np.zeros(int(off[-1]), np.float32)
+        rays = 0
+        for _ in range(r0.steps):
+            ctx.set_state(nH, y)
+            ctx.rt_solve(r0.theta, gamma_out=g)
+            ctx.ionize(r0.dt, y_out=y)
+            rays += ctx.stats()["rays"]
+        share = [r.n_p / max(1, int(off[-1])) for r in reqs]
+        return [(g[off[b]:off[b + 1]].copy(), y[off[b]:off[b + 1]].copy(), int(rays * share[b]))
+                for b in range(len(reqs))]
+
+    def _solve(self, w: _Worker, reqs, t0: float, t_admit: float, est: int):
         from . import START_ENOMEM, StartError
+        if not isinstance(reqs, list):
+            reqs = [reqs]
         try:
+            def run():
+                if len(reqs) == 1:
+                    return [self._run(w.ctx, reqs[0])]
+                return self._run_batch(w.ctx, reqs)
             try:
-                g, y, rays = self._run(w.ctx, req)
+                outs = run()
             except StartError as e:
                 if e.code != START_ENOMEM:
                     raise
                 self._fresh_context(w)            # out of memory: once more, from scratch
                 with self.cv:
                     self.retries += 1
-                g, y, rays = self._run(w.ctx, req)
-            res = SolveResult(req.rid, req.t_arrive, t_admit, time.perf_counter() - t0, g, y, rays,
-                              est)
+                outs = run()
+            t_done = time.perf_counter() - t0
             with self.cv:
-                self.results.append(res)
+                if len(reqs) > 1:
+                    self.batches += 1
+                for req, (g, y, rays) in zip(reqs, outs):
+                    self.results.append(SolveResult(req.rid, req.t_arrive, t_admit, t_done, g, y,
+                                                    rays, est))
             if memory_in_use() > self.trim_bytes:
                 self._fresh_context(w)
                 with self.cv:
                     self.trims += 1
         except Exception as e:  # reported by serve()
             with self.cv:
-                self.errors.append((req.rid, repr(e)))
+                self.errors.append((reqs[0].rid, repr(e)))
         finally:
             with self.cv:
                 w.busy = False
@@ -175,7 +213,10 @@ class Server:
         self.results, self.errors = [], []
         threads = []
         t0 = time.perf_counter()
-        for req in reqs:
+        i = 0
+        while i < len(reqs):
+            req = reqs[i]
+            i += 1
             if realtime:
                 wait = req.t_arrive - (time.perf_counter() - t0)
                 if wait > 0:
@@ -191,8 +232,25 @@ class Server:
                         self.reserved += est
                         break
                     self.cv.wait()
+                batch = [req]
+                if self.batch_small > 1 and req.n_p <= self.small_n_p:
+                    # the compatible small requests that have arrived meanwhile
+                    now = time.perf_counter() - t0 if realtime else float("inf")
+                    while (i < len(reqs) and len(batch) < self.batch_small and
+                           reqs[i].t_arrive <= now and reqs[i].n_p <= self.small_n_p and
+                           reqs[i].theta == req.theta and reqs[i].dt == req.dt and
+                           reqs[i].steps == req.steps):
+                        e = memory_estimate(reqs[i].n_p, reqs[i].n_s, reqs[i].theta,
+                                            self.max_pairs)
+                        if self.reserved + e > self.budget:
+                            break
+                        self.reserved += e
+                        est += e
+                        batch.append(reqs[i])
+                        i += 1
             t_admit = time.perf_counter() - t0
-            th = threading.Thread(target=self._solve, args=(w, req, t0, t_admit, est), daemon=True)
+            th = threading.Thread(target=self._solve, args=(w, batch, t0, t_admit, est),
+                                  daemon=True)
             th.start()
             threads.append(th)
         for th in threads:

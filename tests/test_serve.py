@@ -66,3 +66,29 @@ def test_results_identical_alone_and_in_a_mix():
     trimmed.close()
     for a, b in zip(r1, r4):
         assert np.array_equal(a.gamma, b.gamma) and np.array_equal(a.y, b.y)
+
+
+@pytest.mark.gpu
+def test_batched_small_requests_identical_to_alone():
+    """Small requests that have arrived together are solved as one batch
+    (start_build_batch): every request's Gamma and y are bitwise those of
+    solving it alone, over two coupled steps (full solves each step: a batch
+    keeps no resident chains)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1005_5312_gb300 as S
+    from paper_1005_5312_gb300.serve import Server, make_requests
+    S.build()
+    reqs = make_requests(24, rate_hz=1e6, log2_np=(9, 13), seed=12, steps=2)
+    alone = Server(workers=1, reuse_chains=0)
+    r1 = alone.serve(reqs, realtime=False)
+    alone.close()
+    batched = Server(workers=2, batch_small=8, small_n_p=1 << 13, reuse_chains=0)
+    r2 = batched.serve(reqs, realtime=True)
+    assert batched.batches > 0
+    batched.close()
+    for a, b in zip(r1, r2):
+        assert a.rid == b.rid
+        assert np.array_equal(a.gamma, b.gamma)
+        assert np.array_equal(a.y, b.y)
