@@ -405,11 +405,13 @@ def headline(S, w, dev, args, T, clk_index):
     r1 = run(args.theta, args.steps, args.warmup, clk)
     r2 = None if args.no_theta2 else run(args.theta2, args.side_steps, 1)
     # the starting state once more, for the parity check against the oracle
-    ctx.build_trees(pos, h, sp, sL, V, diffuse=True)
-    ctx.set_state(T(w.n_H), y0)
-    g0 = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
-    ctx.rt_solve(args.theta, gamma_out=g0)
-    g_start = g0.cpu().numpy()
+    g_start = None
+    if not args.no_cpu:
+        ctx.build_trees(pos, h, sp, sL, V, diffuse=True)
+        ctx.set_state(T(w.n_H), y0)
+        g0 = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
+        ctx.rt_solve(args.theta, gamma_out=g0)
+        g_start = g0.cpu().numpy()
     ctx.close()
     return r1, r2, clk.summary(), g_start
 
