@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--theta2", type=float, default=1.0)
     ap.add_argument("--march-group", type=int, default=2)
+    ap.add_argument("--row-bins", type=int, default=4,
+                    help="first-hop direction bins per cube-face edge (0: scan every neighbour)")
     ap.add_argument("--max-pairs", type=int, default=1_500_000_000,
                     help="interaction pairs per group of the large run (device memory of the "
                          "march about 90 B per pair)")
@@ -351,7 +353,7 @@ def headline(S, w, dev, args, T, clk_index):
     then the theta2 line; per-step CUDA events on the context's stream."""
     import torch
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream,
+    ctx = S.Context(timing=1, march_group=args.march_group, row_bins=args.row_bins, stream=stream,
                     max_pairs=args.max_pairs)
     pos, h, sp, sL, V = T(w.pos), T(w.h), T(w.src_pos), T(w.src_L), T(w.V)
     mass = T((w.n_H.astype(np.float64) * w.V).astype(np.float32))
@@ -419,7 +421,7 @@ def headline(S, w, dev, args, T, clk_index):
 def headline_e2e(S, w, args):
     """The same step through the C ABI with host buffers (numpy arrays): every
     step copies its inputs to the device and Gamma and y back."""
-    ctx = S.Context(march_group=args.march_group, max_pairs=args.max_pairs)
+    ctx = S.Context(march_group=args.march_group, row_bins=args.row_bins, max_pairs=args.max_pairs)
     mass = (w.n_H.astype(np.float64) * w.V).astype(np.float32)
     rho = np.zeros(w.n_p, np.float32)
     y = w.y0.copy()
@@ -458,7 +460,7 @@ def resident_steps(S, w, dev, args, T):
     (one replayed CUDA graph) and applies the implicit update."""
     import torch
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(reuse_chains=1, march_group=args.march_group, stream=stream)
+    ctx = S.Context(reuse_chains=1, march_group=args.march_group, row_bins=args.row_bins, stream=stream)
     ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
     ctx.set_state(T(w.n_H), T(w.y0))
     g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
@@ -531,7 +533,7 @@ def h2_dissociation(S, w, dev, args, T, flush):
     import numpy as np
     import torch
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(stream=stream, march_group=args.march_group)
+    ctx = S.Context(stream=stream, march_group=args.march_group, row_bins=args.row_bins)
     ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
     nH2 = T(np.random.default_rng(5).lognormal(np.log(1e-4), 1.5, w.n_p).astype(np.float32))
     k = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
@@ -563,7 +565,7 @@ def method_error(S, w, dev, args, T):
     import numpy as np
     import torch
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(stream=stream, march_group=args.march_group, reuse_chains=0)
+    ctx = S.Context(stream=stream, march_group=args.march_group, row_bins=args.row_bins, reuse_chains=0)
     ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
     floor = 1e-8 / (w.params["sigma_cm2"] * w.dt_s)
     out = {"floor": floor}
@@ -597,7 +599,7 @@ def blackbody_sources(S, w, dev, args, T, flush):
     rate per pair from the spectral tables; L2 flushed before every call."""
     import torch
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(stream=stream, march_group=args.march_group, T_eff=1e5)
+    ctx = S.Context(stream=stream, march_group=args.march_group, row_bins=args.row_bins, T_eff=1e5)
     ctx.build_trees(T(w.pos), T(w.h), T(w.src_pos), T(w.src_L))
     ctx.set_state(T(w.n_H), T(w.y0))
     g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
@@ -631,7 +633,7 @@ def diffuse_workload(S, dev, args, T, T_rec=0.0):
     from start_inputs import config3
     w = config3()
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream, max_pairs=1 << 29,
+    ctx = S.Context(timing=1, march_group=args.march_group, row_bins=args.row_bins, stream=stream, max_pairs=1 << 29,
                     T_rec=T_rec)
     y = T(w.y0)
     g = torch.zeros(w.n_p, dtype=torch.float32, device=dev)
@@ -670,7 +672,7 @@ def serving(args):
     of small requests, where a solve is bound by launches and host round
     trips, served by more workers with the autotuned knobs of each problem
     class (tuned before the stream starts)."""
-    from paper_1005_5312_gb300.autotune import Tuner
+    from paper_1005_5312_gb300.autotune import SEARCH_SPACE, Tuner
     from paper_1005_5312_gb300.serve import Server, make_requests, summarize
     lo, hi = (float(x) for x in args.serve_log2np.split(","))
     slo, shi = (float(x) for x in args.serve_small_log2np.split(","))
@@ -721,7 +723,7 @@ def serving(args):
             out[key]["batched_solves_per_s_vs_plain"] = (res["served_batched"]["solves_per_s"] /
                                                          res["plain"]["solves_per_s"])
     out["small_requests"]["autotuner"] = {"classes_tuned": len(tuned), "tuning_s": tune_s,
-                                          "knobs": "march_group, ptree_leaf, row_warps",
+                                          "knobs": ", ".join(sorted(SEARCH_SPACE)),
                                           "tuned_outside_the_stream": True}
     return out
 
@@ -732,7 +734,7 @@ def multisource_lines(S, dev, args, T, flush, w2, peak):
     resident-chain steps, the method's own error and the next-row lines."""
     import torch
     stream = torch.cuda.current_stream(dev)
-    ctx = S.Context(timing=1, march_group=args.march_group, stream=stream)
+    ctx = S.Context(timing=1, march_group=args.march_group, row_bins=args.row_bins, stream=stream)
     pos, h, spos, sL = T(w2.pos), T(w2.h), T(w2.src_pos), T(w2.src_L)
     nH, y0 = T(w2.n_H), T(w2.y0)
     y = y0.clone()
@@ -788,7 +790,7 @@ def multisource_lines(S, dev, args, T, flush, w2, peak):
         out["h2_dissociation"] = h2_dissociation(S, w2, dev, args, T, flush)
         out["blackbody_sources"] = blackbody_sources(S, w2, dev, args, T, flush)
     # Gamma at the neutral start, for the parity check against the oracle
-    ctx = S.Context(march_group=args.march_group, stream=stream)
+    ctx = S.Context(march_group=args.march_group, row_bins=args.row_bins, stream=stream)
     ctx.build_trees(pos, h, spos, sL)
     g0 = torch.zeros(w2.n_p, dtype=torch.float32, device=dev)
     ctx.rt_solve(args.theta, n_HI=T(w2.n_HI()), gamma_out=g0)
@@ -858,7 +860,7 @@ def run_gpu(args):
            "data": "synthetic",
            "config": {"workload": w.name, "n_p": w.n_p, "n_s": w.n_s, "emitters": w.n_p,
                       "theta": args.theta, "dt_s": w.dt_s, "march_group": args.march_group,
-                      "max_pairs": args.max_pairs, "march": "memoised",
+                      "max_pairs": args.max_pairs, "row_bins": args.row_bins, "march": "memoised",
                       "l2": "no flush: every step streams inputs and buffers far larger than "
                             "L2 (particles 16.7M x 60 B, neighbour lists 2.1 GB, chain slots "
                             "tens of GB)",

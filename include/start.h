@@ -174,6 +174,17 @@ typedef struct start_params {
                               adjacent targets already walk nearly the same
                               cells, and the shared traversal measured 3 %
                               slower).  Does not change any result */
+    int row_bins;          /* first hop of the memoised march: 0 scans every
+                              staged neighbour of the target for each pair; N in
+                              2..6 (default 4) bins the source direction on a
+                              cube map of N x N bins per face and scans only the
+                              bin's candidate set -- the neighbours that can
+                              still be the upstream choice for some direction in
+                              the bin, from bounds on their angle to it (6 N^2
+                              64-bit masks per particle, built once per build).
+                              Pairs whose source is not farther than every
+                              neighbour scan them all.  Does not change any
+                              result */
 } start_params;
 
 /* Counters of the last start_rt_solve. */
@@ -198,6 +209,10 @@ typedef struct start_stats {
                                    (first successor read, write), 16 per further
                                    successor read, 16 per slot copied once when its
                                    chain closed */
+    long long first_hop_scanned;  /* memoised march, every 64th target: candidates
+                                     the first hops of its pairs scanned */
+    long long first_hop_full;     /* the same targets: neighbours x pairs (what a
+                                     scan of every neighbour reads) */
 } start_stats;
 
 /* Phases timed when start_params.timing = 1 (milliseconds summed over every

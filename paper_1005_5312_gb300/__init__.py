@@ -40,14 +40,15 @@ class StartParams(C.Structure):
                 ("spin_cap", C.c_longlong),
                 ("stream", C.c_void_p),
                 ("T_eff", C.c_double), ("T_rec", C.c_double), ("row_warps", C.c_int),
-                ("thermal", C.c_int), ("lum_kernel", C.c_int), ("walk_warp", C.c_int)]
+                ("thermal", C.c_int), ("lum_kernel", C.c_int), ("walk_warp", C.c_int),
+                ("row_bins", C.c_int)]
 
 
 class StartStats(C.Structure):
     _fields_ = [(n, C.c_longlong) for n in (
         "rays", "hops", "march_fallbacks", "walk_fallbacks", "nbr_fallbacks", "nodes_src",
         "nodes_emit", "nodes_part", "nbr_total", "max_hops", "launches", "evals", "links", "chunks",
-        "jump_rounds", "jump_bytes")]
+        "jump_rounds", "jump_bytes", "first_hop_scanned", "first_hop_full")]
 
 
 class StartError(RuntimeError):

@@ -4,7 +4,9 @@
 * ``march_group`` -- lanes cooperating on one neighbour-list evaluation of
   the later chain levels (the warp-per-target grouping of the march),
 * ``row_warps``   -- the first hop's tile shape: target rows per block,
-* ``walk_warp``   -- one tree walk per warp of 32 targets, or per thread.
+* ``walk_warp``   -- one tree walk per warp of 32 targets, or per thread,
+* ``row_bins``    -- the first hop's direction bins (candidate sets per bin,
+  or a scan of every neighbour).
 
 Each knob is varied in turn around the current best (coordinate descent),
 timing one full step (build + solve) per candidate with CUDA events, and the
@@ -24,8 +26,9 @@ SEARCH_SPACE = {
     "ptree_leaf": (8, 16, 32),
     "row_warps": (4, 8),
     "walk_warp": (0, 1),
+    "row_bins": (0, 4, 6),
 }
-DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "row_warps": 8, "walk_warp": 0}
+DEFAULTS = {"march_group": 2, "ptree_leaf": 16, "row_warps": 8, "walk_warp": 0, "row_bins": 4}
 
 
 def problem_class(n_p: int, n_s: int, theta: float, diffuse: bool = False) -> tuple:

@@ -388,7 +388,8 @@ static void release_all(start_ctx *c)
                    &c->scan_tmp, &c->stage, &c->flags, &c->counters, &c->m_vid, &c->m_j, &c->m_ord, &c->pord, &c->m_nx0, &c->m_dl,
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_hard, &c->m_part, &c->m_table,
-                   &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc, &c->klum_big, &c->trange, &c->trf2};
+                   &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc, &c->klum_big, &c->trange, &c->trf2,
+                   &c->rb_mask, &c->rb_geo};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);
@@ -435,6 +436,7 @@ int start_default_params(start_params *p)
     p->march_mode = 1;
     p->row_warps = 8;
     p->walk_warp = 0;
+    p->row_bins = 4;
     p->sigma_cm2 = 6.3e-18;
     p->len_unit_cm = 3.0857e21;
     p->L_unit = 1e48;
@@ -461,6 +463,7 @@ static int check_params(start_params &d)
     if (d.thermal != 0 && d.thermal != 1) return START_EINVAL;
     if (d.lum_kernel != 0 && d.lum_kernel != 1) return START_EINVAL;
     if (d.walk_warp != 0 && d.walk_warp != 1) return START_EINVAL;
+    if (d.row_bins != 0 && (d.row_bins < 2 || d.row_bins > 6)) return START_EINVAL;
     if (d.row_warps == 0) d.row_warps = 8;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
     if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;
@@ -535,6 +538,7 @@ int start_build_trees(start_ctx *c, const float *pos, const float *h, long long 
     DeviceGuard g(c);
     c->built = c->has_state = c->solved = false;
     c->nbatch = 0;
+    c->rb_n = 0;
     resident_reset(c);
     if (n_p < 0 || n_s < 0) return set_err(c, START_EINVAL, "negative size");
     if (n_p >= START_MAX_N || n_s >= START_MAX_N)
@@ -627,6 +631,7 @@ int start_build_batch(start_ctx *c, int nb, const long long *n_p, const long lon
     DeviceGuard g(c);
     c->built = c->has_state = c->solved = false;
     c->nbatch = 0;
+    c->rb_n = 0;
     resident_reset(c);
     if (nb < 1 || !n_p || !n_s || !pos || !h || !src_pos || !src_L)
         return set_err(c, START_EINVAL, "a batch needs n >= 1 problems and their arrays");
@@ -1179,6 +1184,8 @@ int start_get_stats(start_ctx *c, start_stats *out)
     out->chunks = c->chunks;
     out->jump_rounds = c->jump_rounds;
     out->jump_bytes = (long long)c->jump_bytes;
+    out->first_hop_scanned = (long long)v[C_ROW_CAND];
+    out->first_hop_full = (long long)v[C_ROW_NB];
     return START_OK;
 }
 

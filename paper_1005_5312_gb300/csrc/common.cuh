@@ -159,6 +159,11 @@ struct start_ctx {
 
     // memoised march: per chain link (virtual source, particle)
     st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_hard, m_part, m_table, m_nx0, m_dl;
+    // first-hop candidate sets per particle and direction bin (row_bins = N:
+    // 6 N^2 u64 masks per particle) and the bins' cones; rb_n: the N they
+    // were built for, 0 when stale
+    st::DBuf rb_mask, rb_geo;
+    int rb_n = 0;
     long long memo_slots = 0;          // slots of the last memoised chunk
 
     // resident chains (reuse_chains = 1): the link forest of the last full
@@ -215,6 +220,8 @@ enum Counter {
     C_LEVEL,      // memoised march: device frontier {fbase, nf, total} (3 words)
     C_WALK_FB_GROUP = C_LEVEL + 3,   // opening tests re-decided by the walks of a group
     C_KLUM_BIG,   // kernel-weighted cell luminosities: cells left to a block each
+    C_ROW_CAND,   // staged first hop, every 64th target: candidates scanned over its pairs
+    C_ROW_NB,     // the same targets: staged neighbours x pairs (a full scan)
     C_COUNT = 32
 };
 

@@ -29,6 +29,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "common.cuh"
 #include "march.cuh"
@@ -87,6 +89,8 @@ struct MemoArgs {
     u32 cap;                        // slot capacity
     HEntry *table;
     unsigned long long hmask;
+    const unsigned long long *rbm;  // first-hop candidate sets per target and direction
+    int rbn;                        // bin (k_row_bins), N x N bins per cube face; 0: none
 };
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
@@ -174,33 +178,36 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
 // entry sits close to the caller's guess g (the same relative position in the
 // row, scaled by the two rows' lengths: within 8 entries for ~90 % of the
 // links on a uniform 64^3 workload); the 20 entries around g are read at
-// once as five aligned 16-byte vectors, and only a miss falls back to a
-// binary search on the order key (key of the cell holding vid).  Canonical
-// ids within a row are distinct (a row holds a count-1 cell or its member,
-// never both), so a match is the slot.  Reads stay below r1 + 12, inside the
-// slot arrays (their capacity exceeds the pair count by more than that).
-__device__ __forceinline__ u32 find_in_bounds(const MemoArgs &a, u32 r0, u32 r1, u32 vid, u32 key,
+// once as five aligned 16-byte vectors (find_in_window: kNone when the entry
+// is not among them), and find_in_bounds falls back to a binary search on the
+// order key (key of the cell holding vid).  Canonical ids within a row are
+// distinct (a row holds a count-1 cell or its member, never both), so a
+// match is the slot.  Reads stay below r1 + 12, inside the slot arrays (their
+// capacity exceeds the pair count by more than that).
+__device__ __forceinline__ u32 find_in_window(const MemoArgs &a, u32 r0, u32 r1, u32 vid,
                                               long long g)
 {
-    if (r1 <= r0) return kNone;
-    if (g >= 0) {
-        long long bb = (g - 8) & ~3ll;
-        const u32 b = bb < 0 ? 0u : (u32)bb;
-        const uint4 *v4 = reinterpret_cast<const uint4 *>(a.svid + b);
-        uint4 q[5];
+    if (r1 <= r0 || g < 0) return kNone;
+    long long bb = (g - 8) & ~3ll;
+    const u32 b = bb < 0 ? 0u : (u32)bb;
+    const uint4 *v4 = reinterpret_cast<const uint4 *>(a.svid + b);
+    uint4 q[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) q[k] = v4[k];
-        // matches among the 20 entries, restricted to those inside the row
-        u32 m = 0;
+    for (int k = 0; k < 5; ++k) q[k] = v4[k];
+    // matches among the 20 entries, restricted to those inside the row
+    u32 m = 0;
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-            m |= ((u32)(q[k].x == vid) | (u32)(q[k].y == vid) << 1 | (u32)(q[k].z == vid) << 2 |
-                  (u32)(q[k].w == vid) << 3) << (4 * k);
-        const u32 lo = r0 > b ? r0 - b : 0u;                 // < 20 when g >= r0
-        const u32 hi = r1 - b < 20u ? r1 - b : 20u;           // > 0 when g < r1
-        m &= ((1u << hi) - 1u) & ~((1u << lo) - 1u);
-        if (m) return b + (u32)(__ffs(m) - 1);
-    }
+    for (int k = 0; k < 5; ++k)
+        m |= ((u32)(q[k].x == vid) | (u32)(q[k].y == vid) << 1 | (u32)(q[k].z == vid) << 2 |
+              (u32)(q[k].w == vid) << 3) << (4 * k);
+    const u32 lo = r0 > b ? r0 - b : 0u;                 // < 20 when g >= r0
+    const u32 hi = r1 - b < 20u ? r1 - b : 20u;           // > 0 when g < r1
+    m &= ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+    return m ? b + (u32)(__ffs(m) - 1) : kNone;
+}
+
+__device__ __forceinline__ u32 search_row(const MemoArgs &a, u32 r0, u32 r1, u32 vid, u32 key)
+{
     u32 lo = r0, hi = r1;
     while (lo < hi) {
         u32 mid = lo + ((hi - lo) >> 1);
@@ -210,6 +217,14 @@ __device__ __forceinline__ u32 find_in_bounds(const MemoArgs &a, u32 r0, u32 r1,
     for (u32 e = lo; e < r1 && a.sord[e] == key; ++e)
         if (a.svid[e] == vid) return e;
     return kNone;
+}
+
+__device__ __forceinline__ u32 find_in_bounds(const MemoArgs &a, u32 r0, u32 r1, u32 vid, u32 key,
+                                              long long g)
+{
+    if (r1 <= r0) return kNone;
+    const u32 e = find_in_window(a, r0, r1, vid, g);
+    return e != kNone ? e : search_row(a, r0, r1, vid, key);
 }
 
 // Whether the walk of target up lists the virtual source vid whose order key
@@ -293,17 +308,226 @@ __device__ __forceinline__ void warp_append(bool flag, u32 slot, u32 tgt, uint2 
     if (flag) list[b + __popc(m & ((1u << lane) - 1u))] = make_uint2(slot, tgt);
 }
 
-// W target rows per block (the tile shape; 8 KB of stage per row): 40 warps
-// per SM either way.
+// Stages the neighbour list of target i (record pj) for one warp: the
+// source-independent terms of every distinct neighbour k, in list order --
+// nba (r_k - r_j, rsqrt |r_k - r_j|^2), nbb (|r_k - r_j|^2, e1, e0, -) with
+// e1 |b| + e0 the error bound of the closer-than test, nbp the record of k,
+// nbr (k, its row bounds when its row belongs to [t0, t1)).  Returns the
+// number staged; odd is set (warp-uniform) when a distinct neighbour's FP32
+// offset underflowed, amax2 is the largest |r_k - r_j|^2 staged.
+__device__ __forceinline__ int stage_row(const MarchArgs &m, u32 s0, u32 s1, float4 pj,
+                                         long long t0, long long t1, const u64 *off, u64 base,
+                                         float4 *nba, float4 *nbb, float4 *nbp, uint4 *nbr,
+                                         bool &odd, float &amax2)
+{
+    const float eps_q = 16.f * kU32;
+    const int lane = threadIdx.x & 31;
+    const unsigned me = 1u << lane;
+    int nst = 0;
+    bool od = false;
+    float mx = 0.f;
+    for (u32 b = s0; b < s1; b += 32) {
+        u32 s = b + lane;
+        bool ok = false;
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, P = A;
+        uint4 R = make_uint4(0u, 0u, 0u, 0u);
+        if (s < s1) {
+            u32 k = m.nb_idx[s];
+            if (k < m.np) {
+                P = m.pq[k];
+                float ax = P.x - pj.x, ay = P.y - pj.y, az = P.z - pj.z;
+                float a2 = ax * ax + ay * ay + az * az;
+                if (a2 == 0.f) {
+                    if (P.x != pj.x || P.y != pj.y || P.z != pj.z) od = true;
+                } else {
+                    float ra = rsqrtf(a2);
+                    float an = a2 * ra;
+                    A = make_float4(ax, ay, az, ra);
+                    B = make_float4(a2, eps_q * 2.f * an, eps_q * a2 + 1e-37f, 0.f);
+                    R.x = k;
+                    if ((long long)k >= t0 && (long long)k < t1) {
+                        R.y = (u32)(off[k] - base);
+                        R.z = (u32)(off[k + 1] - base);
+                    }
+                    mx = fmaxf(mx, a2);
+                    ok = true;
+                }
+            }
+        }
+        unsigned msk = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            int q = nst + __popc(msk & (me - 1u));
+            nba[q] = A;
+            nbb[q] = B;
+            nbp[q] = P;
+            nbr[q] = R;
+        }
+        nst += __popc(msk);
+    }
+    odd = __any_sync(0xffffffffu, od);
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    amax2 = mx;
+    __syncwarp();
+    return nst;
+}
+
+// Direction bins of the first hop: the cube map of b = r_s - r_j with N x N
+// bins on each face, bin (f N + iu) N + iv for face f = 2 axis + (component
+// < 0) and the two other components over the major one in [-1, 1] cut into N
+// intervals each (y, z on the x faces; z, x on the y faces; x, y on the z
+// faces).  b must not be zero.
+__device__ __forceinline__ int dir_bin(float x, float y, float z, int N)
+{
+    const float ax = fabsf(x), ay = fabsf(y), az = fabsf(z);
+    int f;
+    float mj, s, t;
+    if (ax >= ay && ax >= az) {
+        f = x >= 0.f ? 0 : 1;
+        mj = ax;
+        s = y;
+        t = z;
+    } else if (ay >= az) {
+        f = y >= 0.f ? 2 : 3;
+        mj = ay;
+        s = z;
+        t = x;
+    } else {
+        f = z >= 0.f ? 4 : 5;
+        mj = az;
+        s = x;
+        t = y;
+    }
+    const float hn = 0.5f * (float)N / mj;
+    const int iu = min(N - 1, max(0, (int)((s + mj) * hn)));
+    const int iv = min(N - 1, max(0, (int)((t + mj) * hn)));
+    return (f * N + iu) * N + iv;
+}
+
+// Candidate sets of the first hop per target and direction bin (an exact
+// pruning of the upstream search; the choice is the same).  For a bin B, a
+// cone (axis c, half-angle rho) around it, and a staged neighbour k at angle
+// theta_k from c, the score cos(angle(b, r_k - r_j)) over directions b in B
+// lies in [lo_k, hi_k] = [cos(min(pi, theta_k + rho)), cos(max(0, theta_k -
+// rho))].  Let L = max lo_j over the neighbours j that pass the closer-than
+// test for every b in B with |b| > amax (the largest |r_k - r_j| of the row):
+// lo_j > |r_j - r_i| / (2 amax) + eta suffices, since j is closer to the
+// source iff cos > |r_j - r_i| / (2 |b|).  Such a j makes the winner's score
+// at least L, so a neighbour with hi_k < L - eta never wins: the set of B is
+// {k : hi_k >= L - eta} (bit k of a 64-bit mask over the staged order), or 0
+// when no j qualifies (the search then scans every neighbour).  eta = 1e-3
+// and the 2e-3 rad widening of rho cover the FP32 rounding of the binning,
+// of the staged offsets and of these bounds (each below 1e-6; the sines are
+// taken from 1 - cos^2 + 1e-6, an upper bound); the rows that leave the
+// stage (more than kRowNB neighbours, or an underflowed offset) get 0 masks.
+constexpr float kBinEta = 1e-3f;
+
 template <int W>
-__global__ void __launch_bounds__(32 * W, 40 / W) k_memo_hop_rows(MemoArgs a)
+__global__ void __launch_bounds__(32 * W) k_row_bins(MarchArgs m, const float4 *geo, int N,
+                                                     unsigned long long *out)
+{
+    __shared__ float4 nba[W][kRowNB], nbb[W][kRowNB], nbp[W][kRowNB];
+    __shared__ uint4 nbr[W][kRowNB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= (long long)m.np) return;   // warp-uniform
+    const int nbins = 6 * N * N;
+    unsigned long long *row = out + (u64)i * nbins;
+    const u32 s0 = m.nb_off[i], s1 = m.nb_off[i + 1];
+    int nst = 0;
+    bool odd = false;
+    float amax2 = 0.f;
+    if (s1 - s0 <= (u32)kRowNB)
+        nst = stage_row(m, s0, s1, m.pq[i], 0, 0, nullptr, 0, nba[w], nbb[w], nbp[w], nbr[w],
+                        odd, amax2);
+    if (odd || nst == 0 || s1 - s0 > (u32)kRowNB) {
+        for (int b = lane; b < nbins; b += 32) row[b] = 0ull;
+        return;
+    }
+    // unit offsets and the closer-than threshold |r_k - r_j| / (2 amax),
+    // written over the staged records (not needed here)
+    const float inv = 0.5f * rsqrtf(amax2);
+    for (int q = lane; q < nst; q += 32) {
+        const float4 A = nba[w][q];
+        nbp[w][q] = make_float4(A.x * A.w, A.y * A.w, A.z * A.w, nbb[w][q].x * A.w * inv);
+    }
+    __syncwarp();
+    for (int b = lane; b < nbins; b += 32) {
+        const float4 g = geo[2 * b];
+        const float cr = g.w, sr = geo[2 * b + 1].x;
+        float L = -2.f;
+        for (int q = 0; q < nst; ++q) {
+            const float4 u = nbp[w][q];
+            const float ct = u.x * g.x + u.y * g.y + u.z * g.z;
+            const float sn = sqrtf(fmaxf(0.f, 1.f - ct * ct) + 1e-6f);
+            const float lo = ct <= -cr ? -1.f : ct * cr - sn * sr;
+            if (lo > u.w + kBinEta) L = fmaxf(L, lo);
+        }
+        unsigned long long mk = 0ull;
+        if (L > -2.f) {
+            for (int q = 0; q < nst; ++q) {
+                const float4 u = nbp[w][q];
+                const float ct = u.x * g.x + u.y * g.y + u.z * g.z;
+                const float sn = sqrtf(fmaxf(0.f, 1.f - ct * ct) + 1e-6f);
+                const float hi = ct >= cr ? 1.f : ct * cr + sn * sr;
+                if (hi >= L - kBinEta) mk |= 1ull << q;
+            }
+        }
+        row[b] = mk;
+    }
+}
+
+// One staged candidate q of the first hop for a source at b = r_s - r_j
+// (|b| = bn): hop<G>'s closer-than test and score with their error bounds;
+// keeps the best and second-best scores, the best candidate and the
+// smallest margin of the tests.
+__device__ __forceinline__ void score_staged(const float4 A, const float4 B, float bx, float by,
+                                             float bz, float bn, int q, float &bc, float &sc,
+                                             int &bq, float &margin)
+{
+    const float dot = bx * A.x + by * A.y + bz * A.z;
+    const float qv = 2.f * dot - B.x;
+    const float eq = B.y * bn + B.z;
+    const bool pass = qv > eq;
+    margin = fminf(margin, fabsf(qv) - eq);
+    const float cv = pass ? dot * A.w : -2.f;
+    const bool better = cv > bc;
+    sc = better ? bc : fmaxf(sc, cv);
+    bc = better ? cv : bc;
+    bq = better ? q : bq;
+}
+
+// Appends the flagged lanes' (slot, upstream) to the first level's list of
+// links left to k_memo_link; every lane of the warp calls it.
+__device__ __forceinline__ void append_miss(const MemoArgs &a, bool flag, u32 slot, u32 upv)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    unsigned long long b = 0;
+    if (lane == leader) b = atomicAdd(a.nmiss, (unsigned long long)__popc(m));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (flag) {
+        const unsigned long long q = b + __popc(m & ((1u << lane) - 1u));
+        a.miss[q] = slot;
+        a.ups[q] = upv;
+    }
+}
+
+// W target rows per block (the tile shape; 8 KB of stage per row): 32 warps
+// per SM either way.  With direction bins (a.rbn = N > 0) a pair whose
+// source is farther than every neighbour scans only its bin's candidate set;
+// the warp scans the union of its lanes' sets (a superset of each lane's:
+// the extra candidates change no decision), each entry read by every lane.
+template <int W>
+__global__ void __launch_bounds__(32 * W, 32 / W) k_memo_hop_rows(MemoArgs a)
 {
     __shared__ float4 nba[W][kRowNB];   // (r_k - r_j, rsqrt |r_k - r_j|^2)
     __shared__ float4 nbb[W][kRowNB];   // (|r_k - r_j|^2, e1, e0, -): bound e1 |b| + e0
     __shared__ float4 nbp[W][kRowNB];   // record of k
     __shared__ uint4 nbr[W][kRowNB];    // (k, row start, row end, -), slot indices
+    __shared__ unsigned char qsel[W][kRowNB];   // the candidates a warp iteration scans
     const float two_eps = 32.f * kU32;
-    const float eps_q = 16.f * kU32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned me = 1u << lane;
     const long long i = a.t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -317,74 +541,66 @@ __global__ void __launch_bounds__(32 * W, 40 / W) k_memo_hop_rows(MemoArgs a)
             warp_append(p0 + lane < r1, (u32)(p0 + lane), (u32)i, a.hard, a.nhard);
         return;
     }
-    int nst = 0;
     bool odd = false;   // a distinct neighbour whose FP32 offset underflowed
-    for (u32 b = s0; b < s1; b += 32) {
-        u32 s = b + lane;
-        bool ok = false;
-        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, P = A;
-        uint4 R = make_uint4(0u, 0u, 0u, 0u);
-        if (s < s1) {
-            u32 k = a.m.nb_idx[s];
-            if (k < a.m.np) {
-                P = a.m.pq[k];
-                float ax = P.x - pj.x, ay = P.y - pj.y, az = P.z - pj.z;
-                float a2 = ax * ax + ay * ay + az * az;
-                if (a2 == 0.f) {
-                    if (P.x != pj.x || P.y != pj.y || P.z != pj.z) odd = true;
-                } else {
-                    float ra = rsqrtf(a2);
-                    float an = a2 * ra;
-                    A = make_float4(ax, ay, az, ra);
-                    B = make_float4(a2, eps_q * 2.f * an, eps_q * a2 + 1e-37f, 0.f);
-                    R.x = k;
-                    if ((long long)k >= a.t0 && (long long)k < a.t1) {
-                        R.y = (u32)(a.off[k] - a.base);
-                        R.z = (u32)(a.off[k + 1] - a.base);
-                    }
-                    ok = true;
-                }
-            }
-        }
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            int q = nst + __popc(m & (me - 1u));
-            nba[w][q] = A;
-            nbb[w][q] = B;
-            nbp[w][q] = P;
-            nbr[w][q] = R;
-        }
-        nst += __popc(m);
-    }
-    odd = __any_sync(0xffffffffu, odd);
-    __syncwarp();
+    float amax2 = 0.f;
+    const int nst = stage_row(a.m, s0, s1, pj, a.t0, a.t1, a.off, a.base, nba[w], nbb[w],
+                              nbp[w], nbr[w], odd, amax2);
+    const unsigned long long all = nst >= 64 ? ~0ull : (1ull << nst) - 1ull;   // every candidate
+    const float amax = sqrtf(amax2);
+    const int nbins = 6 * a.rbn * a.rbn;
+    const bool count = (i & 63) == 0;   // candidate statistics on every 64th row
+    unsigned cand = 0;
     for (u64 p0 = r0; p0 < r1; p0 += 32) {   // warp-uniform: the list appends below
         const u64 p = p0 + lane;
         const bool valid = p < r1;
         u32 up = kNone, nx = kNone;
         bool hard = false;
+        u32 vid = 0;
+        float4 src = make_float4(0.f, 0.f, 0.f, 0.f);
+        float bx = 0.f, by = 0.f, bz = 0.f, bn = 0.f;
+        unsigned long long um = 0ull;   // candidates this lane must scan
         if (valid) {
-            const u32 vid = a.svid[p];
-            const float4 src = vsource(a, vid);
-            float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
-            float bn = sqrtf(bx * bx + by * by + bz * bz);
+            vid = a.svid[p];
+            src = vsource(a, vid);
+            bx = src.x - pj.x;
+            by = src.y - pj.y;
+            bz = src.z - pj.z;
+            bn = sqrtf(bx * bx + by * by + bz * bz);
+            um = all;
+            if (nbins && bn > amax) {
+                const unsigned long long bm = a.rbm[(u64)i * nbins + dir_bin(bx, by, bz, a.rbn)];
+                if (bm) um = bm;
+            }
+        }
+        int nsel = nst;   // the union of the lanes' sets, listed in qsel when smaller
+        if (nbins) {
+            const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)um);
+            const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(um >> 32));
+            const int n0 = __popc(lo);
+            nsel = n0 + __popc(hi);
+            if (nsel < nst) {
+                const unsigned below = me - 1u;
+                __syncwarp();   // the previous iteration's reads of qsel are done
+                if ((lo >> lane) & 1u) qsel[w][__popc(lo & below)] = (unsigned char)lane;
+                if ((hi >> lane) & 1u) qsel[w][n0 + __popc(hi & below)] = (unsigned char)(32 + lane);
+                __syncwarp();
+            }
+        }
+        if (valid) {
             float bc = -1.f, sc = -1.f;
             int bq = -1;
             float margin = 1.f;   // min |q| - bound: <= 0 when a test is unsure
+            if (count) cand += (unsigned)nsel;
+            if (nsel == nst) {
 #pragma unroll 4
-            for (int q = 0; q < nst; ++q) {
-                float4 A = nba[w][q];
-                float4 B = nbb[w][q];
-                float dot = bx * A.x + by * A.y + bz * A.z;
-                float qv = 2.f * dot - B.x;
-                float eq = B.y * bn + B.z;
-                bool pass = qv > eq;
-                margin = fminf(margin, fabsf(qv) - eq);
-                float cv = pass ? dot * A.w : -2.f;
-                bool better = cv > bc;
-                sc = better ? bc : fmaxf(sc, cv);
-                bc = better ? cv : bc;
-                bq = better ? q : bq;
+                for (int q = 0; q < nst; ++q)
+                    score_staged(nba[w][q], nbb[w][q], bx, by, bz, bn, q, bc, sc, bq, margin);
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < nsel; ++k) {
+                    const int q = qsel[w][k];
+                    score_staged(nba[w][q], nbb[w][q], bx, by, bz, bn, q, bc, sc, bq, margin);
+                }
             }
             if (odd || !(margin > 0.f) || (sc > 0.f && sc > bc - two_eps * bn)) {
                 hard = true;   // decided in FP64 by k_memo_hop_hard
@@ -413,19 +629,14 @@ __global__ void __launch_bounds__(32 * W, 40 / W) k_memo_hop_rows(MemoArgs a)
         }
         warp_append(hard, (u32)p, (u32)i, a.hard, a.nhard);
         // links found in up's row are done; the others are listed for
-        // k_memo_link, marked so that it skips the row search
-        const bool miss = valid && !hard && up != kNone && nx == kNone;
-        const unsigned mm = __ballot_sync(0xffffffffu, miss);
-        if (mm) {
-            const int leader = __ffs(mm) - 1;
-            unsigned long long b = 0;
-            if (lane == leader) b = atomicAdd(a.nmiss, (unsigned long long)__popc(mm));
-            b = __shfl_sync(0xffffffffu, b, leader);
-            if (miss) {
-                unsigned long long q = b + __popc(mm & (me - 1u));
-                a.miss[q] = (u32)p;
-                a.ups[q] = up | kRowMiss;
-            }
+        // k_memo_link's table, marked as searched
+        append_miss(a, valid && !hard && up != kNone && nx == kNone, (u32)p, up | kRowMiss);
+    }
+    if (count) {   // warp-uniform
+        for (int o = 16; o; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
+        if (lane == 0) {
+            atomicAdd(&a.m.counters[C_ROW_CAND], (unsigned long long)cand);
+            atomicAdd(&a.m.counters[C_ROW_NB], (unsigned long long)nst * (r1 - r0));
         }
     }
 }
@@ -943,6 +1154,67 @@ static void launch_memo_hop(const MemoArgs &a, cudaStream_t s, int nsm)
     k_memo_hop<G><<<(unsigned)blocks, 256, 0, s>>>(a);
 }
 
+// The cones of the direction bins (dir_bin) for N x N bins per face: per bin
+// (c, cos rho) and (sin rho, -, -, -), c the normalised sum of the bin's four
+// corner directions and rho the largest angle from c to a corner (the bin is
+// the central projection of a square, so the farthest point is a corner),
+// widened by 2e-3 rad.
+static void bin_cones(int N, std::vector<float4> &g)
+{
+    const int nb = 6 * N * N;
+    g.assign(2 * (size_t)nb, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int b = 0; b < nb; ++b) {
+        const int f = b / (N * N), iu = (b / N) % N, iv = b % N;
+        const double sg = (f & 1) ? -1.0 : 1.0;
+        double cr[4][3], c[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 4; ++k) {
+            const double s = -1.0 + 2.0 * (iu + (k & 1)) / N, t = -1.0 + 2.0 * (iv + (k >> 1)) / N;
+            double v[3];
+            if (f / 2 == 0) { v[0] = sg; v[1] = s; v[2] = t; }
+            else if (f / 2 == 1) { v[0] = t; v[1] = sg; v[2] = s; }
+            else { v[0] = s; v[1] = t; v[2] = sg; }
+            const double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            for (int d = 0; d < 3; ++d) {
+                cr[k][d] = v[d] / n;
+                c[d] += cr[k][d];
+            }
+        }
+        const double cn = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        for (int d = 0; d < 3; ++d) c[d] /= cn;
+        double cmin = 1.0;
+        for (int k = 0; k < 4; ++k)
+            cmin = std::min(cmin, c[0] * cr[k][0] + c[1] * cr[k][1] + c[2] * cr[k][2]);
+        const double rho = std::acos(std::max(-1.0, std::min(1.0, cmin))) + 2e-3;
+        g[2 * b] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)std::cos(rho));
+        g[2 * b + 1] = make_float4((float)std::sin(rho), 0.f, 0.f, 0.f);
+    }
+}
+
+// The first hop's candidate sets of every particle for N = start_params.row_bins
+// (kept until the next build or a change of N).
+static int build_row_bins(start_ctx *c, const MarchArgs &m)
+{
+    const int N = c->p.row_bins;
+    if (c->rb_n == N) return START_OK;
+    c->rb_n = 0;
+    const size_t nb = 6 * (size_t)N * N;
+    std::vector<float4> g;
+    bin_cones(N, g);
+    if (ensure(c->rb_geo, g.size() * sizeof(float4)) ||
+        ensure(c->rb_mask, std::max<size_t>(1, (size_t)c->np * nb) * 8))
+        return set_err(c, START_ENOMEM, "out of device memory (first-hop candidate sets)");
+    ST_CUDA(c, cudaMemcpyAsync(c->rb_geo.p, g.data(), g.size() * sizeof(float4),
+                               cudaMemcpyHostToDevice, c->stream));
+    if (c->np > 0) {
+        k_row_bins<8><<<(unsigned)((c->np + 7) / 8), 256, 0, c->stream>>>(
+            m, c->rb_geo.as<float4>(), N, c->rb_mask.as<unsigned long long>());
+        ++c->launches;
+        ST_CUDA(c, cudaGetLastError());
+    }
+    c->rb_n = N;
+    return START_OK;
+}
+
 static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t cap,
                         bool &overflow, long long t0, long long t1, u64 base)
 {
@@ -999,6 +1271,13 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     a.nmiss = ctr + C_MISS;
     a.hard = c->m_hard.as<uint2>();
     a.nhard = ctr + C_HARD;
+    a.rbm = nullptr;
+    a.rbn = 0;
+    if (c->p.row_bins) {
+        if (int e = build_row_bins(c, m)) return e;
+        a.rbm = c->rb_mask.as<unsigned long long>();
+        a.rbn = c->rb_n;
+    }
     ST_CUDA(c, cudaMemsetAsync(a.nmiss, 0, sizeof(unsigned long long), s));
     ST_CUDA(c, cudaMemsetAsync(a.nhard, 0, sizeof(unsigned long long), s));
     int nsm = 0;

@@ -8,7 +8,7 @@ from paper_1005_5312_gb300.autotune import (DEFAULTS, SEARCH_SPACE, Tuner, coord
 
 
 def test_coordinate_descent_finds_the_separable_minimum():
-    target = {"march_group": 4, "ptree_leaf": 32, "row_warps": 4, "walk_warp": 1}
+    target = {"march_group": 4, "ptree_leaf": 32, "row_warps": 4, "walk_warp": 1, "row_bins": 6}
     calls = []
 
     def cost(p):
@@ -44,7 +44,7 @@ def test_tuned_knobs_are_result_neutral():
     assert set(best) == set(DEFAULTS)
     out = []
     for p in (DEFAULTS, best, {"march_group": 8, "ptree_leaf": 8, "row_warps": 4,
-                               "walk_warp": 1}):
+                               "walk_warp": 1, "row_bins": 0}):
         ctx = S.Context(**p)
         ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
         g = np.zeros(w.n_p, np.float32)

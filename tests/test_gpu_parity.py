@@ -546,6 +546,47 @@ def test_warp_cooperative_walk_is_result_neutral(S, cfg1, diffuse):
         assert np.array_equal(g, ref[2])
 
 
+@pytest.mark.parametrize("which", ["cfg1", "ragged", "diffuse"])
+def test_first_hop_direction_bins_are_result_neutral(S, cfg1, ragged, which):
+    """The first hop scanning only its direction bin's candidate set
+    (row_bins = N) or every staged neighbour (row_bins = 0) makes the same
+    upstream choices: the same rays and chain links and bitwise the same
+    Gamma, in one piece and split into groups of virtual sources (against
+    the same split without bins: a split solve sums Gamma group by group),
+    on a ragged set with duplicated positions and on the diffuse case (emitters
+    inside the neighbour radius scan every neighbour).  The bins prune: the
+    scanned candidates fall below a full scan, and fewer first hops need the
+    FP64 re-decision."""
+    w = {"cfg1": cfg1, "ragged": ragged,
+         "diffuse": random_workload(4001, 33, 22, diffuse=True)}[which]
+    diffuse = which == "diffuse"
+    res = {}
+    for nb in (0, 2, 4, 6):
+        for max_pairs in (0, 60000):
+            ctx = S.Context(row_bins=nb, max_pairs=max_pairs, ptree_leaf=PTREE_LEAF)
+            ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L, w.V if diffuse else None,
+                            diffuse=diffuse)
+            ctx.set_state(w.n_H, w.y0)
+            g = np.zeros(w.n_p, np.float32)
+            ctx.rt_solve(0.6, gamma_out=g)
+            res[nb, max_pairs] = (g, ctx.stats())
+            if max_pairs == 0:   # a second solve reuses the candidate sets
+                g2 = np.zeros(w.n_p, np.float32)
+                ctx.rt_solve(0.6, gamma_out=g2)
+                assert np.array_equal(g, g2)
+    assert res[0, 0][1]["rays"] > 0
+    for (nb, mp), (g, st) in res.items():
+        ref_g, ref_st = res[0, mp]   # a split solve sums Gamma group by group
+        assert np.array_equal(g, ref_g), (nb, mp)
+        assert st["rays"] == ref_st["rays"] and st["hops"] == ref_st["hops"], (nb, mp)
+        assert 0 < st["first_hop_scanned"] <= st["first_hop_full"], (nb, mp)
+        if nb == 0:
+            assert st["first_hop_scanned"] == st["first_hop_full"]
+        else:
+            assert st["first_hop_scanned"] < st["first_hop_full"], (nb, mp)
+            assert st["march_fallbacks"] <= res[0, mp][1]["march_fallbacks"], (nb, mp)
+
+
 def _depth_and_caps(S, w, mode, theta):
     """Solve with no hop cap, then with hop_cap = the longest chain (must pass,
     bitwise the same Gamma) and one less (must report START_ECHAIN)."""
