@@ -869,7 +869,8 @@ def run_gpu(args):
            "gpu_launches": r1["launches"],
            "rays_per_step": st_sum["rays"] / 1.0,
            "evaluations_per_ray": st_sum["evals"] / max(1.0, st_sum["rays"]),
-           "chain_links_per_ray": st_sum["hops"] / max(1.0, st_sum["rays"]),
+           "chain_links_per_ray": (st_sum["hops"] / max(1.0, st_sum["rays"])
+                                   if st_sum["hops"] >= 0 else None),
            "chunks_per_step": st_sum["chunks"],
            "march_fallbacks_per_step": st_sum["march_fallbacks"],
            "roofline": roof, "kernels": kernels, "clocks": clocks}

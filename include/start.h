@@ -185,12 +185,22 @@ typedef struct start_params {
                               Pairs whose source is not farther than every
                               neighbour scan them all.  Does not change any
                               result */
+    int link_counts;       /* memoised march.  0 (default): the pointer jumping
+                              sums each chain's link increments in FP32 over
+                              8-byte link states, and start_stats reports hops
+                              and max_hops as -1.  1: 16-byte states that also
+                              count each chain's links (hops, max_hops) and sum
+                              in compensated double-float.  A hop cap
+                              (hop_cap > 0) or resident chains (reuse_chains)
+                              use the counting form either way */
 } start_params;
 
 /* Counters of the last start_rt_solve. */
 typedef struct start_stats {
     long long rays;             /* (target, virtual source) pairs evaluated */
-    long long hops;             /* chain links over all rays (sum of chain lengths) */
+    long long hops;             /* chain links over all rays (sum of chain lengths);
+                                   -1 when the memoised march did not count them
+                                   (start_params.link_counts) */
     long long march_fallbacks;  /* upstream choices decided in FP64 */
     long long walk_fallbacks;   /* opening tests decided in FP64 */
     long long nbr_fallbacks;    /* neighbour tests decided in FP64 (last build) */
@@ -198,17 +208,17 @@ typedef struct start_stats {
     long long nodes_emit;       /* nodes of the emitter tree (diffuse) */
     long long nodes_part;       /* nodes of the particle tree */
     long long nbr_total;        /* neighbour-list entries */
-    long long max_hops;         /* longest chain of the last solve */
+    long long max_hops;         /* longest chain of the last solve (-1: not counted) */
     long long launches;         /* kernels launched by this context so far */
     long long evals;            /* neighbour-list evaluations performed */
     long long links;            /* distinct chain links (memoised march) */
     long long chunks;           /* target chunks of the last solve */
     long long jump_rounds;      /* pointer-jumping rounds of the last solve (memoised) */
-    long long jump_bytes;       /* bytes those rounds read and wrote: 16 per slot and
-                                   round (own state), 32 per slot that advanced
-                                   (first successor read, write), 16 per further
-                                   successor read, 16 per slot copied once when its
-                                   chain closed */
+    long long jump_bytes;       /* bytes those rounds read and wrote: s per slot and
+                                   round (own state), 2 s per slot that advanced
+                                   (first successor read, write), s per further
+                                   successor read, s per slot copied once when its
+                                   chain closed; s = 8 (16 in the counting form) */
     long long first_hop_scanned;  /* memoised march, every 64th target: candidates
                                      the first hops of its pairs scanned */
     long long first_hop_full;     /* the same targets: neighbours x pairs (what a

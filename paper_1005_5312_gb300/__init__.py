@@ -41,7 +41,7 @@ class StartParams(C.Structure):
                 ("stream", C.c_void_p),
                 ("T_eff", C.c_double), ("T_rec", C.c_double), ("row_warps", C.c_int),
                 ("thermal", C.c_int), ("lum_kernel", C.c_int), ("walk_warp", C.c_int),
-                ("row_bins", C.c_int)]
+                ("row_bins", C.c_int), ("link_counts", C.c_int)]
 
 
 class StartStats(C.Structure):

@@ -389,7 +389,7 @@ static void release_all(start_ctx *c)
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_hard, &c->m_part, &c->m_table,
                    &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc, &c->klum_big, &c->trange, &c->trf2,
-                   &c->rb_mask, &c->rb_geo};
+                   &c->rb_mask, &c->rb_geo, &c->m_w[0], &c->m_w[1]};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);
@@ -464,6 +464,7 @@ static int check_params(start_params &d)
     if (d.lum_kernel != 0 && d.lum_kernel != 1) return START_EINVAL;
     if (d.walk_warp != 0 && d.walk_warp != 1) return START_EINVAL;
     if (d.row_bins != 0 && (d.row_bins < 2 || d.row_bins > 6)) return START_EINVAL;
+    if (d.link_counts != 0 && d.link_counts != 1) return START_EINVAL;
     if (d.row_warps == 0) d.row_warps = 8;
     if (d.max_pairs < 0 || d.hop_cap < 0) return START_EINVAL;
     if (!(d.T_eff == 0.0 || (d.T_eff >= 500.0 && d.T_eff <= 1e7))) return START_EINVAL;
@@ -1168,12 +1169,14 @@ int start_get_stats(start_ctx *c, start_stats *out)
     ST_CUDA(c, cudaMemcpyAsync(v, c->counters.p, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
     memset(out, 0, sizeof(*out));
+    // the memoised march counts chain links only in the counting form
+    const bool counted = c->hops_counted;
     out->rays = (long long)v[C_RAYS];
-    out->hops = (long long)v[C_HOPS];
+    out->hops = counted ? (long long)v[C_HOPS] : -1;
     out->march_fallbacks = (long long)v[C_MARCH_FB];
     out->walk_fallbacks = (long long)v[C_WALK_FB];
     out->nbr_fallbacks = (long long)v[C_NBR_FB];
-    out->max_hops = (long long)v[C_MAX_HOPS];
+    out->max_hops = counted ? (long long)v[C_MAX_HOPS] : -1;
     out->nodes_src = c->stree.n;
     out->nodes_emit = c->et.n;
     out->nodes_part = c->pt.n;

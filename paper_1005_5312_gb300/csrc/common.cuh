@@ -164,6 +164,11 @@ struct start_ctx {
     // were built for, 0 when stale
     st::DBuf rb_mask, rb_geo;
     int rb_n = 0;
+    // the counting form of the pointer jumping: 16-byte states (next, links
+    // to the end, double-float sum); memo_wide: the last memoised solve used it
+    st::DBuf m_w[2];
+    bool memo_wide = false;
+    bool hops_counted = true;   // the last solve counted chain links (start_stats.hops)
     long long memo_slots = 0;          // slots of the last memoised chunk
 
     // resident chains (reuse_chains = 1): the link forest of the last full
@@ -224,6 +229,14 @@ enum Counter {
     C_ROW_NB,     // the same targets: staged neighbours x pairs (a full scan)
     C_COUNT = 32
 };
+
+// Whether the memoised march's pointer jumping counts links (the counting
+// form): asked for, or needed by a hop cap or by resident chains (their
+// depth order).
+inline bool memo_counts_links(const start_ctx *c)
+{
+    return c->p.link_counts != 0 || c->p.hop_cap > 0 || c->p.reuse_chains != 0;
+}
 
 // ---------------------------------------------------------------- error helpers
 int set_err(start_ctx *c, int code, const std::string &msg);

@@ -61,7 +61,10 @@ struct MemoArgs {
     const u64 *off;                 // row offsets of the chunk's targets (minus base)
     long long t0, t1;               // the chunk's targets
     unsigned long long base;
-    uint4 *state;                   // slot: (next slot, links to the end, tau hi, tau lo)
+    uint2 *state;                   // slot: (next slot, d_tau of its link) as the march
+                                    // writes it; the chain sums follow by pointer jumping
+    const uint4 *wstate;            // slot: (-, links to the end, tau hi, tau lo) after
+                                    // the counting form of the jumping (else NULL)
     u32 *nx0;                       // slot: next slot before pointer jumping
     float *dl;                      // slot: geometric length of its link
     u32 *ups;                       // frontier item: upstream particle of its hop
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
         u32 up = hop<G>(a.m, j, pj, src, gl, gmask, dt, fbs, &dl);
         if (gl == 0) {
             a.ups[it] = up;
-            a.state[s] = make_uint4(kNone, 1u, __float_as_uint(dt), 0u);
+            a.state[s] = make_uint2(kNone, __float_as_uint(dt));
             a.dl[s] = dl;
             if (up == kNone) a.nx0[s] = kNone;
         }
@@ -622,7 +625,7 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_memo_hop_rows(MemoArgs a)
                     nx = find_in_bounds(a, R.y, R.z, vid, a.sord[p],
                                         row_guess(R.y, R.z, (u32)(p - r0), (u32)(r1 - r0)));
                 }
-                a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
+                a.state[p] = make_uint2(nx, __float_as_uint(dt));
                 a.dl[p] = dl;
                 a.nx0[p] = nx;
             }
@@ -665,7 +668,7 @@ __global__ void __launch_bounds__(256) k_memo_hop_hard(MemoArgs a)
                 const u64 r0 = a.off[i] - a.base, r1 = a.off[i + 1] - a.base;
                 nx = find_in_row(a, up, vid, a.sord[p], (u32)(p - r0), (u32)(r1 - r0));
             }
-            a.state[p] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
+            a.state[p] = make_uint2(nx, __float_as_uint(dt));
             a.dl[p] = dl;
             a.nx0[p] = nx;
             if (up != kNone && nx == kNone) {
@@ -842,7 +845,7 @@ __global__ void __launch_bounds__(128) k_memo_tail(MemoArgs a, long long max_ite
         u32 nx = kNone;
         bool claimed = false;
         if (up != kNone) nx = link_or_claim(a, vid, up, a.sord[s], claimed);
-        a.state[s] = make_uint4(nx, 1u, __float_as_uint(dt), 0u);
+        a.state[s] = make_uint2(nx, __float_as_uint(dt));
         a.dl[s] = dl;
         a.nx0[s] = nx;
         if (!claimed) break;
@@ -910,12 +913,100 @@ __device__ __forceinline__ float2 cadd(float2 x, float2 y)
 // links afterwards (or reaches the end of its chain).  The additions
 // combine the covered segments from the slot outwards, so the sum order
 // depends only on the chain.  A slot whose chain is resolved (next = kNone)
-// is copied once more so that both buffers hold it, then marked stable (bit
-// 31 of its link count) and never rewritten or re-read.
-constexpr u32 kStable = 0x80000000u;
+// is copied once more so that both buffers hold it, then marked stable and
+// never rewritten or re-read.
+//
+// Two forms.  The default one jumps the march's own 8-byte states (next,
+// FP32 partial sum): half the bytes of the counting form, and twice the
+// slots in flight per register.  The counting form (start_params.link_counts,
+// a hop cap, resident chains) widens them first to 16 bytes (next, links to
+// the end, compensated double-float sum) and jumps those: the chain lengths
+// give the hop statistics, the hop cap and the resident chains' depth order.
+constexpr u32 kStable = 0x80000000u;   // counting form: bit 31 of the link count
+constexpr u32 kDone = 0xfffffffeu;     // 8-byte form: next of a resolved, copied slot
 
-constexpr int kJumpR = 6;   // slots per thread (independent loads in flight)
-constexpr int kJumpG = 3;   // successor reads per slot and round
+constexpr int kJumpR = 6;    // counting form: slots per thread (independent loads in flight)
+constexpr int kJumpG = 3;    // successor reads per slot and round
+constexpr int kJumpR8 = 12;  // 8-byte form: slots per thread
+
+// The march's states widened for the counting form: one link, no
+// compensation term.
+__global__ void k_memo_widen(long long n, const uint2 *__restrict__ st, uint4 *__restrict__ w)
+{
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x) {
+        const uint2 v = st[s];
+        w[s] = make_uint4(v.x, 1u, v.y, 0u);
+    }
+}
+
+// One round of the 8-byte form.  part[3 (8 b + w) ..] accumulate warp w of
+// block b's advancing updates, extra successor reads and copies over the
+// rounds (plain stores: stream-ordered launches of the same grid).
+template <int G, int R>
+__global__ void __launch_bounds__(256) k_memo_jump8(long long n, const uint2 *__restrict__ st,
+                                                    uint2 *__restrict__ st2, unsigned *active,
+                                                    unsigned long long *ctr,
+                                                    unsigned long long *part)
+{
+    const long long s0 = (long long)blockIdx.x * (256 * R) + threadIdx.x;
+    const u32 n32 = (u32)n;
+    uint2 me[R];
+    unsigned go = 0;   // bit r: slot r advances this round
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long s = s0 + 256 * r;
+        me[r] = s < n ? st[s] : make_uint2(kDone, 0u);
+        if (me[r].x < kDone && me[r].x >= n32) {   // never expected
+            atomicAdd(&ctr[C_INTERNAL], 1ull);
+            me[r].x = kNone;
+        }
+        if (me[r].x < n32) go |= 1u << r;
+    }
+    unsigned adv = __popc(go), extra = 0, cpy = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        uint2 nx[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            nx[r] = me[r].x < n32 ? st[me[r].x] : make_uint2(kNone, 0u);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (me[r].x >= n32) continue;
+            if (g > 0) ++extra;
+            me[r] = make_uint2(nx[r].x,
+                               __float_as_uint(__uint_as_float(me[r].y) + __uint_as_float(nx[r].y)));
+        }
+    }
+    bool act = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long s = s0 + 256 * r;
+        if (s >= n) continue;
+        if ((go >> r) & 1u) {
+            if (me[r].x >= n32) me[r].x = kNone;
+            st2[s] = me[r];
+            act |= me[r].x != kNone;
+        } else if (me[r].x == kNone) {
+            me[r].x = kDone;
+            st2[s] = me[r];
+            ++cpy;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        adv += __shfl_xor_sync(0xffffffffu, adv, o);
+        extra += __shfl_xor_sync(0xffffffffu, extra, o);
+        cpy += __shfl_xor_sync(0xffffffffu, cpy, o);
+    }
+    const int lane = threadIdx.x & 31;
+    if (__any_sync(0xffffffffu, act) && lane == 0) *active = 1u;
+    if (lane == 0) {
+        unsigned long long *q = part + 3 * ((long long)blockIdx.x * 8 + (threadIdx.x >> 5));
+        q[0] += adv;
+        q[1] += extra;
+        q[2] += cpy;
+    }
+}
 
 // part[3 b .. 3 b + 2] accumulate block b's advancing updates, extra
 // successor reads and copies over the rounds (plain stores: a block index is
@@ -1062,7 +1153,7 @@ __device__ __forceinline__ float spec_lookup(const float *tab, float sidx)
 // group, the groups in row order: acc carries each target's compensated sums
 // (sum, compensation, heating sum, its compensation) from one group to the
 // next; the first group starts from zero and the last one writes Gamma.
-template <int MODE, int LANES>
+template <int MODE, int LANES, bool WIDE>
 __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, long long t0,
                                                      long long t1, u64 base, float conv,
                                                      const u32 *porig, float *gam, float *gout,
@@ -1091,8 +1182,15 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
             u64 p = e + gl;
             float v = 0.f, hv = 0.f;
             if (p < e1) {
-                uint4 st = a.state[p];
-                float tau = __uint_as_float(st.z) + __uint_as_float(st.w);
+                float tau;
+                u32 l = 0;   // links of the chain (counting form)
+                if (WIDE) {
+                    const uint4 st = a.wstate[p];
+                    tau = __uint_as_float(st.z) + __uint_as_float(st.w);
+                    l = st.y & ~kStable;
+                } else {
+                    tau = __uint_as_float(a.state[p].y);
+                }
                 u32 vid = a.svid[p];
                 float4 src = vsource(a, vid);
                 float rx = pt.x - src.x, ry = pt.y - src.y, rz = pt.z - src.z;
@@ -1109,11 +1207,12 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
                 } else {
                     v = dil * expf(-tau);
                 }
-                u32 l = st.y & ~kStable;
-                hops += l;
-                maxh = max(maxh, l);
+                if (WIDE) {
+                    hops += l;
+                    maxh = max(maxh, l);
+                    if ((long long)l > a.m.hop_cap) ovf += 1;
+                }
                 rays += 1;
-                if ((long long)l > a.m.hop_cap) ovf += 1;
             }
             for (int o = LANES / 2; o; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
             float yk = v - cmp;
@@ -1138,10 +1237,12 @@ __global__ void __launch_bounds__(256) k_memo_gamma(MemoArgs a, const u64 *off, 
         }
     }
     block_add(&a.m.counters[C_RAYS], rays);
-    block_add(&a.m.counters[C_HOPS], hops);
-    block_add(&a.m.counters[C_CHAIN_OVF], ovf);
-    for (int o = 16; o; o >>= 1) maxh = max(maxh, __shfl_xor_sync(0xffffffffu, maxh, o));
-    if (lane == 0 && maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
+    if (WIDE) {
+        block_add(&a.m.counters[C_HOPS], hops);
+        block_add(&a.m.counters[C_CHAIN_OVF], ovf);
+        for (int o = 16; o; o >>= 1) maxh = max(maxh, __shfl_xor_sync(0xffffffffu, maxh, o));
+        if (lane == 0 && maxh) atomicMax(&a.m.counters[C_MAX_HOPS], (unsigned long long)maxh);
+    }
 }
 
 template <int G>
@@ -1226,8 +1327,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     const size_t walked = (size_t)m.npairs * 4;   // the pair slots the walk wrote
     if (ensure_keep(c->m_vid, cap * 4, walked, s) || ensure(c->m_j, cap * 4) ||
         ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) ||
-        ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 16) ||
-        ensure(c->m_st[1], cap * 16) || ensure(c->m_ups, cap * 4) ||
+        ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 8) ||
+        ensure(c->m_st[1], cap * 8) || ensure(c->m_ups, cap * 4) ||
         ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_hard, (size_t)m.npairs * 8) ||
         ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
@@ -1255,7 +1356,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     a.t0 = t0;
     a.t1 = t1;
     a.base = base;
-    a.state = c->m_st[0].as<uint4>();
+    a.state = c->m_st[0].as<uint2>();
+    a.wstate = nullptr;
     a.nx0 = c->m_nx0.as<u32>();
     a.dl = c->m_dl.as<float>();
     a.ups = c->m_ups.as<u32>();
@@ -1419,21 +1521,35 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     c->memo_links += (unsigned long long)nslots;
     // pointer jumping; its flag lives in the context's small scratch (allocated
     // here too: a batch context never runs the builds that allocate it)
+    const bool wide = memo_counts_links(c);
+    if (wide && (ensure(c->m_w[0], cap * 16) || ensure(c->m_w[1], cap * 16)))
+        return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     int b = 0;
     if (ensure(c->flags, 64 + 2 * (kLevels + 1) * sizeof(unsigned long long)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     unsigned *active = c->flags.as<unsigned>() + 12;
-    const long long jblocks = (long long)grid_for(nslots, 256 * kJumpR);
-    if (ensure(c->m_part, (size_t)jblocks * 24))
+    const long long jblocks = (long long)grid_for(nslots, 256 * (wide ? kJumpR : kJumpR8));
+    const long long nparts = wide ? jblocks : jblocks * 8;   // per block / per warp
+    if (ensure(c->m_part, (size_t)nparts * 24))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
-    ST_CUDA(c, cudaMemsetAsync(c->m_part.p, 0, (size_t)jblocks * 24, s));
+    ST_CUDA(c, cudaMemsetAsync(c->m_part.p, 0, (size_t)nparts * 24, s));
+    if (wide) {
+        k_memo_widen<<<grid_for(nslots, 256), 256, 0, s>>>(nslots, c->m_st[0].as<uint2>(),
+                                                           c->m_w[0].as<uint4>());
+        ++c->launches;
+    }
     long long rounds = 0;
     for (int round = 0; round < 40; ++round) {
         ST_CUDA(c, cudaMemsetAsync(active, 0, sizeof(unsigned), s));
         if (timing) cudaEventRecord(c->hev[0], s);
-        k_memo_jump<kJumpG><<<(unsigned)jblocks, 256, 0, s>>>(nslots, c->m_st[b].as<uint4>(),
-                                                       c->m_st[b ^ 1].as<uint4>(), active, ctr,
-                                                       c->m_part.as<unsigned long long>());
+        if (wide)
+            k_memo_jump<kJumpG><<<(unsigned)jblocks, 256, 0, s>>>(
+                nslots, c->m_w[b].as<uint4>(), c->m_w[b ^ 1].as<uint4>(), active, ctr,
+                c->m_part.as<unsigned long long>());
+        else
+            k_memo_jump8<kJumpG, kJumpR8><<<(unsigned)jblocks, 256, 0, s>>>(
+                nslots, c->m_st[b].as<uint2>(), c->m_st[b ^ 1].as<uint2>(), active, ctr,
+                c->m_part.as<unsigned long long>());
         if (timing) cudaEventRecord(c->hev[1], s);
         ++c->launches;
         ++rounds;
@@ -1456,7 +1572,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
         if (cudaEventElapsedTime(&ms, c->lev_ev[2], c->lev_ev[3]) == cudaSuccess) c->link_ms += ms;
         else cudaGetLastError();
     }
-    k_sum_jump_counts<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), jblocks, ctr);
+    k_sum_jump_counts<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), nparts, ctr);
     ++c->launches;
     unsigned long long jc[3] = {0, 0, 0};
     ST_CUDA(c, cudaMemcpyAsync(&jc[0], ctr + C_JUMP_ADV, 8, cudaMemcpyDeviceToHost, s));
@@ -1466,10 +1582,13 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     c->jump_rounds += rounds;
     // own state read per slot and round; per advancing slot one successor read
     // and the write, plus the extra successor reads; closed chains copied once
-    c->jump_bytes += 16ull * (unsigned long long)nslots * (unsigned long long)rounds +
-                     32ull * jc[0] + 16ull * jc[1] + 16ull * jc[2];
+    // (16-byte states in the counting form, 8-byte ones otherwise)
+    const unsigned long long sb = wide ? 16ull : 8ull;
+    c->jump_bytes += sb * (unsigned long long)nslots * (unsigned long long)rounds +
+                     2 * sb * jc[0] + sb * jc[1] + sb * jc[2];
     if (timing) c->jump_ms += jump_ms;
     c->memo_final = b;
+    c->memo_wide = wide;
     return START_OK;
 }
 
@@ -1493,7 +1612,8 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     a.NS = (u32)c->ns;
     a.EN = (u32)(c->walk_emit ? c->et.n : 0);
     a.svid = c->m_vid.as<u32>();
-    a.state = c->m_st[c->memo_final].as<uint4>();
+    a.state = c->m_st[c->memo_final].as<uint2>();
+    a.wstate = c->memo_wide ? c->m_w[c->memo_final].as<uint4>() : nullptr;
     // a whole row per warp; the short rows of one group of a split solve eight
     // lanes each
     const int lanes = (first && last) ? 32 : 8;
@@ -1515,9 +1635,16 @@ int memo_gamma(start_ctx *c, const MarchArgs &m, long long t0, long long t1, u64
     const u64 *lo = c->loff.as<u64>();
     const u32 *po = c->porig.as<u32>();
     float *gm = c->gam.as<float>();
-#define ST_GAMMA(M, LN)                                                                 \
-    k_memo_gamma<M, LN><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, po, gm, gout, x, \
-                                                     acc, f, l)
+#define ST_GAMMA(M, LN)                                                                    \
+    do {                                                                                   \
+        if (c->memo_wide)                                                                  \
+            k_memo_gamma<M, LN, true><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base, conv, \
+                                                                   po, gm, gout, x, acc, f, l); \
+        else                                                                               \
+            k_memo_gamma<M, LN, false><<<grid, 256, 0, c->stream>>>(a, lo, t0, t1, base,    \
+                                                                    conv, po, gm, gout, x, acc, \
+                                                                    f, l);                 \
+    } while (0)
     if (c->solve_kind == 1) {
         if (lanes == 32) ST_GAMMA(1, 32); else ST_GAMMA(1, 8);
     } else if (spec) {

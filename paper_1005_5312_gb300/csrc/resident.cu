@@ -167,7 +167,8 @@ int resident_build(start_ctx *c, float theta)
         ensure(c->r_vid, P * 4))
         return set_err(c, START_ENOMEM, "out of device memory (resident chains)");
     u32 *h = hist.as<u32>(), *cursor = h + (D + 2);
-    const uint4 *st = c->m_st[c->memo_final].as<uint4>();
+    if (!c->memo_wide) return set_err(c, START_ECUDA, "internal inconsistency (chain depths)");
+    const uint4 *st = c->m_w[c->memo_final].as<uint4>();
     ST_CUDA(c, cudaMemsetAsync(h, 0, (D + 2) * sizeof(u32), s));
     k_res_hist<<<grid_for(S, 256), 256, 0, s>>>(st, S, h);
     ++c->launches;

@@ -1182,6 +1182,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     const bool spec = !kdis && spectral_mode(c);      // blackbody sources or band
     // k_dis and the spectra always take the memoised march
     const bool memo = c->p.march_mode == 1 || kdis || spec;
+    c->hops_counted = !memo || memo_counts_links(c);
     if (spec) {
         ST_TRY(spectral_table(c));
         ST_TRY(ensure(c->heat, (np ? np : 1) * sizeof(float)));

@@ -60,16 +60,18 @@ def test_multi_chunk_request_memoised_matches_per_ray_and_oracle():
     S.build()
     r = make_request(1, 609707, 20002, clumpy=False, theta=0.5)
     out = {}
-    for mode in (1, 0):
-        ctx = S.Context(march_mode=mode, tau_cut=1e30)
+    for mode, counts in ((1, 0), (1, 1), (0, 0)):
+        ctx = S.Context(march_mode=mode, tau_cut=1e30, link_counts=counts)
         ctx.build_trees(r.pos, r.h, r.src_pos, r.src_L)
         g = np.zeros(r.n_p, np.float32)
         ctx.rt_solve(r.theta, n_HI=r.n_H, gamma_out=g)
-        out[mode] = (g.astype(np.float64), ctx.stats())
+        out[mode, counts] = (g.astype(np.float64), ctx.stats())
         ctx.close()
-    (g1, s1), (g0, s0) = out[1], out[0]
-    assert s1["chunks"] > 1 and s1["rays"] == s0["rays"] and s1["hops"] == s0["hops"]
+    (g1, s1), (gc, sc), (g0, s0) = out[1, 0], out[1, 1], out[0, 0]
+    assert s1["chunks"] > 1 and s1["rays"] == s0["rays"] == sc["rays"]
+    assert sc["hops"] == s0["hops"] and s1["hops"] == -1   # counted in the counting form
     assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
+    assert np.all(np.abs(gc - g0) <= 2e-5 * np.abs(g0) + G_ABS)
     orc = oracle.Oracle(r.pos, r.h, r.src_pos, r.src_L, ptree_leaf=16, sigma_cm2=6.3e-18,
                         len_unit_cm=3.0857e21, alpha_A=4.18e-13, alpha_B=2.59e-13)
     idx = np.random.default_rng(4).choice(r.n_p, 12, replace=False)

@@ -143,10 +143,21 @@ def test_lists_bitexact(S, cfg1, theta):
 
 
 # ------------------------------------------------------------------ Gamma
-@pytest.mark.parametrize("mode", [0, 1])
+def hops_checked(st, ref, mode, counts):
+    """The memoised march counts chain links only in the counting form."""
+    if mode == 1 and counts == 0:
+        assert st["hops"] == -1 and st["max_hops"] == -1
+    else:
+        assert st["hops"] == ref
+
+
+MODES = [(0, 0), (1, 0), (1, 1)]   # (march_mode, link_counts)
+
+
+@pytest.mark.parametrize("mode,counts", MODES)
 @pytest.mark.parametrize("theta", [0.0, 0.5, 1.0])
-def test_gamma_parity_config1(S, cfg1, theta, mode):
-    ctx, orc = make_pair(S, cfg1, march_mode=mode)
+def test_gamma_parity_config1(S, cfg1, theta, mode, counts):
+    ctx, orc = make_pair(S, cfg1, march_mode=mode, link_counts=counts)
     nHI = cfg1.n_HI()
     g = np.zeros(cfg1.n_p, np.float32)
     ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
@@ -154,13 +165,13 @@ def test_gamma_parity_config1(S, cfg1, theta, mode):
     gamma_close(g, ref)
     st = ctx.stats()
     assert st["rays"] == orc.last_stats["rays"]
-    assert st["hops"] == orc.last_stats["hops"]
+    hops_checked(st, orc.last_stats["hops"], mode, counts)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode,counts", MODES)
 @pytest.mark.parametrize("theta", [0.0, 0.7])
-def test_gamma_parity_ragged_nonuniform(S, ragged, theta, mode):
-    ctx, orc = make_pair(S, ragged, march_mode=mode)
+def test_gamma_parity_ragged_nonuniform(S, ragged, theta, mode, counts):
+    ctx, orc = make_pair(S, ragged, march_mode=mode, link_counts=counts)
     nHI = (ragged.y0 * 1e-3).astype(np.float32)
     g = np.zeros(ragged.n_p, np.float32)
     ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
@@ -168,18 +179,18 @@ def test_gamma_parity_ragged_nonuniform(S, ragged, theta, mode):
     gamma_close(g, ref)
     st = ctx.stats()
     assert st["rays"] == orc.last_stats["rays"]
-    assert st["hops"] == orc.last_stats["hops"]
+    hops_checked(st, orc.last_stats["hops"], mode, counts)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_gamma_parity_mixed_neighbour_counts(S, mode):
+@pytest.mark.parametrize("mode,counts", MODES)
+def test_gamma_parity_mixed_neighbour_counts(S, mode, counts):
     """Every other particle has a 1.8x smoothing length (about 190 neighbours
     instead of 32), so the first hop of the memoised march takes both its
     staged path and its global-memory path; two pairs of particles coincide."""
     w = random_workload(3001, 40, 12, dups=2)
     w.h = w.h.copy()
     w.h[::2] *= np.float32(1.8)
-    ctx, orc = make_pair(S, w, march_mode=mode)
+    ctx, orc = make_pair(S, w, march_mode=mode, link_counts=counts)
     og, _ = ctx.neighbors()
     cnt = np.diff(og.astype(np.int64))
     assert cnt.max() > 64 and cnt.min() <= 64
@@ -190,7 +201,7 @@ def test_gamma_parity_mixed_neighbour_counts(S, mode):
     gamma_close(g, ref)
     st = ctx.stats()
     assert st["rays"] == orc.last_stats["rays"]
-    assert st["hops"] == orc.last_stats["hops"]
+    hops_checked(st, orc.last_stats["hops"], mode, counts)
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -209,21 +220,24 @@ def test_march_group_is_result_neutral(S, cfg1, group, mode):
 
 
 def test_memoised_and_per_ray_march_agree(S, cfg1):
-    """Same chains, so the same rays and chain links; tau differs only in the
-    order of the additions."""
+    """Same chains, so the same rays and chain links (counted by the counting
+    form of the pointer jumping); tau differs only in the order and precision
+    of the additions, in either form."""
     nHI = cfg1.n_HI()
     out = {}
-    for mode in (0, 1):
-        ctx = S.Context(march_mode=mode, tau_cut=1e30)
+    for mode, counts in MODES:
+        ctx = S.Context(march_mode=mode, tau_cut=1e30, link_counts=counts)
         ctx.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
         g = np.zeros(cfg1.n_p, np.float32)
         ctx.rt_solve(0.5, n_HI=nHI, gamma_out=g)
-        out[mode] = (g.astype(np.float64), ctx.stats())
-    (g0, s0), (g1, s1) = out[0], out[1]
-    assert s0["rays"] == s1["rays"] and s0["hops"] == s1["hops"]
-    assert 0 < s1["evals"] < s0["evals"] / 5      # the links are shared
-    assert s1["evals"] >= s1["rays"] and s1["links"] == s1["evals"]
-    assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
+        out[mode, counts] = (g.astype(np.float64), ctx.stats())
+    g0, s0 = out[0, 0]
+    for (g1, s1) in (out[1, 0], out[1, 1]):
+        assert s0["rays"] == s1["rays"]
+        assert 0 < s1["evals"] < s0["evals"] / 5      # the links are shared
+        assert s1["evals"] >= s1["rays"] and s1["links"] == s1["evals"]
+        assert np.all(np.abs(g1 - g0) <= 2e-5 * np.abs(g0) + G_ABS)
+    assert out[1, 1][1]["hops"] == s0["hops"] and out[1, 0][1]["hops"] == -1
 
 
 @pytest.mark.parametrize("theta,max_pairs", [(0.0, 0), (0.0, 300000), (0.6, 0)])
@@ -238,7 +252,7 @@ def test_one_walk_lists_match_the_per_ray_path(S, theta, max_pairs):
     out = {}
     for mode in (0, 1):
         ctx = S.Context(march_mode=mode, tau_cut=1e30, ptree_leaf=PTREE_LEAF,
-                        max_pairs=max_pairs)
+                        max_pairs=max_pairs, link_counts=1)
         ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
         g = np.zeros(w.n_p, np.float32)
         ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
@@ -319,7 +333,7 @@ def test_resident_chains_reproduce_full_solves(S, cfg1):
     """With static particles the links are reused: a resident step gives the
     Gamma of a full solve (same rays and links; tau summed in chain order)."""
     rng = np.random.default_rng(6)
-    full = S.Context()
+    full = S.Context(link_counts=1)
     full.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
     res = S.Context(reuse_chains=1)
     res.build_trees(cfg1.pos, cfg1.h, cfg1.src_pos, cfg1.src_L)
@@ -591,7 +605,7 @@ def _depth_and_caps(S, w, mode, theta):
     """Solve with no hop cap, then with hop_cap = the longest chain (must pass,
     bitwise the same Gamma) and one less (must report START_ECHAIN)."""
     nHI = w.n_HI()
-    ctx = S.Context(tau_cut=1e30, march_mode=mode, ptree_leaf=PTREE_LEAF)
+    ctx = S.Context(tau_cut=1e30, march_mode=mode, ptree_leaf=PTREE_LEAF, link_counts=1)
     ctx.build_trees(w.pos, w.h, w.src_pos, w.src_L)
     g = np.zeros(w.n_p, np.float32)
     ctx.rt_solve(theta, n_HI=nHI, gamma_out=g)
