@@ -174,17 +174,17 @@ typedef struct start_params {
                               adjacent targets already walk nearly the same
                               cells, and the shared traversal measured 3 %
                               slower).  Does not change any result */
-    int row_bins;          /* first hop of the memoised march: 0 scans every
-                              staged neighbour of the target for each pair; N in
-                              2..6 (default 4) bins the source direction on a
-                              cube map of N x N bins per face and scans only the
+    int row_bins;          /* upstream search of the memoised march: 0 tests
+                              every neighbour of the particle for each link; N
+                              in 2..6 (default 4) bins the source direction on a
+                              cube map of N x N bins per face and tests only the
                               bin's candidate set -- the neighbours that can
                               still be the upstream choice for some direction in
                               the bin, from bounds on their angle to it (6 N^2
-                              64-bit masks per particle, built once per build).
-                              Pairs whose source is not farther than every
-                              neighbour scan them all.  Does not change any
-                              result */
+                              64-bit masks per particle, built once per build;
+                              lists of at most 64 neighbours).  Links whose
+                              source is not farther than every neighbour test
+                              them all.  Does not change any result */
     int link_counts;       /* memoised march.  0 (default): the pointer jumping
                               sums each chain's link increments in FP32 over
                               8-byte link states, and start_stats reports hops

@@ -389,7 +389,7 @@ static void release_all(start_ctx *c)
                    &c->r_j, &c->r_up, &c->r_dl, &c->r_next, &c->r_tau, &c->r_pos, &c->r_lvl, &c->r_vid,
                    &c->m_st[0], &c->m_st[1], &c->m_ups, &c->m_fr, &c->m_hard, &c->m_part, &c->m_table,
                    &c->w_scratch, &c->w_over, &c->ctr_save, &c->g_hist, &c->gacc, &c->klum_big, &c->trange, &c->trf2,
-                   &c->rb_mask, &c->rb_geo, &c->m_w[0], &c->m_w[1]};
+                   &c->rb_mask, &c->rb_geo, &c->rb_amax, &c->m_w[0], &c->m_w[1]};
     for (DBuf *b : all) release(*b);
     tree_release(c->pt);
     tree_release(c->stree);

@@ -159,10 +159,11 @@ struct start_ctx {
 
     // memoised march: per chain link (virtual source, particle)
     st::DBuf m_vid, m_j, m_ord, m_st[2], m_ups, m_fr, m_hard, m_part, m_table, m_nx0, m_dl;
-    // first-hop candidate sets per particle and direction bin (row_bins = N:
-    // 6 N^2 u64 masks per particle) and the bins' cones; rb_n: the N they
-    // were built for, 0 when stale
-    st::DBuf rb_mask, rb_geo;
+    // upstream candidate sets per particle and direction bin (row_bins = N:
+    // 6 N^2 u64 masks per particle), each particle's largest neighbour
+    // distance (the sets hold for sources beyond it) and the bins' cones;
+    // rb_n: the N they were built for, 0 when stale
+    st::DBuf rb_mask, rb_geo, rb_amax;
     int rb_n = 0;
     // the counting form of the pointer jumping: 16-byte states (next, links
     // to the end, double-float sum); memo_wide: the last memoised solve used it

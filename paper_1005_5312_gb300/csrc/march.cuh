@@ -35,7 +35,46 @@ struct MarchArgs {
     long long hop_cap;
     float *pcon;           // per-pair contribution L e^-tau / (4 pi r^2), scaled units
     unsigned long long *counters;
+    // direction bins of the upstream search (memoised march; rbn = 0: none):
+    // per particle and bin a 64-bit mask of the neighbour-list offsets that can
+    // be the upstream choice for a source direction in the bin, valid when the
+    // source is farther than ramax (the particle's largest neighbour distance)
+    const unsigned long long *rbm = nullptr;
+    const float *ramax = nullptr;
+    int rbn = 0;
 };
+
+// Direction bins: the cube map of b = r_s - r_j with N x N bins on each face,
+// bin (f N + iu) N + iv for face f = 2 axis + (component < 0) and the two
+// other components over the major one in [-1, 1] cut into N intervals each
+// (y, z on the x faces; z, x on the y faces; x, y on the z faces).  b must
+// not be zero.
+__device__ __forceinline__ int dir_bin(float x, float y, float z, int N)
+{
+    const float ax = fabsf(x), ay = fabsf(y), az = fabsf(z);
+    int f;
+    float mj, s, t;
+    if (ax >= ay && ax >= az) {
+        f = x >= 0.f ? 0 : 1;
+        mj = ax;
+        s = y;
+        t = z;
+    } else if (ay >= az) {
+        f = y >= 0.f ? 2 : 3;
+        mj = ay;
+        s = z;
+        t = x;
+    } else {
+        f = z >= 0.f ? 4 : 5;
+        mj = az;
+        s = x;
+        t = y;
+    }
+    const float hn = 0.5f * (float)N / mj;
+    const int iu = min(N - 1, max(0, (int)((s + mj) * hn)));
+    const int iv = min(N - 1, max(0, (int)((t + mj) * hn)));
+    return (f * N + iu) * N + iv;
+}
 
 // FP64 upstream choice with the definition's operation order; the group's
 // lanes share the neighbour slots and reduce with (c desc, input index asc).
@@ -101,54 +140,82 @@ __device__ __forceinline__ float link_dt(const MarchArgs &a, float4 pj, float4 s
     return a.sig * 0.5f * (pj.w + pu.w) * dl;
 }
 
+// Candidate s of the neighbour list of particle j (record pj) for a source
+// at b = r_s - r_j (|b| = bn): the closer-than test and the score with their
+// certified error bounds; keeps the best and second-best scores and the best
+// candidate, and flags a test inside its bound.
+__device__ __forceinline__ void hop_candidate(const MarchArgs &a, u32 s, float4 pj, float bx,
+                                              float by, float bz, float bn, float &bc, float &sc,
+                                              u32 &bk, bool &unsure)
+{
+    const float eps_q = 16.f * kU32;
+    u32 k = a.nb_idx[s];
+    if (k >= a.np) return;   // cannot happen: lists hold particle indices
+    float4 pk = a.pq[k];
+    float ax = pk.x - pj.x, ay = pk.y - pj.y, az = pk.z - pj.z;
+    float a2 = ax * ax + ay * ay + az * az;
+    if (a2 == 0.f) {
+        // same position as j: never strictly closer; a nonzero offset that
+        // underflowed is left to the FP64 decision
+        if (pk.x != pj.x || pk.y != pj.y || pk.z != pj.z) unsure = true;
+        return;
+    }
+    float dot = bx * ax + by * ay + bz * az;
+    // |score error| <= 16u|b|: dot carries <= 5u|a||b|, rsqrtf <= 2 ulp
+    float ra = rsqrtf(a2);
+    float an = a2 * ra;
+    float q = 2.f * dot - a2;   // > 0 iff |r_k - r_s| < |r_j - r_s|
+    float eq = eps_q * (2.f * an * bn + a2) + 1e-37f;
+    if (q > eq) {
+        float cv = dot * ra;
+        if (cv > bc) {
+            sc = bc;
+            bc = cv;
+            bk = k;
+        } else if (cv > sc) {
+            sc = cv;
+        }
+    } else if (q >= -eq) {
+        unsure = true;
+    }
+}
+
 // One neighbour-list evaluation at particle j (record pj) toward src.
 // Returns the upstream particle (kNone at the end of the chain) and the
 // optical-depth increment dt of the link (link_dt).  Every lane of the group
-// returns the same values; fbs counts FP64 re-decisions.
+// returns the same values; fbs counts FP64 re-decisions.  With direction
+// bins (a.rbn > 0, groups of at most four lanes) a source farther than every
+// neighbour is tested against its bin's candidates only, the group's lanes
+// taking the mask's set bits in turn: the others cannot be the upstream
+// choice, so the decision is the same.
 template <int G>
 __device__ __forceinline__ u32 hop(const MarchArgs &a, u32 j, float4 pj, float4 src, int gl,
                                    unsigned gmask, float &dt, unsigned long long &fbs,
                                    float *dl_out = nullptr)
 {
     const float two_eps = 32.f * kU32;   // 2 x the 16u|b| bound on each score
-    const float eps_q = 16.f * kU32;
     float bx = src.x - pj.x, by = src.y - pj.y, bz = src.z - pj.z;
     float bn = sqrtf(bx * bx + by * by + bz * bz);
     u32 s0 = a.nb_off[j], s1 = a.nb_off[j + 1];
     float bc = -1.f, sc = -1.f;
     u32 bk = kNone;
     bool unsure = false;
+    unsigned long long msk = 0ull;   // list offsets to test, or 0: every neighbour
+    if (G <= 4 && a.rbn && s1 - s0 <= 64u && bn > a.ramax[j])
+        msk = a.rbm[(unsigned long long)j * (6 * a.rbn * a.rbn) + dir_bin(bx, by, bz, a.rbn)];
+    if (msk) {
+        unsigned long long m = msk;
+        for (int t = 0; t < gl; ++t) m &= m - 1ull;   // this lane's first bit
+        while (m) {
+            hop_candidate(a, s0 + (u32)(__ffsll((long long)m) - 1), pj, bx, by, bz, bn, bc, sc,
+                          bk, unsure);
+#pragma unroll
+            for (int t = 0; t < G; ++t) m &= m - 1ull;
+        }
+    } else {
 #pragma unroll 4
-    for (u32 s = s0 + gl; s < s1; s += G) {
-        u32 k = a.nb_idx[s];
-        if (k >= a.np) continue;   // cannot happen: lists hold particle indices
-        float4 pk = a.pq[k];
-        float ax = pk.x - pj.x, ay = pk.y - pj.y, az = pk.z - pj.z;
-        float a2 = ax * ax + ay * ay + az * az;
-        if (a2 == 0.f) {
-            // same position as j: never strictly closer; a nonzero offset that
-            // underflowed is left to the FP64 decision
-            if (pk.x != pj.x || pk.y != pj.y || pk.z != pj.z) unsure = true;
-            continue;
-        }
-        float dot = bx * ax + by * ay + bz * az;
-        // |score error| <= 16u|b|: dot carries <= 5u|a||b|, rsqrtf <= 2 ulp
-        float ra = rsqrtf(a2);
-        float an = a2 * ra;
-        float q = 2.f * dot - a2;   // > 0 iff |r_k - r_s| < |r_j - r_s|
-        float eq = eps_q * (2.f * an * bn + a2) + 1e-37f;
-        if (q > eq) {
-            float cv = dot * ra;
-            if (cv > bc) {
-                sc = bc;
-                bc = cv;
-                bk = k;
-            } else if (cv > sc) {
-                sc = cv;
-            }
-        } else if (q >= -eq) {
-            unsure = true;
-        }
+        for (u32 s = s0 + gl; s < s1; s += G)
+            hop_candidate(a, s, pj, bx, by, bz, bn, bc, sc, bk, unsure);
     }
     float mc = bc;
     u32 mk = bk;

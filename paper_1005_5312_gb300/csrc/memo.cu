@@ -92,8 +92,6 @@ struct MemoArgs {
     u32 cap;                        // slot capacity
     HEntry *table;
     unsigned long long hmask;
-    const unsigned long long *rbm;  // first-hop candidate sets per target and direction
-    int rbn;                        // bin (k_row_bins), N x N bins per cube face; 0: none
 };
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long x)
@@ -311,13 +309,15 @@ __device__ __forceinline__ void warp_append(bool flag, u32 slot, u32 tgt, uint2 
     if (flag) list[b + __popc(m & ((1u << lane) - 1u))] = make_uint2(slot, tgt);
 }
 
-// Stages the neighbour list of target i (record pj) for one warp: the
-// source-independent terms of every distinct neighbour k, in list order --
-// nba (r_k - r_j, rsqrt |r_k - r_j|^2), nbb (|r_k - r_j|^2, e1, e0, -) with
-// e1 |b| + e0 the error bound of the closer-than test, nbp the record of k,
-// nbr (k, its row bounds when its row belongs to [t0, t1)).  Returns the
-// number staged; odd is set (warp-uniform) when a distinct neighbour's FP32
-// offset underflowed, amax2 is the largest |r_k - r_j|^2 staged.
+// Stages the neighbour list of target i (record pj) for one warp, entry q at
+// list offset q: the source-independent terms of neighbour k -- nba (r_k -
+// r_j, rsqrt |r_k - r_j|^2), nbb (|r_k - r_j|^2, e1, e0, -) with e1 |b| + e0
+// the error bound of the closer-than test, nbp the record of k, nbr (k, its
+// row bounds when its row belongs to [t0, t1)).  An entry at j's own
+// position is staged as one that never passes the test (A = 0, B = (1, 0,
+// 0)).  Returns the number staged (the list length); odd is set
+// (warp-uniform) when a distinct neighbour's FP32 offset underflowed, amax2
+// is the largest |r_k - r_j|^2.
 __device__ __forceinline__ int stage_row(const MarchArgs &m, u32 s0, u32 s1, float4 pj,
                                          long long t0, long long t1, const u64 *off, u64 base,
                                          float4 *nba, float4 *nbb, float4 *nbp, uint4 *nbr,
@@ -325,14 +325,11 @@ __device__ __forceinline__ int stage_row(const MarchArgs &m, u32 s0, u32 s1, flo
 {
     const float eps_q = 16.f * kU32;
     const int lane = threadIdx.x & 31;
-    const unsigned me = 1u << lane;
-    int nst = 0;
     bool od = false;
     float mx = 0.f;
     for (u32 b = s0; b < s1; b += 32) {
         u32 s = b + lane;
-        bool ok = false;
-        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, P = A;
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = make_float4(1.f, 0.f, 0.f, 0.f), P = A;
         uint4 R = make_uint4(0u, 0u, 0u, 0u);
         if (s < s1) {
             u32 k = m.nb_idx[s];
@@ -353,57 +350,20 @@ __device__ __forceinline__ int stage_row(const MarchArgs &m, u32 s0, u32 s1, flo
                         R.z = (u32)(off[k + 1] - base);
                     }
                     mx = fmaxf(mx, a2);
-                    ok = true;
                 }
             }
-        }
-        unsigned msk = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            int q = nst + __popc(msk & (me - 1u));
+            const u32 q = s - s0;
             nba[q] = A;
             nbb[q] = B;
             nbp[q] = P;
             nbr[q] = R;
         }
-        nst += __popc(msk);
     }
     odd = __any_sync(0xffffffffu, od);
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     amax2 = mx;
     __syncwarp();
-    return nst;
-}
-
-// Direction bins of the first hop: the cube map of b = r_s - r_j with N x N
-// bins on each face, bin (f N + iu) N + iv for face f = 2 axis + (component
-// < 0) and the two other components over the major one in [-1, 1] cut into N
-// intervals each (y, z on the x faces; z, x on the y faces; x, y on the z
-// faces).  b must not be zero.
-__device__ __forceinline__ int dir_bin(float x, float y, float z, int N)
-{
-    const float ax = fabsf(x), ay = fabsf(y), az = fabsf(z);
-    int f;
-    float mj, s, t;
-    if (ax >= ay && ax >= az) {
-        f = x >= 0.f ? 0 : 1;
-        mj = ax;
-        s = y;
-        t = z;
-    } else if (ay >= az) {
-        f = y >= 0.f ? 2 : 3;
-        mj = ay;
-        s = z;
-        t = x;
-    } else {
-        f = z >= 0.f ? 4 : 5;
-        mj = az;
-        s = x;
-        t = y;
-    }
-    const float hn = 0.5f * (float)N / mj;
-    const int iu = min(N - 1, max(0, (int)((s + mj) * hn)));
-    const int iv = min(N - 1, max(0, (int)((t + mj) * hn)));
-    return (f * N + iu) * N + iv;
+    return (int)(s1 - s0);
 }
 
 // Candidate sets of the first hop per target and direction bin (an exact
@@ -416,17 +376,19 @@ __device__ __forceinline__ int dir_bin(float x, float y, float z, int N)
 // lo_j > |r_j - r_i| / (2 amax) + eta suffices, since j is closer to the
 // source iff cos > |r_j - r_i| / (2 |b|).  Such a j makes the winner's score
 // at least L, so a neighbour with hi_k < L - eta never wins: the set of B is
-// {k : hi_k >= L - eta} (bit k of a 64-bit mask over the staged order), or 0
-// when no j qualifies (the search then scans every neighbour).  eta = 1e-3
-// and the 2e-3 rad widening of rho cover the FP32 rounding of the binning,
-// of the staged offsets and of these bounds (each below 1e-6; the sines are
-// taken from 1 - cos^2 + 1e-6, an upper bound); the rows that leave the
-// stage (more than kRowNB neighbours, or an underflowed offset) get 0 masks.
+// {k : hi_k >= L - eta} (bit q of a 64-bit mask for the neighbour at list
+// offset q; entries at the target's own position are left out), or 0 when no
+// j qualifies (the search then scans every neighbour).  eta = 1e-3 and the
+// 2e-3 rad widening of rho cover the FP32 rounding of the binning, of the
+// staged offsets and of these bounds (each below 1e-6; the sines are taken
+// from 1 - cos^2 + 1e-6, an upper bound).  ramax[i] = amax; the rows that
+// leave the stage (more than kRowNB neighbours, or an underflowed offset)
+// get 0 masks and ramax = +inf.
 constexpr float kBinEta = 1e-3f;
 
 template <int W>
 __global__ void __launch_bounds__(32 * W) k_row_bins(MarchArgs m, const float4 *geo, int N,
-                                                     unsigned long long *out)
+                                                     unsigned long long *out, float *ramax)
 {
     __shared__ float4 nba[W][kRowNB], nbb[W][kRowNB], nbp[W][kRowNB];
     __shared__ uint4 nbr[W][kRowNB];
@@ -442,16 +404,21 @@ __global__ void __launch_bounds__(32 * W) k_row_bins(MarchArgs m, const float4 *
     if (s1 - s0 <= (u32)kRowNB)
         nst = stage_row(m, s0, s1, m.pq[i], 0, 0, nullptr, 0, nba[w], nbb[w], nbp[w], nbr[w],
                         odd, amax2);
-    if (odd || nst == 0 || s1 - s0 > (u32)kRowNB) {
+    if (odd || nst == 0 || s1 - s0 > (u32)kRowNB || !(amax2 > 0.f)) {
         for (int b = lane; b < nbins; b += 32) row[b] = 0ull;
+        if (lane == 0) ramax[i] = __int_as_float(0x7f800000);
         return;
     }
+    if (lane == 0) ramax[i] = sqrtf(amax2);
     // unit offsets and the closer-than threshold |r_k - r_j| / (2 amax),
-    // written over the staged records (not needed here)
+    // written over the staged records (not needed here); 2 marks an entry at
+    // the target's own position
     const float inv = 0.5f * rsqrtf(amax2);
     for (int q = lane; q < nst; q += 32) {
         const float4 A = nba[w][q];
-        nbp[w][q] = make_float4(A.x * A.w, A.y * A.w, A.z * A.w, nbb[w][q].x * A.w * inv);
+        nbp[w][q] = A.w > 0.f
+                        ? make_float4(A.x * A.w, A.y * A.w, A.z * A.w, nbb[w][q].x * A.w * inv)
+                        : make_float4(0.f, 0.f, 0.f, 2.f);
     }
     __syncwarp();
     for (int b = lane; b < nbins; b += 32) {
@@ -472,7 +439,7 @@ __global__ void __launch_bounds__(32 * W) k_row_bins(MarchArgs m, const float4 *
                 const float ct = u.x * g.x + u.y * g.y + u.z * g.z;
                 const float sn = sqrtf(fmaxf(0.f, 1.f - ct * ct) + 1e-6f);
                 const float hi = ct >= cr ? 1.f : ct * cr + sn * sr;
-                if (hi >= L - kBinEta) mk |= 1ull << q;
+                if (u.w < 1.5f && hi >= L - kBinEta) mk |= 1ull << q;
             }
         }
         row[b] = mk;
@@ -518,7 +485,7 @@ __device__ __forceinline__ void append_miss(const MemoArgs &a, bool flag, u32 sl
 }
 
 // W target rows per block (the tile shape; 8 KB of stage per row): 32 warps
-// per SM either way.  With direction bins (a.rbn = N > 0) a pair whose
+// per SM either way.  With direction bins (a.m.rbn = N > 0) a pair whose
 // source is farther than every neighbour scans only its bin's candidate set;
 // the warp scans the union of its lanes' sets (a superset of each lane's:
 // the extra candidates change no decision), each entry read by every lane.
@@ -550,7 +517,7 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_memo_hop_rows(MemoArgs a)
                               nbp[w], nbr[w], odd, amax2);
     const unsigned long long all = nst >= 64 ? ~0ull : (1ull << nst) - 1ull;   // every candidate
     const float amax = sqrtf(amax2);
-    const int nbins = 6 * a.rbn * a.rbn;
+    const int nbins = 6 * a.m.rbn * a.m.rbn;
     const bool count = (i & 63) == 0;   // candidate statistics on every 64th row
     unsigned cand = 0;
     for (u64 p0 = r0; p0 < r1; p0 += 32) {   // warp-uniform: the list appends below
@@ -571,7 +538,8 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_memo_hop_rows(MemoArgs a)
             bn = sqrtf(bx * bx + by * by + bz * bz);
             um = all;
             if (nbins && bn > amax) {
-                const unsigned long long bm = a.rbm[(u64)i * nbins + dir_bin(bx, by, bz, a.rbn)];
+                const unsigned long long bm =
+                    a.m.rbm[(u64)i * nbins + dir_bin(bx, by, bz, a.m.rbn)];
                 if (bm) um = bm;
             }
         }
@@ -1302,13 +1270,15 @@ static int build_row_bins(start_ctx *c, const MarchArgs &m)
     std::vector<float4> g;
     bin_cones(N, g);
     if (ensure(c->rb_geo, g.size() * sizeof(float4)) ||
-        ensure(c->rb_mask, std::max<size_t>(1, (size_t)c->np * nb) * 8))
+        ensure(c->rb_mask, std::max<size_t>(1, (size_t)c->np * nb) * 8) ||
+        ensure(c->rb_amax, std::max<size_t>(1, (size_t)c->np) * sizeof(float)))
         return set_err(c, START_ENOMEM, "out of device memory (first-hop candidate sets)");
     ST_CUDA(c, cudaMemcpyAsync(c->rb_geo.p, g.data(), g.size() * sizeof(float4),
                                cudaMemcpyHostToDevice, c->stream));
     if (c->np > 0) {
         k_row_bins<8><<<(unsigned)((c->np + 7) / 8), 256, 0, c->stream>>>(
-            m, c->rb_geo.as<float4>(), N, c->rb_mask.as<unsigned long long>());
+            m, c->rb_geo.as<float4>(), N, c->rb_mask.as<unsigned long long>(),
+            c->rb_amax.as<float>());
         ++c->launches;
         ST_CUDA(c, cudaGetLastError());
     }
@@ -1373,12 +1343,14 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     a.nmiss = ctr + C_MISS;
     a.hard = c->m_hard.as<uint2>();
     a.nhard = ctr + C_HARD;
-    a.rbm = nullptr;
-    a.rbn = 0;
+    a.m.rbm = nullptr;
+    a.m.ramax = nullptr;
+    a.m.rbn = 0;
     if (c->p.row_bins) {
         if (int e = build_row_bins(c, m)) return e;
-        a.rbm = c->rb_mask.as<unsigned long long>();
-        a.rbn = c->rb_n;
+        a.m.rbm = c->rb_mask.as<unsigned long long>();
+        a.m.ramax = c->rb_amax.as<float>();
+        a.m.rbn = c->rb_n;
     }
     ST_CUDA(c, cudaMemsetAsync(a.nmiss, 0, sizeof(unsigned long long), s));
     ST_CUDA(c, cudaMemsetAsync(a.nhard, 0, sizeof(unsigned long long), s));
