@@ -305,27 +305,30 @@ def phase_models(st, n_p, n_s, diffuse, chunk_count):
         "emit": {"kernels": "k_emitters, k_moments_level",
                  "bytes": (n_p * 32 + st["nodes_emit"] * 64) if diffuse else 0,
                  "model": "per particle 32 B (y, n_H, V, L out); 64 B per emitter-tree node"},
-        "walk": {"kernels": "k_walk (count, fill), k_order_keys, k_walk_compact",
-                 "bytes": rays * 12 + n_p * 16 * chunk_count,
-                 "model": "per pair 12 B (canonical id written, read, order key written); per "
-                          "target and walk its 16 B record"},
+        "walk": {"kernels": "k_walk (one walk into scratch rows, or count and fill), "
+                            "k_walk_compact, k_order_keys, k_walk_hist, k_row_bins",
+                 "bytes": rays * 16 + n_p * 16 * chunk_count,
+                 "model": "per pair 16 B (canonical id written to the scratch row, read, "
+                          "written to its slot, order key written); per target and walk its "
+                          "16 B record"},
         "hops": {"kernels": "k_memo_hop_rows, k_memo_hop_hard, k_memo_hop<G>, k_memo_tail",
                  "bytes": links * 32 + off * ALGO_BYTES_PER_EVAL + n_p * chunk_count * 676,
-                 "model": "per chain link 32 B (id and order key read; state, length and next "
-                          "written); per link outside the lists its neighbour list (516 B); per "
-                          "target and chunk its staged neighbour list (33 x 20 B + 16 B)"},
+                 "model": "per chain link 32 B (id, order key and its direction bin's candidate "
+                          "mask read; state (next, d_tau), length and next written); per link "
+                          "outside the lists its neighbour list (516 B); per target and chunk its "
+                          "staged neighbour list (33 x 20 B + 16 B)"},
         "link": {"kernels": "k_memo_link, k_memo_resolve",
                  "bytes": off * 56 + rays * 8,
                  "model": "per link outside the lists 56 B (upstream, id, key, table entry, "
                           "claimed slot, next written); per pair 8 B (row search)"},
-        "jump": {"kernels": "k_memo_jump<3>",
+        "jump": {"kernels": "k_memo_jump8<3, 12>",
                  "bytes": st["jump_bytes"],
-                 "model": "16 B own state per slot and round; 32 B per slot that advances "
-                          "(first successor read and the write); 16 B per further successor "
-                          "read; 16 B per closed chain copied once"},
+                 "model": "8 B own state (next, FP32 sum) per slot and round; 16 B per slot "
+                          "that advances (first successor read and the write); 8 B per further "
+                          "successor read; 8 B per closed chain copied once"},
         "gamma": {"kernels": "k_memo_gamma",
-                  "bytes": rays * 20 + n_p * 8,
-                  "model": "per pair 20 B (chain state, id); per target 8 B"},
+                  "bytes": rays * 12 + n_p * 8,
+                  "model": "per pair 12 B (8-byte chain state, id); per target 8 B"},
         "ionize": {"kernels": "k_ionize",
                    "bytes": n_p * (36 if diffuse else 28),
                    "model": "per particle: y read and written (16), Gamma (4), n_H (4), n_HI "

@@ -1063,11 +1063,14 @@ __global__ void __launch_bounds__(256, 2) k_memo_jump(long long n, const uint4 *
 }
 
 // Sums the per-block pointer-jumping counts into their counters.
+// (grid-strided over the entries; each block adds its sums to the counters,
+// which the caller cleared)
 __global__ void k_sum_jump_counts(const unsigned long long *part, long long nblocks,
                                   unsigned long long *ctr)
 {
     unsigned long long v[3] = {0, 0, 0};
-    for (long long k = threadIdx.x; k < nblocks; k += blockDim.x)
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nblocks;
+         k += (long long)gridDim.x * blockDim.x)
         for (int q = 0; q < 3; ++q) v[q] += part[3 * k + q];
     __shared__ unsigned long long sv[3][32];
     for (int q = 0; q < 3; ++q) {
@@ -1079,9 +1082,9 @@ __global__ void k_sum_jump_counts(const unsigned long long *part, long long nblo
         unsigned long long t[3] = {0, 0, 0};
         for (unsigned k = 0; k < blockDim.x / 32; ++k)
             for (int q = 0; q < 3; ++q) t[q] += sv[q][k];
-        ctr[C_JUMP_ADV] = t[0];
-        ctr[C_JUMP_EXTRA] = t[1];
-        ctr[C_JUMP_COPY] = t[2];
+        if (t[0]) atomicAdd(&ctr[C_JUMP_ADV], t[0]);
+        if (t[1]) atomicAdd(&ctr[C_JUMP_EXTRA], t[1]);
+        if (t[2]) atomicAdd(&ctr[C_JUMP_COPY], t[2]);
     }
 }
 
@@ -1544,7 +1547,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
         if (cudaEventElapsedTime(&ms, c->lev_ev[2], c->lev_ev[3]) == cudaSuccess) c->link_ms += ms;
         else cudaGetLastError();
     }
-    k_sum_jump_counts<<<1, 1024, 0, s>>>(c->m_part.as<unsigned long long>(), nparts, ctr);
+    for (int q : {(int)C_JUMP_ADV, (int)C_JUMP_EXTRA, (int)C_JUMP_COPY})
+        ST_CUDA(c, cudaMemsetAsync(ctr + q, 0, sizeof(unsigned long long), s));
+    k_sum_jump_counts<<<grid_for(nparts, 1024, 4 * (long long)nsm), 1024, 0, s>>>(
+        c->m_part.as<unsigned long long>(), nparts, ctr);
     ++c->launches;
     unsigned long long jc[3] = {0, 0, 0};
     ST_CUDA(c, cudaMemcpyAsync(&jc[0], ctr + C_JUMP_ADV, 8, cudaMemcpyDeviceToHost, s));
