@@ -137,7 +137,6 @@ struct start_ctx {
     st::DBuf ctr_save;            // counters before a memoised-march attempt (retries)
     bool walk_scratch = false;    // the last count walk also filled w_scratch
     unsigned long long walk_nover = 0;
-    unsigned walk_rw = 1024;      // ids per scratch row of the last one-walk count
     st::DBuf pent;    // u32 entry per pair
     st::DBuf ptgt;    // u32 target per pair
     st::DBuf pord;    // u32 order key per pair (tree tag, node of the entry)

@@ -246,14 +246,11 @@ __device__ __forceinline__ void walk_tree_warp(const TreeView &t, float4 p, bool
 
 constexpr u32 kWalkRow = 1024;                 // scratch row of the one-walk lists
 constexpr size_t kWalkScratchMax = 1ull << 30;   // bytes: larger problems count first
-// a group of a split solve: a scratch row of about 1.5x the group's mean row
-// (a power of two in [32, 1024]), the scratch at most 12 GiB
-constexpr size_t kGroupScratchMax = 12ull << 30;
 
 // Targets [t0, t1), or when only is set the listed targets only[0, t1 - t0)
-// that lie in [lo, hi) (MODE 2).  MODE 3: the first rw ids of the row of
-// target i go to ent[(i - t0) rw ...], its length to cnt[i], and targets
-// with longer rows are appended to over[].
+// that lie in [lo, hi) (MODE 2).  MODE 3: the row of target i goes to
+// ent[(i - t0) kWalkRow ...], its length to cnt[i], and targets with longer
+// rows are appended to over[].
 template <int MODE>
 __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, long long t1,
                                               TreeView st_, TreeView et_, CanonBase scb,
@@ -262,7 +259,7 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
                                               u32 *ent, u32 *tgt, u32 *ord,
                                               unsigned long long *fb_total, const u32 *only,
                                               long long lo, long long hi, u32 *over,
-                                              unsigned long long *n_over, u32 rw = kWalkRow)
+                                              unsigned long long *n_over)
 {
     constexpr bool FILL = MODE != 0;
     constexpr bool COUNT = MODE == 0 || MODE == 3;
@@ -280,10 +277,10 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
     const bool warp = st_.level != nullptr && st_.trange == nullptr;
     u32 c = 0;
     const u64 w0 = !live ? 0ull
-                         : (MODE == 3 ? (u64)(i - t0) * rw : (FILL ? off[i] - base : 0ull));
+                         : (MODE == 3 ? (u64)(i - t0) * kWalkRow : (FILL ? off[i] - base : 0ull));
     u64 w = w0;
     const u64 wend = !live ? 0ull
-                           : (MODE == 3 ? w0 + rw : (FILL ? off[i + 1] - base : 0ull));
+                           : (MODE == 3 ? w0 + kWalkRow : (FILL ? off[i + 1] - base : 0ull));
     if (live || warp) {                         // warp: every lane takes part
         float4 p = live ? pq[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         const u32 self = live ? (u32)i : kNone;
@@ -319,7 +316,7 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
             cnt[i] = c;
         } else if (MODE == 3) {
             cnt[i] = (u32)(w - w0);
-            if (w - w0 > rw) over[atomicAdd(n_over, 1ull)] = (u32)i;
+            if (w - w0 > kWalkRow) over[atomicAdd(n_over, 1ull)] = (u32)i;
         } else if (w != wend) {
             atomicAdd(fb_total, 1ull);   // internal-error counter in FILL
         }
@@ -744,7 +741,6 @@ static int walk_count(start_ctx *c, float theta, const TreeView &sv, const TreeV
                                    cudaMemcpyDeviceToHost, s));
     ST_CUDA(c, cudaStreamSynchronize(s));
     c->walk_scratch = one_walk;
-    c->walk_rw = kWalkRow;
     return START_OK;
 }
 
@@ -788,21 +784,21 @@ __global__ void k_order_keys(long long n, const u32 *vid, u32 SN, u32 NS, u32 EN
 // coalesced pass; the first hop knows each row's target, so the pair slots'
 // particle is not stored.
 // The rows of targets [t0, t1) from the one-walk scratch (rows of at most
-// rw ids; longer rows were filled in place by a second walk), copied to
-// their slots with their order keys, one warp per target.
+// kWalkRow ids; longer rows were filled in place by a second walk), copied
+// to their slots with their order keys, one warp per target.
 __global__ void k_walk_compact(long long t0, long long t1, u64 base, const u32 *cnt,
                                const u64 *off, const u32 *scratch, u32 *vid, u32 SN, u32 NS,
-                               u32 EN, const u32 *leaf_s, const u32 *leaf_e, u32 *key, u32 rw)
+                               u32 EN, const u32 *leaf_s, const u32 *leaf_e, u32 *key)
 {
     const long long i = t0 + ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x & 31;
     if (i >= t1) return;
     const u32 c = cnt[i];
     const u64 o = off[i] - base;
-    const u32 *src = scratch + (size_t)i * rw;
+    const u32 *src = scratch + (size_t)i * kWalkRow;
     for (u32 k = lane; k < c; k += 32) {
-        u32 v = c <= rw ? src[k] : vid[o + k];
-        if (c <= rw) vid[o + k] = v;
+        u32 v = c <= kWalkRow ? src[k] : vid[o + k];
+        if (c <= kWalkRow) vid[o + k] = v;
         u32 q;
         if (v < SN) q = v;
         else if ((v -= SN) < NS) q = leaf_s[v];
@@ -831,7 +827,7 @@ int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 b
         k_walk_compact<<<grid_for((t1 - t0) * 32, 256), 256, 0, c->stream>>>(
             t0, t1, base, c->lcount.as<u32>(), c->loff.as<u64>(), c->w_scratch.as<u32>(),
             c->m_vid.as<u32>(), SN, NS, EN, c->stree.leafof.as<u32>(), c->et.leafof.as<u32>(),
-            c->m_ord.as<u32>(), c->walk_rw);
+            c->m_ord.as<u32>());
         ++c->launches;
         return cuda_check(c, cudaGetLastError(), "k_walk_compact");
     }
@@ -1132,46 +1128,18 @@ static int run_grouped(start_ctx *c, float theta, float *gout_dev, long long max
         c->grp_e[0] = (u32)(std::max(P0, SN) - SN);
         c->grp_e[1] = (u32)(std::max(P1, SN) - SN);
         phase_mark(c, START_PHASE_WALK, false);
-        // one walk: the group's rows go to a scratch row per target as they
-        // are counted (longer rows are walked again into their slots)
-        double est = 0.0;
-        for (int b = groups[q].first; b < groups[q].second; ++b) est += (double)h[b];
-        est *= (double)kGroupStride / (double)(np > 0 ? np : 1);
-        u32 rw = 32;
-        while (rw < kWalkRow && (double)rw < 1.5 * est) rw *= 2;
-        while (rw > 32 && (size_t)np * rw * sizeof(u32) > kGroupScratchMax) rw /= 2;
-        const bool one = (size_t)np * rw * sizeof(u32) <= kGroupScratchMax &&
-                         !ensure(c->w_scratch, (size_t)np * rw * sizeof(u32)) &&
-                         !ensure(c->w_over, (size_t)np * sizeof(u32));
-        const u32 SN32 = (u32)SN, NS32 = (u32)c->ns, EN32 = (u32)(NT - SN);
-        if (one) {
-            ST_CUDA(c, cudaMemsetAsync(ctr + C_WALK_OVER, 0, sizeof(unsigned long long), s));
-            k_walk<3><<<grid_for(np, 128), 128, 0, s>>>(
-                c->pq.as<float4>(), 0, np, source_view(c), emitter_view(c),
-                CanonBase{0u, SN32}, CanonBase{SN32 + NS32, SN32 + NS32 + EN32}, theta * theta,
-                (double)theta * (double)theta, c->fr.cmag, c->lcount.as<u32>(), nullptr, 0ull,
-                c->w_scratch.as<u32>(), nullptr, nullptr, ctr + C_WALK_FB_GROUP, nullptr, 0, 0,
-                c->w_over.as<u32>(), ctr + C_WALK_OVER, rw);
-        } else {
-            k_walk<0><<<grid_for(np, 128), 128, 0, s>>>(
-                c->pq.as<float4>(), 0, np, source_view(c), emitter_view(c), CanonBase{},
-                CanonBase{}, theta * theta, (double)theta * (double)theta, c->fr.cmag,
-                c->lcount.as<u32>(), nullptr, 0ull, nullptr, nullptr, nullptr,
-                ctr + C_WALK_FB_GROUP, nullptr, 0, 0, nullptr, nullptr);
-        }
+        k_walk<0><<<grid_for(np, 128), 128, 0, s>>>(
+            c->pq.as<float4>(), 0, np, source_view(c), emitter_view(c), CanonBase{}, CanonBase{},
+            theta * theta, (double)theta * (double)theta, c->fr.cmag, c->lcount.as<u32>(),
+            nullptr, 0ull, nullptr, nullptr, nullptr, ctr + C_WALK_FB_GROUP, nullptr, 0, 0,
+            nullptr, nullptr);
         ++c->launches;
         ST_CUDA(c, cudaGetLastError());
         ST_TRY(exclusive_scan_u32_to_u64(c, c->lcount.as<u32>(), c->loff.as<u64>(), np));
         unsigned long long total = 0;
         ST_CUDA(c, cudaMemcpyAsync(&total, c->loff.as<u64>() + np, sizeof(total),
                                    cudaMemcpyDeviceToHost, s));
-        c->walk_nover = 0;
-        if (one)
-            ST_CUDA(c, cudaMemcpyAsync(&c->walk_nover, ctr + C_WALK_OVER, sizeof(c->walk_nover),
-                                       cudaMemcpyDeviceToHost, s));
         ST_CUDA(c, cudaStreamSynchronize(s));
-        c->walk_scratch = one;
-        c->walk_rw = rw;
         phase_mark(c, START_PHASE_WALK, true);
         if ((double)total > 1.5 * (double)maxp && groups[q].second - groups[q].first > 1) {
             const int mid = (groups[q].first + groups[q].second) / 2;
