@@ -305,12 +305,11 @@ def phase_models(st, n_p, n_s, diffuse, chunk_count):
         "emit": {"kernels": "k_emitters, k_moments_level",
                  "bytes": (n_p * 32 + st["nodes_emit"] * 64) if diffuse else 0,
                  "model": "per particle 32 B (y, n_H, V, L out); 64 B per emitter-tree node"},
-        "walk": {"kernels": "k_walk (one walk into scratch rows, or count and fill), "
-                            "k_walk_compact, k_order_keys, k_walk_hist, k_row_bins",
-                 "bytes": rays * 16 + n_p * 16 * chunk_count,
-                 "model": "per pair 16 B (canonical id written to the scratch row, read, "
-                          "written to its slot, order key written); per target and walk its "
-                          "16 B record"},
+        "walk": {"kernels": "k_walk (count, fill; or one walk into scratch rows and "
+                            "k_walk_compact), k_order_keys, k_walk_hist, k_row_bins",
+                 "bytes": rays * 12 + n_p * 16 * chunk_count,
+                 "model": "per pair 12 B (canonical id written, read, order key written); per "
+                          "target and walk its 16 B record"},
         "hops": {"kernels": "k_memo_hop_rows, k_memo_hop_hard, k_memo_hop<G>, k_memo_tail",
                  "bytes": links * 32 + off * ALGO_BYTES_PER_EVAL + n_p * chunk_count * 676,
                  "model": "per chain link 32 B (id, order key and its direction bin's candidate "
