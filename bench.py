@@ -306,7 +306,8 @@ def phase_models(st, n_p, n_s, diffuse, chunk_count):
                  "bytes": (n_p * 32 + st["nodes_emit"] * 64) if diffuse else 0,
                  "model": "per particle 32 B (y, n_H, V, L out); 64 B per emitter-tree node"},
         "walk": {"kernels": "k_walk (count, fill; or one walk into scratch rows and "
-                            "k_walk_compact), k_order_keys, k_walk_hist, k_row_bins",
+                            "k_walk_compact; the fill writes the order keys), k_walk_hist, "
+                            "k_row_bins",
                  "bytes": rays * 12 + n_p * 16 * chunk_count,
                  "model": "per pair 12 B (canonical id written, read, order key written); per "
                           "target and walk its 16 B record"},

@@ -171,6 +171,8 @@ struct start_ctx {
     bool memo_wide = false;
     bool hops_counted = true;   // the last solve counted chain links (start_stats.hops)
     long long memo_slots = 0;          // slots of the last memoised chunk
+    double memo_off_frac = -1.0;       // links outside the lists per pair, last whole-target
+    float memo_off_theta = -1.f;       // march (-1: none yet), and its opening angle
 
     // resident chains (reuse_chains = 1): the link forest of the last full
     // solve in chain-end-first level order, replayed as a CUDA graph

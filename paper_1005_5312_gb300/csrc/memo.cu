@@ -1492,6 +1492,10 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     }
     long long nslots = (long long)nslots_host;
     c->memo_slots = nslots;
+    if (t0 == 0 && t1 == c->np && m.npairs > 0) {
+        c->memo_off_frac = (double)(nslots - m.npairs) / (double)m.npairs;
+        c->memo_off_theta = theta;
+    }
     c->memo_evals += (unsigned long long)nslots;
     c->memo_links += (unsigned long long)nslots;
     // pointer jumping; its flag lives in the context's small scratch (allocated
@@ -1641,7 +1645,14 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     if (m.npairs == 0) return START_OK;
     // a chunk that does not cover every target cuts chains: more links leave its lists
     bool partial = t0 > 0 || t1 < c->np;
-    size_t cap = (size_t)m.npairs + (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
+    size_t extra = (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
+    // a whole-target march at the opening angle of the last one: 1.5x its share
+    // of links outside the lists (the slot arrays and the table shrink with it;
+    // a shortfall is retried larger)
+    if (!partial && c->memo_off_theta == theta && c->memo_off_frac >= 0.0)
+        extra = std::min(extra, (size_t)(1.5 * c->memo_off_frac * (double)m.npairs) +
+                                    (size_t)c->np / 4 + 4096);
+    size_t cap = (size_t)m.npairs + extra;
     if (ensure(c->m_vid, cap * 4) || ensure(c->m_ord, cap * 4))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
     ST_TRY(walk_fill_slots(c, theta, t0, t1, base, m.npairs));

@@ -68,25 +68,32 @@ struct RawRows {
 };
 
 struct SlotRows {
-    u32 *ent;             // canonical ids only: the order key is a function of the id
+    u32 *ent;             // canonical ids
+    u32 *key = nullptr;   // their order keys, when set (the slots' keys)
     u64 g = 0;            // group (w / 4) of the buffered entries
     int lo = 0, hi = 0;   // buffered positions [lo, hi) of the group
-    u32 e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    u32 e0 = 0, e1 = 0, e2 = 0, e3 = 0, k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+    __device__ __forceinline__ static void store4(u32 *dst, u64 b, int lo, int hi, u32 v0, u32 v1,
+                                                  u32 v2, u32 v3)
+    {
+        if (lo == 0 && hi == 4) {
+            *reinterpret_cast<uint4 *>(dst + b) = make_uint4(v0, v1, v2, v3);
+        } else {
+            if (lo <= 0 && 0 < hi) dst[b] = v0;
+            if (lo <= 1 && 1 < hi) dst[b + 1] = v1;
+            if (lo <= 2 && 2 < hi) dst[b + 2] = v2;
+            if (lo <= 3 && 3 < hi) dst[b + 3] = v3;
+        }
+    }
     __device__ __forceinline__ void flush()
     {
         if (hi <= lo) return;
         u64 b = g * 4;
-        if (lo == 0 && hi == 4) {
-            *reinterpret_cast<uint4 *>(ent + b) = make_uint4(e0, e1, e2, e3);
-        } else {
-            if (lo <= 0 && 0 < hi) ent[b] = e0;
-            if (lo <= 1 && 1 < hi) ent[b + 1] = e1;
-            if (lo <= 2 && 2 < hi) ent[b + 2] = e2;
-            if (lo <= 3 && 3 < hi) ent[b + 3] = e3;
-        }
+        store4(ent, b, lo, hi, e0, e1, e2, e3);
+        if (key) store4(key, b, lo, hi, k0, k1, k2, k3);
         lo = hi = 0;
     }
-    __device__ __forceinline__ void put(u64 w, u32 e, u32)
+    __device__ __forceinline__ void put(u64 w, u32 e, u32 kk)
     {
         u64 gw = w >> 2;
         int k = (int)(w & 3);
@@ -95,10 +102,10 @@ struct SlotRows {
             g = gw;
             lo = k;
         }
-        if (k == 0) e0 = e;
-        if (k == 1) e1 = e;
-        if (k == 2) e2 = e;
-        if (k == 3) e3 = e;
+        if (k == 0) e0 = e, k0 = kk;
+        if (k == 1) e1 = e, k1 = kk;
+        if (k == 2) e2 = e, k2 = kk;
+        if (k == 3) e3 = e, k3 = kk;
         hi = k + 1;
         if (hi == 4) flush();
     }
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(128) k_walk(const float4 *pq, long long t0, lo
         float4 p = live ? pq[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         const u32 self = live ? (u32)i : kNone;
         if (MODE >= 2) {
-            SlotRows rows{ent};
+            SlotRows rows{ent, MODE == 2 ? ord : nullptr};
             if (warp) {
                 walk_tree_warp<MODE>(st_, p, live, th2f, th2d, cmag, kNone, 0u, scb, c, w, wend,
                                      rows, fb);
@@ -761,27 +768,11 @@ static int walk_fill(start_ctx *c, float theta, const TreeView &sv, const TreeVi
 static TreeView source_view(start_ctx *c);
 static TreeView emitter_view(start_ctx *c);
 
-// Order key (tree tag, cell) of a canonical virtual-source id: the cell
-// itself, or the leaf holding a member (a count-1 cell's id is its member's,
-// and its key is that leaf either way) -- the key the walk orders rows by.
-__global__ void k_order_keys(long long n, const u32 *vid, u32 SN, u32 NS, u32 EN,
-                             const u32 *leaf_s, const u32 *leaf_e, u32 *key)
-{
-    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    u32 v = vid[p];
-    u32 k;
-    if (v < SN) k = v;
-    else if ((v -= SN) < NS) k = leaf_s[v];
-    else if ((v -= NS) < EN) k = 0x80000000u | v;
-    else k = 0x80000000u | leaf_e[v - EN];
-    key[p] = k;
-}
-
 // The memoised march's pair slots of targets [t0, t1): canonical virtual
-// source of every pair written straight into the first slots (the vid
-// buffer, which the caller sized), then its order key (ord buffer) by one
-// coalesced pass; the first hop knows each row's target, so the pair slots'
+// source of every pair and its order key (tree tag, node id of the accepted
+// cell or of the leaf holding the member: the key the rows are sorted by)
+// written straight into the first slots (the vid and ord buffers, which the
+// caller sized); the first hop knows each row's target, so the pair slots'
 // particle is not stored.
 // The rows of targets [t0, t1) from the one-walk scratch (rows of at most
 // kWalkRow ids; longer rows were filled in place by a second walk), copied
@@ -831,14 +822,14 @@ int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 b
         ++c->launches;
         return cuda_check(c, cudaGetLastError(), "k_walk_compact");
     }
+    // the walk writes every slot's order key beside its canonical id
+    (void)n;
     k_walk<2><<<grid_for(t1 - t0, 128), 128, 0, c->stream>>>(
         c->pq.as<float4>(), t0, t1, source_view(c), emitter_view(c), scb, ecb, theta * theta,
         (double)theta * (double)theta, c->fr.cmag, nullptr, c->loff.as<u64>(), base,
-        c->m_vid.as<u32>(), nullptr, nullptr, ctr + C_INTERNAL, nullptr, 0, 0, nullptr, nullptr);
-    k_order_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(
-        n, c->m_vid.as<u32>(), SN, NS, EN, c->stree.leafof.as<u32>(), c->et.leafof.as<u32>(),
-        c->m_ord.as<u32>());
-    c->launches += 2;
+        c->m_vid.as<u32>(), nullptr, c->m_ord.as<u32>(), ctr + C_INTERNAL, nullptr, 0, 0, nullptr,
+        nullptr);
+    ++c->launches;
     return cuda_check(c, cudaGetLastError(), "k_walk");
 }
 
