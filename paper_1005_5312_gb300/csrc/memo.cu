@@ -65,8 +65,9 @@ struct MemoArgs {
                                     // writes it; the chain sums follow by pointer jumping
     const uint4 *wstate;            // slot: (-, links to the end, tau hi, tau lo) after
                                     // the counting form of the jumping (else NULL)
-    u32 *nx0;                       // slot: next slot before pointer jumping
-    float *dl;                      // slot: geometric length of its link
+    u32 *nx0;                       // slot: next slot before pointer jumping } kept for
+    float *dl;                      // slot: geometric length of its link    } resident
+                                    // chains only (else NULL)
     u32 *ups;                       // frontier item: upstream particle of its hop
     unsigned long long *nslots;     // slots allocated so far
     u32 fbase;                      // frontier: slots [fbase, fbase + nf) (the links
@@ -165,8 +166,8 @@ __global__ void __launch_bounds__(256) k_memo_hop(MemoArgs a)
         if (gl == 0) {
             a.ups[it] = up;
             a.state[s] = make_uint2(kNone, __float_as_uint(dt));
-            a.dl[s] = dl;
-            if (up == kNone) a.nx0[s] = kNone;
+            if (a.dl) a.dl[s] = dl;
+            if (up == kNone && a.nx0) a.nx0[s] = kNone;
         }
     }
     if (gl != 0) fbs = 0;
@@ -594,8 +595,8 @@ __global__ void __launch_bounds__(32 * W, 32 / W) k_memo_hop_rows(MemoArgs a)
                                         row_guess(R.y, R.z, (u32)(p - r0), (u32)(r1 - r0)));
                 }
                 a.state[p] = make_uint2(nx, __float_as_uint(dt));
-                a.dl[p] = dl;
-                a.nx0[p] = nx;
+                if (a.dl) a.dl[p] = dl;
+                if (a.nx0) a.nx0[p] = nx;
             }
         }
         warp_append(hard, (u32)p, (u32)i, a.hard, a.nhard);
@@ -637,8 +638,8 @@ __global__ void __launch_bounds__(256) k_memo_hop_hard(MemoArgs a)
                 nx = find_in_row(a, up, vid, a.sord[p], (u32)(p - r0), (u32)(r1 - r0));
             }
             a.state[p] = make_uint2(nx, __float_as_uint(dt));
-            a.dl[p] = dl;
-            a.nx0[p] = nx;
+            if (a.dl) a.dl[p] = dl;
+            if (a.nx0) a.nx0[p] = nx;
             if (up != kNone && nx == kNone) {
                 unsigned long long q = atomicAdd(a.nmiss, 1ull);
                 a.miss[q] = p;
@@ -730,7 +731,7 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
         }
         if (act) {
             a.state[s].x = nx;
-            a.nx0[s] = nx;
+            if (a.nx0) a.nx0[s] = nx;
         }
     }
 }
@@ -814,8 +815,8 @@ __global__ void __launch_bounds__(128) k_memo_tail(MemoArgs a, long long max_ite
         bool claimed = false;
         if (up != kNone) nx = link_or_claim(a, vid, up, a.sord[s], claimed);
         a.state[s] = make_uint2(nx, __float_as_uint(dt));
-        a.dl[s] = dl;
-        a.nx0[s] = nx;
+        if (a.dl) a.dl[s] = dl;
+        if (a.nx0) a.nx0[s] = nx;
         if (!claimed) break;
         s = nx;
     }
@@ -836,7 +837,7 @@ __global__ void k_memo_resolve(MemoArgs a)
             u32 v = a.table[nx & ~kPending].val;
             if (v == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
             a.state[s].x = v;
-            a.nx0[s] = v;
+            if (a.nx0) a.nx0[s] = v;
         }
     }
 }
@@ -1298,9 +1299,12 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     size_t hsize = 1;
     while (hsize < 2 * (cap - (size_t)m.npairs) + 1024) hsize <<= 1;
     const size_t walked = (size_t)m.npairs * 4;   // the pair slots the walk wrote
+    // every link's pre-jump next and length, for the resident chains' capture
+    const bool keep = c->p.reuse_chains != 0;
     if (ensure_keep(c->m_vid, cap * 4, walked, s) || ensure(c->m_j, cap * 4) ||
-        ensure_keep(c->m_ord, cap * 4, walked, s) || ensure(c->m_nx0, cap * 4) ||
-        ensure(c->m_dl, cap * 4) || ensure(c->m_st[0], cap * 8) ||
+        ensure_keep(c->m_ord, cap * 4, walked, s) ||
+        (keep && (ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4))) ||
+        ensure(c->m_st[0], cap * 8) ||
         ensure(c->m_st[1], cap * 8) || ensure(c->m_ups, cap * 4) ||
         ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_hard, (size_t)m.npairs * 8) ||
         ensure(c->m_table, hsize * sizeof(HEntry)))
@@ -1331,8 +1335,8 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
     a.base = base;
     a.state = c->m_st[0].as<uint2>();
     a.wstate = nullptr;
-    a.nx0 = c->m_nx0.as<u32>();
-    a.dl = c->m_dl.as<float>();
+    a.nx0 = keep ? c->m_nx0.as<u32>() : nullptr;
+    a.dl = keep ? c->m_dl.as<float>() : nullptr;
     a.ups = c->m_ups.as<u32>();
     a.nslots = ctr + C_SLOTS;
     a.cap = (u32)cap;
