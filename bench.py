@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--march-group", type=int, default=2)
     ap.add_argument("--row-bins", type=int, default=4,
                     help="first-hop direction bins per cube-face edge (0: scan every neighbour)")
-    ap.add_argument("--max-pairs", type=int, default=1_500_000_000,
+    ap.add_argument("--max-pairs", type=int, default=3_000_000_000,
                     help="interaction pairs per group of the large run (device memory of the "
-                         "march about 90 B per pair)")
+                         "march about 60 B per pair)")
     ap.add_argument("--nside", type=int, default=256,
                     help="lattice side of the headline workload (256: the benchmark; "
                          "smaller: profiling cases)")

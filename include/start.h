@@ -112,7 +112,9 @@ typedef struct start_params {
                               subnormal relative to any representable flux) */
     long long hop_cap;     /* max upstream steps per ray (0 = N_p + 1) */
     long long max_pairs;   /* interaction pairs solved at once (bounds the device
-                              memory of a solve, about 90 B per pair; 0 = 2^27).
+                              memory of a solve, about 60 B per pair; 0 = 2^27;
+                              a group of a memoised solve holds at most 3.5e9:
+                              32-bit link ids).
                               A larger memoised solve is split by virtual source:
                               groups of cells (depth-first index ranges) whose
                               rows are walked and marched over every target at

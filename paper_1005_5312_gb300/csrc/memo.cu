@@ -41,7 +41,11 @@ int walk_fill_slots(start_ctx *c, float theta, long long t0, long long t1, u64 b
                     long long npairs);
 int ensure_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s);
 
-constexpr u32 kPending = 0x80000000u;
+// next of a link whose slot another thread claims in the same launch: the
+// link's table index waits in ups[] at the item's frontier position until
+// k_memo_resolve reads the published slot (slot ids use all 32 bits below
+// the three reserved values kPendMark, kDone and kNone)
+constexpr u32 kPendMark = 0xfffffffdu;
 constexpr u32 kRowMiss = 0x80000000u;   // frontier item: upstream not in its row
 constexpr unsigned long long kEmptyKey = ~0ull;
 
@@ -701,7 +705,11 @@ __global__ void __launch_bounds__(256) k_memo_link(MemoArgs a)
                     }
                     if (k == lk) {
                         u32 v = *(volatile unsigned int *)&a.table[h].val;
-                        nx = (v != kNone) ? v : (kPending | (u32)h);
+                        nx = v;
+                        if (v == kNone) {
+                            nx = kPendMark;
+                            a.ups[it] = (u32)h;
+                        }
                         placed = true;
                         break;
                     }
@@ -751,7 +759,7 @@ constexpr long long kTailMax = 1 << 18;   // frontier size that switches to the 
 // of the table -- found (or pending when its claimant has not published it
 // yet) or claimed here (claimed = true).
 __device__ __forceinline__ u32 link_or_claim(const MemoArgs &a, u32 vid, u32 up, u32 key,
-                                             bool &claimed)
+                                             bool &claimed, u32 &hpend)
 {
     claimed = false;
     if ((long long)up >= a.t0 && (long long)up < a.t1 && in_row(a, up, vid, key)) {
@@ -782,7 +790,11 @@ __device__ __forceinline__ u32 link_or_claim(const MemoArgs &a, u32 vid, u32 up,
         }
         if (k == lk) {
             u32 v = *(volatile unsigned int *)&a.table[h].val;
-            return (v != kNone) ? v : (kPending | (u32)h);
+            if (v == kNone) {
+                hpend = (u32)h;
+                return kPendMark;
+            }
+            return v;
         }
         h = (h + 1) & a.hmask;
     }
@@ -811,9 +823,12 @@ __global__ void __launch_bounds__(128) k_memo_tail(MemoArgs a, long long max_ite
         const float4 src = vsource(a, vid);
         float dt, dl;
         const u32 up = hop<1>(a.m, j, a.m.pq[j], src, 0, me, dt, fbs, &dl);
-        u32 nx = kNone;
+        u32 nx = kNone, hpend = 0;
         bool claimed = false;
-        if (up != kNone) nx = link_or_claim(a, vid, up, a.sord[s], claimed);
+        if (up != kNone) nx = link_or_claim(a, vid, up, a.sord[s], claimed, hpend);
+        // a pending link's table index at the slot's position after fbase
+        // (k_memo_resolve then runs over the slots from fbase on)
+        if (nx == kPendMark) a.ups[s - a.fbase] = hpend;
         a.state[s] = make_uint2(nx, __float_as_uint(dt));
         if (a.dl) a.dl[s] = dl;
         if (a.nx0) a.nx0[s] = nx;
@@ -833,8 +848,8 @@ __global__ void k_memo_resolve(MemoArgs a)
          it += (long long)gridDim.x * blockDim.x) {
         u32 s = a.fr ? a.fr[it] : fbase + (u32)it;
         u32 nx = a.state[s].x;
-        if (nx != kNone && (nx & kPending)) {
-            u32 v = a.table[nx & ~kPending].val;
+        if (nx == kPendMark) {
+            u32 v = a.table[a.ups[it]].val;
             if (v == kNone) atomicAdd(&a.m.counters[C_INTERNAL], 1ull);
             a.state[s].x = v;
             if (a.nx0) a.nx0[s] = v;
@@ -1649,7 +1664,7 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     if (m.npairs == 0) return START_OK;
     // a chunk that does not cover every target cuts chains: more links leave its lists
     bool partial = t0 > 0 || t1 < c->np;
-    size_t extra = (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
+    size_t extra = (size_t)(m.npairs / (partial ? 2 : 6)) + (size_t)c->np + 4096;
     // a whole-target march at the opening angle of the last one: 1.5x its share
     // of links outside the lists (the slot arrays and the table shrink with it;
     // a shortfall is retried larger)
@@ -1669,8 +1684,8 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     unsigned long long *saved = c->ctr_save.as<unsigned long long>();
     ST_CUDA(c, cudaMemcpyAsync(saved, ctr, C_COUNT * sizeof(unsigned long long),
                                cudaMemcpyDeviceToDevice, c->stream));
-    // slot ids and table indices must stay below the pending flag (2^31)
-    const size_t cap_max = (1ull << 31) - 1;
+    // slot ids stay below the reserved values kPendMark, kDone and kNone
+    const size_t cap_max = 0xfffffff0ull;
     if ((size_t)m.npairs >= cap_max) return set_err(c, START_ERANGE, "too many chain links");
     cap = std::min(cap, cap_max);
     for (int attempt = 0; attempt < 5; ++attempt) {

@@ -1133,9 +1133,9 @@ static int run_grouped(start_ctx *c, float theta, float *gout_dev, long long max
         ST_CUDA(c, cudaStreamSynchronize(s));
         phase_mark(c, START_PHASE_WALK, true);
         // a group far above its plan is split in two; so is one whose links
-        // could outgrow the 31-bit slot ids (chain links run about 10 % above
+        // could outgrow the 32-bit slot ids (chain links run about 10 % above
         // the pairs)
-        if (((double)total > 1.5 * (double)maxp || (double)total > 1.75e9) &&
+        if (((double)total > 1.5 * (double)maxp || (double)total > 3.5e9) &&
             groups[q].second - groups[q].first > 1) {
             const int mid = (groups[q].first + groups[q].second) / 2;
             groups.insert(groups.begin() + q + 1, {mid, groups[q].second});
