@@ -376,6 +376,7 @@ static int shift_copy(start_ctx *c, u32 *dst, const u32 *src, long long n, u32 a
 
 static void release_all(start_ctx *c)
 {
+    c->rb_n = c->rb_geo_n = 0;
     destroy_batch_parts(c);
     resident_reset(c);
     if (c->r_cap) cudaStreamDestroy(c->r_cap);

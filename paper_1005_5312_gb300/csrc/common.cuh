@@ -164,7 +164,7 @@ struct start_ctx {
     // distance (the sets hold for sources beyond it) and the bins' cones;
     // rb_n: the N they were built for, 0 when stale
     st::DBuf rb_mask, rb_geo, rb_amax;
-    int rb_n = 0;
+    int rb_n = 0, rb_geo_n = 0;   // rb_geo_n: the N of the cones in rb_geo
     // the counting form of the pointer jumping: 16-byte states (next, links
     // to the end, double-float sum); memo_wide: the last memoised solve used it
     st::DBuf m_w[2];

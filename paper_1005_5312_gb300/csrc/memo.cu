@@ -1286,14 +1286,18 @@ static int build_row_bins(start_ctx *c, const MarchArgs &m)
     if (c->rb_n == N) return START_OK;
     c->rb_n = 0;
     const size_t nb = 6 * (size_t)N * N;
-    std::vector<float4> g;
-    bin_cones(N, g);
-    if (ensure(c->rb_geo, g.size() * sizeof(float4)) ||
-        ensure(c->rb_mask, std::max<size_t>(1, (size_t)c->np * nb) * 8) ||
+    if (ensure(c->rb_mask, std::max<size_t>(1, (size_t)c->np * nb) * 8) ||
         ensure(c->rb_amax, std::max<size_t>(1, (size_t)c->np) * sizeof(float)))
         return set_err(c, START_ENOMEM, "out of device memory (first-hop candidate sets)");
-    ST_CUDA(c, cudaMemcpyAsync(c->rb_geo.p, g.data(), g.size() * sizeof(float4),
-                               cudaMemcpyHostToDevice, c->stream));
+    if (c->rb_geo_n != N) {   // the cones depend on N only: uploaded once (a pageable copy)
+        std::vector<float4> g;
+        bin_cones(N, g);
+        if (ensure(c->rb_geo, g.size() * sizeof(float4)))
+            return set_err(c, START_ENOMEM, "out of device memory (first-hop candidate sets)");
+        ST_CUDA(c, cudaMemcpyAsync(c->rb_geo.p, g.data(), g.size() * sizeof(float4),
+                                   cudaMemcpyHostToDevice, c->stream));
+        c->rb_geo_n = N;
+    }
     if (c->np > 0) {
         k_row_bins<8><<<(unsigned)((c->np + 7) / 8), 256, 0, c->stream>>>(
             m, c->rb_geo.as<float4>(), N, c->rb_mask.as<unsigned long long>(),
@@ -1320,7 +1324,7 @@ static int memo_attempt(start_ctx *c, const MarchArgs &m, float theta, size_t ca
         ensure_keep(c->m_ord, cap * 4, walked, s) ||
         (keep && (ensure(c->m_nx0, cap * 4) || ensure(c->m_dl, cap * 4))) ||
         ensure(c->m_st[0], cap * 8) ||
-        ensure(c->m_st[1], cap * 8) || ensure(c->m_ups, cap * 4) ||
+        (!memo_counts_links(c) && ensure(c->m_st[1], cap * 8)) || ensure(c->m_ups, cap * 4) ||
         ensure(c->m_fr, (size_t)m.npairs * 4) || ensure(c->m_hard, (size_t)m.npairs * 8) ||
         ensure(c->m_table, hsize * sizeof(HEntry)))
         return set_err(c, START_ENOMEM, "out of device memory (memoised march)");
@@ -1664,10 +1668,11 @@ int run_memo(start_ctx *c, const MarchArgs &m, float theta, long long t0, long l
     if (m.npairs == 0) return START_OK;
     // a chunk that does not cover every target cuts chains: more links leave its lists
     bool partial = t0 > 0 || t1 < c->np;
-    size_t extra = (size_t)(m.npairs / (partial ? 2 : 6)) + (size_t)c->np + 4096;
-    // a whole-target march at the opening angle of the last one: 1.5x its share
-    // of links outside the lists (the slot arrays and the table shrink with it;
-    // a shortfall is retried larger)
+    size_t extra = (size_t)(m.npairs / (partial ? 2 : 4)) + (size_t)c->np + 4096;
+    // a later group of a split solve: 1.5x the last group's share of links
+    // outside the lists (the slot arrays and the table shrink with it; a
+    // shortfall is retried larger).  Unrelated solves (a server's requests)
+    // start from the default: a retry costs a whole march.
     if (!partial && c->memo_off_theta == theta && c->memo_off_frac >= 0.0)
         extra = std::min(extra, (size_t)(1.5 * c->memo_off_frac * (double)m.npairs) +
                                     (size_t)c->np / 4 + 4096);

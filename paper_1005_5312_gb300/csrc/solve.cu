@@ -1170,6 +1170,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
     cudaStream_t s = c->stream;
     c->npairs = 0;
     c->memo_evals = c->memo_links = 0;
+    c->memo_off_frac = -1.0;   // measured per solve, for its later groups
     c->jump_rounds = 0;
     c->jump_bytes = 0;
     ST_CUDA(c, cudaMemsetAsync(c->counters.p, 0, C_COUNT * sizeof(unsigned long long), s));

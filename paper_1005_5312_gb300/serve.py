@@ -113,6 +113,9 @@ class Server:
         self.retries = 0
         self.trims = 0
         self.max_pairs = int(max_pairs)
+        # resident chains pay off over several coupled steps of one request;
+        # unless fixed here, each request sets them by its step count
+        self.reuse_fixed = "reuse_chains" in params
         self.params = dict(dict(reuse_chains=1), **params, max_pairs=self.max_pairs)
         self.workers = []
         for _ in range(max(1, workers)):
@@ -137,8 +140,11 @@ class Server:
         w.ctx = Context(stream=w.stream, **self.params)
 
     def _run(self, ctx, req: SolveRequest):
+        knobs = {} if self.reuse_fixed else {"reuse_chains": int(req.steps > 1)}
         if self.tuner is not None:
-            ctx.set_params(**self.tuner.params_for(req.n_p, req.n_s, req.theta))
+            knobs.update(self.tuner.params_for(req.n_p, req.n_s, req.theta))
+        if knobs:
+            ctx.set_params(**knobs)
         ctx.build_trees(req.pos, req.h, req.src_pos, req.src_L)
         y = np.ascontiguousarray(req.y0, dtype=np.float64).copy()
         g = np.zeros(req.n_p, np.float32)
