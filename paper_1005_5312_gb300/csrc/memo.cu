@@ -415,36 +415,47 @@ __global__ void __launch_bounds__(32 * W) k_row_bins(MarchArgs m, const float4 *
         return;
     }
     if (lane == 0) ramax[i] = sqrtf(amax2);
-    // unit offsets and the closer-than threshold |r_k - r_j| / (2 amax),
-    // written over the staged records (not needed here); 2 marks an entry at
-    // the target's own position
+    // per neighbour: unit offset e_k and t_k = |r_k - r_j| / (2 amax) + eta
+    // (over the staged record; 2 marks an entry at the target's own position)
+    // and sqrt(1 - t_k^2) (over the bound coefficients); with a_k = acos t_k,
+    // k passes the closer-than test for the whole bin iff theta_k < a_k - rho
+    // (a_k > rho), i.e. cos theta_k > cos(a_k - rho) = t_k cos rho + sqrt(1 -
+    // t_k^2) sin rho; the qualifying neighbour of largest cos theta_k sets L
     const float inv = 0.5f * rsqrtf(amax2);
     for (int q = lane; q < nst; q += 32) {
         const float4 A = nba[w][q];
-        nbp[w][q] = A.w > 0.f
-                        ? make_float4(A.x * A.w, A.y * A.w, A.z * A.w, nbb[w][q].x * A.w * inv)
-                        : make_float4(0.f, 0.f, 0.f, 2.f);
+        if (A.w > 0.f) {
+            const float t = nbb[w][q].x * A.w * inv + kBinEta;
+            nbp[w][q] = make_float4(A.x * A.w, A.y * A.w, A.z * A.w, t);
+            nbb[w][q].w = sqrtf(fmaxf(0.f, 1.f - t * t));
+        } else {
+            nbp[w][q] = make_float4(0.f, 0.f, 0.f, 2.f);
+        }
     }
     __syncwarp();
     for (int b = lane; b < nbins; b += 32) {
         const float4 g = geo[2 * b];
-        const float cr = g.w, sr = geo[2 * b + 1].x;
-        float L = -2.f;
+        const float cr = g.w, sr = geo[2 * b + 1].x, rho = geo[2 * b + 1].y;
+        float best = -2.f;   // cos theta of the qualifying neighbour nearest the axis
         for (int q = 0; q < nst; ++q) {
             const float4 u = nbp[w][q];
             const float ct = u.x * g.x + u.y * g.y + u.z * g.z;
-            const float sn = sqrtf(fmaxf(0.f, 1.f - ct * ct) + 1e-6f);
-            const float lo = ct <= -cr ? -1.f : ct * cr - sn * sr;
-            if (lo > u.w + kBinEta) L = fmaxf(L, lo);
+            const float thr = u.w * cr + nbb[w][q].w * sr;
+            if (u.w < cr && ct > thr + 1e-5f) best = fmaxf(best, ct);
         }
         unsigned long long mk = 0ull;
-        if (L > -2.f) {
+        if (best > -2.f) {
+            // L = cos(theta + rho) of that neighbour (its sine from above: L
+            // from below); k can win only if theta_k <= acos(L - eta) + rho
+            const float sn = sqrtf(fmaxf(0.f, 1.f - best * best) + 1e-6f);
+            const float L = best <= -cr ? -1.f : best * cr - sn * sr;
+            const float Lp = L - kBinEta;
+            const float ang = Lp <= -1.f ? 4.f : acosf(Lp) + rho;
+            const float cmin = ang >= 3.14159f ? -2.f : cosf(ang) - 1e-5f;
             for (int q = 0; q < nst; ++q) {
                 const float4 u = nbp[w][q];
                 const float ct = u.x * g.x + u.y * g.y + u.z * g.z;
-                const float sn = sqrtf(fmaxf(0.f, 1.f - ct * ct) + 1e-6f);
-                const float hi = ct >= cr ? 1.f : ct * cr + sn * sr;
-                if (u.w < 1.5f && hi >= L - kBinEta) mk |= 1ull << q;
+                if (u.w < 1.5f && ct >= cmin) mk |= 1ull << q;
             }
         }
         row[b] = mk;
@@ -1243,7 +1254,7 @@ static void launch_memo_hop(const MemoArgs &a, cudaStream_t s, int nsm)
 }
 
 // The cones of the direction bins (dir_bin) for N x N bins per face: per bin
-// (c, cos rho) and (sin rho, -, -, -), c the normalised sum of the bin's four
+// (c, cos rho) and (sin rho, rho, -, -), c the normalised sum of the bin's four
 // corner directions and rho the largest angle from c to a corner (the bin is
 // the central projection of a square, so the farthest point is a corner),
 // widened by 2e-3 rad.
@@ -1274,7 +1285,7 @@ static void bin_cones(int N, std::vector<float4> &g)
             cmin = std::min(cmin, c[0] * cr[k][0] + c[1] * cr[k][1] + c[2] * cr[k][2]);
         const double rho = std::acos(std::max(-1.0, std::min(1.0, cmin))) + 2e-3;
         g[2 * b] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)std::cos(rho));
-        g[2 * b + 1] = make_float4((float)std::sin(rho), 0.f, 0.f, 0.f);
+        g[2 * b + 1] = make_float4((float)std::sin(rho), (float)rho, 0.f, 0.f);
     }
 }
 
