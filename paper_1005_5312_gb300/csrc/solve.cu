@@ -988,11 +988,11 @@ __global__ void k_set_evals(unsigned long long *ctr, unsigned long long evals,
 // whenever k's walk lists v, so only the method's own boundary links leave
 // the lists -- splitting by target would cut every chain at the edge of the
 // target range.  Groups are planned from a histogram of the pairs over
-// kGroupBins equal ranges of cell index, taken on every kGroupStride-th
-// target; each group's exact count comes from its own counting walk, and a
-// group that exceeds the plan by half is halved.
+// kGroupBins equal ranges of cell index, taken on every stride-th target
+// (4 up to 4 M targets, then about a million samples: at most 64); each
+// group's exact count comes from its own counting walk, and a group that
+// exceeds the plan by half is halved.
 constexpr int kGroupBins = 2048;
-constexpr int kGroupStride = 4;
 
 struct HistRows {
     u32 *bins;
@@ -1019,15 +1019,15 @@ struct HistRows {
     }
 };
 
-__global__ void __launch_bounds__(128) k_walk_hist(const float4 *pq, long long np, TreeView st_,
-                                                   TreeView et_, float th2f, double th2d,
-                                                   float cmag, u32 SN, unsigned long long NT,
-                                                   unsigned long long *hist)
+__global__ void __launch_bounds__(128) k_walk_hist(const float4 *pq, long long np, int stride,
+                                                   TreeView st_, TreeView et_, float th2f,
+                                                   double th2d, float cmag, u32 SN,
+                                                   unsigned long long NT, unsigned long long *hist)
 {
     __shared__ u32 bins[kGroupBins];
     for (int k = threadIdx.x; k < kGroupBins; k += blockDim.x) bins[k] = 0u;
     __syncthreads();
-    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kGroupStride;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * stride;
     if (i < np) {
         const float4 p = pq[i];
         u32 c = 0;
@@ -1055,7 +1055,8 @@ struct GroupViews {
     }
 };
 
-// Sampled pair histogram over the cell index ranges (kGroupBins values).
+// Sampled pair histogram over the cell index ranges (kGroupBins values),
+// scaled to estimates of the pairs of every target.
 static int group_histogram(start_ctx *c, float theta, std::vector<unsigned long long> &h)
 {
     const u32 SN = (u32)c->stree.n, EN = (u32)(c->walk_emit ? c->et.n : 0);
@@ -1064,15 +1065,17 @@ static int group_histogram(start_ctx *c, float theta, std::vector<unsigned long 
     ST_TRY(ensure(c->g_hist, kGroupBins * sizeof(unsigned long long)));
     unsigned long long *d = c->g_hist.as<unsigned long long>();
     ST_CUDA(c, cudaMemsetAsync(d, 0, kGroupBins * sizeof(unsigned long long), c->stream));
-    const long long ns = (c->np + kGroupStride - 1) / kGroupStride;
+    const int stride = (int)std::min<long long>(64, std::max<long long>(4, c->np >> 20));
+    const long long ns = (c->np + stride - 1) / stride;
     k_walk_hist<<<grid_for(ns, 128), 128, 0, c->stream>>>(
-        c->pq.as<float4>(), c->np, source_view(c), emitter_view(c), theta * theta,
+        c->pq.as<float4>(), c->np, stride, source_view(c), emitter_view(c), theta * theta,
         (double)theta * (double)theta, c->fr.cmag, SN, (unsigned long long)SN + EN, d);
     ++c->launches;
     ST_CUDA(c, cudaGetLastError());
     ST_CUDA(c, cudaMemcpyAsync(h.data(), d, kGroupBins * sizeof(unsigned long long),
                                cudaMemcpyDeviceToHost, c->stream));
     ST_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (unsigned long long &v : h) v *= (unsigned long long)stride;
     return START_OK;
 }
 
@@ -1090,7 +1093,7 @@ static int run_grouped(start_ctx *c, float theta, float *gout_dev, long long max
     // bins [b0, b1) of each group, about 0.8 max_pairs each by the sample
     std::vector<std::pair<int, int>> groups;
     {
-        const double target = 0.9 * (double)maxp / kGroupStride;
+        const double target = 0.9 * (double)maxp;
         int b0 = 0;
         double acc = 0.0;
         for (int b = 0; b < kGroupBins; ++b) {
@@ -1205,7 +1208,7 @@ int run_solve(start_ctx *c, float theta, float *gout_dev)
         // needs groups skips the counting walk over every target
         ST_TRY(group_histogram(c, theta, hist));
         double est = 0.0;
-        for (unsigned long long v : hist) est += (double)v * kGroupStride;
+        for (unsigned long long v : hist) est += (double)v;
         grouped = est > 1.25 * (double)maxp;
     }
     if (!grouped) {
