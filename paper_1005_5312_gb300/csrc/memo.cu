@@ -13,16 +13,19 @@
 // Work is level-synchronous:
 //   1. every interaction pair (v, target) is slot p; links outside the lists
 //      get slots through a hash table keyed by (v, particle);
-//   2. each frontier slot takes one hop; its upstream link (v, up) is found
-//      in the table or claimed as a new slot, which joins the next frontier;
-//      links claimed by another group in the same launch are resolved by a
-//      second kernel, after the launch boundary.  The frontier's size stays
-//      on the device, so several levels are issued per host round trip, and
-//      once it is small one kernel follows each remaining chain to its end;
-//   3. tau of every slot follows by compensated pointer jumping over the
-//      link forest (each round reads three successors, so log4 of the longest
-//      chain rounds; double-buffered, so the sum order depends only on the
-//      chain);
+//   2. each frontier slot takes one hop (the upstream search tests only the
+//      neighbours of its direction bin that can win); its upstream link
+//      (v, up) is found in up's row or the table, or claimed as a new slot,
+//      which joins the next frontier; links claimed by another group in the
+//      same launch are resolved by a second kernel, after the launch
+//      boundary.  The frontier's size stays on the device, so several levels
+//      are issued per host round trip, and once it is small one kernel
+//      follows each remaining chain to its end;
+//   3. tau of every slot follows by pointer jumping over the link forest
+//      (each round reads three successors, so log4 of the longest chain
+//      rounds; double-buffered, so the sum order depends only on the chain):
+//      FP32 sums over the march's 8-byte (next, d_tau) states, or compensated
+//      double-float sums with link counts in the 16-byte counting form;
 //   4. each pair contributes L e^-tau / (4 pi r^2).
 // Count-1 source cells and their single member are the same source and
 // share one chain forest.
