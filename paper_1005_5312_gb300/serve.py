@@ -100,6 +100,16 @@ class _Worker:
     busy: bool = False
 
 
+def request_knobs(req, reuse_fixed: bool = False, tuner=None) -> dict:
+    """Parameters a worker sets before serving req: resident chains only for
+    a request of several coupled steps (unless the server fixed them), and
+    the tuner's knobs of the request's problem class."""
+    knobs = {} if reuse_fixed else {"reuse_chains": int(req.steps > 1)}
+    if tuner is not None:
+        knobs.update(tuner.params_for(req.n_p, req.n_s, req.theta))
+    return knobs
+
+
 class Server:
     """FIFO admission by worker slots and a device-memory budget."""
 
@@ -140,9 +150,7 @@ class Server:
         w.ctx = Context(stream=w.stream, **self.params)
 
     def _run(self, ctx, req: SolveRequest):
-        knobs = {} if self.reuse_fixed else {"reuse_chains": int(req.steps > 1)}
-        if self.tuner is not None:
-            knobs.update(self.tuner.params_for(req.n_p, req.n_s, req.theta))
+        knobs = request_knobs(req, self.reuse_fixed, self.tuner)
         if knobs:
             ctx.set_params(**knobs)
         ctx.build_trees(req.pos, req.h, req.src_pos, req.src_L)

@@ -31,6 +31,22 @@ def test_memory_estimate_is_monotone_and_capped():
     assert d < memory_estimate(1 << 21, 1 << 20, 0.5, 1 << 40)   # the pair budget caps it
 
 
+def test_request_knobs_policy():
+    """Resident chains only for requests of several coupled steps (unless
+    fixed by the server); the tuner's knobs of the request's class on top."""
+    from paper_1005_5312_gb300.autotune import Tuner, problem_class
+    from paper_1005_5312_gb300.serve import make_requests, request_knobs
+    one, two = make_requests(2, log2_np=(12, 13), seed=5, steps=1)[0], \
+        make_requests(1, log2_np=(12, 13), seed=6, steps=2)[0]
+    assert request_knobs(one) == {"reuse_chains": 0}
+    assert request_knobs(two) == {"reuse_chains": 1}
+    assert request_knobs(two, reuse_fixed=True) == {}
+    t = Tuner()
+    t.cache[problem_class(one.n_p, one.n_s, one.theta)] = {"march_group": 4, "row_bins": 6}
+    k = request_knobs(one, tuner=t)
+    assert k["reuse_chains"] == 0 and k["march_group"] == 4 and k["row_bins"] == 6
+
+
 @pytest.mark.gpu
 def test_results_identical_alone_and_in_a_mix():
     torch = pytest.importorskip("torch")
