@@ -473,6 +473,18 @@ const char *start_status_string(int status);
  * against a budget with it). */
 long long start_memory_in_use(void);
 
+/* The direction bins of start_params.row_bins = N (host only, no device
+ * work): a source direction b (nonzero) falls in bin (f N + iu) N + iv,
+ * where f = 2 a + (b_a < 0) for the axis a of b's component of largest
+ * magnitude, and iu, iv = floor((s / |b_a| + 1) N / 2), clamped to [0, N),
+ * for the two other components (s, t) = (b_y, b_z), (b_z, b_x) or (b_x, b_y)
+ * on the x, y or z faces.  cones[8 k .. 8 k + 7] receives bin k's cone
+ * (unit axis x, y, z, cos rho, sin rho, rho, 0, 0): every direction of the
+ * bin lies within rho of the axis (the largest angle to a corner of the
+ * bin, widened by 2e-3 rad).  cones holds 48 N^2 floats.  START_EINVAL for
+ * N outside 2..6 or a NULL array. */
+int start_direction_bins(int N, float *cones);
+
 /* ---- allocation-free Morton ordering (no counterpart in the paper) ----
  *
  * For callers that cannot let the library allocate device memory: codes

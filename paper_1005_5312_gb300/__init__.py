@@ -101,6 +101,7 @@ def lib():
             "start_status_string": (C.c_char_p, [i]),
             "start_morton_order_noalloc": (i, [vp, ll, vp, vp, vp, vp]),
             "start_memory_in_use": (ll, []),
+            "start_direction_bins": (i, [i, P(f)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

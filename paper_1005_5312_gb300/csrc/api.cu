@@ -1230,6 +1230,13 @@ const char *start_last_error(const start_ctx *c)
 
 long long start_memory_in_use(void) { return bytes_in_use(); }
 
+int start_direction_bins(int N, float *cones)
+{
+    if (N < 2 || N > 6 || !cones) return START_EINVAL;
+    direction_bin_cones(N, cones);
+    return START_OK;
+}
+
 const char *start_status_string(int s)
 {
     switch (s) {

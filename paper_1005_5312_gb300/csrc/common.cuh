@@ -241,6 +241,8 @@ inline bool memo_counts_links(const start_ctx *c)
     return c->p.link_counts != 0 || c->p.hop_cap > 0 || c->p.reuse_chains != 0;
 }
 
+void direction_bin_cones(int N, float *out);   // memo.cu; 8 floats per bin
+
 // ---------------------------------------------------------------- error helpers
 int set_err(start_ctx *c, int code, const std::string &msg);
 int cuda_check(start_ctx *c, cudaError_t e, const char *what);

@@ -1292,6 +1292,18 @@ static void bin_cones(int N, std::vector<float4> &g)
     }
 }
 
+// The cones as plain floats (start_direction_bins): 8 per bin.
+void direction_bin_cones(int N, float *out)
+{
+    std::vector<float4> g;
+    bin_cones(N, g);
+    for (size_t b = 0; b < g.size() / 2; ++b) {
+        const float4 a = g[2 * b], q = g[2 * b + 1];
+        const float v[8] = {a.x, a.y, a.z, a.w, q.x, q.y, 0.f, 0.f};
+        for (int k = 0; k < 8; ++k) out[8 * b + k] = v[k];
+    }
+}
+
 // The first hop's candidate sets of every particle for N = start_params.row_bins
 // (kept until the next build or a change of N).
 static int build_row_bins(start_ctx *c, const MarchArgs &m)

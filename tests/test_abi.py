@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -77,3 +78,56 @@ def test_stats_struct_layout_and_phases_match_header():
     assert [f for f, _ in S.StartStats._fields_] == fields
     n = int(re.search(r"#define START_NPHASES (\d+)", src).group(1))
     assert len(S.Context.PHASES) == n
+
+
+def _bins_by_rule(d, N):
+    """The binning rule of start_direction_bins, written from its description."""
+    a = np.argmax(np.abs(d), axis=1)
+    neg = d[np.arange(len(d)), a] < 0
+    f = 2 * a + neg
+    m = np.abs(d[np.arange(len(d)), a])
+    others = {0: (1, 2), 1: (2, 0), 2: (0, 1)}
+    s = np.empty(len(d))
+    t = np.empty(len(d))
+    for ax, (i, j) in others.items():
+        k = a == ax
+        s[k] = d[k, i]
+        t[k] = d[k, j]
+    iu = np.clip(np.floor((s / m + 1.0) * N / 2.0), 0, N - 1).astype(int)
+    iv = np.clip(np.floor((t / m + 1.0) * N / 2.0), 0, N - 1).astype(int)
+    return (f * N + iu) * N + iv
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6])
+def test_direction_bin_cones_contain_their_bins(libstart, N):
+    """Every sampled direction lies within its bin's cone (the pruning of
+    the upstream search is exact only if it does), and the cones are tight:
+    the farthest sampled direction of every bin is within a few degrees of
+    the cone's edge."""
+    import paper_1005_5312_gb300 as S
+    L = S.lib()
+    nb = 6 * N * N
+    cones = np.zeros(8 * nb, np.float32)
+    assert L.start_direction_bins(N, cones.ctypes.data_as(C.POINTER(C.c_float))) == S.START_OK
+    cones = cones.reshape(nb, 8).astype(np.float64)
+    axis, cr, sr, rho = cones[:, :3], cones[:, 3], cones[:, 4], cones[:, 5]
+    assert np.allclose(np.linalg.norm(axis, axis=1), 1.0, atol=1e-6)
+    assert np.allclose(np.cos(rho), cr, atol=1e-6) and np.allclose(np.sin(rho), sr, atol=1e-6)
+    rng = np.random.default_rng(N)
+    d = rng.normal(size=(400000, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    # plus the bins' corners and edges, where the cone is tightest
+    g = np.linspace(-1.0, 1.0, 2 * N + 1)
+    u, v = np.meshgrid(g, g)
+    face = np.stack([np.ones(u.size), u.ravel(), v.ravel()], axis=1)
+    extra = np.concatenate([np.roll(sg * face, r, axis=1) for r in range(3) for sg in (1, -1)])
+    d = np.concatenate([d, extra / np.linalg.norm(extra, axis=1)[:, None]])
+    b = _bins_by_rule(d, N)
+    ang = np.arccos(np.clip(np.sum(d * axis[b], axis=1), -1.0, 1.0))
+    assert np.all(ang <= rho[b] + 1e-6)
+    far = np.zeros(nb)
+    np.maximum.at(far, b, ang)
+    assert np.all(far >= rho - 2e-3 - 0.05)
+    assert np.bincount(b, minlength=nb).min() > 0
+    assert L.start_direction_bins(1, cones.ctypes.data_as(C.POINTER(C.c_float))) == S.START_EINVAL
+    assert L.start_direction_bins(N, None) == S.START_EINVAL
